@@ -1,0 +1,178 @@
+/*
+ * net.h — C ABI of the device-resident CNN forward-pass library (sm_103a).
+ *
+ * The paper (Yamato et al., Sec. 3.2) reduces CPU<->GPU traffic by hoisting
+ * every copy of a GPU loop's data to the outermost loop that does not touch
+ * it on the CPU, so that data moves once instead of once per loop.  This
+ * library takes that rule to its limit for the loop nests that dominate the
+ * Darknet workload the paper offloads (Sec. 5.1.1): the convolutional
+ * network forward pass.  Weights are uploaded once (net_load_weights); a
+ * frame crosses host->device once and its result device->host once
+ * (net_forward); every activation in between stays in device memory.
+ *
+ * Layer semantics (conv stride 1, pad k/2; batchnorm folded into the
+ * weights; bias; leaky rectifier 0.1 or linear; optional 2x2 max pool) are
+ * the plain definitions of a Darknet convolutional layer; the paper prints
+ * none of them.
+ *
+ * Conventions for every entry point:
+ *  - Host buffers are owned by the caller and only read/written during the
+ *    call (net_submit copies the frame before returning).
+ *  - Device pointers ("d_" prefix) are CUDA device addresses on the
+ *    handle's device, owned by the caller, used in stream order on the
+ *    handle's stream.
+ *  - Frames are NCHW float32, C = in_c; results are NCHW float32 with the
+ *    last layer's channel count and the spatial size after all pools.
+ *  - Every call returns a net_status; nothing aborts.  The message of the
+ *    last failure on the calling thread is available from net_last_error.
+ *  - A handle is not safe for concurrent net_forward* calls; the request
+ *    queue entry points (net_submit .. net_stats) are thread-safe.
+ */
+#ifndef NET_H_
+#define NET_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct net net_t;
+
+typedef enum {
+    NET_OK = 0,
+    NET_E_INVAL = 1,       /* bad argument (NULL, size, capacity)            */
+    NET_E_SHAPE = 2,       /* frame shape outside what the handle supports   */
+    NET_E_WEIGHTS = 3,     /* blob length mismatch / weights not loaded      */
+    NET_E_OOM = 4,         /* device allocation failed                       */
+    NET_E_BUDGET = 5,      /* request needs more than the HBM budget         */
+    NET_E_TIMEOUT = 6,     /* net_wait timed out                             */
+    NET_E_CUDA = 7,        /* a CUDA call failed (message kept)              */
+    NET_E_DEVICE_WAIT = 8, /* a bounded device-side wait gave up             */
+    NET_E_STATE = 9,       /* call not valid in the handle's current state   */
+    NET_E_UNSUPPORTED = 10 /* configuration not built into this library      */
+} net_status;
+
+typedef enum { NET_FP32 = 0, NET_BF16 = 1, NET_FP8 = 2 } net_precision;
+typedef enum { NET_ACT_LINEAR = 0, NET_ACT_LEAKY = 1 } net_act;
+typedef enum { NET_POOL_NONE = 0, NET_POOL_2X2S2 = 1, NET_POOL_2X2S1_SAME = 2 } net_pool;
+
+/* One convolutional layer: k in {1,3}, stride 1, zero pad k/2.
+ * bn != 0: batchnorm (running statistics) folded into W and bias;
+ * act: NET_ACT_*; pool: NET_POOL_* (2x2 stride 2 needs even H, W; the
+ * stride-1 "same" pool keeps the size, its window clipped at bottom/right). */
+typedef struct {
+    int k, cout, bn, act, pool;
+} net_layer;
+
+typedef struct {
+    int in_c;                 /* frame channels                                  */
+    int n_layers;
+    const net_layer* layers;  /* copied by net_create                            */
+    int prec;                 /* net_precision of the conv operands (bulk)       */
+    const int* layer_prec;    /* optional per-layer net_precision, or NULL       */
+    int max_batch;            /* largest batch for net_forward*                  */
+    int max_side;             /* largest frame height/width                      */
+    size_t hbm_budget_bytes;  /* activation budget of the request queue; 0: 40 GB */
+    void* cuda_stream;        /* cudaStream_t used for all work; NULL: own stream */
+    int device;               /* CUDA device ordinal                             */
+} net_desc;
+
+/* Creates a handle: validates the layer list, plans the device activation
+ * arena for (max_batch, max_side) and allocates it.  *out is set on NET_OK. */
+net_status net_create(const net_desc* desc, net_t** out);
+
+/* Uploads the float32 weight blob (host, caller-owned, copied once) and
+ * folds it on the device in FP64: s = gamma/sqrt(var+1e-5), W' = W*s,
+ * b' = beta - mean*s, then reorders W' to [cout][kh][kw][cin] and casts it
+ * to each layer's precision (FP8: per-output-channel scale max|W'_o|/448).
+ * Blob layout per layer: [beta, gamma, mean, var] (cout each) if bn, else
+ * [bias] (cout); then W as [cout][cin][k][k].  n_floats must equal the
+ * layers' total, else NET_E_WEIGHTS. */
+net_status net_load_weights(net_t* net, const float* blob, size_t n_floats);
+
+/* FP8 layers: static per-tensor scale of each layer's input activation
+ * (value = code * scale).  scales has n = n_layers entries (host). */
+net_status net_set_act_scales(net_t* net, const float* scales, int n);
+
+/* Measures FP8 activation scales on the device: runs the FP32 copy of the
+ * folded weights over the caller's frames (device NCHW float32) and sets
+ * scale_l = max|input of layer l| / 448.  Writes them to scales_out (host,
+ * n_layers floats) when it is not NULL. */
+net_status net_calibrate(net_t* net, const float* d_frames, int batch, int h, int w,
+                         float* scales_out);
+
+/* Output shape of the network for an h x w frame. */
+net_status net_output_shape(const net_t* net, int h, int w, int* c, int* ho, int* wo);
+
+/* Synchronous forward pass from host memory: one host->device copy of the
+ * batch, the whole network on the device, one device->host copy of the
+ * result.  out_cap_floats must hold batch*c*ho*wo floats. */
+net_status net_forward(net_t* net, const float* in_nchw, int batch, int h, int w,
+                       float* out_nchw, size_t out_cap_floats);
+
+/* Stream-ordered forward pass between device buffers (no host copies, no
+ * synchronisation). */
+net_status net_forward_device(net_t* net, const float* d_in, int batch, int h, int w,
+                              float* d_out);
+
+/* As net_forward_device, and also writes every layer's output (after its
+ * pool) as NCHW float32 into d_layer_out[l] (device pointers, one per
+ * layer, each sized for that layer's output).  Diagnostic path. */
+net_status net_forward_trace(net_t* net, const float* d_in, int batch, int h, int w,
+                             float* const* d_layer_out);
+
+/* Uneven batch: n frames of different square sides in one pass.  Frame i
+ * is d_in[i] (1 x in_c x side[i] x side[i], device) and its result goes to
+ * d_out[i].  Every layer of every frame runs in one grouped launch per
+ * layer (frames share no reduction, so each result equals the frame's own
+ * net_forward_device result bit for bit).  Stream-ordered. */
+net_status net_forward_uneven(net_t* net, const float* const* d_in, const int* side, int n,
+                              float* const* d_out);
+
+/* ---- request queue (continuous batching) ------------------------------
+ * net_submit copies one frame (host NCHW float32, 1 x in_c x h x w) into a
+ * pinned staging slot and returns a request id.  A scheduler thread admits
+ * queued requests while slots and the HBM activation budget allow, and
+ * advances every admitted request by one layer per step in one grouped
+ * launch; requests arriving while others run join at the next step.  A
+ * frame whose activations exceed the whole budget fails with NET_E_BUDGET. */
+net_status net_submit(net_t* net, const float* frame, int h, int w, uint64_t* req_id);
+
+/* Non-blocking: *done = 1 and the result copied to out when finished. */
+net_status net_poll(net_t* net, uint64_t req_id, float* out, size_t cap_floats, int* done);
+
+/* Blocks up to timeout_ms (negative: forever); NET_E_TIMEOUT if not done. */
+net_status net_wait(net_t* net, uint64_t req_id, float* out, size_t cap_floats, int timeout_ms);
+
+/* Completed-request statistics since the queue started: throughput and
+ * latency percentiles (completion minus submission). */
+net_status net_stats(net_t* net, double* fps, double* p50_ms, double* p99_ms);
+
+/* Per-layer timing: with enable != 0 every later forward pass records a
+ * CUDA event pair around each layer's conv kernel (on the handle's stream;
+ * CUDA-graph replays record them too).  net_layer_times waits for the most
+ * recent pass and writes each layer's conv-kernel time in milliseconds to
+ * ms_out (host, n = n_layers entries). */
+net_status net_profile(net_t* net, int enable);
+net_status net_layer_times(net_t* net, double* ms_out, int n);
+
+/* Total number of kernels this handle has launched (a CUDA-graph replay
+ * counts every kernel node in the graph). */
+net_status net_launches(const net_t* net, uint64_t* total);
+
+/* Releases every device and host resource of the handle (stops the
+ * scheduler thread first).  NULL is accepted. */
+net_status net_free(net_t* net);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* net_last_error(void);
+
+/* Library build identification string (static). */
+const char* net_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NET_H_ */

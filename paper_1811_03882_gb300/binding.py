@@ -1,0 +1,230 @@
+"""ctypes binding of libnet.so (include/net.h): argument marshalling only.
+
+Every step of the forward pass runs in the library's CUDA kernels; this
+module only converts Python/NumPy/torch arguments into the C ABI's plain
+pointers and sizes.  If libnet.so is missing the import of ``lib()`` raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnet.so")
+
+NET_OK, NET_E_INVAL, NET_E_SHAPE, NET_E_WEIGHTS, NET_E_OOM, NET_E_BUDGET = 0, 1, 2, 3, 4, 5
+NET_E_TIMEOUT, NET_E_CUDA, NET_E_DEVICE_WAIT, NET_E_STATE, NET_E_UNSUPPORTED = 6, 7, 8, 9, 10
+NET_FP32, NET_BF16, NET_FP8 = 0, 1, 2
+PREC = {"fp32": NET_FP32, "bf16": NET_BF16, "fp8": NET_FP8}
+
+STATUS_NAMES = {0: "NET_OK", 1: "NET_E_INVAL", 2: "NET_E_SHAPE", 3: "NET_E_WEIGHTS", 4: "NET_E_OOM",
+                5: "NET_E_BUDGET", 6: "NET_E_TIMEOUT", 7: "NET_E_CUDA", 8: "NET_E_DEVICE_WAIT",
+                9: "NET_E_STATE", 10: "NET_E_UNSUPPORTED"}
+
+
+class NetError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class net_layer(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("cout", ctypes.c_int), ("bn", ctypes.c_int),
+                ("act", ctypes.c_int), ("pool", ctypes.c_int)]
+
+
+class net_desc(ctypes.Structure):
+    _fields_ = [("in_c", ctypes.c_int), ("n_layers", ctypes.c_int),
+                ("layers", ctypes.POINTER(net_layer)), ("prec", ctypes.c_int),
+                ("layer_prec", ctypes.POINTER(ctypes.c_int)), ("max_batch", ctypes.c_int),
+                ("max_side", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "net_create": [ctypes.POINTER(net_desc), ctypes.POINTER(ctypes.c_void_p)],
+    "net_load_weights": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
+    "net_set_act_scales": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
+    "net_calibrate": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                      ctypes.c_void_p],
+    "net_output_shape": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "net_forward": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                    ctypes.c_void_p, ctypes.c_size_t],
+    "net_forward_device": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_void_p],
+    "net_forward_trace": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_void_p],
+    "net_forward_uneven": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                           ctypes.c_void_p],
+    "net_submit": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                   ctypes.POINTER(ctypes.c_uint64)],
+    "net_poll": [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t,
+                 ctypes.POINTER(ctypes.c_int)],
+    "net_wait": [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int],
+    "net_stats": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                  ctypes.POINTER(ctypes.c_double)],
+    "net_profile": [ctypes.c_void_p, ctypes.c_int],
+    "net_layer_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
+    "net_launches": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
+    "net_free": [ctypes.c_void_p],
+    "net_last_error": [],
+    "net_version": [],
+}
+
+
+def lib():
+    """Loads libnet.so (built by paper_1811_03882_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libnet.so not built: run paper_1811_03882_gb300.build.build() "
+                                   "(the CUDA library is the only implementation)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = ctypes.c_char_p if name in ("net_last_error", "net_version") else ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().net_last_error().decode()
+
+
+def check(status: int):
+    if status != NET_OK:
+        raise NetError(status, last_error())
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        return ctypes.c_void_p(a.ctypes.data)
+    return ctypes.c_void_p(int(a))
+
+
+class Net:
+    """Owning wrapper of a net_t handle."""
+
+    def __init__(self, layers, in_c: int, prec="fp32", layer_prec=None, max_batch: int = 1,
+                 max_side: int = 416, stream=None, budget_bytes: int = 0, device: int = 0):
+        L = lib()
+        self._layers = (net_layer * len(layers))(
+            *[net_layer(l.k, l.cout, int(l.bn), l.act, l.pool) for l in layers])
+        self.n_layers = len(layers)
+        self.layers = list(layers)
+        self.in_c = in_c
+        lp = None
+        if layer_prec is not None:
+            self._lp = (ctypes.c_int * len(layers))(*[PREC.get(p, p) for p in layer_prec])
+            lp = ctypes.cast(self._lp, ctypes.POINTER(ctypes.c_int))
+        d = net_desc(in_c, len(layers), ctypes.cast(self._layers, ctypes.POINTER(net_layer)),
+                     PREC.get(prec, prec), lp, max_batch, max_side, budget_bytes,
+                     ctypes.c_void_p(stream) if stream else None, device)
+        h = ctypes.c_void_p()
+        check(L.net_create(ctypes.byref(d), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().net_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def load_weights(self, blob: np.ndarray):
+        blob = np.ascontiguousarray(blob, dtype=np.float32)
+        check(lib().net_load_weights(self.h, _ptr(blob), blob.size))
+
+    def set_act_scales(self, scales):
+        s = np.ascontiguousarray(scales, dtype=np.float32)
+        check(lib().net_set_act_scales(self.h, _ptr(s), s.size))
+
+    def calibrate(self, d_frames, batch, h, w) -> np.ndarray:
+        out = np.zeros(self.n_layers, np.float32)
+        check(lib().net_calibrate(self.h, _ptr(d_frames), batch, h, w, _ptr(out)))
+        return out
+
+    def output_shape(self, h: int, w: int):
+        c, ho, wo = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(lib().net_output_shape(self.h, h, w, ctypes.byref(c), ctypes.byref(ho), ctypes.byref(wo)))
+        return c.value, ho.value, wo.value
+
+    def forward(self, x: np.ndarray, out: np.ndarray = None) -> np.ndarray:
+        """Host NCHW float32 in -> host NCHW float32 out (1 H2D + 1 D2H)."""
+        n, _, h, w = x.shape
+        c, ho, wo = self.output_shape(h, w)
+        if out is None:
+            out = np.empty((n, c, ho, wo), np.float32)
+        check(lib().net_forward(self.h, _ptr(x), n, h, w, _ptr(out), out.size))
+        return out
+
+    def forward_device(self, d_in, batch, h, w, d_out):
+        check(lib().net_forward_device(self.h, _ptr(d_in), batch, h, w, _ptr(d_out)))
+
+    def forward_trace(self, d_in, batch, h, w, d_layer_outs):
+        arr = (ctypes.c_void_p * len(d_layer_outs))(*[t.data_ptr() for t in d_layer_outs])
+        check(lib().net_forward_trace(self.h, _ptr(d_in), batch, h, w, arr))
+
+    def forward_uneven(self, d_ins, sides, d_outs):
+        n = len(d_ins)
+        a = (ctypes.c_void_p * n)(*[t.data_ptr() for t in d_ins])
+        s = (ctypes.c_int * n)(*[int(v) for v in sides])
+        o = (ctypes.c_void_p * n)(*[t.data_ptr() for t in d_outs])
+        check(lib().net_forward_uneven(self.h, a, s, n, o))
+
+    def submit(self, frame: np.ndarray) -> int:
+        rid = ctypes.c_uint64()
+        _, _, h, w = frame.shape
+        check(lib().net_submit(self.h, _ptr(frame), h, w, ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, rid: int, out: np.ndarray) -> bool:
+        done = ctypes.c_int()
+        check(lib().net_poll(self.h, rid, _ptr(out), out.size, ctypes.byref(done)))
+        return bool(done.value)
+
+    def wait(self, rid: int, out: np.ndarray, timeout_ms: int = -1):
+        check(lib().net_wait(self.h, rid, _ptr(out), out.size, timeout_ms))
+
+    def profile(self, enable: bool = True):
+        check(lib().net_profile(self.h, int(enable)))
+
+    def layer_times(self) -> np.ndarray:
+        ms = np.zeros(self.n_layers, np.float64)
+        check(lib().net_layer_times(self.h, _ptr(ms), self.n_layers))
+        return ms
+
+    def launches(self) -> int:
+        t = ctypes.c_uint64()
+        check(lib().net_launches(self.h, ctypes.byref(t)))
+        return t.value
+
+    def stats(self):
+        f, p50, p99 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        check(lib().net_stats(self.h, ctypes.byref(f), ctypes.byref(p50), ctypes.byref(p99)))
+        return f.value, p50.value, p99.value

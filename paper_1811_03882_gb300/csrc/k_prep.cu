@@ -1,0 +1,230 @@
+// k_prep.cu — memory-bound helper kernels: frame pack, result unpack,
+// stride-1 "same" max pool, one-time FP64 batchnorm fold and FP8 weight
+// quantisation, FP8 scale helpers.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dn {
+
+static inline unsigned grid_for(size_t n, int threads) {
+    size_t b = (n + threads - 1) / threads;
+    if (b > 152u * 32u) b = 152u * 32u;   // grid-stride beyond 32 CTAs per SM
+    return (unsigned)(b ? b : 1);
+}
+
+// ---------------------------------------------------------------- pack
+template <int DT>
+__global__ void pack_kernel(const float* __restrict__ x, void* __restrict__ y, int n, int C, int H,
+                            int W, int Cp, float inv_scale) {
+    constexpr int V = DT == DT_F32 ? 4 : DT == DT_BF16 ? 8 : 16;   // elements per 16 B
+    const int groups = Cp / V;
+    const size_t HW = (size_t)H * W;
+    const size_t total = (size_t)n * HW * groups;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int g = (int)(i % groups);
+        const size_t pix = i / groups;          // n*HW + yx
+        const size_t nn = pix / HW, yx = pix % HW;
+        float v[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const int c = g * V + j;
+            v[j] = c < C ? x[(nn * C + c) * HW + yx] : 0.f;
+        }
+        uint8_t* dst = reinterpret_cast<uint8_t*>(y) + (pix * Cp + (size_t)g * V) * dt_size(DT);
+        if (DT == DT_F32) {
+            *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+        } else if (DT == DT_BF16) {
+            uint4 pk;
+            uint32_t* p = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                p[j] = *reinterpret_cast<uint32_t*>(&b);
+            }
+            *reinterpret_cast<uint4*>(dst) = pk;
+        } else {
+            uint4 pk;
+            uint8_t* p = reinterpret_cast<uint8_t*>(&pk);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) p[j] = f32_to_e4m3_sat(v[j] * inv_scale);
+            *reinterpret_cast<uint4*>(dst) = pk;
+        }
+    }
+}
+
+cudaError_t pack_frames(const float* x, void* y, int n, int C, int H, int W, int Cp, int dt,
+                        float inv_scale, cudaStream_t st) {
+    const int V = dt == DT_F32 ? 4 : dt == DT_BF16 ? 8 : 16;
+    const size_t total = (size_t)n * H * W * (Cp / V);
+    const unsigned g = grid_for(total, 256);
+    if (dt == DT_F32) pack_kernel<DT_F32><<<g, 256, 0, st>>>(x, y, n, C, H, W, Cp, inv_scale);
+    else if (dt == DT_BF16) pack_kernel<DT_BF16><<<g, 256, 0, st>>>(x, y, n, C, H, W, Cp, inv_scale);
+    else pack_kernel<DT_FP8><<<g, 256, 0, st>>>(x, y, n, C, H, W, Cp, inv_scale);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- unpack
+__device__ __forceinline__ float load_as_f32(const void* base, size_t i, int dt, float scale) {
+    if (dt == DT_F32) return reinterpret_cast<const float*>(base)[i];
+    if (dt == DT_BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(base)[i]);
+    return e4m3_to_f32(reinterpret_cast<const uint8_t*>(base)[i]) * scale;
+}
+
+__global__ void unpack_kernel(const void* __restrict__ x, float* __restrict__ y, int n, int C, int H,
+                              int W, int cs, int dt, float scale) {
+    const size_t HW = (size_t)H * W, total = (size_t)n * C * HW;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t yx = i % HW, nc = i / HW;
+        const int c = (int)(nc % C);
+        const size_t nn = nc / C;
+        y[i] = load_as_f32(x, (nn * HW + yx) * cs + c, dt, scale);
+    }
+}
+
+cudaError_t unpack_nchw(const void* x, float* y, int n, int C, int H, int W, int cs, int dt,
+                        float scale, cudaStream_t st) {
+    const size_t total = (size_t)n * C * H * W;
+    unpack_kernel<<<grid_for(total, 256), 256, 0, st>>>(x, y, n, C, H, W, cs, dt, scale);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- s1 "same" pool
+// out(i,j) = max over rows i..i+1, cols j..j+1 inside the image.  Max of
+// values in one storage format is one of them, so no re-rounding happens.
+__device__ __forceinline__ float dec(const uint8_t* p, int j, int dt) {
+    if (dt == DT_F32) return reinterpret_cast<const float*>(p)[j];
+    if (dt == DT_BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[j]);
+    return e4m3_to_f32(p[j]);
+}
+
+__global__ void pool_s1_kernel(const uint8_t* __restrict__ x, uint8_t* __restrict__ y, int n, int H,
+                               int W, int cs, int dt) {
+    const int esz = dt == DT_F32 ? 4 : dt == DT_BF16 ? 2 : 1;
+    const int V = 16 / esz;
+    const int groups = cs / V;
+    const size_t total = (size_t)n * H * W * groups;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int g = (int)(i % groups);
+        size_t pix = i / groups;
+        const int xx = (int)(pix % W);
+        const int yy = (int)((pix / W) % H);
+        const size_t rowb = (size_t)cs * esz;
+        const uint8_t* p00 = x + pix * rowb + (size_t)g * 16;
+        uint4 best = *reinterpret_cast<const uint4*>(p00);
+        for (int d = 1; d < 4; ++d) {
+            const int dy = d >> 1, dx = d & 1;
+            if (yy + dy >= H || xx + dx >= W) continue;
+            const uint8_t* q = p00 + ((size_t)dy * W + dx) * rowb;
+            uint4 cand = *reinterpret_cast<const uint4*>(q);
+            uint8_t* bb = reinterpret_cast<uint8_t*>(&best);
+            const uint8_t* cb = reinterpret_cast<const uint8_t*>(&cand);
+            for (int j = 0; j < V; ++j)
+                if (dec(cb, j, dt) > dec(bb, j, dt))
+                    for (int b = 0; b < esz; ++b) bb[j * esz + b] = cb[j * esz + b];
+        }
+        *reinterpret_cast<uint4*>(y + pix * rowb + (size_t)g * 16) = best;
+    }
+}
+
+cudaError_t maxpool_s1_same(const void* x, void* y, int n, int H, int W, int cs, int dt,
+                            cudaStream_t st) {
+    const int V = 16 / (int)dt_size(dt);
+    const size_t total = (size_t)n * H * W * (cs / V);
+    pool_s1_kernel<<<grid_for(total, 256), 256, 0, st>>>(reinterpret_cast<const uint8_t*>(x),
+                                                         reinterpret_cast<uint8_t*>(y), n, H, W, cs, dt);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- fold
+// One block per output channel: s_o, b'_o and max|W'_o| in FP64.
+__global__ void fold_scale_kernel(FoldArgs a) {
+    const int o = blockIdx.x;
+    const bool bn = a.gamma != nullptr;
+    const double s = bn ? (double)a.gamma[o] / sqrt((double)a.var[o] + kBnEps) : 1.0;
+    const int fan = a.cin * a.k * a.k;
+    const float* wr = a.raw_w + (size_t)o * fan;
+    double m = 0.0;
+    for (int i = threadIdx.x; i < fan; i += blockDim.x) m = fmax(m, fabs((double)wr[i] * s));
+    __shared__ double red[32];
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
+        m = fmax(m, red[0]);
+        a.tmp_s[o] = s;
+        a.tmp_amax[o] = m;
+        const double b = bn ? (double)a.beta[o] - (double)a.mean[o] * s : (double)a.bias[o];
+        a.out_bias[o] = (float)b;
+        if (a.out_wscale) a.out_wscale[o] = (float)(fmax(m, 1e-30) / (double)kFp8Max);
+    }
+}
+
+// One thread per element of the [w_rows][k*k][Cp] output: reorder + cast.
+__global__ void fold_write_kernel(FoldArgs a) {
+    const int KK = a.k * a.k;
+    const size_t total = (size_t)a.w_rows * KK * a.Cp;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % a.Cp);
+        const int tap = (int)((i / a.Cp) % KK);
+        const int o = (int)(i / ((size_t)a.Cp * KK));
+        double v = 0.0;
+        if (o < a.cout && c < a.cin) {
+            const int kh = tap / a.k, kw = tap % a.k;
+            v = (double)a.raw_w[(((size_t)o * a.cin + c) * a.k + kh) * a.k + kw] * a.tmp_s[o];
+        }
+        if (a.dt == DT_F32) {
+            reinterpret_cast<float*>(a.out_w)[i] = (float)v;
+        } else if (a.dt == DT_BF16) {
+            reinterpret_cast<__nv_bfloat16*>(a.out_w)[i] = __double2bfloat16(v);
+        } else {
+            const double sw = (o < a.cout) ? fmax(a.tmp_amax[o], 1e-30) / (double)kFp8Max : 1.0;
+            reinterpret_cast<uint8_t*>(a.out_w)[i] =
+                (uint8_t)__nv_cvt_double_to_fp8(v / sw, __NV_SATFINITE, __NV_E4M3);
+        }
+        if (a.out_w32 && c < a.Cp32)
+            a.out_w32[((size_t)o * KK + tap) * a.Cp32 + c] = (float)v;
+    }
+    // channels [Cp, Cp32) of the FP32 copy (when it is wider) stay zero:
+    // the caller zero-fills it.
+}
+
+cudaError_t fold_layer(const FoldArgs& a, cudaStream_t st) {
+    fold_scale_kernel<<<a.cout, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t total = (size_t)a.w_rows * a.k * a.k * a.Cp;
+    fold_write_kernel<<<grid_for(total, 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void alpha_kernel(const float* wscale, double act_scale, float* alpha, int cout) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o < cout) alpha[o] = (float)((double)wscale[o] * act_scale);
+}
+
+cudaError_t make_alpha(const float* wscale, double act_scale, float* alpha, int cout,
+                       cudaStream_t st) {
+    alpha_kernel<<<cdiv(cout, 256), 256, 0, st>>>(wscale, act_scale, alpha, cout);
+    return cudaGetLastError();
+}
+
+__global__ void absmax_kernel(const float* __restrict__ x, size_t count, float* out) {
+    float m = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
+}
+
+cudaError_t absmax_f32(const float* x, size_t count, float* out, cudaStream_t st) {
+    absmax_kernel<<<grid_for(count, 256), 256, 0, st>>>(x, count, out);
+    return cudaGetLastError();
+}
+
+}  // namespace dn

@@ -1,0 +1,67 @@
+// kernels.h — internal launchers (C++), called by the executor in net.cu.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "common.cuh"
+
+namespace dn {
+
+// One conv layer over a batch of n equal frames, NHWC in / out.
+struct ConvLaunch {
+    const void* x;   // input activation, NHWC, channel stride Cp, dtype of the layer
+    const void* w;   // folded weights [w_rows][k*k][Cp], dtype of the layer
+    void* y;         // output (layout/dtype per ep)
+    int n, H, W;     // batch and (pre-pool) spatial size
+    int Cp;          // padded input channels
+    int k;           // 1 or 3
+    int w_rows;      // allocated weight rows (>= every column a tile touches)
+    Epilogue ep;
+};
+
+cudaError_t conv_simt(const ConvLaunch& L, cudaStream_t st);
+
+// Frame NCHW float32 -> NHWC (channel stride Cp, zero padded) in dtype dt;
+// FP8 codes are value * inv_scale.
+cudaError_t pack_frames(const float* x, void* y, int n, int C, int H, int W, int Cp, int dt,
+                        float inv_scale, cudaStream_t st);
+
+// NHWC (dtype dt, channel stride cs, value = code*scale for FP8) -> NCHW f32.
+cudaError_t unpack_nchw(const void* x, float* y, int n, int C, int H, int W, int cs, int dt,
+                        float scale, cudaStream_t st);
+
+// 2x2 stride-1 max pool, window clipped at the bottom/right edge, NHWC.
+cudaError_t maxpool_s1_same(const void* x, void* y, int n, int H, int W, int cs, int dt,
+                            cudaStream_t st);
+
+// Batchnorm fold and cast of one layer, FP64 on the device.
+//  raw_w: [cout][cin][k][k] f32; bn arrays (or bias) f32, device.
+//  out_w: [w_rows][k*k][Cp] in dt (zero padded); out_bias[cout] f32;
+//  out_wscale[cout] (FP8 per-channel weight scale, may be null otherwise);
+//  out_w32: optional FP32 copy of W' in the same layout (Cp32 channels).
+struct FoldArgs {
+    const float* raw_w;
+    const float *beta, *gamma, *mean, *var, *bias;  // bn: first four; else bias
+    int cout, cin, k, Cp, w_rows, dt;
+    void* out_w;
+    float* out_bias;
+    float* out_wscale;
+    double* tmp_s;      // [cout] scratch: per-channel BN scale
+    double* tmp_amax;   // [cout] scratch: per-channel max |W'|
+    float* out_w32;
+    int Cp32;
+};
+cudaError_t fold_layer(const FoldArgs& a, cudaStream_t st);
+
+// alpha[o] = (float)((double)wscale[o] * act_scale), FP8 layers.
+cudaError_t make_alpha(const float* wscale, double act_scale, float* alpha, int cout,
+                       cudaStream_t st);
+
+// max |x| over count floats, atomically folded into *out (out >= 0 floats).
+cudaError_t absmax_f32(const float* x, size_t count, float* out, cudaStream_t st);
+
+}  // namespace dn
+
+namespace dn {
+// Tensor-core conv (BF16 / FP8 operands in_dt, FP32 accumulation in TMEM).
+cudaError_t conv_tc(const ConvLaunch& L, int in_dt, cudaStream_t st);
+}  // namespace dn

@@ -1,0 +1,576 @@
+// net.cu — C ABI, layer-graph executor and device buffer planner.
+//
+// Data-transfer rule (paper, Sec. 3.2) taken to its limit: weights are
+// uploaded and folded once, a forward pass copies the frames to the device
+// once and the result back once, and every activation in between lives in
+// a ping-pong pair of device buffers planned at net_create for the largest
+// batch and frame side.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <memory>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/net.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "net_internal.h"
+
+using namespace dn;
+
+static thread_local std::string g_err;
+
+net_status dn::fail(net_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? NET_E_OOM : NET_E_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                 \
+    } while (0)
+
+// ------------------------------------------------------------- planning
+static int layer_engine(int prec, int cin) {
+    // Tensor cores need K chunks of >= 32 bytes of one tap; the 3-channel
+    // first layer (K = 27) runs on the CUDA cores in FP32 instead.
+    if (prec == NET_FP32) return ENG_SIMT;
+    return cin >= 16 ? ENG_TC : ENG_SIMT;
+}
+
+static int prec_dt(int prec) { return prec == NET_FP32 ? DT_F32 : prec == NET_BF16 ? DT_BF16 : DT_FP8; }
+
+// Spatial size of the input of every layer (and the final output) for h x w.
+void dn::layer_dims(const net* n, int h, int w, std::vector<int>& H, std::vector<int>& W) {
+    H.assign(n->L.size() + 1, 0);
+    W.assign(n->L.size() + 1, 0);
+    H[0] = h;
+    W[0] = w;
+    for (size_t l = 0; l < n->L.size(); ++l) {
+        const bool s2 = n->L[l].d.pool == NET_POOL_2X2S2;
+        H[l + 1] = s2 ? H[l] / 2 : H[l];
+        W[l + 1] = s2 ? W[l] / 2 : W[l];
+    }
+}
+
+net_status dn::check_shape(const net* n, int batch, int h, int w) {
+    if (batch < 1 || batch > n->max_batch)
+        return fail(NET_E_SHAPE, "batch %d outside [1, %d]", batch, n->max_batch);
+    if (h < 1 || w < 1 || h > n->max_side || w > n->max_side)
+        return fail(NET_E_SHAPE, "frame %dx%d outside [1, %d]", h, w, n->max_side);
+    int hh = h, ww = w;
+    for (size_t l = 0; l < n->L.size(); ++l) {
+        if (n->L[l].d.pool == NET_POOL_2X2S2) {
+            if ((hh & 1) || (ww & 1))
+                return fail(NET_E_SHAPE, "layer %zu: 2x2/s2 pool needs even size, got %dx%d", l, hh, ww);
+            hh /= 2;
+            ww /= 2;
+        }
+    }
+    return NET_OK;
+}
+
+size_t dn::act_bytes_for(const net* n, int batch, int h, int w) {
+    std::vector<int> H, W;
+    layer_dims(n, h, w, H, W);
+    size_t mx = 0;
+    for (size_t l = 0; l < n->L.size(); ++l) {
+        const Layer& L = n->L[l];
+        // input of layer l
+        mx = std::max(mx, (size_t)batch * H[l] * W[l] * L.in_cs * dt_size(L.in_dt));
+        // un-pooled output kept for the standalone stride-1 pool
+        if (L.d.pool == NET_POOL_2X2S1_SAME) {
+            const bool last = l + 1 == n->L.size();
+            const int cs = last ? rup(L.d.cout, 4) : n->L[l + 1].in_cs;
+            const int dt = last ? DT_F32 : n->L[l + 1].in_dt;
+            mx = std::max(mx, (size_t)batch * H[l + 1] * W[l + 1] * cs * dt_size(dt));
+        }
+    }
+    // the last layer's NHWC float32 output (trace / standalone pool paths)
+    const size_t nl = n->L.size();
+    mx = std::max(mx, (size_t)batch * H[nl] * W[nl] * rup(n->L.back().d.cout, 4) * 4);
+    return std::max((size_t)256, ((mx + 255) / 256) * 256);
+}
+
+extern "C" net_status net_create(const net_desc* d, net_t** out) {
+    if (!d || !out) return fail(NET_E_INVAL, "NULL argument");
+    *out = nullptr;
+    if (d->n_layers < 1 || !d->layers) return fail(NET_E_INVAL, "no layers");
+    if (d->in_c < 1 || d->in_c > 4096) return fail(NET_E_INVAL, "in_c %d", d->in_c);
+    if (d->max_batch < 1 || d->max_side < 1 || d->max_side > 8192)
+        return fail(NET_E_INVAL, "max_batch %d / max_side %d", d->max_batch, d->max_side);
+    if (d->prec < NET_FP32 || d->prec > NET_FP8) return fail(NET_E_INVAL, "precision %d", d->prec);
+    for (int l = 0; l < d->n_layers; ++l) {
+        const net_layer& s = d->layers[l];
+        const int p = d->layer_prec ? d->layer_prec[l] : d->prec;
+        if ((s.k != 1 && s.k != 3) || s.cout < 1 || s.cout > 16384 || s.act < 0 || s.act > 1 ||
+            s.pool < 0 || s.pool > 2 || s.bn < 0 || s.bn > 1)
+            return fail(NET_E_INVAL, "layer %d: unsupported (k=%d cout=%d bn=%d act=%d pool=%d)", l,
+                        s.k, s.cout, s.bn, s.act, s.pool);
+        if (p < NET_FP32 || p > NET_FP8) return fail(NET_E_INVAL, "layer %d precision %d", l, p);
+    }
+    std::unique_ptr<net> n(new net());
+    n->device = d->device;
+    CK(cudaSetDevice(n->device));
+    n->in_c = d->in_c;
+    n->max_batch = d->max_batch;
+    n->max_side = d->max_side;
+    n->budget = d->hbm_budget_bytes ? d->hbm_budget_bytes : (size_t)40 << 30;
+    int cin = d->in_c;
+    for (int l = 0; l < d->n_layers; ++l) {
+        const net_layer& s = d->layers[l];
+        Layer L;
+        L.d = s;
+        L.cin = cin;
+        L.prec = d->layer_prec ? d->layer_prec[l] : d->prec;
+        L.engine = layer_engine(L.prec, cin);
+        L.in_dt = L.engine == ENG_SIMT ? DT_F32 : prec_dt(L.prec);
+        L.in_cs = pad_channels(cin, L.in_dt, L.engine == ENG_TC);
+        L.w_rows = rup(std::max(s.cout, rup(s.cout, 128)), 256);
+        L.act_scale = 1.0;
+        n->L.push_back(L);
+        cin = s.cout;
+    }
+    for (auto& L : n->L)
+        if (L.prec == NET_FP8) n->has_fp8 = true;
+    if (d->cuda_stream) {
+        n->stream = (cudaStream_t)d->cuda_stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking));
+        n->own_stream = true;
+    }
+    n->act_bytes = act_bytes_for(n.get(), n->max_batch, n->max_side, n->max_side);
+    for (int i = 0; i < 2; ++i) {
+        CK(cudaMalloc(&n->act[i], n->act_bytes));
+        CK(cudaMemsetAsync(n->act[i], 0, n->act_bytes, n->stream));
+    }
+    int co, ho, wo;
+    net_output_shape(n.get(), n->max_side, n->max_side, &co, &ho, &wo);
+    n->in_stage_bytes = (size_t)n->max_batch * n->in_c * n->max_side * n->max_side * sizeof(float);
+    n->out_stage_bytes = (size_t)n->max_batch * co * ho * wo * sizeof(float);
+    CK(cudaMalloc(&n->d_in_stage, n->in_stage_bytes));
+    CK(cudaMalloc(&n->d_out_stage, n->out_stage_bytes));
+    CK(cudaStreamSynchronize(n->stream));
+    *out = n.release();
+    return NET_OK;
+}
+
+extern "C" net_status net_output_shape(const net_t* n, int h, int w, int* c, int* ho, int* wo) {
+    if (!n || !c || !ho || !wo) return fail(NET_E_INVAL, "NULL argument");
+    std::vector<int> H, W;
+    layer_dims(n, h, w, H, W);
+    *c = n->L.back().d.cout;
+    *ho = H.back();
+    *wo = W.back();
+    return NET_OK;
+}
+
+// ------------------------------------------------------------- weights
+extern "C" net_status net_load_weights(net_t* n, const float* blob, size_t n_floats) {
+    if (!n || !blob) return fail(NET_E_INVAL, "NULL argument");
+    size_t need = 0;
+    for (auto& L : n->L)
+        need += (size_t)L.d.cout * (L.d.bn ? 4 : 1) + (size_t)L.d.cout * L.cin * L.d.k * L.d.k;
+    if (n_floats != need)
+        return fail(NET_E_WEIGHTS, "weight blob has %zu floats, layers need %zu", n_floats, need);
+    CK(cudaSetDevice(n->device));
+    CK(cudaStreamSynchronize(n->stream));
+    float* d_blob = nullptr;
+    CK(cudaMalloc(&d_blob, need * sizeof(float)));
+    cudaError_t e = cudaMemcpyAsync(d_blob, blob, need * sizeof(float), cudaMemcpyHostToDevice, n->stream);
+    int maxc = 0;
+    for (auto& L : n->L) maxc = std::max(maxc, L.d.cout);
+    double* tmp = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, 2 * (size_t)maxc * sizeof(double));
+    size_t off = 0;
+    for (size_t l = 0; l < n->L.size() && e == cudaSuccess; ++l) {
+        Layer& L = n->L[l];
+        const int KK = L.d.k * L.d.k;
+        FoldArgs a{};
+        if (L.d.bn) {
+            a.beta = d_blob + off;
+            a.gamma = d_blob + off + L.d.cout;
+            a.mean = d_blob + off + 2 * L.d.cout;
+            a.var = d_blob + off + 3 * L.d.cout;
+            off += 4 * (size_t)L.d.cout;
+        } else {
+            a.bias = d_blob + off;
+            off += L.d.cout;
+        }
+        a.raw_w = d_blob + off;
+        off += (size_t)L.d.cout * L.cin * KK;
+        const int dt = L.in_dt;
+        const size_t wbytes = (size_t)L.w_rows * KK * L.in_cs * dt_size(dt);
+        if (!L.w) e = cudaMalloc(&L.w, wbytes);
+        if (e == cudaSuccess && !L.bias) e = cudaMalloc(&L.bias, L.d.cout * sizeof(float));
+        if (e == cudaSuccess && dt == DT_FP8 && !L.wscale) e = cudaMalloc(&L.wscale, L.d.cout * sizeof(float));
+        if (e == cudaSuccess && dt == DT_FP8 && !L.alpha) e = cudaMalloc(&L.alpha, L.d.cout * sizeof(float));
+        L.cs32 = rup(L.cin, 4);
+        const bool want32 = n->has_fp8 && dt != DT_F32;
+        if (e == cudaSuccess && want32 && !L.w32) {
+            e = cudaMalloc(&L.w32, (size_t)L.w_rows * KK * L.cs32 * sizeof(float));
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(L.w32, 0, (size_t)L.w_rows * KK * L.cs32 * sizeof(float), n->stream);
+        }
+        if (e != cudaSuccess) break;
+        a.cout = L.d.cout;
+        a.cin = L.cin;
+        a.k = L.d.k;
+        a.Cp = L.in_cs;
+        a.w_rows = L.w_rows;
+        a.dt = dt;
+        a.out_w = L.w;
+        a.out_bias = L.bias;
+        a.out_wscale = L.wscale;
+        a.tmp_s = tmp;
+        a.tmp_amax = tmp + maxc;
+        a.out_w32 = want32 ? L.w32 : nullptr;
+        a.Cp32 = L.cs32;
+        e = fold_layer(a, n->stream);
+        if (e == cudaSuccess && dt == DT_FP8) e = make_alpha(L.wscale, L.act_scale, L.alpha, L.d.cout, n->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+    cudaFree(d_blob);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return fail(NET_E_CUDA, "weight fold: %s", cudaGetErrorString(e));
+    n->weights_loaded = true;
+    n->graphs_clear();
+    return NET_OK;
+}
+
+extern "C" net_status net_set_act_scales(net_t* n, const float* scales, int cnt) {
+    if (!n || !scales) return fail(NET_E_INVAL, "NULL argument");
+    if (cnt != (int)n->L.size()) return fail(NET_E_INVAL, "need %zu scales, got %d", n->L.size(), cnt);
+    for (int l = 0; l < cnt; ++l)
+        if (!(scales[l] > 0.f) || !std::isfinite(scales[l]))
+            return fail(NET_E_INVAL, "scale %d = %g not positive finite", l, (double)scales[l]);
+    CK(cudaSetDevice(n->device));
+    for (int l = 0; l < cnt; ++l) {
+        Layer& L = n->L[l];
+        L.act_scale = scales[l];
+        if (L.in_dt == DT_FP8 && L.alpha && L.wscale) {
+            cudaError_t e = make_alpha(L.wscale, L.act_scale, L.alpha, L.d.cout, n->stream);
+            if (e != cudaSuccess) return fail(NET_E_CUDA, "alpha: %s", cudaGetErrorString(e));
+        }
+    }
+    CK(cudaStreamSynchronize(n->stream));
+    n->graphs_clear();
+    return NET_OK;
+}
+
+// ------------------------------------------------------------ executor
+// Input scale of layer l's storage for the FP8 format (1 otherwise).
+static float in_scale(const Layer& L) { return L.in_dt == DT_FP8 ? (float)L.act_scale : 1.f; }
+
+net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int w, float* d_out,
+                               float* const* trace, bool fp32_copy, float* amax) {
+    std::vector<int> H, W;
+    layer_dims(n, h, w, H, W);
+    cudaStream_t st = n->stream;
+    const int nl = (int)n->L.size();
+    auto in_dt = [&](int l) { return fp32_copy ? DT_F32 : n->L[l].in_dt; };
+    auto in_cs = [&](int l) { return fp32_copy ? n->L[l].cs32 : n->L[l].in_cs; };
+    void* buf[2] = {fp32_copy ? n->cal[0] : n->act[0], fp32_copy ? n->cal[1] : n->act[1]};
+    int cur = 0;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap);
+    auto mark = [&](cudaEvent_t ev) {
+        return cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                                    : cudaEventRecord(ev, st);
+    };
+    const bool prof = n->prof && !fp32_copy && (int)n->prof_ev.size() == 2 * nl;
+    n->pending = 1;
+    cudaError_t e = pack_frames(d_in, buf[cur], batch, n->in_c, h, w, in_cs(0), in_dt(0),
+                                1.f / in_scale(n->L[0]), st);
+    if (e != cudaSuccess) return fail(NET_E_CUDA, "pack: %s", cudaGetErrorString(e));
+    for (int l = 0; l < nl; ++l) {
+        const Layer& L = n->L[l];
+        const bool last = l + 1 == nl;
+        if (amax && e == cudaSuccess) {
+            ++n->pending;
+            e = absmax_f32(reinterpret_cast<const float*>(buf[cur]),
+                           (size_t)batch * H[l] * W[l] * in_cs(l), amax + l, st);
+        }
+        ConvLaunch c{};
+        c.x = buf[cur];
+        c.w = fp32_copy ? (const void*)L.w32 : L.w;
+        c.n = batch;
+        c.H = H[l];
+        c.W = W[l];
+        c.Cp = in_cs(l);
+        c.k = L.d.k;
+        c.w_rows = L.w_rows;
+        c.ep.bias = L.bias;
+        c.ep.alpha = (!fp32_copy && L.in_dt == DT_FP8) ? L.alpha : nullptr;
+        c.ep.act = L.d.act;
+        c.ep.pool = L.d.pool == NET_POOL_2X2S2 ? POOL_S2 : POOL_NONE;
+        c.ep.cout = L.d.cout;
+        const bool s1 = L.d.pool == NET_POOL_2X2S1_SAME;
+        const bool direct_nchw = last && !s1 && !trace;
+        if (direct_nchw) {
+            c.y = d_out;
+            c.ep.out_layout = LAYOUT_NCHW;
+            c.ep.out_dt = DT_F32;
+            c.ep.out_cs = L.d.cout;
+        } else {
+            c.y = buf[cur ^ 1];
+            c.ep.out_layout = LAYOUT_NHWC;
+            c.ep.out_dt = last ? DT_F32 : in_dt(l + 1);
+            c.ep.out_cs = last ? rup(L.d.cout, 4) : in_cs(l + 1);
+            c.ep.out_inv_scale = (!last && c.ep.out_dt == DT_FP8) ? 1.f / in_scale(n->L[l + 1]) : 1.f;
+        }
+        if (e == cudaSuccess && prof) e = mark(n->prof_ev[2 * l]);
+        if (e == cudaSuccess) {
+            ++n->pending;
+            if (!fp32_copy && L.engine == ENG_TC) e = conv_tc(c, L.in_dt, st);
+            else e = conv_simt(c, st);
+        }
+        if (e == cudaSuccess && prof) e = mark(n->prof_ev[2 * l + 1]);
+        if (e != cudaSuccess) return fail(NET_E_CUDA, "layer %d conv: %s", l, cudaGetErrorString(e));
+        if (direct_nchw) break;
+        const float osc = (last || c.ep.out_dt != DT_FP8) ? 1.f : in_scale(n->L[l + 1]);
+        if (s1) {
+            ++n->pending;
+            e = maxpool_s1_same(buf[cur ^ 1], buf[cur], batch, H[l + 1], W[l + 1], c.ep.out_cs,
+                                c.ep.out_dt, st);
+            // pooled result is back in buf[cur]
+        } else {
+            cur ^= 1;
+        }
+        if (e == cudaSuccess && (trace && trace[l]) && ++n->pending)
+            e = unpack_nchw(buf[cur], trace[l], batch, L.d.cout, H[l + 1], W[l + 1], c.ep.out_cs,
+                            c.ep.out_dt, osc, st);
+        if (e == cudaSuccess && last && ++n->pending)
+            e = unpack_nchw(buf[cur], d_out, batch, L.d.cout, H[l + 1], W[l + 1], c.ep.out_cs,
+                            c.ep.out_dt, osc, st);
+        if (e != cudaSuccess) return fail(NET_E_CUDA, "layer %d: %s", l, cudaGetErrorString(e));
+    }
+    return NET_OK;
+}
+
+void net::graphs_clear() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+    graph_kernels.clear();
+}
+
+net_status dn::run_forward(net* n, const float* d_in, int batch, int h, int w, float* d_out) {
+    if (!n->use_graphs) {
+        net_status s = enqueue_forward(n, d_in, batch, h, w, d_out, nullptr, false, nullptr);
+        if (s == NET_OK) n->launches += n->pending;
+        return s;
+    }
+    auto key = std::make_tuple(batch, h, w, (const void*)d_in, (const void*)d_out);
+    auto it = n->graphs.find(key);
+    if (it == n->graphs.end()) {
+        if (n->graphs.size() >= 64) n->graphs_clear();
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(n->stream, cudaStreamCaptureModeThreadLocal));
+        net_status s = enqueue_forward(n, d_in, batch, h, w, d_out, nullptr, false, nullptr);
+        cudaError_t e = cudaStreamEndCapture(n->stream, &g);
+        if (s != NET_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return fail(NET_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(NET_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        it = n->graphs.emplace(key, ex).first;
+        n->graph_kernels[key] = n->pending;
+    }
+    CK(cudaGraphLaunch(it->second, n->stream));
+    n->launches += n->graph_kernels[key];
+    return NET_OK;
+}
+
+extern "C" net_status net_forward_device(net_t* n, const float* d_in, int batch, int h, int w,
+                                         float* d_out) {
+    if (!n || !d_in || !d_out) return fail(NET_E_INVAL, "NULL argument");
+    if (!n->weights_loaded) return fail(NET_E_WEIGHTS, "weights not loaded");
+    net_status s = check_shape(n, batch, h, w);
+    if (s != NET_OK) return s;
+    CK(cudaSetDevice(n->device));
+    return run_forward(n, d_in, batch, h, w, d_out);
+}
+
+extern "C" net_status net_forward(net_t* n, const float* in, int batch, int h, int w, float* out,
+                                  size_t cap) {
+    if (!n || !in || !out) return fail(NET_E_INVAL, "NULL argument");
+    if (!n->weights_loaded) return fail(NET_E_WEIGHTS, "weights not loaded");
+    net_status s = check_shape(n, batch, h, w);
+    if (s != NET_OK) return s;
+    int c, ho, wo;
+    net_output_shape(n, h, w, &c, &ho, &wo);
+    const size_t nout = (size_t)batch * c * ho * wo;
+    if (cap < nout) return fail(NET_E_INVAL, "output capacity %zu < %zu floats", cap, nout);
+    CK(cudaSetDevice(n->device));
+    const size_t nin = (size_t)batch * n->in_c * h * w;
+    CK(cudaMemcpyAsync(n->d_in_stage, in, nin * sizeof(float), cudaMemcpyHostToDevice, n->stream));
+    s = run_forward(n, n->d_in_stage, batch, h, w, n->d_out_stage);
+    if (s != NET_OK) return s;
+    CK(cudaMemcpyAsync(out, n->d_out_stage, nout * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+    CK(cudaStreamSynchronize(n->stream));
+    return NET_OK;
+}
+
+extern "C" net_status net_forward_trace(net_t* n, const float* d_in, int batch, int h, int w,
+                                        float* const* d_layer_out) {
+    if (!n || !d_in || !d_layer_out) return fail(NET_E_INVAL, "NULL argument");
+    if (!n->weights_loaded) return fail(NET_E_WEIGHTS, "weights not loaded");
+    net_status s = check_shape(n, batch, h, w);
+    if (s != NET_OK) return s;
+    CK(cudaSetDevice(n->device));
+    net_status s2 = enqueue_forward(n, d_in, batch, h, w, d_layer_out[n->L.size() - 1], d_layer_out,
+                                    false, nullptr);
+    if (s2 == NET_OK) n->launches += n->pending;
+    return s2;
+}
+
+extern "C" net_status net_profile(net_t* n, int enable) {
+    if (!n) return fail(NET_E_INVAL, "NULL argument");
+    CK(cudaSetDevice(n->device));
+    CK(cudaStreamSynchronize(n->stream));
+    if (enable && n->prof_ev.empty()) {
+        n->prof_ev.resize(2 * n->L.size());
+        for (auto& ev : n->prof_ev) CK(cudaEventCreate(&ev));
+    }
+    n->prof = enable != 0;
+    n->graphs_clear();
+    return NET_OK;
+}
+
+extern "C" net_status net_layer_times(net_t* n, double* ms, int cnt) {
+    if (!n || !ms) return fail(NET_E_INVAL, "NULL argument");
+    if (cnt != (int)n->L.size()) return fail(NET_E_INVAL, "need %zu entries", n->L.size());
+    if (!n->prof) return fail(NET_E_STATE, "profiling not enabled");
+    CK(cudaStreamSynchronize(n->stream));
+    for (int l = 0; l < cnt; ++l) {
+        float t = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&t, n->prof_ev[2 * l], n->prof_ev[2 * l + 1]);
+        if (e != cudaSuccess) return fail(NET_E_STATE, "layer %d has no timing yet: %s", l, cudaGetErrorString(e));
+        ms[l] = t;
+    }
+    return NET_OK;
+}
+
+extern "C" net_status net_launches(const net_t* n, uint64_t* total) {
+    if (!n || !total) return fail(NET_E_INVAL, "NULL argument");
+    *total = n->launches;
+    return NET_OK;
+}
+
+extern "C" net_status net_calibrate(net_t* n, const float* d_frames, int batch, int h, int w,
+                                    float* scales_out) {
+    if (!n || !d_frames) return fail(NET_E_INVAL, "NULL argument");
+    if (!n->weights_loaded) return fail(NET_E_WEIGHTS, "weights not loaded");
+    if (!n->has_fp8) return fail(NET_E_STATE, "no FP8 layer to calibrate");
+    net_status s = check_shape(n, batch, h, w);
+    if (s != NET_OK) return s;
+    CK(cudaSetDevice(n->device));
+    // FP32 buffers for the calibration pass (FP32 copy of the folded weights)
+    std::vector<int> H, W;
+    layer_dims(n, h, w, H, W);
+    size_t mx = 0;
+    for (size_t l = 0; l < n->L.size(); ++l) {
+        mx = std::max(mx, (size_t)batch * H[l] * W[l] * n->L[l].cs32 * 4);
+        mx = std::max(mx, (size_t)batch * H[l + 1] * W[l + 1] * rup(n->L[l].d.cout, 4) * 4);
+    }
+    float *amax = nullptr, *dout = nullptr;
+    int c, ho, wo;
+    net_output_shape(n, h, w, &c, &ho, &wo);
+    CK(cudaMalloc(&n->cal[0], mx));
+    CK(cudaMalloc(&n->cal[1], mx));
+    CK(cudaMalloc(&amax, n->L.size() * sizeof(float)));
+    CK(cudaMalloc(&dout, (size_t)batch * c * ho * wo * sizeof(float)));
+    CK(cudaMemsetAsync(n->cal[0], 0, mx, n->stream));
+    CK(cudaMemsetAsync(n->cal[1], 0, mx, n->stream));
+    CK(cudaMemsetAsync(amax, 0, n->L.size() * sizeof(float), n->stream));
+    // layers whose own weights are FP32 use them directly
+    std::vector<float*> saved(n->L.size());
+    for (size_t l = 0; l < n->L.size(); ++l) {
+        saved[l] = n->L[l].w32;
+        if (!n->L[l].w32) n->L[l].w32 = reinterpret_cast<float*>(n->L[l].w);
+    }
+    s = enqueue_forward(n, d_frames, batch, h, w, dout, nullptr, true, amax);
+    std::vector<float> hm(n->L.size());
+    cudaError_t e = cudaMemcpyAsync(hm.data(), amax, hm.size() * sizeof(float), cudaMemcpyDeviceToHost, n->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+    for (size_t l = 0; l < n->L.size(); ++l) n->L[l].w32 = saved[l];
+    cudaFree(n->cal[0]);
+    cudaFree(n->cal[1]);
+    n->cal[0] = n->cal[1] = nullptr;
+    cudaFree(amax);
+    cudaFree(dout);
+    if (s != NET_OK) return s;
+    if (e != cudaSuccess) return fail(NET_E_CUDA, "calibrate: %s", cudaGetErrorString(e));
+    std::vector<float> sc(n->L.size());
+    for (size_t l = 0; l < n->L.size(); ++l) sc[l] = std::max(hm[l], 1e-30f) / kFp8Max;
+    if (scales_out) std::memcpy(scales_out, sc.data(), sc.size() * sizeof(float));
+    return net_set_act_scales(n, sc.data(), (int)sc.size());
+}
+
+extern "C" net_status net_forward_uneven(net_t* n, const float* const* d_in, const int* side, int cnt,
+                                         float* const* d_out) {
+    if (!n || !d_in || !side || !d_out || cnt < 1) return fail(NET_E_INVAL, "bad argument");
+    if (!n->weights_loaded) return fail(NET_E_WEIGHTS, "weights not loaded");
+    for (int i = 0; i < cnt; ++i) {
+        net_status s = check_shape(n, 1, side[i], side[i]);
+        if (s != NET_OK) return s;
+        if (!d_in[i] || !d_out[i]) return fail(NET_E_INVAL, "NULL frame pointer %d", i);
+    }
+    CK(cudaSetDevice(n->device));
+    return enqueue_uneven(n, d_in, side, cnt, d_out);
+}
+
+extern "C" net_status net_free(net_t* n) {
+    if (!n) return NET_OK;
+    cudaSetDevice(n->device);
+    serve_stop(n);
+    if (n->stream) cudaStreamSynchronize(n->stream);
+    n->graphs_clear();
+    for (auto ev : n->prof_ev) cudaEventDestroy(ev);
+    for (auto& L : n->L) {
+        cudaFree(L.w);
+        cudaFree(L.bias);
+        cudaFree(L.wscale);
+        cudaFree(L.alpha);
+        cudaFree(L.w32);
+    }
+    cudaFree(n->act[0]);
+    cudaFree(n->act[1]);
+    cudaFree(n->d_in_stage);
+    cudaFree(n->d_out_stage);
+    uneven_free(n);
+    if (n->own_stream) cudaStreamDestroy(n->stream);
+    delete n;
+    return NET_OK;
+}
+
+extern "C" const char* net_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* net_version(void) { return "gb300-darknet-resident 0.1 (sm_103a)"; }

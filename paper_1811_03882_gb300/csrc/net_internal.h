@@ -1,0 +1,80 @@
+// net_internal.h — the handle and the executor's internal entry points.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "../../include/net.h"
+#include "kernels.h"
+
+namespace dn {
+
+enum { ENG_SIMT = 0, ENG_TC = 1 };
+
+struct Layer {
+    net_layer d{};
+    int cin = 0;
+    int prec = 0;        // net_precision of the operands
+    int engine = 0;      // ENG_SIMT or ENG_TC
+    int in_dt = 0;       // storage dtype of this layer's input activation
+    int in_cs = 0;       // its channel stride (padded channels)
+    int w_rows = 0;      // allocated weight rows (zero beyond cout)
+    int cs32 = 0;        // channel stride of the FP32 calibration copy
+    void* w = nullptr;   // [w_rows][k*k][in_cs], dtype in_dt
+    float* bias = nullptr;
+    float* wscale = nullptr;  // FP8 per-channel weight scale
+    float* alpha = nullptr;   // FP8: wscale * act_scale
+    float* w32 = nullptr;     // FP32 copy of W' for calibration (FP8 nets)
+    double act_scale = 1.0;   // FP8 scale of this layer's input
+};
+
+struct UnevenState;
+struct ServeState;
+
+}  // namespace dn
+
+struct net {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int in_c = 0;
+    std::vector<dn::Layer> L;
+    int max_batch = 1, max_side = 1;
+    size_t budget = 0;
+    bool has_fp8 = false;
+    bool weights_loaded = false;
+    bool use_graphs = true;
+    void* act[2] = {nullptr, nullptr};
+    size_t act_bytes = 0;
+    void* cal[2] = {nullptr, nullptr};
+    float* d_in_stage = nullptr;
+    float* d_out_stage = nullptr;
+    size_t in_stage_bytes = 0, out_stage_bytes = 0;
+    std::map<std::tuple<int, int, int, const void*, const void*>, cudaGraphExec_t> graphs;
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev;   // 2 per layer
+    uint64_t launches = 0;              // kernels launched so far
+    int pending = 0;                    // kernels enqueued by the current forward
+    std::map<std::tuple<int, int, int, const void*, const void*>, int> graph_kernels;
+    dn::UnevenState* uneven = nullptr;
+    dn::ServeState* serve = nullptr;
+    void graphs_clear();
+};
+
+namespace dn {
+
+net_status fail(net_status s, const char* fmt, ...);
+void layer_dims(const net* n, int h, int w, std::vector<int>& H, std::vector<int>& W);
+net_status check_shape(const net* n, int batch, int h, int w);
+size_t act_bytes_for(const net* n, int batch, int h, int w);
+net_status enqueue_forward(net* n, const float* d_in, int batch, int h, int w, float* d_out,
+                           float* const* trace, bool fp32_copy, float* amax);
+net_status run_forward(net* n, const float* d_in, int batch, int h, int w, float* d_out);
+net_status enqueue_uneven(net* n, const float* const* d_in, const int* side, int cnt,
+                          float* const* d_out);
+void uneven_free(net* n);
+void serve_stop(net* n);
+
+}  // namespace dn
