@@ -181,7 +181,8 @@ def main():
     netname, batch, side, prec, seed = WORKLOADS[wl]
     spec = synth.NETS[netname]()
     _, x, blob = synth.workload_net(spec, seed, batch, side, side)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     net = binding.Net(spec.layers, 3, prec=prec, max_batch=batch, max_side=side,
                       stream=stream.cuda_stream, device=dev)
     net.load_weights(blob)

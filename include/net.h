@@ -75,7 +75,8 @@ typedef struct {
     int max_batch;            /* largest batch for net_forward*                  */
     int max_side;             /* largest frame height/width                      */
     size_t hbm_budget_bytes;  /* activation budget of the request queue; 0: 40 GB */
-    void* cuda_stream;        /* cudaStream_t used for all work; NULL: own stream */
+    void* cuda_stream;        /* cudaStream_t for all work; NULL: an own stream that
+                                 synchronises with the legacy default stream  */
     int device;               /* CUDA device ordinal                             */
 } net_desc;
 

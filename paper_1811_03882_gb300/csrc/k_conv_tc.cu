@@ -1,9 +1,479 @@
-// k_conv_tc.cu — tensor-core implicit-GEMM convolution (tcgen05 + TMA).
+// k_conv_tc.cu — tensor-core implicit-GEMM convolution for sm_103a.
+//
+// y[n,i,j,o] = sum_{kh,kw,c} x[n, i+kh-p, j+kw-p, c] * W'[o, kh, kw, c]
+// as a GEMM with M = output pixels, N = Cout, K = k*k*Cin: tcgen05.mma
+// (BF16: kind::f16, FP8 E4M3: kind::f8f6f4) with FP32 accumulators in
+// tensor memory, operands staged in shared memory by TMA.
+//
+// The A operand of one K step is one box of the NHWC activation: a TH x TW
+// rectangle of pixels (TH*TW = 128 = the MMA's M) shifted by the tap
+// (kh, kw), times one chunk of channels (32, 64 or 128 bytes, the swizzle
+// width).  TMA's out-of-bounds zero fill supplies the convolution's zero
+// padding, so no im2col buffer exists.  B is the matching [BN x chunk]
+// box of the K-major weights [Cout][kh][kw][Cin].
+//
+// Persistent, warp-specialised CTA (one per SM, 192 threads):
+//   warp 0     TMA producer (one lane), STAGES-deep smem ring
+//   warp 1     TMEM owner and MMA issuer (one lane)
+//   warps 2-5  epilogue: tcgen05.ld from TMEM, alpha/bias, leaky, 2x2 max
+//              via warp shuffles, downcast, 16-byte stores
+// Two TMEM accumulators let the epilogue of one tile overlap the
+// mainloop of the next.  Every mbarrier wait is bounded: on expiry the
+// kernel records an error code, drains its TMA copies, frees TMEM and
+// returns.
+#include <cuda.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace dn {
 
-cudaError_t conv_tc(const ConvLaunch&, int, cudaStream_t) { return cudaErrorNotSupported; }
+namespace tc {
+
+constexpr int THREADS = 192;
+constexpr int A_BYTES = 128 * 128;            // 128 rows x 128-byte chunk (max)
+constexpr long long WAIT_LIMIT = 4000000000LL;  // clock64 cycles (~2 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false (and the error code recorded) when the limit passed
+// or another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err, int code) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_LIMIT) {
+            *abort_flag = 1;
+            atomicExch(err, code);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void* tmap, int c0, int c1, int c2,
+                                            int c3, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05), K-major operand with 32/64/128
+// byte swizzle: start >> 4, leading offset (unused for swizzled K-major) 16,
+// stride offset = 8 rows * row bytes, fixed version bits 46..48 = 0b001.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int chb) {
+    const uint64_t swz = chb == 128 ? 2 : chb == 64 ? 4 : 6;
+    const uint64_t sbo = (uint64_t)(8 * chb) >> 4;
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | (sbo << 32) | ((uint64_t)1 << 46) |
+           (swz << 61);
+}
+
+// Instruction descriptor: D = F32, A/B = BF16 (kind::f16) or E4M3
+// (kind::f8f6f4), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+template <int DT>
+__device__ __forceinline__ uint32_t instr_desc(int n) {
+    const uint32_t ab = DT == DT_BF16 ? 1u : 0u;
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+template <int DT>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                    uint32_t accumulate) {
+    if (DT == DT_BF16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+        " [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+struct Smem {
+    uint64_t full[8], empty[8], accf[2], acce[2], done;
+    uint32_t tmem;
+    int abort;
+};
+
+}  // namespace tc
+
+template <int BN, int DT, int STAGES>
+__global__ void __launch_bounds__(tc::THREADS, 1)
+conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+    using namespace tc;
+    constexpr int B_BYTES = BN * 128;
+    constexpr int TMEM_COLS = 2 * BN;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * A_BYTES;
+    Smem* sm = reinterpret_cast<Smem*>(sB + STAGES * B_BYTES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int KK = a.k * a.k;
+    const int nk = KK * a.chunks;                 // K steps per tile
+    const int total = a.m_tiles * a.n_tiles;
+    const int pad = a.k >> 1;
+    const uint32_t a_bytes = 128u * a.chb, b_bytes = (uint32_t)BN * a.chb;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(smem_u32(&sm->full[s]), 1);
+            tc::mbar_init(smem_u32(&sm->empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(smem_u32(&sm->accf[b]), 1);
+            tc::mbar_init(smem_u32(&sm->acce[b]), 4);
+        }
+        tc::mbar_init(smem_u32(&sm->done), 1);
+        sm->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&sm->tmem)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem_base = sm->tmem;
+    volatile int* abort_flag = &sm->abort;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+                const int mt = tile / a.n_tiles, nt = tile % a.n_tiles;
+                int p = 0;
+                while (p + 1 < a.nprob && a.probs[p + 1].tile_begin <= mt) ++p;
+                const ConvProblem& P = a.probs[p];
+                const int local = mt - P.tile_begin;
+                const int tx = local % P.tiles_x;
+                const int ty = (local / P.tiles_x) % P.tiles_y;
+                const int img = local / (P.tiles_x * P.tiles_y);
+                const int x0 = tx * a.TW, y0 = ty * a.TH;
+                for (int tap = 0; tap < KK && ok; ++tap) {
+                    const int kh = tap / a.k, kw = tap % a.k;
+                    for (int ch = 0; ch < a.chunks; ++ch, ++it) {
+                        const int s = it % STAGES;
+                        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                        if (!tc::mbar_wait(smem_u32(&sm->empty[s]), ph ^ 1u, abort_flag, a.err, 1)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t fb = smem_u32(&sm->full[s]);
+                        tc::mbar_expect_tx(fb, a_bytes + b_bytes);
+                        const int c0 = ch * a.cpc;
+                        tc::tma_load_4d(smem_u32(sA + s * A_BYTES), &P.tmA, c0, x0 + kw - pad, y0 + kh - pad,
+                                        img, fb);
+                        tc::tma_load_2d(smem_u32(sB + s * B_BYTES), &tmB, tap * a.Cp + c0, nt * BN, fb);
+                    }
+                }
+            }
+            // drain: every copy issued must have landed before smem goes away
+            for (int j = (it > STAGES ? it - STAGES : 0); j < it; ++j)
+                if (!tc::mbar_wait(smem_u32(&sm->full[j % STAGES]), (uint32_t)(j / STAGES) & 1u, abort_flag,
+                                   a.err, 5)) {
+                    // abort already flagged: give the copies a bounded grace period
+                    const long long t0 = clock64();
+                    while (!tc::mbar_try(smem_u32(&sm->full[j % STAGES]), (uint32_t)(j / STAGES) & 1u) &&
+                           clock64() - t0 < WAIT_LIMIT) {
+                    }
+                }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = tc::instr_desc<DT>(BN);
+            int it = 0, tcount = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x, ++tcount) {
+                const int b = tcount & 1;
+                const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
+                if (!tc::mbar_wait(smem_u32(&sm->acce[b]), aph ^ 1u, abort_flag, a.err, 2)) break;
+                tc::fence_after();
+                const uint32_t dtm = tmem_base + (uint32_t)(b * BN);
+                for (int ks = 0; ks < nk; ++ks, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!tc::mbar_wait(smem_u32(&sm->full[s]), ph, abort_flag, a.err, 3)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after();
+                    const uint64_t ad = tc::smem_desc(smem_u32(sA + s * A_BYTES), a.chb);
+                    const uint64_t bd = tc::smem_desc(smem_u32(sB + s * B_BYTES), a.chb);
+                    const int nmma = a.chb / 32;   // 32 bytes of K per MMA
+                    for (int j = 0; j < nmma; ++j)
+                        tc::mma<DT>(dtm, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc,
+                                    (ks | j) != 0);
+                    tc::mma_commit(smem_u32(&sm->empty[s]));
+                }
+                if (ok) tc::mma_commit(smem_u32(&sm->accf[b]));
+            }
+            // every MMA issued has finished before TMEM and smem are released
+            tc::mma_commit(smem_u32(&sm->done));
+            const long long t0 = clock64();
+            while (!tc::mbar_try(smem_u32(&sm->done), 0) && clock64() - t0 < WAIT_LIMIT) {
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue (warps 2..5)
+        const int q = warp & 3;                 // TMEM lane quarter of this warp
+        const int row = q * 32 + lane;          // pixel index in the tile
+        const int py = row / a.TW, px = row % a.TW;
+        const bool pool = a.ep.pool == POOL_S2;
+        const int ymask = a.TW == 16 ? 16 : 8;  // lane distance of the pixel below (pool tiles)
+        int tcount = 0;
+        for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++tcount) {
+            const int b = tcount & 1;
+            const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
+            if (!tc::mbar_wait(smem_u32(&sm->accf[b]), aph, abort_flag, a.err, 4)) break;
+            tc::fence_after();
+            const int mt = tile / a.n_tiles, nt = tile % a.n_tiles;
+            int p = 0;
+            while (p + 1 < a.nprob && a.probs[p + 1].tile_begin <= mt) ++p;
+            const ConvProblem& P = a.probs[p];
+            void* ybase = a.y_override ? a.y_override : P.y;
+            const int local = mt - P.tile_begin;
+            const int tx = local % P.tiles_x;
+            const int ty = (local / P.tiles_x) % P.tiles_y;
+            const int img = local / (P.tiles_x * P.tiles_y);
+            const int gy = ty * a.TH + py, gx = tx * a.TW + px;
+            const bool valid = gy < P.H && gx < P.W;
+            const int Ho = pool ? P.H / 2 : P.H, Wo = pool ? P.W / 2 : P.W;
+            const int yo = pool ? gy / 2 : gy, xo = pool ? gx / 2 : gx;
+            const bool writer = valid && (!pool || ((lane & 1) == 0 && (lane & ymask) == 0));
+            const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                float v[16];
+                __syncwarp();
+                tc::tmem_ld16(trow + (uint32_t)c0, v);
+                const int o0 = nt * BN + c0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int o = o0 + j;
+                    const float al = (a.ep.alpha && o < a.ep.cout) ? __ldg(a.ep.alpha + o) : 1.f;
+                    const float bi = o < a.ep.cout ? __ldg(a.ep.bias + o) : 0.f;
+                    float t = act_apply(fmaf(v[j], al, bi), a.ep.act);
+                    if (pool) {
+                        t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, 1));
+                        t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, ymask));
+                    }
+                    v[j] = t;
+                }
+                if (!writer) continue;
+                if (a.ep.out_layout == LAYOUT_NCHW) {
+                    float* yf = reinterpret_cast<float*>(ybase);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (o0 + j < a.ep.cout)
+                            yf[(((size_t)img * a.ep.cout + o0 + j) * Ho + yo) * Wo + xo] = v[j];
+                    continue;
+                }
+                if (o0 >= a.ep.out_cs) continue;
+                const size_t pix = ((size_t)img * Ho + yo) * Wo + xo;
+                if (a.ep.out_dt == DT_BF16) {
+                    uint4 pk[2];
+                    uint32_t* w = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        w[j] = *reinterpret_cast<uint32_t*>(&h2);
+                    }
+                    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ybase) +
+                                                          pix * a.ep.out_cs + o0);
+                    dst[0] = pk[0];
+                    dst[1] = pk[1];
+                } else if (a.ep.out_dt == DT_FP8) {
+                    uint4 pk;
+                    uint8_t* w = reinterpret_cast<uint8_t*>(&pk);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) w[j] = f32_to_e4m3_sat(v[j] * a.ep.out_inv_scale);
+                    *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(ybase) + pix * a.ep.out_cs + o0) = pk;
+                } else {
+                    float* dst = reinterpret_cast<float*>(ybase) + pix * a.ep.out_cs + o0;
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        if (o0 + j < a.ep.out_cs)
+                            *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+            }
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(smem_u32(&sm->acce[b]));
+        }
+    }
+
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    __syncwarp();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+}
+
+// ----------------------------------------------------------------- host
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+static CUtensorMapSwizzle swz_of(int chb) {
+    return chb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : chb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+}
+
+int tc_chunk_bytes(int Cp, int dt) {
+    const int bytes = Cp * (int)dt_size(dt);
+    return bytes >= 128 ? 128 : bytes;   // Cp is 32/64 bytes or a multiple of 128
+}
+
+cudaError_t tc_encode_act(CUtensorMap* tm, const void* base, int dt, int n, int H, int W, int Cp, int TW,
+                          int TH) {
+    EncodeTiled enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const int es = (int)dt_size(dt);
+    const int chb = tc_chunk_bytes(Cp, dt);
+    cuuint64_t dims[4] = {(cuuint64_t)Cp, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
+    cuuint64_t strides[3] = {(cuuint64_t)Cp * es, (cuuint64_t)W * Cp * es, (cuuint64_t)H * W * Cp * es};
+    cuuint32_t box[4] = {(cuuint32_t)(chb / es), (cuuint32_t)TW, (cuuint32_t)TH, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(tm, dt == DT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 4,
+                     const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz_of(chb),
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, int KK, int Cp, int BN) {
+    EncodeTiled enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const int es = (int)dt_size(dt);
+    const int chb = tc_chunk_bytes(Cp, dt);
+    cuuint64_t dims[2] = {(cuuint64_t)KK * Cp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)KK * Cp * es};
+    cuuint32_t box[2] = {(cuuint32_t)(chb / es), (cuuint32_t)BN};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(tm, dt == DT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                     const_cast<void*>(w), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz_of(chb),
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BN, int DT>
+static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a, int grid, cudaStream_t st) {
+    constexpr int STAGES = BN == 256 ? 4 : BN == 128 ? 6 : 8;
+    const size_t smem = 1024 + (size_t)STAGES * (tc::A_BYTES + BN * 128) + sizeof(tc::Smem);
+    auto kern = conv_tc_kernel<BN, DT, STAGES>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    kern<<<grid, tc::THREADS, smem, st>>>(tmB, a);
+    return cudaGetLastError();
+}
+
+cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int grid, cudaStream_t st) {
+    if (dt == DT_BF16) {
+        if (BN == 64) return launch_tc_bn<64, DT_BF16>(tmB, a, grid, st);
+        if (BN == 128) return launch_tc_bn<128, DT_BF16>(tmB, a, grid, st);
+        if (BN == 256) return launch_tc_bn<256, DT_BF16>(tmB, a, grid, st);
+    } else if (dt == DT_FP8) {
+        if (BN == 64) return launch_tc_bn<64, DT_FP8>(tmB, a, grid, st);
+        if (BN == 128) return launch_tc_bn<128, DT_FP8>(tmB, a, grid, st);
+        if (BN == 256) return launch_tc_bn<256, DT_FP8>(tmB, a, grid, st);
+    }
+    return cudaErrorInvalidValue;
+}
 
 }  // namespace dn

@@ -1,5 +1,6 @@
 // kernels.h — internal launchers (C++), called by the executor in net.cu.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "common.cuh"
@@ -62,6 +63,33 @@ cudaError_t absmax_f32(const float* x, size_t count, float* out, cudaStream_t st
 }  // namespace dn
 
 namespace dn {
-// Tensor-core conv (BF16 / FP8 operands in_dt, FP32 accumulation in TMEM).
-cudaError_t conv_tc(const ConvLaunch& L, int in_dt, cudaStream_t st);
+// One group member of a tensor-core conv launch: a batch of n equal frames
+// with its own activation tensor map and output.  The device-side table of
+// problems lets one launch cover frames of different sizes.
+struct alignas(64) ConvProblem {
+    CUtensorMap tmA;    // NHWC activation, box (chunk, TW, TH, 1)
+    const void* x;      // activation base (CUDA-core kernels)
+    void* y;            // output base
+    int n, H, W;        // frames, pre-pool size
+    int tiles_x, tiles_y;
+    int tile_begin;     // first M tile of this problem in the launch
+};
+
+struct TcArgs {
+    const ConvProblem* probs;  // device table, nprob entries
+    int nprob, m_tiles, n_tiles;
+    int Cp, k, TW, TH;
+    int chb;      // bytes of one K chunk (32, 64 or 128): the swizzle width
+    int cpc;      // channels per chunk
+    int chunks;   // chunks per tap (Cp / cpc)
+    void* y_override;  // if not null, output base for every problem
+    Epilogue ep;
+    int* err;     // bounded-wait failure code (0 = none)
+};
+
+int tc_chunk_bytes(int Cp, int dt);
+cudaError_t tc_encode_act(CUtensorMap* tm, const void* base, int dt, int n, int H, int W, int Cp, int TW,
+                          int TH);
+cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, int KK, int Cp, int BN);
+cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int grid, cudaStream_t st);
 }  // namespace dn

@@ -159,9 +159,13 @@ extern "C" net_status net_create(const net_desc* d, net_t** out) {
     if (d->cuda_stream) {
         n->stream = (cudaStream_t)d->cuda_stream;
     } else {
-        CK(cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking));
+        CK(cudaStreamCreate(&n->stream));   // blocking: ordered with the legacy default stream
         n->own_stream = true;
     }
+    CK(cudaDeviceGetAttribute(&n->num_sms, cudaDevAttrMultiProcessorCount, n->device));
+    CK(cudaHostAlloc((void**)&n->err_host, sizeof(int), cudaHostAllocMapped));
+    *n->err_host = 0;
+    CK(cudaHostGetDevicePointer((void**)&n->err_dev, n->err_host, 0));
     n->act_bytes = act_bytes_for(n.get(), n->max_batch, n->max_side, n->max_side);
     for (int i = 0; i < 2; ++i) {
         CK(cudaMalloc(&n->act[i], n->act_bytes));
@@ -250,6 +254,11 @@ extern "C" net_status net_load_weights(net_t* n, const float* blob, size_t n_flo
         a.out_w32 = want32 ? L.w32 : nullptr;
         a.Cp32 = L.cs32;
         e = fold_layer(a, n->stream);
+        if (e == cudaSuccess && L.engine == ENG_TC) {
+            const int bns[3] = {64, 128, 256};
+            for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+                e = tc_encode_weights(&L.tmB[i], L.w, dt, L.w_rows, KK, L.in_cs, bns[i]);
+        }
         if (e == cudaSuccess && dt == DT_FP8) e = make_alpha(L.wscale, L.act_scale, L.alpha, L.d.cout, n->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
@@ -285,12 +294,107 @@ extern "C" net_status net_set_act_scales(net_t* n, const float* scales, int cnt)
 // Input scale of layer l's storage for the FP8 format (1 otherwise).
 static float in_scale(const Layer& L) { return L.in_dt == DT_FP8 ? (float)L.act_scale : 1.f; }
 
+Plan::~Plan() {
+    for (auto& r : runs)
+        if (r.d_prob) cudaFree(r.d_prob);
+}
+
+void dn::tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, int* TW, int* TH, int* BN) {
+    static const int tws[5] = {16, 8, 32, 64, 128};
+    long best = -1;
+    for (int i = 0; i < 5; ++i) {
+        const int tw = tws[i], th = 128 / tw;
+        if (pool && tw > 16) continue;
+        const long cover = (long)cdiv(H, th) * th * cdiv(W, tw) * tw;
+        if (best < 0 || cover < best) {
+            best = cover;
+            *TW = tw;
+            *TH = th;
+        }
+    }
+    const long m_tiles = (long)batch * cdiv(H, *TH) * cdiv(W, *TW);
+    // widest N tile that still gives every SM a tile; else the narrowest
+    *BN = 64;
+    for (int bn : {256, 128}) {
+        if (bn > rup(ncols, 64)) continue;
+        if (m_tiles * cdiv(ncols, bn) >= num_sms) {
+            *BN = bn;
+            break;
+        }
+    }
+}
+
+// Buffer sequence and TC launch tables for one (batch, h, w).
+net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
+    auto key = std::make_tuple(batch, h, w);
+    auto it = n->plans.find(key);
+    if (it != n->plans.end()) {
+        *out = it->second;
+        return NET_OK;
+    }
+    std::unique_ptr<Plan> P(new Plan());
+    std::vector<int> H, W;
+    layer_dims(n, h, w, H, W);
+    const int nl = (int)n->L.size();
+    int cur = 0;
+    for (int l = 0; l < nl; ++l) {
+        const Layer& L = n->L[l];
+        const bool last = l + 1 == nl;
+        LayerRun r;
+        r.in_buf = cur;
+        r.out_buf = cur ^ 1;
+        r.H = H[l];
+        r.W = W[l];
+        if (L.engine == ENG_TC) {
+            const int out_cs = last ? rup(L.d.cout, 4) : n->L[l + 1].in_cs;
+            const int ncols = std::max(L.d.cout, out_cs);
+            tc_choose(batch, r.H, r.W, L.d.pool == NET_POOL_2X2S2, ncols, n->num_sms, &r.TW, &r.TH, &r.BN);
+            r.m_tiles = batch * cdiv(r.H, r.TH) * cdiv(r.W, r.TW);
+            r.n_tiles = cdiv(ncols, r.BN);
+            r.grid = std::min(r.m_tiles * r.n_tiles, n->num_sms);
+            ConvProblem hp;
+            std::memset(&hp, 0, sizeof hp);
+            cudaError_t e = tc_encode_act(&hp.tmA, n->act[r.in_buf], L.in_dt, batch, r.H, r.W, L.in_cs, r.TW, r.TH);
+            if (e != cudaSuccess) return fail(NET_E_CUDA, "layer %d: activation tensor map: %s", l, cudaGetErrorString(e));
+            hp.x = n->act[r.in_buf];
+            hp.y = n->act[r.out_buf];
+            hp.n = batch;
+            hp.H = r.H;
+            hp.W = r.W;
+            hp.tiles_x = cdiv(r.W, r.TW);
+            hp.tiles_y = cdiv(r.H, r.TH);
+            hp.tile_begin = 0;
+            CK(cudaMalloc(&r.d_prob, sizeof(ConvProblem)));
+            CK(cudaMemcpy(r.d_prob, &hp, sizeof hp, cudaMemcpyHostToDevice));
+        }
+        P->runs.push_back(r);
+        if (L.d.pool != NET_POOL_2X2S1_SAME) cur ^= 1;
+    }
+    *out = P.get();
+    n->plans[key] = P.release();
+    return NET_OK;
+}
+
+net_status dn::check_device_error(net* n) {
+    if (n->err_host && *(volatile int*)n->err_host) {
+        const int code = *(volatile int*)n->err_host;
+        *(volatile int*)n->err_host = 0;
+        return fail(NET_E_DEVICE_WAIT, "a bounded device-side wait expired (code %d)", code);
+    }
+    return NET_OK;
+}
+
 net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int w, float* d_out,
                                float* const* trace, bool fp32_copy, float* amax) {
     std::vector<int> H, W;
     layer_dims(n, h, w, H, W);
     cudaStream_t st = n->stream;
     const int nl = (int)n->L.size();
+    Plan* plan = nullptr;
+    if (!fp32_copy) {
+        net_status ps = get_plan(n, batch, h, w, &plan);
+        if (ps != NET_OK) return ps;
+    }
     auto in_dt = [&](int l) { return fp32_copy ? DT_F32 : n->L[l].in_dt; };
     auto in_cs = [&](int l) { return fp32_copy ? n->L[l].cs32 : n->L[l].in_cs; };
     void* buf[2] = {fp32_copy ? n->cal[0] : n->act[0], fp32_copy ? n->cal[1] : n->act[1]};
@@ -314,58 +418,79 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
             e = absmax_f32(reinterpret_cast<const float*>(buf[cur]),
                            (size_t)batch * H[l] * W[l] * in_cs(l), amax + l, st);
         }
-        ConvLaunch c{};
-        c.x = buf[cur];
-        c.w = fp32_copy ? (const void*)L.w32 : L.w;
-        c.n = batch;
-        c.H = H[l];
-        c.W = W[l];
-        c.Cp = in_cs(l);
-        c.k = L.d.k;
-        c.w_rows = L.w_rows;
-        c.ep.bias = L.bias;
-        c.ep.alpha = (!fp32_copy && L.in_dt == DT_FP8) ? L.alpha : nullptr;
-        c.ep.act = L.d.act;
-        c.ep.pool = L.d.pool == NET_POOL_2X2S2 ? POOL_S2 : POOL_NONE;
-        c.ep.cout = L.d.cout;
+        Epilogue ep{};
+        ep.bias = L.bias;
+        ep.alpha = (!fp32_copy && L.in_dt == DT_FP8) ? L.alpha : nullptr;
+        ep.act = L.d.act;
+        ep.pool = L.d.pool == NET_POOL_2X2S2 ? POOL_S2 : POOL_NONE;
+        ep.cout = L.d.cout;
         const bool s1 = L.d.pool == NET_POOL_2X2S1_SAME;
         const bool direct_nchw = last && !s1 && !trace;
+        void* y = nullptr;
         if (direct_nchw) {
-            c.y = d_out;
-            c.ep.out_layout = LAYOUT_NCHW;
-            c.ep.out_dt = DT_F32;
-            c.ep.out_cs = L.d.cout;
+            y = d_out;
+            ep.out_layout = LAYOUT_NCHW;
+            ep.out_dt = DT_F32;
+            ep.out_cs = L.d.cout;
         } else {
-            c.y = buf[cur ^ 1];
-            c.ep.out_layout = LAYOUT_NHWC;
-            c.ep.out_dt = last ? DT_F32 : in_dt(l + 1);
-            c.ep.out_cs = last ? rup(L.d.cout, 4) : in_cs(l + 1);
-            c.ep.out_inv_scale = (!last && c.ep.out_dt == DT_FP8) ? 1.f / in_scale(n->L[l + 1]) : 1.f;
+            y = buf[cur ^ 1];
+            ep.out_layout = LAYOUT_NHWC;
+            ep.out_dt = last ? DT_F32 : in_dt(l + 1);
+            ep.out_cs = last ? rup(L.d.cout, 4) : in_cs(l + 1);
+            ep.out_inv_scale = (!last && ep.out_dt == DT_FP8) ? 1.f / in_scale(n->L[l + 1]) : 1.f;
         }
         if (e == cudaSuccess && prof) e = mark(n->prof_ev[2 * l]);
         if (e == cudaSuccess) {
             ++n->pending;
-            if (!fp32_copy && L.engine == ENG_TC) e = conv_tc(c, L.in_dt, st);
-            else e = conv_simt(c, st);
+            if (!fp32_copy && L.engine == ENG_TC) {
+                const LayerRun& r = plan->runs[l];
+                TcArgs a{};
+                a.probs = r.d_prob;
+                a.nprob = 1;
+                a.m_tiles = r.m_tiles;
+                a.n_tiles = r.n_tiles;
+                a.Cp = L.in_cs;
+                a.k = L.d.k;
+                a.TW = r.TW;
+                a.TH = r.TH;
+                a.chb = tc_chunk_bytes(L.in_cs, L.in_dt);
+                a.cpc = a.chb / (int)dt_size(L.in_dt);
+                a.chunks = L.in_cs / a.cpc;
+                a.y_override = y;
+                a.ep = ep;
+                a.err = n->err_dev;
+                const int bi = r.BN == 64 ? 0 : r.BN == 128 ? 1 : 2;
+                e = conv_tc_launch(L.tmB[bi], a, r.BN, L.in_dt, r.grid, st);
+            } else {
+                ConvLaunch c{};
+                c.x = buf[cur];
+                c.w = fp32_copy ? (const void*)L.w32 : L.w;
+                c.y = y;
+                c.n = batch;
+                c.H = H[l];
+                c.W = W[l];
+                c.Cp = in_cs(l);
+                c.k = L.d.k;
+                c.w_rows = L.w_rows;
+                c.ep = ep;
+                e = conv_simt(c, st);
+            }
         }
         if (e == cudaSuccess && prof) e = mark(n->prof_ev[2 * l + 1]);
         if (e != cudaSuccess) return fail(NET_E_CUDA, "layer %d conv: %s", l, cudaGetErrorString(e));
         if (direct_nchw) break;
-        const float osc = (last || c.ep.out_dt != DT_FP8) ? 1.f : in_scale(n->L[l + 1]);
+        const float osc = (last || ep.out_dt != DT_FP8) ? 1.f : in_scale(n->L[l + 1]);
         if (s1) {
             ++n->pending;
-            e = maxpool_s1_same(buf[cur ^ 1], buf[cur], batch, H[l + 1], W[l + 1], c.ep.out_cs,
-                                c.ep.out_dt, st);
+            e = maxpool_s1_same(buf[cur ^ 1], buf[cur], batch, H[l + 1], W[l + 1], ep.out_cs, ep.out_dt, st);
             // pooled result is back in buf[cur]
         } else {
             cur ^= 1;
         }
         if (e == cudaSuccess && (trace && trace[l]) && ++n->pending)
-            e = unpack_nchw(buf[cur], trace[l], batch, L.d.cout, H[l + 1], W[l + 1], c.ep.out_cs,
-                            c.ep.out_dt, osc, st);
+            e = unpack_nchw(buf[cur], trace[l], batch, L.d.cout, H[l + 1], W[l + 1], ep.out_cs, ep.out_dt, osc, st);
         if (e == cudaSuccess && last && ++n->pending)
-            e = unpack_nchw(buf[cur], d_out, batch, L.d.cout, H[l + 1], W[l + 1], c.ep.out_cs,
-                            c.ep.out_dt, osc, st);
+            e = unpack_nchw(buf[cur], d_out, batch, L.d.cout, H[l + 1], W[l + 1], ep.out_cs, ep.out_dt, osc, st);
         if (e != cudaSuccess) return fail(NET_E_CUDA, "layer %d: %s", l, cudaGetErrorString(e));
     }
     return NET_OK;
@@ -386,6 +511,9 @@ net_status dn::run_forward(net* n, const float* d_in, int batch, int h, int w, f
     auto key = std::make_tuple(batch, h, w, (const void*)d_in, (const void*)d_out);
     auto it = n->graphs.find(key);
     if (it == n->graphs.end()) {
+        Plan* plan = nullptr;
+        net_status ps = get_plan(n, batch, h, w, &plan);   // allocations happen outside capture
+        if (ps != NET_OK) return ps;
         if (n->graphs.size() >= 64) n->graphs_clear();
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(n->stream, cudaStreamCaptureModeThreadLocal));
@@ -414,6 +542,8 @@ extern "C" net_status net_forward_device(net_t* n, const float* d_in, int batch,
     if (!n->weights_loaded) return fail(NET_E_WEIGHTS, "weights not loaded");
     net_status s = check_shape(n, batch, h, w);
     if (s != NET_OK) return s;
+    s = check_device_error(n);   // a failure recorded by an earlier stream-ordered call
+    if (s != NET_OK) return s;
     CK(cudaSetDevice(n->device));
     return run_forward(n, d_in, batch, h, w, d_out);
 }
@@ -435,7 +565,7 @@ extern "C" net_status net_forward(net_t* n, const float* in, int batch, int h, i
     if (s != NET_OK) return s;
     CK(cudaMemcpyAsync(out, n->d_out_stage, nout * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
     CK(cudaStreamSynchronize(n->stream));
-    return NET_OK;
+    return check_device_error(n);
 }
 
 extern "C" net_status net_forward_trace(net_t* n, const float* d_in, int batch, int h, int w,
@@ -561,6 +691,9 @@ extern "C" net_status net_free(net_t* n) {
         cudaFree(L.alpha);
         cudaFree(L.w32);
     }
+    for (auto& kv : n->plans) delete kv.second;
+    n->plans.clear();
+    if (n->err_host) cudaFreeHost(n->err_host);
     cudaFree(n->act[0]);
     cudaFree(n->act[1]);
     cudaFree(n->d_in_stage);

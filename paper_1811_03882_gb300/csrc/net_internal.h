@@ -28,7 +28,26 @@ struct Layer {
     float* alpha = nullptr;   // FP8: wscale * act_scale
     float* w32 = nullptr;     // FP32 copy of W' for calibration (FP8 nets)
     double act_scale = 1.0;   // FP8 scale of this layer's input
+    CUtensorMap tmB[3];       // TC weights, box rows BN = 64, 128, 256
 };
+
+// Launch plan of one layer for one input shape.
+struct LayerRun {
+    int in_buf = 0, out_buf = 1;   // activation buffers read / written by the conv
+    int H = 0, W = 0;              // conv input (= pre-pool output) size
+    int TW = 16, TH = 8, BN = 128; // TC tile: TH x TW pixels x BN channels
+    int m_tiles = 0, n_tiles = 0, grid = 0;
+    ConvProblem* d_prob = nullptr; // TC: device problem table (one entry)
+};
+
+struct Plan {
+    std::vector<LayerRun> runs;
+    ~Plan();
+};
+
+// TC tile choice for an H x W map (pooled layers need whole 2x2 windows in
+// one warp: TW = 8 or 16).
+void tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, int* TW, int* TH, int* BN);
 
 struct UnevenState;
 struct ServeState;
@@ -58,6 +77,10 @@ struct net {
     uint64_t launches = 0;              // kernels launched so far
     int pending = 0;                    // kernels enqueued by the current forward
     std::map<std::tuple<int, int, int, const void*, const void*>, int> graph_kernels;
+    std::map<std::tuple<int, int, int>, dn::Plan*> plans;
+    int num_sms = 148;
+    int* err_host = nullptr;   // mapped pinned: bounded device waits that expired
+    int* err_dev = nullptr;
     dn::UnevenState* uneven = nullptr;
     dn::ServeState* serve = nullptr;
     void graphs_clear();
@@ -71,6 +94,8 @@ net_status check_shape(const net* n, int batch, int h, int w);
 size_t act_bytes_for(const net* n, int batch, int h, int w);
 net_status enqueue_forward(net* n, const float* d_in, int batch, int h, int w, float* d_out,
                            float* const* trace, bool fp32_copy, float* amax);
+net_status get_plan(net* n, int batch, int h, int w, Plan** out);
+net_status check_device_error(net* n);
 net_status run_forward(net* n, const float* d_in, int batch, int h, int w, float* d_out);
 net_status enqueue_uneven(net* n, const float* const* d_in, const int* side, int cnt,
                           float* const* d_out);

@@ -1,0 +1,145 @@
+"""Tensor-core paths (BF16, FP8 E4M3) on the GPU against the oracle.
+
+Two references: the exact FP64 oracle (the stated budgets: BF16 <= 2e-2,
+FP8 <= 8e-2 normwise max relative error on the final map, argmax agreement
+>= 99%) and the quantisation-aware oracle, which rounds weights and
+activations exactly as the library stores them, so a kernel bug cannot hide
+inside the rounding budget.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_03882_gb300 import synth
+from helpers import default_precs, make_net, run_device
+
+pytestmark = pytest.mark.gpu
+TOL = {"bf16": 2e-2, "fp8": 8e-2}
+# against the quantisation-aware oracle: one FP32-vs-FP64 rounding flip of a
+# stored BF16/E4M3 activation moves an element by one unit in the last place
+QTOL = {"bf16": 5e-3, "fp8": 3e-2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1811_03882_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _check(spec, x, blob, prec, max_batch, max_side, scales=None, tight=None):
+    precs = default_precs(spec, prec)
+    ex = oracle.forward(spec.layers, spec.in_c, x, blob)
+    qa = oracle.forward_quant(spec.layers, spec.in_c, x, blob, precs, scales)
+    with make_net(spec, prec=prec, max_batch=max_batch, max_side=max_side) as net:
+        net.load_weights(blob)
+        if scales is not None:
+            net.set_act_scales(np.asarray(scales, np.float32))
+        y = run_device(net, x)
+    e_q = oracle.normwise_rel_err(y, qa)
+    e_x = oracle.normwise_rel_err(y, ex)
+    agree, npos, ties = oracle.argmax_agreement(y, ex, TOL[prec])
+    print("%s %s: err vs quant-aware %.3e, vs exact %.3e, argmax %.4f (%d pos, %d ties)"
+          % (spec.name, prec, e_q, e_x, agree, npos, ties))
+    assert np.isfinite(y).all()
+    assert e_q <= (tight if tight is not None else QTOL[prec]), e_q
+    assert e_x <= TOL[prec], e_x
+    assert agree >= 0.99
+    return y
+
+
+def test_bf16_single_tc_layer():
+    # 16 input channels: the conv itself runs on the tensor cores (32-byte K chunks)
+    spec, x, blob = synth.workload_single()
+    _check(spec, x, blob, "bf16", 1, 32, tight=1e-4)
+
+
+@pytest.mark.parametrize("cin,cout,k,pool,hw", [
+    (32, 64, 3, synth.POOL_2X2S2, (24, 40)),     # 64-byte chunks, pool tiles, ragged
+    (64, 128, 3, synth.POOL_NONE, (13, 13)),    # 128-byte chunks, odd map
+    (128, 64, 1, synth.POOL_NONE, (28, 28)),    # 1x1
+    (256, 256, 3, synth.POOL_2X2S2, (16, 16)),  # two K chunks per tap, BN 256 region
+    (96, 1000, 1, synth.POOL_NONE, (14, 14)),   # N tail: 1000 outputs
+])
+def test_bf16_layer_shapes(cin, cout, k, pool, hw):
+    L = synth.Layer
+    spec = synth.NetSpec("layer", cin, [L(k, cout, True, synth.ACT_LEAKY, pool)])
+    s = synth.Stream(cin * 7 + cout)
+    x = synth.make_frames(s, 2, cin, hw[0], hw[1], -1, 1)
+    blob = synth.pack_blob(spec, synth.make_params(s, spec))
+    _check(spec, x, blob, "bf16", 2, max(hw), tight=1e-4)
+
+
+def test_bf16_9conv_small_ragged():
+    spec = synth.net_9conv()
+    s = synth.Stream(41)
+    x = synth.make_frames(s, 2, 3, 96, 160)
+    blob = synth.pack_blob(spec, synth.make_params(s, spec))
+    _check(spec, x, blob, "bf16", 2, 160)
+
+
+def test_bf16_19conv_small():
+    spec = synth.net_19conv()
+    s = synth.Stream(42)
+    x = synth.make_frames(s, 2, 3, 64, 96)
+    blob = synth.pack_blob(spec, synth.make_params(s, spec))
+    _check(spec, x, blob, "bf16", 2, 96)
+
+
+def _fp8_scales(spec, blob, side):
+    s = synth.Stream(synth.SEED_CALIB)
+    xc = synth.make_frames(s, 1, spec.in_c, side, side)
+    return oracle.act_scales_from(spec.layers, spec.in_c, xc, blob)
+
+
+def test_fp8_single_tc_layer():
+    spec = synth.net_single_conv()
+    s = synth.Stream(43)
+    x = synth.make_frames(s, 1, 16, 32, 32, -1, 1)
+    blob = synth.pack_blob(spec, synth.make_params(s, spec))
+    sc = oracle.act_scales_from(spec.layers, 16, x, blob)
+    _check(spec, x, blob, "fp8", 1, 32, scales=sc, tight=2e-3)
+
+
+def test_fp8_9conv_small():
+    spec = synth.net_9conv()
+    s = synth.Stream(44)
+    x = synth.make_frames(s, 2, 3, 64, 64)
+    blob = synth.pack_blob(spec, synth.make_params(s, spec))
+    _check(spec, x, blob, "fp8", 2, 64, scales=_fp8_scales(spec, blob, 64))
+
+
+def _full_size(netfn, seed, batch, side, prec, frames):
+    """Full-size batch on the GPU (the launch configuration bench.py times);
+    the oracle recomputes the sampled frames one by one."""
+    spec = netfn()
+    _, x, blob = synth.workload_net(spec, seed, batch, side, side)
+    precs = default_precs(spec, prec)
+    sc = _fp8_scales(spec, blob, side) if prec == "fp8" else None
+    with make_net(spec, prec=prec, max_batch=batch, max_side=side) as net:
+        net.load_weights(blob)
+        if sc is not None:
+            net.set_act_scales(np.asarray(sc, np.float32))
+        y = run_device(net, x)
+    assert np.isfinite(y).all()
+    for f in frames:
+        ex = oracle.forward(spec.layers, 3, x[f:f + 1], blob)
+        qa = oracle.forward_quant(spec.layers, 3, x[f:f + 1], blob, precs, sc)
+        e_x = oracle.normwise_rel_err(y[f:f + 1], ex)
+        e_q = oracle.normwise_rel_err(y[f:f + 1], qa)
+        agree, npos, ties = oracle.argmax_agreement(y[f:f + 1], ex, TOL[prec])
+        print("%s %s frame %d: vs exact %.3e, vs quant-aware %.3e, argmax %.4f (%d ties)"
+              % (spec.name, prec, f, e_x, e_q, agree, ties))
+        assert e_x <= TOL[prec] and e_q <= QTOL[prec] and agree >= 0.99
+
+
+def test_19conv_448_b8_bf16_full_size():
+    _full_size(synth.net_19conv, synth.SEED_19CONV, 8, 448, "bf16", [0, 7])
+
+
+def test_19conv_448_b8_fp8_full_size():
+    _full_size(synth.net_19conv, synth.SEED_19CONV, 8, 448, "fp8", [3])
+
+
+def test_9conv_416_bf16_full_size():
+    _full_size(synth.net_9conv, synth.SEED_9CONV, 1, 416, "bf16", [0])
