@@ -266,7 +266,7 @@ def main():
         flops_l.append(2.0 * batch * h * h * l.cout * ci * l.k * l.k)
         if l.pool == synth.POOL_2X2S2:
             h //= 2
-    engines = ["fp32" if (prec == "fp32" or ci < 16) else prec for ci in cins]
+    engines = ["bf16" if (prec == "fp8" and ci < 16) else prec for ci in cins]
     dom = max(set(engines), key=lambda e: sum(t for t, en in zip(layer_ms, engines) if en == e))
     sel = [i for i, en in enumerate(engines) if en == dom]
     dom_flops = sum(flops_l[i] for i in sel)

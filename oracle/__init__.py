@@ -282,6 +282,13 @@ def normwise_rel_err(y, r) -> float:
     return float(np.abs(y - r).max() / (den if den > 0 else 1.0))
 
 
+def rms_rel_err(y, r) -> float:
+    """||y - r||_2 / ||r||_2."""
+    y, r = _f64(y), _f64(r)
+    den = np.sqrt((r * r).sum())
+    return float(np.sqrt(((y - r) ** 2).sum()) / (den if den > 0 else 1.0))
+
+
 def argmax_agreement(y, r, tie_tol: float):
     """Per spatial position, argmax over channels (axis 1).  Positions whose
     reference top-2 gap is below tie_tol * max|r| are near-ties and accepted

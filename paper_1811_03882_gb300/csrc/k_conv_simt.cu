@@ -35,7 +35,8 @@ template <int BN, int TH, int TW>
 __global__ void __launch_bounds__(256)
 conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
                  void* __restrict__ y, int H, int W, int Cp, int k, int kw_rows,
-                 int tiles_x, int tiles_y, Epilogue ep) {
+                 int tiles_x, int tiles_y, Epilogue ep, int ksplit, float* __restrict__ ws,
+                 int ws_cols) {
     using C = SimtCfg<BN, TH, TW>;
     __shared__ __align__(16) float As[2][C::BK][C::PX];
     __shared__ __align__(16) float Bs[2][C::BK][BN];
@@ -50,13 +51,17 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
     const int pad = k / 2;
     const int KK = k * k;
     const int csteps = (Cp + C::BK - 1) / C::BK;
-    const int nsteps = KK * csteps;
+    const int nall = KK * csteps;
+    const int z = blockIdx.z;
+    const int s_begin = (int)((long)nall * z / ksplit), s_end = (int)((long)nall * (z + 1) / ksplit);
+    const int nsteps = s_end - s_begin;
     const size_t wrow = (size_t)KK * Cp;
 
     float4 ra[C::A_VEC];
     float4 rb;
 
-    auto load = [&](int step) {
+    auto load = [&](int lstep) {
+        const int step = s_begin + lstep;
         const int tap = step / csteps;
         const int c0 = (step % csteps) * C::BK;
         const int kh = tap / k, kwi = tap % k;
@@ -108,8 +113,10 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
 
     const int cg = tid % C::CG, pg = tid / C::CG;
-    load(0);
-    store(0);
+    if (nsteps > 0) {
+        load(0);
+        store(0);
+    }
     __syncthreads();
     for (int s = 0; s < nsteps; ++s) {
         const int buf = s & 1;
@@ -137,8 +144,23 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
         }
     }
 
-    // ---- epilogue: alpha/bias, activation, optional 2x2/s2 max, store ----
     const int obase = n0 + cg * 4;
+    if (ksplit > 1) {
+        // raw partial sums; the reduction kernel applies the epilogue
+        const size_t mbase = (size_t)blockIdx.x * C::PX;
+        float* wz = ws + (size_t)z * gridDim.x * C::PX * ws_cols;
+#pragma unroll
+        for (int i = 0; i < C::PPT; ++i) {
+            const int pos = pg * C::PPT + i;
+            const int q = pos >> 2;
+            const int py = 2 * (q / C::QX) + ((pos >> 1) & 1), px = 2 * (q % C::QX) + (pos & 1);
+            *reinterpret_cast<float4*>(wz + (mbase + py * TW + px) * ws_cols + obase) =
+                make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        }
+        return;
+    }
+
+    // ---- epilogue: alpha/bias, activation, optional 2x2/s2 max, store ----
     float bia[4], alp[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -213,23 +235,31 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
 }
 
 template <int BN, int TH, int TW>
-static cudaError_t launch_simt(const ConvLaunch& L, cudaStream_t st) {
+static cudaError_t launch_simt(const ConvLaunch& L, int ncols, cudaStream_t st) {
     const int tiles_x = cdiv(L.W, TW), tiles_y = cdiv(L.H, TH);
-    const int ncols = L.ep.out_layout == LAYOUT_NCHW ? L.ep.cout
-                                                      : (L.ep.out_cs > L.ep.cout ? L.ep.out_cs : L.ep.cout);
-    dim3 grid((unsigned)(L.n * tiles_x * tiles_y), (unsigned)cdiv(ncols, BN));
+    const int ks = L.ksplit > 1 ? L.ksplit : 1;
+    const int n_tiles = cdiv(ncols, BN);
+    dim3 grid((unsigned)(L.n * tiles_x * tiles_y), (unsigned)n_tiles, (unsigned)ks);
     conv_simt_kernel<BN, TH, TW><<<grid, 256, 0, st>>>(
         reinterpret_cast<const float*>(L.x), reinterpret_cast<const float*>(L.w), L.y, L.H, L.W,
-        L.Cp, L.k, L.w_rows, tiles_x, tiles_y, L.ep);
+        L.Cp, L.k, L.w_rows, tiles_x, tiles_y, L.ep, ks, L.ws, n_tiles * BN);
     return cudaGetLastError();
+}
+
+void simt_tile(int ncols, int* bn, int* th, int* tw) {
+    if (ncols <= 16) { *bn = 16; *th = 16; *tw = 16; }
+    else if (ncols <= 32) { *bn = 32; *th = 8; *tw = 16; }
+    else { *bn = 64; *th = 8; *tw = 16; }
 }
 
 cudaError_t conv_simt(const ConvLaunch& L, cudaStream_t st) {
     const int ncols = L.ep.out_layout == LAYOUT_NCHW ? L.ep.cout
                                                       : (L.ep.out_cs > L.ep.cout ? L.ep.out_cs : L.ep.cout);
-    if (ncols <= 16) return launch_simt<16, 16, 16>(L, st);
-    if (ncols <= 32) return launch_simt<32, 8, 16>(L, st);
-    return launch_simt<64, 8, 16>(L, st);
+    int bn, th, tw;
+    simt_tile(ncols, &bn, &th, &tw);
+    if (bn == 16) return launch_simt<16, 16, 16>(L, ncols, st);
+    if (bn == 32) return launch_simt<32, 8, 16>(L, ncols, st);
+    return launch_simt<64, 8, 16>(L, ncols, st);
 }
 
 }  // namespace dn

@@ -182,7 +182,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int KK = a.k * a.k;
     const int nk = KK * a.chunks;                 // K steps per tile
-    const int total = a.m_tiles * a.n_tiles;
+    const int total = a.m_tiles * a.n_tiles * a.ksplit;
     const int pad = a.k >> 1;
     const uint32_t a_bytes = 128u * a.chb, b_bytes = (uint32_t)BN * a.chb;
 
@@ -218,7 +218,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             int it = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
-                const int mt = tile / a.n_tiles, nt = tile % a.n_tiles;
+                const int z = tile % a.ksplit, mn = tile / a.ksplit;
+                const int mt = mn / a.n_tiles, nt = mn % a.n_tiles;
+                const int ks0 = (int)((long)nk * z / a.ksplit), ks1 = (int)((long)nk * (z + 1) / a.ksplit);
                 int p = 0;
                 while (p + 1 < a.nprob && a.probs[p + 1].tile_begin <= mt) ++p;
                 const ConvProblem& P = a.probs[p];
@@ -227,9 +229,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 const int ty = (local / P.tiles_x) % P.tiles_y;
                 const int img = local / (P.tiles_x * P.tiles_y);
                 const int x0 = tx * a.TW, y0 = ty * a.TH;
-                for (int tap = 0; tap < KK && ok; ++tap) {
+                for (int ks = ks0; ks < ks1; ++ks, ++it) {
+                    const int tap = ks / a.chunks, ch = ks % a.chunks;
                     const int kh = tap / a.k, kw = tap % a.k;
-                    for (int ch = 0; ch < a.chunks; ++ch, ++it) {
+                    {
                         const int s = it % STAGES;
                         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                         if (!tc::mbar_wait(smem_u32(&sm->empty[s]), ph ^ 1u, abort_flag, a.err, 1)) {
@@ -263,12 +266,14 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             int it = 0, tcount = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x, ++tcount) {
+                const int z = tile % a.ksplit;
+                const int ks0 = (int)((long)nk * z / a.ksplit), ks1 = (int)((long)nk * (z + 1) / a.ksplit);
                 const int b = tcount & 1;
                 const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
                 if (!tc::mbar_wait(smem_u32(&sm->acce[b]), aph ^ 1u, abort_flag, a.err, 2)) break;
                 tc::fence_after();
                 const uint32_t dtm = tmem_base + (uint32_t)(b * BN);
-                for (int ks = 0; ks < nk; ++ks, ++it) {
+                for (int ks = ks0; ks < ks1; ++ks, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                     if (!tc::mbar_wait(smem_u32(&sm->full[s]), ph, abort_flag, a.err, 3)) {
@@ -281,7 +286,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     const int nmma = a.chb / 32;   // 32 bytes of K per MMA
                     for (int j = 0; j < nmma; ++j)
                         tc::mma<DT>(dtm, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc,
-                                    (ks | j) != 0);
+                                    (ks != ks0 || j != 0) ? 1u : 0u);
                     tc::mma_commit(smem_u32(&sm->empty[s]));
                 }
                 if (ok) tc::mma_commit(smem_u32(&sm->accf[b]));
@@ -305,7 +310,27 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
             if (!tc::mbar_wait(smem_u32(&sm->accf[b]), aph, abort_flag, a.err, 4)) break;
             tc::fence_after();
-            const int mt = tile / a.n_tiles, nt = tile % a.n_tiles;
+            const int z = tile % a.ksplit, mn = tile / a.ksplit;
+            const int mt = mn / a.n_tiles, nt = mn % a.n_tiles;
+            if (a.ksplit > 1) {
+                // raw partial sums of this K slice; the reduction applies the epilogue
+                const int ncp = a.n_tiles * BN;
+                float* wr = a.ws + ((size_t)z * a.m_tiles * 128 + (size_t)mt * 128 + row) * ncp + nt * BN;
+                const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
+#pragma unroll 1
+                for (int c0 = 0; c0 < BN; c0 += 16) {
+                    float v[16];
+                    __syncwarp();
+                    tc::tmem_ld16(trow + (uint32_t)c0, v);
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4*>(wr + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(smem_u32(&sm->acce[b]));
+                continue;
+            }
             int p = 0;
             while (p + 1 < a.nprob && a.probs[p + 1].tile_begin <= mt) ++p;
             const ConvProblem& P = a.probs[p];

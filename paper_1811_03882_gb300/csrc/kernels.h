@@ -17,9 +17,25 @@ struct ConvLaunch {
     int k;           // 1 or 3
     int w_rows;      // allocated weight rows (>= every column a tile touches)
     Epilogue ep;
+    int bn, th, tw;  // tile: th x tw pixels x bn channels (0: choose from ep)
+    int ksplit;      // > 1: K split over grid.z, raw sums to ws
+    float* ws;       // split-K partial sums [ksplit][m_tiles*th*tw][n_tiles*bn]
 };
 
+// CUDA-core tile choice for a layer with `ncols` output columns.
+void simt_tile(int ncols, int* bn, int* th, int* tw);
 cudaError_t conv_simt(const ConvLaunch& L, cudaStream_t st);
+
+// Split-K reduction + epilogue: y = epilogue(sum_z ws[z]) in fixed z order.
+struct SplitReduce {
+    const float* ws;
+    int ksplit, m_rows, ncols_pad;   // ws geometry: [ksplit][m_rows][ncols_pad]
+    int TW, TH, tiles_x, tiles_y;    // tile geometry (row m = tile*TW*TH + py*TW + px)
+    int n, H, W;                     // frames and pre-pool size
+    void* y;
+    Epilogue ep;
+};
+cudaError_t splitk_reduce(const SplitReduce& r, cudaStream_t st);
 
 // Frame NCHW float32 -> NHWC (channel stride Cp, zero padded) in dtype dt;
 // FP8 codes are value * inv_scale.
@@ -83,6 +99,8 @@ struct TcArgs {
     int cpc;      // channels per chunk
     int chunks;   // chunks per tap (Cp / cpc)
     void* y_override;  // if not null, output base for every problem
+    int ksplit;        // K split factor (tiles x ksplit work items)
+    float* ws;         // ksplit > 1: raw sums [ksplit][m_tiles*128][n_tiles*BN]
     Epilogue ep;
     int* err;     // bounded-wait failure code (0 = none)
 };

@@ -54,12 +54,12 @@ net_status dn::fail(net_status s, const char* fmt, ...) {
     } while (0)
 
 // ------------------------------------------------------------- planning
-static int layer_engine(int prec, int cin) {
-    // Tensor cores need K chunks of >= 32 bytes of one tap; the 3-channel
-    // first layer (K = 27) runs on the CUDA cores in FP32 instead.
-    if (prec == NET_FP32) return ENG_SIMT;
-    return cin >= 16 ? ENG_TC : ENG_SIMT;
-}
+static int layer_engine(int prec) { return prec == NET_FP32 ? ENG_SIMT : ENG_TC; }
+
+// A layer reading fewer than 16 channels (the raw 3-channel frame) keeps its
+// operands in BF16 even in an FP8 network: its K chunk is padded to 32 bytes
+// either way, and E4M3 would round the frame itself to 4 significant bits.
+static int effective_prec(int prec, int cin) { return (prec == NET_FP8 && cin < 16) ? NET_BF16 : prec; }
 
 static int prec_dt(int prec) { return prec == NET_FP32 ? DT_F32 : prec == NET_BF16 ? DT_BF16 : DT_FP8; }
 
@@ -145,8 +145,8 @@ extern "C" net_status net_create(const net_desc* d, net_t** out) {
         Layer L;
         L.d = s;
         L.cin = cin;
-        L.prec = d->layer_prec ? d->layer_prec[l] : d->prec;
-        L.engine = layer_engine(L.prec, cin);
+        L.prec = effective_prec(d->layer_prec ? d->layer_prec[l] : d->prec, cin);
+        L.engine = layer_engine(L.prec);
         L.in_dt = L.engine == ENG_SIMT ? DT_F32 : prec_dt(L.prec);
         L.in_cs = pad_channels(cin, L.in_dt, L.engine == ENG_TC);
         L.w_rows = rup(std::max(s.cout, rup(s.cout, 128)), 256);
@@ -345,13 +345,33 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
         r.out_buf = cur ^ 1;
         r.H = H[l];
         r.W = W[l];
+        const int out_cs = last ? rup(L.d.cout, 4) : n->L[l + 1].in_cs;
+        const int ncols = std::max(L.d.cout, out_cs);
+        const int KK = L.d.k * L.d.k;
+        if (L.engine == ENG_SIMT) {
+            simt_tile(ncols, &r.sbn, &r.sth, &r.stw);
+            r.m_tiles = batch * cdiv(r.H, r.sth) * cdiv(r.W, r.stw);
+            r.n_tiles = cdiv(ncols, r.sbn);
+            const int grid = r.m_tiles * r.n_tiles;
+            const int nall = KK * cdiv(L.in_cs, 8);
+            if (grid < 2 * n->num_sms && nall >= 32)
+                r.ksplit = std::max(1, std::min({cdiv(4 * n->num_sms, grid), nall / 16, 32}));
+            if (r.ksplit > 1)
+                P->ws_bytes = std::max(P->ws_bytes, (size_t)r.ksplit * r.m_tiles * r.sth * r.stw *
+                                                        r.n_tiles * r.sbn * sizeof(float));
+        }
         if (L.engine == ENG_TC) {
-            const int out_cs = last ? rup(L.d.cout, 4) : n->L[l + 1].in_cs;
-            const int ncols = std::max(L.d.cout, out_cs);
             tc_choose(batch, r.H, r.W, L.d.pool == NET_POOL_2X2S2, ncols, n->num_sms, &r.TW, &r.TH, &r.BN);
             r.m_tiles = batch * cdiv(r.H, r.TH) * cdiv(r.W, r.TW);
             r.n_tiles = cdiv(ncols, r.BN);
-            r.grid = std::min(r.m_tiles * r.n_tiles, n->num_sms);
+            const int tiles = r.m_tiles * r.n_tiles;
+            const int nk = KK * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
+            if (tiles < n->num_sms && nk >= 16)
+                r.ksplit = std::max(1, std::min({cdiv(n->num_sms, tiles), nk / 8, 16}));
+            if (r.ksplit > 1)
+                P->ws_bytes = std::max(P->ws_bytes, (size_t)r.ksplit * r.m_tiles * 128 * r.n_tiles * r.BN *
+                                                        sizeof(float));
+            r.grid = std::min(tiles * r.ksplit, n->num_sms);
             ConvProblem hp;
             std::memset(&hp, 0, sizeof hp);
             cudaError_t e = tc_encode_act(&hp.tmA, n->act[r.in_buf], L.in_dt, batch, r.H, r.W, L.in_cs, r.TW, r.TH);
@@ -369,6 +389,15 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
         }
         P->runs.push_back(r);
         if (L.d.pool != NET_POOL_2X2S1_SAME) cur ^= 1;
+    }
+    if (P->ws_bytes > n->ws_bytes) {
+        // grow the split-K workspace; graphs captured on the old one are dropped
+        n->graphs_clear();
+        if (n->ws) cudaFree(n->ws);
+        n->ws = nullptr;
+        n->ws_bytes = 0;
+        CK(cudaMalloc(&n->ws, P->ws_bytes));
+        n->ws_bytes = P->ws_bytes;
     }
     *out = P.get();
     n->plans[key] = P.release();
@@ -457,10 +486,18 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.cpc = a.chb / (int)dt_size(L.in_dt);
                 a.chunks = L.in_cs / a.cpc;
                 a.y_override = y;
+                a.ksplit = r.ksplit;
+                a.ws = n->ws;
                 a.ep = ep;
                 a.err = n->err_dev;
                 const int bi = r.BN == 64 ? 0 : r.BN == 128 ? 1 : 2;
                 e = conv_tc_launch(L.tmB[bi], a, r.BN, L.in_dt, r.grid, st);
+                if (e == cudaSuccess && r.ksplit > 1) {
+                    ++n->pending;
+                    SplitReduce sr{n->ws, r.ksplit, r.m_tiles * 128, r.n_tiles * r.BN, r.TW, r.TH,
+                                   cdiv(r.W, r.TW), cdiv(r.H, r.TH), batch, r.H, r.W, y, ep};
+                    e = splitk_reduce(sr, st);
+                }
             } else {
                 ConvLaunch c{};
                 c.x = buf[cur];
@@ -473,7 +510,20 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 c.k = L.d.k;
                 c.w_rows = L.w_rows;
                 c.ep = ep;
+                const LayerRun* r = plan ? &plan->runs[l] : nullptr;
+                c.ksplit = r ? r->ksplit : 1;
+                c.ws = n->ws;
                 e = conv_simt(c, st);
+                if (e == cudaSuccess && c.ksplit > 1) {
+                    ++n->pending;
+                    const int nc = ep.out_layout == LAYOUT_NCHW ? ep.cout : std::max(ep.out_cs, ep.cout);
+                    int bn, th, tw;
+                    simt_tile(nc, &bn, &th, &tw);
+                    const int tx = cdiv(W[l], tw), ty = cdiv(H[l], th);
+                    SplitReduce sr{n->ws, c.ksplit, batch * tx * ty * th * tw, cdiv(nc, bn) * bn, tw, th,
+                                   tx, ty, batch, H[l], W[l], y, ep};
+                    e = splitk_reduce(sr, st);
+                }
             }
         }
         if (e == cudaSuccess && prof) e = mark(n->prof_ev[2 * l + 1]);
@@ -693,6 +743,7 @@ extern "C" net_status net_free(net_t* n) {
     }
     for (auto& kv : n->plans) delete kv.second;
     n->plans.clear();
+    if (n->ws) cudaFree(n->ws);
     if (n->err_host) cudaFreeHost(n->err_host);
     cudaFree(n->act[0]);
     cudaFree(n->act[1]);

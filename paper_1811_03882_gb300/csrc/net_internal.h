@@ -37,11 +37,14 @@ struct LayerRun {
     int H = 0, W = 0;              // conv input (= pre-pool output) size
     int TW = 16, TH = 8, BN = 128; // TC tile: TH x TW pixels x BN channels
     int m_tiles = 0, n_tiles = 0, grid = 0;
+    int ksplit = 1;                // split-K factor (partial sums in the workspace)
+    int sbn = 64, sth = 8, stw = 16; // CUDA-core tile
     ConvProblem* d_prob = nullptr; // TC: device problem table (one entry)
 };
 
 struct Plan {
     std::vector<LayerRun> runs;
+    size_t ws_bytes = 0;           // split-K workspace this plan needs
     ~Plan();
 };
 
@@ -79,6 +82,8 @@ struct net {
     std::map<std::tuple<int, int, int, const void*, const void*>, int> graph_kernels;
     std::map<std::tuple<int, int, int>, dn::Plan*> plans;
     int num_sms = 148;
+    float* ws = nullptr;       // split-K workspace (grown by plans, before any capture)
+    size_t ws_bytes = 0;
     int* err_host = nullptr;   // mapped pinned: bounded device waits that expired
     int* err_dev = nullptr;
     dn::UnevenState* uneven = nullptr;

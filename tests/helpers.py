@@ -25,12 +25,14 @@ def run_device(net, x):
     return d_out.cpu().numpy()
 
 
-def default_precs(spec, prec):
-    """Per-layer operand format the library uses for a network at `prec`:
-    the 3-channel first layer runs in FP32 on the CUDA cores."""
+def default_precs(spec, prec, layer_prec=None):
+    """Per-layer operand format the library uses for a network at `prec`
+    (or the per-layer list): a layer reading fewer than 16 channels keeps
+    BF16 operands in an FP8 network."""
     out = []
     c = spec.in_c
-    for l in spec.layers:
-        out.append("fp32" if (prec == "fp32" or c < 16) else prec)
+    for i, l in enumerate(spec.layers):
+        p = layer_prec[i] if layer_prec is not None else prec
+        out.append("bf16" if (p == "fp8" and c < 16) else p)
         c = l.cout
     return out

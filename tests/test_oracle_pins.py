@@ -310,6 +310,7 @@ def test_metrics(orc):
     r = np.array([[1.0, -4.0], [2.0, 0.0]])
     y = r + np.array([[0.0, 0.2], [0.0, 0.0]])
     assert orc.normwise_rel_err(y, r) == pytest.approx(0.05)
+    assert orc.rms_rel_err(y, r) == pytest.approx(0.2 / np.sqrt(21.0))
     ref = np.zeros((1, 3, 1, 2))
     ref[0, :, 0, 0] = [1.0, 3.0, 2.0]
     ref[0, :, 0, 1] = [1.0, 1.0005, 0.0]   # near-tie at position 1
