@@ -163,6 +163,35 @@ net_status net_layer_times(net_t* net, double* ms_out, int n);
  * counts every kernel node in the graph). */
 net_status net_launches(const net_t* net, uint64_t* total);
 
+/* ---- conv layer without allocation ------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they call (code running while a CUDA
+ * graph is captured, real-time loops that allow no allocation after
+ * start-up, hosts with a fixed device-memory budget).
+ *
+ * One FP32 conv layer: y = pool(act(conv(x, weight) + bias)), stride 1,
+ * zero pad k/2, computed by the same split-K FP32 kernels as the network
+ * path.  d_x: n x cin x h x w float32 NCHW; d_weight: cout x cin x k x k
+ * float32 (batchnorm, if any, already folded in); d_bias: cout floats;
+ * d_y: n x cout x h' x w' float32 NCHW (h' = h/2 with the 2x2/s2 pool).
+ * act: NET_ACT_*; pool: NET_POOL_NONE or NET_POOL_2X2S2.  All pointers are
+ * caller-owned device memory on the current device; work is queued on
+ * cuda_stream (NULL: legacy default stream) and not synchronised.
+ *
+ * It calls no cudaMalloc/cudaFree or allocating library routine.  Every
+ * intermediate lives in one static device array of
+ * NET_NOALLOC_SCRATCH_BYTES that each device loading the library holds
+ * until exit; a layer needing more returns NET_E_INVAL before touching the
+ * device.  The first call on a device looks the array's address up (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the array and a call overwrites what the previous one
+ * left there, so calls that may overlap on the GPU (different streams,
+ * several host threads) race: serialise them. */
+#define NET_NOALLOC_SCRATCH_BYTES (32u << 20)
+net_status net_conv2d_f32_noalloc(const float* d_x, int n, int cin, int h, int w,
+                                  const float* d_weight, const float* d_bias, int cout, int k,
+                                  int act, int pool, float* d_y, void* cuda_stream);
+
 /* Releases every device and host resource of the handle (stops the
  * scheduler thread first).  NULL is accepted. */
 net_status net_free(net_t* net);

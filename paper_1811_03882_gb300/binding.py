@@ -74,6 +74,9 @@ _SIGS = {
     "net_profile": [ctypes.c_void_p, ctypes.c_int],
     "net_layer_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "net_launches": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
+    "net_conv2d_f32_noalloc": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "net_free": [ctypes.c_void_p],
     "net_last_error": [],
     "net_version": [],
@@ -228,3 +231,10 @@ class Net:
         f, p50, p99 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         check(lib().net_stats(self.h, ctypes.byref(f), ctypes.byref(p50), ctypes.byref(p99)))
         return f.value, p50.value, p99.value
+
+
+def conv2d_f32_noalloc(d_x, n, cin, h, w, d_weight, d_bias, cout, k, act, pool, d_y, stream=None):
+    """net_conv2d_f32_noalloc: one FP32 conv layer using only the library's
+    static scratch array (no device allocation)."""
+    check(lib().net_conv2d_f32_noalloc(_ptr(d_x), n, cin, h, w, _ptr(d_weight), _ptr(d_bias), cout, k,
+                                       act, pool, _ptr(d_y), ctypes.c_void_p(stream) if stream else None))
