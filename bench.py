@@ -33,6 +33,8 @@ WORKLOADS = {
     "19conv-448-b8-fp8": ("19-conv", 8, 448, "fp8", synth.SEED_19CONV),
     "9conv-416-b1-fp32": ("9-conv", 1, 416, "fp32", synth.SEED_9CONV),
     "9conv-416-b1-bf16": ("9-conv", 1, 416, "bf16", synth.SEED_9CONV),
+    # 64 frames, sides drawn from {320, 416, 512, 608}, one grouped launch per layer
+    "uneven64-9conv-bf16": ("9-conv", 64, 0, "bf16", synth.SEED_UNEVEN),
 }
 DEFAULT = "9conv-416-b1-fp32"
 
@@ -129,23 +131,28 @@ def run_reference(args, wl):
         return
     netname, batch, side, prec, seed = WORKLOADS[wl]
     spec = synth.NETS[netname]()
-    _, x, blob = synth.workload_net(spec, seed, 1, side, side)
+    if side:
+        _, x, blob = synth.workload_net(spec, seed, 1, side, side)
+        frames = [x] * args.steps
+    else:
+        blob = synth.weights_for(spec, seed)
+        sides = synth.uneven_sides(batch, seed)
+        frames = [synth.frame_for(seed, i % batch, int(sides[i % batch])) for i in range(args.steps)]
     import oracle
     oracle.build()
-    for _ in range(args.warmup if args.warmup <= 1 else 1):
-        oracle.forward(spec.layers, 3, x, blob)
+    oracle.forward(spec.layers, 3, frames[0], blob)   # warm-up (one frame)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.forward(spec.layers, 3, x, blob)
+    for f in frames:
+        oracle.forward(spec.layers, 3, f, blob)
     el = time.perf_counter() - t0
     fps = args.steps / el
     line = {"impl": "reference", "metric": "frames/s", "value": fps, "unit": "frames/s",
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": wl, "frames_per_step": 1, "side": side, "network": netname},
+            "config": {"workload": wl, "frames_per_step": 1, "side": side or "uneven", "network": netname},
             "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": oracle.threads(),
-                             "kind": "oracle", "sample": "%d frames of %dx%d" % (args.steps, side, side)},
+                             "kind": "oracle", "sample": "%d frames (side %s)" % (args.steps, side or "uneven")},
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -180,19 +187,51 @@ def main():
 
     netname, batch, side, prec, seed = WORKLOADS[wl]
     spec = synth.NETS[netname]()
-    _, x, blob = synth.workload_net(spec, seed, batch, side, side)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    net = binding.Net(spec.layers, 3, prec=prec, max_batch=batch, max_side=side,
-                      stream=stream.cuda_stream, device=dev)
+    if side:
+        sides = [side] * batch
+        _, x, blob = synth.workload_net(spec, seed, batch, side, side)
+        frames = [x]
+    else:
+        # uneven batch: frame i has its own side and its own random stream
+        sides = [int(v) for v in synth.uneven_sides(batch, seed)]
+        blob = synth.weights_for(spec, seed)
+        frames = [synth.frame_for(seed, i, s) for i, s in enumerate(sides)]
+    net = binding.Net(spec.layers, 3, prec=prec, max_batch=batch if side else 1,
+                      max_side=max(sides), stream=stream.cuda_stream, device=dev)
     net.load_weights(blob)
-    c, ho, wo = net.output_shape(side, side)
-    d_in = torch.from_numpy(x).cuda()
-    d_out = torch.empty((batch, c, ho, wo), device="cuda")
     if prec == "fp8":
         s = synth.Stream(synth.SEED_CALIB)
-        xc = synth.make_frames(s, 2, 3, side, side)
-        net.calibrate(torch.from_numpy(xc).cuda(), 2, side, side)
+        cs = max(sides)
+        xc = synth.make_frames(s, 2, 3, cs, cs)
+        net.calibrate(torch.from_numpy(xc).cuda(), 2, cs, cs)
+    d_in = [torch.from_numpy(f).cuda() for f in frames]
+    d_out, h_in, h_out = [], [], []
+    for f in frames:
+        c, ho, wo = net.output_shape(f.shape[2], f.shape[3])
+        d_out.append(torch.empty((f.shape[0], c, ho, wo), device="cuda"))
+        h_in.append(torch.from_numpy(f).pin_memory())
+        h_out.append(torch.empty((f.shape[0], c, ho, wo)).pin_memory())
+
+    def step():
+        if side:
+            net.forward_device(d_in[0], batch, side, side, d_out[0])
+        else:
+            net.forward_uneven(d_in, sides, d_out)
+
+    def step_e2e():
+        if side:
+            # the host API: one H2D of the batch, the pass, one D2H of the result
+            net.forward(h_in[0].numpy(), h_out[0].numpy())
+        else:
+            for a, b in zip(d_in, h_in):
+                a.copy_(b, non_blocking=True)
+            net.forward_uneven(d_in, sides, d_out)
+            for a, b in zip(h_out, d_out):
+                a.copy_(b, non_blocking=True)
+            stream.synchronize()
+
     flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
 
     def barrier():
@@ -201,7 +240,7 @@ def main():
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        net.forward_device(d_in, batch, side, side, d_out)
+        step()
     barrier()
 
     # ---- timed region: K steps, L2 flushed between steps (outside events)
@@ -214,7 +253,7 @@ def main():
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
-            net.forward_device(d_in, batch, side, side, d_out)
+            step()
             ev[i][1].record(stream)
         barrier()
         wall = time.perf_counter() - w0
@@ -231,41 +270,42 @@ def main():
     # ---- per-layer conv-kernel times (second pass, events around each conv)
     net.profile(True)
     for _ in range(2):
-        net.forward_device(d_in, batch, side, side, d_out)
+        step()
     torch.cuda.synchronize()
     layer_ms = np.zeros(len(spec.layers))
     for i in range(args.steps):
         flush.zero_()
-        net.forward_device(d_in, batch, side, side, d_out)
+        step()
         layer_ms += net.layer_times()
     layer_ms /= args.steps
     net.profile(False)
 
     # ---- end to end through the host API (pinned host buffers)
-    h_in = torch.from_numpy(x).pin_memory()
-    h_out = torch.empty((batch, c, ho, wo)).pin_memory()
     for _ in range(2):
-        net.forward(h_in.numpy(), h_out.numpy())
+        step_e2e()
     barrier()
     t0 = time.perf_counter()
     for i in range(args.steps):
-        net.forward(h_in.numpy(), h_out.numpy())
+        step_e2e()
     barrier()
     e2e_s = time.perf_counter() - t0
     if ws > 1:
         t = torch.tensor([e2e_s], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
+    h2d = sum(int(f.nbytes) for f in frames)
+    d2h = sum(int(o.numel() * 4) for o in d_out)
 
     # ---- roofline of the dominant kernel (conv, by engine)
     pk, pk_kind = peaks()
     cins = spec.cins()
-    flops_l = []
-    h = side
-    for l, ci in zip(spec.layers, cins):
-        flops_l.append(2.0 * batch * h * h * l.cout * ci * l.k * l.k)
-        if l.pool == synth.POOL_2X2S2:
-            h //= 2
+    flops_l = np.zeros(len(spec.layers))
+    for sd, f in zip(sides, [1] * len(sides)):
+        h = sd
+        for i, (l, ci) in enumerate(zip(spec.layers, cins)):
+            flops_l[i] += 2.0 * f * h * h * l.cout * ci * l.k * l.k
+            if l.pool == synth.POOL_2X2S2:
+                h //= 2
     engines = ["bf16" if (prec == "fp8" and ci < 16) else prec for ci in cins]
     dom = max(set(engines), key=lambda e: sum(t for t, en in zip(layer_ms, engines) if en == e))
     sel = [i for i, en in enumerate(engines) if en == dom]
@@ -285,28 +325,30 @@ def main():
             "kernel": "conv_%s (%d layers)" % ("simt" if dom == "fp32" else "tc_" + dom, len(sel)),
             "peak_source": pnote, "launches_per_step": len(sel)}
 
-    conv_flops = sum(flops_l)
+    conv_flops = float(sum(flops_l))
     line = {
         "metric": "frames/s", "value": value, "unit": "frames/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[prec], "data": "synthetic",
         "config": {"workload": wl, "network": netname, "global_batch": batch * ws,
-                   "frames_per_step_per_gpu": batch, "side": side, "precision": prec,
+                   "frames_per_step_per_gpu": batch, "side": side if side else "uneven {320,416,512,608}",
+                   "precision": prec,
                    "parallelism": "replicas%d" % ws, "l2": "flushed between steps (256 MB write)"},
         "conv_tflops": conv_flops * args.steps * ws / (total_ms / 1e3) / 1e12,
         "roofline": roof,
         "layer_ms": [round(float(t), 5) for t in layer_ms],
         "e2e": {"value": frames_all / e2e_s, "unit": "frames/s",
-                "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(batch * c * ho * wo * 4)},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "wall_s_timed": wall,
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline:
-        fps, nfr, el, cores = oracle_frames_per_s(spec, x[:1], blob, args.cpu_budget_s)
+        f0 = frames[0][:1]
+        fps, nfr, el, cores = oracle_frames_per_s(spec, f0, blob, args.cpu_budget_s)
         line["cpu_baseline"] = {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
-                                "sample": "%d frame(s) of %dx%d, %.1f s" % (nfr, side, side, el)}
+                                "sample": "%d frame(s) of %dx%d, %.1f s" % (nfr, f0.shape[2], f0.shape[3], el)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     net.close()

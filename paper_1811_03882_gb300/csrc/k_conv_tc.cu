@@ -12,11 +12,12 @@
 // padding, so no im2col buffer exists.  B is the matching [BN x chunk]
 // box of the K-major weights [Cout][kh][kw][Cin].
 //
-// Persistent, warp-specialised CTA (one per SM, 192 threads):
+// Persistent, warp-specialised CTA (one per SM, 320 threads):
 //   warp 0     TMA producer (one lane), STAGES-deep smem ring
 //   warp 1     TMEM owner and MMA issuer (one lane)
-//   warps 2-5  epilogue: tcgen05.ld from TMEM, alpha/bias, leaky, 2x2 max
-//              via warp shuffles, downcast, 16-byte stores
+//   warps 2-9  epilogue (two warps per TMEM lane quarter, half the
+//              columns each): tcgen05.ld, alpha/bias, leaky, 2x2 max via
+//              warp shuffles, downcast, 16-byte stores
 // Two TMEM accumulators let the epilogue of one tile overlap the
 // mainloop of the next.  Every mbarrier wait is bounded: on expiry the
 // kernel records an error code, drains its TMA copies, frees TMEM and
@@ -30,7 +31,7 @@ namespace dn {
 
 namespace tc {
 
-constexpr int THREADS = 192;
+constexpr int THREADS = 320;   // producer, MMA issuer, 8 epilogue warps
 constexpr int A_BYTES = 128 * 128;            // 128 rows x 128-byte chunk (max)
 constexpr long long WAIT_LIMIT = 4000000000LL;  // clock64 cycles (~2 s)
 
@@ -159,6 +160,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 struct Smem {
     uint64_t full[8], empty[8], accf[2], acce[2], done;
     uint32_t tmem;
@@ -193,7 +210,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(smem_u32(&sm->accf[b]), 1);
-            tc::mbar_init(smem_u32(&sm->acce[b]), 4);
+            tc::mbar_init(smem_u32(&sm->acce[b]), 8);
         }
         tc::mbar_init(smem_u32(&sm->done), 1);
         sm->abort = 0;
@@ -298,8 +315,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             }
         }
     } else {
-        // ------------------------------------------------ epilogue (warps 2..5)
+        // ------------------------------------------------ epilogue (warps 2..9)
+        // Two warps per TMEM lane quarter, each taking half of the tile's
+        // columns, so every SM sub-partition runs two epilogue warps.
         const int q = warp & 3;                 // TMEM lane quarter of this warp
+        const int half = (warp - 2) >> 2;       // column half of the tile
+        constexpr int HC = BN / 2;              // columns per warp
         const int row = q * 32 + lane;          // pixel index in the tile
         const int py = row / a.TW, px = row % a.TW;
         const bool pool = a.ep.pool == POOL_S2;
@@ -312,92 +333,126 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             tc::fence_after();
             const int z = tile % a.ksplit, mn = tile / a.ksplit;
             const int mt = mn / a.n_tiles, nt = mn % a.n_tiles;
+            const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * HC);
             if (a.ksplit > 1) {
                 // raw partial sums of this K slice; the reduction applies the epilogue
                 const int ncp = a.n_tiles * BN;
-                float* wr = a.ws + ((size_t)z * a.m_tiles * 128 + (size_t)mt * 128 + row) * ncp + nt * BN;
-                const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
+                float* wr = a.ws + ((size_t)z * a.m_tiles * 128 + (size_t)mt * 128 + row) * ncp + nt * BN + half * HC;
 #pragma unroll 1
-                for (int c0 = 0; c0 < BN; c0 += 16) {
-                    float v[16];
+                for (int c0 = 0; c0 < HC; c0 += 32) {
+                    float v[32];
                     __syncwarp();
-                    tc::tmem_ld16(trow + (uint32_t)c0, v);
+                    tc::tmem_ld32(trow + (uint32_t)c0, v);
 #pragma unroll
-                    for (int j = 0; j < 16; j += 4)
+                    for (int j = 0; j < 32; j += 4)
                         *reinterpret_cast<float4*>(wr + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                 }
-                tc::fence_before();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(smem_u32(&sm->acce[b]));
-                continue;
-            }
-            int p = 0;
-            while (p + 1 < a.nprob && a.probs[p + 1].tile_begin <= mt) ++p;
-            const ConvProblem& P = a.probs[p];
-            void* ybase = a.y_override ? a.y_override : P.y;
-            const int local = mt - P.tile_begin;
-            const int tx = local % P.tiles_x;
-            const int ty = (local / P.tiles_x) % P.tiles_y;
-            const int img = local / (P.tiles_x * P.tiles_y);
-            const int gy = ty * a.TH + py, gx = tx * a.TW + px;
-            const bool valid = gy < P.H && gx < P.W;
-            const int Ho = pool ? P.H / 2 : P.H, Wo = pool ? P.W / 2 : P.W;
-            const int yo = pool ? gy / 2 : gy, xo = pool ? gx / 2 : gx;
-            const bool writer = valid && (!pool || ((lane & 1) == 0 && (lane & ymask) == 0));
-            const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                float v[16];
-                __syncwarp();
-                tc::tmem_ld16(trow + (uint32_t)c0, v);
-                const int o0 = nt * BN + c0;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int o = o0 + j;
-                    const float al = (a.ep.alpha && o < a.ep.cout) ? __ldg(a.ep.alpha + o) : 1.f;
-                    const float bi = o < a.ep.cout ? __ldg(a.ep.bias + o) : 0.f;
-                    float t = act_apply(fmaf(v[j], al, bi), a.ep.act);
-                    if (pool) {
-                        t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, 1));
-                        t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, ymask));
-                    }
-                    v[j] = t;
-                }
-                if (!writer) continue;
-                if (a.ep.out_layout == LAYOUT_NCHW) {
-                    float* yf = reinterpret_cast<float*>(ybase);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (o0 + j < a.ep.cout)
-                            yf[(((size_t)img * a.ep.cout + o0 + j) * Ho + yo) * Wo + xo] = v[j];
-                    continue;
-                }
-                if (o0 >= a.ep.out_cs) continue;
+            } else {
+                int p = 0;
+                while (p + 1 < a.nprob && a.probs[p + 1].tile_begin <= mt) ++p;
+                const ConvProblem& P = a.probs[p];
+                void* ybase = a.y_override ? a.y_override : P.y;
+                const int local = mt - P.tile_begin;
+                const int tx = local % P.tiles_x;
+                const int ty = (local / P.tiles_x) % P.tiles_y;
+                const int img = local / (P.tiles_x * P.tiles_y);
+                const int gy = ty * a.TH + py, gx = tx * a.TW + px;
+                const bool valid = gy < P.H && gx < P.W;
+                const int Ho = pool ? P.H / 2 : P.H, Wo = pool ? P.W / 2 : P.W;
+                const int yo = pool ? gy / 2 : gy, xo = pool ? gx / 2 : gx;
+                const bool writer = valid && (!pool || ((lane & 1) == 0 && (lane & ymask) == 0));
                 const size_t pix = ((size_t)img * Ho + yo) * Wo + xo;
-                if (a.ep.out_dt == DT_BF16) {
-                    uint4 pk[2];
-                    uint32_t* w = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll 1
+                for (int c0 = 0; c0 < HC; c0 += 32) {
+                    float v[32];
+                    __syncwarp();
+                    tc::tmem_ld32(trow + (uint32_t)c0, v);
+                    const int o0 = nt * BN + half * HC + c0;   // first output channel of the chunk
+                    // bias / alpha are padded with zeros to the weight rows: no bounds checks
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                        w[j] = *reinterpret_cast<uint32_t*>(&h2);
+                    for (int j = 0; j < 32; j += 4) {
+                        const float4 bb = __ldg(reinterpret_cast<const float4*>(a.ep.bias + o0 + j));
+                        float4 aa = make_float4(1.f, 1.f, 1.f, 1.f);
+                        if (a.ep.alpha) aa = __ldg(reinterpret_cast<const float4*>(a.ep.alpha + o0 + j));
+                        v[j] = act_apply(fmaf(v[j], aa.x, bb.x), a.ep.act);
+                        v[j + 1] = act_apply(fmaf(v[j + 1], aa.y, bb.y), a.ep.act);
+                        v[j + 2] = act_apply(fmaf(v[j + 2], aa.z, bb.z), a.ep.act);
+                        v[j + 3] = act_apply(fmaf(v[j + 3], aa.w, bb.w), a.ep.act);
                     }
-                    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ybase) +
-                                                          pix * a.ep.out_cs + o0);
-                    dst[0] = pk[0];
-                    dst[1] = pk[1];
-                } else if (a.ep.out_dt == DT_FP8) {
-                    uint4 pk;
-                    uint8_t* w = reinterpret_cast<uint8_t*>(&pk);
+                    if (a.ep.out_layout == LAYOUT_NCHW) {
+                        if (pool) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) w[j] = f32_to_e4m3_sat(v[j] * a.ep.out_inv_scale);
-                    *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(ybase) + pix * a.ep.out_cs + o0) = pk;
-                } else {
-                    float* dst = reinterpret_cast<float*>(ybase) + pix * a.ep.out_cs + o0;
+                            for (int j = 0; j < 32; ++j) {
+                                v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
+                                v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], ymask));
+                            }
+                        }
+                        if (writer) {
+                            float* yf = reinterpret_cast<float*>(ybase);
 #pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        if (o0 + j < a.ep.out_cs)
-                            *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                            for (int j = 0; j < 32; ++j)
+                                if (o0 + j < a.ep.cout)
+                                    yf[(((size_t)img * a.ep.cout + o0 + j) * Ho + yo) * Wo + xo] = v[j];
+                        }
+                        continue;
+                    }
+                    if (a.ep.out_dt == DT_BF16) {
+                        // round first, then pool on packed pairs: RNE is monotone,
+                        // so max(rn(a), rn(b)) == rn(max(a, b)) and half the shuffles go
+                        uint32_t w[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                            w[j] = *reinterpret_cast<uint32_t*>(&h2);
+                        }
+                        if (pool) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                uint32_t o = __shfl_xor_sync(0xffffffffu, w[j], 1);
+                                __nv_bfloat162 m = __hmax2(*reinterpret_cast<__nv_bfloat162*>(&w[j]),
+                                                           *reinterpret_cast<__nv_bfloat162*>(&o));
+                                w[j] = *reinterpret_cast<uint32_t*>(&m);
+                                o = __shfl_xor_sync(0xffffffffu, w[j], ymask);
+                                m = __hmax2(*reinterpret_cast<__nv_bfloat162*>(&w[j]),
+                                            *reinterpret_cast<__nv_bfloat162*>(&o));
+                                w[j] = *reinterpret_cast<uint32_t*>(&m);
+                            }
+                        }
+                        if (writer && o0 < a.ep.out_cs) {
+                            uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ybase) +
+                                                                  pix * a.ep.out_cs + o0);
+                            // out_cs is 16, 32 or a multiple of 64: a 32-channel chunk may be half outside
+                            const int nvec = (a.ep.out_cs - o0) >= 32 ? 4 : 2;
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                if (i < nvec) dst[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+                        }
+                        continue;
+                    }
+                    if (pool) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
+                            v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], ymask));
+                        }
+                    }
+                    if (!writer || o0 >= a.ep.out_cs) continue;
+                    if (a.ep.out_dt == DT_FP8) {
+                        uint4 pk[2];
+                        uint8_t* w8 = reinterpret_cast<uint8_t*>(pk);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) w8[j] = f32_to_e4m3_sat(v[j] * a.ep.out_inv_scale);
+                        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(ybase) + pix * a.ep.out_cs + o0);
+                        // out_cs is 32, 64 or a multiple of 128 here
+                        dst[0] = pk[0];
+                        dst[1] = pk[1];
+                    } else {
+                        float* dst = reinterpret_cast<float*>(ybase) + pix * a.ep.out_cs + o0;
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4)
+                            if (o0 + j < a.ep.out_cs)
+                                *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    }
                 }
             }
             tc::fence_before();

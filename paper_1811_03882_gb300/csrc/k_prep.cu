@@ -64,6 +64,66 @@ cudaError_t pack_frames(const float* x, void* y, int n, int C, int H, int W, int
     return cudaGetLastError();
 }
 
+template <typename J>
+__device__ __forceinline__ int find_job(const J* jobs, int njobs, long long i) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].begin <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int DT>
+__global__ void pack_grouped_kernel(const PackJob* __restrict__ jobs, int njobs, long long total,
+                                    float inv_scale) {
+    constexpr int V = DT == DT_F32 ? 4 : DT == DT_BF16 ? 8 : 16;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const PackJob& J = jobs[find_job(jobs, njobs, i)];
+        const long long li = i - J.begin;
+        const int groups = J.Cp / V;
+        const int g = (int)(li % groups);
+        const long long yx = li / groups;
+        const long long HW = (long long)J.H * J.W;
+        float v[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const int c = g * V + j;
+            v[j] = c < J.C ? J.src[c * HW + yx] : 0.f;
+        }
+        uint8_t* dst = reinterpret_cast<uint8_t*>(J.dst) + (yx * J.Cp + (long long)g * V) * dt_size(DT);
+        if (DT == DT_F32) {
+            *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+        } else if (DT == DT_BF16) {
+            uint4 pk;
+            uint32_t* p = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                p[j] = *reinterpret_cast<uint32_t*>(&b);
+            }
+            *reinterpret_cast<uint4*>(dst) = pk;
+        } else {
+            uint4 pk;
+            uint8_t* p = reinterpret_cast<uint8_t*>(&pk);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) p[j] = f32_to_e4m3_sat(v[j] * inv_scale);
+            *reinterpret_cast<uint4*>(dst) = pk;
+        }
+    }
+}
+
+cudaError_t pack_frames_grouped(const PackJob* jobs, int njobs, long long total, int dt, float inv_scale,
+                                cudaStream_t st) {
+    const unsigned g = grid_for((size_t)total, 256);
+    if (dt == DT_F32) pack_grouped_kernel<DT_F32><<<g, 256, 0, st>>>(jobs, njobs, total, inv_scale);
+    else if (dt == DT_BF16) pack_grouped_kernel<DT_BF16><<<g, 256, 0, st>>>(jobs, njobs, total, inv_scale);
+    else pack_grouped_kernel<DT_FP8><<<g, 256, 0, st>>>(jobs, njobs, total, inv_scale);
+    return cudaGetLastError();
+}
+
 // -------------------------------------------------------------- unpack
 __device__ __forceinline__ float load_as_f32(const void* base, size_t i, int dt, float scale) {
     if (dt == DT_F32) return reinterpret_cast<const float*>(base)[i];
@@ -127,6 +187,42 @@ __global__ void pool_s1_kernel(const uint8_t* __restrict__ x, uint8_t* __restric
         }
         *reinterpret_cast<uint4*>(y + pix * rowb + (size_t)g * 16) = best;
     }
+}
+
+__global__ void pool_s1_grouped_kernel(const PoolJob* __restrict__ jobs, int njobs, long long total, int cs,
+                                       int dt) {
+    const int esz = dt == DT_F32 ? 4 : dt == DT_BF16 ? 2 : 1;
+    const int V = 16 / esz;
+    const int groups = cs / V;
+    const size_t rowb = (size_t)cs * esz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const PoolJob& J = jobs[find_job(jobs, njobs, i)];
+        const long long li = i - J.begin;
+        const int g = (int)(li % groups);
+        const long long pix = li / groups;
+        const int xx = (int)(pix % J.W), yy = (int)(pix / J.W);
+        const uint8_t* x = reinterpret_cast<const uint8_t*>(J.x);
+        const uint8_t* p00 = x + pix * rowb + (size_t)g * 16;
+        uint4 best = *reinterpret_cast<const uint4*>(p00);
+        for (int d = 1; d < 4; ++d) {
+            const int dy = d >> 1, dx = d & 1;
+            if (yy + dy >= J.H || xx + dx >= J.W) continue;
+            uint4 cand = *reinterpret_cast<const uint4*>(p00 + ((size_t)dy * J.W + dx) * rowb);
+            uint8_t* bb = reinterpret_cast<uint8_t*>(&best);
+            const uint8_t* cb = reinterpret_cast<const uint8_t*>(&cand);
+            for (int j = 0; j < V; ++j)
+                if (dec(cb, j, dt) > dec(bb, j, dt))
+                    for (int b = 0; b < esz; ++b) bb[j * esz + b] = cb[j * esz + b];
+        }
+        *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(J.y) + pix * rowb + (size_t)g * 16) = best;
+    }
+}
+
+cudaError_t maxpool_s1_grouped(const PoolJob* jobs, int njobs, long long total, int cs, int dt,
+                               cudaStream_t st) {
+    pool_s1_grouped_kernel<<<grid_for((size_t)total, 256), 256, 0, st>>>(jobs, njobs, total, cs, dt);
+    return cudaGetLastError();
 }
 
 cudaError_t maxpool_s1_same(const void* x, void* y, int n, int H, int W, int cs, int dt,

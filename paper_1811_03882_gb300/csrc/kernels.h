@@ -105,6 +105,26 @@ struct TcArgs {
     int* err;     // bounded-wait failure code (0 = none)
 };
 
+// Grouped memory-bound helpers: one launch over several frames of
+// different sizes.  Jobs are a device table; `begin` is each job's first
+// work item (16-byte vector) in the launch's flat index space.
+struct PackJob {
+    const float* src;   // NCHW float32 frame
+    void* dst;          // NHWC, channel stride Cp
+    int C, H, W, Cp;
+    long long begin;
+};
+cudaError_t pack_frames_grouped(const PackJob* jobs, int njobs, long long total, int dt, float inv_scale,
+                                cudaStream_t st);
+struct PoolJob {
+    const void* x;
+    void* y;
+    int H, W;
+    long long begin;
+};
+cudaError_t maxpool_s1_grouped(const PoolJob* jobs, int njobs, long long total, int cs, int dt,
+                               cudaStream_t st);
+
 int tc_chunk_bytes(int Cp, int dt);
 cudaError_t tc_encode_act(CUtensorMap* tm, const void* base, int dt, int n, int H, int W, int Cp, int TW,
                           int TH);

@@ -229,9 +229,15 @@ extern "C" net_status net_load_weights(net_t* n, const float* blob, size_t n_flo
         const int dt = L.in_dt;
         const size_t wbytes = (size_t)L.w_rows * KK * L.in_cs * dt_size(dt);
         if (!L.w) e = cudaMalloc(&L.w, wbytes);
-        if (e == cudaSuccess && !L.bias) e = cudaMalloc(&L.bias, L.d.cout * sizeof(float));
+        // bias and alpha are padded with zeros to w_rows: the tensor-core
+        // epilogue reads them four at a time without bounds checks
+        if (e == cudaSuccess && !L.bias) e = cudaMalloc(&L.bias, L.w_rows * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemsetAsync(L.bias, 0, L.w_rows * sizeof(float), n->stream);
         if (e == cudaSuccess && dt == DT_FP8 && !L.wscale) e = cudaMalloc(&L.wscale, L.d.cout * sizeof(float));
-        if (e == cudaSuccess && dt == DT_FP8 && !L.alpha) e = cudaMalloc(&L.alpha, L.d.cout * sizeof(float));
+        if (e == cudaSuccess && dt == DT_FP8 && !L.alpha) {
+            e = cudaMalloc(&L.alpha, L.w_rows * sizeof(float));
+            if (e == cudaSuccess) e = cudaMemsetAsync(L.alpha, 0, L.w_rows * sizeof(float), n->stream);
+        }
         L.cs32 = rup(L.cin, 4);
         const bool want32 = n->has_fp8 && dt != DT_F32;
         if (e == cudaSuccess && want32 && !L.w32) {
@@ -299,6 +305,21 @@ Plan::~Plan() {
         if (r.d_prob) cudaFree(r.d_prob);
 }
 
+// Analytic tile/split choice for the tensor-core kernel.  Per K step of a
+// 128-byte chunk, an SM needs max(MMA cycles, L2 bytes / ~84 B per cycle):
+// the A box (16 KB) is fetched once per tap and N tile, B is BN x 128 B;
+// N = 64 MMAs also run short of shared-memory bandwidth.  Rounds of
+// ceil(items / SMs) persistent tiles, plus the split-K workspace traffic.
+static double tc_cost(long m_tiles, int ncols, int BN, int ks, int nk, int num_sms) {
+    static const double kstep_clk[3] = {292.0, 390.0, 585.0};   // BN = 64, 128, 256
+    const int bi = BN == 64 ? 0 : BN == 128 ? 1 : 2;
+    const long items = m_tiles * cdiv(ncols, BN) * ks;
+    const long rounds = (items + num_sms - 1) / num_sms;
+    double t = (double)rounds * ((double)nk / ks) * kstep_clk[bi] + rounds * 1500.0;   // + epilogue tail
+    if (ks > 1) t += (double)ks * m_tiles * 128 * cdiv(ncols, BN) * BN * 4.0 * 2.0 / 3450.0;
+    return t;
+}
+
 void dn::tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, int* TW, int* TH, int* BN) {
     static const int tws[5] = {16, 8, 32, 64, 128};
     long best = -1;
@@ -312,15 +333,28 @@ void dn::tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, i
             *TH = th;
         }
     }
-    const long m_tiles = (long)batch * cdiv(H, *TH) * cdiv(W, *TW);
-    // widest N tile that still gives every SM a tile; else the narrowest
-    *BN = 64;
-    for (int bn : {256, 128}) {
+    (void)batch;
+    (void)num_sms;
+    *BN = ncols > 128 ? 256 : ncols > 64 ? 128 : 64;   // refined by tc_choose_split
+}
+
+// Picks BN and the split-K factor together with the cost model above.
+void dn::tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks) {
+    double best = -1.0;
+    for (int bn : {64, 128, 256}) {
         if (bn > rup(ncols, 64)) continue;
-        if (m_tiles * cdiv(ncols, bn) >= num_sms) {
-            *BN = bn;
-            break;
+        for (int ks = 1; ks <= max_ks && (ks == 1 || ks * 4 <= nk); ks = ks < 2 ? ks + 1 : ks * 2) {
+            const double t = tc_cost(m_tiles, ncols, bn, ks, nk, num_sms);
+            if (best < 0 || t < best) {
+                best = t;
+                *BN = bn;
+                *ksplit = ks;
+            }
         }
+    }
+    if (best < 0) {
+        *BN = 64;
+        *ksplit = 1;
     }
 }
 
@@ -363,11 +397,10 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
         if (L.engine == ENG_TC) {
             tc_choose(batch, r.H, r.W, L.d.pool == NET_POOL_2X2S2, ncols, n->num_sms, &r.TW, &r.TH, &r.BN);
             r.m_tiles = batch * cdiv(r.H, r.TH) * cdiv(r.W, r.TW);
+            const int nk = KK * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
+            tc_choose_split(r.m_tiles, ncols, nk, n->num_sms, &r.BN, &r.ksplit);
             r.n_tiles = cdiv(ncols, r.BN);
             const int tiles = r.m_tiles * r.n_tiles;
-            const int nk = KK * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
-            if (tiles < n->num_sms && nk >= 16)
-                r.ksplit = std::max(1, std::min({cdiv(n->num_sms, tiles), nk / 8, 16}));
             if (r.ksplit > 1)
                 P->ws_bytes = std::max(P->ws_bytes, (size_t)r.ksplit * r.m_tiles * 128 * r.n_tiles * r.BN *
                                                         sizeof(float));
@@ -550,6 +583,7 @@ void net::graphs_clear() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
     graph_kernels.clear();
+    uneven_graphs_clear(this);   // uneven-batch graphs bake epilogue scales and weight maps too
 }
 
 net_status dn::run_forward(net* n, const float* d_in, int batch, int h, int w, float* d_out) {

@@ -51,6 +51,7 @@ struct Plan {
 // TC tile choice for an H x W map (pooled layers need whole 2x2 windows in
 // one warp: TW = 8 or 16).
 void tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, int* TW, int* TH, int* BN);
+void tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks = 16);
 
 struct UnevenState;
 struct ServeState;
@@ -105,6 +106,7 @@ net_status run_forward(net* n, const float* d_in, int batch, int h, int w, float
 net_status enqueue_uneven(net* n, const float* const* d_in, const int* side, int cnt,
                           float* const* d_out);
 void uneven_free(net* n);
+void uneven_graphs_clear(net* n);
 void serve_stop(net* n);
 
 }  // namespace dn
