@@ -151,6 +151,46 @@ net_status net_wait(net_t* net, uint64_t req_id, float* out, size_t cap_floats, 
  * latency percentiles (completion minus submission). */
 net_status net_stats(net_t* net, double* fps, double* p50_ms, double* p99_ms);
 
+/* ---- per-layer precision ------------------------------------------------
+ * A handle created with NET_FP8 keeps, for every tensor-core layer, both an
+ * E4M3 and a BF16 copy of its folded weights, so each such layer can run in
+ * either format.  net_set_layer_prec takes n_layers net_precision values
+ * (other layers must keep the precision they were created with). */
+net_status net_set_layer_prec(net_t* net, const int* layer_prec, int n);
+net_status net_get_layer_prec(const net_t* net, int* layer_prec, int n);
+
+/* Genetic search over the FP8/BF16 choice of every switchable layer: the
+ * paper's offload search (Sec. 3.3, 4; parameters of Sec. 5.1.2) with one
+ * gene per layer instead of per loop.  Fitness is (time per forward pass in
+ * ms)^(-1/2); a plan whose output on d_frames deviates from the FP32 path by
+ * more than max_err (normwise max relative error) scores as a 10^6 ms run,
+ * like the paper's timed-out individuals; the best individual survives
+ * unchanged; parents are drawn by roulette; single-point crossover with
+ * probability `crossover`, bit-flip mutation with probability `mutation`;
+ * a gene seen before reuses its measurement.  FP8 activation scales must be
+ * set (net_calibrate).  On NET_OK the handle is left on the best plan and
+ * layer_prec_out (n_layers entries) holds it; NET_E_STATE if no plan met
+ * the budget (the handle keeps its previous formats). */
+typedef struct {
+    int population;          /* M (paper: 30, at most the gene length)        */
+    int generations;         /* T (paper: 20)                                 */
+    double crossover;        /* Pc (paper: 0.9)                               */
+    double mutation;         /* Pm (paper: 0.05)                              */
+    double max_err;          /* error budget against the FP32 path            */
+    int reps;                /* timed forward passes per evaluation            */
+    unsigned long long seed; /* search random stream (0: fixed default)        */
+} net_ga_opts;
+
+typedef struct {
+    double ms, err;                  /* best plan                               */
+    double ms_all_bf16, err_all_bf16;/* every switchable layer in BF16          */
+    double ms_all_fp8, err_all_fp8;  /* every switchable layer in FP8           */
+    int evaluations, memo_hits, fp8_layers;
+} net_ga_result;
+
+net_status net_tune_precision(net_t* net, const float* d_frames, int batch, int h, int w,
+                              const net_ga_opts* opts, int* layer_prec_out, net_ga_result* result);
+
 /* Per-layer timing: with enable != 0 every later forward pass records a
  * CUDA event pair around each layer's conv kernel (on the handle's stream;
  * CUDA-graph replays record them too).  net_layer_times waits for the most

@@ -45,6 +45,19 @@ class net_desc(ctypes.Structure):
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
 
 
+class net_ga_opts(ctypes.Structure):
+    _fields_ = [("population", ctypes.c_int), ("generations", ctypes.c_int),
+                ("crossover", ctypes.c_double), ("mutation", ctypes.c_double),
+                ("max_err", ctypes.c_double), ("reps", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
+
+
+class net_ga_result(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("err", ctypes.c_double),
+                ("ms_all_bf16", ctypes.c_double), ("err_all_bf16", ctypes.c_double),
+                ("ms_all_fp8", ctypes.c_double), ("err_all_fp8", ctypes.c_double),
+                ("evaluations", ctypes.c_int), ("memo_hits", ctypes.c_int), ("fp8_layers", ctypes.c_int)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -71,6 +84,10 @@ _SIGS = {
     "net_wait": [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int],
     "net_stats": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                   ctypes.POINTER(ctypes.c_double)],
+    "net_set_layer_prec": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
+    "net_get_layer_prec": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
+    "net_tune_precision": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                           ctypes.POINTER(net_ga_opts), ctypes.c_void_p, ctypes.POINTER(net_ga_result)],
     "net_profile": [ctypes.c_void_p, ctypes.c_int],
     "net_layer_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "net_launches": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
@@ -213,6 +230,27 @@ class Net:
 
     def wait(self, rid: int, out: np.ndarray, timeout_ms: int = -1):
         check(lib().net_wait(self.h, rid, _ptr(out), out.size, timeout_ms))
+
+    def set_layer_prec(self, precs):
+        a = np.ascontiguousarray([PREC.get(p, p) for p in precs], dtype=np.int32)
+        check(lib().net_set_layer_prec(self.h, _ptr(a), a.size))
+
+    def layer_prec(self):
+        a = np.zeros(self.n_layers, np.int32)
+        check(lib().net_get_layer_prec(self.h, _ptr(a), a.size))
+        names = {v: k for k, v in PREC.items()}
+        return [names[int(v)] for v in a]
+
+    def tune_precision(self, d_frames, batch, h, w, max_err, population=16, generations=12,
+                       crossover=0.9, mutation=0.05, reps=3, seed=0):
+        """Genetic FP8/BF16 plan search; returns (layer precisions, result dict)."""
+        o = net_ga_opts(population, generations, crossover, mutation, max_err, reps, seed)
+        r = net_ga_result()
+        out = np.zeros(self.n_layers, np.int32)
+        check(lib().net_tune_precision(self.h, _ptr(d_frames), batch, h, w, ctypes.byref(o), _ptr(out),
+                                       ctypes.byref(r)))
+        names = {v: k for k, v in PREC.items()}
+        return [names[int(v)] for v in out], {f: getattr(r, f) for f, _ in net_ga_result._fields_}
 
     def profile(self, enable: bool = True):
         check(lib().net_profile(self.h, int(enable)))

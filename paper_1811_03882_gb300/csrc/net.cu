@@ -155,7 +155,12 @@ extern "C" net_status net_create(const net_desc* d, net_t** out) {
         cin = s.cout;
     }
     for (auto& L : n->L)
-        if (L.prec == NET_FP8) n->has_fp8 = true;
+        if (L.prec == NET_FP8) {
+            n->has_fp8 = true;
+            L.fp8_capable = true;
+            L.cs_var[0] = pad_channels(L.cin, DT_BF16, true);
+            L.cs_var[1] = pad_channels(L.cin, DT_FP8, true);
+        }
     if (d->cuda_stream) {
         n->stream = (cudaStream_t)d->cuda_stream;
     } else {
@@ -167,6 +172,17 @@ extern "C" net_status net_create(const net_desc* d, net_t** out) {
     *n->err_host = 0;
     CK(cudaHostGetDevicePointer((void**)&n->err_dev, n->err_host, 0));
     n->act_bytes = act_bytes_for(n.get(), n->max_batch, n->max_side, n->max_side);
+    if (n->has_fp8) {
+        // room for every FP8-capable layer switched to BF16 (the wider format)
+        std::vector<Layer> keep = n->L;
+        for (auto& L : n->L)
+            if (L.fp8_capable) {
+                L.in_dt = DT_BF16;
+                L.in_cs = L.cs_var[0];
+            }
+        n->act_bytes = std::max(n->act_bytes, act_bytes_for(n.get(), n->max_batch, n->max_side, n->max_side));
+        n->L = keep;
+    }
     for (int i = 0; i < 2; ++i) {
         CK(cudaMalloc(&n->act[i], n->act_bytes));
         CK(cudaMemsetAsync(n->act[i], 0, n->act_bytes, n->stream));
@@ -193,6 +209,20 @@ extern "C" net_status net_output_shape(const net_t* n, int h, int w, int* c, int
 }
 
 // ------------------------------------------------------------- weights
+static const int bns_all[3] = {64, 128, 256};
+
+void dn::set_layer_format(Layer& L, int prec) {
+    if (!L.fp8_capable) return;
+    const int v = prec == NET_FP8 ? 1 : 0;
+    L.prec = v ? NET_FP8 : NET_BF16;
+    L.in_dt = v ? DT_FP8 : DT_BF16;
+    L.in_cs = L.cs_var[v];
+    if (L.w_var[v]) {
+        L.w = L.w_var[v];
+        std::memcpy(L.tmB, L.tmB_var[v], sizeof(L.tmB));
+    }
+}
+
 extern "C" net_status net_load_weights(net_t* n, const float* blob, size_t n_floats) {
     if (!n || !blob) return fail(NET_E_INVAL, "NULL argument");
     size_t need = 0;
@@ -233,8 +263,9 @@ extern "C" net_status net_load_weights(net_t* n, const float* blob, size_t n_flo
         // epilogue reads them four at a time without bounds checks
         if (e == cudaSuccess && !L.bias) e = cudaMalloc(&L.bias, L.w_rows * sizeof(float));
         if (e == cudaSuccess) e = cudaMemsetAsync(L.bias, 0, L.w_rows * sizeof(float), n->stream);
-        if (e == cudaSuccess && dt == DT_FP8 && !L.wscale) e = cudaMalloc(&L.wscale, L.d.cout * sizeof(float));
-        if (e == cudaSuccess && dt == DT_FP8 && !L.alpha) {
+        const bool fp8w = dt == DT_FP8 || L.fp8_capable;
+        if (e == cudaSuccess && fp8w && !L.wscale) e = cudaMalloc(&L.wscale, L.d.cout * sizeof(float));
+        if (e == cudaSuccess && fp8w && !L.alpha) {
             e = cudaMalloc(&L.alpha, L.w_rows * sizeof(float));
             if (e == cudaSuccess) e = cudaMemsetAsync(L.alpha, 0, L.w_rows * sizeof(float), n->stream);
         }
@@ -265,7 +296,30 @@ extern "C" net_status net_load_weights(net_t* n, const float* blob, size_t n_flo
             for (int i = 0; i < 3 && e == cudaSuccess; ++i)
                 e = tc_encode_weights(&L.tmB[i], L.w, dt, L.w_rows, KK, L.in_cs, bns[i]);
         }
-        if (e == cudaSuccess && dt == DT_FP8) e = make_alpha(L.wscale, L.act_scale, L.alpha, L.d.cout, n->stream);
+        if (e == cudaSuccess && L.fp8_capable) {
+            // both formats, whichever is active now: FP8 [1] and BF16 [0]
+            for (int v = 0; v < 2 && e == cudaSuccess; ++v) {
+                const int vdt = v ? DT_FP8 : DT_BF16;
+                if (vdt == dt) {
+                    L.w_var[v] = L.w;
+                    std::memcpy(L.tmB_var[v], L.tmB, sizeof(L.tmB));
+                    continue;
+                }
+                const size_t vb = (size_t)L.w_rows * KK * L.cs_var[v] * dt_size(vdt);
+                if (!L.w_var[v]) e = cudaMalloc(&L.w_var[v], vb);
+                if (e != cudaSuccess) break;
+                FoldArgs b = a;
+                b.Cp = L.cs_var[v];
+                b.dt = vdt;
+                b.out_w = L.w_var[v];
+                b.out_w32 = nullptr;
+                b.out_wscale = v ? L.wscale : nullptr;
+                e = fold_layer(b, n->stream);
+                for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+                    e = tc_encode_weights(&L.tmB_var[v][i], L.w_var[v], vdt, L.w_rows, KK, L.cs_var[v], bns_all[i]);
+            }
+        }
+        if (e == cudaSuccess && fp8w) e = make_alpha(L.wscale, L.act_scale, L.alpha, L.d.cout, n->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
     cudaFree(d_blob);
@@ -286,7 +340,7 @@ extern "C" net_status net_set_act_scales(net_t* n, const float* scales, int cnt)
     for (int l = 0; l < cnt; ++l) {
         Layer& L = n->L[l];
         L.act_scale = scales[l];
-        if (L.in_dt == DT_FP8 && L.alpha && L.wscale) {
+        if ((L.in_dt == DT_FP8 || L.fp8_capable) && L.alpha && L.wscale) {
             cudaError_t e = make_alpha(L.wscale, L.act_scale, L.alpha, L.d.cout, n->stream);
             if (e != cudaSuccess) return fail(NET_E_CUDA, "alpha: %s", cudaGetErrorString(e));
         }
@@ -698,6 +752,39 @@ extern "C" net_status net_launches(const net_t* n, uint64_t* total) {
     return NET_OK;
 }
 
+net_status dn::run_fp32_reference(net* n, const float* d_frames, int batch, int h, int w, float* d_out,
+                                  float* amax) {
+    // FP32 buffers for the pass over the FP32 copy of the folded weights
+    std::vector<int> H, W;
+    layer_dims(n, h, w, H, W);
+    size_t mx = 0;
+    for (size_t l = 0; l < n->L.size(); ++l) {
+        mx = std::max(mx, (size_t)batch * H[l] * W[l] * n->L[l].cs32 * 4);
+        mx = std::max(mx, (size_t)batch * H[l + 1] * W[l + 1] * rup(n->L[l].d.cout, 4) * 4);
+    }
+    CK(cudaMalloc(&n->cal[0], mx));
+    cudaError_t e = cudaMalloc(&n->cal[1], mx);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->cal[0], 0, mx, n->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->cal[1], 0, mx, n->stream);
+    // layers whose own weights are FP32 use them directly
+    std::vector<float*> saved(n->L.size());
+    for (size_t l = 0; l < n->L.size(); ++l) {
+        saved[l] = n->L[l].w32;
+        if (!n->L[l].w32) n->L[l].w32 = reinterpret_cast<float*>(n->L[l].w);
+    }
+    net_status s = e == cudaSuccess ? enqueue_forward(n, d_frames, batch, h, w, d_out, nullptr, true, amax)
+                                    : fail(NET_E_OOM, "reference buffers: %s", cudaGetErrorString(e));
+    if (s == NET_OK) {
+        e = cudaStreamSynchronize(n->stream);
+        if (e != cudaSuccess) s = fail(NET_E_CUDA, "reference pass: %s", cudaGetErrorString(e));
+    }
+    for (size_t l = 0; l < n->L.size(); ++l) n->L[l].w32 = saved[l];
+    cudaFree(n->cal[0]);
+    cudaFree(n->cal[1]);
+    n->cal[0] = n->cal[1] = nullptr;
+    return s;
+}
+
 extern "C" net_status net_calibrate(net_t* n, const float* d_frames, int batch, int h, int w,
                                     float* scales_out) {
     if (!n || !d_frames) return fail(NET_E_INVAL, "NULL argument");
@@ -706,38 +793,15 @@ extern "C" net_status net_calibrate(net_t* n, const float* d_frames, int batch, 
     net_status s = check_shape(n, batch, h, w);
     if (s != NET_OK) return s;
     CK(cudaSetDevice(n->device));
-    // FP32 buffers for the calibration pass (FP32 copy of the folded weights)
-    std::vector<int> H, W;
-    layer_dims(n, h, w, H, W);
-    size_t mx = 0;
-    for (size_t l = 0; l < n->L.size(); ++l) {
-        mx = std::max(mx, (size_t)batch * H[l] * W[l] * n->L[l].cs32 * 4);
-        mx = std::max(mx, (size_t)batch * H[l + 1] * W[l + 1] * rup(n->L[l].d.cout, 4) * 4);
-    }
     float *amax = nullptr, *dout = nullptr;
     int c, ho, wo;
     net_output_shape(n, h, w, &c, &ho, &wo);
-    CK(cudaMalloc(&n->cal[0], mx));
-    CK(cudaMalloc(&n->cal[1], mx));
     CK(cudaMalloc(&amax, n->L.size() * sizeof(float)));
     CK(cudaMalloc(&dout, (size_t)batch * c * ho * wo * sizeof(float)));
-    CK(cudaMemsetAsync(n->cal[0], 0, mx, n->stream));
-    CK(cudaMemsetAsync(n->cal[1], 0, mx, n->stream));
     CK(cudaMemsetAsync(amax, 0, n->L.size() * sizeof(float), n->stream));
-    // layers whose own weights are FP32 use them directly
-    std::vector<float*> saved(n->L.size());
-    for (size_t l = 0; l < n->L.size(); ++l) {
-        saved[l] = n->L[l].w32;
-        if (!n->L[l].w32) n->L[l].w32 = reinterpret_cast<float*>(n->L[l].w);
-    }
-    s = enqueue_forward(n, d_frames, batch, h, w, dout, nullptr, true, amax);
+    s = run_fp32_reference(n, d_frames, batch, h, w, dout, amax);
     std::vector<float> hm(n->L.size());
-    cudaError_t e = cudaMemcpyAsync(hm.data(), amax, hm.size() * sizeof(float), cudaMemcpyDeviceToHost, n->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
-    for (size_t l = 0; l < n->L.size(); ++l) n->L[l].w32 = saved[l];
-    cudaFree(n->cal[0]);
-    cudaFree(n->cal[1]);
-    n->cal[0] = n->cal[1] = nullptr;
+    cudaError_t e = cudaMemcpy(hm.data(), amax, hm.size() * sizeof(float), cudaMemcpyDeviceToHost);
     cudaFree(amax);
     cudaFree(dout);
     if (s != NET_OK) return s;
@@ -746,6 +810,37 @@ extern "C" net_status net_calibrate(net_t* n, const float* d_frames, int batch, 
     for (size_t l = 0; l < n->L.size(); ++l) sc[l] = std::max(hm[l], 1e-30f) / kFp8Max;
     if (scales_out) std::memcpy(scales_out, sc.data(), sc.size() * sizeof(float));
     return net_set_act_scales(n, sc.data(), (int)sc.size());
+}
+
+void dn::invalidate_plans(net* n) {
+    n->graphs_clear();
+    for (auto& kv : n->plans) delete kv.second;
+    n->plans.clear();
+    uneven_free(n);
+}
+
+extern "C" net_status net_set_layer_prec(net_t* n, const int* prec, int cnt) {
+    if (!n || !prec) return fail(NET_E_INVAL, "NULL argument");
+    if (cnt != (int)n->L.size()) return fail(NET_E_INVAL, "need %zu entries", n->L.size());
+    for (int l = 0; l < cnt; ++l) {
+        const Layer& L = n->L[l];
+        const bool ok = L.fp8_capable ? (prec[l] == NET_FP8 || prec[l] == NET_BF16) : prec[l] == L.prec;
+        if (!ok)
+            return fail(NET_E_INVAL, "layer %d: precision %d not available (created as %d%s)", l, prec[l], L.prec,
+                        L.fp8_capable ? ", FP8/BF16 switchable" : "");
+    }
+    CK(cudaSetDevice(n->device));
+    CK(cudaStreamSynchronize(n->stream));
+    for (int l = 0; l < cnt; ++l) set_layer_format(n->L[l], prec[l]);
+    invalidate_plans(n);
+    return NET_OK;
+}
+
+extern "C" net_status net_get_layer_prec(const net_t* n, int* prec, int cnt) {
+    if (!n || !prec) return fail(NET_E_INVAL, "NULL argument");
+    if (cnt != (int)n->L.size()) return fail(NET_E_INVAL, "need %zu entries", n->L.size());
+    for (int l = 0; l < cnt; ++l) prec[l] = n->L[l].prec;
+    return NET_OK;
 }
 
 extern "C" net_status net_forward_uneven(net_t* n, const float* const* d_in, const int* side, int cnt,
@@ -769,6 +864,8 @@ extern "C" net_status net_free(net_t* n) {
     n->graphs_clear();
     for (auto ev : n->prof_ev) cudaEventDestroy(ev);
     for (auto& L : n->L) {
+        for (int v = 0; v < 2; ++v)
+            if (L.w_var[v] && L.w_var[v] != L.w) cudaFree(L.w_var[v]);
         cudaFree(L.w);
         cudaFree(L.bias);
         cudaFree(L.wscale);

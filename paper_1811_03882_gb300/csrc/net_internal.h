@@ -29,7 +29,22 @@ struct Layer {
     float* w32 = nullptr;     // FP32 copy of W' for calibration (FP8 nets)
     double act_scale = 1.0;   // FP8 scale of this layer's input
     CUtensorMap tmB[3];       // TC weights, box rows BN = 64, 128, 256
+    // Layers created as FP8 tensor-core layers also keep a BF16 copy, so the
+    // precision of each can be switched after loading (precision search).
+    bool fp8_capable = false;
+    void* w_var[2] = {nullptr, nullptr};   // [0] BF16, [1] FP8 weights
+    CUtensorMap tmB_var[2][3];
+    int cs_var[2] = {0, 0};                // channel stride of each format
 };
+
+// Switches an FP8-capable layer between its BF16 and FP8 operands.
+void set_layer_format(Layer& L, int prec);
+// Drops every plan and graph that baked a layer format in.
+void invalidate_plans(net* n);
+// Runs the FP32 copy of the folded weights over d_frames into d_out
+// (NCHW float32) and, if amax is not null, the per-layer input max|x|.
+net_status run_fp32_reference(net* n, const float* d_frames, int batch, int h, int w, float* d_out,
+                              float* amax);
 
 // Launch plan of one layer for one input shape.
 struct LayerRun {

@@ -1,0 +1,206 @@
+// tune.cu — genetic search over per-layer operand precision.
+//
+// The paper's offload search (Sec. 3.3 and 4; parameters in Sec. 5.1.2)
+// encodes one bit per parallelisable loop (1 = run it on the GPU), measures
+// each candidate program, scores it with fitness = (time)^(-1/2), keeps the
+// best individual unchanged (elitism), picks parents by roulette in
+// proportion to fitness, crosses them at one point with rate Pc = 0.9,
+// flips each bit with rate Pm = 0.05, reuses the measurement of a gene seen
+// before instead of re-running it, and scores a run that exceeds the time
+// limit as if it took 1000 s.  Here the same search runs over the choice
+// the paper's loops have no counterpart for but this pass does: one bit per
+// FP8-capable layer, 1 = E4M3 operands, 0 = BF16.  A plan whose output
+// leaves the error budget (normwise max relative error against the FP32
+// path on the caller's frames) is scored like the paper's timed-out runs.
+// Times are CUDA-event measurements of the whole forward pass.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "../../include/net.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "net_internal.h"
+
+using namespace dn;
+
+namespace {
+
+struct Rng {   // SplitMix64 stream
+    uint64_t s;
+    uint64_t next() {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+    int below(int n) { return (int)(next() % (uint64_t)n); }
+};
+
+struct Eval {
+    double ms = 0.0, err = 0.0, fitness = 0.0;
+};
+
+constexpr double kTimeoutMs = 1.0e6;   // the paper's "counts as 1000 s"
+
+}  // namespace
+
+extern "C" net_status net_tune_precision(net_t* n, const float* d_frames, int batch, int h, int w,
+                                         const net_ga_opts* opt, int* prec_out, net_ga_result* res) {
+    if (!n || !d_frames || !opt || !prec_out || !res) return fail(NET_E_INVAL, "NULL argument");
+    if (!n->weights_loaded) return fail(NET_E_WEIGHTS, "weights not loaded");
+    if (opt->population < 2 || opt->generations < 1 || opt->reps < 1 || !(opt->max_err > 0) ||
+        opt->crossover < 0 || opt->crossover > 1 || opt->mutation < 0 || opt->mutation > 1)
+        return fail(NET_E_INVAL, "bad search options");
+    net_status s = check_shape(n, batch, h, w);
+    if (s != NET_OK) return s;
+    std::vector<int> genes;   // layer index of each gene
+    for (int l = 0; l < (int)n->L.size(); ++l)
+        if (n->L[l].fp8_capable) genes.push_back(l);
+    if (genes.empty()) return fail(NET_E_STATE, "no FP8-capable layer: create the handle with NET_FP8");
+    cudaError_t e = cudaSetDevice(n->device);
+    if (e != cudaSuccess) return fail(NET_E_CUDA, "%s", cudaGetErrorString(e));
+    const int nl = (int)n->L.size();
+    int c, ho, wo;
+    net_output_shape(n, h, w, &c, &ho, &wo);
+    const size_t nout = (size_t)batch * c * ho * wo;
+    float *d_ref = nullptr, *d_out = nullptr;
+    if (cudaMalloc(&d_ref, nout * sizeof(float)) != cudaSuccess || cudaMalloc(&d_out, nout * sizeof(float)) != cudaSuccess) {
+        cudaFree(d_ref);
+        return fail(NET_E_OOM, "search buffers");
+    }
+    std::vector<float> ref(nout), out(nout);
+    std::vector<int> saved(nl);
+    for (int l = 0; l < nl; ++l) saved[l] = n->L[l].prec;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+
+    // reference: the FP32 path over the same frames
+    s = run_fp32_reference(n, d_frames, batch, h, w, d_ref, nullptr);
+    if (s == NET_OK && cudaMemcpy(ref.data(), d_ref, nout * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+        s = fail(NET_E_CUDA, "reference copy");
+    double rmax = 0.0;
+    for (float v : ref) rmax = std::max(rmax, (double)std::fabs(v));
+    if (rmax == 0.0) rmax = 1.0;
+
+    std::map<std::vector<int>, Eval> memo;
+    int evaluations = 0, hits = 0;
+    auto evaluate = [&](const std::vector<int>& g) -> Eval {
+        auto it = memo.find(g);
+        if (it != memo.end()) {
+            ++hits;
+            return it->second;
+        }
+        Eval ev;
+        for (size_t i = 0; i < genes.size(); ++i) set_layer_format(n->L[genes[i]], g[i] ? NET_FP8 : NET_BF16);
+        invalidate_plans(n);
+        net_status st = run_forward(n, d_frames, batch, h, w, d_out);   // plans, capture, warm-up
+        if (st == NET_OK) {
+            cudaEventRecord(e0, n->stream);
+            for (int r = 0; r < opt->reps && st == NET_OK; ++r) st = run_forward(n, d_frames, batch, h, w, d_out);
+            cudaEventRecord(e1, n->stream);
+        }
+        float ms = 0.f;
+        if (st == NET_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            cudaMemcpy(out.data(), d_out, nout * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess &&
+            check_device_error(n) == NET_OK) {
+            double d = 0.0;
+            for (size_t i = 0; i < nout; ++i) d = std::max(d, std::fabs((double)out[i] - (double)ref[i]));
+            ev.ms = ms / opt->reps;
+            ev.err = d / rmax;
+            if (!std::isfinite(ev.err)) ev.err = 1e30;
+        } else {
+            ev.ms = kTimeoutMs;
+            ev.err = 1e30;
+        }
+        const double t = ev.err <= opt->max_err ? ev.ms : kTimeoutMs;
+        ev.fitness = 1.0 / std::sqrt(t);
+        memo[g] = ev;
+        ++evaluations;
+        return ev;
+    };
+
+    const int a = (int)genes.size();
+    Rng rng{opt->seed ? opt->seed : 0x1811038820ull};
+    std::vector<std::vector<int>> pop(opt->population, std::vector<int>(a));
+    for (auto& g : pop)
+        for (int& b : g) b = rng.below(2);
+    std::vector<int> best_g(a, 0);
+    Eval best;
+    best.fitness = -1.0;
+    for (int gen = 0; gen < opt->generations && s == NET_OK; ++gen) {
+        std::vector<Eval> ev(pop.size());
+        double fsum = 0.0;
+        int elite = 0;
+        for (size_t i = 0; i < pop.size(); ++i) {
+            ev[i] = evaluate(pop[i]);
+            fsum += ev[i].fitness;
+            if (ev[i].fitness > ev[elite].fitness) elite = (int)i;
+            if (ev[i].fitness > best.fitness) {
+                best = ev[i];
+                best_g = pop[i];
+            }
+        }
+        if (gen + 1 == opt->generations) break;
+        // next generation: elite kept unchanged, the rest bred from roulette parents
+        auto roulette = [&]() -> const std::vector<int>& {
+            double r = rng.uniform() * fsum;
+            for (size_t i = 0; i < pop.size(); ++i) {
+                r -= ev[i].fitness;
+                if (r <= 0) return pop[i];
+            }
+            return pop.back();
+        };
+        std::vector<std::vector<int>> next;
+        next.push_back(pop[elite]);
+        while ((int)next.size() < opt->population) {
+            std::vector<int> p1 = roulette(), p2 = roulette();
+            if (a > 1 && rng.uniform() < opt->crossover) {
+                const int cut = 1 + rng.below(a - 1);
+                for (int i = cut; i < a; ++i) std::swap(p1[i], p2[i]);
+            }
+            for (auto* ch : {&p1, &p2}) {
+                for (int& b : *ch)
+                    if (rng.uniform() < opt->mutation) b ^= 1;
+                if ((int)next.size() < opt->population) next.push_back(*ch);
+            }
+        }
+        pop.swap(next);
+    }
+    // reference points for the report
+    Eval all_bf16, all_fp8;
+    if (s == NET_OK) {
+        all_bf16 = evaluate(std::vector<int>(a, 0));
+        all_fp8 = evaluate(std::vector<int>(a, 1));
+    }
+    // leave the handle on the best feasible plan (else on its original formats)
+    const bool feasible = best.fitness > 1.0 / std::sqrt(kTimeoutMs) + 1e-12 && best.err <= opt->max_err;
+    for (int l = 0; l < nl; ++l) set_layer_format(n->L[l], saved[l]);
+    if (feasible)
+        for (size_t i = 0; i < genes.size(); ++i) set_layer_format(n->L[genes[i]], best_g[i] ? NET_FP8 : NET_BF16);
+    invalidate_plans(n);
+    for (int l = 0; l < nl; ++l) prec_out[l] = n->L[l].prec;
+    std::memset(res, 0, sizeof(*res));
+    res->ms = best.ms;
+    res->err = best.err;
+    res->ms_all_bf16 = all_bf16.ms;
+    res->err_all_bf16 = all_bf16.err;
+    res->ms_all_fp8 = all_fp8.ms;
+    res->err_all_fp8 = all_fp8.err;
+    res->evaluations = evaluations;
+    res->memo_hits = hits;
+    res->fp8_layers = feasible ? (int)std::count(best_g.begin(), best_g.end(), 1) : -1;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_ref);
+    cudaFree(d_out);
+    if (s != NET_OK) return s;
+    if (!feasible) return fail(NET_E_STATE, "no plan within the error budget %g", opt->max_err);
+    return NET_OK;
+}
