@@ -36,7 +36,9 @@ WORKLOADS = {
     # 64 frames, sides drawn from {320, 416, 512, 608}, one grouped launch per layer
     "uneven64-9conv-bf16": ("9-conv", 64, 0, "bf16", synth.SEED_UNEVEN),
 }
-DEFAULT = "9conv-416-b1-fp32"
+# open-loop serving streams: 32 cameras, Poisson arrivals, sides {320,416,608}
+SERVE_RATES = (200.0, 1000.0, 4000.0)
+DEFAULT = "19conv-448-b8-bf16"
 
 # ncu DRAM traffic per launch of the dominant kernel (read + write bytes),
 # from the capture summarised under profiles/; None until captured.
@@ -157,6 +159,237 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, torch, binding, dev):
+    """Serving streams through the request queue (net_submit / net_wait):
+    32 cameras with Poisson arrivals at each aggregate rate, frame sides
+    drawn from {320, 416, 608}, the 19-conv network with a GA-tuned FP8/BF16
+    plan, a 40 GB activation budget.  Latency = completion - submission,
+    measured by the library; the submitters keep to the arrival schedule
+    (their lag is reported) so the queue does not hide load."""
+    import queue
+    import threading
+    spec = synth.net_19conv()
+    blob = synth.weights_for(spec, synth.SEED_SERVE)
+    sides = (320, 416, 608)
+    pool = {s_: [synth.frame_for(synth.SEED_SERVE, i, s_) for i in range(4)] for s_ in sides}
+    duration, warm = args.serve_seconds, 1.0
+    out = {"rates": {}}
+
+    def make(prec):
+        net = binding.Net(spec.layers, 3, prec=prec, max_batch=1, max_side=608, budget_bytes=40 << 30, device=dev)
+        net.load_weights(blob)
+        return net
+
+    # FP32 unbatched reference: each frame alone through the host API
+    n32 = make("fp32")
+    lat32 = []
+    for s_ in sides:
+        f = pool[s_][0]
+        o = np.empty((1,) + n32.output_shape(s_, s_), np.float32)
+        n32.forward(f, o)
+        for _ in range(3):
+            t0 = time.perf_counter()
+            n32.forward(f, o)
+            lat32.append((s_, 1e3 * (time.perf_counter() - t0)))
+    n32.close()
+    mean32 = {s_: float(np.mean([t for ss, t in lat32 if ss == s_])) for s_ in sides}
+    out["fp32_unbatched_ms"] = mean32
+    out["fp32_unbatched_max_fps"] = 1e3 / float(np.mean(list(mean32.values())))
+
+    net = make("fp8")
+    xc = synth.make_frames(synth.Stream(synth.SEED_CALIB), 1, 3, 416, 416)
+    d_c = torch.from_numpy(xc).cuda()
+    net.calibrate(d_c, 1, 416, 416)
+    plan, ga = net.tune_precision(d_c, 1, 416, 416, max_err=0.05, population=12, generations=8, reps=2, seed=5)
+    out["plan"] = plan
+    out["ga"] = ga
+    for rate in SERVE_RATES:
+        t_arr, cam, side = synth.poisson_arrivals(rate, warm + duration, synth.SEED_SERVE)
+        pending = queue.Queue()
+        lag = []
+        n_sub = 4
+        t0 = time.perf_counter() + 0.05
+
+        def submitter(k):
+            for i in range(k, len(t_arr), n_sub):
+                now = time.perf_counter() - t0
+                if t_arr[i] > now:
+                    time.sleep(t_arr[i] - now)
+                f = pool[int(side[i])][i % 4]
+                lag.append(time.perf_counter() - t0 - t_arr[i])
+                pending.put((net.submit(f), int(side[i])))
+            pending.put(None)
+
+        done_ct = [0]
+
+        def collector():
+            ends = 0
+            while ends < n_sub:
+                it = pending.get()
+                if it is None:
+                    ends += 1
+                    continue
+                rid, s_ = it
+                o = np.empty((1,) + net.output_shape(s_, s_), np.float32)
+                net.wait(rid, o, 120000)
+                done_ct[0] += 1
+
+        def reset_after_warmup():
+            time.sleep(max(0.0, t0 + warm - time.perf_counter()))
+            net.stats_reset()
+
+        ths = [threading.Thread(target=submitter, args=(k,)) for k in range(n_sub)]
+        ths.append(threading.Thread(target=reset_after_warmup))
+        col = threading.Thread(target=collector)
+        col.start()
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        col.join()
+        fps, p50, p99 = net.stats()
+        out["rates"][str(int(rate))] = {"offered_fps": rate, "frames": int(len(t_arr)), "measured_s": duration,
+                                        "fps": fps,
+                                        "p50_ms": p50, "p99_ms": p99,
+                                        "submit_lag_p99_ms": 1e3 * float(np.percentile(lag, 99))}
+    net.close()
+    return out
+
+
+class Workload:
+    """Frames, weights and step functions of one bench workload."""
+
+    def __init__(self, torch, binding, dev, wl, prec, stream):
+        netname, batch, side, _, seed = WORKLOADS[wl]
+        self.spec = spec = synth.NETS[netname]()
+        self.batch, self.side, self.prec = batch, side, prec
+        if side:
+            self.sides = [side] * batch
+            _, x, self.blob = synth.workload_net(spec, seed, batch, side, side)
+            self.frames = [x]
+        else:
+            self.sides = [int(v) for v in synth.uneven_sides(batch, seed)]
+            self.blob = synth.weights_for(spec, seed)
+            self.frames = [synth.frame_for(seed, i, s) for i, s in enumerate(self.sides)]
+        self.net = binding.Net(spec.layers, 3, prec=prec, max_batch=batch if side else 1,
+                               max_side=max(self.sides), stream=stream.cuda_stream, device=dev)
+        self.net.load_weights(self.blob)
+        self.stream = stream
+        self.d_in = [torch.from_numpy(f).cuda() for f in self.frames]
+        self.d_out, self.h_in, self.h_out = [], [], []
+        for f in self.frames:
+            c, ho, wo = self.net.output_shape(f.shape[2], f.shape[3])
+            self.d_out.append(torch.empty((f.shape[0], c, ho, wo), device="cuda"))
+            self.h_in.append(torch.from_numpy(f).pin_memory())
+            self.h_out.append(torch.empty((f.shape[0], c, ho, wo)).pin_memory())
+        self.h2d = sum(int(f.nbytes) for f in self.frames)
+        self.d2h = sum(int(o.numel() * 4) for o in self.d_out)
+        cins = spec.cins()
+        self.flops_l = np.zeros(len(spec.layers))
+        for sd in self.sides:
+            h = sd
+            for i, (l, ci) in enumerate(zip(spec.layers, cins)):
+                self.flops_l[i] += 2.0 * h * h * l.cout * ci * l.k * l.k
+                if l.pool == synth.POOL_2X2S2:
+                    h //= 2
+
+    def step(self):
+        if self.side:
+            self.net.forward_device(self.d_in[0], self.batch, self.side, self.side, self.d_out[0])
+        else:
+            self.net.forward_uneven(self.d_in, self.sides, self.d_out)
+
+    def step_e2e(self):
+        if self.side:
+            # the host API: one H2D of the batch, the pass, one D2H of the result
+            self.net.forward(self.h_in[0].numpy(), self.h_out[0].numpy())
+        else:
+            for a, b in zip(self.d_in, self.h_in):
+                a.copy_(b, non_blocking=True)
+            self.net.forward_uneven(self.d_in, self.sides, self.d_out)
+            for a, b in zip(self.h_out, self.d_out):
+                a.copy_(b, non_blocking=True)
+            self.stream.synchronize()
+
+
+def measure(torch, W, args, flush, barrier, ws, with_clocks=False, dev=0):
+    """Warm-up, K device-timed steps (L2 flushed between them, outside the
+    events), a second pass with per-layer conv events, and the e2e pass."""
+    for _ in range(args.warmup):
+        W.step()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = W.net.launches()
+    barrier()
+    clk = Clocks(dev) if with_clocks else None
+    if clk:
+        clk.__enter__()
+    w0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(W.stream)
+        W.step()
+        ev[i][1].record(W.stream)
+    barrier()
+    wall = time.perf_counter() - w0
+    if clk:
+        clk.__exit__(None, None, None)
+    launches = W.net.launches() - l0
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    W.net.profile(True)
+    for _ in range(2):
+        W.step()
+    torch.cuda.synchronize()
+    layer_ms = np.zeros(len(W.spec.layers))
+    for i in range(args.steps):
+        flush.zero_()
+        W.step()
+        layer_ms += W.net.layer_times()
+    layer_ms /= args.steps
+    W.net.profile(False)
+    for _ in range(2):
+        W.step_e2e()
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        W.step_e2e()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    frames_all = W.batch * args.steps * ws
+    return {"value": frames_all / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+            "conv_tflops": float(W.flops_l.sum()) * args.steps * ws / (total_ms / 1e3) / 1e12,
+            "layer_ms": layer_ms, "launches": launches, "wall": wall, "clocks": clk.summary() if clk else None,
+            "e2e_fps": frames_all / e2e_s}
+
+
+def roofline(W, layer_ms, precs):
+    """Dominant kernel family (by engine) over its layers: algorithmic FLOPs
+    / summed CUDA-event time, against the measured peak."""
+    pk, pk_kind = peaks()
+    fam = ["simt" if p == "fp32" else "tc_" + p for p in precs]
+    dom = max(set(fam), key=lambda f: sum(t for t, g in zip(layer_ms, fam) if g == f))
+    sel = [i for i, g in enumerate(fam) if g == dom]
+    achieved = float(sum(W.flops_l[i] for i in sel)) / (float(sum(layer_ms[i] for i in sel)) / 1e3) / 1e12
+    if dom == "simt":
+        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        bound, pnote = "alu", "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % pk.get("sm_max_mhz", 2070.0)
+    else:
+        peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * (2.0 if dom == "tc_fp8" else 1.0)
+        bound = "tensor"
+        pnote = ("bf16 sustained, %s" % pk_kind) + (" x 2 (fp8/bf16 nominal ratio)" if dom == "tc_fp8" else "")
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": TRAFFIC.get(dom), "kernel": "conv_%s (%d layers)" % (dom, len(sel)),
+            "peak_source": pnote, "launches_per_step": len(sel)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -165,7 +398,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the other-precision runs")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
+    ap.add_argument("--serve", action="store_true", help="add the serving streams to the line")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = args.workload
@@ -184,54 +420,8 @@ def main():
 
     from paper_1811_03882_gb300 import build, binding
     build.build()
-
-    netname, batch, side, prec, seed = WORKLOADS[wl]
-    spec = synth.NETS[netname]()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    if side:
-        sides = [side] * batch
-        _, x, blob = synth.workload_net(spec, seed, batch, side, side)
-        frames = [x]
-    else:
-        # uneven batch: frame i has its own side and its own random stream
-        sides = [int(v) for v in synth.uneven_sides(batch, seed)]
-        blob = synth.weights_for(spec, seed)
-        frames = [synth.frame_for(seed, i, s) for i, s in enumerate(sides)]
-    net = binding.Net(spec.layers, 3, prec=prec, max_batch=batch if side else 1,
-                      max_side=max(sides), stream=stream.cuda_stream, device=dev)
-    net.load_weights(blob)
-    if prec == "fp8":
-        s = synth.Stream(synth.SEED_CALIB)
-        cs = max(sides)
-        xc = synth.make_frames(s, 2, 3, cs, cs)
-        net.calibrate(torch.from_numpy(xc).cuda(), 2, cs, cs)
-    d_in = [torch.from_numpy(f).cuda() for f in frames]
-    d_out, h_in, h_out = [], [], []
-    for f in frames:
-        c, ho, wo = net.output_shape(f.shape[2], f.shape[3])
-        d_out.append(torch.empty((f.shape[0], c, ho, wo), device="cuda"))
-        h_in.append(torch.from_numpy(f).pin_memory())
-        h_out.append(torch.empty((f.shape[0], c, ho, wo)).pin_memory())
-
-    def step():
-        if side:
-            net.forward_device(d_in[0], batch, side, side, d_out[0])
-        else:
-            net.forward_uneven(d_in, sides, d_out)
-
-    def step_e2e():
-        if side:
-            # the host API: one H2D of the batch, the pass, one D2H of the result
-            net.forward(h_in[0].numpy(), h_out[0].numpy())
-        else:
-            for a, b in zip(d_in, h_in):
-                a.copy_(b, non_blocking=True)
-            net.forward_uneven(d_in, sides, d_out)
-            for a, b in zip(h_out, d_out):
-                a.copy_(b, non_blocking=True)
-            stream.synchronize()
-
     flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
 
     def barrier():
@@ -239,119 +429,68 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        step()
-    barrier()
+    netname, batch, side, prec, seed = WORKLOADS[wl]
 
-    # ---- timed region: K steps, L2 flushed between steps (outside events)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    l0 = net.launches()
-    barrier()
-    with Clocks(dev) as clk:
-        w0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.zero_()
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
-        barrier()
-        wall = time.perf_counter() - w0
-    launches = net.launches() - l0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    frames_all = batch * args.steps * ws
-    value = frames_all / (total_ms / 1e3)
+    def setup(p, tune=False):
+        W = Workload(torch, binding, dev, wl, p, stream)
+        info = {}
+        if p == "fp8":
+            cs = max(W.sides) if side else 416
+            xc = synth.make_frames(synth.Stream(synth.SEED_CALIB), 1, 3, cs, cs)
+            d_c = torch.from_numpy(xc).cuda()
+            W.net.calibrate(d_c, 1, cs, cs)
+            if tune:
+                plan, ga = W.net.tune_precision(d_c, 1, cs, cs, max_err=0.05, population=12, generations=8,
+                                                reps=2, seed=3)
+                info = {"plan": plan, "ga": ga}
+        return W, info
 
-    # ---- per-layer conv-kernel times (second pass, events around each conv)
-    net.profile(True)
-    for _ in range(2):
-        step()
-    torch.cuda.synchronize()
-    layer_ms = np.zeros(len(spec.layers))
-    for i in range(args.steps):
-        flush.zero_()
-        step()
-        layer_ms += net.layer_times()
-    layer_ms /= args.steps
-    net.profile(False)
-
-    # ---- end to end through the host API (pinned host buffers)
-    for _ in range(2):
-        step_e2e()
-    barrier()
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        step_e2e()
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    h2d = sum(int(f.nbytes) for f in frames)
-    d2h = sum(int(o.numel() * 4) for o in d_out)
-
-    # ---- roofline of the dominant kernel (conv, by engine)
-    pk, pk_kind = peaks()
-    cins = spec.cins()
-    flops_l = np.zeros(len(spec.layers))
-    for sd, f in zip(sides, [1] * len(sides)):
-        h = sd
-        for i, (l, ci) in enumerate(zip(spec.layers, cins)):
-            flops_l[i] += 2.0 * f * h * h * l.cout * ci * l.k * l.k
-            if l.pool == synth.POOL_2X2S2:
-                h //= 2
-    engines = ["bf16" if (prec == "fp8" and ci < 16) else prec for ci in cins]
-    dom = max(set(engines), key=lambda e: sum(t for t, en in zip(layer_ms, engines) if en == e))
-    sel = [i for i, en in enumerate(engines) if en == dom]
-    dom_flops = sum(flops_l[i] for i in sel)
-    dom_ms = sum(layer_ms[i] for i in sel)
-    achieved = dom_flops / (dom_ms / 1e3) / 1e12
-    if dom == "fp32":
-        peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        bound, pnote = "alu", "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % pk.get("sm_max_mhz", 2070.0)
-    else:
-        peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * (2.0 if dom == "fp8" else 1.0)
-        bound = "tensor"
-        pnote = ("bf16 sustained of %s" % pk_kind) + (" x 2 (fp8/bf16 nominal ratio)" if dom == "fp8" else "")
-    tr = TRAFFIC.get(wl)
-    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": tr,
-            "kernel": "conv_%s (%d layers)" % ("simt" if dom == "fp32" else "tc_" + dom, len(sel)),
-            "peak_source": pnote, "launches_per_step": len(sel)}
-
-    conv_flops = float(sum(flops_l))
+    W, info = setup(prec, tune=(prec == "fp8"))
+    precs = W.net.layer_prec()
+    m = measure(torch, W, args, flush, barrier, ws, with_clocks=True, dev=dev)
+    roof = roofline(W, m["layer_ms"], precs)
     line = {
-        "metric": "frames/s", "value": value, "unit": "frames/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "metric": "frames/s", "value": m["value"], "unit": "frames/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[prec], "data": "synthetic",
         "config": {"workload": wl, "network": netname, "global_batch": batch * ws,
                    "frames_per_step_per_gpu": batch, "side": side if side else "uneven {320,416,512,608}",
-                   "precision": prec,
+                   "precision": prec, "layer_precision": precs,
                    "parallelism": "replicas%d" % ws, "l2": "flushed between steps (256 MB write)"},
-        "conv_tflops": conv_flops * args.steps * ws / (total_ms / 1e3) / 1e12,
+        "conv_tflops": m["conv_tflops"],
         "roofline": roof,
-        "layer_ms": [round(float(t), 5) for t in layer_ms],
-        "e2e": {"value": frames_all / e2e_s, "unit": "frames/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches),
-        "wall_s_timed": wall,
-        "clocks": clk.summary(),
+        "layer_ms": [round(float(t), 5) for t in m["layer_ms"]],
+        "e2e": {"value": m["e2e_fps"], "unit": "frames/s", "h2d_bytes_per_step": W.h2d, "d2h_bytes_per_step": W.d2h},
+        "gpu_launches": int(m["launches"]),
+        "wall_s_timed": m["wall"],
+        "clocks": m["clocks"],
     }
+    if info:
+        line["precision_search"] = info
+    W.net.close()
+    if not args.no_compare and side:
+        # the same workload on the other paths: FP32 (CUDA cores) and FP8 (GA-tuned plan) or BF16
+        cmp = {}
+        for p in ("fp32", "fp8" if prec != "fp8" else "bf16"):
+            W2, info2 = setup(p, tune=(p == "fp8"))
+            m2 = measure(torch, W2, args, flush, barrier, ws)
+            cmp[p] = {"value": m2["value"], "ms_per_step": m2["ms_per_step"], "conv_tflops": m2["conv_tflops"],
+                      "e2e": m2["e2e_fps"], "roofline_frac": roofline(W2, m2["layer_ms"], W2.net.layer_prec())["frac"],
+                      "layer_precision": W2.net.layer_prec()}
+            if info2:
+                cmp[p]["precision_search"] = info2
+            W2.net.close()
+        line["compare"] = cmp
+    if args.serve and rank == 0:
+        line["serving"] = run_serving(args, torch, binding, dev)
     if rank == 0 and not args.no_cpu_baseline:
-        f0 = frames[0][:1]
-        fps, nfr, el, cores = oracle_frames_per_s(spec, f0, blob, args.cpu_budget_s)
+        f0 = W.frames[0][:1]
+        fps, nfr, el, cores = oracle_frames_per_s(W.spec, f0, W.blob, args.cpu_budget_s)
         line["cpu_baseline"] = {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
                                 "sample": "%d frame(s) of %dx%d, %.1f s" % (nfr, f0.shape[2], f0.shape[3], el)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    net.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
 

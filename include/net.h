@@ -151,6 +151,9 @@ net_status net_wait(net_t* net, uint64_t req_id, float* out, size_t cap_floats, 
  * latency percentiles (completion minus submission). */
 net_status net_stats(net_t* net, double* fps, double* p50_ms, double* p99_ms);
 
+/* Restarts the statistics of net_stats (e.g. after a warm-up period). */
+net_status net_stats_reset(net_t* net);
+
 /* ---- per-layer precision ------------------------------------------------
  * A handle created with NET_FP8 keeps, for every tensor-core layer, both an
  * E4M3 and a BF16 copy of its folded weights, so each such layer can run in

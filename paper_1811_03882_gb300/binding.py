@@ -88,6 +88,7 @@ _SIGS = {
     "net_get_layer_prec": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "net_tune_precision": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                            ctypes.POINTER(net_ga_opts), ctypes.c_void_p, ctypes.POINTER(net_ga_result)],
+    "net_stats_reset": [ctypes.c_void_p],
     "net_profile": [ctypes.c_void_p, ctypes.c_int],
     "net_layer_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "net_launches": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
@@ -251,6 +252,9 @@ class Net:
                                        ctypes.byref(r)))
         names = {v: k for k, v in PREC.items()}
         return [names[int(v)] for v in out], {f: getattr(r, f) for f, _ in net_ga_result._fields_}
+
+    def stats_reset(self):
+        check(lib().net_stats_reset(self.h))
 
     def profile(self, enable: bool = True):
         check(lib().net_profile(self.h, int(enable)))

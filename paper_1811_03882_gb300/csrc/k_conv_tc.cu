@@ -176,6 +176,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Problem whose M tiles contain tile mt (tile_begin is increasing).
+__device__ __forceinline__ int find_problem(const ConvProblem* probs, int nprob, int mt) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (probs[mid].tile_begin <= mt) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 struct Smem {
     uint64_t full[8], empty[8], accf[2], acce[2], done;
     uint32_t tmem;
@@ -238,8 +249,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 const int z = tile % a.ksplit, mn = tile / a.ksplit;
                 const int mt = mn / a.n_tiles, nt = mn % a.n_tiles;
                 const int ks0 = (int)((long)nk * z / a.ksplit), ks1 = (int)((long)nk * (z + 1) / a.ksplit);
-                int p = 0;
-                while (p + 1 < a.nprob && a.probs[p + 1].tile_begin <= mt) ++p;
+                const int p = tc::find_problem(a.probs, a.nprob, mt);
                 const ConvProblem& P = a.probs[p];
                 const int local = mt - P.tile_begin;
                 const int tx = local % P.tiles_x;
@@ -325,6 +335,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         const int py = row / a.TW, px = row % a.TW;
         const bool pool = a.ep.pool == POOL_S2;
         const int ymask = a.TW == 16 ? 16 : 8;  // lane distance of the pixel below (pool tiles)
+        // columns at or beyond `live` are padding nobody reads: skipped
+        const int live = a.ep.out_layout == LAYOUT_NCHW ? a.ep.cout : max(a.ep.out_cs, a.ep.cout);
         int tcount = 0;
         for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++tcount) {
             const int b = tcount & 1;
@@ -340,6 +352,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 float* wr = a.ws + ((size_t)z * a.m_tiles * 128 + (size_t)mt * 128 + row) * ncp + nt * BN + half * HC;
 #pragma unroll 1
                 for (int c0 = 0; c0 < HC; c0 += 32) {
+                    if (nt * BN + half * HC + c0 >= live) break;
                     float v[32];
                     __syncwarp();
                     tc::tmem_ld32(trow + (uint32_t)c0, v);
@@ -348,8 +361,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         *reinterpret_cast<float4*>(wr + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                 }
             } else {
-                int p = 0;
-                while (p + 1 < a.nprob && a.probs[p + 1].tile_begin <= mt) ++p;
+                const int p = tc::find_problem(a.probs, a.nprob, mt);
                 const ConvProblem& P = a.probs[p];
                 void* ybase = a.y_override ? a.y_override : P.y;
                 const int local = mt - P.tile_begin;
@@ -364,10 +376,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 const size_t pix = ((size_t)img * Ho + yo) * Wo + xo;
 #pragma unroll 1
                 for (int c0 = 0; c0 < HC; c0 += 32) {
+                    const int o0 = nt * BN + half * HC + c0;   // first output channel of the chunk
+                    if (o0 >= live) break;
                     float v[32];
                     __syncwarp();
                     tc::tmem_ld32(trow + (uint32_t)c0, v);
-                    const int o0 = nt * BN + half * HC + c0;   // first output channel of the chunk
                     // bias / alpha are padded with zeros to the weight rows: no bounds checks
 #pragma unroll
                     for (int j = 0; j < 32; j += 4) {

@@ -64,6 +64,69 @@ cudaError_t pack_frames(const float* x, void* y, int n, int C, int H, int W, int
     return cudaGetLastError();
 }
 
+// Value of channel j of the im2col layout at pixel (yy, xx) of frame x.
+__device__ __forceinline__ float im2col_value(const float* __restrict__ x, int C, int H, int W, int k, int j,
+                                              int yy, int xx) {
+    if (j >= C * k * k) return 0.f;
+    const int tap = j / C, c = j % C;
+    const int iy = yy + tap / k - k / 2, ix = xx + tap % k - k / 2;
+    if (iy < 0 || iy >= H || ix < 0 || ix >= W) return 0.f;
+    return x[((size_t)c * H + iy) * W + ix];
+}
+
+template <int DT>
+__device__ __forceinline__ void store_vec(uint8_t* dst, const float* v, float inv_scale) {
+    if (DT == DT_F32) {
+        *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if (DT == DT_BF16) {
+        uint4 pk;
+        uint32_t* p = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            p[j] = *reinterpret_cast<uint32_t*>(&b);
+        }
+        *reinterpret_cast<uint4*>(dst) = pk;
+    } else {
+        uint4 pk;
+        uint8_t* p = reinterpret_cast<uint8_t*>(&pk);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) p[j] = f32_to_e4m3_sat(v[j] * inv_scale);
+        *reinterpret_cast<uint4*>(dst) = pk;
+    }
+}
+
+template <int DT>
+__global__ void pack_im2col_kernel(const float* __restrict__ x, void* __restrict__ y, int n, int C, int H, int W,
+                                   int Cp, int k, float inv_scale) {
+    constexpr int V = DT == DT_F32 ? 4 : DT == DT_BF16 ? 8 : 16;
+    const int groups = Cp / V;
+    const size_t HW = (size_t)H * W;
+    const size_t total = (size_t)n * HW * groups;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int g = (int)(i % groups);
+        const size_t pix = i / groups;
+        const size_t nn = pix / HW, yx = pix % HW;
+        const int yy = (int)(yx / W), xx = (int)(yx % W);
+        float v[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) v[j] = im2col_value(x + nn * C * HW, C, H, W, k, g * V + j, yy, xx);
+        store_vec<DT>(reinterpret_cast<uint8_t*>(y) + (pix * Cp + (size_t)g * V) * dt_size(DT), v, inv_scale);
+    }
+}
+
+cudaError_t pack_frames_im2col(const float* x, void* y, int n, int C, int H, int W, int Cp, int k, int dt,
+                               float inv_scale, cudaStream_t st) {
+    const int V = dt == DT_F32 ? 4 : dt == DT_BF16 ? 8 : 16;
+    const size_t total = (size_t)n * H * W * (Cp / V);
+    const unsigned g = grid_for(total, 256);
+    if (dt == DT_F32) pack_im2col_kernel<DT_F32><<<g, 256, 0, st>>>(x, y, n, C, H, W, Cp, k, inv_scale);
+    else if (dt == DT_BF16) pack_im2col_kernel<DT_BF16><<<g, 256, 0, st>>>(x, y, n, C, H, W, Cp, k, inv_scale);
+    else pack_im2col_kernel<DT_FP8><<<g, 256, 0, st>>>(x, y, n, C, H, W, Cp, k, inv_scale);
+    return cudaGetLastError();
+}
+
 template <typename J>
 __device__ __forceinline__ int find_job(const J* jobs, int njobs, long long i) {
     int lo = 0, hi = njobs - 1;
@@ -88,30 +151,18 @@ __global__ void pack_grouped_kernel(const PackJob* __restrict__ jobs, int njobs,
         const long long yx = li / groups;
         const long long HW = (long long)J.H * J.W;
         float v[V];
+        if (J.im2col_k) {
+            const int yy = (int)(yx / J.W), xx = (int)(yx % J.W);
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-            const int c = g * V + j;
-            v[j] = c < J.C ? J.src[c * HW + yx] : 0.f;
-        }
-        uint8_t* dst = reinterpret_cast<uint8_t*>(J.dst) + (yx * J.Cp + (long long)g * V) * dt_size(DT);
-        if (DT == DT_F32) {
-            *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
-        } else if (DT == DT_BF16) {
-            uint4 pk;
-            uint32_t* p = reinterpret_cast<uint32_t*>(&pk);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                p[j] = *reinterpret_cast<uint32_t*>(&b);
-            }
-            *reinterpret_cast<uint4*>(dst) = pk;
+            for (int j = 0; j < V; ++j) v[j] = im2col_value(J.src, J.C, J.H, J.W, J.im2col_k, g * V + j, yy, xx);
         } else {
-            uint4 pk;
-            uint8_t* p = reinterpret_cast<uint8_t*>(&pk);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) p[j] = f32_to_e4m3_sat(v[j] * inv_scale);
-            *reinterpret_cast<uint4*>(dst) = pk;
+            for (int j = 0; j < V; ++j) {
+                const int c = g * V + j;
+                v[j] = c < J.C ? J.src[c * HW + yx] : 0.f;
+            }
         }
+        store_vec<DT>(reinterpret_cast<uint8_t*>(J.dst) + (yx * J.Cp + (long long)g * V) * dt_size(DT), v, inv_scale);
     }
 }
 
@@ -261,15 +312,21 @@ __global__ void fold_scale_kernel(FoldArgs a) {
 
 // One thread per element of the [w_rows][k*k][Cp] output: reorder + cast.
 __global__ void fold_write_kernel(FoldArgs a) {
-    const int KK = a.k * a.k;
+    const int KK = a.im2col ? 1 : a.k * a.k;
     const size_t total = (size_t)a.w_rows * KK * a.Cp;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % a.Cp);
-        const int tap = (int)((i / a.Cp) % KK);
+        int c = (int)(i % a.Cp);
+        int tap = (int)((i / a.Cp) % KK);
         const int o = (int)(i / ((size_t)a.Cp * KK));
+        bool real = o < a.cout && c < a.cin;
+        if (a.im2col) {   // one row of Cp = taps x cin (+ zero padding)
+            real = o < a.cout && c < a.cin * a.k * a.k;
+            tap = c / a.cin;
+            c = c % a.cin;
+        }
         double v = 0.0;
-        if (o < a.cout && c < a.cin) {
+        if (real) {
             const int kh = tap / a.k, kw = tap % a.k;
             v = (double)a.raw_w[(((size_t)o * a.cin + c) * a.k + kh) * a.k + kw] * a.tmp_s[o];
         }
@@ -293,7 +350,7 @@ cudaError_t fold_layer(const FoldArgs& a, cudaStream_t st) {
     fold_scale_kernel<<<a.cout, 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t total = (size_t)a.w_rows * a.k * a.k * a.Cp;
+    const size_t total = (size_t)a.w_rows * (a.im2col ? 1 : a.k * a.k) * a.Cp;
     fold_write_kernel<<<grid_for(total, 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }

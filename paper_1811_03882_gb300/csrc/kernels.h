@@ -42,6 +42,13 @@ cudaError_t splitk_reduce(const SplitReduce& r, cudaStream_t st);
 cudaError_t pack_frames(const float* x, void* y, int n, int C, int H, int W, int Cp, int dt,
                         float inv_scale, cudaStream_t st);
 
+// Frame NCHW float32 -> "im2col" NHWC for a k x k first layer with few
+// channels: channel j = (kh*k + kw)*C + c of pixel (i, j) holds
+// x[c, i+kh-k/2, j+kw-k/2] (zero outside), zero beyond C*k*k; the layer then
+// runs as a 1x1 conv over Cp channels.
+cudaError_t pack_frames_im2col(const float* x, void* y, int n, int C, int H, int W, int Cp, int k, int dt,
+                               float inv_scale, cudaStream_t st);
+
 // NHWC (dtype dt, channel stride cs, value = code*scale for FP8) -> NCHW f32.
 cudaError_t unpack_nchw(const void* x, float* y, int n, int C, int H, int W, int cs, int dt,
                         float scale, cudaStream_t st);
@@ -66,6 +73,7 @@ struct FoldArgs {
     double* tmp_amax;   // [cout] scratch: per-channel max |W'|
     float* out_w32;
     int Cp32;
+    int im2col;         // 1: write [w_rows][Cp] with channel j = (kh*k + kw)*cin + c
 };
 cudaError_t fold_layer(const FoldArgs& a, cudaStream_t st);
 
@@ -82,7 +90,7 @@ namespace dn {
 // One group member of a tensor-core conv launch: a batch of n equal frames
 // with its own activation tensor map and output.  The device-side table of
 // problems lets one launch cover frames of different sizes.
-struct alignas(64) ConvProblem {
+struct alignas(128) ConvProblem {
     CUtensorMap tmA;    // NHWC activation, box (chunk, TW, TH, 1)
     const void* x;      // activation base (CUDA-core kernels)
     void* y;            // output base
@@ -112,6 +120,7 @@ struct PackJob {
     const float* src;   // NCHW float32 frame
     void* dst;          // NHWC, channel stride Cp
     int C, H, W, Cp;
+    int im2col_k;       // 0: plain pack; k: im2col pack for a k x k layer
     long long begin;
 };
 cudaError_t pack_frames_grouped(const PackJob* jobs, int njobs, long long total, int dt, float inv_scale,

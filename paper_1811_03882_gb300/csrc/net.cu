@@ -149,6 +149,15 @@ extern "C" net_status net_create(const net_desc* d, net_t** out) {
         L.engine = layer_engine(L.prec);
         L.in_dt = L.engine == ENG_SIMT ? DT_F32 : prec_dt(L.prec);
         L.in_cs = pad_channels(cin, L.in_dt, L.engine == ENG_TC);
+        L.kx = s.k;
+        if (l == 0 && L.engine == ENG_TC && L.in_dt == DT_BF16 && s.k == 3 && cin * 9 <= 32) {
+            // first layer on few channels: fold its 9 taps into 32 channels at
+            // pack time and run it as a 1x1 conv (one 64-byte K chunk per tile
+            // instead of nine 32-byte ones)
+            L.im2col_k = 3;
+            L.kx = 1;
+            L.in_cs = 32;
+        }
         L.w_rows = rup(std::max(s.cout, rup(s.cout, 128)), 256);
         L.act_scale = 1.0;
         n->L.push_back(L);
@@ -257,7 +266,8 @@ extern "C" net_status net_load_weights(net_t* n, const float* blob, size_t n_flo
         a.raw_w = d_blob + off;
         off += (size_t)L.d.cout * L.cin * KK;
         const int dt = L.in_dt;
-        const size_t wbytes = (size_t)L.w_rows * KK * L.in_cs * dt_size(dt);
+        const int KKx = L.kx * L.kx;   // taps of the stored layout (1 when im2col-packed)
+        const size_t wbytes = (size_t)L.w_rows * KKx * L.in_cs * dt_size(dt);
         if (!L.w) e = cudaMalloc(&L.w, wbytes);
         // bias and alpha are padded with zeros to w_rows: the tensor-core
         // epilogue reads them four at a time without bounds checks
@@ -288,13 +298,25 @@ extern "C" net_status net_load_weights(net_t* n, const float* blob, size_t n_flo
         a.out_wscale = L.wscale;
         a.tmp_s = tmp;
         a.tmp_amax = tmp + maxc;
-        a.out_w32 = want32 ? L.w32 : nullptr;
+        a.out_w32 = (want32 && !L.im2col_k) ? L.w32 : nullptr;
         a.Cp32 = L.cs32;
+        a.im2col = L.im2col_k ? 1 : 0;
         e = fold_layer(a, n->stream);
+        if (e == cudaSuccess && want32 && L.im2col_k) {
+            // the FP32 reference copy keeps the plain [kh][kw][cin] layout
+            FoldArgs b = a;
+            b.im2col = 0;
+            b.dt = DT_F32;
+            b.Cp = L.cs32;
+            b.out_w = L.w32;
+            b.out_w32 = nullptr;
+            b.out_wscale = nullptr;
+            e = fold_layer(b, n->stream);
+        }
         if (e == cudaSuccess && L.engine == ENG_TC) {
             const int bns[3] = {64, 128, 256};
             for (int i = 0; i < 3 && e == cudaSuccess; ++i)
-                e = tc_encode_weights(&L.tmB[i], L.w, dt, L.w_rows, KK, L.in_cs, bns[i]);
+                e = tc_encode_weights(&L.tmB[i], L.w, dt, L.w_rows, KKx, L.in_cs, bns[i]);
         }
         if (e == cudaSuccess && L.fp8_capable) {
             // both formats, whichever is active now: FP8 [1] and BF16 [0]
@@ -435,7 +457,7 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
         r.W = W[l];
         const int out_cs = last ? rup(L.d.cout, 4) : n->L[l + 1].in_cs;
         const int ncols = std::max(L.d.cout, out_cs);
-        const int KK = L.d.k * L.d.k;
+        const int KK = L.kx * L.kx;
         if (L.engine == ENG_SIMT) {
             simt_tile(ncols, &r.sbn, &r.sth, &r.stw);
             r.m_tiles = batch * cdiv(r.H, r.sth) * cdiv(r.W, r.stw);
@@ -523,8 +545,11 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
     };
     const bool prof = n->prof && !fp32_copy && (int)n->prof_ev.size() == 2 * nl;
     n->pending = 1;
-    cudaError_t e = pack_frames(d_in, buf[cur], batch, n->in_c, h, w, in_cs(0), in_dt(0),
-                                1.f / in_scale(n->L[0]), st);
+    cudaError_t e = (!fp32_copy && n->L[0].im2col_k)
+                        ? pack_frames_im2col(d_in, buf[cur], batch, n->in_c, h, w, in_cs(0), n->L[0].im2col_k,
+                                             in_dt(0), 1.f / in_scale(n->L[0]), st)
+                        : pack_frames(d_in, buf[cur], batch, n->in_c, h, w, in_cs(0), in_dt(0),
+                                      1.f / in_scale(n->L[0]), st);
     if (e != cudaSuccess) return fail(NET_E_CUDA, "pack: %s", cudaGetErrorString(e));
     for (int l = 0; l < nl; ++l) {
         const Layer& L = n->L[l];
@@ -566,7 +591,7 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.m_tiles = r.m_tiles;
                 a.n_tiles = r.n_tiles;
                 a.Cp = L.in_cs;
-                a.k = L.d.k;
+                a.k = L.kx;
                 a.TW = r.TW;
                 a.TH = r.TH;
                 a.chb = tc_chunk_bytes(L.in_cs, L.in_dt);

@@ -18,6 +18,8 @@ struct Layer {
     int cin = 0;
     int prec = 0;        // net_precision of the operands
     int engine = 0;      // ENG_SIMT or ENG_TC
+    int kx = 0;          // kernel size the conv kernel runs (1 for an im2col-packed layer)
+    int im2col_k = 0;    // k > 0: the input is packed im2col-style (taps folded into channels)
     int in_dt = 0;       // storage dtype of this layer's input activation
     int in_cs = 0;       // its channel stride (padded channels)
     int w_rows = 0;      // allocated weight rows (zero beyond cout)

@@ -93,7 +93,8 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
         const int V = 16 / (int)dt_size(n->L[0].in_dt);
         long long b = 0;
         for (int f = 0; f < cnt; ++f) {
-            jobs[f] = PackJob{d_in[f], bufp(0, off[0][f]), n->in_c, side[f], side[f], n->L[0].in_cs, b};
+            jobs[f] = PackJob{d_in[f], bufp(0, off[0][f]), n->in_c, side[f], side[f], n->L[0].in_cs,
+                              n->L[0].im2col_k, b};
             b += (long long)side[f] * side[f] * (n->L[0].in_cs / V);
         }
         P->pack_total = b;
@@ -146,7 +147,7 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
         }
         r.m_tiles = mt;
         int ks_unused = 1;
-        const int nk = L.d.k * L.d.k * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
+        const int nk = L.kx * L.kx * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
         // grouped launches do not split K; pick the N tile for ks = 1
         tc_choose_split(mt, ncols, nk, n->num_sms, &r.BN, &ks_unused, 1);
         r.n_tiles = cdiv(ncols, r.BN);
@@ -193,7 +194,7 @@ static net_status enqueue_uplan(net* n, UPlan* P, int cnt, int* kernels) {
         a.m_tiles = r.m_tiles;
         a.n_tiles = r.n_tiles;
         a.Cp = L.in_cs;
-        a.k = L.d.k;
+        a.k = L.kx;
         a.TW = r.TW;
         a.TH = r.TH;
         a.chb = tc_chunk_bytes(L.in_cs, L.in_dt);

@@ -149,7 +149,7 @@ static net_status serve_step(net* n, ServeState* S, std::vector<std::shared_ptr<
         if (r->layer == 0 && r->cur == -1) {
             const size_t fb = up256((size_t)n->in_c * r->h * r->w * sizeof(float));
             S->h_pack[np] = PackJob{reinterpret_cast<const float*>(base + r->block), base + r->block + fb, n->in_c,
-                                    r->h, r->w, n->L[0].in_cs, ptotal};
+                                    r->h, r->w, n->L[0].in_cs, n->L[0].im2col_k, ptotal};
             ptotal += (long long)r->h * r->w * (n->L[0].in_cs / V0);
             r->cur = 0;
             ++np;
@@ -240,7 +240,7 @@ static net_status serve_step(net* n, ServeState* S, std::vector<std::shared_ptr<
                 q.tile_begin = mt;
                 mt += q.tiles_x * q.tiles_y;
             }
-            const int nk = L.d.k * L.d.k * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
+            const int nk = L.kx * L.kx * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
             tc_choose_split(mt, ncols, nk, n->num_sms, &BN, &ks, 1);
             e = cudaMemcpyAsync(S->d_tab + tab_used, ht, sizeof(ConvProblem) * grp.size(), cudaMemcpyHostToDevice, st);
             TcArgs a{};
@@ -249,7 +249,7 @@ static net_status serve_step(net* n, ServeState* S, std::vector<std::shared_ptr<
             a.m_tiles = mt;
             a.n_tiles = cdiv(ncols, BN);
             a.Cp = L.in_cs;
-            a.k = L.d.k;
+            a.k = L.kx;
             a.TW = TW;
             a.TH = TH;
             a.chb = tc_chunk_bytes(L.in_cs, L.in_dt);
@@ -516,5 +516,14 @@ extern "C" net_status net_stats(net_t* n, double* fps, double* p50, double* p99)
     auto pct = [&](double p) { return v[std::min(v.size() - 1, (size_t)(p * (v.size() - 1) + 0.5))]; };
     *p50 = pct(0.50);
     *p99 = pct(0.99);
+    return NET_OK;
+}
+
+extern "C" net_status net_stats_reset(net_t* n) {
+    if (!n) return fail(NET_E_INVAL, "NULL argument");
+    if (!n->serve) return NET_OK;
+    std::lock_guard<std::mutex> lk(n->serve->mu);
+    n->serve->lat_ms.clear();
+    n->serve->completed = 0;
     return NET_OK;
 }

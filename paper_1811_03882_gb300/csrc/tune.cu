@@ -131,6 +131,10 @@ extern "C" net_status net_tune_precision(net_t* n, const float* d_frames, int ba
     std::vector<std::vector<int>> pop(opt->population, std::vector<int>(a));
     for (auto& g : pop)
         for (int& b : g) b = rng.below(2);
+    // One individual starts as the all-BF16 plan, the counterpart of the
+    // paper's all-zero gene (everything on the CPU, its reference run): the
+    // search then always holds a plan inside the error budget.
+    std::fill(pop[0].begin(), pop[0].end(), 0);
     std::vector<int> best_g(a, 0);
     Eval best;
     best.fitness = -1.0;
