@@ -98,6 +98,27 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int 
         : "memory");
 }
 
+// Multicast variant: the box lands at the same smem offset of every CTA in
+// `mask` and completes bytes on each destination's barrier at `bar`.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const void* tmap, int c0, int c1, uint32_t bar,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(bar), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor (tcgen05), K-major operand with 32/64/128
 // byte swizzle: start >> 4, leading offset (unused for swizzled K-major) 16,
 // stride offset = 8 rows * row bytes, fixed version bits 46..48 = 0b001.
@@ -137,6 +158,13 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bd
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
+}
+
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"(mask)
+        : "memory");
 }
 
 __device__ __forceinline__ void fence_before() {
@@ -195,7 +223,10 @@ struct Smem {
 
 }  // namespace tc
 
-template <int BN, int DT, int STAGES>
+// CS = cluster size: with CS = 2 the two CTAs of a cluster work on
+// neighbouring M tiles of the same N tile, and each loads half of the
+// weight (B) box and multicasts it to both, halving the B traffic from L2.
+template <int BN, int DT, int STAGES, int CS>
 __global__ void __launch_bounds__(tc::THREADS, 1)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     using namespace tc;
@@ -210,14 +241,20 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int KK = a.k * a.k;
     const int nk = KK * a.chunks;                 // K steps per tile
-    const int total = a.m_tiles * a.n_tiles * a.ksplit;
+    // work items: (group of CS m-tiles, n-tile, K slice); a cluster takes one
+    // item at a time and CTA `rank` of it the m-tile group*CS + rank
+    const int rank = CS > 1 ? (int)tc::cluster_rank() : 0;
+    const int worker = blockIdx.x / CS, nworkers = gridDim.x / CS;
+    const int m_groups = (a.m_tiles + CS - 1) / CS;
+    const int total = m_groups * a.n_tiles * a.ksplit;
+    const uint16_t cmask = (uint16_t)((1u << CS) - 1u);
     const int pad = a.k >> 1;
     const uint32_t a_bytes = 128u * a.chb, b_bytes = (uint32_t)BN * a.chb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             tc::mbar_init(smem_u32(&sm->full[s]), 1);
-            tc::mbar_init(smem_u32(&sm->empty[s]), 1);
+            tc::mbar_init(smem_u32(&sm->empty[s]), CS);   // every consumer of the cluster frees a stage
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(smem_u32(&sm->accf[b]), 1);
@@ -235,7 +272,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc::fence_before();
-    __syncthreads();
+    if (CS > 1) tc::cluster_sync();   // peers' barriers exist before any multicast
+    else __syncthreads();
     tc::fence_after();
     const uint32_t tmem_base = sm->tmem;
     volatile int* abort_flag = &sm->abort;
@@ -245,9 +283,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         if (lane == 0) {
             int it = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x) {
+            for (int tile = worker; tile < total && ok; tile += nworkers) {
                 const int z = tile % a.ksplit, mn = tile / a.ksplit;
-                const int mt = mn / a.n_tiles, nt = mn % a.n_tiles;
+                const int mt = (mn / a.n_tiles) * CS + rank, nt = mn % a.n_tiles;
                 const int ks0 = (int)((long)nk * z / a.ksplit), ks1 = (int)((long)nk * (z + 1) / a.ksplit);
                 const int p = tc::find_problem(a.probs, a.nprob, mt);
                 const ConvProblem& P = a.probs[p];
@@ -271,7 +309,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         const int c0 = ch * a.cpc;
                         tc::tma_load_4d(smem_u32(sA + s * A_BYTES), &P.tmA, c0, x0 + kw - pad, y0 + kh - pad,
                                         img, fb);
-                        tc::tma_load_2d(smem_u32(sB + s * B_BYTES), &tmB, tap * a.Cp + c0, nt * BN, fb);
+                        if (CS == 1) {
+                            tc::tma_load_2d(smem_u32(sB + s * B_BYTES), &tmB, tap * a.Cp + c0, nt * BN, fb);
+                        } else {
+                            constexpr int BR = BN / CS;   // rows of B this CTA loads for the cluster
+                            tc::tma_load_2d_mc(smem_u32(sB + s * B_BYTES + rank * BR * a.chb), &tmB, tap * a.Cp + c0,
+                                               nt * BN + rank * BR, fb, cmask);
+                        }
                     }
                 }
             }
@@ -292,7 +336,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             const uint32_t idesc = tc::instr_desc<DT>(BN);
             int it = 0, tcount = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < total && ok; tile += gridDim.x, ++tcount) {
+            for (int tile = worker; tile < total && ok; tile += nworkers, ++tcount) {
                 const int z = tile % a.ksplit;
                 const int ks0 = (int)((long)nk * z / a.ksplit), ks1 = (int)((long)nk * (z + 1) / a.ksplit);
                 const int b = tcount & 1;
@@ -314,7 +358,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     for (int j = 0; j < nmma; ++j)
                         tc::mma<DT>(dtm, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc,
                                     (ks != ks0 || j != 0) ? 1u : 0u);
-                    tc::mma_commit(smem_u32(&sm->empty[s]));
+                    if (CS == 1) tc::mma_commit(smem_u32(&sm->empty[s]));
+                    else tc::mma_commit_mc(smem_u32(&sm->empty[s]), cmask);   // frees the stage in every CTA
                 }
                 if (ok) tc::mma_commit(smem_u32(&sm->accf[b]));
             }
@@ -337,14 +382,24 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         const int ymask = a.TW == 16 ? 16 : 8;  // lane distance of the pixel below (pool tiles)
         // columns at or beyond `live` are padding nobody reads: skipped
         const int live = a.ep.out_layout == LAYOUT_NCHW ? a.ep.cout : max(a.ep.out_cs, a.ep.cout);
+        void* pY = nullptr;
+        int pH = 0, pW = 0, pTX = 1, pTY = 1, pBegin = 0;
         int tcount = 0;
-        for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++tcount) {
+        for (int tile = worker; tile < total; tile += nworkers, ++tcount) {
             const int b = tcount & 1;
             const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
             if (!tc::mbar_wait(smem_u32(&sm->accf[b]), aph, abort_flag, a.err, 4)) break;
             tc::fence_after();
             const int z = tile % a.ksplit, mn = tile / a.ksplit;
-            const int mt = mn / a.n_tiles, nt = mn % a.n_tiles;
+            const int mt = (mn / a.n_tiles) * CS + rank, nt = mn % a.n_tiles;
+            if (mt >= a.m_tiles) {
+                // the cluster's spare CTA on an odd tile count: loads and MMAs ran on
+                // zero-filled operands; nothing to store
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(smem_u32(&sm->acce[b]));
+                continue;
+            }
             const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * HC);
             if (a.ksplit > 1) {
                 // raw partial sums of this K slice; the reduction applies the epilogue
@@ -361,16 +416,24 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         *reinterpret_cast<float4*>(wr + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                 }
             } else {
-                const int p = tc::find_problem(a.probs, a.nprob, mt);
-                const ConvProblem& P = a.probs[p];
-                void* ybase = a.y_override ? a.y_override : P.y;
-                const int local = mt - P.tile_begin;
-                const int tx = local % P.tiles_x;
-                const int ty = (local / P.tiles_x) % P.tiles_y;
-                const int img = local / (P.tiles_x * P.tiles_y);
+                // the single-problem case keeps its fields in registers (read once)
+                if (a.nprob > 1 || tcount == 0) {
+                    const ConvProblem& P = a.probs[a.nprob > 1 ? tc::find_problem(a.probs, a.nprob, mt) : 0];
+                    pY = P.y;
+                    pH = P.H;
+                    pW = P.W;
+                    pTX = P.tiles_x;
+                    pTY = P.tiles_y;
+                    pBegin = P.tile_begin;
+                }
+                void* ybase = a.y_override ? a.y_override : pY;
+                const int local = mt - pBegin;
+                const int tx = local % pTX;
+                const int ty = (local / pTX) % pTY;
+                const int img = local / (pTX * pTY);
                 const int gy = ty * a.TH + py, gx = tx * a.TW + px;
-                const bool valid = gy < P.H && gx < P.W;
-                const int Ho = pool ? P.H / 2 : P.H, Wo = pool ? P.W / 2 : P.W;
+                const bool valid = gy < pH && gx < pW;
+                const int Ho = pool ? pH / 2 : pH, Wo = pool ? pW / 2 : pW;
                 const int yo = pool ? gy / 2 : gy, xo = pool ? gx / 2 : gx;
                 const bool writer = valid && (!pool || ((lane & 1) == 0 && (lane & ymask) == 0));
                 const size_t pix = ((size_t)img * Ho + yo) * Wo + xo;
@@ -378,19 +441,24 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 for (int c0 = 0; c0 < HC; c0 += 32) {
                     const int o0 = nt * BN + half * HC + c0;   // first output channel of the chunk
                     if (o0 >= live) break;
+                    // bias / alpha are padded with zeros to the weight rows: no bounds
+                    // checks; loaded before the TMEM read so the two latencies overlap
+                    float4 bb[8], aa[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        bb[j] = __ldg(reinterpret_cast<const float4*>(a.ep.bias + o0) + j);
+                        aa[j] = a.ep.alpha ? __ldg(reinterpret_cast<const float4*>(a.ep.alpha + o0) + j)
+                                           : make_float4(1.f, 1.f, 1.f, 1.f);
+                    }
                     float v[32];
                     __syncwarp();
                     tc::tmem_ld32(trow + (uint32_t)c0, v);
-                    // bias / alpha are padded with zeros to the weight rows: no bounds checks
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        const float4 bb = __ldg(reinterpret_cast<const float4*>(a.ep.bias + o0 + j));
-                        float4 aa = make_float4(1.f, 1.f, 1.f, 1.f);
-                        if (a.ep.alpha) aa = __ldg(reinterpret_cast<const float4*>(a.ep.alpha + o0 + j));
-                        v[j] = act_apply(fmaf(v[j], aa.x, bb.x), a.ep.act);
-                        v[j + 1] = act_apply(fmaf(v[j + 1], aa.y, bb.y), a.ep.act);
-                        v[j + 2] = act_apply(fmaf(v[j + 2], aa.z, bb.z), a.ep.act);
-                        v[j + 3] = act_apply(fmaf(v[j + 3], aa.w, bb.w), a.ep.act);
+                    for (int j = 0; j < 8; ++j) {
+                        v[4 * j] = act_apply(fmaf(v[4 * j], aa[j].x, bb[j].x), a.ep.act);
+                        v[4 * j + 1] = act_apply(fmaf(v[4 * j + 1], aa[j].y, bb[j].y), a.ep.act);
+                        v[4 * j + 2] = act_apply(fmaf(v[4 * j + 2], aa[j].z, bb[j].z), a.ep.act);
+                        v[4 * j + 3] = act_apply(fmaf(v[4 * j + 3], aa[j].w, bb[j].w), a.ep.act);
                     }
                     if (a.ep.out_layout == LAYOUT_NCHW) {
                         if (pool) {
@@ -475,7 +543,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     }
 
     tc::fence_before();
-    __syncthreads();
+    if (CS > 1) tc::cluster_sync();   // no peer multicasts into this CTA's smem any more
+    else __syncthreads();
     tc::fence_after();
     __syncwarp();
     if (warp == 1)
@@ -541,30 +610,51 @@ cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int BN, int DT>
-static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a, int grid, cudaStream_t st) {
+template <int BN, int DT, int CS>
+static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a, int workers, cudaStream_t st) {
     constexpr int STAGES = BN == 256 ? 4 : BN == 128 ? 6 : 8;
     const size_t smem = 1024 + (size_t)STAGES * (tc::A_BYTES + BN * 128) + sizeof(tc::Smem);
-    auto kern = conv_tc_kernel<BN, DT, STAGES>;
+    auto kern = conv_tc_kernel<BN, DT, STAGES, CS>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    kern<<<grid, tc::THREADS, smem, st>>>(tmB, a);
-    return cudaGetLastError();
+    if (CS == 1) {
+        kern<<<workers, tc::THREADS, smem, st>>>(tmB, a);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(workers * CS));
+    cfg.blockDim = dim3(tc::THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, tmB, a);
 }
 
-cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int grid, cudaStream_t st) {
+// BN x (cluster size): cs = 2 needs the weight map whose box has BN / 2 rows.
+cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, int cs,
+                           cudaStream_t st) {
     if (dt == DT_BF16) {
-        if (BN == 64) return launch_tc_bn<64, DT_BF16>(tmB, a, grid, st);
-        if (BN == 128) return launch_tc_bn<128, DT_BF16>(tmB, a, grid, st);
-        if (BN == 256) return launch_tc_bn<256, DT_BF16>(tmB, a, grid, st);
+        if (BN == 64 && cs == 1) return launch_tc_bn<64, DT_BF16, 1>(tmB, a, workers, st);
+        if (BN == 128 && cs == 1) return launch_tc_bn<128, DT_BF16, 1>(tmB, a, workers, st);
+        if (BN == 256 && cs == 1) return launch_tc_bn<256, DT_BF16, 1>(tmB, a, workers, st);
+        if (BN == 128 && cs == 2) return launch_tc_bn<128, DT_BF16, 2>(tmB, a, workers, st);
+        if (BN == 256 && cs == 2) return launch_tc_bn<256, DT_BF16, 2>(tmB, a, workers, st);
     } else if (dt == DT_FP8) {
-        if (BN == 64) return launch_tc_bn<64, DT_FP8>(tmB, a, grid, st);
-        if (BN == 128) return launch_tc_bn<128, DT_FP8>(tmB, a, grid, st);
-        if (BN == 256) return launch_tc_bn<256, DT_FP8>(tmB, a, grid, st);
+        if (BN == 64 && cs == 1) return launch_tc_bn<64, DT_FP8, 1>(tmB, a, workers, st);
+        if (BN == 128 && cs == 1) return launch_tc_bn<128, DT_FP8, 1>(tmB, a, workers, st);
+        if (BN == 256 && cs == 1) return launch_tc_bn<256, DT_FP8, 1>(tmB, a, workers, st);
+        if (BN == 128 && cs == 2) return launch_tc_bn<128, DT_FP8, 2>(tmB, a, workers, st);
+        if (BN == 256 && cs == 2) return launch_tc_bn<256, DT_FP8, 2>(tmB, a, workers, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -138,5 +138,8 @@ int tc_chunk_bytes(int Cp, int dt);
 cudaError_t tc_encode_act(CUtensorMap* tm, const void* base, int dt, int n, int H, int W, int Cp, int TW,
                           int TH);
 cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, int KK, int Cp, int BN);
-cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int grid, cudaStream_t st);
+// workers = persistent CTAs (cs = 1) or 2-CTA clusters (cs = 2); tmB has
+// box rows BN / cs.
+cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, int cs,
+                           cudaStream_t st);
 }  // namespace dn

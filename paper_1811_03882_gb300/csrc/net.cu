@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <memory>
 #include <cstring>
 #include <deque>
@@ -381,13 +382,15 @@ Plan::~Plan() {
         if (r.d_prob) cudaFree(r.d_prob);
 }
 
-// Analytic tile/split choice for the tensor-core kernel.  Per K step of a
-// 128-byte chunk, an SM needs max(MMA cycles, L2 bytes / ~84 B per cycle):
-// the A box (16 KB) is fetched once per tap and N tile, B is BN x 128 B;
-// N = 64 MMAs also run short of shared-memory bandwidth.  Rounds of
-// ceil(items / SMs) persistent tiles, plus the split-K workspace traffic.
+// Analytic tile/split choice for the tensor-core kernel.  The mainloop is
+// bound by the operand traffic from L2 (about 10 TB/s over the chip): per
+// K step of a 128-byte chunk an SM moves the A box (16 KB, once per tap and
+// N tile) plus BN x 128 B of B.  Measured K-step times with every SM busy:
+// ~900, ~1020, ~1450 cycles for BN = 64, 128, 256 (so 256 does 1.4x the
+// work per byte of 128).  Rounds of ceil(items / SMs) persistent tiles,
+// plus the split-K workspace traffic.
 static double tc_cost(long m_tiles, int ncols, int BN, int ks, int nk, int num_sms) {
-    static const double kstep_clk[3] = {292.0, 390.0, 585.0};   // BN = 64, 128, 256
+    static const double kstep_clk[3] = {900.0, 1020.0, 1450.0};   // BN = 64, 128, 256
     const int bi = BN == 64 ? 0 : BN == 128 ? 1 : 2;
     const long items = m_tiles * cdiv(ncols, BN) * ks;
     const long rounds = (items + num_sms - 1) / num_sms;
@@ -415,6 +418,24 @@ void dn::tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, i
 }
 
 // Picks BN and the split-K factor together with the cost model above.
+// Cluster size and persistent worker count of a tensor-core launch: BN >=
+// 128 runs on 2-CTA clusters that share the weight box (multicast), unless
+// NET_TC_CLUSTER=1 asks for single CTAs.
+void dn::tc_workers(int m_tiles, int n_tiles, int ks, int BN, int num_sms, int* cs, int* workers) {
+    static const int forced = [] {
+        const char* e = getenv("NET_TC_CLUSTER");
+        return e ? atoi(e) : 0;
+    }();
+    *cs = (BN >= 128 && m_tiles >= 2 && forced != 1) ? 2 : 1;
+    const int items = cdiv(m_tiles, *cs) * n_tiles * ks;
+    *workers = std::max(1, std::min(items, num_sms / *cs));
+}
+
+int dn::tmb_index(int BN, int cs) {
+    const int rows = BN / cs;
+    return rows == 64 ? 0 : rows == 128 ? 1 : 2;
+}
+
 void dn::tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks) {
     double best = -1.0;
     for (int bn : {64, 128, 256}) {
@@ -480,7 +501,8 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             if (r.ksplit > 1)
                 P->ws_bytes = std::max(P->ws_bytes, (size_t)r.ksplit * r.m_tiles * 128 * r.n_tiles * r.BN *
                                                         sizeof(float));
-            r.grid = std::min(tiles * r.ksplit, n->num_sms);
+            tc_workers(r.m_tiles, r.n_tiles, r.ksplit, r.BN, n->num_sms, &r.cs, &r.grid);
+            (void)tiles;
             ConvProblem hp;
             std::memset(&hp, 0, sizeof hp);
             cudaError_t e = tc_encode_act(&hp.tmA, n->act[r.in_buf], L.in_dt, batch, r.H, r.W, L.in_cs, r.TW, r.TH);
@@ -602,8 +624,7 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.ws = n->ws;
                 a.ep = ep;
                 a.err = n->err_dev;
-                const int bi = r.BN == 64 ? 0 : r.BN == 128 ? 1 : 2;
-                e = conv_tc_launch(L.tmB[bi], a, r.BN, L.in_dt, r.grid, st);
+                e = conv_tc_launch(L.tmB[tmb_index(r.BN, r.cs)], a, r.BN, L.in_dt, r.grid, r.cs, st);
                 if (e == cudaSuccess && r.ksplit > 1) {
                     ++n->pending;
                     SplitReduce sr{n->ws, r.ksplit, r.m_tiles * 128, r.n_tiles * r.BN, r.TW, r.TH,

@@ -54,6 +54,7 @@ struct LayerRun {
     int H = 0, W = 0;              // conv input (= pre-pool output) size
     int TW = 16, TH = 8, BN = 128; // TC tile: TH x TW pixels x BN channels
     int m_tiles = 0, n_tiles = 0, grid = 0;
+    int cs = 1;                    // TC cluster size (grid = workers * cs CTAs)
     int ksplit = 1;                // split-K factor (partial sums in the workspace)
     int sbn = 64, sth = 8, stw = 16; // CUDA-core tile
     ConvProblem* d_prob = nullptr; // TC: device problem table (one entry)
@@ -69,6 +70,8 @@ struct Plan {
 // one warp: TW = 8 or 16).
 void tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, int* TW, int* TH, int* BN);
 void tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks = 16);
+void tc_workers(int m_tiles, int n_tiles, int ks, int BN, int num_sms, int* cs, int* workers);
+int tmb_index(int BN, int cs);
 
 struct UnevenState;
 struct ServeState;

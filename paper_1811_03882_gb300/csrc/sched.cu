@@ -151,7 +151,7 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
         // grouped launches do not split K; pick the N tile for ks = 1
         tc_choose_split(mt, ncols, nk, n->num_sms, &r.BN, &ks_unused, 1);
         r.n_tiles = cdiv(ncols, r.BN);
-        r.grid = std::min(r.m_tiles * r.n_tiles, n->num_sms);
+        tc_workers(r.m_tiles, r.n_tiles, 1, r.BN, n->num_sms, &r.cs, &r.grid);
         cudaError_t e = cudaMalloc(&r.d_prob, sizeof(ConvProblem) * cnt);
         if (e == cudaSuccess) e = cudaMemcpy(r.d_prob, probs.data(), sizeof(ConvProblem) * cnt, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(NET_E_CUDA, "layer %d problem table: %s", l, cudaGetErrorString(e));
@@ -219,10 +219,9 @@ static net_status enqueue_uplan(net* n, UPlan* P, int cnt, int* kernels) {
             a.ep.out_cs = n->L[l + 1].in_cs;
             a.ep.out_inv_scale = a.ep.out_dt == DT_FP8 ? 1.f / in_scale_of(n->L[l + 1]) : 1.f;
         }
-        const int bi = r.BN == 64 ? 0 : r.BN == 128 ? 1 : 2;
         const bool prof = n->prof && (int)n->prof_ev.size() == 2 * nl;
         if (prof) e = cudaEventRecordWithFlags(n->prof_ev[2 * l], st, cudaEventRecordExternal);
-        if (e == cudaSuccess) e = conv_tc_launch(L.tmB[bi], a, r.BN, L.in_dt, r.grid, st);
+        if (e == cudaSuccess) e = conv_tc_launch(L.tmB[tmb_index(r.BN, r.cs)], a, r.BN, L.in_dt, r.grid, r.cs, st);
         if (e == cudaSuccess && prof) e = cudaEventRecordWithFlags(n->prof_ev[2 * l + 1], st, cudaEventRecordExternal);
         ++k;
         if (e == cudaSuccess && P->d_pool[l]) {

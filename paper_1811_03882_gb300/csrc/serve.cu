@@ -258,9 +258,9 @@ static net_status serve_step(net* n, ServeState* S, std::vector<std::shared_ptr<
             a.ksplit = 1;
             a.ep = ep;
             a.err = n->err_dev;
-            const int bi = BN == 64 ? 0 : BN == 128 ? 1 : 2;
-            if (e == cudaSuccess)
-                e = conv_tc_launch(L.tmB[bi], a, BN, L.in_dt, std::min(mt * a.n_tiles, n->num_sms), st);
+            int cs = 1, workers = 1;
+            tc_workers(mt, a.n_tiles, 1, BN, n->num_sms, &cs, &workers);
+            if (e == cudaSuccess) e = conv_tc_launch(L.tmB[tmb_index(BN, cs)], a, BN, L.in_dt, workers, cs, st);
             ++n->launches;
             tab_used += (int)grp.size();
         }
