@@ -12,11 +12,12 @@
 // padding, so no im2col buffer exists.  B is the matching [BN x chunk]
 // box of the K-major weights [Cout][kh][kw][Cin].
 //
-// Persistent, warp-specialised CTA (one per SM, 320 threads):
-//   warp 0     TMA producer (one lane), STAGES-deep smem ring
+// Persistent, warp-specialised CTA (one per SM, 352 threads):
+//   warps 0,10 TMA producers (one lane each, alternate K steps), STAGES-deep
+//              smem ring (STAGES even)
 //   warp 1     TMEM owner and MMA issuer (one lane)
-//   warps 2-9  epilogue (two warps per TMEM lane quarter, half the
-//              columns each): tcgen05.ld, alpha/bias, leaky, 2x2 max via
+//   warps 2-9  epilogue: two warpgroups, one per TMEM accumulator buffer
+//              (alternate tiles): tcgen05.ld, alpha/bias, leaky, 2x2 max via
 //              warp shuffles, downcast, 16-byte stores
 // Two TMEM accumulators let the epilogue of one tile overlap the
 // mainloop of the next.  Every mbarrier wait is bounded: on expiry the
@@ -31,7 +32,8 @@ namespace dn {
 
 namespace tc {
 
-constexpr int THREADS = 320;   // producer, MMA issuer, 8 epilogue warps
+constexpr int THREADS = 352;   // producer, MMA issuer, 8 epilogue warps, second producer
+constexpr int NUM_WARPS = THREADS / 32;
 constexpr int A_BYTES = 128 * 128;            // 128 rows x 128-byte chunk (max)
 constexpr long long WAIT_LIMIT = 4000000000LL;  // clock64 cycles (~2 s)
 
@@ -258,7 +260,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(smem_u32(&sm->accf[b]), 1);
-            tc::mbar_init(smem_u32(&sm->acce[b]), 8);
+            tc::mbar_init(smem_u32(&sm->acce[b]), 4);   // the 4 warps of warpgroup b
         }
         tc::mbar_init(smem_u32(&sm->done), 1);
         sm->abort = 0;
@@ -278,8 +280,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     const uint32_t tmem_base = sm->tmem;
     volatile int* abort_flag = &sm->abort;
 
-    if (warp == 0) {
-        // ------------------------------------------------ TMA producer
+    if (warp == 0 || warp == NUM_WARPS - 1) {
+        // ------------------------------------------------ TMA producers
+        // A cp.async.bulk.tensor blocks its issuing thread for hundreds of
+        // cycles, so one thread cannot keep the tensor pipe fed: two producer
+        // warps take alternate K steps (and so alternate stages).
+        const int pid = warp == 0 ? 0 : 1;
         if (lane == 0) {
             int it = 0;
             bool ok = true;
@@ -295,6 +301,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 const int img = local / (P.tiles_x * P.tiles_y);
                 const int x0 = tx * a.TW, y0 = ty * a.TH;
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
+                    if ((it & 1) != pid) continue;
                     const int tap = ks / a.chunks, ch = ks % a.chunks;
                     const int kh = tap / a.k, kw = tap % a.k;
                     {
@@ -321,7 +328,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             }
             // drain: every copy issued must have landed before smem goes away
             for (int j = (it > STAGES ? it - STAGES : 0); j < it; ++j)
-                if (!tc::mbar_wait(smem_u32(&sm->full[j % STAGES]), (uint32_t)(j / STAGES) & 1u, abort_flag,
+                if ((j & 1) == pid && !tc::mbar_wait(smem_u32(&sm->full[j % STAGES]), (uint32_t)(j / STAGES) & 1u, abort_flag,
                                    a.err, 5)) {
                     // abort already flagged: give the copies a bounded grace period
                     const long long t0 = clock64();
@@ -371,11 +378,14 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         }
     } else {
         // ------------------------------------------------ epilogue (warps 2..9)
-        // Two warps per TMEM lane quarter, each taking half of the tile's
-        // columns, so every SM sub-partition runs two epilogue warps.
+        // Two warpgroups, one per TMEM accumulator buffer: warpgroup g takes
+        // the tiles whose buffer is g (every other tile) and all their
+        // columns, so both groups stay busy even when a layer has only a few
+        // live output channels.  Each SM sub-partition runs one warp of each.
         const int q = warp & 3;                 // TMEM lane quarter of this warp
-        const int half = (warp - 2) >> 2;       // column half of the tile
-        constexpr int HC = BN / 2;              // columns per warp
+        const int grp = (warp - 2) >> 2;        // warpgroup = accumulator buffer
+        constexpr int half = 0;
+        constexpr int HC = BN;                  // columns per warp
         const int row = q * 32 + lane;          // pixel index in the tile
         const int py = row / a.TW, px = row % a.TW;
         const bool pool = a.ep.pool == POOL_S2;
@@ -387,6 +397,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         int tcount = 0;
         for (int tile = worker; tile < total; tile += nworkers, ++tcount) {
             const int b = tcount & 1;
+            if (b != grp) continue;
             const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
             if (!tc::mbar_wait(smem_u32(&sm->accf[b]), aph, abort_flag, a.err, 4)) break;
             tc::fence_after();
@@ -417,7 +428,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 }
             } else {
                 // the single-problem case keeps its fields in registers (read once)
-                if (a.nprob > 1 || tcount == 0) {
+                if (a.nprob > 1 || tcount == grp) {
                     const ConvProblem& P = a.probs[a.nprob > 1 ? tc::find_problem(a.probs, a.nprob, mt) : 0];
                     pY = P.y;
                     pH = P.H;
