@@ -110,6 +110,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(torch, value: float, ws: int, device="cuda") -> float:
+    """The slowest rank's time: replicas run independently, the job takes as
+    long as its slowest replica."""
+    if ws <= 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_frames_per_s(frames_per_rank: int, ws: int, slowest_s: float) -> float:
+    """Whole-job throughput of ws replicas: all ranks' frames over the
+    slowest rank's time."""
+    return frames_per_rank * ws / slowest_s
+
+
 def oracle_frames_per_s(spec, x1, blob, budget_s: float):
     """FP64 oracle timed on this host's cores over whole frames until
     budget_s of CPU work has passed (at least one frame)."""
@@ -335,11 +351,7 @@ def measure(torch, W, args, flush, barrier, ws, with_clocks=False, dev=0):
     if clk:
         clk.__exit__(None, None, None)
     launches = W.net.launches() - l0
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(torch, sum(a.elapsed_time(b) for a, b in ev), ws)
     W.net.profile(True)
     for _ in range(2):
         W.step()
@@ -358,13 +370,9 @@ def measure(torch, W, args, flush, barrier, ws, with_clocks=False, dev=0):
     for i in range(args.steps):
         W.step_e2e()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(torch, time.perf_counter() - t0, ws)
     frames_all = W.batch * args.steps * ws
-    return {"value": frames_all / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+    return {"value": job_frames_per_s(W.batch * args.steps, ws, total_ms / 1e3), "ms_per_step": total_ms / args.steps,
             "conv_tflops": float(W.flops_l.sum()) * args.steps * ws / (total_ms / 1e3) / 1e12,
             "layer_ms": layer_ms, "launches": launches, "wall": wall, "clocks": clk.summary() if clk else None,
             "e2e_fps": frames_all / e2e_s}

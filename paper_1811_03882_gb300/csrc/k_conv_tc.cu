@@ -454,22 +454,36 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     if (o0 >= live) break;
                     // bias / alpha are padded with zeros to the weight rows: no bounds
                     // checks; loaded before the TMEM read so the two latencies overlap
-                    float4 bb[8], aa[8];
+                    float bb[32];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        bb[j] = __ldg(reinterpret_cast<const float4*>(a.ep.bias + o0) + j);
-                        aa[j] = a.ep.alpha ? __ldg(reinterpret_cast<const float4*>(a.ep.alpha + o0) + j)
-                                           : make_float4(1.f, 1.f, 1.f, 1.f);
+                        const float4 t = __ldg(reinterpret_cast<const float4*>(a.ep.bias + o0) + j);
+                        bb[4 * j] = t.x;
+                        bb[4 * j + 1] = t.y;
+                        bb[4 * j + 2] = t.z;
+                        bb[4 * j + 3] = t.w;
                     }
                     float v[32];
                     __syncwarp();
                     tc::tmem_ld32(trow + (uint32_t)c0, v);
+                    // warp-uniform branches: each variant is one straight-line loop
+                    if (a.ep.alpha) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        v[4 * j] = act_apply(fmaf(v[4 * j], aa[j].x, bb[j].x), a.ep.act);
-                        v[4 * j + 1] = act_apply(fmaf(v[4 * j + 1], aa[j].y, bb[j].y), a.ep.act);
-                        v[4 * j + 2] = act_apply(fmaf(v[4 * j + 2], aa[j].z, bb[j].z), a.ep.act);
-                        v[4 * j + 3] = act_apply(fmaf(v[4 * j + 3], aa[j].w, bb[j].w), a.ep.act);
+                        for (int j = 0; j < 8; ++j) {
+                            const float4 t = __ldg(reinterpret_cast<const float4*>(a.ep.alpha + o0) + j);
+                            v[4 * j] = fmaf(v[4 * j], t.x, bb[4 * j]);
+                            v[4 * j + 1] = fmaf(v[4 * j + 1], t.y, bb[4 * j + 1]);
+                            v[4 * j + 2] = fmaf(v[4 * j + 2], t.z, bb[4 * j + 2]);
+                            v[4 * j + 3] = fmaf(v[4 * j + 3], t.w, bb[4 * j + 3]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] += bb[j];
+                    }
+                    if (a.ep.act == ACT_LEAKY) {
+                        // leaky(v) = max(v, 0.1 v): v for v > 0, 0.1 v otherwise
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j], kLeakySlope * v[j]);
                     }
                     if (a.ep.out_layout == LAYOUT_NCHW) {
                         if (pool) {

@@ -64,16 +64,6 @@ cudaError_t pack_frames(const float* x, void* y, int n, int C, int H, int W, int
     return cudaGetLastError();
 }
 
-// Value of channel j of the im2col layout at pixel (yy, xx) of frame x.
-__device__ __forceinline__ float im2col_value(const float* __restrict__ x, int C, int H, int W, int k, int j,
-                                              int yy, int xx) {
-    if (j >= C * k * k) return 0.f;
-    const int tap = j / C, c = j % C;
-    const int iy = yy + tap / k - k / 2, ix = xx + tap % k - k / 2;
-    if (iy < 0 || iy >= H || ix < 0 || ix >= W) return 0.f;
-    return x[((size_t)c * H + iy) * W + ix];
-}
-
 template <int DT>
 __device__ __forceinline__ void store_vec(uint8_t* dst, const float* v, float inv_scale) {
     if (DT == DT_F32) {
@@ -96,30 +86,57 @@ __device__ __forceinline__ void store_vec(uint8_t* dst, const float* v, float in
     }
 }
 
+// One thread per output pixel: the C*K*K taps are read with neighbouring
+// threads on neighbouring pixels (coalesced), and the pixel's 32 channels
+// are written as whole 16-byte vectors.  C and K are compile-time so the
+// 32 values stay in registers.
+template <int DT, int C, int K>
+__device__ __forceinline__ void im2col_pixel(const float* __restrict__ x, int H, int W, int yy, int xx,
+                                             uint8_t* dst, float inv_scale) {
+    constexpr int V = DT == DT_F32 ? 4 : DT == DT_BF16 ? 8 : 16;
+    constexpr int CP = 32;
+    static_assert(C * K * K <= CP, "im2col layout holds 32 channels");
+    float v[CP];
+#pragma unroll
+    for (int j = 0; j < CP; ++j) v[j] = 0.f;
+#pragma unroll
+    for (int tap = 0; tap < K * K; ++tap) {
+        const int iy = yy + tap / K - K / 2, ix = xx + tap % K - K / 2;
+        if (iy >= 0 && iy < H && ix >= 0 && ix < W) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) v[tap * C + c] = __ldg(x + ((size_t)c * H + iy) * W + ix);
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < CP / V; ++g) store_vec<DT>(dst + (size_t)g * V * dt_size(DT), v + g * V, inv_scale);
+}
+
+template <int DT>
+__device__ __forceinline__ void im2col_dispatch(const float* x, int C, int H, int W, int yy, int xx, uint8_t* dst,
+                                                float inv_scale) {
+    if (C == 3) im2col_pixel<DT, 3, 3>(x, H, W, yy, xx, dst, inv_scale);
+    else if (C == 2) im2col_pixel<DT, 2, 3>(x, H, W, yy, xx, dst, inv_scale);
+    else im2col_pixel<DT, 1, 3>(x, H, W, yy, xx, dst, inv_scale);
+}
+
 template <int DT>
 __global__ void pack_im2col_kernel(const float* __restrict__ x, void* __restrict__ y, int n, int C, int H, int W,
                                    int Cp, int k, float inv_scale) {
-    constexpr int V = DT == DT_F32 ? 4 : DT == DT_BF16 ? 8 : 16;
-    const int groups = Cp / V;
     const size_t HW = (size_t)H * W;
-    const size_t total = (size_t)n * HW * groups;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int g = (int)(i % groups);
-        const size_t pix = i / groups;
+    const size_t total = (size_t)n * HW;
+    for (size_t pix = blockIdx.x * (size_t)blockDim.x + threadIdx.x; pix < total;
+         pix += (size_t)gridDim.x * blockDim.x) {
         const size_t nn = pix / HW, yx = pix % HW;
-        const int yy = (int)(yx / W), xx = (int)(yx % W);
-        float v[V];
-#pragma unroll
-        for (int j = 0; j < V; ++j) v[j] = im2col_value(x + nn * C * HW, C, H, W, k, g * V + j, yy, xx);
-        store_vec<DT>(reinterpret_cast<uint8_t*>(y) + (pix * Cp + (size_t)g * V) * dt_size(DT), v, inv_scale);
+        uint8_t* dst = reinterpret_cast<uint8_t*>(y) + pix * Cp * dt_size(DT);
+        im2col_dispatch<DT>(x + nn * C * HW, C, H, W, (int)(yx / W), (int)(yx % W), dst, inv_scale);
     }
 }
 
 cudaError_t pack_frames_im2col(const float* x, void* y, int n, int C, int H, int W, int Cp, int k, int dt,
                                float inv_scale, cudaStream_t st) {
-    const int V = dt == DT_F32 ? 4 : dt == DT_BF16 ? 8 : 16;
-    const size_t total = (size_t)n * H * W * (Cp / V);
+    // the first-layer im2col layout: 32 channels, a 3x3 kernel over <= 3 channels
+    if (Cp != 32 || k != 3 || C < 1 || C > 3) return cudaErrorInvalidValue;
+    const size_t total = (size_t)n * H * W;
     const unsigned g = grid_for(total, 256);
     if (dt == DT_F32) pack_im2col_kernel<DT_F32><<<g, 256, 0, st>>>(x, y, n, C, H, W, Cp, k, inv_scale);
     else if (dt == DT_BF16) pack_im2col_kernel<DT_BF16><<<g, 256, 0, st>>>(x, y, n, C, H, W, Cp, k, inv_scale);
@@ -146,16 +163,17 @@ __global__ void pack_grouped_kernel(const PackJob* __restrict__ jobs, int njobs,
          i += (long long)gridDim.x * blockDim.x) {
         const PackJob& J = jobs[find_job(jobs, njobs, i)];
         const long long li = i - J.begin;
+        if (J.im2col_k) {   // one work item per pixel (the job counts pixels)
+            uint8_t* dst = reinterpret_cast<uint8_t*>(J.dst) + li * J.Cp * dt_size(DT);
+            im2col_dispatch<DT>(J.src, J.C, J.H, J.W, (int)(li / J.W), (int)(li % J.W), dst, inv_scale);
+            continue;
+        }
         const int groups = J.Cp / V;
         const int g = (int)(li % groups);
         const long long yx = li / groups;
         const long long HW = (long long)J.H * J.W;
         float v[V];
-        if (J.im2col_k) {
-            const int yy = (int)(yx / J.W), xx = (int)(yx % J.W);
-#pragma unroll
-            for (int j = 0; j < V; ++j) v[j] = im2col_value(J.src, J.C, J.H, J.W, J.im2col_k, g * V + j, yy, xx);
-        } else {
+        {
 #pragma unroll
             for (int j = 0; j < V; ++j) {
                 const int c = g * V + j;

@@ -2,7 +2,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <map>
+#include <mutex>
 #include <tuple>
 #include <vector>
 
@@ -108,7 +110,10 @@ struct net {
     int* err_host = nullptr;   // mapped pinned: bounded device waits that expired
     int* err_dev = nullptr;
     dn::UnevenState* uneven = nullptr;
-    dn::ServeState* serve = nullptr;
+    // request queue, started by the first net_submit; serve_mu serialises
+    // concurrent first submits so exactly one queue is created
+    std::atomic<dn::ServeState*> serve{nullptr};
+    std::mutex serve_mu;
     void graphs_clear();
 };
 

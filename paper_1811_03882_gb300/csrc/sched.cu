@@ -95,7 +95,7 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
         for (int f = 0; f < cnt; ++f) {
             jobs[f] = PackJob{d_in[f], bufp(0, off[0][f]), n->in_c, side[f], side[f], n->L[0].in_cs,
                               n->L[0].im2col_k, b};
-            b += (long long)side[f] * side[f] * (n->L[0].in_cs / V);
+            b += (long long)side[f] * side[f] * (n->L[0].im2col_k ? 1 : n->L[0].in_cs / V);
         }
         P->pack_total = b;
         cudaError_t e = cudaMalloc(&P->d_pack, sizeof(PackJob) * cnt);

@@ -117,3 +117,78 @@ with make_net(spec, prec="bf16", max_side=64) as net:
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert "OK" in r.stdout and "NO-TIMEOUT" not in r.stdout
+
+
+def test_serving_in_flight_cap_queues_and_completes():
+    """With at most 2 requests on the device (NET_SERVE_MAX_ACTIVE, read when
+    the queue starts) a burst of 12 frames still completes, in a child
+    process so the knob stays local."""
+    code = r'''
+import sys, numpy as np
+sys.path.insert(0, %r); sys.path.insert(0, %r)
+import oracle
+from paper_1811_03882_gb300 import synth
+from helpers import make_net
+spec = synth.net_9conv()
+blob = synth.weights_for(spec, 64)
+frames = [synth.frame_for(64, i, 32 * (1 + i %% 3)) for i in range(12)]
+with make_net(spec, prec="bf16", max_side=96) as net:
+    net.load_weights(blob)
+    ids = [net.submit(f) for f in frames]
+    for f, rid in zip(frames, ids):
+        c, ho, wo = net.output_shape(f.shape[2], f.shape[3])
+        y = np.zeros((1, c, ho, wo), np.float32)
+        net.wait(rid, y, 60000)
+        assert oracle.normwise_rel_err(y, oracle.forward(spec.layers, 3, f, blob)) <= 2e-2
+print("OK")
+''' % (ROOT, os.path.join(ROOT, "tests"))
+    env = dict(os.environ, NET_SERVE_MAX_ACTIVE="2")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "OK" in r.stdout
+
+
+def test_serving_concurrent_submitters_and_full_steps():
+    """Four threads submit at once into a fresh queue (one queue must start),
+    and a slow first step lets a burst pile up so that the next steps carry
+    up to the in-flight cap: 19 layers x 128 requests of problem tables in
+    one step.  Every result is checked against the same frame alone."""
+    code = r'''
+import sys, threading, numpy as np
+sys.path.insert(0, %r); sys.path.insert(0, %r)
+import oracle
+from paper_1811_03882_gb300 import synth
+from helpers import make_net
+spec = synth.net_19conv()
+blob = synth.weights_for(spec, 65)
+frames = [synth.frame_for(65, i, 32 * (1 + i %% 3)) for i in range(160)]
+with make_net(spec, prec="bf16", max_side=96) as net:
+    net.load_weights(blob)
+    ids = [None] * len(frames)
+    def sub(k):
+        for i in range(k, len(frames), 4):
+            ids[i] = net.submit(frames[i])
+    ths = [threading.Thread(target=sub, args=(k,)) for k in range(4)]
+    for t in ths: t.start()
+    for t in ths: t.join()
+    assert len(set(ids)) == len(frames)
+    outs = []
+    for f, rid in zip(frames, ids):
+        c, ho, wo = net.output_shape(f.shape[2], f.shape[3])
+        y = np.full((1, c, ho, wo), np.nan, np.float32)
+        net.wait(rid, y, 120000)
+        outs.append(y)
+    for i in (0, 1, 2, 77, 159):
+        rid = net.submit(frames[i])
+        alone = np.full_like(outs[i], np.nan)
+        net.wait(rid, alone, 60000)
+        assert np.array_equal(alone, outs[i]), i
+    for i in (0, 2, 100):
+        e = oracle.normwise_rel_err(outs[i], oracle.forward(spec.layers, 3, frames[i], blob))
+        assert e <= 2e-2, (i, e)
+print("OK")
+''' % (ROOT, os.path.join(ROOT, "tests"))
+    env = dict(os.environ, NET_SERVE_STEP_DELAY_US="20000")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "OK" in r.stdout
