@@ -5,6 +5,8 @@
 #include <cuda_fp8.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace dn {
 
 enum { ACT_LINEAR = 0, ACT_LEAKY = 1 };
@@ -58,6 +60,35 @@ __device__ __forceinline__ uint8_t f32_to_e4m3_sat(float v) {
 __device__ __forceinline__ float e4m3_to_f32(uint8_t b) {
     __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, __NV_E4M3);
     return __half2float(__half(h));
+}
+
+// Programmatic dependent launch.  A kernel launched with launch_pdl may be
+// scheduled while the previous kernel in its stream is still finishing:
+// pdl_trigger lets the next kernel start its own prologue early, and
+// pdl_wait blocks until every earlier kernel of the stream has completed and
+// its writes are visible, so it must come before the first global access.
+// Both are no-ops for a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Whether launches use the programmatic-serialisation attribute (on unless
+// NET_PDL=0 in the environment).
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                     Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 }  // namespace dn

@@ -12,17 +12,18 @@
 // padding, so no im2col buffer exists.  B is the matching [BN x chunk]
 // box of the K-major weights [Cout][kh][kw][Cin].
 //
-// Persistent, warp-specialised CTA (one per SM, 352 threads):
+// Persistent, warp-specialised CTA (one per SM, 384 threads):
 //   warps 0,10 TMA producers (one lane each, alternate K steps), STAGES-deep
 //              smem ring (STAGES even)
-//   warp 1     TMEM owner and MMA issuer (one lane)
-//   warps 2-9  epilogue: two warpgroups, one per TMEM accumulator buffer
-//              (alternate tiles): tcgen05.ld, alpha/bias, leaky, 2x2 max via
-//              warp shuffles, downcast, 16-byte stores
-// Two TMEM accumulators let the epilogue of one tile overlap the
-// mainloop of the next.  Every mbarrier wait is bounded: on expiry the
-// kernel records an error code, drains its TMA copies, frees TMEM and
-// returns.
+//   warps 1,11 MMA issuers (one lane each, alternate tiles); warp 1 owns TMEM
+//   warps 2-9  epilogue: two warpgroups, one per issuer's tiles:
+//              tcgen05.ld, alpha/bias, leaky, 2x2 max via warp shuffles,
+//              downcast, 16-byte stores
+// Several TMEM accumulators (four up to BN = 128, else two) let the
+// epilogue of one tile overlap the mainloop of the next; an accumulator is
+// handed back as soon as its last live column is in registers.  Every
+// mbarrier wait is bounded: on expiry the kernel records an error code,
+// drains its TMA copies, frees TMEM and returns.
 #include <cuda.h>
 
 #include "common.cuh"
@@ -32,7 +33,7 @@ namespace dn {
 
 namespace tc {
 
-constexpr int THREADS = 352;   // producer, MMA issuer, 8 epilogue warps, second producer
+constexpr int THREADS = 384;   // producer, MMA issuer, 8 epilogue warps, second producer, second MMA issuer
 constexpr int NUM_WARPS = THREADS / 32;
 constexpr int A_BYTES = 128 * 128;            // 128 rows x 128-byte chunk (max)
 constexpr long long WAIT_LIMIT = 4000000000LL;  // clock64 cycles (~2 s)
@@ -218,7 +219,11 @@ __device__ __forceinline__ int find_problem(const ConvProblem* probs, int nprob,
 }
 
 struct Smem {
-    uint64_t full[8], empty[8], accf[2], acce[2], done;
+    // full[m][s]: stage s holds data for a tile of MMA issuer m.  One barrier
+    // per (issuer, stage) keeps every barrier's phases consumed in order by a
+    // single waiter, which a parity wait needs: with one barrier per stage the
+    // second issuer could test a stage two phases ahead and pass on old data.
+    uint64_t full[2][8], empty[8], accf[4], acce[4], done;
     uint32_t tmem;
     int abort;
 };
@@ -233,13 +238,17 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     using namespace tc;
     constexpr int B_BYTES = BN * 128;
-    constexpr int TMEM_COLS = 2 * BN;
+    // accumulator buffers in TMEM (512 columns): four up to BN = 128, so the
+    // MMAs of the next tiles never wait for an epilogue's round trip
+    constexpr int NBUF = BN <= 128 ? 4 : 2;
+    constexpr int TMEM_COLS = NBUF * BN;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
     uint8_t* sB = smem + STAGES * A_BYTES;
     Smem* sm = reinterpret_cast<Smem*>(sB + STAGES * B_BYTES);
 
+    pdl_trigger();   // the next kernel may start its prologue as SMs free up
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int KK = a.k * a.k;
     const int nk = KK * a.chunks;                 // K steps per tile
@@ -255,14 +264,15 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            tc::mbar_init(smem_u32(&sm->full[s]), 1);
+            tc::mbar_init(smem_u32(&sm->full[0][s]), 1);
+            tc::mbar_init(smem_u32(&sm->full[1][s]), 1);
             tc::mbar_init(smem_u32(&sm->empty[s]), CS);   // every consumer of the cluster frees a stage
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NBUF; ++b) {
             tc::mbar_init(smem_u32(&sm->accf[b]), 1);
-            tc::mbar_init(smem_u32(&sm->acce[b]), 4);   // the 4 warps of warpgroup b
+            tc::mbar_init(smem_u32(&sm->acce[b]), 4);   // the 4 warps of the warpgroup that drains buffer b
         }
-        tc::mbar_init(smem_u32(&sm->done), 1);
+        tc::mbar_init(smem_u32(&sm->done), 2);   // one commit from each MMA issuer
         sm->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -279,85 +289,140 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     tc::fence_after();
     const uint32_t tmem_base = sm->tmem;
     volatile int* abort_flag = &sm->abort;
+    // the prologue above may overlap the previous kernel; activations,
+    // problem tables and split-K workspace are touched only after it ended
+    pdl_wait();
 
-    if (warp == 0 || warp == NUM_WARPS - 1) {
+    if (warp == 0 || warp == NUM_WARPS - 2) {
         // ------------------------------------------------ TMA producers
         // A cp.async.bulk.tensor blocks its issuing thread for hundreds of
         // cycles, so one thread cannot keep the tensor pipe fed: two producer
         // warps take alternate K steps (and so alternate stages).
         const int pid = warp == 0 ? 0 : 1;
         if (lane == 0) {
-            int it = 0;
+            int it = 0, tcount = 0;
             bool ok = true;
-            for (int tile = worker; tile < total && ok; tile += nworkers) {
-                const int z = tile % a.ksplit, mn = tile / a.ksplit;
-                const int mt = (mn / a.n_tiles) * CS + rank, nt = mn % a.n_tiles;
-                const int ks0 = (int)((long)nk * z / a.ksplit), ks1 = (int)((long)nk * (z + 1) / a.ksplit);
-                const int p = tc::find_problem(a.probs, a.nprob, mt);
-                const ConvProblem& P = a.probs[p];
-                const int local = mt - P.tile_begin;
-                const int tx = local % P.tiles_x;
-                const int ty = (local / P.tiles_x) % P.tiles_y;
-                const int img = local / (P.tiles_x * P.tiles_y);
-                const int x0 = tx * a.TW, y0 = ty * a.TH;
+            // per issuer: bit s = phase parity of the next use of full[m][s];
+            // per stage this producer fills: the issuer of its last use
+            uint32_t pph0 = 0u, pph1 = 0u, last_owner = 0u, issued = 0u;
+            // a single-problem launch keeps the problem's fields in registers
+            const ConvProblem* P1 = a.nprob == 1 ? a.probs : nullptr;
+            int tiles_x = 1, tiles_y = 1, tbeg = 0;
+            if (P1) {
+                tiles_x = P1->tiles_x;
+                tiles_y = P1->tiles_y;
+                tbeg = P1->tile_begin;
+            }
+            for (int tile = worker; tile < total && ok; tile += nworkers, ++tcount) {
+                const int z = a.ksplit > 1 ? tile % a.ksplit : 0;
+                const int mn = a.ksplit > 1 ? tile / a.ksplit : tile;
+                const int mq = mn / a.n_tiles;
+                const int mt = mq * CS + rank, nt = mn - mq * a.n_tiles;
+                const int ks0 = nk * z / a.ksplit, ks1 = nk * (z + 1) / a.ksplit;
+                const int owner = tcount & 1;   // MMA issuer of this tile
+                // no K step of this tile falls to this producer: skip its set-up
+                if (ks1 - ks0 < 2 && (it & 1) != pid) {
+                    it += ks1 - ks0;
+                    continue;
+                }
+                const ConvProblem* P = P1 ? P1 : a.probs + tc::find_problem(a.probs, a.nprob, mt);
+                if (!P1) {
+                    tiles_x = P->tiles_x;
+                    tiles_y = P->tiles_y;
+                    tbeg = P->tile_begin;
+                }
+                const int local = mt - tbeg;
+                const int txy = local / tiles_x;
+                const int tx = local - txy * tiles_x;
+                const int img = txy / tiles_y;
+                const int ty = txy - img * tiles_y;
+                const int x0 = tx * a.TW - pad, y0 = ty * a.TH - pad;
+                // (tap row, tap column, chunk) of the first K step, then stepped
+                int ch = ks0 % a.chunks;
+                const int tap0 = ks0 / a.chunks;
+                int kh = tap0 / a.k, kw = tap0 - kh * a.k;
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
-                    if ((it & 1) != pid) continue;
-                    const int tap = ks / a.chunks, ch = ks % a.chunks;
-                    const int kh = tap / a.k, kw = tap % a.k;
-                    {
+                    if ((it & 1) == pid) {
                         const int s = it % STAGES;
                         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                         if (!tc::mbar_wait(smem_u32(&sm->empty[s]), ph ^ 1u, abort_flag, a.err, 1)) {
                             ok = false;
                             break;
                         }
-                        const uint32_t fb = smem_u32(&sm->full[s]);
+                        const uint32_t fb = smem_u32(&sm->full[owner][s]);
+                        if (owner) pph1 ^= 1u << s;
+                        else pph0 ^= 1u << s;
+                        last_owner = (last_owner & ~(1u << s)) | ((uint32_t)owner << s);
+                        issued |= 1u << s;
                         tc::mbar_expect_tx(fb, a_bytes + b_bytes);
                         const int c0 = ch * a.cpc;
-                        tc::tma_load_4d(smem_u32(sA + s * A_BYTES), &P.tmA, c0, x0 + kw - pad, y0 + kh - pad,
-                                        img, fb);
+                        const int kcol = (kh * a.k + kw) * a.Cp + c0;   // K column of the weights
+                        tc::tma_load_4d(smem_u32(sA + s * A_BYTES), &P->tmA, c0, x0 + kw, y0 + kh, img, fb);
                         if (CS == 1) {
-                            tc::tma_load_2d(smem_u32(sB + s * B_BYTES), &tmB, tap * a.Cp + c0, nt * BN, fb);
+                            tc::tma_load_2d(smem_u32(sB + s * B_BYTES), &tmB, kcol, nt * BN, fb);
                         } else {
                             constexpr int BR = BN / CS;   // rows of B this CTA loads for the cluster
-                            tc::tma_load_2d_mc(smem_u32(sB + s * B_BYTES + rank * BR * a.chb), &tmB, tap * a.Cp + c0,
+                            tc::tma_load_2d_mc(smem_u32(sB + s * B_BYTES + rank * BR * a.chb), &tmB, kcol,
                                                nt * BN + rank * BR, fb, cmask);
+                        }
+                    }
+                    if (++ch == a.chunks) {
+                        ch = 0;
+                        if (++kw == a.k) {
+                            kw = 0;
+                            ++kh;
                         }
                     }
                 }
             }
-            // drain: every copy issued must have landed before smem goes away
-            for (int j = (it > STAGES ? it - STAGES : 0); j < it; ++j)
-                if ((j & 1) == pid && !tc::mbar_wait(smem_u32(&sm->full[j % STAGES]), (uint32_t)(j / STAGES) & 1u, abort_flag,
-                                   a.err, 5)) {
+            // drain: every copy issued must have landed before smem goes away.
+            // Earlier uses of a stage were consumed before it was refilled, so
+            // only the last use of each stage can still be in flight.
+            for (int st = 0; st < STAGES; ++st) {
+                if (!((issued >> st) & 1u)) continue;
+                const int o = (int)((last_owner >> st) & 1u);
+                const uint32_t bar = smem_u32(&sm->full[o][st]);
+                const uint32_t lph = (((o ? pph1 : pph0) >> st) & 1u) ^ 1u;   // parity of the last use
+                if (!tc::mbar_wait(bar, lph, abort_flag, a.err, 5)) {
                     // abort already flagged: give the copies a bounded grace period
                     const long long t0 = clock64();
-                    while (!tc::mbar_try(smem_u32(&sm->full[j % STAGES]), (uint32_t)(j / STAGES) & 1u) &&
-                           clock64() - t0 < WAIT_LIMIT) {
+                    while (!tc::mbar_try(bar, lph) && clock64() - t0 < WAIT_LIMIT) {
                     }
                 }
+            }
         }
-    } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer
+    } else if (warp == 1 || warp == NUM_WARPS - 1) {
+        // ------------------------------------------------ MMA issuers
+        // One thread pays ~150 cycles to issue each tcgen05 instruction, more
+        // than a small MMA keeps the tensor pipe busy: two issuer warps take
+        // alternate tiles (and so alternate accumulator buffers) and their
+        // issue latencies overlap.
+        const int mid = warp == 1 ? 0 : 1;
         if (lane == 0) {
             const uint32_t idesc = tc::instr_desc<DT>(BN);
             int it = 0, tcount = 0;
+            uint32_t fph = 0u;   // bit s = phase parity of this issuer's next use of stage s
             bool ok = true;
             for (int tile = worker; tile < total && ok; tile += nworkers, ++tcount) {
-                const int z = tile % a.ksplit;
-                const int ks0 = (int)((long)nk * z / a.ksplit), ks1 = (int)((long)nk * (z + 1) / a.ksplit);
-                const int b = tcount & 1;
-                const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
+                const int z = a.ksplit > 1 ? tile % a.ksplit : 0;
+                const int ks0 = nk * z / a.ksplit, ks1 = nk * (z + 1) / a.ksplit;
+                if ((tcount & 1) != mid) {   // the other issuer's tile: its stages are skipped
+                    it += ks1 - ks0;
+                    continue;
+                }
+                const int b = tcount % NBUF;
+                const uint32_t aph = (uint32_t)(tcount / NBUF) & 1u;
                 if (!tc::mbar_wait(smem_u32(&sm->acce[b]), aph ^ 1u, abort_flag, a.err, 2)) break;
                 tc::fence_after();
                 const uint32_t dtm = tmem_base + (uint32_t)(b * BN);
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
                     const int s = it % STAGES;
-                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                    if (!tc::mbar_wait(smem_u32(&sm->full[s]), ph, abort_flag, a.err, 3)) {
+                    const uint32_t ph = (fph >> s) & 1u;
+                    if (!tc::mbar_wait(smem_u32(&sm->full[mid][s]), ph, abort_flag, a.err, 3)) {
                         ok = false;
                         break;
                     }
+                    fph ^= 1u << s;
                     tc::fence_after();
                     const uint64_t ad = tc::smem_desc(smem_u32(sA + s * A_BYTES), a.chb);
                     const uint64_t bd = tc::smem_desc(smem_u32(sB + s * B_BYTES), a.chb);
@@ -396,13 +461,15 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         int pH = 0, pW = 0, pTX = 1, pTY = 1, pBegin = 0;
         int tcount = 0;
         for (int tile = worker; tile < total; tile += nworkers, ++tcount) {
-            const int b = tcount & 1;
-            if (b != grp) continue;
-            const uint32_t aph = (uint32_t)(tcount >> 1) & 1u;
+            if ((tcount & 1) != grp) continue;
+            const int b = tcount % NBUF;
+            const uint32_t aph = (uint32_t)(tcount / NBUF) & 1u;
             if (!tc::mbar_wait(smem_u32(&sm->accf[b]), aph, abort_flag, a.err, 4)) break;
             tc::fence_after();
-            const int z = tile % a.ksplit, mn = tile / a.ksplit;
-            const int mt = (mn / a.n_tiles) * CS + rank, nt = mn % a.n_tiles;
+            const int z = a.ksplit > 1 ? tile % a.ksplit : 0;
+            const int mn = a.ksplit > 1 ? tile / a.ksplit : tile;
+            const int mq = mn / a.n_tiles;
+            const int mt = mq * CS + rank, nt = mn - mq * a.n_tiles;
             if (mt >= a.m_tiles) {
                 // the cluster's spare CTA on an odd tile count: loads and MMAs ran on
                 // zero-filled operands; nothing to store
@@ -412,6 +479,15 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 continue;
             }
             const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * HC);
+            // the buffer goes back to the MMA issuer right after its last live
+            // column is in registers; the math and stores of that chunk follow
+            bool released = false;
+            auto release = [&] {
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(smem_u32(&sm->acce[b]));
+                released = true;
+            };
             if (a.ksplit > 1) {
                 // raw partial sums of this K slice; the reduction applies the epilogue
                 const int ncp = a.n_tiles * BN;
@@ -422,6 +498,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     float v[32];
                     __syncwarp();
                     tc::tmem_ld32(trow + (uint32_t)c0, v);
+                    if (c0 + 32 >= HC || nt * BN + half * HC + c0 + 32 >= live) release();
 #pragma unroll
                     for (int j = 0; j < 32; j += 4)
                         *reinterpret_cast<float4*>(wr + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
@@ -439,9 +516,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 }
                 void* ybase = a.y_override ? a.y_override : pY;
                 const int local = mt - pBegin;
-                const int tx = local % pTX;
-                const int ty = (local / pTX) % pTY;
-                const int img = local / (pTX * pTY);
+                const int txy = local / pTX;
+                const int tx = local - txy * pTX;
+                const int img = txy / pTY;
+                const int ty = txy - img * pTY;
                 const int gy = ty * a.TH + py, gx = tx * a.TW + px;
                 const bool valid = gy < pH && gx < pW;
                 const int Ho = pool ? pH / 2 : pH, Wo = pool ? pW / 2 : pW;
@@ -466,6 +544,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     float v[32];
                     __syncwarp();
                     tc::tmem_ld32(trow + (uint32_t)c0, v);
+                    if (c0 + 32 >= HC || o0 + 32 >= live) release();
                     // warp-uniform branches: each variant is one straight-line loop
                     if (a.ep.alpha) {
 #pragma unroll
@@ -561,9 +640,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     }
                 }
             }
-            tc::fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(smem_u32(&sm->acce[b]));
+            if (!released) release();   // a tile without live columns (not produced by the planner)
         }
     }
 
@@ -646,22 +723,27 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a, int wor
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    if (CS == 1) {
-        kern<<<workers, tc::THREADS, smem, st>>>(tmB, a);
-        return cudaGetLastError();
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(workers * CS));
     cfg.blockDim = dim3(tc::THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CS;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
+    cudaLaunchAttribute at[2];
+    int na = 0;
+    if (CS > 1) {
+        at[na].id = cudaLaunchAttributeClusterDimension;
+        at[na].val.clusterDim.x = CS;
+        at[na].val.clusterDim.y = 1;
+        at[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    if (pdl_enabled()) {
+        at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = na;
     return cudaLaunchKernelEx(&cfg, kern, tmB, a);
 }
 

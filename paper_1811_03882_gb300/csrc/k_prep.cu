@@ -230,6 +230,8 @@ __device__ __forceinline__ float dec(const uint8_t* p, int j, int dt) {
 
 __global__ void pool_s1_kernel(const uint8_t* __restrict__ x, uint8_t* __restrict__ y, int n, int H,
                                int W, int cs, int dt) {
+    pdl_trigger();
+    pdl_wait();
     const int esz = dt == DT_F32 ? 4 : dt == DT_BF16 ? 2 : 1;
     const int V = 16 / esz;
     const int groups = cs / V;
@@ -260,6 +262,8 @@ __global__ void pool_s1_kernel(const uint8_t* __restrict__ x, uint8_t* __restric
 
 __global__ void pool_s1_grouped_kernel(const PoolJob* __restrict__ jobs, int njobs, long long total, int cs,
                                        int dt) {
+    pdl_trigger();
+    pdl_wait();
     const int esz = dt == DT_F32 ? 4 : dt == DT_BF16 ? 2 : 1;
     const int V = 16 / esz;
     const int groups = cs / V;
@@ -290,17 +294,16 @@ __global__ void pool_s1_grouped_kernel(const PoolJob* __restrict__ jobs, int njo
 
 cudaError_t maxpool_s1_grouped(const PoolJob* jobs, int njobs, long long total, int cs, int dt,
                                cudaStream_t st) {
-    pool_s1_grouped_kernel<<<grid_for((size_t)total, 256), 256, 0, st>>>(jobs, njobs, total, cs, dt);
-    return cudaGetLastError();
+    return launch_pdl(pool_s1_grouped_kernel, dim3(grid_for((size_t)total, 256)), dim3(256), 0, st, jobs, njobs, total,
+                      cs, dt);
 }
 
 cudaError_t maxpool_s1_same(const void* x, void* y, int n, int H, int W, int cs, int dt,
                             cudaStream_t st) {
     const int V = 16 / (int)dt_size(dt);
     const size_t total = (size_t)n * H * W * (cs / V);
-    pool_s1_kernel<<<grid_for(total, 256), 256, 0, st>>>(reinterpret_cast<const uint8_t*>(x),
-                                                         reinterpret_cast<uint8_t*>(y), n, H, W, cs, dt);
-    return cudaGetLastError();
+    return launch_pdl(pool_s1_kernel, dim3(grid_for(total, 256)), dim3(256), 0, st,
+                      reinterpret_cast<const uint8_t*>(x), reinterpret_cast<uint8_t*>(y), n, H, W, cs, dt);
 }
 
 // ---------------------------------------------------------------- fold

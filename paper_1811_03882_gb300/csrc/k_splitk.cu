@@ -11,6 +11,8 @@
 namespace dn {
 
 __global__ void splitk_reduce_kernel(SplitReduce r) {
+    pdl_trigger();
+    pdl_wait();   // the partial sums come from the conv launch before this one
     const bool pool = r.ep.pool == POOL_S2;
     const int Ho = pool ? r.H / 2 : r.H, Wo = pool ? r.W / 2 : r.W;
     const bool nchw = r.ep.out_layout == LAYOUT_NCHW;
@@ -100,8 +102,7 @@ cudaError_t splitk_reduce(const SplitReduce& r, cudaStream_t st) {
     const size_t total = npix * ((ncols + 3) / 4);
     size_t blocks = (total + 255) / 256;
     if (blocks > 152u * 16u) blocks = 152u * 16u;
-    splitk_reduce_kernel<<<(unsigned)(blocks ? blocks : 1), 256, 0, st>>>(r);
-    return cudaGetLastError();
+    return launch_pdl(splitk_reduce_kernel, dim3((unsigned)(blocks ? blocks : 1)), dim3(256), 0, st, r);
 }
 
 }  // namespace dn

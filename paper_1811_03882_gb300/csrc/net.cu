@@ -431,6 +431,14 @@ void dn::tc_workers(int m_tiles, int n_tiles, int ks, int BN, int num_sms, int* 
     *workers = std::max(1, std::min(items, num_sms / *cs));
 }
 
+bool dn::pdl_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("NET_PDL");
+        return !(e && atoi(e) == 0);
+    }();
+    return on;
+}
+
 int dn::tmb_index(int BN, int cs) {
     const int rows = BN / cs;
     return rows == 64 ? 0 : rows == 128 ? 1 : 2;
