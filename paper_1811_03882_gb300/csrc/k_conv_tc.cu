@@ -13,8 +13,12 @@
 // box of the K-major weights [Cout][kh][kw][Cin].
 //
 // Persistent, warp-specialised CTA (one per SM, 384 threads):
-//   warps 0,10 TMA producers (one lane each, alternate K steps), STAGES-deep
-//              smem ring (STAGES even)
+//   warps 0,10 TMA producers (one lane each, alternate K steps) into a
+//              shared-memory ring of nst stages (nst even).  A stage holds one
+//              K step's A box and B box (A only when the weights are
+//              resident); the ring is sized from the actual box bytes, since
+//              a box takes ~2000 cycles to land under load and throughput is
+//              stages in flight over that latency
 //   warps 1,11 MMA issuers (one lane each, alternate tiles); warp 1 owns TMEM
 //   warps 2-9  epilogue: two warpgroups, one per issuer's tiles:
 //              tcgen05.ld, alpha/bias, leaky, 2x2 max via warp shuffles,
@@ -26,6 +30,8 @@
 // drains its TMA copies, frees TMEM and returns.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -35,7 +41,8 @@ namespace tc {
 
 constexpr int THREADS = 384;   // producer, MMA issuer, 8 epilogue warps, second producer, second MMA issuer
 constexpr int NUM_WARPS = THREADS / 32;
-constexpr int A_BYTES = 128 * 128;            // 128 rows x 128-byte chunk (max)
+constexpr int kMaxStages = 32;                // ring stages (bit masks below are 32 bits)
+constexpr int kEpiCols = 1024;                // bias / alpha columns kept in shared memory
 constexpr long long WAIT_LIMIT = 4000000000LL;  // clock64 cycles (~2 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -223,7 +230,7 @@ struct Smem {
     // per (issuer, stage) keeps every barrier's phases consumed in order by a
     // single waiter, which a parity wait needs: with one barrier per stage the
     // second issuer could test a stage two phases ahead and pass on old data.
-    uint64_t full[2][8], empty[8], accf[4], acce[4], done;
+    uint64_t full[2][kMaxStages], empty[kMaxStages], accf[4], acce[4], done, bres;
     uint32_t tmem;
     int abort;
 };
@@ -233,20 +240,26 @@ struct Smem {
 // CS = cluster size: with CS = 2 the two CTAs of a cluster work on
 // neighbouring M tiles of the same N tile, and each loads half of the
 // weight (B) box and multicasts it to both, halving the B traffic from L2.
-template <int BN, int DT, int STAGES, int CS>
+template <int BN, int DT, int CS>
 __global__ void __launch_bounds__(tc::THREADS, 1)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     using namespace tc;
-    constexpr int B_BYTES = BN * 128;
     // accumulator buffers in TMEM (512 columns): four up to BN = 128, so the
     // MMAs of the next tiles never wait for an epilogue's round trip
     constexpr int NBUF = BN <= 128 ? 4 : 2;
     constexpr int TMEM_COLS = NBUF * BN;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* sA = smem;
-    uint8_t* sB = smem + STAGES * A_BYTES;
-    Smem* sm = reinterpret_cast<Smem*>(sB + STAGES * B_BYTES);
+    // ring stages of st_bytes at smem (A box, then B box), resident weights at
+    // bres_off, then the control block (host-computed geometry: tc_geometry)
+    uint8_t* sRing = smem;
+    uint8_t* sBres = smem + a.bres_off;
+    Smem* sm = reinterpret_cast<Smem*>(smem + a.ctrl_off);
+    const int nst = a.nst;
+    const uint32_t st_bytes = (uint32_t)a.st_bytes;
+    // epilogue copies of bias / alpha (launches with at most kEpiCols columns)
+    float* s_bias = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(sm) + ((sizeof(Smem) + 15) & ~(size_t)15));
+    float* s_alpha = s_bias + kEpiCols;
 
     pdl_trigger();   // the next kernel may start its prologue as SMs free up
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -263,7 +276,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     const uint32_t a_bytes = 128u * a.chb, b_bytes = (uint32_t)BN * a.chb;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < nst; ++s) {
             tc::mbar_init(smem_u32(&sm->full[0][s]), 1);
             tc::mbar_init(smem_u32(&sm->full[1][s]), 1);
             tc::mbar_init(smem_u32(&sm->empty[s]), CS);   // every consumer of the cluster frees a stage
@@ -273,6 +286,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             tc::mbar_init(smem_u32(&sm->acce[b]), 4);   // the 4 warps of the warpgroup that drains buffer b
         }
         tc::mbar_init(smem_u32(&sm->done), 2);   // one commit from each MMA issuer
+        tc::mbar_init(smem_u32(&sm->bres), 1);
         sm->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -295,16 +309,32 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
 
     if (warp == 0 || warp == NUM_WARPS - 2) {
         // ------------------------------------------------ TMA producers
-        // A cp.async.bulk.tensor blocks its issuing thread for hundreds of
-        // cycles, so one thread cannot keep the tensor pipe fed: two producer
-        // warps take alternate K steps (and so alternate stages).
+        // A warp issues one cp.async.bulk.tensor instruction per ~500 cycles
+        // whatever its size, but lanes of one instruction are nearly free:
+        // each of the two producer warps runs G lanes, lane j filling the K
+        // steps it = pid + 2j (mod 2G) of this CTA's sequence.  2G divides
+        // the stage count, so every stage is always filled by the same lane
+        // and sees its uses in order (its empty phases are waited in order).
         const int pid = warp == 0 ? 0 : 1;
-        if (lane == 0) {
-            int it = 0, tcount = 0;
-            bool ok = true;
-            // per issuer: bit s = phase parity of the next use of full[m][s];
-            // per stage this producer fills: the issuer of its last use
-            uint32_t pph0 = 0u, pph1 = 0u, last_owner = 0u, issued = 0u;
+        const int G = a.plane;
+        const int S2 = 2 * G;
+        if (a.bres && pid == 0 && lane == 0) {
+            // resident weights: every K step's [BN x chunk] box, once, side by
+            // side (the launch has one N tile and no K split)
+            const uint32_t rb = smem_u32(&sm->bres);
+            tc::mbar_expect_tx(rb, (uint32_t)nk * b_bytes);
+            int ch = 0, tap = 0;
+            for (int ks = 0; ks < nk; ++ks) {
+                tc::tma_load_2d(smem_u32(sBres + (size_t)ks * b_bytes), &tmB, tap * a.Cp + ch * a.cpc, 0, rb);
+                if (++ch == a.chunks) {
+                    ch = 0;
+                    ++tap;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane < G) {
+            const unsigned gmask = (1u << G) - 1u;
             // a single-problem launch keeps the problem's fields in registers
             const ConvProblem* P1 = a.nprob == 1 ? a.probs : nullptr;
             int tiles_x = 1, tiles_y = 1, tbeg = 0;
@@ -313,20 +343,25 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 tiles_y = P1->tiles_y;
                 tbeg = P1->tile_begin;
             }
-            for (int tile = worker; tile < total && ok; tile += nworkers, ++tcount) {
+            // this lane's position: tile sequence index t (tile = worker + t *
+            // nworkers), K step ks of that tile's slice [ks0, ks1), and `it`
+            int t = 0, tile = worker, ks0 = 0, ks1 = 0, ks = 0;
+            int ch = 0, kw = 0, kh = 0;   // chunk, tap column, tap row of ks
+            int owner = 0, nt = 0, img = 0, x0 = 0, y0 = 0;
+            const ConvProblem* P = P1;
+            auto slice = [&] {
                 const int z = a.ksplit > 1 ? tile % a.ksplit : 0;
+                ks0 = nk * z / a.ksplit;
+                ks1 = nk * (z + 1) / a.ksplit;
+            };
+            auto setup = [&] {   // coordinates of the lane's current tile
                 const int mn = a.ksplit > 1 ? tile / a.ksplit : tile;
                 const int mq = mn / a.n_tiles;
-                const int mt = mq * CS + rank, nt = mn - mq * a.n_tiles;
-                const int ks0 = nk * z / a.ksplit, ks1 = nk * (z + 1) / a.ksplit;
-                const int owner = tcount & 1;   // MMA issuer of this tile
-                // no K step of this tile falls to this producer: skip its set-up
-                if (ks1 - ks0 < 2 && (it & 1) != pid) {
-                    it += ks1 - ks0;
-                    continue;
-                }
-                const ConvProblem* P = P1 ? P1 : a.probs + tc::find_problem(a.probs, a.nprob, mt);
+                const int mt = mq * CS + rank;
+                nt = mn - mq * a.n_tiles;
+                owner = t & 1;
                 if (!P1) {
+                    P = a.probs + tc::find_problem(a.probs, a.nprob, mt);
                     tiles_x = P->tiles_x;
                     tiles_y = P->tiles_y;
                     tbeg = P->tile_begin;
@@ -334,51 +369,100 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 const int local = mt - tbeg;
                 const int txy = local / tiles_x;
                 const int tx = local - txy * tiles_x;
-                const int img = txy / tiles_y;
+                img = txy / tiles_y;
                 const int ty = txy - img * tiles_y;
-                const int x0 = tx * a.TW - pad, y0 = ty * a.TH - pad;
-                // (tap row, tap column, chunk) of the first K step, then stepped
-                int ch = ks0 % a.chunks;
-                const int tap0 = ks0 / a.chunks;
-                int kh = tap0 / a.k, kw = tap0 - kh * a.k;
-                for (int ks = ks0; ks < ks1; ++ks, ++it) {
-                    if ((it & 1) == pid) {
-                        const int s = it % STAGES;
-                        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                        if (!tc::mbar_wait(smem_u32(&sm->empty[s]), ph ^ 1u, abort_flag, a.err, 1)) {
-                            ok = false;
-                            break;
-                        }
-                        const uint32_t fb = smem_u32(&sm->full[owner][s]);
-                        if (owner) pph1 ^= 1u << s;
-                        else pph0 ^= 1u << s;
-                        last_owner = (last_owner & ~(1u << s)) | ((uint32_t)owner << s);
-                        issued |= 1u << s;
-                        tc::mbar_expect_tx(fb, a_bytes + b_bytes);
-                        const int c0 = ch * a.cpc;
-                        const int kcol = (kh * a.k + kw) * a.Cp + c0;   // K column of the weights
-                        tc::tma_load_4d(smem_u32(sA + s * A_BYTES), &P->tmA, c0, x0 + kw, y0 + kh, img, fb);
-                        if (CS == 1) {
-                            tc::tma_load_2d(smem_u32(sB + s * B_BYTES), &tmB, kcol, nt * BN, fb);
-                        } else {
-                            constexpr int BR = BN / CS;   // rows of B this CTA loads for the cluster
-                            tc::tma_load_2d_mc(smem_u32(sB + s * B_BYTES + rank * BR * a.chb), &tmB, kcol,
-                                               nt * BN + rank * BR, fb, cmask);
-                        }
-                    }
-                    if (++ch == a.chunks) {
-                        ch = 0;
+                x0 = tx * a.TW - pad;
+                y0 = ty * a.TH - pad;
+            };
+            auto decompose = [&] {   // (ch, kw, kh) of ks, by division (tile changes only)
+                const int tap = ks / a.chunks;
+                ch = ks - tap * a.chunks;
+                kh = tap / a.k;
+                kw = tap - kh * a.k;
+            };
+            // moves the position forward by d K steps (across tiles)
+            auto advance = [&](int d) {
+                ks += d;
+                if (ks < ks1) {   // same tile: step the chunk / tap counters
+                    ch += d;
+                    while (ch >= a.chunks) {
+                        ch -= a.chunks;
                         if (++kw == a.k) {
                             kw = 0;
                             ++kh;
                         }
                     }
+                    return;
+                }
+                while (tile < total && ks >= ks1) {
+                    const int over = ks - ks1;
+                    ++t;
+                    tile += nworkers;
+                    if (tile >= total) return;
+                    slice();
+                    ks = ks0 + over;
+                }
+                setup();
+                decompose();
+            };
+            if (tile < total) {
+                slice();
+                ks = ks0;
+                setup();
+                decompose();
+                advance(pid + 2 * lane);
+            }
+            int it = pid + 2 * lane;
+            int ps = it;                 // stage of `it` (S2 divides nst: stepped by S2)
+            uint32_t eph = 0u;           // parity of that stage's next empty phase
+            bool ok = true;
+            // per issuer: bit s = phase parity of the next use of full[m][s];
+            // per stage this lane fills: the issuer of its last use
+            uint32_t pph0 = 0u, pph1 = 0u, last_owner = 0u, issued = 0u;
+            while (true) {
+                const bool act = ok && tile < total;
+                if (!__any_sync(gmask, act) || __any_sync(gmask, !ok)) break;
+                if (act && !tc::mbar_wait(smem_u32(&sm->empty[ps]), eph ^ 1u, abort_flag, a.err, 1)) ok = false;
+                __syncwarp(gmask);
+                if (act && ok) {
+                    const int s = ps;
+                    const uint32_t fb = smem_u32(&sm->full[owner][s]);
+                    if (owner) pph1 ^= 1u << s;
+                    else pph0 ^= 1u << s;
+                    last_owner = (last_owner & ~(1u << s)) | ((uint32_t)owner << s);
+                    issued |= 1u << s;
+                    tc::mbar_expect_tx(fb, a.bres ? a_bytes : a_bytes + b_bytes);
+                    const int c0 = ch * a.cpc;
+                    const int kcol = (kh * a.k + kw) * a.Cp + c0;   // K column of the weights
+                    uint8_t* stg = sRing + (size_t)s * st_bytes;
+                    tc::tma_load_4d(smem_u32(stg), &P->tmA, c0, x0 + kw, y0 + kh, img, fb);
+                    if (a.bres) {
+                    } else if (CS == 1) {
+                        tc::tma_load_2d(smem_u32(stg + a_bytes), &tmB, kcol, nt * BN, fb);
+                    } else {
+                        constexpr int BR = BN / CS;   // rows of B this CTA loads for the cluster
+                        tc::tma_load_2d_mc(smem_u32(stg + a_bytes + rank * BR * a.chb), &tmB, kcol,
+                                           nt * BN + rank * BR, fb, cmask);
+                    }
+                    it += S2;
+                    ps += S2;
+                    if (ps >= nst) {
+                        ps -= nst;
+                        eph ^= 1u;
+                    }
+                    advance(S2);
+                }
+            }
+            if (a.bres && pid == 0 && lane == 0 &&
+                !tc::mbar_wait(smem_u32(&sm->bres), 0u, abort_flag, a.err, 5)) {
+                const long long t0 = clock64();
+                while (!tc::mbar_try(smem_u32(&sm->bres), 0u) && clock64() - t0 < WAIT_LIMIT) {
                 }
             }
             // drain: every copy issued must have landed before smem goes away.
             // Earlier uses of a stage were consumed before it was refilled, so
             // only the last use of each stage can still be in flight.
-            for (int st = 0; st < STAGES; ++st) {
+            for (int st = 0; st < nst; ++st) {
                 if (!((issued >> st) & 1u)) continue;
                 const int o = (int)((last_owner >> st) & 1u);
                 const uint32_t bar = smem_u32(&sm->full[o][st]);
@@ -403,6 +487,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             int it = 0, tcount = 0;
             uint32_t fph = 0u;   // bit s = phase parity of this issuer's next use of stage s
             bool ok = true;
+            if (a.bres) {
+                ok = tc::mbar_wait(smem_u32(&sm->bres), 0u, abort_flag, a.err, 6);
+                tc::fence_after();
+            }
             for (int tile = worker; tile < total && ok; tile += nworkers, ++tcount) {
                 const int z = a.ksplit > 1 ? tile % a.ksplit : 0;
                 const int ks0 = nk * z / a.ksplit, ks1 = nk * (z + 1) / a.ksplit;
@@ -415,8 +503,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 if (!tc::mbar_wait(smem_u32(&sm->acce[b]), aph ^ 1u, abort_flag, a.err, 2)) break;
                 tc::fence_after();
                 const uint32_t dtm = tmem_base + (uint32_t)(b * BN);
+                int ms = it % nst;   // stage of this tile's first K step
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
-                    const int s = it % STAGES;
+                    const int s = ms;
+                    if (++ms == nst) ms = 0;
                     const uint32_t ph = (fph >> s) & 1u;
                     if (!tc::mbar_wait(smem_u32(&sm->full[mid][s]), ph, abort_flag, a.err, 3)) {
                         ok = false;
@@ -424,8 +514,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     }
                     fph ^= 1u << s;
                     tc::fence_after();
-                    const uint64_t ad = tc::smem_desc(smem_u32(sA + s * A_BYTES), a.chb);
-                    const uint64_t bd = tc::smem_desc(smem_u32(sB + s * B_BYTES), a.chb);
+                    uint8_t* stg = sRing + (size_t)s * st_bytes;
+                    const uint64_t ad = tc::smem_desc(smem_u32(stg), a.chb);
+                    const uint64_t bd =
+                        tc::smem_desc(smem_u32(a.bres ? sBres + (size_t)ks * b_bytes : stg + a_bytes), a.chb);
                     const int nmma = a.chb / 32;   // 32 bytes of K per MMA
                     for (int j = 0; j < nmma; ++j)
                         tc::mma<DT>(dtm, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc,
@@ -443,17 +535,30 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         }
     } else {
         // ------------------------------------------------ epilogue (warps 2..9)
-        // Two warpgroups, one per TMEM accumulator buffer: warpgroup g takes
-        // the tiles whose buffer is g (every other tile) and all their
-        // columns, so both groups stay busy even when a layer has only a few
-        // live output channels.  Each SM sub-partition runs one warp of each.
+        // Two warpgroups: warpgroup g drains the tiles of MMA issuer g (every
+        // other tile), all their columns, so both groups stay busy even when a
+        // layer has only a few live output channels.  Each SM sub-partition
+        // runs one warp of each.
         const int q = warp & 3;                 // TMEM lane quarter of this warp
-        const int grp = (warp - 2) >> 2;        // warpgroup = accumulator buffer
+        const int grp = (warp - 2) >> 2;        // warpgroup = MMA issuer whose tiles it drains
         constexpr int half = 0;
         constexpr int HC = BN;                  // columns per warp
         const int row = q * 32 + lane;          // pixel index in the tile
         const int py = row / a.TW, px = row % a.TW;
         const bool pool = a.ep.pool == POOL_S2;
+        // bias / alpha of the launch's columns into shared memory once (they are
+        // padded with zeros to the weight rows, which cover every N tile)
+        const int ncol_all = a.n_tiles * BN;
+        const bool epi_smem = ncol_all <= kEpiCols;
+        if (epi_smem) {
+            for (int i = threadIdx.x - 64; i < ncol_all; i += 256) {
+                s_bias[i] = a.ep.bias[i];
+                if (a.ep.alpha) s_alpha[i] = a.ep.alpha[i];
+            }
+            asm volatile("bar.sync 1, 256;" ::: "memory");   // the 8 epilogue warps
+        }
+        const float* e_bias = epi_smem ? s_bias : a.ep.bias;
+        const float* e_alpha = epi_smem ? s_alpha : a.ep.alpha;
         const int ymask = a.TW == 16 ? 16 : 8;  // lane distance of the pixel below (pool tiles)
         // columns at or beyond `live` are padding nobody reads: skipped
         const int live = a.ep.out_layout == LAYOUT_NCHW ? a.ep.cout : max(a.ep.out_cs, a.ep.cout);
@@ -535,7 +640,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     float bb[32];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        const float4 t = __ldg(reinterpret_cast<const float4*>(a.ep.bias + o0) + j);
+                        const float4 t = reinterpret_cast<const float4*>(e_bias + o0)[j];
                         bb[4 * j] = t.x;
                         bb[4 * j + 1] = t.y;
                         bb[4 * j + 2] = t.z;
@@ -549,7 +654,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     if (a.ep.alpha) {
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            const float4 t = __ldg(reinterpret_cast<const float4*>(a.ep.alpha + o0) + j);
+                            const float4 t = reinterpret_cast<const float4*>(e_alpha + o0)[j];
                             v[4 * j] = fmaf(v[4 * j], t.x, bb[4 * j]);
                             v[4 * j + 1] = fmaf(v[4 * j + 1], t.y, bb[4 * j + 1]);
                             v[4 * j + 2] = fmaf(v[4 * j + 2], t.z, bb[4 * j + 2]);
@@ -712,14 +817,49 @@ cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+constexpr size_t kSmemLimit = 232448;   // opt-in dynamic shared memory per block (227 KB)
+
+static size_t tc_ctrl_bytes() { return ((sizeof(tc::Smem) + 15) & ~(size_t)15) + 2 * tc::kEpiCols * sizeof(float); }
+static size_t tc_avail() { return kSmemLimit - 1024 - tc_ctrl_bytes(); }
+
+// Ring geometry: as many stages of (A box + B box, or A only with resident
+// weights) as fit beside the resident weights and the control block.
+static bool tc_geometry(int BN, int chb, int bres, int nk, TcArgs* g) {
+    const size_t a_bytes = 128 * (size_t)chb, b_bytes = (size_t)BN * chb;
+    const size_t st = a_bytes + (bres ? 0 : b_bytes);
+    const size_t bres_bytes = bres ? (size_t)nk * b_bytes : 0;
+    if (tc_avail() < bres_bytes + 2 * st) return false;
+    int nst = (int)std::min<size_t>(tc::kMaxStages, (tc_avail() - bres_bytes) / st) & ~1;
+    // producer lanes: four per warp on deep rings (stage count cut to a
+    // multiple of eight).  The lanes of a warp issue in lockstep, so on a
+    // shallow ring one lane per warp keeps stages refilling one by one.
+    int plane = 1;
+    if (nst >= 16) {
+        plane = 4;
+        nst -= nst % 8;
+    }
+    g->plane = plane;
+    g->nst = nst;
+    g->st_bytes = (int)st;
+    g->bres_off = (int)(nst * st);
+    g->ctrl_off = (int)(nst * st + bres_bytes);
+    return true;
+}
+
+bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb) {
+    // resident weights must leave room for at least 8 A-only stages
+    return n_tiles == 1 && ksplit == 1 && (size_t)nk * BN * chb + 8 * 128 * (size_t)chb <= tc_avail();
+}
+
 template <int BN, int DT, int CS>
-static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a, int workers, cudaStream_t st) {
-    constexpr int STAGES = BN == 256 ? 4 : BN == 128 ? 6 : 8;
-    const size_t smem = 1024 + (size_t)STAGES * (tc::A_BYTES + BN * 128) + sizeof(tc::Smem);
-    auto kern = conv_tc_kernel<BN, DT, STAGES, CS>;
+static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int workers, cudaStream_t st) {
+    TcArgs a = a0;
+    if (!tc_geometry(BN, a.chb, a.bres, a.k * a.k * a.chunks, &a)) return cudaErrorInvalidValue;
+    const size_t smem = 1024 + (size_t)a.ctrl_off + tc_ctrl_bytes();
+    auto kern = conv_tc_kernel<BN, DT, CS>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
         if (e != cudaSuccess) return e;
         attr = true;
     }

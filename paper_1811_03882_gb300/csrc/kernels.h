@@ -109,6 +109,11 @@ struct TcArgs {
     void* y_override;  // if not null, output base for every problem
     int ksplit;        // K split factor (tiles x ksplit work items)
     float* ws;         // ksplit > 1: raw sums [ksplit][m_tiles*128][n_tiles*BN]
+    int bres;          // 1: the whole weight slice stays in shared memory (tc_b_resident)
+    // shared-memory geometry, filled by conv_tc_launch: ring stages, stage
+    // bytes, resident-weight offset, control-block offset
+    int nst, st_bytes, bres_off, ctrl_off;
+    int plane;    // producer lanes per producer warp (2 * plane divides nst)
     Epilogue ep;
     int* err;     // bounded-wait failure code (0 = none)
 };
@@ -135,6 +140,10 @@ cudaError_t maxpool_s1_grouped(const PoolJob* jobs, int njobs, long long total, 
                                cudaStream_t st);
 
 int tc_chunk_bytes(int Cp, int dt);
+// Whether a launch keeps all of its weights resident in shared memory: one
+// N tile, no K split, and nk boxes of BN x chunk bytes fit in the B ring.
+// Such launches run without clusters (cs = 1).
+bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb);
 cudaError_t tc_encode_act(CUtensorMap* tm, const void* base, int dt, int n, int H, int W, int Cp, int TW,
                           int TH);
 cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, int KK, int Cp, int BN);

@@ -421,12 +421,14 @@ void dn::tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, i
 // Cluster size and persistent worker count of a tensor-core launch: BN >=
 // 128 runs on 2-CTA clusters that share the weight box (multicast), unless
 // NET_TC_CLUSTER=1 asks for single CTAs.
-void dn::tc_workers(int m_tiles, int n_tiles, int ks, int BN, int num_sms, int* cs, int* workers) {
+void dn::tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int num_sms, int* cs, int* workers,
+                    int* bres) {
     static const int forced = [] {
         const char* e = getenv("NET_TC_CLUSTER");
         return e ? atoi(e) : 0;
     }();
-    *cs = (BN >= 128 && m_tiles >= 2 && forced != 1) ? 2 : 1;
+    *bres = tc_b_resident(BN, n_tiles, ks, nk, chb) ? 1 : 0;
+    *cs = (!*bres && BN >= 128 && m_tiles >= 2 && forced != 1) ? 2 : 1;
     const int items = cdiv(m_tiles, *cs) * n_tiles * ks;
     *workers = std::max(1, std::min(items, num_sms / *cs));
 }
@@ -509,7 +511,8 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             if (r.ksplit > 1)
                 P->ws_bytes = std::max(P->ws_bytes, (size_t)r.ksplit * r.m_tiles * 128 * r.n_tiles * r.BN *
                                                         sizeof(float));
-            tc_workers(r.m_tiles, r.n_tiles, r.ksplit, r.BN, n->num_sms, &r.cs, &r.grid);
+            tc_workers(r.m_tiles, r.n_tiles, r.ksplit, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, &r.cs,
+                       &r.grid, &r.bres);
             (void)tiles;
             ConvProblem hp;
             std::memset(&hp, 0, sizeof hp);
@@ -630,6 +633,7 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.y_override = y;
                 a.ksplit = r.ksplit;
                 a.ws = n->ws;
+                a.bres = r.bres;
                 a.ep = ep;
                 a.err = n->err_dev;
                 e = conv_tc_launch(L.tmB[tmb_index(r.BN, r.cs)], a, r.BN, L.in_dt, r.grid, r.cs, st);

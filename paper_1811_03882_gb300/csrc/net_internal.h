@@ -58,6 +58,7 @@ struct LayerRun {
     int m_tiles = 0, n_tiles = 0, grid = 0;
     int cs = 1;                    // TC cluster size (grid = workers * cs CTAs)
     int ksplit = 1;                // split-K factor (partial sums in the workspace)
+    int bres = 0;                  // TC: weights resident in shared memory
     int sbn = 64, sth = 8, stw = 16; // CUDA-core tile
     ConvProblem* d_prob = nullptr; // TC: device problem table (one entry)
 };
@@ -72,7 +73,10 @@ struct Plan {
 // one warp: TW = 8 or 16).
 void tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, int* TW, int* TH, int* BN);
 void tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks = 16);
-void tc_workers(int m_tiles, int n_tiles, int ks, int BN, int num_sms, int* cs, int* workers);
+// Cluster size, persistent worker count and resident-weight mode of a
+// tensor-core launch (nk K steps of chb bytes per tile).
+void tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int num_sms, int* cs, int* workers,
+                int* bres);
 int tmb_index(int BN, int cs);
 
 struct UnevenState;

@@ -151,7 +151,8 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
         // grouped launches do not split K; pick the N tile for ks = 1
         tc_choose_split(mt, ncols, nk, n->num_sms, &r.BN, &ks_unused, 1);
         r.n_tiles = cdiv(ncols, r.BN);
-        tc_workers(r.m_tiles, r.n_tiles, 1, r.BN, n->num_sms, &r.cs, &r.grid);
+        tc_workers(r.m_tiles, r.n_tiles, 1, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, &r.cs, &r.grid,
+                   &r.bres);
         cudaError_t e = cudaMalloc(&r.d_prob, sizeof(ConvProblem) * cnt);
         if (e == cudaSuccess) e = cudaMemcpy(r.d_prob, probs.data(), sizeof(ConvProblem) * cnt, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(NET_E_CUDA, "layer %d problem table: %s", l, cudaGetErrorString(e));
@@ -203,6 +204,7 @@ static net_status enqueue_uplan(net* n, UPlan* P, int cnt, int* kernels) {
         a.y_override = nullptr;
         a.ksplit = 1;
         a.ws = nullptr;
+        a.bres = r.bres;
         a.err = n->err_dev;
         a.ep.bias = L.bias;
         a.ep.alpha = L.in_dt == DT_FP8 ? L.alpha : nullptr;

@@ -350,7 +350,7 @@ static net_status enqueue_step(net* n, ServeState* S, StepSlot& sl) {
             a.ep = ep;
             a.err = n->err_dev;
             P.BN = BN;
-            tc_workers(mt, a.n_tiles, 1, BN, n->num_sms, &P.cs, &P.workers);
+            tc_workers(mt, a.n_tiles, 1, BN, nk, a.chb, n->num_sms, &P.cs, &P.workers, &a.bres);
             ntab += na;
         }
         if (L.d.pool == NET_POOL_2X2S1_SAME && !last) {
