@@ -347,7 +347,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             // nworkers), K step ks of that tile's slice [ks0, ks1), and `it`
             int t = 0, tile = worker, ks0 = 0, ks1 = 0, ks = 0;
             int ch = 0, kw = 0, kh = 0;   // chunk, tap column, tap row of ks
-            int owner = 0, nt = 0, img = 0, x0 = 0, y0 = 0;
+            int towner = 0, nt = 0, img = 0, x0 = 0, y0 = 0;
             const ConvProblem* P = P1;
             auto slice = [&] {
                 const int z = a.ksplit > 1 ? tile % a.ksplit : 0;
@@ -359,7 +359,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 const int mq = mn / a.n_tiles;
                 const int mt = mq * CS + rank;
                 nt = mn - mq * a.n_tiles;
-                owner = t & 1;
+                towner = t & 1;
                 if (!P1) {
                     P = a.probs + tc::find_problem(a.probs, a.nprob, mt);
                     tiles_x = P->tiles_x;
@@ -426,6 +426,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 __syncwarp(gmask);
                 if (act && ok) {
                     const int s = ps;
+                    // the issuer that consumes this K step: the tile's, or in
+                    // K-alternating mode the K step's parity within the tile
+                    const int owner = a.kalt ? ((ks - ks0) & 1) : towner;
                     const uint32_t fb = smem_u32(&sm->full[owner][s]);
                     if (owner) pph1 ^= 1u << s;
                     else pph0 ^= 1u << s;
@@ -480,7 +483,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         // One thread pays ~150 cycles to issue each tcgen05 instruction, more
         // than a small MMA keeps the tensor pipe busy: two issuer warps take
         // alternate tiles (and so alternate accumulator buffers) and their
-        // issue latencies overlap.
+        // issue latencies overlap.  When a CTA has a single work item they
+        // take alternate K steps of it instead (K-alternating mode), each into
+        // its own accumulator of the tile's pair; the epilogue adds the two.
         const int mid = warp == 1 ? 0 : 1;
         if (lane == 0) {
             const uint32_t idesc = tc::instr_desc<DT>(BN);
@@ -494,19 +499,23 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             for (int tile = worker; tile < total && ok; tile += nworkers, ++tcount) {
                 const int z = a.ksplit > 1 ? tile % a.ksplit : 0;
                 const int ks0 = nk * z / a.ksplit, ks1 = nk * (z + 1) / a.ksplit;
-                if ((tcount & 1) != mid) {   // the other issuer's tile: its stages are skipped
+                if (!a.kalt && (tcount & 1) != mid) {   // the other issuer's tile: its stages are skipped
                     it += ks1 - ks0;
                     continue;
                 }
-                const int b = tcount % NBUF;
-                const uint32_t aph = (uint32_t)(tcount / NBUF) & 1u;
+                const int nslot = a.kalt ? NBUF / 2 : NBUF;
+                const int slot = tcount % nslot;
+                const int b = a.kalt ? 2 * slot + mid : slot;
+                const uint32_t aph = (uint32_t)(tcount / nslot) & 1u;
                 if (!tc::mbar_wait(smem_u32(&sm->acce[b]), aph ^ 1u, abort_flag, a.err, 2)) break;
                 tc::fence_after();
                 const uint32_t dtm = tmem_base + (uint32_t)(b * BN);
                 int ms = it % nst;   // stage of this tile's first K step
+                bool first = true;   // the issuer's first K step of the tile overwrites its accumulator
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
                     const int s = ms;
                     if (++ms == nst) ms = 0;
+                    if (a.kalt && ((ks - ks0) & 1) != mid) continue;   // the other issuer's K step
                     const uint32_t ph = (fph >> s) & 1u;
                     if (!tc::mbar_wait(smem_u32(&sm->full[mid][s]), ph, abort_flag, a.err, 3)) {
                         ok = false;
@@ -521,7 +530,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     const int nmma = a.chb / 32;   // 32 bytes of K per MMA
                     for (int j = 0; j < nmma; ++j)
                         tc::mma<DT>(dtm, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc,
-                                    (ks != ks0 || j != 0) ? 1u : 0u);
+                                    (!first || j != 0) ? 1u : 0u);
+                    first = false;
                     if (CS == 1) tc::mma_commit(smem_u32(&sm->empty[s]));
                     else tc::mma_commit_mc(smem_u32(&sm->empty[s]), cmask);   // frees the stage in every CTA
                 }
@@ -567,9 +577,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         int tcount = 0;
         for (int tile = worker; tile < total; tile += nworkers, ++tcount) {
             if ((tcount & 1) != grp) continue;
-            const int b = tcount % NBUF;
-            const uint32_t aph = (uint32_t)(tcount / NBUF) & 1u;
+            // the tile's accumulator (or pair of them in K-alternating mode)
+            const int nslot = a.kalt ? NBUF / 2 : NBUF;
+            const int slot = tcount % nslot;
+            const int b = a.kalt ? 2 * slot : slot;
+            const uint32_t aph = (uint32_t)(tcount / nslot) & 1u;
             if (!tc::mbar_wait(smem_u32(&sm->accf[b]), aph, abort_flag, a.err, 4)) break;
+            if (a.kalt && !tc::mbar_wait(smem_u32(&sm->accf[b + 1]), aph, abort_flag, a.err, 4)) break;
             tc::fence_after();
             const int z = a.ksplit > 1 ? tile % a.ksplit : 0;
             const int mn = a.ksplit > 1 ? tile / a.ksplit : tile;
@@ -580,17 +594,34 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 // zero-filled operands; nothing to store
                 tc::fence_before();
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(smem_u32(&sm->acce[b]));
+                if (lane == 0) {
+                    tc::mbar_arrive(smem_u32(&sm->acce[b]));
+                    if (a.kalt) tc::mbar_arrive(smem_u32(&sm->acce[b + 1]));
+                }
                 continue;
             }
             const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * HC);
             // the buffer goes back to the MMA issuer right after its last live
             // column is in registers; the math and stores of that chunk follow
+            // K-alternating mode: add the second accumulator (odd K steps),
+            // 16 columns at a time to keep registers down
+            auto add_pair = [&](uint32_t taddr, float* v) {
+                float u[16];
+                tc::tmem_ld16(taddr, u);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] += u[j];
+                tc::tmem_ld16(taddr + 16u, u);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[16 + j] += u[j];
+            };
             bool released = false;
             auto release = [&] {
                 tc::fence_before();
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(smem_u32(&sm->acce[b]));
+                if (lane == 0) {
+                    tc::mbar_arrive(smem_u32(&sm->acce[b]));
+                    if (a.kalt) tc::mbar_arrive(smem_u32(&sm->acce[b + 1]));
+                }
                 released = true;
             };
             if (a.ksplit > 1) {
@@ -603,6 +634,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     float v[32];
                     __syncwarp();
                     tc::tmem_ld32(trow + (uint32_t)c0, v);
+                    if (a.kalt) add_pair(trow + (uint32_t)(BN + c0), v);
                     if (c0 + 32 >= HC || nt * BN + half * HC + c0 + 32 >= live) release();
 #pragma unroll
                     for (int j = 0; j < 32; j += 4)
@@ -649,6 +681,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     float v[32];
                     __syncwarp();
                     tc::tmem_ld32(trow + (uint32_t)c0, v);
+                    if (a.kalt) add_pair(trow + (uint32_t)(BN + c0), v);
                     if (c0 + 32 >= HC || o0 + 32 >= live) release();
                     // warp-uniform branches: each variant is one straight-line loop
                     if (a.ep.alpha) {

@@ -114,6 +114,8 @@ struct TcArgs {
     // bytes, resident-weight offset, control-block offset
     int nst, st_bytes, bres_off, ctrl_off;
     int plane;    // producer lanes per producer warp (2 * plane divides nst)
+    int kalt;     // 1: the two MMA issuers take alternate K steps of each tile
+                  //    (needs at least two K steps per work item)
     Epilogue ep;
     int* err;     // bounded-wait failure code (0 = none)
 };

@@ -513,6 +513,18 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
                                                         sizeof(float));
             tc_workers(r.m_tiles, r.n_tiles, r.ksplit, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, &r.cs,
                        &r.grid, &r.bres);
+            {
+                // one work item per CTA (or cluster): the two MMA issuers share
+                // each tile's K steps instead of idling one of them.  Fixed-batch
+                // plans only: grouped launches keep one summation order for a
+                // frame whatever else is in the batch.
+                static const bool kalt_on = [] {
+                    const char* e = getenv("NET_TC_KALT");
+                    return !(e && atoi(e) == 0);
+                }();
+                const int items = cdiv(r.m_tiles, r.cs) * r.n_tiles * r.ksplit;
+                r.kalt = (kalt_on && items <= r.grid && nk / r.ksplit >= 2) ? 1 : 0;
+            }
             (void)tiles;
             ConvProblem hp;
             std::memset(&hp, 0, sizeof hp);
@@ -634,6 +646,7 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.ksplit = r.ksplit;
                 a.ws = n->ws;
                 a.bres = r.bres;
+                a.kalt = r.kalt;
                 a.ep = ep;
                 a.err = n->err_dev;
                 e = conv_tc_launch(L.tmB[tmb_index(r.BN, r.cs)], a, r.BN, L.in_dt, r.grid, r.cs, st);

@@ -59,6 +59,7 @@ struct LayerRun {
     int cs = 1;                    // TC cluster size (grid = workers * cs CTAs)
     int ksplit = 1;                // split-K factor (partial sums in the workspace)
     int bres = 0;                  // TC: weights resident in shared memory
+    int kalt = 0;                  // TC: both MMA issuers on each tile (one work item per CTA)
     int sbn = 64, sth = 8, stw = 16; // CUDA-core tile
     ConvProblem* d_prob = nullptr; // TC: device problem table (one entry)
 };
