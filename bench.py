@@ -40,9 +40,11 @@ WORKLOADS = {
 SERVE_RATES = (200.0, 1000.0, 4000.0)
 DEFAULT = "19conv-448-b8-bf16"
 
-# ncu DRAM traffic per launch of the dominant kernel (read + write bytes),
-# from the capture summarised under profiles/; None until captured.
-TRAFFIC = {}
+# ncu DRAM traffic per launch of the dominant kernel family (read + write
+# bytes, averaged over the family's launches in one forward pass of the
+# default workload), from the capture summarised in
+# profiles/conv_tc_19conv_448_b8_bf16.md; None where not captured.
+TRAFFIC = {"19conv-448-b8-bf16": {"tc_bf16": 288.13e6 / 19}}
 
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 
@@ -394,7 +396,7 @@ def roofline(W, layer_ms, precs):
         bound = "tensor"
         pnote = ("bf16 sustained, %s" % pk_kind) + (" x 2 (fp8/bf16 nominal ratio)" if dom == "tc_fp8" else "")
     return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": TRAFFIC.get(dom), "kernel": "conv_%s (%d layers)" % (dom, len(sel)),
+            "traffic": TRAFFIC.get(W.name, {}).get(dom), "kernel": "conv_%s (%d layers)" % (dom, len(sel)),
             "peak_source": pnote, "launches_per_step": len(sel)}
 
 
