@@ -278,6 +278,7 @@ class Workload:
     """Frames, weights and step functions of one bench workload."""
 
     def __init__(self, torch, binding, dev, wl, prec, stream):
+        self.name = wl
         netname, batch, side, _, seed = WORKLOADS[wl]
         self.spec = spec = synth.NETS[netname]()
         self.batch, self.side, self.prec = batch, side, prec
