@@ -418,9 +418,9 @@ void dn::tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, i
 }
 
 // Picks BN and the split-K factor together with the cost model above.
-// Cluster size and persistent worker count of a tensor-core launch: BN >=
-// 128 runs on 2-CTA clusters that share the weight box (multicast), unless
-// NET_TC_CLUSTER=1 asks for single CTAs.
+// Cluster size and persistent worker count of a tensor-core launch: single
+// CTAs, or with NET_TC_CLUSTER=2 2-CTA clusters for BN >= 128 that share the
+// weight box (multicast).
 void dn::tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int num_sms, int* cs, int* workers,
                     int* bres) {
     static const int forced = [] {
@@ -428,7 +428,10 @@ void dn::tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, i
         return e ? atoi(e) : 0;
     }();
     *bres = tc_b_resident(BN, n_tiles, ks, nk, chb) ? 1 : 0;
-    *cs = (!*bres && BN >= 128 && m_tiles >= 2 && forced != 1) ? 2 : 1;
+    // 2-CTA clusters sharing the weight box only on request: the shared empty
+    // barriers couple the pair's rings and, measured, cost more than the
+    // halved L2 reads of B save
+    *cs = (!*bres && BN >= 128 && m_tiles >= 2 && forced == 2) ? 2 : 1;
     const int items = cdiv(m_tiles, *cs) * n_tiles * ks;
     *workers = std::max(1, std::min(items, num_sms / *cs));
 }
