@@ -43,6 +43,7 @@ constexpr int THREADS = 384;   // producer, MMA issuer, 8 epilogue warps, second
 constexpr int NUM_WARPS = THREADS / 32;
 constexpr int kMaxStages = 32;                // ring stages (bit masks below are 32 bits)
 constexpr int kEpiCols = 1024;                // bias / alpha columns kept in shared memory
+constexpr int kRawHalo = 3 * 18 * 10;         // raw first layer: 3 channels x (16+2) x (8+2) of a 16 x 8 tile
 constexpr long long WAIT_LIMIT = 4000000000LL;  // clock64 cycles (~2 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -260,6 +261,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     // epilogue copies of bias / alpha (launches with at most kEpiCols columns)
     float* s_bias = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(sm) + ((sizeof(Smem) + 15) & ~(size_t)15));
     float* s_alpha = s_bias + kEpiCols;
+    float* s_raw = s_alpha + kEpiCols;   // raw mode: one input-halo staging area per producer warp
 
     pdl_trigger();   // the next kernel may start its prologue as SMs free up
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -333,7 +335,113 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             }
         }
         __syncwarp();
-        if (lane < G) {
+        if (a.raw) {
+            // ---- software im2col of the first layer: this warp fills the A
+            // tiles of its K steps (one per tile, every other tile) from the
+            // raw frames; lane l builds pixels l, l+32, l+64, l+96 of the tile.
+            // The smem image is what a SWIZZLE_64B TMA box would write: row r
+            // at r*64 bytes, 16-byte unit u of the row stored at unit
+            // u ^ ((r >> 1) & 3).
+            const ConvProblem* P = a.probs;
+            const int H = P->H, W = P->W;
+            const int tiles_x = P->tiles_x, tiles_y = P->tiles_y;
+            // the halo of a 16 x 8 tile, three channels: 3 x 10 x 18 floats,
+            // element e -> (c, hy, hx); lane l holds elements l + 32k
+            constexpr int HW = 18, HH = 10, HN = 3 * HH * HW, PER = (HN + 31) / 32;
+            float* hal = s_raw + pid * kRawHalo;
+            // halos of this warp's next two tiles, in flight while the current
+            // tile is built (the frames come from DRAM: ~thousands of cycles)
+            float hA[PER], hB[PER];
+            auto load_halo = [&](float (&R)[PER], int tile) {
+                if (tile >= total) return;
+                const int txy = tile / tiles_x;
+                const int tx = tile - txy * tiles_x;
+                const int img = txy / tiles_y;
+                const int ty = txy - img * tiles_y;
+                const int y0 = ty * 8 - 1, x0 = tx * 16 - 1;
+                const float* X = a.x_raw + (size_t)img * 3 * H * W;
+#pragma unroll
+                for (int k = 0; k < PER; ++k) {
+                    const int e = lane + 32 * k;
+                    const int c = e / (HH * HW), rem = e - c * (HH * HW);
+                    const int hy = rem / HW, hx = rem - hy * HW;
+                    const int yy = y0 + hy, xx = x0 + hx;
+                    R[k] = (e < HN && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                               ? __ldg(X + ((size_t)c * H + yy) * W + xx)
+                               : 0.f;
+                }
+            };
+            int ps = pid;
+            uint32_t eph = 0u;
+            bool ok = true;
+            int t = pid, tile = worker + pid * nworkers;
+            const int step2 = 2 * nworkers;   // this warp's tiles: every other tile of the CTA
+            load_halo(hA, tile);
+            load_halo(hB, tile + step2);
+            // one tile: stage its halo (R), refill R with the tile two ahead,
+            // build the A tile, hand it to MMA issuer t & 1
+            auto one = [&](float (&R)[PER]) -> bool {
+                if (tile >= total || !ok) return false;
+                __syncwarp();   // the previous tile's reads of the staging area are done
+#pragma unroll
+                for (int k = 0; k < PER; ++k)
+                    if (lane + 32 * k < HN) hal[lane + 32 * k] = R[k];
+                __syncwarp();
+                load_halo(R, tile + 2 * step2);
+                if (!tc::mbar_wait(smem_u32(&sm->empty[ps]), eph ^ 1u, abort_flag, a.err, 1)) {
+                    ok = false;
+                    return false;
+                }
+                uint8_t* stg = sRing + (size_t)ps * st_bytes;
+#pragma unroll 2
+                for (int i = 0; i < 4; ++i) {
+                    const int r = lane + 32 * i;
+                    const int py = r >> 4, px = r & 15;
+                    // element q = (kh*3 + kw)*3 + c (three channels), zero from 27 on
+                    float v[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        v[q] = 0.f;
+                        if (q < 27) {
+                            const int kh = q / 9, kw = (q / 3) % 3, c = q % 3;
+                            v[q] = hal[(c * HH + py + kh) * HW + px + kw];
+                        }
+                    }
+                    uint8_t* row = stg + r * 64;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        uint32_t w4[4];
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * u + 2 * h], v[8 * u + 2 * h + 1]);
+                            w4[h] = *reinterpret_cast<uint32_t*>(&b2);
+                        }
+                        *reinterpret_cast<uint4*>(row + ((u ^ ((r >> 1) & 3)) << 4)) =
+                            make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                    }
+                }
+                // generic-proxy writes made visible to the tensor core's async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(smem_u32(&sm->full[t & 1][ps]));
+                ps += 2;
+                if (ps >= nst) {
+                    ps -= nst;
+                    eph ^= 1u;
+                }
+                t += 2;
+                tile += step2;
+                return true;
+            };
+            while (one(hA) && one(hB)) {
+            }
+            if (a.bres && pid == 0 && lane == 0 &&
+                !tc::mbar_wait(smem_u32(&sm->bres), 0u, abort_flag, a.err, 5)) {
+                const long long t0 = clock64();
+                while (!tc::mbar_try(smem_u32(&sm->bres), 0u) && clock64() - t0 < WAIT_LIMIT) {
+                }
+            }
+        } else if (lane < G) {
             const unsigned gmask = (1u << G) - 1u;
             // a single-problem launch keeps the problem's fields in registers
             const ConvProblem* P1 = a.nprob == 1 ? a.probs : nullptr;
@@ -852,7 +960,9 @@ cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, 
 
 constexpr size_t kSmemLimit = 232448;   // opt-in dynamic shared memory per block (227 KB)
 
-static size_t tc_ctrl_bytes() { return ((sizeof(tc::Smem) + 15) & ~(size_t)15) + 2 * tc::kEpiCols * sizeof(float); }
+static size_t tc_ctrl_bytes() {
+    return ((sizeof(tc::Smem) + 15) & ~(size_t)15) + (2 * tc::kEpiCols + 2 * tc::kRawHalo) * sizeof(float);
+}
 static size_t tc_avail() { return kSmemLimit - 1024 - tc_ctrl_bytes(); }
 
 // Ring geometry: as many stages of (A box + B box, or A only with resident

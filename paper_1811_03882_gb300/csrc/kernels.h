@@ -116,6 +116,13 @@ struct TcArgs {
     int plane;    // producer lanes per producer warp (2 * plane divides nst)
     int kalt;     // 1: the two MMA issuers take alternate K steps of each tile
                   //    (needs at least two K steps per work item)
+    // raw = 1: the first layer's A tile is built by the producer warps from
+    // the NCHW FP32 frames at x_raw (raw_c channels, 3 x 3 taps, im2col order
+    // j = (kh*3 + kw)*raw_c + c over one 32-channel BF16 chunk) instead of
+    // being loaded by TMA from a packed buffer; one problem, one K step,
+    // 16 x 8 tiles, three channels.
+    int raw, raw_c;
+    const float* x_raw;
     Epilogue ep;
     int* err;     // bounded-wait failure code (0 = none)
 };

@@ -592,12 +592,27 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                                                     : cudaEventRecord(ev, st);
     };
     const bool prof = n->prof && !fp32_copy && (int)n->prof_ev.size() == 2 * nl;
-    n->pending = 1;
-    cudaError_t e = (!fp32_copy && n->L[0].im2col_k)
-                        ? pack_frames_im2col(d_in, buf[cur], batch, n->in_c, h, w, in_cs(0), n->L[0].im2col_k,
-                                             in_dt(0), 1.f / in_scale(n->L[0]), st)
-                        : pack_frames(d_in, buf[cur], batch, n->in_c, h, w, in_cs(0), in_dt(0),
-                                      1.f / in_scale(n->L[0]), st);
+    // The first layer builds its im2col tiles from the raw frames inside the
+    // tensor-core kernel (no pack launch, no im2col buffer) when it is a BF16
+    // 3x3 layer over three channels with resident weights in one launch
+    // shape; calibration passes keep the pack, which they measure.
+    static const bool raw_on = [] {
+        const char* v = getenv("NET_RAW_L0");
+        return !(v && atoi(v) == 0);
+    }();
+    const LayerRun* r0 = plan ? &plan->runs[0] : nullptr;
+    const bool raw0 = raw_on && !fp32_copy && !amax && n->L[0].engine == ENG_TC && n->L[0].im2col_k == 3 &&
+                      n->in_c == 3 && n->L[0].in_dt == DT_BF16 && r0 && r0->bres && r0->ksplit == 1 && r0->cs == 1 &&
+                      r0->n_tiles == 1 && tc_chunk_bytes(n->L[0].in_cs, DT_BF16) == 64 && r0->TW == 16 && r0->TH == 8;
+    n->pending = raw0 ? 0 : 1;
+    cudaError_t e = cudaSuccess;
+    if (raw0) {
+    } else if (!fp32_copy && n->L[0].im2col_k) {
+        e = pack_frames_im2col(d_in, buf[cur], batch, n->in_c, h, w, in_cs(0), n->L[0].im2col_k, in_dt(0),
+                               1.f / in_scale(n->L[0]), st);
+    } else {
+        e = pack_frames(d_in, buf[cur], batch, n->in_c, h, w, in_cs(0), in_dt(0), 1.f / in_scale(n->L[0]), st);
+    }
     if (e != cudaSuccess) return fail(NET_E_CUDA, "pack: %s", cudaGetErrorString(e));
     for (int l = 0; l < nl; ++l) {
         const Layer& L = n->L[l];
@@ -650,6 +665,11 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.ws = n->ws;
                 a.bres = r.bres;
                 a.kalt = r.kalt;
+                if (l == 0 && raw0) {
+                    a.raw = 1;
+                    a.raw_c = n->in_c;
+                    a.x_raw = d_in;
+                }
                 a.ep = ep;
                 a.err = n->err_dev;
                 e = conv_tc_launch(L.tmB[tmb_index(r.BN, r.cs)], a, r.BN, L.in_dt, r.grid, r.cs, st);
