@@ -266,7 +266,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     pdl_trigger();   // the next kernel may start its prologue as SMs free up
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int KK = a.k * a.k;
-    const int nk = KK * a.chunks;                 // K steps per tile
+    const int nkb = KK * a.chunks;                // weight boxes (tap, chunk) per tile
+    const int nk = a.tapm ? a.chunks : nkb;       // pipeline steps per tile
     // work items: (group of CS m-tiles, n-tile, K slice); a cluster takes one
     // item at a time and CTA `rank` of it the m-tile group*CS + rank
     const int rank = CS > 1 ? (int)tc::cluster_rank() : 0;
@@ -275,7 +276,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     const int total = m_groups * a.n_tiles * a.ksplit;
     const uint16_t cmask = (uint16_t)((1u << CS) - 1u);
     const int pad = a.k >> 1;
-    const uint32_t a_bytes = 128u * a.chb, b_bytes = (uint32_t)BN * a.chb;
+    // A bytes per stage: one 128-row box, or three (TH + 2)-row boxes (tapm)
+    const uint32_t a_box = a.tapm ? (uint32_t)(a.TH + 2) * a.TW * a.chb : 128u * a.chb;
+    const uint32_t a_bytes = a.tapm ? 3u * a_box : a_box, b_bytes = (uint32_t)BN * a.chb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < nst; ++s) {
@@ -324,9 +327,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             // resident weights: every K step's [BN x chunk] box, once, side by
             // side (the launch has one N tile and no K split)
             const uint32_t rb = smem_u32(&sm->bres);
-            tc::mbar_expect_tx(rb, (uint32_t)nk * b_bytes);
+            tc::mbar_expect_tx(rb, (uint32_t)nkb * b_bytes);
             int ch = 0, tap = 0;
-            for (int ks = 0; ks < nk; ++ks) {
+            for (int ks = 0; ks < nkb; ++ks) {
                 tc::tma_load_2d(smem_u32(sBres + (size_t)ks * b_bytes), &tmB, tap * a.Cp + ch * a.cpc, 0, rb);
                 if (++ch == a.chunks) {
                     ch = 0;
@@ -546,7 +549,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     const int c0 = ch * a.cpc;
                     const int kcol = (kh * a.k + kw) * a.Cp + c0;   // K column of the weights
                     uint8_t* stg = sRing + (size_t)s * st_bytes;
-                    tc::tma_load_4d(smem_u32(stg), &P->tmA, c0, x0 + kw, y0 + kh, img, fb);
+                    if (a.tapm) {   // step = chunk ks of all nine taps: one box per tap column
+                        for (int dx = 0; dx < 3; ++dx)
+                            tc::tma_load_4d(smem_u32(stg + dx * a_box), &P->tmA, ks * a.cpc, x0 + dx, y0, img, fb);
+                    } else {
+                        tc::tma_load_4d(smem_u32(stg), &P->tmA, c0, x0 + kw, y0 + kh, img, fb);
+                    }
                     if (a.bres) {
                     } else if (CS == 1) {
                         tc::tma_load_2d(smem_u32(stg + a_bytes), &tmB, kcol, nt * BN, fb);
@@ -632,14 +640,29 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     fph ^= 1u << s;
                     tc::fence_after();
                     uint8_t* stg = sRing + (size_t)s * st_bytes;
-                    const uint64_t ad = tc::smem_desc(smem_u32(stg), a.chb);
-                    const uint64_t bd =
-                        tc::smem_desc(smem_u32(a.bres ? sBres + (size_t)ks * b_bytes : stg + a_bytes), a.chb);
                     const int nmma = a.chb / 32;   // 32 bytes of K per MMA
-                    for (int j = 0; j < nmma; ++j)
-                        tc::mma<DT>(dtm, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc,
-                                    (!first || j != 0) ? 1u : 0u);
-                    first = false;
+                    if (a.tapm) {
+                        // nine taps of chunk ks: tap (dy, dx) reads box dx from row dy * TW
+                        for (int dx = 0; dx < 3; ++dx)
+                            for (int dy = 0; dy < 3; ++dy) {
+                                const uint64_t ad =
+                                    tc::smem_desc(smem_u32(stg + dx * a_box + dy * a.TW * a.chb), a.chb);
+                                const uint64_t bd = tc::smem_desc(
+                                    smem_u32(sBres + (size_t)((dy * 3 + dx) * a.chunks + ks) * b_bytes), a.chb);
+                                for (int j = 0; j < nmma; ++j)
+                                    tc::mma<DT>(dtm, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc,
+                                                (!first || j != 0) ? 1u : 0u);
+                                first = false;
+                            }
+                    } else {
+                        const uint64_t ad = tc::smem_desc(smem_u32(stg), a.chb);
+                        const uint64_t bd =
+                            tc::smem_desc(smem_u32(a.bres ? sBres + (size_t)ks * b_bytes : stg + a_bytes), a.chb);
+                        for (int j = 0; j < nmma; ++j)
+                            tc::mma<DT>(dtm, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc,
+                                        (!first || j != 0) ? 1u : 0u);
+                        first = false;
+                    }
                     if (CS == 1) tc::mma_commit(smem_u32(&sm->empty[s]));
                     else tc::mma_commit_mc(smem_u32(&sm->empty[s]), cmask);   // frees the stage in every CTA
                 }
@@ -968,7 +991,8 @@ static size_t tc_avail() { return kSmemLimit - 1024 - tc_ctrl_bytes(); }
 // Ring geometry: as many stages of (A box + B box, or A only with resident
 // weights) as fit beside the resident weights and the control block.
 static bool tc_geometry(int BN, int chb, int bres, int nk, TcArgs* g) {
-    const size_t a_bytes = 128 * (size_t)chb, b_bytes = (size_t)BN * chb;
+    const size_t a_bytes = g->tapm ? 3 * (size_t)(g->TH + 2) * g->TW * chb : 128 * (size_t)chb;
+    const size_t b_bytes = (size_t)BN * chb;
     const size_t st = a_bytes + (bres ? 0 : b_bytes);
     const size_t bres_bytes = bres ? (size_t)nk * b_bytes : 0;
     if (tc_avail() < bres_bytes + 2 * st) return false;

@@ -123,6 +123,11 @@ struct TcArgs {
     // 16 x 8 tiles, three channels.
     int raw, raw_c;
     const float* x_raw;
+    // tapm = 1 (3 x 3 layers with resident weights, 16 x 8 or 8 x 16 tiles):
+    // a ring stage is one channel chunk of all nine taps, three TMA boxes of
+    // TH + 2 rows (one per tap column; the activation map's box is TH + 2
+    // rows high), and each tap's A operand starts dy * TW rows into its box.
+    int tapm;
     Epilogue ep;
     int* err;     // bounded-wait failure code (0 = none)
 };

@@ -525,13 +525,25 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
                     const char* e = getenv("NET_TC_KALT");
                     return !(e && atoi(e) == 0);
                 }();
+                // 3x3 layers with resident weights: one ring stage per channel
+                // chunk of all nine taps (three boxes of TH + 2 rows)
+                static const bool tapm_on = [] {
+                    const char* e = getenv("NET_TC_TAPM");
+                    return !(e && atoi(e) == 0);
+                }();
+                r.tapm = (tapm_on && r.bres && L.kx == 3 && r.ksplit == 1 &&
+                          ((r.TW == 16 && r.TH == 8) || (r.TW == 8 && r.TH == 16)))
+                             ? 1
+                             : 0;
+                const int steps = r.tapm ? nk / 9 : nk;   // pipeline steps per tile
                 const int items = cdiv(r.m_tiles, r.cs) * r.n_tiles * r.ksplit;
-                r.kalt = (kalt_on && items <= r.grid && nk / r.ksplit >= 2) ? 1 : 0;
+                r.kalt = (kalt_on && items <= r.grid && steps / r.ksplit >= 2) ? 1 : 0;
             }
             (void)tiles;
             ConvProblem hp;
             std::memset(&hp, 0, sizeof hp);
-            cudaError_t e = tc_encode_act(&hp.tmA, n->act[r.in_buf], L.in_dt, batch, r.H, r.W, L.in_cs, r.TW, r.TH);
+            cudaError_t e = tc_encode_act(&hp.tmA, n->act[r.in_buf], L.in_dt, batch, r.H, r.W, L.in_cs, r.TW,
+                                          r.tapm ? r.TH + 2 : r.TH);
             if (e != cudaSuccess) return fail(NET_E_CUDA, "layer %d: activation tensor map: %s", l, cudaGetErrorString(e));
             hp.x = n->act[r.in_buf];
             hp.y = n->act[r.out_buf];
@@ -665,6 +677,7 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.ws = n->ws;
                 a.bres = r.bres;
                 a.kalt = r.kalt;
+                a.tapm = r.tapm;
                 if (l == 0 && raw0) {
                     a.raw = 1;
                     a.raw_c = n->in_c;

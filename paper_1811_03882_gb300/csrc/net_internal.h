@@ -60,6 +60,7 @@ struct LayerRun {
     int ksplit = 1;                // split-K factor (partial sums in the workspace)
     int bres = 0;                  // TC: weights resident in shared memory
     int kalt = 0;                  // TC: both MMA issuers on each tile (one work item per CTA)
+    int tapm = 0;                  // TC: ring stages of all nine taps (3x3, resident weights)
     int sbn = 64, sth = 8, stw = 16; // CUDA-core tile
     ConvProblem* d_prob = nullptr; // TC: device problem table (one entry)
 };
