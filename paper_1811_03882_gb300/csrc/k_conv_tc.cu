@@ -288,7 +288,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         }
         for (int b = 0; b < NBUF; ++b) {
             tc::mbar_init(smem_u32(&sm->accf[b]), 1);
-            tc::mbar_init(smem_u32(&sm->acce[b]), 4);   // the 4 warps of the warpgroup that drains buffer b
+            // the 4 warps of the warpgroup that drains buffer b; in K-alternating
+            // mode both warpgroups drain every tile (half of its columns each)
+            tc::mbar_init(smem_u32(&sm->acce[b]), a.kalt ? 8 : 4);
         }
         tc::mbar_init(smem_u32(&sm->done), 2);   // one commit from each MMA issuer
         tc::mbar_init(smem_u32(&sm->bres), 1);
@@ -682,8 +684,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         // runs one warp of each.
         const int q = warp & 3;                 // TMEM lane quarter of this warp
         const int grp = (warp - 2) >> 2;        // warpgroup = MMA issuer whose tiles it drains
-        constexpr int half = 0;
-        constexpr int HC = BN;                  // columns per warp
+        // columns of a tile this warp drains: all, or in K-alternating mode
+        // (one tile per CTA) half of them, so the last tile's epilogue, which
+        // nothing overlaps, runs on both warpgroups
+        const int half = a.kalt ? grp : 0;
+        const int HC = a.kalt ? BN / 2 : BN;
         const int row = q * 32 + lane;          // pixel index in the tile
         const int py = row / a.TW, px = row % a.TW;
         const bool pool = a.ep.pool == POOL_S2;
@@ -706,8 +711,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         void* pY = nullptr;
         int pH = 0, pW = 0, pTX = 1, pTY = 1, pBegin = 0;
         int tcount = 0;
+        bool have_p = false;   // problem fields loaded (single-problem launches read them once)
         for (int tile = worker; tile < total; tile += nworkers, ++tcount) {
-            if ((tcount & 1) != grp) continue;
+            if (!a.kalt && (tcount & 1) != grp) continue;
             // the tile's accumulator (or pair of them in K-alternating mode)
             const int nslot = a.kalt ? NBUF / 2 : NBUF;
             const int slot = tcount % nslot;
@@ -773,7 +779,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 }
             } else {
                 // the single-problem case keeps its fields in registers (read once)
-                if (a.nprob > 1 || tcount == grp) {
+                if (a.nprob > 1 || !have_p) {
+                    have_p = true;
                     const ConvProblem& P = a.probs[a.nprob > 1 ? tc::find_problem(a.probs, a.nprob, mt) : 0];
                     pY = P.y;
                     pH = P.H;
