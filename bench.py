@@ -5,8 +5,9 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One step = one forward pass of the whole network over one batch of
 synthetic frames that are already resident in device memory (value), and
-the same through the host API net_forward with pinned host buffers, the
-H2D and D2H copies inside the timed region (e2e).  Under torchrun every
+the same through the host API (net_forward_async over two pinned buffer
+pairs, then net_forward_wait), the H2D and D2H copies of every step inside
+the timed region (e2e).  Under torchrun every
 rank runs its own replica on its own GPU (frames are independent; no
 collective on the data path) and rank 0 prints one JSON line.
 """
@@ -301,6 +302,10 @@ class Workload:
             self.d_out.append(torch.empty((f.shape[0], c, ho, wo), device="cuda"))
             self.h_in.append(torch.from_numpy(f).pin_memory())
             self.h_out.append(torch.empty((f.shape[0], c, ho, wo)).pin_memory())
+        if side:
+            # a second pinned pair: the async host API alternates between two
+            self.h_in.append(self.h_in[0].clone().pin_memory())
+            self.h_out.append(torch.empty_like(self.h_out[0]).pin_memory())
         self.h2d = sum(int(f.nbytes) for f in self.frames)
         self.d2h = sum(int(o.numel() * 4) for o in self.d_out)
         cins = spec.cins()
@@ -318,10 +323,12 @@ class Workload:
         else:
             self.net.forward_uneven(self.d_in, self.sides, self.d_out)
 
-    def step_e2e(self):
+    def step_e2e(self, i=0):
         if self.side:
-            # the host API: one H2D of the batch, the pass, one D2H of the result
-            self.net.forward(self.h_in[0].numpy(), self.h_out[0].numpy())
+            # the host API, stream-ordered: one H2D of the batch, the pass, one
+            # D2H of the result per call; two pinned buffer pairs alternate so
+            # one call's copies overlap the previous call's pass
+            self.net.forward_async(self.h_in[i % 2].numpy(), self.h_out[i % 2].numpy())
         else:
             for a, b in zip(self.d_in, self.h_in):
                 a.copy_(b, non_blocking=True)
@@ -329,6 +336,10 @@ class Workload:
             for a, b in zip(self.h_out, self.d_out):
                 a.copy_(b, non_blocking=True)
             self.stream.synchronize()
+
+    def e2e_done(self):
+        if self.side:
+            self.net.forward_wait()
 
 
 def measure(torch, W, args, flush, barrier, ws, with_clocks=False, dev=0):
@@ -366,12 +377,14 @@ def measure(torch, W, args, flush, barrier, ws, with_clocks=False, dev=0):
         layer_ms += W.net.layer_times()
     layer_ms /= args.steps
     W.net.profile(False)
-    for _ in range(2):
-        W.step_e2e()
+    for i in range(2):
+        W.step_e2e(i)
+    W.e2e_done()
     barrier()
     t0 = time.perf_counter()
     for i in range(args.steps):
-        W.step_e2e()
+        W.step_e2e(i)
+    W.e2e_done()
     barrier()
     e2e_s = max_over_ranks(torch, time.perf_counter() - t0, ws)
     frames_all = W.batch * args.steps * ws

@@ -113,6 +113,23 @@ net_status net_output_shape(const net_t* net, int h, int w, int* c, int* ho, int
 net_status net_forward(net_t* net, const float* in_nchw, int batch, int h, int w,
                        float* out_nchw, size_t out_cap_floats);
 
+/* Asynchronous form of net_forward for a stream of batches: enqueues the
+ * host->device copy of in_nchw (on an upload stream), the forward pass (on
+ * the handle's stream) and the device->host copy into out_nchw (on a
+ * download stream), and returns.  Two device staging slots alternate, so
+ * the copies of one call overlap the pass of the previous one; before a
+ * slot is reused the call waits until that slot's previous work finished.
+ * The caller keeps in_nchw unchanged and out_nchw unread until
+ * net_forward_wait returns (host buffers should be pinned: pageable copies
+ * serialise).  Arguments and errors as net_forward. */
+net_status net_forward_async(net_t* net, const float* in_nchw, int batch, int h, int w,
+                             float* out_nchw, size_t out_cap_floats);
+
+/* Blocks until every net_forward_async call of the handle has finished;
+ * returns the first error of the batch of calls (NET_E_DEVICE_WAIT when a
+ * bounded device-side wait expired). */
+net_status net_forward_wait(net_t* net);
+
 /* Stream-ordered forward pass between device buffers (no host copies, no
  * synchronisation). */
 net_status net_forward_device(net_t* net, const float* d_in, int batch, int h, int w,

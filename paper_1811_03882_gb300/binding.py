@@ -71,6 +71,9 @@ _SIGS = {
                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "net_forward": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                     ctypes.c_void_p, ctypes.c_size_t],
+    "net_forward_async": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_void_p, ctypes.c_size_t],
+    "net_forward_wait": [ctypes.c_void_p],
     "net_forward_device": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                            ctypes.c_void_p],
     "net_forward_trace": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -203,6 +206,15 @@ class Net:
             out = np.empty((n, c, ho, wo), np.float32)
         check(lib().net_forward(self.h, _ptr(x), n, h, w, _ptr(out), out.size))
         return out
+
+    def forward_async(self, x: np.ndarray, out: np.ndarray) -> None:
+        """Enqueues net_forward's work and returns; x must stay unchanged and
+        out unread until forward_wait() (pinned host arrays overlap best)."""
+        n, _, h, w = x.shape
+        check(lib().net_forward_async(self.h, _ptr(x), n, h, w, _ptr(out), out.size))
+
+    def forward_wait(self) -> None:
+        check(lib().net_forward_wait(self.h))
 
     def forward_device(self, d_in, batch, h, w, d_out):
         check(lib().net_forward_device(self.h, _ptr(d_in), batch, h, w, _ptr(d_out)))

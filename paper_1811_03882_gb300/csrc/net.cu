@@ -813,6 +813,112 @@ extern "C" net_status net_forward(net_t* n, const float* in, int batch, int h, i
     return check_device_error(n);
 }
 
+static net_status async_start(net* n) {
+    if (n->async) return NET_OK;
+    std::unique_ptr<net::AsyncState> A(new net::AsyncState());
+    // own staging for both slots: a synchronous net_forward may run between
+    // asynchronous calls without touching their buffers
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMalloc(&A->d_in[k], n->in_stage_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&A->d_out[k], n->out_stage_bytes);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&A->s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&A->s_out, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventCreateWithFlags(&A->ev_in[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&A->ev_comp[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&A->ev_free[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        for (int k = 0; k < 2; ++k) {
+            cudaFree(A->d_in[k]);
+            cudaFree(A->d_out[k]);
+        }
+        if (A->s_in) cudaStreamDestroy(A->s_in);
+        if (A->s_out) cudaStreamDestroy(A->s_out);
+        for (int k = 0; k < 2; ++k) {
+            if (A->ev_in[k]) cudaEventDestroy(A->ev_in[k]);
+            if (A->ev_comp[k]) cudaEventDestroy(A->ev_comp[k]);
+            if (A->ev_free[k]) cudaEventDestroy(A->ev_free[k]);
+        }
+        return fail(NET_E_OOM, "async staging: %s", cudaGetErrorString(e));
+    }
+    n->async = A.release();
+    return NET_OK;
+}
+
+static void async_free(net* n) {
+    net::AsyncState* A = n->async;
+    if (!A) return;
+    cudaStreamSynchronize(A->s_in);
+    cudaStreamSynchronize(n->stream);
+    cudaStreamSynchronize(A->s_out);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(A->d_in[k]);
+        cudaFree(A->d_out[k]);
+    }
+    cudaStreamDestroy(A->s_in);
+    cudaStreamDestroy(A->s_out);
+    for (int k = 0; k < 2; ++k) {
+        cudaEventDestroy(A->ev_in[k]);
+        cudaEventDestroy(A->ev_comp[k]);
+        cudaEventDestroy(A->ev_free[k]);
+    }
+    delete A;
+    n->async = nullptr;
+}
+
+extern "C" net_status net_forward_async(net_t* n, const float* in, int batch, int h, int w, float* out,
+                                        size_t cap) {
+    if (!n || !in || !out) return fail(NET_E_INVAL, "NULL argument");
+    if (!n->weights_loaded) return fail(NET_E_WEIGHTS, "weights not loaded");
+    net_status s = check_shape(n, batch, h, w);
+    if (s != NET_OK) return s;
+    int c, ho, wo;
+    net_output_shape(n, h, w, &c, &ho, &wo);
+    const size_t nout = (size_t)batch * c * ho * wo;
+    if (cap < nout) return fail(NET_E_INVAL, "output capacity %zu < %zu floats", cap, nout);
+    CK(cudaSetDevice(n->device));
+    s = async_start(n);
+    if (s != NET_OK) return s;
+    net::AsyncState* A = n->async;
+    const int k = A->next;
+    A->next ^= 1;
+    // the slot's previous batch: its download done means its pass and upload are too
+    if (A->used[k]) CK(cudaEventSynchronize(A->ev_free[k]));
+    A->used[k] = true;
+    const size_t nin = (size_t)batch * n->in_c * h * w;
+    CK(cudaMemcpyAsync(A->d_in[k], in, nin * sizeof(float), cudaMemcpyHostToDevice, A->s_in));
+    CK(cudaEventRecord(A->ev_in[k], A->s_in));
+    CK(cudaStreamWaitEvent(n->stream, A->ev_in[k], 0));
+    s = run_forward(n, A->d_in[k], batch, h, w, A->d_out[k]);
+    if (s != NET_OK) {
+        if (A->first_err == NET_OK) A->first_err = s;
+        return s;
+    }
+    CK(cudaEventRecord(A->ev_comp[k], n->stream));
+    CK(cudaStreamWaitEvent(A->s_out, A->ev_comp[k], 0));
+    CK(cudaMemcpyAsync(out, A->d_out[k], nout * sizeof(float), cudaMemcpyDeviceToHost, A->s_out));
+    CK(cudaEventRecord(A->ev_free[k], A->s_out));
+    return NET_OK;
+}
+
+extern "C" net_status net_forward_wait(net_t* n) {
+    if (!n) return fail(NET_E_INVAL, "NULL argument");
+    net::AsyncState* A = n->async;
+    if (!A) return NET_OK;
+    CK(cudaSetDevice(n->device));
+    CK(cudaStreamSynchronize(A->s_in));
+    CK(cudaStreamSynchronize(n->stream));
+    CK(cudaStreamSynchronize(A->s_out));
+    net_status s = A->first_err;
+    A->first_err = NET_OK;
+    A->used[0] = A->used[1] = false;
+    if (s != NET_OK) return s;
+    return check_device_error(n);
+}
+
 extern "C" net_status net_forward_trace(net_t* n, const float* d_in, int batch, int h, int w,
                                         float* const* d_layer_out) {
     if (!n || !d_in || !d_layer_out) return fail(NET_E_INVAL, "NULL argument");
@@ -985,6 +1091,7 @@ extern "C" net_status net_free(net_t* n) {
     if (n->err_host) cudaFreeHost(n->err_host);
     cudaFree(n->act[0]);
     cudaFree(n->act[1]);
+    async_free(n);
     cudaFree(n->d_in_stage);
     cudaFree(n->d_out_stage);
     uneven_free(n);

@@ -103,6 +103,18 @@ struct net {
     float* d_in_stage = nullptr;
     float* d_out_stage = nullptr;
     size_t in_stage_bytes = 0, out_stage_bytes = 0;
+    // net_forward_async: two staging slots of its own,
+    // upload and download streams, per slot: upload done, pass done, slot free
+    struct AsyncState {
+        float* d_in[2] = {nullptr, nullptr};
+        float* d_out[2] = {nullptr, nullptr};
+        cudaStream_t s_in = nullptr, s_out = nullptr;
+        cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+        bool used[2] = {false, false};
+        int next = 0;
+        net_status first_err = NET_OK;
+    };
+    AsyncState* async = nullptr;
     std::map<std::tuple<int, int, int, const void*, const void*>, cudaGraphExec_t> graphs;
     bool prof = false;
     std::vector<cudaEvent_t> prof_ev;   // 2 per layer
