@@ -555,6 +555,13 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             hp.tile_begin = 0;
             CK(cudaMalloc(&r.d_prob, sizeof(ConvProblem)));
             CK(cudaMemcpy(r.d_prob, &hp, sizeof hp, cudaMemcpyHostToDevice));
+            static const bool dump = getenv("NET_PLAN_DUMP") != nullptr;   // diagnostics: one line per layer
+            if (dump)
+                fprintf(stderr,
+                        "plan b%d %dx%d layer %d: tile %dx%d BN %d m_tiles %d n_tiles %d ksplit %d cs %d grid %d "
+                        "bres %d kalt %d tapm %d\n",
+                        batch, h, w, l, r.TW, r.TH, r.BN, r.m_tiles, r.n_tiles, r.ksplit, r.cs, r.grid, r.bres, r.kalt,
+                        r.tapm);
         }
         P->runs.push_back(r);
         if (L.d.pool != NET_POOL_2X2S1_SAME) cur ^= 1;
