@@ -426,6 +426,8 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--serve", action="store_true", help="add the serving streams to the line")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--no-tile-search", action="store_true",
+                    help="keep the analytic tile plan (skip the genetic tile-plan search)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = args.workload
@@ -467,9 +469,16 @@ def main():
                 plan, ga = W.net.tune_precision(d_c, 1, cs, cs, max_err=0.05, population=12, generations=8,
                                                 reps=2, seed=3)
                 info = {"plan": plan, "ga": ga}
+        if tune and side and p != "fp32" and not args.no_tile_search:
+            # the genetic tile-plan search on the workload's own batch shape
+            # (setup, outside every timed region)
+            tiles, tr = W.net.tune_tiles(W.d_in[0], batch, side, side, population=12, generations=8, reps=3,
+                                         seed=5)
+            info["tile_plan"] = tiles
+            info["tile_search"] = tr
         return W, info
 
-    W, info = setup(prec, tune=(prec == "fp8"))
+    W, info = setup(prec, tune=True)
     precs = W.net.layer_prec()
     m = measure(torch, W, args, flush, barrier, ws, with_clocks=True, dev=dev)
     roof = roofline(W, m["layer_ms"], precs)
@@ -490,8 +499,12 @@ def main():
         "wall_s_timed": m["wall"],
         "clocks": m["clocks"],
     }
-    if info:
-        line["precision_search"] = info
+    if "plan" in info:
+        line["precision_search"] = {"plan": info["plan"], "ga": info["ga"]}
+    if "tile_plan" in info:
+        # [N tile, split-K] per layer ([0, 0]: CUDA cores), from the genetic search
+        line["config"]["tile_plan"] = info["tile_plan"]
+        line["tile_search"] = info["tile_search"]
     W.net.close()
     if not args.no_compare and side:
         # the same workload on the other paths: FP32 (CUDA cores) and FP8 (GA-tuned plan) or BF16
@@ -502,8 +515,11 @@ def main():
             cmp[p] = {"value": m2["value"], "ms_per_step": m2["ms_per_step"], "conv_tflops": m2["conv_tflops"],
                       "e2e": m2["e2e_fps"], "roofline_frac": roofline(W2, m2["layer_ms"], W2.net.layer_prec())["frac"],
                       "layer_precision": W2.net.layer_prec()}
-            if info2:
-                cmp[p]["precision_search"] = info2
+            if "plan" in info2:
+                cmp[p]["precision_search"] = {"plan": info2["plan"], "ga": info2["ga"]}
+            if "tile_plan" in info2:
+                cmp[p]["tile_plan"] = info2["tile_plan"]
+                cmp[p]["tile_search"] = info2["tile_search"]
             W2.net.close()
         line["compare"] = cmp
     if args.serve and rank == 0:

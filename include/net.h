@@ -211,6 +211,32 @@ typedef struct {
 net_status net_tune_precision(net_t* net, const float* d_frames, int batch, int h, int w,
                               const net_ga_opts* opts, int* layer_prec_out, net_ga_result* result);
 
+/* Tile plan of one tensor-core layer for the fixed-batch passes
+ * (net_forward*): N tile bn in {64, 128, 256} and split-K factor ksplit in
+ * {1, 2, 4, 8, 16}; 0 keeps the analytic choice.  A value the layer cannot take
+ * (bn above its padded output columns, ksplit with fewer than four K steps
+ * per slice) is NET_E_INVAL.  Captured graphs and plans are rebuilt. */
+net_status net_set_layer_tiles(net_t* net, int layer, int bn, int ksplit);
+
+/* The tile plan the fixed-batch path uses for a batch x h x w pass, after
+ * overrides: bn[n] and ksplit[n] per layer (0 for CUDA-core layers). */
+net_status net_plan_tiles(net_t* net, int batch, int h, int w, int* bn, int* ksplit, int n);
+
+/* Genetic search over the tile plan: the same algorithm and options as
+ * net_tune_precision (max_err bounds the deviation from the analytic plan's
+ * output; every plan computes the same sums, only their order differs), one
+ * gene per tensor-core layer whose alphabet is that layer's valid (bn,
+ * ksplit) pairs, mutation drawing another pair; the analytic plan is one of
+ * the initial individuals.  On NET_OK the handle keeps the best plan as
+ * overrides and bn_out / ksplit_out (n_layers entries) hold it. */
+typedef struct {
+    double ms, ms_analytic;          /* best plan / the analytic plan           */
+    int evaluations, memo_hits, changed_layers;
+} net_tile_result;
+
+net_status net_tune_tiles(net_t* net, const float* d_frames, int batch, int h, int w, const net_ga_opts* opts,
+                          int* bn_out, int* ksplit_out, net_tile_result* result);
+
 /* Per-layer timing: with enable != 0 every later forward pass records a
  * CUDA event pair around each layer's conv kernel (on the handle's stream;
  * CUDA-graph replays record them too).  net_layer_times waits for the most

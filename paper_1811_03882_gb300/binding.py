@@ -58,6 +58,11 @@ class net_ga_result(ctypes.Structure):
                 ("evaluations", ctypes.c_int), ("memo_hits", ctypes.c_int), ("fp8_layers", ctypes.c_int)]
 
 
+class net_tile_result(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("ms_analytic", ctypes.c_double),
+                ("evaluations", ctypes.c_int), ("memo_hits", ctypes.c_int), ("changed_layers", ctypes.c_int)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -91,6 +96,11 @@ _SIGS = {
     "net_get_layer_prec": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "net_tune_precision": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                            ctypes.POINTER(net_ga_opts), ctypes.c_void_p, ctypes.POINTER(net_ga_result)],
+    "net_set_layer_tiles": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "net_plan_tiles": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                       ctypes.c_int],
+    "net_tune_tiles": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                       ctypes.POINTER(net_ga_opts), ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(net_tile_result)],
     "net_stats_reset": [ctypes.c_void_p],
     "net_profile": [ctypes.c_void_p, ctypes.c_int],
     "net_layer_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
@@ -264,6 +274,28 @@ class Net:
                                        ctypes.byref(r)))
         names = {v: k for k, v in PREC.items()}
         return [names[int(v)] for v in out], {f: getattr(r, f) for f, _ in net_ga_result._fields_}
+
+    def set_layer_tiles(self, layer, bn=0, ksplit=0):
+        """Overrides one tensor-core layer's N tile / split-K (0: analytic)."""
+        check(lib().net_set_layer_tiles(self.h, layer, bn, ksplit))
+
+    def plan_tiles(self, batch, h, w):
+        """[(bn, ksplit)] per layer of the fixed-batch plan ((0, 0): CUDA cores)."""
+        bn = np.zeros(self.n_layers, np.int32)
+        ks = np.zeros(self.n_layers, np.int32)
+        check(lib().net_plan_tiles(self.h, batch, h, w, _ptr(bn), _ptr(ks), self.n_layers))
+        return [(int(a), int(b)) for a, b in zip(bn, ks)]
+
+    def tune_tiles(self, d_frames, batch, h, w, max_err=2e-2, population=12, generations=8,
+                   crossover=0.9, mutation=0.05, reps=3, seed=0):
+        """Genetic tile-plan search; returns ([(bn, ksplit)] per layer, result dict)."""
+        o = net_ga_opts(population, generations, crossover, mutation, max_err, reps, seed)
+        r = net_tile_result()
+        bn = np.zeros(self.n_layers, np.int32)
+        ks = np.zeros(self.n_layers, np.int32)
+        check(lib().net_tune_tiles(self.h, _ptr(d_frames), batch, h, w, ctypes.byref(o), _ptr(bn), _ptr(ks),
+                                   ctypes.byref(r)))
+        return [(int(a), int(b)) for a, b in zip(bn, ks)], {f: getattr(r, f) for f, _ in net_tile_result._fields_}
 
     def stats_reset(self):
         check(lib().net_stats_reset(self.h))

@@ -468,6 +468,21 @@ void dn::tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, 
     }
 }
 
+void dn::tc_tile_options(const net* n, int l, std::vector<std::pair<int, int>>* opts) {
+    opts->clear();
+    const Layer& L = n->L[l];
+    if (L.engine != ENG_TC) return;
+    const bool last = l + 1 == (int)n->L.size();
+    const int out_cs = last ? rup(L.d.cout, 4) : n->L[l + 1].in_cs;
+    const int ncols = std::max(L.d.cout, out_cs);
+    const int nk = L.kx * L.kx * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
+    for (int bn : {64, 128, 256}) {
+        if (bn > rup(ncols, 64)) continue;
+        for (int ks : {1, 2, 4, 8, 16})
+            if (ks == 1 || ks * 4 <= nk) opts->push_back({bn, ks});
+    }
+}
+
 // Buffer sequence and TC launch tables for one (batch, h, w).
 net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
     auto key = std::make_tuple(batch, h, w);
@@ -509,6 +524,10 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             r.m_tiles = batch * cdiv(r.H, r.TH) * cdiv(r.W, r.TW);
             const int nk = KK * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
             tc_choose_split(r.m_tiles, ncols, nk, n->num_sms, &r.BN, &r.ksplit);
+            // overrides (net_set_layer_tiles / net_tune_tiles), if still valid
+            // for the layer's current format
+            if (L.tile_bn > 0 && L.tile_bn <= rup(ncols, 64)) r.BN = L.tile_bn;
+            if (L.tile_ks == 1 || (L.tile_ks > 1 && L.tile_ks * 4 <= nk)) r.ksplit = L.tile_ks;
             r.n_tiles = cdiv(ncols, r.BN);
             const int tiles = r.m_tiles * r.n_tiles;
             if (r.ksplit > 1)
@@ -820,6 +839,47 @@ extern "C" net_status net_forward(net_t* n, const float* in, int batch, int h, i
     return check_device_error(n);
 }
 
+extern "C" net_status net_set_layer_tiles(net_t* n, int layer, int bn, int ksplit) {
+    if (!n) return fail(NET_E_INVAL, "NULL argument");
+    if (layer < 0 || layer >= (int)n->L.size()) return fail(NET_E_INVAL, "layer %d out of range", layer);
+    if ((bn != 0 && bn != 64 && bn != 128 && bn != 256) ||
+        (ksplit != 0 && ksplit != 1 && ksplit != 2 && ksplit != 4 && ksplit != 8 && ksplit != 16))
+        return fail(NET_E_INVAL, "tile bn %d / ksplit %d not in {0,64,128,256} / {0,1,2,4,8,16}", bn, ksplit);
+    Layer& L = n->L[layer];
+    if (L.engine != ENG_TC && (bn || ksplit)) return fail(NET_E_INVAL, "layer %d runs on CUDA cores", layer);
+    std::vector<std::pair<int, int>> opts;
+    tc_tile_options(n, layer, &opts);
+    bool bn_ok = bn == 0, ks_ok = ksplit == 0;
+    for (auto& o : opts) {
+        bn_ok |= o.first == bn;
+        ks_ok |= o.second == ksplit;
+    }
+    if (!bn_ok || !ks_ok) return fail(NET_E_INVAL, "layer %d cannot take bn %d / ksplit %d", layer, bn, ksplit);
+    if (L.tile_bn != bn || L.tile_ks != ksplit) {
+        L.tile_bn = bn;
+        L.tile_ks = ksplit;
+        invalidate_plans(n);
+    }
+    return NET_OK;
+}
+
+extern "C" net_status net_plan_tiles(net_t* n, int batch, int h, int w, int* bn, int* ks, int nn) {
+    if (!n || !bn || !ks) return fail(NET_E_INVAL, "NULL argument");
+    if (nn < (int)n->L.size()) return fail(NET_E_INVAL, "need %d entries", (int)n->L.size());
+    net_status s = check_shape(n, batch, h, w);
+    if (s != NET_OK) return s;
+    CK(cudaSetDevice(n->device));
+    Plan* P = nullptr;
+    s = get_plan(n, batch, h, w, &P);
+    if (s != NET_OK) return s;
+    for (size_t l = 0; l < n->L.size(); ++l) {
+        const bool tc = n->L[l].engine == ENG_TC;
+        bn[l] = tc ? P->runs[l].BN : 0;
+        ks[l] = tc ? P->runs[l].ksplit : 0;
+    }
+    return NET_OK;
+}
+
 static net_status async_start(net* n) {
     if (n->async) return NET_OK;
     std::unique_ptr<net::AsyncState> A(new net::AsyncState());
@@ -1021,7 +1081,9 @@ extern "C" net_status net_calibrate(net_t* n, const float* d_frames, int batch, 
     CK(cudaMemsetAsync(amax, 0, n->L.size() * sizeof(float), n->stream));
     s = run_fp32_reference(n, d_frames, batch, h, w, dout, amax);
     std::vector<float> hm(n->L.size());
-    cudaError_t e = cudaMemcpy(hm.data(), amax, hm.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    // the handle's stream may be non-blocking: finish it before a plain copy
+    cudaError_t e = cudaStreamSynchronize(n->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(hm.data(), amax, hm.size() * sizeof(float), cudaMemcpyDeviceToHost);
     cudaFree(amax);
     cudaFree(dout);
     if (s != NET_OK) return s;

@@ -6,6 +6,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "../../include/net.h"
@@ -32,6 +33,7 @@ struct Layer {
     float* alpha = nullptr;   // FP8: wscale * act_scale
     float* w32 = nullptr;     // FP32 copy of W' for calibration (FP8 nets)
     double act_scale = 1.0;   // FP8 scale of this layer's input
+    int tile_bn = 0, tile_ks = 0;   // fixed-batch plan overrides: N tile, split-K (0: analytic choice)
     CUtensorMap tmB[3];       // TC weights, box rows BN = 64, 128, 256
     // Layers created as FP8 tensor-core layers also keep a BF16 copy, so the
     // precision of each can be switched after loading (precision search).
@@ -75,6 +77,8 @@ struct Plan {
 // one warp: TW = 8 or 16).
 void tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, int* TW, int* TH, int* BN);
 void tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks = 16);
+// (N tile, split-K) pairs a tensor-core layer can take in its current format.
+void tc_tile_options(const net* n, int l, std::vector<std::pair<int, int>>* opts);
 // Cluster size, persistent worker count and resident-weight mode of a
 // tensor-core launch (nk K steps of chb bytes per tile).
 void tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int num_sms, int* cs, int* workers,

@@ -17,6 +17,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <vector>
@@ -47,6 +49,64 @@ struct Eval {
 };
 
 constexpr double kTimeoutMs = 1.0e6;   // the paper's "counts as 1000 s"
+
+// The paper's GA over integer genes, gene i taking values in [0, alpha[i])
+// (two-valued genes are the paper's bits).  evaluate(gene) returns its Eval
+// (memoised by the caller).  The first individual is `seed`; the best
+// individual ever seen is returned in best / best_g.
+template <class Evaluate>
+void ga_run(const std::vector<int>& alpha, const net_ga_opts* opt, const std::vector<int>& seed, Evaluate evaluate,
+            std::vector<int>* best_g, Eval* best) {
+    const int a = (int)alpha.size();
+    Rng rng{opt->seed ? opt->seed : 0x1811038820ull};
+    std::vector<std::vector<int>> pop(opt->population, std::vector<int>(a));
+    for (auto& g : pop)
+        for (int i = 0; i < a; ++i) g[i] = rng.below(alpha[i]);
+    pop[0] = seed;
+    *best_g = seed;
+    best->fitness = -1.0;
+    for (int gen = 0; gen < opt->generations; ++gen) {
+        std::vector<Eval> ev(pop.size());
+        double fsum = 0.0;
+        int elite = 0;
+        for (size_t i = 0; i < pop.size(); ++i) {
+            ev[i] = evaluate(pop[i]);
+            fsum += ev[i].fitness;
+            if (ev[i].fitness > ev[elite].fitness) elite = (int)i;
+            if (ev[i].fitness > best->fitness) {
+                *best = ev[i];
+                *best_g = pop[i];
+            }
+        }
+        if (gen + 1 == opt->generations) break;
+        // next generation: elite kept unchanged, the rest bred from roulette parents
+        auto roulette = [&]() -> const std::vector<int>& {
+            double r = rng.uniform() * fsum;
+            for (size_t i = 0; i < pop.size(); ++i) {
+                r -= ev[i].fitness;
+                if (r <= 0) return pop[i];
+            }
+            return pop.back();
+        };
+        std::vector<std::vector<int>> next;
+        next.push_back(pop[elite]);
+        while ((int)next.size() < opt->population) {
+            std::vector<int> p1 = roulette(), p2 = roulette();
+            if (a > 1 && rng.uniform() < opt->crossover) {
+                const int cut = 1 + rng.below(a - 1);
+                for (int i = cut; i < a; ++i) std::swap(p1[i], p2[i]);
+            }
+            for (auto* ch : {&p1, &p2}) {
+                // mutation: a bit flips; a many-valued gene takes another value
+                for (int i = 0; i < a; ++i)
+                    if (rng.uniform() < opt->mutation && alpha[i] > 1)
+                        (*ch)[i] = alpha[i] == 2 ? (*ch)[i] ^ 1 : ((*ch)[i] + 1 + rng.below(alpha[i] - 1)) % alpha[i];
+                if ((int)next.size() < opt->population) next.push_back(*ch);
+            }
+        }
+        pop.swap(next);
+    }
+}
 
 }  // namespace
 
@@ -83,7 +143,9 @@ extern "C" net_status net_tune_precision(net_t* n, const float* d_frames, int ba
 
     // reference: the FP32 path over the same frames
     s = run_fp32_reference(n, d_frames, batch, h, w, d_ref, nullptr);
-    if (s == NET_OK && cudaMemcpy(ref.data(), d_ref, nout * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+    // the handle's stream may be non-blocking: finish it before a plain copy
+    if (s == NET_OK && (cudaStreamSynchronize(n->stream) != cudaSuccess ||
+                        cudaMemcpy(ref.data(), d_ref, nout * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess))
         s = fail(NET_E_CUDA, "reference copy");
     double rmax = 0.0;
     for (float v : ref) rmax = std::max(rmax, (double)std::fabs(v));
@@ -127,56 +189,13 @@ extern "C" net_status net_tune_precision(net_t* n, const float* d_frames, int ba
     };
 
     const int a = (int)genes.size();
-    Rng rng{opt->seed ? opt->seed : 0x1811038820ull};
-    std::vector<std::vector<int>> pop(opt->population, std::vector<int>(a));
-    for (auto& g : pop)
-        for (int& b : g) b = rng.below(2);
     // One individual starts as the all-BF16 plan, the counterpart of the
     // paper's all-zero gene (everything on the CPU, its reference run): the
     // search then always holds a plan inside the error budget.
-    std::fill(pop[0].begin(), pop[0].end(), 0);
     std::vector<int> best_g(a, 0);
     Eval best;
     best.fitness = -1.0;
-    for (int gen = 0; gen < opt->generations && s == NET_OK; ++gen) {
-        std::vector<Eval> ev(pop.size());
-        double fsum = 0.0;
-        int elite = 0;
-        for (size_t i = 0; i < pop.size(); ++i) {
-            ev[i] = evaluate(pop[i]);
-            fsum += ev[i].fitness;
-            if (ev[i].fitness > ev[elite].fitness) elite = (int)i;
-            if (ev[i].fitness > best.fitness) {
-                best = ev[i];
-                best_g = pop[i];
-            }
-        }
-        if (gen + 1 == opt->generations) break;
-        // next generation: elite kept unchanged, the rest bred from roulette parents
-        auto roulette = [&]() -> const std::vector<int>& {
-            double r = rng.uniform() * fsum;
-            for (size_t i = 0; i < pop.size(); ++i) {
-                r -= ev[i].fitness;
-                if (r <= 0) return pop[i];
-            }
-            return pop.back();
-        };
-        std::vector<std::vector<int>> next;
-        next.push_back(pop[elite]);
-        while ((int)next.size() < opt->population) {
-            std::vector<int> p1 = roulette(), p2 = roulette();
-            if (a > 1 && rng.uniform() < opt->crossover) {
-                const int cut = 1 + rng.below(a - 1);
-                for (int i = cut; i < a; ++i) std::swap(p1[i], p2[i]);
-            }
-            for (auto* ch : {&p1, &p2}) {
-                for (int& b : *ch)
-                    if (rng.uniform() < opt->mutation) b ^= 1;
-                if ((int)next.size() < opt->population) next.push_back(*ch);
-            }
-        }
-        pop.swap(next);
-    }
+    if (s == NET_OK) ga_run(std::vector<int>(a, 2), opt, std::vector<int>(a, 0), evaluate, &best_g, &best);
     // reference points for the report
     Eval all_bf16, all_fp8;
     if (s == NET_OK) {
@@ -206,5 +225,173 @@ extern "C" net_status net_tune_precision(net_t* n, const float* d_frames, int ba
     cudaFree(d_out);
     if (s != NET_OK) return s;
     if (!feasible) return fail(NET_E_STATE, "no plan within the error budget %g", opt->max_err);
+    return NET_OK;
+}
+
+// Genetic search over the fixed-batch tile plan: one gene per tensor-core
+// layer with more than one valid (N tile, split-K) pair, the same GA as the
+// precision search.  Every plan computes the same sums in another order, so
+// the error check against the analytic plan's output only guards against a
+// broken configuration.
+extern "C" net_status net_tune_tiles(net_t* n, const float* d_frames, int batch, int h, int w,
+                                     const net_ga_opts* opt, int* bn_out, int* ks_out, net_tile_result* res) {
+    if (!n || !d_frames || !opt || !bn_out || !ks_out || !res) return fail(NET_E_INVAL, "NULL argument");
+    if (!n->weights_loaded) return fail(NET_E_WEIGHTS, "weights not loaded");
+    if (opt->population < 2 || opt->generations < 1 || opt->reps < 1 || !(opt->max_err > 0) ||
+        opt->crossover < 0 || opt->crossover > 1 || opt->mutation < 0 || opt->mutation > 1)
+        return fail(NET_E_INVAL, "bad search options");
+    net_status s = check_shape(n, batch, h, w);
+    if (s != NET_OK) return s;
+    cudaError_t e = cudaSetDevice(n->device);
+    if (e != cudaSuccess) return fail(NET_E_CUDA, "%s", cudaGetErrorString(e));
+    const int nl = (int)n->L.size();
+    std::vector<int> saved_bn(nl), saved_ks(nl);
+    for (int l = 0; l < nl; ++l) {
+        saved_bn[l] = n->L[l].tile_bn;
+        saved_ks[l] = n->L[l].tile_ks;
+        n->L[l].tile_bn = n->L[l].tile_ks = 0;   // the analytic plan first
+    }
+    invalidate_plans(n);
+    std::vector<int> genes;                                  // layer of each gene
+    std::vector<std::vector<std::pair<int, int>>> options;   // its (bn, ksplit) alphabet
+    for (int l = 0; l < nl; ++l) {
+        std::vector<std::pair<int, int>> o;
+        tc_tile_options(n, l, &o);
+        if (o.size() > 1) {
+            genes.push_back(l);
+            options.push_back(o);
+        }
+    }
+    int c, ho, wo;
+    net_output_shape(n, h, w, &c, &ho, &wo);
+    const size_t nout = (size_t)batch * c * ho * wo;
+    float *d_ref = nullptr, *d_out = nullptr;
+    if (cudaMalloc(&d_ref, nout * sizeof(float)) != cudaSuccess || cudaMalloc(&d_out, nout * sizeof(float)) != cudaSuccess) {
+        cudaFree(d_ref);
+        for (int l = 0; l < nl; ++l) {
+            n->L[l].tile_bn = saved_bn[l];
+            n->L[l].tile_ks = saved_ks[l];
+        }
+        return fail(NET_E_OOM, "search buffers");
+    }
+    std::vector<float> ref(nout), out(nout);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // the analytic plan: its output is the reference, its genes the seed
+    std::vector<int> seed(genes.size(), 0);
+    Plan* P = nullptr;
+    s = get_plan(n, batch, h, w, &P);
+    if (s == NET_OK)
+        for (size_t i = 0; i < genes.size(); ++i)
+            for (size_t j = 0; j < options[i].size(); ++j)
+                if (options[i][j].first == P->runs[genes[i]].BN && options[i][j].second == P->runs[genes[i]].ksplit)
+                    seed[i] = (int)j;
+    if (s == NET_OK) s = run_forward(n, d_frames, batch, h, w, d_ref);
+    // the handle's stream may be non-blocking: finish it before a plain copy
+    if (s == NET_OK && (cudaStreamSynchronize(n->stream) != cudaSuccess ||
+                        cudaMemcpy(ref.data(), d_ref, nout * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess))
+        s = fail(NET_E_CUDA, "reference copy");
+    double rmax = 0.0;
+    for (float v : ref) rmax = std::max(rmax, (double)std::fabs(v));
+    if (rmax == 0.0) rmax = 1.0;
+
+    std::map<std::vector<int>, Eval> memo;
+    int evaluations = 0, hits = 0;
+    auto apply = [&](const std::vector<int>& g) {
+        for (size_t i = 0; i < genes.size(); ++i) {
+            n->L[genes[i]].tile_bn = options[i][g[i]].first;
+            n->L[genes[i]].tile_ks = options[i][g[i]].second;
+        }
+        invalidate_plans(n);
+    };
+    auto evaluate = [&](const std::vector<int>& g) -> Eval {
+        auto it = memo.find(g);
+        if (it != memo.end()) {
+            ++hits;
+            return it->second;
+        }
+        Eval ev;
+        apply(g);
+        net_status st = run_forward(n, d_frames, batch, h, w, d_out);   // plans, capture, warm-up
+        if (st == NET_OK) {
+            cudaEventRecord(e0, n->stream);
+            for (int r = 0; r < opt->reps && st == NET_OK; ++r) st = run_forward(n, d_frames, batch, h, w, d_out);
+            cudaEventRecord(e1, n->stream);
+        }
+        float ms = 0.f;
+        if (st == NET_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            cudaMemcpy(out.data(), d_out, nout * sizeof(float), cudaMemcpyDeviceToHost) == cudaSuccess &&
+            check_device_error(n) == NET_OK) {
+            double d = 0.0;
+            for (size_t i = 0; i < nout; ++i) d = std::max(d, std::fabs((double)out[i] - (double)ref[i]));
+            ev.ms = ms / opt->reps;
+            ev.err = std::isfinite(d) ? d / rmax : 1e30;
+        } else {
+            ev.ms = kTimeoutMs;
+            ev.err = 1e30;
+        }
+        ev.fitness = 1.0 / std::sqrt(ev.err <= opt->max_err ? ev.ms : kTimeoutMs);
+        static const bool verbose = getenv("NET_TUNE_VERBOSE") != nullptr;   // diagnostics
+        if (verbose) {
+            fprintf(stderr, "tile plan [");
+            for (size_t i = 0; i < genes.size(); ++i)
+                fprintf(stderr, " L%d:%d/%d", genes[i], options[i][g[i]].first, options[i][g[i]].second);
+            fprintf(stderr, " ] status %d (%s) ms %.4f err %.3e\n", (int)st, st == NET_OK ? "" : net_last_error(),
+                    ev.ms, ev.err);
+        }
+        memo[g] = ev;
+        ++evaluations;
+        return ev;
+    };
+    std::vector<int> best_g = seed;
+    Eval best;
+    best.fitness = -1.0;
+    Eval analytic;
+    if (s == NET_OK) {
+        analytic = evaluate(seed);
+        if (!genes.empty()) {
+            std::vector<int> alpha;
+            for (auto& o : options) alpha.push_back((int)o.size());
+            ga_run(alpha, opt, seed, evaluate, &best_g, &best);
+        } else {
+            best = analytic;
+        }
+    }
+    // leave the best plan set (the analytic one when the search failed)
+    const bool found = s == NET_OK && best.fitness > 0 && best.err <= opt->max_err;
+    if (getenv("NET_TUNE_VERBOSE"))
+        fprintf(stderr, "tile search: status %d best ms %.4f err %.3e fitness %.4f analytic ms %.4f err %.3e found %d\n",
+                (int)s, best.ms, best.err, best.fitness, analytic.ms, analytic.err, (int)found);
+    if (found) {
+        apply(best_g);
+    } else {
+        for (int l = 0; l < nl; ++l) {
+            n->L[l].tile_bn = saved_bn[l];
+            n->L[l].tile_ks = saved_ks[l];
+        }
+        invalidate_plans(n);
+    }
+    std::memset(res, 0, sizeof(*res));
+    res->ms = found ? best.ms : analytic.ms;
+    res->ms_analytic = analytic.ms;
+    res->evaluations = evaluations;
+    res->memo_hits = hits;
+    int changed = 0;
+    for (size_t i = 0; i < genes.size(); ++i) changed += found && best_g[i] != seed[i];
+    res->changed_layers = changed;
+    if (s == NET_OK) s = get_plan(n, batch, h, w, &P);
+    if (s == NET_OK)
+        for (int l = 0; l < nl; ++l) {
+            const bool tc = n->L[l].engine == ENG_TC;
+            bn_out[l] = tc ? P->runs[l].BN : 0;
+            ks_out[l] = tc ? P->runs[l].ksplit : 0;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_ref);
+    cudaFree(d_out);
+    if (s != NET_OK) return s;
+    if (!found) return fail(NET_E_STATE, "no tile plan within the error budget %g", opt->max_err);
     return NET_OK;
 }

@@ -63,3 +63,43 @@ def test_layer_precision_switching_round_trip():
     qa = oracle.forward_quant(spec.layers, 3, x, blob, ["bf16"] * 9)
     assert oracle.rms_rel_err(ybf, qa) <= 1.2e-2
     assert oracle.normwise_rel_err(ybf, oracle.forward(spec.layers, 3, x, blob)) <= 2e-2
+
+
+def test_tile_plan_overrides_and_search():
+    """Per-layer (N tile, split-K) overrides and the genetic tile-plan search
+    (net_set_layer_tiles / net_plan_tiles / net_tune_tiles): overrides show in
+    the plan, bad values are refused, every plan stays within the BF16 budget
+    of the oracle, and the search never returns a plan slower than the
+    analytic one it starts from."""
+    import torch
+    from paper_1811_03882_gb300 import binding
+    spec = synth.net_19conv()
+    side, batch = 160, 2
+    _, x, blob = synth.workload_net(spec, 85, batch, side, side)
+    ex = oracle.forward(spec.layers, 3, x, blob)
+    with make_net(spec, prec="bf16", max_batch=batch, max_side=side) as net:
+        net.load_weights(blob)
+        d_x = torch.from_numpy(x).cuda()
+        base = net.plan_tiles(batch, side, side)
+        assert all(bn in (64, 128, 256) and ks in (1, 2, 4, 8, 16) for bn, ks in base)
+        # layer 13 (3x3, 512 -> 1024): a different N tile and split
+        bn13, ks13 = base[13]
+        alt = (128 if bn13 != 128 else 256, 1 if ks13 != 1 else 2)
+        net.set_layer_tiles(13, *alt)
+        assert net.plan_tiles(batch, side, side)[13] == alt
+        y = net.forward(x)
+        assert oracle.normwise_rel_err(y, ex) <= 2e-2
+        with pytest.raises(binding.NetError) as e:
+            net.set_layer_tiles(13, 96, 1)
+        assert e.value.status == binding.NET_E_INVAL
+        with pytest.raises(binding.NetError) as e:
+            net.set_layer_tiles(0, 64, 4)        # the im2col first layer has one K step
+        assert e.value.status == binding.NET_E_INVAL
+        net.set_layer_tiles(13, 0, 0)
+        assert net.plan_tiles(batch, side, side) == base
+        plan, res = net.tune_tiles(d_x, batch, side, side, population=6, generations=3, reps=2, seed=11)
+        print("tile plan", plan, res)
+        assert res["ms"] <= res["ms_analytic"] and res["evaluations"] >= 1
+        assert net.plan_tiles(batch, side, side) == plan
+        y = net.forward(x)
+    assert oracle.normwise_rel_err(y, ex) <= 2e-2
