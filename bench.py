@@ -394,6 +394,36 @@ def measure(torch, W, args, flush, barrier, ws, with_clocks=False, dev=0):
             "e2e_fps": frames_all / e2e_s}
 
 
+def per_layer(W, layer_ms, precs):
+    """Each layer's achieved TFLOP/s and, against its algorithmic bytes
+    (input activation + post-pool output activation + weights, each moved
+    once, in the layer's storage type; the first layer reads the FP32
+    frames), achieved GB/s and the fraction of the measured HBM peak."""
+    pk, _ = peaks()
+    esz = {"fp32": 4, "bf16": 2, "fp8": 1}
+    cins = W.spec.cins()
+    nl = len(W.spec.layers)
+    out = []
+    for i, (l, ci) in enumerate(zip(W.spec.layers, cins)):
+        byt = 0.0
+        for sd in W.sides:
+            h = sd
+            for j in range(i):
+                if W.spec.layers[j].pool == synth.POOL_2X2S2:
+                    h //= 2
+            ho = h // 2 if l.pool == synth.POOL_2X2S2 else h
+            ein = 4 if i == 0 else esz[precs[i]]
+            eout = 4 if i + 1 == nl else esz[precs[i + 1]]
+            byt += h * h * ci * ein + ho * ho * l.cout * eout
+        byt += l.cout * ci * l.k * l.k * esz[precs[i]]
+        t = float(layer_ms[i]) / 1e3
+        out.append({"layer": i, "k": l.k, "cin": ci, "cout": l.cout, "ms": round(float(layer_ms[i]), 5),
+                    "tflops": round(float(W.flops_l[i]) / t / 1e12, 2),
+                    "alg_mb": round(byt / 1e6, 2), "gbs": round(byt / t / 1e9, 1),
+                    "hbm_frac": round(byt / t / 1e9 / pk["hbm_gbs"], 3)})
+    return out
+
+
 def roofline(W, layer_ms, precs):
     """Dominant kernel family (by engine) over its layers: algorithmic FLOPs
     / summed CUDA-event time, against the measured peak."""
@@ -494,6 +524,7 @@ def main():
         "conv_tflops": m["conv_tflops"],
         "roofline": roof,
         "layer_ms": [round(float(t), 5) for t in m["layer_ms"]],
+        "layers": per_layer(W, m["layer_ms"], precs),
         "e2e": {"value": m["e2e_fps"], "unit": "frames/s", "h2d_bytes_per_step": W.h2d, "d2h_bytes_per_step": W.d2h},
         "gpu_launches": int(m["launches"]),
         "wall_s_timed": m["wall"],
