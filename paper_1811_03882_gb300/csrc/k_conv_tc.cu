@@ -43,7 +43,8 @@ constexpr int THREADS = 384;   // producer, MMA issuer, 8 epilogue warps, second
 constexpr int NUM_WARPS = THREADS / 32;
 constexpr int kMaxStages = 32;                // ring stages (bit masks below are 32 bits)
 constexpr int kEpiCols = 1024;                // bias / alpha columns kept in shared memory
-constexpr int kRawHalo = 3 * 18 * 10;         // raw first layer: 3 channels x (16+2) x (8+2) of a 16 x 8 tile
+constexpr int kRawHalo = 3 * 20 * 10;         // raw first layer: 3 channels x (8+2) rows x 20 (16+2 columns, padded)
+constexpr int kRawBufs = 4;                   // raw first layer: halo buffers per producer warp
 constexpr long long WAIT_LIMIT = 4000000000LL;  // clock64 cycles (~2 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -261,7 +262,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     // epilogue copies of bias / alpha (launches with at most kEpiCols columns)
     float* s_bias = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(sm) + ((sizeof(Smem) + 15) & ~(size_t)15));
     float* s_alpha = s_bias + kEpiCols;
-    float* s_raw = s_alpha + kEpiCols;   // raw mode: one input-halo staging area per producer warp
+    float* s_raw = s_alpha + kEpiCols;   // raw mode: kRawBufs input-halo buffers per producer warp
 
     pdl_trigger();   // the next kernel may start its prologue as SMs free up
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -343,7 +344,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         if (a.raw) {
             // ---- software im2col of the first layer: this warp fills the A
             // tiles of its K steps (one per tile, every other tile) from the
-            // raw frames; lane l builds pixels l, l+32, l+64, l+96 of the tile.
+            // raw frames.
             // The smem image is what a SWIZZLE_64B TMA box would write: row r
             // at r*64 bytes, 16-byte unit u of the row stored at unit
             // u ^ ((r >> 1) & 3).
@@ -352,66 +353,86 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             const int tiles_x = P->tiles_x, tiles_y = P->tiles_y;
             // the halo of a 16 x 8 tile, three channels: 3 x 10 x 18 floats,
             // element e -> (c, hy, hx); lane l holds elements l + 32k
-            constexpr int HW = 18, HH = 10, HN = 3 * HH * HW, PER = (HN + 31) / 32;
-            float* hal = s_raw + pid * kRawHalo;
-            // halos of this warp's next two tiles, in flight while the current
-            // tile is built (the frames come from DRAM: ~thousands of cycles)
-            float hA[PER], hB[PER];
-            auto load_halo = [&](float (&R)[PER], int tile) {
-                if (tile >= total) return;
-                const int txy = tile / tiles_x;
-                const int tx = tile - txy * tiles_x;
-                const int img = txy / tiles_y;
-                const int ty = txy - img * tiles_y;
-                const int y0 = ty * 8 - 1, x0 = tx * 16 - 1;
-                const float* X = a.x_raw + (size_t)img * 3 * H * W;
+            // staged with a row pitch of HP = 20 floats (80 bytes, 16-byte aligned rows)
+            constexpr int HW = 18, HH = 10, HP = 20, HN = 3 * HH * HW, PER = (HN + 31) / 32;
+            // two halo buffers per warp, filled by cp.async (global -> shared,
+            // out-of-frame elements zero-filled) one tile ahead of the build
+            auto prefetch = [&](int tile, float* hal) {
+                if (tile < total) {
+                    const int txy = tile / tiles_x;
+                    const int tx = tile - txy * tiles_x;
+                    const int img = txy / tiles_y;
+                    const int ty = txy - img * tiles_y;
+                    const int y0 = ty * 8 - 1, x0 = tx * 16 - 1;
+                    const float* X = a.x_raw + (size_t)img * 3 * H * W;
 #pragma unroll
-                for (int k = 0; k < PER; ++k) {
-                    const int e = lane + 32 * k;
-                    const int c = e / (HH * HW), rem = e - c * (HH * HW);
-                    const int hy = rem / HW, hx = rem - hy * HW;
-                    const int yy = y0 + hy, xx = x0 + hx;
-                    R[k] = (e < HN && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                               ? __ldg(X + ((size_t)c * H + yy) * W + xx)
-                               : 0.f;
+                    for (int k = 0; k < PER; ++k) {
+                        const int e = lane + 32 * k;
+                        if (e < HN) {
+                            const int c = e / (HH * HW), rem = e - c * (HH * HW);
+                            const int hy = rem / HW, hx = rem - hy * HW;
+                            const int yy = y0 + hy, xx = x0 + hx;
+                            const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+                            const float* src = in ? X + ((size_t)c * H + yy) * W + xx : X;
+                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
+                                             smem_u32(hal + (c * HH + hy) * HP + hx)),
+                                         "l"(src), "r"(in ? 4 : 0)
+                                         : "memory");
+                        }
+                    }
                 }
+                asm volatile("cp.async.commit_group;" ::: "memory");   // (an empty group past the last tile)
             };
             int ps = pid;
             uint32_t eph = 0u;
             bool ok = true;
             int t = pid, tile = worker + pid * nworkers;
             const int step2 = 2 * nworkers;   // this warp's tiles: every other tile of the CTA
-            load_halo(hA, tile);
-            load_halo(hB, tile + step2);
-            // one tile: stage its halo (R), refill R with the tile two ahead,
-            // build the A tile, hand it to MMA issuer t & 1
-            auto one = [&](float (&R)[PER]) -> bool {
+            // kRawBufs halo buffers per warp: tiles kRawBufs - 1 ahead in flight
+            int hb = 0;                        // halo buffer of the current tile
+            for (int d = 0; d < kRawBufs - 1; ++d) prefetch(tile + d * step2, s_raw + (kRawBufs * pid + d) * kRawHalo);
+            // lane l builds the four pixels (l / 4, 4 (l % 4) .. 4 (l % 4) + 3) of
+            // the 16 x 8 tile: per channel and tap row one 16-byte and one
+            // 8-byte shared load give the six halo columns those pixels read
+            const int bpy = lane >> 2, bpx = (lane & 3) * 4;
+            // one tile: prefetch the halo kRawBufs - 1 tiles ahead into the buffer
+            // the previous tile used, build this tile's A tile from its halo,
+            // hand it to MMA issuer t & 1
+            auto one = [&]() -> bool {
                 if (tile >= total || !ok) return false;
-                __syncwarp();   // the previous tile's reads of the staging area are done
-#pragma unroll
-                for (int k = 0; k < PER; ++k)
-                    if (lane + 32 * k < HN) hal[lane + 32 * k] = R[k];
+                __syncwarp();   // the previous build's reads of its buffer are done
+                const int pb = hb == 0 ? kRawBufs - 1 : hb - 1;   // that buffer
+                prefetch(tile + (kRawBufs - 1) * step2, s_raw + (kRawBufs * pid + pb) * kRawHalo);
+                asm volatile("cp.async.wait_group %0;" ::"n"(kRawBufs - 1) : "memory");   // this tile's halo landed
                 __syncwarp();
-                load_halo(R, tile + 2 * step2);
+                const float* hal = s_raw + (kRawBufs * pid + hb) * kRawHalo;
                 if (!tc::mbar_wait(smem_u32(&sm->empty[ps]), eph ^ 1u, abort_flag, a.err, 1)) {
                     ok = false;
                     return false;
                 }
                 uint8_t* stg = sRing + (size_t)ps * st_bytes;
-#pragma unroll 2
-                for (int i = 0; i < 4; ++i) {
-                    const int r = lane + 32 * i;
-                    const int py = r >> 4, px = r & 15;
+                float f[3][3][6];   // [channel][tap row][halo column bpx .. bpx + 5]
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int kh = 0; kh < 3; ++kh) {
+                        const float* src = hal + (c * HH + bpy + kh) * HP + bpx;
+                        const float4 q4 = *reinterpret_cast<const float4*>(src);
+                        const float2 q2 = *reinterpret_cast<const float2*>(src + 4);
+                        f[c][kh][0] = q4.x;
+                        f[c][kh][1] = q4.y;
+                        f[c][kh][2] = q4.z;
+                        f[c][kh][3] = q4.w;
+                        f[c][kh][4] = q2.x;
+                        f[c][kh][5] = q2.y;
+                    }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int r = bpy * 16 + bpx + j;
                     // element q = (kh*3 + kw)*3 + c (three channels), zero from 27 on
                     float v[32];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        v[q] = 0.f;
-                        if (q < 27) {
-                            const int kh = q / 9, kw = (q / 3) % 3, c = q % 3;
-                            v[q] = hal[(c * HH + py + kh) * HW + px + kw];
-                        }
-                    }
+                    for (int q = 0; q < 32; ++q) v[q] = q < 27 ? f[q % 3][q / 9][j + (q / 3) % 3] : 0.f;
                     uint8_t* row = stg + r * 64;
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
@@ -436,10 +457,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 }
                 t += 2;
                 tile += step2;
+                hb = hb + 1 == kRawBufs ? 0 : hb + 1;
                 return true;
             };
-            while (one(hA) && one(hB)) {
+            while (one()) {
             }
+            asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the kernel
             if (a.bres && pid == 0 && lane == 0 &&
                 !tc::mbar_wait(smem_u32(&sm->bres), 0u, abort_flag, a.err, 5)) {
                 const long long t0 = clock64();
@@ -991,7 +1014,7 @@ cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, 
 constexpr size_t kSmemLimit = 232448;   // opt-in dynamic shared memory per block (227 KB)
 
 static size_t tc_ctrl_bytes() {
-    return ((sizeof(tc::Smem) + 15) & ~(size_t)15) + (2 * tc::kEpiCols + 2 * tc::kRawHalo) * sizeof(float);
+    return ((sizeof(tc::Smem) + 15) & ~(size_t)15) + (2 * tc::kEpiCols + 2 * tc::kRawBufs * tc::kRawHalo) * sizeof(float);
 }
 static size_t tc_avail() { return kSmemLimit - 1024 - tc_ctrl_bytes(); }
 
