@@ -282,6 +282,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     const uint32_t a_bytes = a.tapm ? 3u * a_box : a_box, b_bytes = (uint32_t)BN * a.chb;
 
     if (threadIdx.x == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
         for (int s = 0; s < nst; ++s) {
             tc::mbar_init(smem_u32(&sm->full[0][s]), 1);
             tc::mbar_init(smem_u32(&sm->full[1][s]), 1);
@@ -311,9 +312,30 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     tc::fence_after();
     const uint32_t tmem_base = sm->tmem;
     volatile int* abort_flag = &sm->abort;
-    // the prologue above may overlap the previous kernel; activations,
-    // problem tables and split-K workspace are touched only after it ended
-    pdl_wait();
+    if (a.bres && warp == 0 && lane == 0) {
+        // resident weights: every K step's [BN x chunk] box, once, side by
+        // side (the launch has one N tile and no K split).  Weights are
+        // written only by the fold at load time, which the host waits for,
+        // so these loads may overlap the previous kernel's tail.
+        const uint32_t rb = smem_u32(&sm->bres);
+        tc::mbar_expect_tx(rb, (uint32_t)nkb * b_bytes);
+        int ch = 0, tap = 0;
+        for (int ks = 0; ks < nkb; ++ks) {
+            tc::tma_load_2d(smem_u32(sBres + (size_t)ks * b_bytes), &tmB, tap * a.Cp + ch * a.cpc, 0, rb);
+            if (++ch == a.chunks) {
+                ch = 0;
+                ++tap;
+            }
+        }
+    }
+    __syncwarp();
+    // the prologue above may overlap the previous kernel; activations and
+    // split-K workspace are touched only after it ended.  The TMA producers
+    // of the im2col-by-TMA path wait further down, after the weight box of
+    // their first K step is on its way (weights and problem tables are
+    // complete before the forward pass starts).
+    const bool lane_producer = (warp == 0 || warp == NUM_WARPS - 2) && !a.raw;
+    if (!lane_producer) pdl_wait();
 
     if (warp == 0 || warp == NUM_WARPS - 2) {
         // ------------------------------------------------ TMA producers
@@ -326,21 +348,6 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         const int pid = warp == 0 ? 0 : 1;
         const int G = a.plane;
         const int S2 = 2 * G;
-        if (a.bres && pid == 0 && lane == 0) {
-            // resident weights: every K step's [BN x chunk] box, once, side by
-            // side (the launch has one N tile and no K split)
-            const uint32_t rb = smem_u32(&sm->bres);
-            tc::mbar_expect_tx(rb, (uint32_t)nkb * b_bytes);
-            int ch = 0, tap = 0;
-            for (int ks = 0; ks < nkb; ++ks) {
-                tc::tma_load_2d(smem_u32(sBres + (size_t)ks * b_bytes), &tmB, tap * a.Cp + ch * a.cpc, 0, rb);
-                if (++ch == a.chunks) {
-                    ch = 0;
-                    ++tap;
-                }
-            }
-        }
-        __syncwarp();
         if (a.raw) {
             // ---- software im2col of the first layer: this warp fills the A
             // tiles of its K steps (one per tile, every other tile) from the
@@ -552,6 +559,19 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             int ps = it;                 // stage of `it` (S2 divides nst: stepped by S2)
             uint32_t eph = 0u;           // parity of that stage's next empty phase
             bool ok = true;
+            // the first K step's weight box does not depend on the previous
+            // kernel: its stage is free, so it is armed for the whole step and
+            // the box is issued before the dependency wait
+            bool pre_b = false;
+            if (!a.bres && CS == 1 && tile < total) {
+                const int owner = a.kalt ? ((ks - ks0) & 1) : towner;
+                const uint32_t fb = smem_u32(&sm->full[owner][ps]);
+                tc::mbar_expect_tx(fb, a_bytes + b_bytes);
+                tc::tma_load_2d(smem_u32(sRing + (size_t)ps * st_bytes + a_bytes), &tmB,
+                                (kh * a.k + kw) * a.Cp + ch * a.cpc, nt * BN, fb);
+                pre_b = true;
+            }
+            pdl_wait();
             // per issuer: bit s = phase parity of the next use of full[m][s];
             // per stage this lane fills: the issuer of its last use
             uint32_t pph0 = 0u, pph1 = 0u, last_owner = 0u, issued = 0u;
@@ -570,7 +590,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     else pph0 ^= 1u << s;
                     last_owner = (last_owner & ~(1u << s)) | ((uint32_t)owner << s);
                     issued |= 1u << s;
-                    tc::mbar_expect_tx(fb, a.bres ? a_bytes : a_bytes + b_bytes);
+                    if (!pre_b) tc::mbar_expect_tx(fb, a.bres ? a_bytes : a_bytes + b_bytes);
                     const int c0 = ch * a.cpc;
                     const int kcol = (kh * a.k + kw) * a.Cp + c0;   // K column of the weights
                     uint8_t* stg = sRing + (size_t)s * st_bytes;
@@ -580,7 +600,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     } else {
                         tc::tma_load_4d(smem_u32(stg), &P->tmA, c0, x0 + kw, y0 + kh, img, fb);
                     }
-                    if (a.bres) {
+                    if (a.bres || pre_b) {
+                        pre_b = false;
                     } else if (CS == 1) {
                         tc::tma_load_2d(smem_u32(stg + a_bytes), &tmB, kcol, nt * BN, fb);
                     } else {

@@ -572,8 +572,11 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             hp.tiles_x = cdiv(r.W, r.TW);
             hp.tiles_y = cdiv(r.H, r.TH);
             hp.tile_begin = 0;
+            // the table is complete on the device before any launch reads it
+            // (kernels read it ahead of their dependency wait)
             CK(cudaMalloc(&r.d_prob, sizeof(ConvProblem)));
-            CK(cudaMemcpy(r.d_prob, &hp, sizeof hp, cudaMemcpyHostToDevice));
+            CK(cudaMemcpyAsync(r.d_prob, &hp, sizeof hp, cudaMemcpyHostToDevice, n->stream));
+            CK(cudaStreamSynchronize(n->stream));
             static const bool dump = getenv("NET_PLAN_DUMP") != nullptr;   // diagnostics: one line per layer
             if (dump)
                 fprintf(stderr,

@@ -154,7 +154,9 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
         tc_workers(r.m_tiles, r.n_tiles, 1, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, &r.cs, &r.grid,
                    &r.bres);
         cudaError_t e = cudaMalloc(&r.d_prob, sizeof(ConvProblem) * cnt);
-        if (e == cudaSuccess) e = cudaMemcpy(r.d_prob, probs.data(), sizeof(ConvProblem) * cnt, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(r.d_prob, probs.data(), sizeof(ConvProblem) * cnt, cudaMemcpyHostToDevice, n->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
         if (e != cudaSuccess) return fail(NET_E_CUDA, "layer %d problem table: %s", l, cudaGetErrorString(e));
         if (L.d.pool == NET_POOL_2X2S1_SAME) {
             if (last) return fail(NET_E_UNSUPPORTED, "stride-1 pool on the last layer of an uneven batch");
