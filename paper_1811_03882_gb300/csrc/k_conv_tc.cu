@@ -249,6 +249,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     // accumulator buffers in TMEM (512 columns): four up to BN = 128, so the
     // MMAs of the next tiles never wait for an epilogue's round trip
     constexpr int NBUF = BN <= 128 ? 4 : 2;
+    constexpr int NBUF_LOG = BN <= 128 ? 2 : 1;
     constexpr int TMEM_COLS = NBUF * BN;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -366,9 +367,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             // out-of-frame elements zero-filled) one tile ahead of the build
             auto prefetch = [&](int tile, float* hal) {
                 if (tile < total) {
-                    const int txy = tile / tiles_x;
+                    const int txy = fdiv(tile, P->fd_tx);
                     const int tx = tile - txy * tiles_x;
-                    const int img = txy / tiles_y;
+                    const int img = fdiv(txy, P->fd_ty);
                     const int ty = txy - img * tiles_y;
                     const int y0 = ty * 8 - 1, x0 = tx * 16 - 1;
                     const float* X = a.x_raw + (size_t)img * 3 * H * W;
@@ -481,10 +482,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             // a single-problem launch keeps the problem's fields in registers
             const ConvProblem* P1 = a.nprob == 1 ? a.probs : nullptr;
             int tiles_x = 1, tiles_y = 1, tbeg = 0;
+            FastDiv fd_tx, fd_ty;
             if (P1) {
                 tiles_x = P1->tiles_x;
                 tiles_y = P1->tiles_y;
                 tbeg = P1->tile_begin;
+                fd_tx = P1->fd_tx;
+                fd_ty = P1->fd_ty;
             }
             // this lane's position: tile sequence index t (tile = worker + t *
             // nworkers), K step ks of that tile's slice [ks0, ks1), and `it`
@@ -493,13 +497,18 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             int towner = 0, nt = 0, img = 0, x0 = 0, y0 = 0;
             const ConvProblem* P = P1;
             auto slice = [&] {
-                const int z = a.ksplit > 1 ? tile % a.ksplit : 0;
-                ks0 = nk * z / a.ksplit;
-                ks1 = nk * (z + 1) / a.ksplit;
+                if (a.ksplit > 1) {
+                    const int z = tile - fdiv(tile, a.fd_ksplit) * a.ksplit;
+                    ks0 = fdiv(nk * z, a.fd_ksplit);
+                    ks1 = fdiv(nk * (z + 1), a.fd_ksplit);
+                } else {
+                    ks0 = 0;
+                    ks1 = nk;
+                }
             };
             auto setup = [&] {   // coordinates of the lane's current tile
-                const int mn = a.ksplit > 1 ? tile / a.ksplit : tile;
-                const int mq = mn / a.n_tiles;
+                const int mn = a.ksplit > 1 ? fdiv(tile, a.fd_ksplit) : tile;
+                const int mq = fdiv(mn, a.fd_ntiles);
                 const int mt = mq * CS + rank;
                 nt = mn - mq * a.n_tiles;
                 towner = t & 1;
@@ -508,19 +517,21 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     tiles_x = P->tiles_x;
                     tiles_y = P->tiles_y;
                     tbeg = P->tile_begin;
+                    fd_tx = P->fd_tx;
+                    fd_ty = P->fd_ty;
                 }
                 const int local = mt - tbeg;
-                const int txy = local / tiles_x;
+                const int txy = fdiv(local, fd_tx);
                 const int tx = local - txy * tiles_x;
-                img = txy / tiles_y;
+                img = fdiv(txy, fd_ty);
                 const int ty = txy - img * tiles_y;
                 x0 = tx * a.TW - pad;
                 y0 = ty * a.TH - pad;
             };
             auto decompose = [&] {   // (ch, kw, kh) of ks, by division (tile changes only)
-                const int tap = ks / a.chunks;
+                const int tap = fdiv(ks, a.fd_chunks);
                 ch = ks - tap * a.chunks;
-                kh = tap / a.k;
+                kh = fdiv(tap, a.fd_k);
                 kw = tap - kh * a.k;
             };
             // moves the position forward by d K steps (across tiles)
@@ -659,20 +670,25 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 tc::fence_after();
             }
             for (int tile = worker; tile < total && ok; tile += nworkers, ++tcount) {
-                const int z = a.ksplit > 1 ? tile % a.ksplit : 0;
-                const int ks0 = nk * z / a.ksplit, ks1 = nk * (z + 1) / a.ksplit;
+                int ks0 = 0, ks1 = nk;
+                if (a.ksplit > 1) {
+                    const int z = tile - fdiv(tile, a.fd_ksplit) * a.ksplit;
+                    ks0 = fdiv(nk * z, a.fd_ksplit);
+                    ks1 = fdiv(nk * (z + 1), a.fd_ksplit);
+                }
                 if (!a.kalt && (tcount & 1) != mid) {   // the other issuer's tile: its stages are skipped
                     it += ks1 - ks0;
                     continue;
                 }
-                const int nslot = a.kalt ? NBUF / 2 : NBUF;
-                const int slot = tcount % nslot;
+                // accumulator slots: NBUF, or NBUF / 2 pairs (both powers of two)
+                const int nsl_log = a.kalt ? NBUF_LOG - 1 : NBUF_LOG;
+                const int slot = tcount & ((1 << nsl_log) - 1);
                 const int b = a.kalt ? 2 * slot + mid : slot;
-                const uint32_t aph = (uint32_t)(tcount / nslot) & 1u;
+                const uint32_t aph = (uint32_t)(tcount >> nsl_log) & 1u;
                 if (!tc::mbar_wait(smem_u32(&sm->acce[b]), aph ^ 1u, abort_flag, a.err, 2)) break;
                 tc::fence_after();
                 const uint32_t dtm = tmem_base + (uint32_t)(b * BN);
-                int ms = it % nst;   // stage of this tile's first K step
+                int ms = it - fdiv(it, a.fd_nst) * nst;   // stage of this tile's first K step
                 bool first = true;   // the issuer's first K step of the tile overwrites its accumulator
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
                     const int s = ms;
@@ -754,21 +770,22 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         const int live = a.ep.out_layout == LAYOUT_NCHW ? a.ep.cout : max(a.ep.out_cs, a.ep.cout);
         void* pY = nullptr;
         int pH = 0, pW = 0, pTX = 1, pTY = 1, pBegin = 0;
+        FastDiv fTX, fTY;
         int tcount = 0;
         bool have_p = false;   // problem fields loaded (single-problem launches read them once)
         for (int tile = worker; tile < total; tile += nworkers, ++tcount) {
             if (!a.kalt && (tcount & 1) != grp) continue;
             // the tile's accumulator (or pair of them in K-alternating mode)
-            const int nslot = a.kalt ? NBUF / 2 : NBUF;
-            const int slot = tcount % nslot;
+            const int nsl_log = a.kalt ? NBUF_LOG - 1 : NBUF_LOG;
+            const int slot = tcount & ((1 << nsl_log) - 1);
             const int b = a.kalt ? 2 * slot : slot;
-            const uint32_t aph = (uint32_t)(tcount / nslot) & 1u;
+            const uint32_t aph = (uint32_t)(tcount >> nsl_log) & 1u;
             if (!tc::mbar_wait(smem_u32(&sm->accf[b]), aph, abort_flag, a.err, 4)) break;
             if (a.kalt && !tc::mbar_wait(smem_u32(&sm->accf[b + 1]), aph, abort_flag, a.err, 4)) break;
             tc::fence_after();
-            const int z = a.ksplit > 1 ? tile % a.ksplit : 0;
-            const int mn = a.ksplit > 1 ? tile / a.ksplit : tile;
-            const int mq = mn / a.n_tiles;
+            const int mn = a.ksplit > 1 ? fdiv(tile, a.fd_ksplit) : tile;
+            const int z = tile - mn * a.ksplit;
+            const int mq = fdiv(mn, a.fd_ntiles);
             const int mt = mq * CS + rank, nt = mn - mq * a.n_tiles;
             if (mt >= a.m_tiles) {
                 // the cluster's spare CTA on an odd tile count: loads and MMAs ran on
@@ -832,12 +849,14 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     pTX = P.tiles_x;
                     pTY = P.tiles_y;
                     pBegin = P.tile_begin;
+                    fTX = P.fd_tx;
+                    fTY = P.fd_ty;
                 }
                 void* ybase = a.y_override ? a.y_override : pY;
                 const int local = mt - pBegin;
-                const int txy = local / pTX;
+                const int txy = fdiv(local, fTX);
                 const int tx = local - txy * pTX;
-                const int img = txy / pTY;
+                const int img = fdiv(txy, fTY);
                 const int ty = txy - img * pTY;
                 const int gy = ty * a.TH + py, gx = tx * a.TW + px;
                 const bool valid = gy < pH && gx < pW;
@@ -1073,6 +1092,12 @@ template <int BN, int DT, int CS>
 static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int workers, cudaStream_t st) {
     TcArgs a = a0;
     if (!tc_geometry(BN, a.chb, a.bres, a.k * a.k * a.chunks, &a)) return cudaErrorInvalidValue;
+    if (a.ksplit < 1 || a.n_tiles < 1 || a.chunks < 1 || a.k < 1) return cudaErrorInvalidValue;
+    a.fd_ksplit = make_fast_div(a.ksplit);
+    a.fd_ntiles = make_fast_div(a.n_tiles);
+    a.fd_chunks = make_fast_div(a.chunks);
+    a.fd_k = make_fast_div(a.k);
+    a.fd_nst = make_fast_div(a.nst);
     const size_t smem = 1024 + (size_t)a.ctrl_off + tc_ctrl_bytes();
     auto kern = conv_tc_kernel<BN, DT, CS>;
     static bool attr = false;

@@ -87,6 +87,30 @@ cudaError_t absmax_f32(const float* x, size_t count, float* out, cudaStream_t st
 }  // namespace dn
 
 namespace dn {
+// n / d for 0 <= n < 2^31 and 1 <= d < 2^31 by one multiply-high, an add and
+// a shift (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (mulhi(n, m) + n) >> l.  The
+// tensor-core kernel's tile and K-step decodes divide by launch constants
+// once per tile; a runtime integer division there costs a dependent chain of
+// some twenty instructions on a warp with nothing else to issue.
+struct FastDiv {
+    uint32_t mul = 1u, shift = 0u;   // d = 1
+};
+inline FastDiv make_fast_div(int d) {
+    FastDiv f;
+    uint32_t l = 0;
+    while ((1ull << l) < (unsigned long long)d) ++l;
+    f.mul = (uint32_t)(((1ull << 32) * ((1ull << l) - (unsigned long long)d)) / (unsigned long long)d + 1ull);
+    f.shift = l;
+    return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ int fdiv(int n, FastDiv f) {
+    return (int)((__umulhi((uint32_t)n, f.mul) + (uint32_t)n) >> f.shift);
+}
+#endif
+
 // One group member of a tensor-core conv launch: a batch of n equal frames
 // with its own activation tensor map and output.  The device-side table of
 // problems lets one launch cover frames of different sizes.
@@ -97,7 +121,13 @@ struct alignas(128) ConvProblem {
     int n, H, W;        // frames, pre-pool size
     int tiles_x, tiles_y;
     int tile_begin;     // first M tile of this problem in the launch
+    FastDiv fd_tx, fd_ty;   // division by tiles_x, tiles_y (set by tc_problem_divisors)
 };
+// Fills a problem's division constants from its tiles_x / tiles_y.
+inline void tc_problem_divisors(ConvProblem& p) {
+    p.fd_tx = make_fast_div(p.tiles_x);
+    p.fd_ty = make_fast_div(p.tiles_y);
+}
 
 struct TcArgs {
     const ConvProblem* probs;  // device table, nprob entries
@@ -130,6 +160,8 @@ struct TcArgs {
     int tapm;
     Epilogue ep;
     int* err;     // bounded-wait failure code (0 = none)
+    // division by ksplit, n_tiles, chunks, k and nst (filled by conv_tc_launch)
+    FastDiv fd_ksplit, fd_ntiles, fd_chunks, fd_k, fd_nst;
 };
 
 // Grouped memory-bound helpers: one launch over several frames of

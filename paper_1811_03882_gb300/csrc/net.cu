@@ -571,6 +571,7 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             hp.W = r.W;
             hp.tiles_x = cdiv(r.W, r.TW);
             hp.tiles_y = cdiv(r.H, r.TH);
+            tc_problem_divisors(hp);
             hp.tile_begin = 0;
             // the table is complete on the device before any launch reads it
             // (kernels read it ahead of their dependency wait)

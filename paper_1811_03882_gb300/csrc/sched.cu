@@ -142,6 +142,7 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
             q.W = W[f][l];
             q.tiles_x = cdiv(q.W, r.TW);
             q.tiles_y = cdiv(q.H, r.TH);
+            tc_problem_divisors(q);
             q.tile_begin = mt;
             mt += q.tiles_x * q.tiles_y;
         }

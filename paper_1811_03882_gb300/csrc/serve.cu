@@ -194,6 +194,7 @@ static net_status build_request_problems(net* n, ServeState* S, Request* r) {
         q.W = r->W[l];
         q.tiles_x = cdiv(q.W, kServeTW);
         q.tiles_y = cdiv(q.H, kServeTH);
+        tc_problem_divisors(q);
         if (L.d.pool != NET_POOL_2X2S1_SAME) cur ^= 1;
     }
     return NET_OK;
