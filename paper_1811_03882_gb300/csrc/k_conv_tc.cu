@@ -823,9 +823,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 released = true;
             };
             if (a.ksplit > 1) {
-                // raw partial sums of this K slice; the reduction applies the epilogue
+                // raw partial sums of this K slice; the reduction applies the
+                // epilogue.  Workspace plane z is tile-major in groups of four
+                // columns ([m_tiles][ncp / 4][128 rows][4]): the 32 rows of a warp
+                // write one contiguous 512-byte run per float4 store.
                 const int ncp = a.n_tiles * BN;
-                float* wr = a.ws + ((size_t)z * a.m_tiles * 128 + (size_t)mt * 128 + row) * ncp + nt * BN + half * HC;
+                float* wr = a.ws + (size_t)z * a.m_tiles * 128 * ncp +
+                            ((size_t)mt * (ncp >> 2) + ((nt * BN + half * HC) >> 2)) * 512 + row * 4;
 #pragma unroll 1
                 for (int c0 = 0; c0 < HC; c0 += 32) {
                     if (nt * BN + half * HC + c0 >= live) break;
@@ -836,7 +840,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     if (c0 + 32 >= HC || nt * BN + half * HC + c0 + 32 >= live) release();
 #pragma unroll
                     for (int j = 0; j < 32; j += 4)
-                        *reinterpret_cast<float4*>(wr + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                        *reinterpret_cast<float4*>(wr + (size_t)((c0 + j) >> 2) * 512) =
+                            make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                 }
             } else {
                 // the single-problem case keeps its fields in registers (read once)

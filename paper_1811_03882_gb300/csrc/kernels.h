@@ -34,6 +34,10 @@ struct SplitReduce {
     int n, H, W;                     // frames and pre-pool size
     void* y;
     Epilogue ep;
+    // 0: each z plane row-major [m_rows][ncols_pad].  1 (tensor-core
+    // launches, 128-row tiles): [m_rows / 128][ncols_pad / 4][128][4], so a
+    // warp that holds one column group of 32 rows writes 512 contiguous bytes.
+    int tile_major;
 };
 cudaError_t splitk_reduce(const SplitReduce& r, cudaStream_t st);
 

@@ -719,7 +719,7 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 if (e == cudaSuccess && r.ksplit > 1) {
                     ++n->pending;
                     SplitReduce sr{n->ws, r.ksplit, r.m_tiles * 128, r.n_tiles * r.BN, r.TW, r.TH,
-                                   cdiv(r.W, r.TW), cdiv(r.H, r.TH), batch, r.H, r.W, y, ep};
+                                   cdiv(r.W, r.TW), cdiv(r.H, r.TH), batch, r.H, r.W, y, ep, 1};
                     e = splitk_reduce(sr, st);
                 }
             } else {
