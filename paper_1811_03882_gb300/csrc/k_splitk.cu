@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256) splitk_tile_reduce_kernel(SplitReduce r) 
         s_b[threadIdx.x] = in ? r.ep.bias[c] : 0.f;
         s_a[threadIdx.x] = in && r.ep.alpha ? r.ep.alpha[c] : 1.f;
     }
-    pdl_wait();   // the partial sums come from the conv launch before this one
+    pdl_wait();   // (a no-op under an ordinary launch)
     {
         // thread -> row rr of the tile and column groups q0, q0 + 2, ..., all
         // eight loads of a plane issued before any is used (memory-level
@@ -268,7 +268,11 @@ cudaError_t splitk_reduce(const SplitReduce& r, cudaStream_t st) {
             if (e != cudaSuccess) return e;
             carve = true;
         }
-        return launch_pdl(splitk_tile_reduce_kernel, grid, dim3(256), 0, st, r);
+        // an ordinary launch: under programmatic launch the blocks become
+        // resident early on the few SMs the conv grid leaves free, several per
+        // SM, and all start there when the conv ends (measured slower)
+        splitk_tile_reduce_kernel<<<grid, 256, 0, st>>>(r);
+        return cudaGetLastError();
     }
     const bool pool = r.ep.pool == POOL_S2;
     const size_t npix = (size_t)r.n * (pool ? r.H / 2 : r.H) * (pool ? r.W / 2 : r.W);
