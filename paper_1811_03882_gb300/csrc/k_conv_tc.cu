@@ -141,6 +141,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int chb) {
            (swz << 61);
 }
 
+// Non-swizzled K-major operand: core matrices of 8 rows x 16 bytes, each
+// 128 contiguous bytes; lbo = byte distance between the two core matrices
+// of one 16-element K step, sbo = distance between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc_plain(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Tap pairs of a pair-mode layer (BF16, 8-channel K chunks, 16 bytes): the
+// nine taps in the order of their A operands' offsets in a tap-merged stage
+// (tap column dx major, tap row dy minor; slot s holds tap (dy, dx) =
+// (s % 3, s / 3)), plus a tenth, all-zero weight slot; MMA j (K = 16) takes
+// slots 2j and 2j + 1.
+constexpr int kPairSlots = 10;
+
 // Instruction descriptor: D = F32, A/B = BF16 (kind::f16) or E4M3
 // (kind::f8f6f4), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 template <int DT>
@@ -319,13 +334,23 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         // written only by the fold at load time, which the host waits for,
         // so these loads may overlap the previous kernel's tail.
         const uint32_t rb = smem_u32(&sm->bres);
-        tc::mbar_expect_tx(rb, (uint32_t)nkb * b_bytes);
-        int ch = 0, tap = 0;
-        for (int ks = 0; ks < nkb; ++ks) {
-            tc::tma_load_2d(smem_u32(sBres + (size_t)ks * b_bytes), &tmB, tap * a.Cp + ch * a.cpc, 0, rb);
-            if (++ch == a.chunks) {
-                ch = 0;
-                ++tap;
+        if (a.pair) {
+            // pair mode: slots in tap-pair order; slot 9 starts at K column
+            // 9 * Cp, past the weights' last column, so TMA fills it with zeros
+            tc::mbar_expect_tx(rb, (uint32_t)kPairSlots * b_bytes);
+            for (int s = 0; s < kPairSlots; ++s) {
+                const int tap = s < 9 ? (s % 3) * 3 + s / 3 : 9;
+                tc::tma_load_2d(smem_u32(sBres + (size_t)s * b_bytes), &tmB, tap * a.Cp, 0, rb);
+            }
+        } else {
+            tc::mbar_expect_tx(rb, (uint32_t)nkb * b_bytes);
+            int ch = 0, tap = 0;
+            for (int ks = 0; ks < nkb; ++ks) {
+                tc::tma_load_2d(smem_u32(sBres + (size_t)ks * b_bytes), &tmB, tap * a.Cp + ch * a.cpc, 0, rb);
+                if (++ch == a.chunks) {
+                    ch = 0;
+                    ++tap;
+                }
             }
         }
     }
@@ -703,7 +728,23 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     tc::fence_after();
                     uint8_t* stg = sRing + (size_t)s * st_bytes;
                     const int nmma = a.chb / 32;   // 32 bytes of K per MMA
-                    if (a.tapm) {
+                    if (a.pair) {
+                        // five MMAs of K = 16, each over two taps: the A core
+                        // matrices of the second tap lie lbo bytes after the
+                        // first's (the same for the tenth, zero-weight slot)
+                        const uint32_t row_b = (uint32_t)a.TW * 16u;
+                        for (int j = 0; j < 5; ++j) {
+                            const int s0 = 2 * j, s1 = 2 * j + 1;
+                            const uint32_t o0 = (uint32_t)(s0 / 3) * a_box + (uint32_t)(s0 % 3) * row_b;
+                            const uint32_t o1 =
+                                s1 < 9 ? (uint32_t)(s1 / 3) * a_box + (uint32_t)(s1 % 3) * row_b : o0;
+                            const uint64_t ad = tc::smem_desc_plain(smem_u32(stg + o0), o1 - o0, 128u);
+                            const uint64_t bd =
+                                tc::smem_desc_plain(smem_u32(sBres + (size_t)s0 * b_bytes), b_bytes, 128u);
+                            tc::mma<DT>(dtm, ad, bd, idesc, (!first || j != 0) ? 1u : 0u);
+                        }
+                        first = false;
+                    } else if (a.tapm) {
                         // nine taps of chunk ks: tap (dy, dx) reads box dx from row dy * TW
                         for (int dx = 0; dx < 3; ++dx)
                             for (int dy = 0; dy < 3; ++dy) {
@@ -1017,12 +1058,15 @@ static EncodeTiled encode_fn() {
 }
 
 static CUtensorMapSwizzle swz_of(int chb) {
-    return chb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : chb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+    return chb == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+           : chb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+           : chb == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                       : CU_TENSOR_MAP_SWIZZLE_NONE;   // 16-byte chunks (pair mode): plain core matrices
 }
 
 int tc_chunk_bytes(int Cp, int dt) {
     const int bytes = Cp * (int)dt_size(dt);
-    return bytes >= 128 ? 128 : bytes;   // Cp is 32/64 bytes or a multiple of 128
+    return bytes >= 128 ? 128 : bytes;   // Cp is 16 (pair mode), 32 or 64 bytes or a multiple of 128
 }
 
 cudaError_t tc_encode_act(CUtensorMap* tm, const void* base, int dt, int n, int H, int W, int Cp, int TW,
@@ -1069,7 +1113,7 @@ static bool tc_geometry(int BN, int chb, int bres, int nk, TcArgs* g) {
     const size_t a_bytes = g->tapm ? 3 * (size_t)(g->TH + 2) * g->TW * chb : 128 * (size_t)chb;
     const size_t b_bytes = (size_t)BN * chb;
     const size_t st = a_bytes + (bres ? 0 : b_bytes);
-    const size_t bres_bytes = bres ? (size_t)nk * b_bytes : 0;
+    const size_t bres_bytes = bres ? (size_t)(g->pair ? tc::kPairSlots : nk) * b_bytes : 0;
     if (tc_avail() < bres_bytes + 2 * st) return false;
     int nst = (int)std::min<size_t>(tc::kMaxStages, (tc_avail() - bres_bytes) / st) & ~1;
     // producer lanes: four per warp on deep rings (stage count cut to a
@@ -1096,6 +1140,11 @@ bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb) {
 template <int BN, int DT, int CS>
 static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int workers, cudaStream_t st) {
     TcArgs a = a0;
+    // 16-byte chunks (K = 8) only in pair mode, and pair mode only in its one shape
+    if ((a.chb == 16) != (a.pair != 0)) return cudaErrorInvalidValue;
+    if (a.pair && (DT != DT_BF16 || CS != 1 || !a.tapm || !a.bres || a.ksplit != 1 || a.k != 3 || a.chunks != 1 ||
+                   a.raw || a.kalt))
+        return cudaErrorInvalidValue;
     if (!tc_geometry(BN, a.chb, a.bres, a.k * a.k * a.chunks, &a)) return cudaErrorInvalidValue;
     if (a.ksplit < 1 || a.n_tiles < 1 || a.chunks < 1 || a.k < 1) return cudaErrorInvalidValue;
     a.fd_ksplit = make_fast_div(a.ksplit);

@@ -13,25 +13,27 @@ static inline unsigned grid_for(size_t n, int threads) {
 }
 
 // ---------------------------------------------------------------- pack
+// One grid row (blockIdx.y) per frame; a thread per (pixel, group of 16
+// bytes); 32-bit indices within a frame (the host checks the size).
 template <int DT>
-__global__ void pack_kernel(const float* __restrict__ x, void* __restrict__ y, int n, int C, int H,
-                            int W, int Cp, float inv_scale) {
+__global__ void pack_kernel(const float* __restrict__ x, void* __restrict__ y, int C, int HW, int Cp,
+                            FastDiv fd_groups, float inv_scale) {
     constexpr int V = DT == DT_F32 ? 4 : DT == DT_BF16 ? 8 : 16;   // elements per 16 B
     const int groups = Cp / V;
-    const size_t HW = (size_t)H * W;
-    const size_t total = (size_t)n * HW * groups;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int g = (int)(i % groups);
-        const size_t pix = i / groups;          // n*HW + yx
-        const size_t nn = pix / HW, yx = pix % HW;
+    const int nn = blockIdx.y;
+    const int total = HW * groups;
+    const float* xf = x + (size_t)nn * C * HW;
+    uint8_t* yf = reinterpret_cast<uint8_t*>(y) + (size_t)nn * HW * Cp * dt_size(DT);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int yx = groups == 1 ? i : fdiv(i, fd_groups);
+        const int g = i - yx * groups;
         float v[V];
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             const int c = g * V + j;
-            v[j] = c < C ? x[(nn * C + c) * HW + yx] : 0.f;
+            v[j] = c < C ? xf[(size_t)c * HW + yx] : 0.f;
         }
-        uint8_t* dst = reinterpret_cast<uint8_t*>(y) + (pix * Cp + (size_t)g * V) * dt_size(DT);
+        uint8_t* dst = yf + ((size_t)yx * Cp + (size_t)g * V) * dt_size(DT);
         if (DT == DT_F32) {
             *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
         } else if (DT == DT_BF16) {
@@ -56,11 +58,18 @@ __global__ void pack_kernel(const float* __restrict__ x, void* __restrict__ y, i
 cudaError_t pack_frames(const float* x, void* y, int n, int C, int H, int W, int Cp, int dt,
                         float inv_scale, cudaStream_t st) {
     const int V = dt == DT_F32 ? 4 : dt == DT_BF16 ? 8 : 16;
-    const size_t total = (size_t)n * H * W * (Cp / V);
-    const unsigned g = grid_for(total, 256);
-    if (dt == DT_F32) pack_kernel<DT_F32><<<g, 256, 0, st>>>(x, y, n, C, H, W, Cp, inv_scale);
-    else if (dt == DT_BF16) pack_kernel<DT_BF16><<<g, 256, 0, st>>>(x, y, n, C, H, W, Cp, inv_scale);
-    else pack_kernel<DT_FP8><<<g, 256, 0, st>>>(x, y, n, C, H, W, Cp, inv_scale);
+    const size_t per = (size_t)H * W * (Cp / V);
+    if (n <= 0 || per == 0) return cudaSuccess;
+    if (per >= (size_t)INT32_MAX || n > 65535 || Cp % V != 0) return cudaErrorInvalidValue;
+    unsigned bx = (unsigned)((per + 255) / 256);
+    const unsigned cap = (152u * 32u + (unsigned)n - 1) / (unsigned)n;   // grid-stride beyond ~32 CTAs per SM
+    if (bx > cap) bx = cap;
+    const dim3 g(bx ? bx : 1, (unsigned)n);
+    const FastDiv fg = make_fast_div(Cp / V);
+    const int HW = H * W;
+    if (dt == DT_F32) pack_kernel<DT_F32><<<g, 256, 0, st>>>(x, y, C, HW, Cp, fg, inv_scale);
+    else if (dt == DT_BF16) pack_kernel<DT_BF16><<<g, 256, 0, st>>>(x, y, C, HW, Cp, fg, inv_scale);
+    else pack_kernel<DT_FP8><<<g, 256, 0, st>>>(x, y, C, HW, Cp, fg, inv_scale);
     return cudaGetLastError();
 }
 

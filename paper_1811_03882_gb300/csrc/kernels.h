@@ -162,6 +162,11 @@ struct TcArgs {
     // TH + 2 rows (one per tap column; the activation map's box is TH + 2
     // rows high), and each tap's A operand starts dy * TW rows into its box.
     int tapm;
+    // pair = 1 (a BF16 3 x 3 first layer over 8 channels: 16-byte K chunks,
+    // tap-merged stages without swizzle, resident weights): each K = 16 MMA
+    // covers two taps, its A descriptor's leading-dimension offset pointing
+    // from the first tap's core matrices to the second's
+    int pair;
     Epilogue ep;
     int* err;     // bounded-wait failure code (0 = none)
     // division by ksplit, n_tiles, chunks, k and nst (filled by conv_tc_launch)

@@ -151,7 +151,16 @@ extern "C" net_status net_create(const net_desc* d, net_t** out) {
         L.in_dt = L.engine == ENG_SIMT ? DT_F32 : prec_dt(L.prec);
         L.in_cs = pad_channels(cin, L.in_dt, L.engine == ENG_TC);
         L.kx = s.k;
-        if (l == 0 && L.engine == ENG_TC && L.in_dt == DT_BF16 && s.k == 3 && cin * 9 <= 32) {
+        static const bool pair_on = [] {
+            const char* e = getenv("NET_L0_PAIR");
+            return !(e && atoi(e) == 0);
+        }();
+        if (l == 0 && L.engine == ENG_TC && L.in_dt == DT_BF16 && s.k == 3 && cin <= 8 && pair_on) {
+            // first layer on few channels: channels padded to 8 (16 bytes a
+            // pixel), nine taps as five MMAs of two taps each (K = 16)
+            L.pair = true;
+            L.in_cs = 8;
+        } else if (l == 0 && L.engine == ENG_TC && L.in_dt == DT_BF16 && s.k == 3 && cin * 9 <= 32) {
             // first layer on few channels: fold its 9 taps into 32 channels at
             // pack time and run it as a 1x1 conv (one 64-byte K chunk per tile
             // instead of nine 32-byte ones)
@@ -479,7 +488,7 @@ void dn::tc_tile_options(const net* n, int l, std::vector<std::pair<int, int>>* 
     for (int bn : {64, 128, 256}) {
         if (bn > rup(ncols, 64)) continue;
         for (int ks : {1, 2, 4, 8, 16})
-            if (ks == 1 || ks * 4 <= nk) opts->push_back({bn, ks});
+            if (ks == 1 || (ks * 4 <= nk && !L.pair)) opts->push_back({bn, ks});
     }
 }
 
@@ -521,6 +530,10 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
         }
         if (L.engine == ENG_TC) {
             tc_choose(batch, r.H, r.W, L.d.pool == NET_POOL_2X2S2, ncols, n->num_sms, &r.TW, &r.TH, &r.BN);
+            if (L.pair && !((r.TW == 16 && r.TH == 8) || (r.TW == 8 && r.TH == 16))) {
+                r.TW = 16;   // pair mode runs on tap-merged 16 x 8 stages
+                r.TH = 8;
+            }
             r.m_tiles = batch * cdiv(r.H, r.TH) * cdiv(r.W, r.TW);
             const int nk = KK * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
             tc_choose_split(r.m_tiles, ncols, nk, n->num_sms, &r.BN, &r.ksplit);
@@ -528,6 +541,7 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             // for the layer's current format
             if (L.tile_bn > 0 && L.tile_bn <= rup(ncols, 64)) r.BN = L.tile_bn;
             if (L.tile_ks == 1 || (L.tile_ks > 1 && L.tile_ks * 4 <= nk)) r.ksplit = L.tile_ks;
+            if (L.pair) r.ksplit = 1;
             r.n_tiles = cdiv(ncols, r.BN);
             const int tiles = r.m_tiles * r.n_tiles;
             if (r.ksplit > 1)
@@ -554,6 +568,10 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
                           ((r.TW == 16 && r.TH == 8) || (r.TW == 8 && r.TH == 16)))
                              ? 1
                              : 0;
+                if (L.pair) {
+                    if (!r.bres) return fail(NET_E_UNSUPPORTED, "layer %d: pair mode needs resident weights", l);
+                    r.tapm = 1;
+                }
                 const int steps = r.tapm ? nk / 9 : nk;   // pipeline steps per tile
                 const int items = cdiv(r.m_tiles, r.cs) * r.n_tiles * r.ksplit;
                 r.kalt = (kalt_on && items <= r.grid && steps / r.ksplit >= 2) ? 1 : 0;
@@ -582,9 +600,9 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             if (dump)
                 fprintf(stderr,
                         "plan b%d %dx%d layer %d: tile %dx%d BN %d m_tiles %d n_tiles %d ksplit %d cs %d grid %d "
-                        "bres %d kalt %d tapm %d\n",
+                        "bres %d kalt %d tapm %d pair %d\n",
                         batch, h, w, l, r.TW, r.TH, r.BN, r.m_tiles, r.n_tiles, r.ksplit, r.cs, r.grid, r.bres, r.kalt,
-                        r.tapm);
+                        r.tapm, L.pair ? 1 : 0);
         }
         P->runs.push_back(r);
         if (L.d.pool != NET_POOL_2X2S1_SAME) cur ^= 1;
@@ -708,6 +726,7 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.bres = r.bres;
                 a.kalt = r.kalt;
                 a.tapm = r.tapm;
+                a.pair = L.pair ? 1 : 0;
                 if (l == 0 && raw0) {
                     a.raw = 1;
                     a.raw_c = n->in_c;

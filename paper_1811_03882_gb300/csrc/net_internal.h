@@ -23,6 +23,7 @@ struct Layer {
     int engine = 0;      // ENG_SIMT or ENG_TC
     int kx = 0;          // kernel size the conv kernel runs (1 for an im2col-packed layer)
     int im2col_k = 0;    // k > 0: the input is packed im2col-style (taps folded into channels)
+    bool pair = false;   // BF16 3x3 first layer over 8 channels, two taps per MMA (TcArgs::pair)
     int in_dt = 0;       // storage dtype of this layer's input activation
     int in_cs = 0;       // its channel stride (padded channels)
     int w_rows = 0;      // allocated weight rows (zero beyond cout)

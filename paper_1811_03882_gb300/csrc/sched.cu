@@ -127,13 +127,17 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
                 r.TH = th;
             }
         }
+        if (L.pair) {   // pair mode: tap-merged 16 x 8 stages
+            r.TW = 16;
+            r.TH = 8;
+        }
         std::vector<ConvProblem> probs(cnt);
         int mt = 0;
         for (int f = 0; f < cnt; ++f) {
             ConvProblem& q = probs[f];
             std::memset(&q, 0, sizeof q);
             cudaError_t e = tc_encode_act(&q.tmA, bufp(cur, off[l][f]), L.in_dt, 1, H[f][l], W[f][l], L.in_cs,
-                                          r.TW, r.TH);
+                                          r.TW, L.pair ? r.TH + 2 : r.TH);
             if (e != cudaSuccess) return fail(NET_E_CUDA, "layer %d frame %d tensor map", l, f);
             q.x = bufp(cur, off[l][f]);
             q.y = last ? (void*)d_out[f] : bufp(cur ^ 1, off[l + 1][f]);
@@ -154,6 +158,8 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
         r.n_tiles = cdiv(ncols, r.BN);
         tc_workers(r.m_tiles, r.n_tiles, 1, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, &r.cs, &r.grid,
                    &r.bres);
+        if (L.pair && !r.bres) return fail(NET_E_UNSUPPORTED, "layer %d: pair mode needs resident weights", l);
+        r.tapm = L.pair ? 1 : 0;
         cudaError_t e = cudaMalloc(&r.d_prob, sizeof(ConvProblem) * cnt);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(r.d_prob, probs.data(), sizeof(ConvProblem) * cnt, cudaMemcpyHostToDevice, n->stream);
@@ -208,6 +214,8 @@ static net_status enqueue_uplan(net* n, UPlan* P, int cnt, int* kernels) {
         a.ksplit = 1;
         a.ws = nullptr;
         a.bres = r.bres;
+        a.tapm = r.tapm;
+        a.pair = L.pair ? 1 : 0;
         a.err = n->err_dev;
         a.ep.bias = L.bias;
         a.ep.alpha = L.in_dt == DT_FP8 ? L.alpha : nullptr;

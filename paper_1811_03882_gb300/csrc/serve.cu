@@ -183,8 +183,9 @@ static net_status build_request_problems(net* n, ServeState* S, Request* r) {
         ConvProblem& q = r->probs[l];
         std::memset(&q, 0, sizeof q);
         if (L.engine == ENG_TC) {
+            // pair mode (tap-merged stages): boxes of TH + 2 rows
             cudaError_t e = tc_encode_act(&q.tmA, half_ptr(n, S, r, cur), L.in_dt, 1, r->H[l], r->W[l], L.in_cs,
-                                          kServeTW, kServeTH);
+                                          kServeTW, L.pair ? kServeTH + 2 : kServeTH);
             if (e != cudaSuccess) return fail(NET_E_CUDA, "serve: tensor map");
         }
         q.x = half_ptr(n, S, r, cur);
@@ -352,6 +353,9 @@ static net_status enqueue_step(net* n, ServeState* S, StepSlot& sl) {
             a.err = n->err_dev;
             P.BN = BN;
             tc_workers(mt, a.n_tiles, 1, BN, nk, a.chb, n->num_sms, &P.cs, &P.workers, &a.bres);
+            // pair mode needs resident weights (the launch refuses it otherwise)
+            a.tapm = L.pair ? 1 : 0;
+            a.pair = L.pair ? 1 : 0;
             ntab += na;
         }
         if (L.d.pool == NET_POOL_2X2S1_SAME && !last) {

@@ -3,7 +3,9 @@ switches are read once per process): 2-CTA clusters sharing the weight box
 (NET_TC_CLUSTER=2), K-alternating MMA issuers off (NET_TC_KALT=0),
 programmatic dependent launch off (NET_PDL=0) and the first layer's
 in-kernel im2col off (NET_RAW_L0=0: a pack kernel writes the im2col buffer
-and TMA loads it) and tap-merged stages off (NET_TC_TAPM=0).  Every mode must give the
+and TMA loads it) and tap-merged stages off (NET_TC_TAPM=0); the first layer as two taps
+per MMA over 8-channel pixels (default) or as an im2col tile of 32
+channels (NET_L0_PAIR=0), built in the kernel or by the pack kernel.  Every mode must give the
 oracle's answer within the BF16 budget and agree with the default mode to
 BF16 rounding; the 19-conv network at 2 x 160 x 160 has layers with one and
 with several work items per CTA, split-K layers and resident-weight
@@ -63,7 +65,8 @@ def test_launch_modes_match_oracle(tmp_path):
     ys = {}
     for name, env in (("default", {}), ("cluster2", {"NET_TC_CLUSTER": "2"}),
                       ("no_kalt", {"NET_TC_KALT": "0"}), ("no_pdl", {"NET_PDL": "0"}),
-                      ("no_raw", {"NET_RAW_L0": "0"}), ("no_tapm", {"NET_TC_TAPM": "0"})):
+                      ("raw", {"NET_L0_PAIR": "0"}), ("pack", {"NET_L0_PAIR": "0", "NET_RAW_L0": "0"}),
+                      ("no_tapm", {"NET_TC_TAPM": "0"})):
         y = _run(tmp_path, name, env)
         assert np.isfinite(y).all(), name
         e = oracle.normwise_rel_err(y, ex)
@@ -73,6 +76,7 @@ def test_launch_modes_match_oracle(tmp_path):
     # programmatic launch changes only when kernels start, never what they add;
     # the in-kernel im2col builds the same BF16 tile the pack kernel writes
     np.testing.assert_array_equal(ys["no_pdl"], ys["default"])
-    np.testing.assert_array_equal(ys["no_raw"], ys["default"])
-    for name in ("cluster2", "no_kalt", "no_tapm"):
+    np.testing.assert_array_equal(ys["raw"], ys["pack"])
+    # the first layer's tap pairs sum the same products in another order
+    for name in ("cluster2", "no_kalt", "no_tapm", "raw"):
         assert oracle.normwise_rel_err(ys[name], ys["default"]) <= 2e-2, name
