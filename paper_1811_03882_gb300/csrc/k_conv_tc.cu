@@ -848,10 +848,19 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 float u[16];
                 tc::tmem_ld16(taddr, u);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] += u[j];
+                for (int j = 0; j < 8; ++j) {
+                    const float2 r = __fadd2_rn(make_float2(v[2 * j], v[2 * j + 1]), make_float2(u[2 * j], u[2 * j + 1]));
+                    v[2 * j] = r.x;
+                    v[2 * j + 1] = r.y;
+                }
                 tc::tmem_ld16(taddr + 16u, u);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[16 + j] += u[j];
+                for (int j = 0; j < 8; ++j) {
+                    const float2 r =
+                        __fadd2_rn(make_float2(v[16 + 2 * j], v[17 + 2 * j]), make_float2(u[2 * j], u[2 * j + 1]));
+                    v[16 + 2 * j] = r.x;
+                    v[17 + 2 * j] = r.y;
+                }
             };
             bool released = false;
             auto release = [&] {
@@ -930,24 +939,40 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     tc::tmem_ld32(trow + (uint32_t)c0, v);
                     if (a.kalt) add_pair(trow + (uint32_t)(BN + c0), v);
                     if (c0 + 32 >= HC || o0 + 32 >= live) release();
-                    // warp-uniform branches: each variant is one straight-line loop
+                    // warp-uniform branches: each variant is one straight-line loop.
+                    // Paired FP32 operations (two lanes of a register pair per
+                    // instruction) round exactly as the scalar ones.
                     if (a.ep.alpha) {
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
                             const float4 t = reinterpret_cast<const float4*>(e_alpha + o0)[j];
-                            v[4 * j] = fmaf(v[4 * j], t.x, bb[4 * j]);
-                            v[4 * j + 1] = fmaf(v[4 * j + 1], t.y, bb[4 * j + 1]);
-                            v[4 * j + 2] = fmaf(v[4 * j + 2], t.z, bb[4 * j + 2]);
-                            v[4 * j + 3] = fmaf(v[4 * j + 3], t.w, bb[4 * j + 3]);
+                            const float2 lo = __ffma2_rn(make_float2(v[4 * j], v[4 * j + 1]), make_float2(t.x, t.y),
+                                                         make_float2(bb[4 * j], bb[4 * j + 1]));
+                            const float2 hi = __ffma2_rn(make_float2(v[4 * j + 2], v[4 * j + 3]), make_float2(t.z, t.w),
+                                                         make_float2(bb[4 * j + 2], bb[4 * j + 3]));
+                            v[4 * j] = lo.x;
+                            v[4 * j + 1] = lo.y;
+                            v[4 * j + 2] = hi.x;
+                            v[4 * j + 3] = hi.y;
                         }
                     } else {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] += bb[j];
+                        for (int j = 0; j < 16; ++j) {
+                            const float2 r = __fadd2_rn(make_float2(v[2 * j], v[2 * j + 1]),
+                                                        make_float2(bb[2 * j], bb[2 * j + 1]));
+                            v[2 * j] = r.x;
+                            v[2 * j + 1] = r.y;
+                        }
                     }
                     if (a.ep.act == ACT_LEAKY) {
                         // leaky(v) = max(v, 0.1 v): v for v > 0, 0.1 v otherwise
+                        const float2 slope = make_float2(kLeakySlope, kLeakySlope);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j], kLeakySlope * v[j]);
+                        for (int j = 0; j < 16; ++j) {
+                            const float2 s2 = __fmul2_rn(make_float2(v[2 * j], v[2 * j + 1]), slope);
+                            v[2 * j] = fmaxf(v[2 * j], s2.x);
+                            v[2 * j + 1] = fmaxf(v[2 * j + 1], s2.y);
+                        }
                     }
                     if (a.ep.out_layout == LAYOUT_NCHW) {
                         if (pool) {
