@@ -45,7 +45,7 @@ DEFAULT = "19conv-448-b8-bf16"
 # bytes, averaged over the family's launches in one forward pass of the
 # default workload), from the capture summarised in
 # profiles/conv_tc_19conv_448_b8_bf16.md; None where not captured.
-TRAFFIC = {"19conv-448-b8-bf16": {"tc_bf16": 202.3e6 / 19}}
+TRAFFIC = {"19conv-448-b8-bf16": {"tc_bf16": 208.7e6 / 19}}
 
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 
