@@ -155,9 +155,11 @@ extern "C" net_status net_create(const net_desc* d, net_t** out) {
             const char* e = getenv("NET_L0_PAIR");
             return !(e && atoi(e) == 0);
         }();
-        if (l == 0 && L.engine == ENG_TC && L.in_dt == DT_BF16 && s.k == 3 && cin <= 8 && pair_on) {
+        if (l == 0 && L.engine == ENG_TC && L.in_dt == DT_BF16 && s.k == 3 && cin <= 8 && s.cout <= 256 &&
+            pair_on) {
             // first layer on few channels: channels padded to 8 (16 bytes a
-            // pixel), nine taps as five MMAs of two taps each (K = 16)
+            // pixel), nine taps as five MMAs of two taps each (K = 16); one
+            // N tile of at most 256 columns keeps its weights resident
             L.pair = true;
             L.in_cs = 8;
         } else if (l == 0 && L.engine == ENG_TC && L.in_dt == DT_BF16 && s.k == 3 && cin * 9 <= 32) {
@@ -487,6 +489,7 @@ void dn::tc_tile_options(const net* n, int l, std::vector<std::pair<int, int>>* 
     const int nk = L.kx * L.kx * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
     for (int bn : {64, 128, 256}) {
         if (bn > rup(ncols, 64)) continue;
+        if (L.pair && bn < ncols) continue;   // pair mode: one N tile
         for (int ks : {1, 2, 4, 8, 16})
             if (ks == 1 || (ks * 4 <= nk && !L.pair)) opts->push_back({bn, ks});
     }
@@ -541,7 +544,10 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             // for the layer's current format
             if (L.tile_bn > 0 && L.tile_bn <= rup(ncols, 64)) r.BN = L.tile_bn;
             if (L.tile_ks == 1 || (L.tile_ks > 1 && L.tile_ks * 4 <= nk)) r.ksplit = L.tile_ks;
-            if (L.pair) r.ksplit = 1;
+            if (L.pair) {   // one N tile, no K split: the weights stay resident
+                r.ksplit = 1;
+                while (r.BN < ncols && r.BN < 256) r.BN *= 2;
+            }
             r.n_tiles = cdiv(ncols, r.BN);
             const int tiles = r.m_tiles * r.n_tiles;
             if (r.ksplit > 1)

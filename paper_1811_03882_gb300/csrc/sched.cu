@@ -155,6 +155,8 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
         const int nk = L.kx * L.kx * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
         // grouped launches do not split K; pick the N tile for ks = 1
         tc_choose_split(mt, ncols, nk, n->num_sms, &r.BN, &ks_unused, 1);
+        if (L.pair)   // one N tile: the weights stay resident
+            while (r.BN < ncols && r.BN < 256) r.BN *= 2;
         r.n_tiles = cdiv(ncols, r.BN);
         tc_workers(r.m_tiles, r.n_tiles, 1, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, &r.cs, &r.grid,
                    &r.bres);

@@ -336,6 +336,8 @@ static net_status enqueue_step(net* n, ServeState* S, StepSlot& sl) {
             const int nk = L.kx * L.kx * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
             int BN = 128, ks = 1;
             tc_choose_split(mt, ncols, nk, n->num_sms, &BN, &ks, 1);
+            if (L.pair)   // one N tile: the weights stay resident
+                while (BN < ncols && BN < 256) BN *= 2;
             TcArgs& a = P.a;
             a.probs = dt + ntab;
             a.nprob = na;

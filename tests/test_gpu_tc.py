@@ -75,6 +75,10 @@ def test_bf16_single_tc_layer():
     (128, 64, 1, synth.POOL_NONE, (28, 28)),    # 1x1
     (256, 256, 3, synth.POOL_2X2S2, (16, 16)),  # two K chunks per tap, BN 256 region
     (96, 1000, 1, synth.POOL_NONE, (14, 14)),   # N tail: 1000 outputs
+    # first layers over few channels: two taps per MMA (8-channel pixels)
+    (3, 128, 3, synth.POOL_2X2S2, (40, 56)),    # one 128-column N tile, pool, ragged x
+    (3, 256, 3, synth.POOL_NONE, (20, 36)),     # N tile widened to 256, 16 x 8 tiles on a 20-wide map
+    (5, 48, 3, synth.POOL_NONE, (17, 23)),      # five channels, odd map
 ])
 def test_bf16_layer_shapes(cin, cout, k, pool, hw):
     L = synth.Layer
