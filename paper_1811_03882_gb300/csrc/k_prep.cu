@@ -55,8 +55,49 @@ __global__ void pack_kernel(const float* __restrict__ x, void* __restrict__ y, i
     }
 }
 
+// BF16, at most 8 channels padded to 8 (one 16-byte group per pixel), the
+// frame's pixel count a multiple of 4: a thread packs four adjacent pixels
+// from one float4 load per channel and stores their 64 contiguous bytes.
+__global__ void pack_bf16_c8_px4_kernel(const float* __restrict__ x, void* __restrict__ y, int C, int HW4) {
+    const int nn = blockIdx.y;
+    const int HW = HW4 * 4;
+    const float4* xf = reinterpret_cast<const float4*>(x + (size_t)nn * C * HW);
+    uint4* yf = reinterpret_cast<uint4*>(y) + (size_t)nn * HW;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < HW4; i += gridDim.x * blockDim.x) {
+        float v[8][4];   // [channel][pixel]
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float4 t = c < C ? xf[(size_t)c * HW4 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[c][0] = t.x;
+            v[c][1] = t.y;
+            v[c][2] = t.z;
+            v[c][3] = t.w;
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            uint4 pk;
+            uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j][p], v[2 * j + 1][p]);
+                w[j] = *reinterpret_cast<uint32_t*>(&b);
+            }
+            yf[(size_t)4 * i + p] = pk;
+        }
+    }
+}
+
 cudaError_t pack_frames(const float* x, void* y, int n, int C, int H, int W, int Cp, int dt,
                         float inv_scale, cudaStream_t st) {
+    if (dt == DT_BF16 && Cp == 8 && C <= 8 && n > 0 && n <= 65535 && ((size_t)H * W) % 4 == 0 &&
+        (size_t)H * W < (size_t)INT32_MAX && ((uintptr_t)x & 15) == 0 && ((uintptr_t)y & 15) == 0) {
+        const int HW4 = H * W / 4;
+        unsigned bx = (unsigned)((HW4 + 255) / 256);
+        const unsigned cap = (152u * 32u + (unsigned)n - 1) / (unsigned)n;
+        if (bx > cap) bx = cap;
+        pack_bf16_c8_px4_kernel<<<dim3(bx ? bx : 1, (unsigned)n), 256, 0, st>>>(x, y, C, HW4);
+        return cudaGetLastError();
+    }
     const int V = dt == DT_F32 ? 4 : dt == DT_BF16 ? 8 : 16;
     const size_t per = (size_t)H * W * (Cp / V);
     if (n <= 0 || per == 0) return cudaSuccess;
