@@ -215,7 +215,11 @@ net_status net_tune_precision(net_t* net, const float* d_frames, int batch, int 
  * (net_forward*): N tile bn in {64, 128, 256} and split-K factor ksplit in
  * {1, 2, 4, 8, 16}; 0 keeps the analytic choice.  A value the layer cannot take
  * (bn above its padded output columns, ksplit with fewer than four K steps
- * per slice) is NET_E_INVAL.  Captured graphs and plans are rebuilt. */
+ * per slice) is NET_E_INVAL.  A BF16 3x3 first layer over at most 8 input
+ * channels and at most 256 outputs runs as tap pairs (two taps per MMA over
+ * 8-channel pixels) with its weights resident in shared memory: it takes
+ * ksplit 1 and an N tile that covers all of its output columns only.
+ * Captured graphs and plans are rebuilt. */
 net_status net_set_layer_tiles(net_t* net, int layer, int bn, int ksplit);
 
 /* The tile plan the fixed-batch path uses for a batch x h x w pass, after
