@@ -735,7 +735,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     if (a.pair) {
                         // five MMAs of K = 16, each over two taps: the A core
                         // matrices of the second tap lie lbo bytes after the
-                        // first's (the same for the tenth, zero-weight slot)
+                        // first's (for the tenth, zero-weight slot lbo is 0:
+                        // the ninth tap's rows are read twice)
                         const uint32_t row_b = (uint32_t)a.TW * 16u;
                         for (int j = 0; j < 5; ++j) {
                             const int s0 = 2 * j, s1 = 2 * j + 1;
@@ -944,8 +945,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     if (a.kalt) add_pair(trow + (uint32_t)(BN + c0), v);
                     if (c0 + 32 >= HC || o0 + 32 >= live) release();
                     // warp-uniform branches: each variant is one straight-line loop.
-                    // Paired FP32 operations (two lanes of a register pair per
-                    // instruction) round exactly as the scalar ones.
+                    // Paired FP32 operations (one instruction on a register
+                    // pair) round exactly as the scalar ones.
                     if (a.ep.alpha) {
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
