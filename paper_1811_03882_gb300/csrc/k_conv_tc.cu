@@ -43,8 +43,6 @@ constexpr int THREADS = 384;   // producer, MMA issuer, 8 epilogue warps, second
 constexpr int NUM_WARPS = THREADS / 32;
 constexpr int kMaxStages = 32;                // ring stages (bit masks below are 32 bits)
 constexpr int kEpiCols = 1024;                // bias / alpha columns kept in shared memory
-constexpr int kRawHalo = 3 * 20 * 10;         // raw first layer: 3 channels x (8+2) rows x 20 (16+2 columns, padded)
-constexpr int kRawBufs = 4;                   // raw first layer: halo buffers per producer warp
 constexpr long long WAIT_LIMIT = 4000000000LL;  // clock64 cycles (~2 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -114,27 +112,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int 
         : "memory");
 }
 
-// Multicast variant: the box lands at the same smem offset of every CTA in
-// `mask` and completes bytes on each destination's barrier at `bar`.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const void* tmap, int c0, int c1, uint32_t bar,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
-        "l"(tmap), "r"(c0), "r"(c1), "r"(bar), "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 // Shared-memory matrix descriptor (tcgen05), K-major operand with 32/64/128
 // byte swizzle: start >> 4, leading offset (unused for swizzled K-major) 16,
 // stride offset = 8 rows * row bytes, fixed version bits 46..48 = 0b001.
@@ -189,13 +166,6 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bd
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
-}
-
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-        "h"(mask)
-        : "memory");
 }
 
 __device__ __forceinline__ void fence_before() {
@@ -258,10 +228,7 @@ struct Smem {
 
 }  // namespace tc
 
-// CS = cluster size: with CS = 2 the two CTAs of a cluster work on
-// neighbouring M tiles of the same N tile, and each loads half of the
-// weight (B) box and multicasts it to both, halving the B traffic from L2.
-template <int BN, int DT, int CS>
+template <int BN, int DT>
 __global__ void __launch_bounds__(tc::THREADS, 1)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     using namespace tc;
@@ -282,20 +249,15 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     // epilogue copies of bias / alpha (launches with at most kEpiCols columns)
     float* s_bias = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(sm) + ((sizeof(Smem) + 15) & ~(size_t)15));
     float* s_alpha = s_bias + kEpiCols;
-    float* s_raw = s_alpha + kEpiCols;   // raw mode: kRawBufs input-halo buffers per producer warp
 
     pdl_trigger();   // the next kernel may start its prologue as SMs free up
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int KK = a.k * a.k;
     const int nkb = KK * a.chunks;                // weight boxes (tap, chunk) per tile
     const int nk = a.tapm ? a.chunks : nkb;       // pipeline steps per tile
-    // work items: (group of CS m-tiles, n-tile, K slice); a cluster takes one
-    // item at a time and CTA `rank` of it the m-tile group*CS + rank
-    const int rank = CS > 1 ? (int)tc::cluster_rank() : 0;
-    const int worker = blockIdx.x / CS, nworkers = gridDim.x / CS;
-    const int m_groups = (a.m_tiles + CS - 1) / CS;
-    const int total = m_groups * a.n_tiles * a.ksplit;
-    const uint16_t cmask = (uint16_t)((1u << CS) - 1u);
+    // work items: (m-tile, n-tile, K slice), taken round robin by the CTAs
+    const int worker = blockIdx.x, nworkers = gridDim.x;
+    const int total = a.m_tiles * a.n_tiles * a.ksplit;
     const int pad = a.k >> 1;
     // A bytes per stage: one 128-row box, or three (TH + 2)-row boxes (tapm)
     const uint32_t a_box = a.tapm ? (uint32_t)(a.TH + 2) * a.TW * a.chb : 128u * a.chb;
@@ -306,7 +268,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         for (int s = 0; s < nst; ++s) {
             tc::mbar_init(smem_u32(&sm->full[0][s]), 1);
             tc::mbar_init(smem_u32(&sm->full[1][s]), 1);
-            tc::mbar_init(smem_u32(&sm->empty[s]), CS);   // every consumer of the cluster frees a stage
+            tc::mbar_init(smem_u32(&sm->empty[s]), 1);
         }
         for (int b = 0; b < NBUF; ++b) {
             tc::mbar_init(smem_u32(&sm->accf[b]), 1);
@@ -327,8 +289,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc::fence_before();
-    if (CS > 1) tc::cluster_sync();   // peers' barriers exist before any multicast
-    else __syncthreads();
+    __syncthreads();
     tc::fence_after();
     const uint32_t tmem_base = sm->tmem;
     volatile int* abort_flag = &sm->abort;
@@ -361,10 +322,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     __syncwarp();
     // the prologue above may overlap the previous kernel; activations and
     // split-K workspace are touched only after it ended.  The TMA producers
-    // of the im2col-by-TMA path wait further down, after the weight box of
-    // their first K step is on its way (weights and problem tables are
-    // complete before the forward pass starts).
-    const bool lane_producer = (warp == 0 || warp == NUM_WARPS - 2) && !a.raw;
+    // wait further down, after the weight box of their first K step is on its
+    // way (weights and problem tables are complete before the forward pass
+    // starts).
+    const bool lane_producer = warp == 0 || warp == NUM_WARPS - 2;
     if (!lane_producer) pdl_wait();
 
     if (warp == 0 || warp == NUM_WARPS - 2) {
@@ -378,135 +339,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         const int pid = warp == 0 ? 0 : 1;
         const int G = a.plane;
         const int S2 = 2 * G;
-        if (a.raw) {
-            // ---- software im2col of the first layer: this warp fills the A
-            // tiles of its K steps (one per tile, every other tile) from the
-            // raw frames.
-            // The smem image is what a SWIZZLE_64B TMA box would write: row r
-            // at r*64 bytes, 16-byte unit u of the row stored at unit
-            // u ^ ((r >> 1) & 3).
-            const ConvProblem* P = a.probs;
-            const int H = P->H, W = P->W;
-            const int tiles_x = P->tiles_x, tiles_y = P->tiles_y;
-            // the halo of a 16 x 8 tile, three channels: 3 x 10 x 18 floats,
-            // element e -> (c, hy, hx); lane l holds elements l + 32k
-            // staged with a row pitch of HP = 20 floats (80 bytes, 16-byte aligned rows)
-            constexpr int HW = 18, HH = 10, HP = 20, HN = 3 * HH * HW, PER = (HN + 31) / 32;
-            // two halo buffers per warp, filled by cp.async (global -> shared,
-            // out-of-frame elements zero-filled) one tile ahead of the build
-            auto prefetch = [&](int tile, float* hal) {
-                if (tile < total) {
-                    const int txy = fdiv(tile, P->fd_tx);
-                    const int tx = tile - txy * tiles_x;
-                    const int img = fdiv(txy, P->fd_ty);
-                    const int ty = txy - img * tiles_y;
-                    const int y0 = ty * 8 - 1, x0 = tx * 16 - 1;
-                    const float* X = a.x_raw + (size_t)img * 3 * H * W;
-#pragma unroll
-                    for (int k = 0; k < PER; ++k) {
-                        const int e = lane + 32 * k;
-                        if (e < HN) {
-                            const int c = e / (HH * HW), rem = e - c * (HH * HW);
-                            const int hy = rem / HW, hx = rem - hy * HW;
-                            const int yy = y0 + hy, xx = x0 + hx;
-                            const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
-                            const float* src = in ? X + ((size_t)c * H + yy) * W + xx : X;
-                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(
-                                             smem_u32(hal + (c * HH + hy) * HP + hx)),
-                                         "l"(src), "r"(in ? 4 : 0)
-                                         : "memory");
-                        }
-                    }
-                }
-                asm volatile("cp.async.commit_group;" ::: "memory");   // (an empty group past the last tile)
-            };
-            int ps = pid;
-            uint32_t eph = 0u;
-            bool ok = true;
-            int t = pid, tile = worker + pid * nworkers;
-            const int step2 = 2 * nworkers;   // this warp's tiles: every other tile of the CTA
-            // kRawBufs halo buffers per warp: tiles kRawBufs - 1 ahead in flight
-            int hb = 0;                        // halo buffer of the current tile
-            for (int d = 0; d < kRawBufs - 1; ++d) prefetch(tile + d * step2, s_raw + (kRawBufs * pid + d) * kRawHalo);
-            // lane l builds the four pixels (l / 4, 4 (l % 4) .. 4 (l % 4) + 3) of
-            // the 16 x 8 tile: per channel and tap row one 16-byte and one
-            // 8-byte shared load give the six halo columns those pixels read
-            const int bpy = lane >> 2, bpx = (lane & 3) * 4;
-            // one tile: prefetch the halo kRawBufs - 1 tiles ahead into the buffer
-            // the previous tile used, build this tile's A tile from its halo,
-            // hand it to MMA issuer t & 1
-            auto one = [&]() -> bool {
-                if (tile >= total || !ok) return false;
-                __syncwarp();   // the previous build's reads of its buffer are done
-                const int pb = hb == 0 ? kRawBufs - 1 : hb - 1;   // that buffer
-                prefetch(tile + (kRawBufs - 1) * step2, s_raw + (kRawBufs * pid + pb) * kRawHalo);
-                asm volatile("cp.async.wait_group %0;" ::"n"(kRawBufs - 1) : "memory");   // this tile's halo landed
-                __syncwarp();
-                const float* hal = s_raw + (kRawBufs * pid + hb) * kRawHalo;
-                if (!tc::mbar_wait(smem_u32(&sm->empty[ps]), eph ^ 1u, abort_flag, a.err, 1)) {
-                    ok = false;
-                    return false;
-                }
-                uint8_t* stg = sRing + (size_t)ps * st_bytes;
-                float f[3][3][6];   // [channel][tap row][halo column bpx .. bpx + 5]
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int kh = 0; kh < 3; ++kh) {
-                        const float* src = hal + (c * HH + bpy + kh) * HP + bpx;
-                        const float4 q4 = *reinterpret_cast<const float4*>(src);
-                        const float2 q2 = *reinterpret_cast<const float2*>(src + 4);
-                        f[c][kh][0] = q4.x;
-                        f[c][kh][1] = q4.y;
-                        f[c][kh][2] = q4.z;
-                        f[c][kh][3] = q4.w;
-                        f[c][kh][4] = q2.x;
-                        f[c][kh][5] = q2.y;
-                    }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int r = bpy * 16 + bpx + j;
-                    // element q = (kh*3 + kw)*3 + c (three channels), zero from 27 on
-                    float v[32];
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) v[q] = q < 27 ? f[q % 3][q / 9][j + (q / 3) % 3] : 0.f;
-                    uint8_t* row = stg + r * 64;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        uint32_t w4[4];
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * u + 2 * h], v[8 * u + 2 * h + 1]);
-                            w4[h] = *reinterpret_cast<uint32_t*>(&b2);
-                        }
-                        *reinterpret_cast<uint4*>(row + ((u ^ ((r >> 1) & 3)) << 4)) =
-                            make_uint4(w4[0], w4[1], w4[2], w4[3]);
-                    }
-                }
-                // generic-proxy writes made visible to the tensor core's async proxy
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(smem_u32(&sm->full[t & 1][ps]));
-                ps += 2;
-                if (ps >= nst) {
-                    ps -= nst;
-                    eph ^= 1u;
-                }
-                t += 2;
-                tile += step2;
-                hb = hb + 1 == kRawBufs ? 0 : hb + 1;
-                return true;
-            };
-            while (one()) {
-            }
-            asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the kernel
-            if (a.bres && pid == 0 && lane == 0 &&
-                !tc::mbar_wait(smem_u32(&sm->bres), 0u, abort_flag, a.err, 5)) {
-                const long long t0 = clock64();
-                while (!tc::mbar_try(smem_u32(&sm->bres), 0u) && clock64() - t0 < WAIT_LIMIT) {
-                }
-            }
-        } else if (lane < G) {
+        if (lane < G) {
             const unsigned gmask = (1u << G) - 1u;
             // a single-problem launch keeps the problem's fields in registers
             const ConvProblem* P1 = a.nprob == 1 ? a.probs : nullptr;
@@ -538,7 +371,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             auto setup = [&] {   // coordinates of the lane's current tile
                 const int mn = a.ksplit > 1 ? fdiv(tile, a.fd_ksplit) : tile;
                 const int mq = fdiv(mn, a.fd_ntiles);
-                const int mt = mq * CS + rank;
+                const int mt = mq;
                 nt = mn - mq * a.n_tiles;
                 towner = t & 1;
                 if (!P1) {
@@ -603,7 +436,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             // kernel: its stage is free, so it is armed for the whole step and
             // the box is issued before the dependency wait
             bool pre_b = false;
-            if (!a.bres && CS == 1 && tile < total) {
+            if (!a.bres && tile < total) {
                 const int owner = a.kalt ? ((ks - ks0) & 1) : towner;
                 const uint32_t fb = smem_u32(&sm->full[owner][ps]);
                 tc::mbar_expect_tx(fb, a_bytes + b_bytes);
@@ -642,12 +475,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     }
                     if (a.bres || pre_b) {
                         pre_b = false;
-                    } else if (CS == 1) {
-                        tc::tma_load_2d(smem_u32(stg + a_bytes), &tmB, kcol, nt * BN, fb);
                     } else {
-                        constexpr int BR = BN / CS;   // rows of B this CTA loads for the cluster
-                        tc::tma_load_2d_mc(smem_u32(stg + a_bytes + rank * BR * a.chb), &tmB, kcol,
-                                           nt * BN + rank * BR, fb, cmask);
+                        tc::tma_load_2d(smem_u32(stg + a_bytes), &tmB, kcol, nt * BN, fb);
                     }
                     it += S2;
                     ps += S2;
@@ -771,8 +600,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                                         (!first || j != 0) ? 1u : 0u);
                         first = false;
                     }
-                    if (CS == 1) tc::mma_commit(smem_u32(&sm->empty[s]));
-                    else tc::mma_commit_mc(smem_u32(&sm->empty[s]), cmask);   // frees the stage in every CTA
+                    tc::mma_commit(smem_u32(&sm->empty[s]));
                 }
                 if (ok) tc::mma_commit(smem_u32(&sm->accf[b]));
             }
@@ -832,18 +660,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             const int mn = a.ksplit > 1 ? fdiv(tile, a.fd_ksplit) : tile;
             const int z = tile - mn * a.ksplit;
             const int mq = fdiv(mn, a.fd_ntiles);
-            const int mt = mq * CS + rank, nt = mn - mq * a.n_tiles;
-            if (mt >= a.m_tiles) {
-                // the cluster's spare CTA on an odd tile count: loads and MMAs ran on
-                // zero-filled operands; nothing to store
-                tc::fence_before();
-                __syncwarp();
-                if (lane == 0) {
-                    tc::mbar_arrive(smem_u32(&sm->acce[b]));
-                    if (a.kalt) tc::mbar_arrive(smem_u32(&sm->acce[b + 1]));
-                }
-                continue;
-            }
+            const int mt = mq, nt = mn - mq * a.n_tiles;
             const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * HC);
             // the buffer goes back to the MMA issuer right after its last live
             // column is in registers; the math and stores of that chunk follow
@@ -1060,8 +877,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     }
 
     tc::fence_before();
-    if (CS > 1) tc::cluster_sync();   // no peer multicasts into this CTA's smem any more
-    else __syncthreads();
+    __syncthreads();
     tc::fence_after();
     __syncwarp();
     if (warp == 1)
@@ -1133,7 +949,7 @@ cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, 
 constexpr size_t kSmemLimit = 232448;   // opt-in dynamic shared memory per block (227 KB)
 
 static size_t tc_ctrl_bytes() {
-    return ((sizeof(tc::Smem) + 15) & ~(size_t)15) + (2 * tc::kEpiCols + 2 * tc::kRawBufs * tc::kRawHalo) * sizeof(float);
+    return ((sizeof(tc::Smem) + 15) & ~(size_t)15) + 2 * tc::kEpiCols * sizeof(float);
 }
 static size_t tc_avail() { return kSmemLimit - 1024 - tc_ctrl_bytes(); }
 
@@ -1167,13 +983,12 @@ bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb) {
     return n_tiles == 1 && ksplit == 1 && (size_t)nk * BN * chb + 8 * 128 * (size_t)chb <= tc_avail();
 }
 
-template <int BN, int DT, int CS>
+template <int BN, int DT>
 static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int workers, cudaStream_t st) {
     TcArgs a = a0;
     // 16-byte chunks (K = 8) only in pair mode, and pair mode only in its one shape
     if ((a.chb == 16) != (a.pair != 0)) return cudaErrorInvalidValue;
-    if (a.pair && (DT != DT_BF16 || CS != 1 || !a.tapm || !a.bres || a.ksplit != 1 || a.k != 3 || a.chunks != 1 ||
-                   a.raw || a.kalt))
+    if (a.pair && (DT != DT_BF16 || !a.tapm || !a.bres || a.ksplit != 1 || a.k != 3 || a.chunks != 1 || a.kalt))
         return cudaErrorInvalidValue;
     if (!tc_geometry(BN, a.chb, a.bres, a.k * a.k * a.chunks, &a)) return cudaErrorInvalidValue;
     if (a.ksplit < 1 || a.n_tiles < 1 || a.chunks < 1 || a.k < 1) return cudaErrorInvalidValue;
@@ -1183,7 +998,7 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     a.fd_k = make_fast_div(a.k);
     a.fd_nst = make_fast_div(a.nst);
     const size_t smem = 1024 + (size_t)a.ctrl_off + tc_ctrl_bytes();
-    auto kern = conv_tc_kernel<BN, DT, CS>;
+    auto kern = conv_tc_kernel<BN, DT>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
@@ -1191,19 +1006,12 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
         attr = true;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(workers * CS));
+    cfg.gridDim = dim3((unsigned)workers);
     cfg.blockDim = dim3(tc::THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute at[2];
+    cudaLaunchAttribute at[1];
     int na = 0;
-    if (CS > 1) {
-        at[na].id = cudaLaunchAttributeClusterDimension;
-        at[na].val.clusterDim.x = CS;
-        at[na].val.clusterDim.y = 1;
-        at[na].val.clusterDim.z = 1;
-        ++na;
-    }
     if (pdl_enabled()) {
         at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         at[na].val.programmaticStreamSerializationAllowed = 1;
@@ -1214,21 +1022,15 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     return cudaLaunchKernelEx(&cfg, kern, tmB, a);
 }
 
-// BN x (cluster size): cs = 2 needs the weight map whose box has BN / 2 rows.
-cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, int cs,
-                           cudaStream_t st) {
+cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, cudaStream_t st) {
     if (dt == DT_BF16) {
-        if (BN == 64 && cs == 1) return launch_tc_bn<64, DT_BF16, 1>(tmB, a, workers, st);
-        if (BN == 128 && cs == 1) return launch_tc_bn<128, DT_BF16, 1>(tmB, a, workers, st);
-        if (BN == 256 && cs == 1) return launch_tc_bn<256, DT_BF16, 1>(tmB, a, workers, st);
-        if (BN == 128 && cs == 2) return launch_tc_bn<128, DT_BF16, 2>(tmB, a, workers, st);
-        if (BN == 256 && cs == 2) return launch_tc_bn<256, DT_BF16, 2>(tmB, a, workers, st);
+        if (BN == 64) return launch_tc_bn<64, DT_BF16>(tmB, a, workers, st);
+        if (BN == 128) return launch_tc_bn<128, DT_BF16>(tmB, a, workers, st);
+        if (BN == 256) return launch_tc_bn<256, DT_BF16>(tmB, a, workers, st);
     } else if (dt == DT_FP8) {
-        if (BN == 64 && cs == 1) return launch_tc_bn<64, DT_FP8, 1>(tmB, a, workers, st);
-        if (BN == 128 && cs == 1) return launch_tc_bn<128, DT_FP8, 1>(tmB, a, workers, st);
-        if (BN == 256 && cs == 1) return launch_tc_bn<256, DT_FP8, 1>(tmB, a, workers, st);
-        if (BN == 128 && cs == 2) return launch_tc_bn<128, DT_FP8, 2>(tmB, a, workers, st);
-        if (BN == 256 && cs == 2) return launch_tc_bn<256, DT_FP8, 2>(tmB, a, workers, st);
+        if (BN == 64) return launch_tc_bn<64, DT_FP8>(tmB, a, workers, st);
+        if (BN == 128) return launch_tc_bn<128, DT_FP8>(tmB, a, workers, st);
+        if (BN == 256) return launch_tc_bn<256, DT_FP8>(tmB, a, workers, st);
     }
     return cudaErrorInvalidValue;
 }

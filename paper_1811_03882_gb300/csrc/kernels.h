@@ -150,13 +150,6 @@ struct TcArgs {
     int plane;    // producer lanes per producer warp (2 * plane divides nst)
     int kalt;     // 1: the two MMA issuers take alternate K steps of each tile
                   //    (needs at least two K steps per work item)
-    // raw = 1: the first layer's A tile is built by the producer warps from
-    // the NCHW FP32 frames at x_raw (raw_c channels, 3 x 3 taps, im2col order
-    // j = (kh*3 + kw)*raw_c + c over one 32-channel BF16 chunk) instead of
-    // being loaded by TMA from a packed buffer; one problem, one K step,
-    // 16 x 8 tiles, three channels.
-    int raw, raw_c;
-    const float* x_raw;
     // tapm = 1 (3 x 3 layers with resident weights, 16 x 8 or 8 x 16 tiles):
     // a ring stage is one channel chunk of all nine taps, three TMA boxes of
     // TH + 2 rows (one per tap column; the activation map's box is TH + 2
@@ -197,13 +190,10 @@ cudaError_t maxpool_s1_grouped(const PoolJob* jobs, int njobs, long long total, 
 int tc_chunk_bytes(int Cp, int dt);
 // Whether a launch keeps all of its weights resident in shared memory: one
 // N tile, no K split, and nk boxes of BN x chunk bytes fit in the B ring.
-// Such launches run without clusters (cs = 1).
 bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb);
 cudaError_t tc_encode_act(CUtensorMap* tm, const void* base, int dt, int n, int H, int W, int Cp, int TW,
                           int TH);
 cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, int KK, int Cp, int BN);
-// workers = persistent CTAs (cs = 1) or 2-CTA clusters (cs = 2); tmB has
-// box rows BN / cs.
-cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, int cs,
-                           cudaStream_t st);
+// workers = persistent CTAs; tmB has box rows BN.
+cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, cudaStream_t st);
 }  // namespace dn

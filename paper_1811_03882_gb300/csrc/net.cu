@@ -428,23 +428,12 @@ void dn::tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, i
     *BN = ncols > 128 ? 256 : ncols > 64 ? 128 : 64;   // refined by tc_choose_split
 }
 
-// Picks BN and the split-K factor together with the cost model above.
-// Cluster size and persistent worker count of a tensor-core launch: single
-// CTAs, or with NET_TC_CLUSTER=2 2-CTA clusters for BN >= 128 that share the
-// weight box (multicast).
-void dn::tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int num_sms, int* cs, int* workers,
-                    int* bres) {
-    static const int forced = [] {
-        const char* e = getenv("NET_TC_CLUSTER");
-        return e ? atoi(e) : 0;
-    }();
+// Persistent worker count and resident-weight mode of a tensor-core launch:
+// one CTA per SM, at most one per work item.
+void dn::tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int num_sms, int* workers, int* bres) {
     *bres = tc_b_resident(BN, n_tiles, ks, nk, chb) ? 1 : 0;
-    // 2-CTA clusters sharing the weight box only on request: the shared empty
-    // barriers couple the pair's rings and, measured, cost more than the
-    // halved L2 reads of B save
-    *cs = (!*bres && BN >= 128 && m_tiles >= 2 && forced == 2) ? 2 : 1;
-    const int items = cdiv(m_tiles, *cs) * n_tiles * ks;
-    *workers = std::max(1, std::min(items, num_sms / *cs));
+    const int items = m_tiles * n_tiles * ks;
+    *workers = std::max(1, std::min(items, num_sms));
 }
 
 bool dn::pdl_enabled() {
@@ -455,10 +444,7 @@ bool dn::pdl_enabled() {
     return on;
 }
 
-int dn::tmb_index(int BN, int cs) {
-    const int rows = BN / cs;
-    return rows == 64 ? 0 : rows == 128 ? 1 : 2;
-}
+int dn::tmb_index(int BN) { return BN == 64 ? 0 : BN == 128 ? 1 : 2; }
 
 void dn::tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks) {
     double best = -1.0;
@@ -553,10 +539,10 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             if (r.ksplit > 1)
                 P->ws_bytes = std::max(P->ws_bytes, (size_t)r.ksplit * r.m_tiles * 128 * r.n_tiles * r.BN *
                                                         sizeof(float));
-            tc_workers(r.m_tiles, r.n_tiles, r.ksplit, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, &r.cs,
-                       &r.grid, &r.bres);
+            tc_workers(r.m_tiles, r.n_tiles, r.ksplit, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, &r.grid,
+                       &r.bres);
             {
-                // one work item per CTA (or cluster): the two MMA issuers share
+                // one work item per CTA: the two MMA issuers share
                 // each tile's K steps instead of idling one of them.  Fixed-batch
                 // plans only: grouped launches keep one summation order for a
                 // frame whatever else is in the batch.
@@ -579,7 +565,7 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
                     r.tapm = 1;
                 }
                 const int steps = r.tapm ? nk / 9 : nk;   // pipeline steps per tile
-                const int items = cdiv(r.m_tiles, r.cs) * r.n_tiles * r.ksplit;
+                const int items = r.m_tiles * r.n_tiles * r.ksplit;
                 r.kalt = (kalt_on && items <= r.grid && steps / r.ksplit >= 2) ? 1 : 0;
             }
             (void)tiles;
@@ -605,9 +591,9 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             static const bool dump = getenv("NET_PLAN_DUMP") != nullptr;   // diagnostics: one line per layer
             if (dump)
                 fprintf(stderr,
-                        "plan b%d %dx%d layer %d: tile %dx%d BN %d m_tiles %d n_tiles %d ksplit %d cs %d grid %d "
+                        "plan b%d %dx%d layer %d: tile %dx%d BN %d m_tiles %d n_tiles %d ksplit %d grid %d "
                         "bres %d kalt %d tapm %d pair %d\n",
-                        batch, h, w, l, r.TW, r.TH, r.BN, r.m_tiles, r.n_tiles, r.ksplit, r.cs, r.grid, r.bres, r.kalt,
+                        batch, h, w, l, r.TW, r.TH, r.BN, r.m_tiles, r.n_tiles, r.ksplit, r.grid, r.bres, r.kalt,
                         r.tapm, L.pair ? 1 : 0);
         }
         P->runs.push_back(r);
@@ -658,22 +644,9 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                                                     : cudaEventRecord(ev, st);
     };
     const bool prof = n->prof && !fp32_copy && (int)n->prof_ev.size() == 2 * nl;
-    // The first layer builds its im2col tiles from the raw frames inside the
-    // tensor-core kernel (no pack launch, no im2col buffer) when it is a BF16
-    // 3x3 layer over three channels with resident weights in one launch
-    // shape; calibration passes keep the pack, which they measure.
-    static const bool raw_on = [] {
-        const char* v = getenv("NET_RAW_L0");
-        return !(v && atoi(v) == 0);
-    }();
-    const LayerRun* r0 = plan ? &plan->runs[0] : nullptr;
-    const bool raw0 = raw_on && !fp32_copy && !amax && n->L[0].engine == ENG_TC && n->L[0].im2col_k == 3 &&
-                      n->in_c == 3 && n->L[0].in_dt == DT_BF16 && r0 && r0->bres && r0->ksplit == 1 && r0->cs == 1 &&
-                      r0->n_tiles == 1 && tc_chunk_bytes(n->L[0].in_cs, DT_BF16) == 64 && r0->TW == 16 && r0->TH == 8;
-    n->pending = raw0 ? 0 : 1;
+    n->pending = 1;
     cudaError_t e = cudaSuccess;
-    if (raw0) {
-    } else if (!fp32_copy && n->L[0].im2col_k) {
+    if (!fp32_copy && n->L[0].im2col_k) {
         e = pack_frames_im2col(d_in, buf[cur], batch, n->in_c, h, w, in_cs(0), n->L[0].im2col_k, in_dt(0),
                                1.f / in_scale(n->L[0]), st);
     } else {
@@ -733,14 +706,9 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.kalt = r.kalt;
                 a.tapm = r.tapm;
                 a.pair = L.pair ? 1 : 0;
-                if (l == 0 && raw0) {
-                    a.raw = 1;
-                    a.raw_c = n->in_c;
-                    a.x_raw = d_in;
-                }
                 a.ep = ep;
                 a.err = n->err_dev;
-                e = conv_tc_launch(L.tmB[tmb_index(r.BN, r.cs)], a, r.BN, L.in_dt, r.grid, r.cs, st);
+                e = conv_tc_launch(L.tmB[tmb_index(r.BN)], a, r.BN, L.in_dt, r.grid, st);
                 if (e == cudaSuccess && r.ksplit > 1) {
                     ++n->pending;
                     SplitReduce sr{n->ws, r.ksplit, r.m_tiles * 128, r.n_tiles * r.BN, r.TW, r.TH,

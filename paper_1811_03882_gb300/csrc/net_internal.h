@@ -59,7 +59,6 @@ struct LayerRun {
     int H = 0, W = 0;              // conv input (= pre-pool output) size
     int TW = 16, TH = 8, BN = 128; // TC tile: TH x TW pixels x BN channels
     int m_tiles = 0, n_tiles = 0, grid = 0;
-    int cs = 1;                    // TC cluster size (grid = workers * cs CTAs)
     int ksplit = 1;                // split-K factor (partial sums in the workspace)
     int bres = 0;                  // TC: weights resident in shared memory
     int kalt = 0;                  // TC: both MMA issuers on each tile (one work item per CTA)
@@ -80,11 +79,11 @@ void tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, int* 
 void tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks = 16);
 // (N tile, split-K) pairs a tensor-core layer can take in its current format.
 void tc_tile_options(const net* n, int l, std::vector<std::pair<int, int>>* opts);
-// Cluster size, persistent worker count and resident-weight mode of a
-// tensor-core launch (nk K steps of chb bytes per tile).
-void tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int num_sms, int* cs, int* workers,
-                int* bres);
-int tmb_index(int BN, int cs);
+// Persistent worker count and resident-weight mode of a tensor-core launch
+// (nk K steps of chb bytes per tile).
+void tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int num_sms, int* workers, int* bres);
+// Index into Layer::tmB of the weight map whose box has BN rows.
+int tmb_index(int BN);
 
 struct UnevenState;
 struct ServeState;

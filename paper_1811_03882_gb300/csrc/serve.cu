@@ -278,7 +278,7 @@ static net_status enqueue_step(net* n, ServeState* S, StepSlot& sl) {
     struct LayerStep {
         int l = 0;
         TcArgs a{};
-        int BN = 0, cs = 1, workers = 1;
+        int BN = 0, workers = 1;
         size_t simt_begin = 0, simt_end = 0;
         int pool_begin = 0, npool = 0;
         long long pool_total = 0;
@@ -354,7 +354,7 @@ static net_status enqueue_step(net* n, ServeState* S, StepSlot& sl) {
             a.ep = ep;
             a.err = n->err_dev;
             P.BN = BN;
-            tc_workers(mt, a.n_tiles, 1, BN, nk, a.chb, n->num_sms, &P.cs, &P.workers, &a.bres);
+            tc_workers(mt, a.n_tiles, 1, BN, nk, a.chb, n->num_sms, &P.workers, &a.bres);
             // pair mode needs resident weights (the launch refuses it otherwise)
             a.tapm = L.pair ? 1 : 0;
             a.pair = L.pair ? 1 : 0;
@@ -392,7 +392,7 @@ static net_status enqueue_step(net* n, ServeState* S, StepSlot& sl) {
                 ++n->launches;
             }
         } else {
-            SERVE_CK(conv_tc_launch(L.tmB[tmb_index(P.BN, P.cs)], P.a, P.BN, L.in_dt, P.workers, P.cs, st), "conv");
+            SERVE_CK(conv_tc_launch(L.tmB[tmb_index(P.BN)], P.a, P.BN, L.in_dt, P.workers, st), "conv");
             ++n->launches;
         }
         if (P.npool) {
