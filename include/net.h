@@ -273,7 +273,11 @@ net_status net_launches(const net_t* net, uint64_t* total);
  * NET_NOALLOC_SCRATCH_BYTES that each device loading the library holds
  * until exit; a layer needing more returns NET_E_INVAL before touching the
  * device.  The first call on a device looks the array's address up (with
- * that device current); make that first call before any stream capture.
+ * that device current) and keeps it for the life of the process; make that
+ * first call before any stream capture.  A cudaDeviceReset re-creates the
+ * device's context and moves the array, so the kept address goes stale:
+ * a process that resets a device must not call this entry point on that
+ * device afterwards.
  * All calls share the array and a call overwrites what the previous one
  * left there, so calls that may overlap on the GPU (different streams,
  * several host threads) race: serialise them. */

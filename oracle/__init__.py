@@ -23,7 +23,9 @@ Two forward passes are provided:
   per-output-channel weight scales and a per-layer activation scale).  It
   separates rounding error from kernel bugs.
 
-Parity pins for every function here are in tests/test_oracle_pins.py.
+Parity pins for every function here are in tests/test_oracle_pins.py and,
+for ``forward_quant`` and ``act_scales_from``, tests/test_oracle_quant_pins.py
+(an independent float64 torch composition, matched to 1e-12 layer by layer).
 """
 from __future__ import annotations
 
@@ -234,12 +236,14 @@ def weight_scales_fp8(w_folded) -> np.ndarray:
 
 
 def forward_quant(layers, in_c: int, x, blob, precs, act_scales=None,
-                  keep_all: bool = False):
+                  keep_all: bool = False, out_store=None):
     """FP64 forward pass over operands rounded as a reduced-precision path
     stores them.  precs[l] in {'fp32','bf16','fp8'} is the operand format of
     layer l: its input activation and its folded weights are stored in it
     (FP8: activation / act_scales[l], weights / per-channel scale).  Bias is
-    FP32; the epilogue (bias, leaky, pool) is exact; the final map is FP32."""
+    FP32; the epilogue (bias, leaky, pool) is exact; the final map is FP32,
+    or, with out_store = (prec, scale), stored as a following layer of that
+    format would read it (used to run one layer of a deeper network)."""
     ps = parse_blob(layers, in_c, blob)
     n = len(layers)
     a = _store(_f64(x), precs[0], act_scales[0] if precs[0] == "fp8" else 1.0)
@@ -259,6 +263,8 @@ def forward_quant(layers, in_c: int, x, blob, precs, act_scales=None,
         if li + 1 < n:
             nxt = precs[li + 1]
             a = _store(y, nxt, act_scales[li + 1] if nxt == "fp8" else 1.0)
+        elif out_store is not None:
+            a = _store(y, out_store[0], out_store[1])
         else:
             a = y.astype(np.float32).astype(np.float64)
         if keep_all:

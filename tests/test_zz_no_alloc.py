@@ -65,6 +65,14 @@ CASES = [
     (71, 1, 64, 26, 26, 128, 3, synth.ACT_LEAKY, synth.POOL_2X2S2),
     # a different layer right after it: 1x1, linear, no pool, batch 2
     (72, 2, 256, 13, 13, 64, 1, synth.ACT_LINEAR, synth.POOL_NONE),
+    # 20 outputs (not a multiple of 8: the reduction's 4-wide path, padded
+    # weight rows) over 37 inputs (odd, padded to 40), split in two along K
+    (73, 1, 37, 20, 22, 20, 3, synth.ACT_LEAKY, synth.POOL_2X2S2),
+    # scratch within 11 KB of the array's end: 796 -> 72 channels on 42 x 46,
+    # K split 17 ways on 148 to 152 SMs, so the partial sums fill the tail
+    (74, 1, 796, 42, 46, 72, 3, synth.ACT_LEAKY, synth.POOL_NONE),
+    # the packed input alone nearly fills the array (1440 x 1440 x 4 floats)
+    (75, 1, 4, 1440, 1440, 8, 3, synth.ACT_LINEAR, synth.POOL_NONE),
 ]
 
 
