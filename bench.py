@@ -41,13 +41,38 @@ WORKLOADS = {
 SERVE_RATES = (200.0, 1000.0, 4000.0)
 DEFAULT = "19conv-448-b8-bf16"
 
-# ncu DRAM traffic per launch of the dominant kernel family (read + write
-# bytes, averaged over the family's launches in one forward pass of the
-# default workload), from the capture summarised in
-# profiles/conv_tc_19conv_448_b8_bf16.md; None where not captured.
-TRAFFIC = {"19conv-448-b8-bf16": {"tc_bf16": 208.7e6 / 19}}
+# DRAM traffic per launch of the dominant kernel family (ncu
+# dram__bytes_read.sum + dram__bytes_write.sum, averaged over the family's
+# launches in one forward pass of the workload), with the first 16 hex digits
+# of the SHA-256 of the conv kernel's source when it was captured: the figure
+# is reported only while the source is unchanged, null otherwise.
+TRAFFIC = {}
+KERNEL_SRC = os.path.join(ROOT, "paper_1811_03882_gb300", "csrc", "k_conv_tc.cu")
 
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+
+
+def kernel_sha16():
+    import hashlib
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def cpu_model():
+    """Host CPU model (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def peaks():
@@ -129,19 +154,37 @@ def job_frames_per_s(frames_per_rank: int, ws: int, slowest_s: float) -> float:
     return frames_per_rank * ws / slowest_s
 
 
-def oracle_frames_per_s(spec, x1, blob, budget_s: float):
+def oracle_frames_per_s(spec, x1, blob, budget_s: float, threads: int = 0):
     """FP64 oracle timed on this host's cores over whole frames until
-    budget_s of CPU work has passed (at least one frame)."""
+    budget_s of CPU work has passed (at least one frame); threads > 0 limits
+    its OpenMP threads for this measurement."""
     import oracle
     oracle.build()
-    n, t0 = 0, time.perf_counter()
-    while True:
-        oracle.forward(spec.layers, spec.in_c, x1, blob)
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s:
-            break
-    return n / el, n, el, oracle.threads()
+    full = oracle.threads()
+    if threads:
+        oracle.set_threads(threads)
+    try:
+        used = oracle.threads()
+        n, t0 = 0, time.perf_counter()
+        while True:
+            oracle.forward(spec.layers, spec.in_c, x1, blob)
+            n += 1
+            el = time.perf_counter() - t0
+            if el >= budget_s:
+                break
+    finally:
+        oracle.set_threads(full)
+    return n / el, n, el, used
+
+
+def workload_config(wl, ws):
+    """The line's config, shared by both arms: the workload and how this run
+    lays it out (the reference arm times a bounded sample of the same
+    workload, stated in its cpu_baseline.sample)."""
+    netname, batch, side, prec, _ = WORKLOADS[wl]
+    return {"workload": wl, "network": netname, "global_batch": batch * ws, "frames_per_step_per_gpu": batch,
+            "side": side if side else "uneven {320,416,512,608}", "precision": prec,
+            "parallelism": "replicas%d" % ws, "l2": "flushed between steps (256 MB write)"}
 
 
 def run_reference(args, wl):
@@ -171,9 +214,10 @@ def run_reference(args, wl):
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": wl, "frames_per_step": 1, "side": side or "uneven", "network": netname},
+            "config": workload_config(wl, ws), "frames_per_step": 1,
             "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": oracle.threads(),
-                             "kind": "oracle", "sample": "%d frames (side %s)" % (args.steps, side or "uneven")},
+                             "kind": "oracle", "cpu_model": cpu_model(),
+                             "sample": "%d frames (side %s), one per step" % (args.steps, side or "uneven")},
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -306,6 +350,16 @@ class Workload:
             # a second pinned pair: the async host API alternates between two
             self.h_in.append(self.h_in[0].clone().pin_memory())
             self.h_out.append(torch.empty_like(self.h_out[0]).pin_memory())
+        else:
+            # uneven batches, end to end: two device slots, so that one step's
+            # uploads and downloads (own streams) overlap another step's pass
+            self.slots = [(self.d_in, self.d_out)]
+            self.slots.append(([torch.empty_like(t) for t in self.d_in], [torch.empty_like(t) for t in self.d_out]))
+            self.h_out2 = [[torch.empty_like(o).pin_memory() for o in self.h_out] for _ in range(2)]
+            self.s_up, self.s_down = torch.cuda.Stream(), torch.cuda.Stream()
+            self.ev_up = [torch.cuda.Event() for _ in range(2)]
+            self.ev_comp = [torch.cuda.Event() for _ in range(2)]
+            self.ev_free = [None, None]   # slot's download done (its device buffers reusable)
         self.h2d = sum(int(f.nbytes) for f in self.frames)
         self.d2h = sum(int(o.numel() * 4) for o in self.d_out)
         cins = spec.cins()
@@ -330,16 +384,32 @@ class Workload:
             # one call's copies overlap the previous call's pass
             self.net.forward_async(self.h_in[i % 2].numpy(), self.h_out[i % 2].numpy())
         else:
-            for a, b in zip(self.d_in, self.h_in):
-                a.copy_(b, non_blocking=True)
-            self.net.forward_uneven(self.d_in, self.sides, self.d_out)
-            for a, b in zip(self.h_out, self.d_out):
-                a.copy_(b, non_blocking=True)
-            self.stream.synchronize()
+            import torch
+            k = i % 2
+            d_in, d_out = self.slots[k]
+            with torch.cuda.stream(self.s_up):
+                if self.ev_free[k] is not None:
+                    self.s_up.wait_event(self.ev_free[k])
+                for a, b in zip(d_in, self.h_in):
+                    a.copy_(b, non_blocking=True)
+                self.ev_up[k].record(self.s_up)
+            self.stream.wait_event(self.ev_up[k])
+            self.net.forward_uneven(d_in, self.sides, d_out)
+            self.ev_comp[k].record(self.stream)
+            with torch.cuda.stream(self.s_down):
+                self.s_down.wait_event(self.ev_comp[k])
+                for a, b in zip(self.h_out2[k], d_out):
+                    a.copy_(b, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(self.s_down)
+                self.ev_free[k] = ev
 
     def e2e_done(self):
         if self.side:
             self.net.forward_wait()
+        else:
+            import torch
+            torch.cuda.synchronize()
 
 
 def measure(torch, W, args, flush, barrier, ws, with_clocks=False, dev=0):
@@ -424,24 +494,36 @@ def per_layer(W, layer_ms, precs):
     return out
 
 
-def roofline(W, layer_ms, precs):
-    """Dominant kernel family (by engine) over its layers: algorithmic FLOPs
-    / summed CUDA-event time, against the measured peak."""
+def roofline(W, ms_per_step, precs):
+    """The dominant kernel family (tensor-core conv, or the CUDA-core conv of
+    the FP32 path): all its layers' algorithmic FLOPs per pass over the whole
+    measured step time (which also holds the frame pack and any split-K
+    reductions, so this is a lower bound on the conv kernels' own rate),
+    against the measured burst peak (the timed region is tens of ms of
+    sub-ms passes) of each layer's operand type."""
     pk, pk_kind = peaks()
-    fam = ["simt" if p == "fp32" else "tc_" + p for p in precs]
-    dom = max(set(fam), key=lambda f: sum(t for t, g in zip(layer_ms, fam) if g == f))
-    sel = [i for i, g in enumerate(fam) if g == dom]
-    achieved = float(sum(W.flops_l[i] for i in sel)) / (float(sum(layer_ms[i] for i in sel)) / 1e3) / 1e12
-    if dom == "simt":
+    tc = [i for i, p in enumerate(precs) if p != "fp32"]
+    sel = tc if tc else list(range(len(precs)))
+    flops = float(sum(W.flops_l[i] for i in sel))
+    achieved = flops / (ms_per_step / 1e3) / 1e12
+    if not tc:
         peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        bound, pnote = "alu", "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % pk.get("sm_max_mhz", 2070.0)
+        bound, kern = "alu", "conv_simt_kernel"
+        pnote = "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % pk.get("sm_max_mhz", 2070.0)
     else:
-        peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) * (2.0 if dom == "tc_fp8" else 1.0)
-        bound = "tensor"
-        pnote = ("bf16 sustained, %s" % pk_kind) + (" x 2 (fp8/bf16 nominal ratio)" if dom == "tc_fp8" else "")
+        # FLOP-weighted: the time each layer's FLOPs take at its own type's peak
+        bf = pk["bf16_tflops"]
+        t_peak = sum(W.flops_l[i] / (bf * (2.0 if precs[i] == "fp8" else 1.0)) for i in sel)
+        peak = flops / t_peak
+        bound, kern = "tensor", "conv_tc_kernel"
+        nfp8 = sum(1 for i in sel if precs[i] == "fp8")
+        pnote = "bf16 burst, %s" % pk_kind + ("; fp8 layers at bf16 x 2 (nominal ratio), FLOP-weighted" if nfp8 else "")
+    tr = TRAFFIC.get(W.name, {}).get(kern)
+    traffic = tr[0] if tr and tr[1] == kernel_sha16() else None
     return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": TRAFFIC.get(W.name, {}).get(dom), "kernel": "conv_%s (%d layers)" % (dom, len(sel)),
-            "peak_source": pnote, "launches_per_step": len(sel)}
+            "traffic": traffic, "kernel": "%s (%d launches per pass)" % (kern, len(sel)),
+            "time_basis": "ms_per_step (whole pass, pack and split-K reductions included)",
+            "flops_per_pass": flops, "peak_source": pnote, "kernel_src_sha16": kernel_sha16()}
 
 
 def main():
@@ -454,8 +536,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other-precision runs")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
-    ap.add_argument("--serve", action="store_true", help="add the serving streams to the line")
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--no-serve", action="store_true", help="leave the serving streams out of the line")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--no-tile-search", action="store_true",
                     help="keep the analytic tile plan (skip the genetic tile-plan search)")
     args = ap.parse_args()
@@ -511,19 +593,19 @@ def main():
     W, info = setup(prec, tune=True)
     precs = W.net.layer_prec()
     m = measure(torch, W, args, flush, barrier, ws, with_clocks=True, dev=dev)
-    roof = roofline(W, m["layer_ms"], precs)
+    roof = roofline(W, m["ms_per_step"], precs)
     line = {
         "metric": "frames/s", "value": m["value"], "unit": "frames/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[prec], "data": "synthetic",
-        "config": {"workload": wl, "network": netname, "global_batch": batch * ws,
-                   "frames_per_step_per_gpu": batch, "side": side if side else "uneven {320,416,512,608}",
-                   "precision": prec, "layer_precision": precs,
-                   "parallelism": "replicas%d" % ws, "l2": "flushed between steps (256 MB write)"},
+        "config": workload_config(wl, ws),
+        "layer_precision": precs,
         "conv_tflops": m["conv_tflops"],
         "roofline": roof,
         "layer_ms": [round(float(t), 5) for t in m["layer_ms"]],
+        "layer_ms_basis": "CUDA events around each layer in a second pass; the events serialise "
+                          "programmatic launch, so their sum exceeds ms_per_step",
         "layers": per_layer(W, m["layer_ms"], precs),
         "e2e": {"value": m["e2e_fps"], "unit": "frames/s", "h2d_bytes_per_step": W.h2d, "d2h_bytes_per_step": W.d2h},
         "gpu_launches": int(m["launches"]),
@@ -534,7 +616,7 @@ def main():
         line["precision_search"] = {"plan": info["plan"], "ga": info["ga"]}
     if "tile_plan" in info:
         # [N tile, split-K] per layer ([0, 0]: CUDA cores), from the genetic search
-        line["config"]["tile_plan"] = info["tile_plan"]
+        line["tile_plan"] = info["tile_plan"]
         line["tile_search"] = info["tile_search"]
     W.net.close()
     if not args.no_compare and side:
@@ -544,7 +626,7 @@ def main():
             W2, info2 = setup(p, tune=(p == "fp8"))
             m2 = measure(torch, W2, args, flush, barrier, ws)
             cmp[p] = {"value": m2["value"], "ms_per_step": m2["ms_per_step"], "conv_tflops": m2["conv_tflops"],
-                      "e2e": m2["e2e_fps"], "roofline_frac": roofline(W2, m2["layer_ms"], W2.net.layer_prec())["frac"],
+                      "e2e": m2["e2e_fps"], "roofline_frac": roofline(W2, m2["ms_per_step"], W2.net.layer_prec())["frac"],
                       "layer_precision": W2.net.layer_prec()}
             if "plan" in info2:
                 cmp[p]["precision_search"] = {"plan": info2["plan"], "ga": info2["ga"]}
@@ -553,13 +635,17 @@ def main():
                 cmp[p]["tile_search"] = info2["tile_search"]
             W2.net.close()
         line["compare"] = cmp
-    if args.serve and rank == 0:
+    if not args.no_serve and rank == 0:
         line["serving"] = run_serving(args, torch, binding, dev)
     if rank == 0 and not args.no_cpu_baseline:
         f0 = W.frames[0][:1]
         fps, nfr, el, cores = oracle_frames_per_s(W.spec, f0, W.blob, args.cpu_budget_s)
+        fps1, nfr1, el1, _ = oracle_frames_per_s(W.spec, f0, W.blob, 1.0, threads=1)
         line["cpu_baseline"] = {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
-                                "sample": "%d frame(s) of %dx%d, %.1f s" % (nfr, f0.shape[2], f0.shape[3], el)}
+                                "sample": "%d frame(s) of %dx%d, %.1f s" % (nfr, f0.shape[2], f0.shape[3], el),
+                                "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+                                "single_thread": {"value": fps1, "unit": "frames/s",
+                                                  "sample": "%d frame(s), %.1f s" % (nfr1, el1)}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

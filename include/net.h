@@ -81,10 +81,14 @@ typedef struct {
 } net_desc;
 
 /* Creates a handle: validates the layer list, plans the device activation
- * arena for (max_batch, max_side) and allocates it.  *out is set on NET_OK. */
+ * arena for (max_batch, max_side) and allocates it.  *out is set on NET_OK.
+ * Paper Sec. 3.2: the device buffers of the offloaded loops are created once,
+ * outside them, so that no pass allocates or copies per layer. */
 net_status net_create(const net_desc* desc, net_t** out);
 
-/* Uploads the float32 weight blob (host, caller-owned, copied once) and
+/* Paper Sec. 3.2 (data a GPU loop only reads crosses to the device once,
+ * before the outermost loop): the weights.
+ * Uploads the float32 weight blob (host, caller-owned, copied once) and
  * folds it on the device in FP64: s = gamma/sqrt(var+1e-5), W' = W*s,
  * b' = beta - mean*s, then reorders W' to [cout][kh][kw][cin] and casts it
  * to each layer's precision (FP8: per-output-channel scale max|W'_o|/448).
@@ -94,10 +98,13 @@ net_status net_create(const net_desc* desc, net_t** out);
 net_status net_load_weights(net_t* net, const float* blob, size_t n_floats);
 
 /* FP8 layers: static per-tensor scale of each layer's input activation
- * (value = code * scale).  scales has n = n_layers entries (host). */
+ * (value = code * scale).  scales has n = n_layers entries (host), each
+ * positive and finite (else NET_E_INVAL).  The paper runs in one precision;
+ * the scales belong to this library's FP8 format. */
 net_status net_set_act_scales(net_t* net, const float* scales, int n);
 
-/* Measures FP8 activation scales on the device: runs the FP32 copy of the
+/* No paper counterpart (FP8 format of this library).
+ * Measures FP8 activation scales on the device: runs the FP32 copy of the
  * folded weights over the caller's frames (device NCHW float32) and sets
  * scale_l = max|input of layer l| / 448.  Writes them to scales_out (host,
  * n_layers floats) when it is not NULL. */
@@ -107,13 +114,19 @@ net_status net_calibrate(net_t* net, const float* d_frames, int batch, int h, in
 /* Output shape of the network for an h x w frame. */
 net_status net_output_shape(const net_t* net, int h, int w, int* c, int* ho, int* wo);
 
-/* Synchronous forward pass from host memory: one host->device copy of the
- * batch, the whole network on the device, one device->host copy of the
- * result.  out_cap_floats must hold batch*c*ho*wo floats. */
+/* Paper Sec. 3.2 (copies hoisted to the outermost loop) and Sec. 5.1.1 (the
+ * Darknet image-analysis pass that is offloaded): synchronous forward pass
+ * from host memory: one host->device copy of the batch, the whole network on
+ * the device, one device->host copy of the result.  in_nchw: batch x in_c x
+ * h x w float32 (host, caller-owned); out_cap_floats must hold
+ * batch*c*ho*wo floats (else NET_E_INVAL); NET_E_SHAPE for a batch or side
+ * beyond the handle's maxima or an odd size before a 2x2/s2 pool;
+ * NET_E_DEVICE_WAIT when a bounded device-side wait expired. */
 net_status net_forward(net_t* net, const float* in_nchw, int batch, int h, int w,
                        float* out_nchw, size_t out_cap_floats);
 
-/* Asynchronous form of net_forward for a stream of batches: enqueues the
+/* Paper Sec. 3.2, as net_forward.
+ * Asynchronous form of net_forward for a stream of batches: enqueues the
  * host->device copy of in_nchw (on an upload stream), the forward pass (on
  * the handle's stream) and the device->host copy into out_nchw (on a
  * download stream), and returns.  Two device staging slots alternate, so
@@ -130,18 +143,25 @@ net_status net_forward_async(net_t* net, const float* in_nchw, int batch, int h,
  * bounded device-side wait expired). */
 net_status net_forward_wait(net_t* net);
 
-/* Stream-ordered forward pass between device buffers (no host copies, no
- * synchronisation). */
+/* Paper Sec. 3.2: the pass with its data already on the device.
+ * Stream-ordered forward pass between device buffers (no host copies, no
+ * synchronisation).  d_in: batch x in_c x h x w float32, d_out: batch x c x
+ * ho x wo float32, both device memory owned by the caller; errors as
+ * net_forward (a device-wait expiry shows on a later call). */
 net_status net_forward_device(net_t* net, const float* d_in, int batch, int h, int w,
                               float* d_out);
 
 /* As net_forward_device, and also writes every layer's output (after its
  * pool) as NCHW float32 into d_layer_out[l] (device pointers, one per
- * layer, each sized for that layer's output).  Diagnostic path. */
+ * layer, each sized for that layer's output): the values the next layer
+ * reads, FP8 codes times their scale.  Diagnostic path (per-layer error
+ * against the oracle); the paper has no counterpart. */
 net_status net_forward_trace(net_t* net, const float* d_in, int batch, int h, int w,
                              float* const* d_layer_out);
 
-/* Uneven batch: n frames of different square sides in one pass.  Frame i
+/* Paper Sec. 1 and 5.1.1 (frames from many shared cameras analysed by one
+ * service) with the transfer rule of Sec. 3.2.
+ * Uneven batch: n frames of different square sides in one pass.  Frame i
  * is d_in[i] (1 x in_c x side[i] x side[i], device) and its result goes to
  * d_out[i].  Every layer of every frame runs in one grouped launch per
  * layer (frames share no reduction, so each result equals the frame's own
@@ -150,12 +170,21 @@ net_status net_forward_uneven(net_t* net, const float* const* d_in, const int* s
                               float* const* d_out);
 
 /* ---- request queue (continuous batching) ------------------------------
+ * Paper Sec. 1 and 5.1.1: a camera image-analysis service shared by many
+ * cameras and uses.
  * net_submit copies one frame (host NCHW float32, 1 x in_c x h x w) into a
- * pinned staging slot and returns a request id.  A scheduler thread admits
- * queued requests while slots and the HBM activation budget allow, and
- * advances every admitted request by one layer per step in one grouped
- * launch; requests arriving while others run join at the next step.  A
- * frame whose activations exceed the whole budget fails with NET_E_BUDGET. */
+ * pinned staging arena and returns a request id.  A scheduler thread admits
+ * queued requests first come, first served while the in-flight cap, the
+ * staging arena and the HBM activation budget allow, and runs the requests
+ * admitted together as one step: one forward pass of all of them, every
+ * layer one grouped launch over the step's frames.  Two steps are in flight
+ * at once: requests that arrive while a step runs are admitted into the
+ * next one, whose frames upload while the first computes and whose kernels
+ * follow the first's on the device; a finished step frees its budget for
+ * the requests still queued.  A frame's result does not depend on the other
+ * frames of its step.  A frame whose activations exceed the whole budget
+ * fails with NET_E_BUDGET; NET_E_SHAPE for a side beyond the handle's
+ * maximum. */
 net_status net_submit(net_t* net, const float* frame, int h, int w, uint64_t* req_id);
 
 /* Non-blocking: *done = 1 and the result copied to out when finished. */
@@ -179,7 +208,8 @@ net_status net_stats_reset(net_t* net);
 net_status net_set_layer_prec(net_t* net, const int* layer_prec, int n);
 net_status net_get_layer_prec(const net_t* net, int* layer_prec, int n);
 
-/* Genetic search over the FP8/BF16 choice of every switchable layer: the
+/* Paper Sec. 3.3 and 4 (the GA), Sec. 5.1.2 (its parameters).
+ * Genetic search over the FP8/BF16 choice of every switchable layer: the
  * paper's offload search (Sec. 3.3, 4; parameters of Sec. 5.1.2) with one
  * gene per layer instead of per loop.  Fitness is (time per forward pass in
  * ms)^(-1/2); a plan whose output on d_frames deviates from the FP32 path by
@@ -211,7 +241,9 @@ typedef struct {
 net_status net_tune_precision(net_t* net, const float* d_frames, int batch, int h, int w,
                               const net_ga_opts* opts, int* layer_prec_out, net_ga_result* result);
 
-/* Tile plan of one tensor-core layer for the fixed-batch passes
+/* No paper counterpart (the tile plan of this library's conv kernel; the
+ * search below applies the paper's GA to it).
+ * Tile plan of one tensor-core layer for the fixed-batch passes
  * (net_forward*): N tile bn in {64, 128, 256} and split-K factor ksplit in
  * {1, 2, 4, 8, 16}; 0 keeps the analytic choice.  A value the layer cannot take
  * (bn above its padded output columns, ksplit with fewer than four K steps
@@ -226,7 +258,8 @@ net_status net_set_layer_tiles(net_t* net, int layer, int bn, int ksplit);
  * overrides: bn[n] and ksplit[n] per layer (0 for CUDA-core layers). */
 net_status net_plan_tiles(net_t* net, int batch, int h, int w, int* bn, int* ksplit, int n);
 
-/* Genetic search over the tile plan: the same algorithm and options as
+/* Paper Sec. 3.3 and 4 (the GA) over this library's tile plan.
+ * Genetic search over the tile plan: the same algorithm and options as
  * net_tune_precision (max_err bounds the deviation from the analytic plan's
  * output; every plan computes the same sums, only their order differs), one
  * gene per tensor-core layer whose alphabet is that layer's valid (bn,
@@ -241,7 +274,9 @@ typedef struct {
 net_status net_tune_tiles(net_t* net, const float* d_frames, int batch, int h, int w, const net_ga_opts* opts,
                           int* bn_out, int* ksplit_out, net_tile_result* result);
 
-/* Per-layer timing: with enable != 0 every later forward pass records a
+/* Paper Sec. 3.3 measures each candidate's run time; this is the per-layer
+ * form of that measurement.
+ * Per-layer timing: with enable != 0 every later forward pass records a
  * CUDA event pair around each layer's conv kernel (on the handle's stream;
  * CUDA-graph replays record them too).  net_layer_times waits for the most
  * recent pass and writes each layer's conv-kernel time in milliseconds to

@@ -77,12 +77,18 @@ def lib():
             L.oracle_round_bf16.argtypes = [D, l]
             L.oracle_round_e4m3_sat.argtypes = [D, l]
             L.oracle_threads.restype = ctypes.c_int
+            L.oracle_set_threads.argtypes = [i]
             _lib = L
     return _lib
 
 
 def threads() -> int:
     return int(lib().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of later oracle calls (OpenMP); timing use only."""
+    lib().oracle_set_threads(int(n))
 
 
 def _p(a: np.ndarray):

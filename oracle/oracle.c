@@ -39,6 +39,16 @@ int oracle_threads(void) {
 #endif
 }
 
+/* Threads used by later calls (the CPU baseline times 1 and all cores). */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* 2-D convolution, NCHW in / OIHW weights / NCHW out, zero pad p=(k-1)/2. */
 void oracle_conv2d(const double* x, int N, int C, int H, int W,
                    const double* w, int O, int k, double* y) {
