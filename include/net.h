@@ -288,6 +288,18 @@ net_status net_layer_times(net_t* net, double* ms_out, int n);
  * counts every kernel node in the graph). */
 net_status net_launches(const net_t* net, uint64_t* total);
 
+/* Fault injection for tests of the failure path; the paper has no
+ * counterpart.  Every wait inside the tensor-core conv kernel is bounded;
+ * when one expires the kernel records the failure in a flag the host reads,
+ * drains its copies and MMAs, frees its tensor memory and returns, so the
+ * CUDA context stays usable.  After this call the handle's next
+ * fixed-batch pass (net_forward*, not captured in a graph) launches
+ * tensor-core layer `layer` with a ~1 ms bound on those waits and one of
+ * its K steps never loaded, so the wait for it expires: that pass returns
+ * NET_E_DEVICE_WAIT (its output is not valid) and later passes are
+ * unaffected.  NET_E_INVAL for a layer that does not run on tensor cores. */
+net_status net_inject_device_fault(net_t* net, int layer);
+
 /* ---- conv layer without allocation ------------------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory when they call (code running while a CUDA

@@ -105,6 +105,7 @@ _SIGS = {
     "net_profile": [ctypes.c_void_p, ctypes.c_int],
     "net_layer_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "net_launches": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
+    "net_inject_device_fault": [ctypes.c_void_p, ctypes.c_int],
     "net_conv2d_f32_noalloc": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
@@ -307,6 +308,10 @@ class Net:
         ms = np.zeros(self.n_layers, np.float64)
         check(lib().net_layer_times(self.h, _ptr(ms), self.n_layers))
         return ms
+
+    def inject_device_fault(self, layer: int):
+        """Test hook: the next fixed-batch pass faults layer `layer` (see net.h)."""
+        check(lib().net_inject_device_fault(self.h, layer))
 
     def launches(self) -> int:
         t = ctypes.c_uint64()

@@ -43,7 +43,7 @@ constexpr int THREADS = 384;   // producer, MMA issuer, 8 epilogue warps, second
 constexpr int NUM_WARPS = THREADS / 32;
 constexpr int kMaxStages = 32;                // ring stages (bit masks below are 32 bits)
 constexpr int kEpiCols = 1024;                // bias / alpha columns kept in shared memory
-constexpr long long WAIT_LIMIT = 4000000000LL;  // clock64 cycles (~2 s)
+constexpr long long WAIT_LIMIT = 4000000000LL;  // clock64 cycles (~2 s): bound of the drains, default of the waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -78,16 +78,16 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; false (and the error code recorded) when the limit passed
-// or another role already aborted.
+// Bounded wait; false (and the error code recorded) when `lim` clock64
+// cycles passed or another role already aborted.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err, int code) {
+                                          int* err, int code, long long lim) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (clock64() - t0 > WAIT_LIMIT) {
+        if (clock64() - t0 > lim) {
             *abort_flag = 1;
             atomicExch(err, code);
             return false;
@@ -251,6 +251,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     float* s_alpha = s_bias + kEpiCols;
 
     pdl_trigger();   // the next kernel may start its prologue as SMs free up
+    const long long lim = a.wait_limit;   // bound of every pipeline wait (clock64 cycles)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int KK = a.k * a.k;
     const int nkb = KK * a.chunks;                // weight boxes (tap, chunk) per tile
@@ -451,8 +452,21 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             while (true) {
                 const bool act = ok && tile < total;
                 if (!__any_sync(gmask, act) || __any_sync(gmask, !ok)) break;
-                if (act && !tc::mbar_wait(smem_u32(&sm->empty[ps]), eph ^ 1u, abort_flag, a.err, 1)) ok = false;
+                if (act && !tc::mbar_wait(smem_u32(&sm->empty[ps]), eph ^ 1u, abort_flag, a.err, 1, lim)) ok = false;
                 __syncwarp(gmask);
+                if (act && ok && a.withhold && it == S2) {
+                    // fault injection (tests only): the second K step of producer
+                    // 0's first lane is never loaded, so the wait of the issuer that
+                    // consumes it runs out; nothing is armed, issued or recorded
+                    it += S2;
+                    ps += S2;
+                    if (ps >= nst) {
+                        ps -= nst;
+                        eph ^= 1u;
+                    }
+                    advance(S2);
+                    continue;
+                }
                 if (act && ok) {
                     const int s = ps;
                     // the issuer that consumes this K step: the tile's, or in
@@ -488,7 +502,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 }
             }
             if (a.bres && pid == 0 && lane == 0 &&
-                !tc::mbar_wait(smem_u32(&sm->bres), 0u, abort_flag, a.err, 5)) {
+                !tc::mbar_wait(smem_u32(&sm->bres), 0u, abort_flag, a.err, 5, lim)) {
                 const long long t0 = clock64();
                 while (!tc::mbar_try(smem_u32(&sm->bres), 0u) && clock64() - t0 < WAIT_LIMIT) {
                 }
@@ -501,7 +515,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 const int o = (int)((last_owner >> st) & 1u);
                 const uint32_t bar = smem_u32(&sm->full[o][st]);
                 const uint32_t lph = (((o ? pph1 : pph0) >> st) & 1u) ^ 1u;   // parity of the last use
-                if (!tc::mbar_wait(bar, lph, abort_flag, a.err, 5)) {
+                if (!tc::mbar_wait(bar, lph, abort_flag, a.err, 5, lim)) {
                     // abort already flagged: give the copies a bounded grace period
                     const long long t0 = clock64();
                     while (!tc::mbar_try(bar, lph) && clock64() - t0 < WAIT_LIMIT) {
@@ -524,7 +538,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             uint32_t fph = 0u;   // bit s = phase parity of this issuer's next use of stage s
             bool ok = true;
             if (a.bres) {
-                ok = tc::mbar_wait(smem_u32(&sm->bres), 0u, abort_flag, a.err, 6);
+                ok = tc::mbar_wait(smem_u32(&sm->bres), 0u, abort_flag, a.err, 6, lim);
                 tc::fence_after();
             }
             for (int tile = worker; tile < total && ok; tile += nworkers, ++tcount) {
@@ -543,7 +557,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 const int slot = tcount & ((1 << nsl_log) - 1);
                 const int b = a.kalt ? 2 * slot + mid : slot;
                 const uint32_t aph = (uint32_t)(tcount >> nsl_log) & 1u;
-                if (!tc::mbar_wait(smem_u32(&sm->acce[b]), aph ^ 1u, abort_flag, a.err, 2)) break;
+                if (!tc::mbar_wait(smem_u32(&sm->acce[b]), aph ^ 1u, abort_flag, a.err, 2, lim)) break;
                 tc::fence_after();
                 const uint32_t dtm = tmem_base + (uint32_t)(b * BN);
                 int ms = it - fdiv(it, a.fd_nst) * nst;   // stage of this tile's first K step
@@ -553,7 +567,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     if (++ms == nst) ms = 0;
                     if (a.kalt && ((ks - ks0) & 1) != mid) continue;   // the other issuer's K step
                     const uint32_t ph = (fph >> s) & 1u;
-                    if (!tc::mbar_wait(smem_u32(&sm->full[mid][s]), ph, abort_flag, a.err, 3)) {
+                    if (!tc::mbar_wait(smem_u32(&sm->full[mid][s]), ph, abort_flag, a.err, 3, lim)) {
                         ok = false;
                         break;
                     }
@@ -654,8 +668,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             const int slot = tcount & ((1 << nsl_log) - 1);
             const int b = a.kalt ? 2 * slot : slot;
             const uint32_t aph = (uint32_t)(tcount >> nsl_log) & 1u;
-            if (!tc::mbar_wait(smem_u32(&sm->accf[b]), aph, abort_flag, a.err, 4)) break;
-            if (a.kalt && !tc::mbar_wait(smem_u32(&sm->accf[b + 1]), aph, abort_flag, a.err, 4)) break;
+            if (!tc::mbar_wait(smem_u32(&sm->accf[b]), aph, abort_flag, a.err, 4, lim)) break;
+            if (a.kalt && !tc::mbar_wait(smem_u32(&sm->accf[b + 1]), aph, abort_flag, a.err, 4, lim)) break;
             tc::fence_after();
             const int mn = a.ksplit > 1 ? fdiv(tile, a.fd_ksplit) : tile;
             const int z = tile - mn * a.ksplit;
@@ -997,6 +1011,7 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     a.fd_chunks = make_fast_div(a.chunks);
     a.fd_k = make_fast_div(a.k);
     a.fd_nst = make_fast_div(a.nst);
+    if (a.wait_limit <= 0) a.wait_limit = tc::WAIT_LIMIT;
     const size_t smem = 1024 + (size_t)a.ctrl_off + tc_ctrl_bytes();
     auto kern = conv_tc_kernel<BN, DT>;
     static bool attr = false;

@@ -162,6 +162,8 @@ struct TcArgs {
     int pair;
     Epilogue ep;
     int* err;     // bounded-wait failure code (0 = none)
+    long long wait_limit;   // bound of each pipeline wait, clock64 cycles (<= 0: ~2 s)
+    int withhold;           // fault injection (tests): one producer skips one K step
     // division by ksplit, n_tiles, chunks, k and nst (filled by conv_tc_launch)
     FastDiv fd_ksplit, fd_ntiles, fd_chunks, fd_k, fd_nst;
 };

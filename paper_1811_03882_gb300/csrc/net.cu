@@ -708,6 +708,13 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.pair = L.pair ? 1 : 0;
                 a.ep = ep;
                 a.err = n->err_dev;
+                if (l == n->fault_layer) {
+                    // net_inject_device_fault: a ~1 ms bound (clock64 cycles at
+                    // ~2 GHz) and one K step withheld by a producer, once
+                    a.wait_limit = 2000000;
+                    a.withhold = 1;
+                    n->fault_layer = -1;
+                }
                 e = conv_tc_launch(L.tmB[tmb_index(r.BN)], a, r.BN, L.in_dt, r.grid, st);
                 if (e == cudaSuccess && r.ksplit > 1) {
                     ++n->pending;
@@ -771,7 +778,7 @@ void net::graphs_clear() {
 }
 
 net_status dn::run_forward(net* n, const float* d_in, int batch, int h, int w, float* d_out) {
-    if (!n->use_graphs) {
+    if (!n->use_graphs || n->fault_layer >= 0) {   // an injected fault is not baked into a graph
         net_status s = enqueue_forward(n, d_in, batch, h, w, d_out, nullptr, false, nullptr);
         if (s == NET_OK) n->launches += n->pending;
         return s;
@@ -834,6 +841,14 @@ extern "C" net_status net_forward(net_t* n, const float* in, int batch, int h, i
     CK(cudaMemcpyAsync(out, n->d_out_stage, nout * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
     CK(cudaStreamSynchronize(n->stream));
     return check_device_error(n);
+}
+
+extern "C" net_status net_inject_device_fault(net_t* n, int layer) {
+    if (!n) return fail(NET_E_INVAL, "NULL argument");
+    if (layer < 0 || layer >= (int)n->L.size()) return fail(NET_E_INVAL, "layer %d out of range", layer);
+    if (n->L[layer].engine != ENG_TC) return fail(NET_E_INVAL, "layer %d runs on CUDA cores", layer);
+    n->fault_layer = layer;
+    return NET_OK;
 }
 
 extern "C" net_status net_set_layer_tiles(net_t* n, int layer, int bn, int ksplit) {

@@ -131,6 +131,7 @@ struct net {
     size_t ws_bytes = 0;
     int* err_host = nullptr;   // mapped pinned: bounded device waits that expired
     int* err_dev = nullptr;
+    int fault_layer = -1;      // net_inject_device_fault: layer of the next pass to fault (tests)
     dn::UnevenState* uneven = nullptr;
     // request queue, started by the first net_submit; serve_mu serialises
     // concurrent first submits so exactly one queue is created

@@ -254,7 +254,7 @@ def test_per_layer_error_report(prec, mix):
         d = np.abs(o - loc)
         e_loc = oracle.normwise_rel_err(o, loc)
         r_loc = oracle.rms_rel_err(o, loc)
-        flips = float((d > 0).mean())
+        flips = float((d > 1e-5 * np.abs(loc).max()).mean())   # stored values that moved
         print("layer %2d %s: local max %.3e rms %.3e, %.4f%% elements moved | end to end: vs exact %.3e, "
               "vs quant-aware %.3e (rms %.3e)"
               % (l, precs[l], e_loc, r_loc, 100.0 * flips, oracle.normwise_rel_err(o, exs[l]),
@@ -262,8 +262,14 @@ def test_per_layer_error_report(prec, mix):
         if last:
             assert e_loc <= 1e-5, (l, e_loc)
         else:
-            step = _step(loc, store[0], store[1])
-            assert (d <= step * (1 + 1e-6) + 1e-30).all(), (l, float((d / step).max()))
+            # each side rounds its own sum (FP32 accumulator / FP64) to the
+            # nearest stored value: |g - r| <= half a step at g + half a step
+            # at r + the accumulators' difference, at most 1e-5 of the layer's
+            # largest value (which also covers the FP32 product code * scale
+            # the trace writes for an FP8 value)
+            eps = 1e-5 * np.abs(loc).max()
+            bound = 0.5 * (_step(loc, store[0], store[1]) + _step(o, store[0], store[1])) + eps
+            assert (d <= bound).all(), (l, float((d / bound).max()))
             assert flips <= 1e-2, (l, flips)
             assert r_loc <= 2e-3, (l, r_loc)
         a, cin = o, layer.cout
