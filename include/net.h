@@ -169,6 +169,65 @@ net_status net_forward_trace(net_t* net, const float* d_in, int batch, int h, in
 net_status net_forward_uneven(net_t* net, const float* const* d_in, const int* side, int n,
                               float* const* d_out);
 
+/* ---- detection post-processing -----------------------------------------
+ * Paper Sec. 5.1.1: the offloaded benchmark is Darknet's "detection" app;
+ * with the transfer rule of Sec. 3.2 the network's final map is decoded on
+ * the device and only the detections cross back.  The map is read as the
+ * region output of an anchor-box detector: anchor a owns channels
+ * a*(5+C) .. a*(5+C)+4+C (tx, ty, tw, th, objectness logit, C class logits);
+ * cell (i, j) and anchor a form box id (i*GW + j)*A + a, centred at
+ * ((j + sigmoid(tx))/GW, (i + sigmoid(ty))/GH) with size
+ * (exp(tw)*pw/GW, exp(th)*ph/GH) as fractions of the frame; the class-c
+ * score is sigmoid(to) * softmax(logits)_c.  Boxes scoring above
+ * score_thresh in a class are its candidates; greedy non-maximum
+ * suppression per class takes them by score (descending, equal scores by
+ * id) and drops a box whose IoU with a kept box of its class exceeds
+ * nms_iou.  A frame's detections are its kept boxes class by class
+ * (ascending), each class in that order, at most max_det of them; its count
+ * is the number kept before that cut.  Decode, suppression and compaction
+ * run in FP32 in three kernels; the result does not depend on the order in
+ * which the device appended candidates. */
+#define NET_REGION_MAX_ANCHORS 16
+typedef struct {
+    int n_anchors;          /* A (1 .. NET_REGION_MAX_ANCHORS)                  */
+    int n_classes;          /* C; the last layer must have A * (5 + C) outputs  */
+    float anchors[2 * NET_REGION_MAX_ANCHORS]; /* (pw, ph) per anchor, in grid cells */
+    float score_thresh;     /* candidate when objectness * p(class) > this      */
+    float nms_iou;          /* dropped when IoU with a kept box exceeds this    */
+    int max_det;            /* detections reported per frame                    */
+} net_region;
+
+typedef struct {
+    float x, y, w, h;       /* centre and size, fractions of the frame          */
+    float score;            /* objectness * p(class)                            */
+    int cls;                /* class                                            */
+    int id;                 /* box id (i*GW + j)*A + a                          */
+    int pad;
+} net_detection;            /* 32 bytes                                         */
+
+/* Sets the decode and suppression parameters (copied) and allocates their
+ * device buffers for max_batch frames of the largest grid the handle's
+ * max_side gives.  NET_E_INVAL for a parameter out of range or a last layer
+ * whose output count is not A * (5 + C); NET_E_UNSUPPORTED when that grid
+ * times A exceeds 4096 boxes (the suppression sorts a class's candidates in
+ * shared memory). */
+net_status net_set_region(net_t* net, const net_region* region);
+
+/* Stream-ordered detection of a device map (batch x A*(5+C) x gh x gw
+ * float32, NCHW, caller-owned): d_counts[batch] kept boxes per frame and
+ * d_det[batch][max_det] the detections (device memory, caller-owned; rows
+ * past a frame's count are left as they were).  NET_E_STATE without
+ * net_set_region; NET_E_SHAPE for a batch or grid beyond its set-up. */
+net_status net_detect_device(net_t* net, const float* d_map, int batch, int gh, int gw, int* d_counts,
+                             net_detection* d_det);
+
+/* Frames (host NCHW float32) to detections: one host->device copy of the
+ * batch, the forward pass and the detection on the device, one
+ * device->host copy of the counts and detections.  counts: batch ints;
+ * det: batch * max_det detections (host, caller-owned). */
+net_status net_forward_detect(net_t* net, const float* in_nchw, int batch, int h, int w, int* counts,
+                              net_detection* det);
+
 /* ---- request queue (continuous batching) ------------------------------
  * Paper Sec. 1 and 5.1.1: a camera image-analysis service shared by many
  * cameras and uses.

@@ -63,6 +63,19 @@ class net_tile_result(ctypes.Structure):
                 ("evaluations", ctypes.c_int), ("memo_hits", ctypes.c_int), ("changed_layers", ctypes.c_int)]
 
 
+REGION_MAX_ANCHORS = 16
+
+
+class net_region(ctypes.Structure):
+    _fields_ = [("n_anchors", ctypes.c_int), ("n_classes", ctypes.c_int),
+                ("anchors", ctypes.c_float * (2 * REGION_MAX_ANCHORS)), ("score_thresh", ctypes.c_float),
+                ("nms_iou", ctypes.c_float), ("max_det", ctypes.c_int)]
+
+
+# net_detection as a numpy record (32 bytes)
+DETECTION = np.dtype([("x", np.float32), ("y", np.float32), ("w", np.float32), ("h", np.float32),
+                      ("score", np.float32), ("cls", np.int32), ("id", np.int32), ("pad", np.int32)])
+
 _lib = None
 _lock = threading.Lock()
 
@@ -106,6 +119,11 @@ _SIGS = {
     "net_layer_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "net_launches": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
     "net_inject_device_fault": [ctypes.c_void_p, ctypes.c_int],
+    "net_set_region": [ctypes.c_void_p, ctypes.POINTER(net_region)],
+    "net_detect_device": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_void_p, ctypes.c_void_p],
+    "net_forward_detect": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_void_p, ctypes.c_void_p],
     "net_conv2d_f32_noalloc": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
@@ -308,6 +326,34 @@ class Net:
         ms = np.zeros(self.n_layers, np.float64)
         check(lib().net_layer_times(self.h, _ptr(ms), self.n_layers))
         return ms
+
+    def set_region(self, anchors, n_classes: int, score_thresh: float, nms_iou: float, max_det: int):
+        """Detection parameters (net_set_region); anchors: [(pw, ph)] in grid cells."""
+        r = net_region()
+        r.n_anchors = len(anchors)
+        r.n_classes = n_classes
+        for i, (pw, ph) in enumerate(anchors):
+            r.anchors[2 * i] = pw
+            r.anchors[2 * i + 1] = ph
+        r.score_thresh = score_thresh
+        r.nms_iou = nms_iou
+        r.max_det = max_det
+        check(lib().net_set_region(self.h, ctypes.byref(r)))
+        self.max_det = max_det
+
+    def detect_device(self, d_map, batch, gh, gw, d_counts, d_det):
+        """Stream-ordered detection of a device map into device counts / rows
+        (d_det: a uint8 tensor of batch * max_det * 32 bytes)."""
+        check(lib().net_detect_device(self.h, _ptr(d_map), batch, gh, gw, _ptr(d_counts), _ptr(d_det)))
+
+    def forward_detect(self, x: np.ndarray):
+        """Host frames -> (counts[batch], detections[batch, max_det] as DETECTION records)."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        n, _, h, w = x.shape
+        counts = np.zeros(n, np.int32)
+        det = np.zeros((n, self.max_det), DETECTION)
+        check(lib().net_forward_detect(self.h, _ptr(x), n, h, w, _ptr(counts), _ptr(det)))
+        return counts, det
 
     def inject_device_fault(self, layer: int):
         """Test hook: the next fixed-batch pass faults layer `layer` (see net.h)."""

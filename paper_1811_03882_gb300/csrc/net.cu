@@ -1176,6 +1176,7 @@ extern "C" net_status net_free(net_t* n) {
     cudaFree(n->d_in_stage);
     cudaFree(n->d_out_stage);
     uneven_free(n);
+    region_free(n);
     if (n->own_stream) cudaStreamDestroy(n->stream);
     delete n;
     return NET_OK;

@@ -87,6 +87,7 @@ int tmb_index(int BN);
 
 struct UnevenState;
 struct ServeState;
+struct RegionState;
 
 }  // namespace dn
 
@@ -133,6 +134,7 @@ struct net {
     int* err_dev = nullptr;
     int fault_layer = -1;      // net_inject_device_fault: layer of the next pass to fault (tests)
     dn::UnevenState* uneven = nullptr;
+    dn::RegionState* region = nullptr;   // detection post-processing (net_set_region)
     // request queue, started by the first net_submit; serve_mu serialises
     // concurrent first submits so exactly one queue is created
     std::atomic<dn::ServeState*> serve{nullptr};
@@ -156,5 +158,6 @@ net_status enqueue_uneven(net* n, const float* const* d_in, const int* side, int
 void uneven_free(net* n);
 void uneven_graphs_clear(net* n);
 void serve_stop(net* n);
+void region_free(net* n);
 
 }  // namespace dn
