@@ -46,7 +46,7 @@ DEFAULT = "19conv-448-b8-bf16"
 # launches in one forward pass of the workload), with the first 16 hex digits
 # of the SHA-256 of the conv kernel's source when it was captured: the figure
 # is reported only while the source is unchanged, null otherwise.
-TRAFFIC = {}
+TRAFFIC = {"19conv-448-b8-bf16": {"conv_tc_kernel": (208.55e6 / 19, "cb075788d4cce2d3")}}
 KERNEL_SRC = os.path.join(ROOT, "paper_1811_03882_gb300", "csrc", "k_conv_tc.cu")
 
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
@@ -319,6 +319,106 @@ def run_serving(args, torch, binding, dev):
     return out
 
 
+JACOBI_SIDE, JACOBI_SWEEPS = 8192, 200
+
+
+def run_jacobi(torch, binding, dev, cpu_budget_s=4.0):
+    """Jacobi solver of the Laplace equation (paper Sec. 4's sample app) on an
+    8192 x 8192 grid (each iterate 268 MB, above L2): JACOBI_SWEEPS sweeps
+    (tol 0) timed with CUDA events on the solver's stream (device-resident),
+    then end to end from host memory (one H2D, one D2H), and the FP64 oracle
+    on the host over a bounded number of sweeps.  Algorithmic bytes per
+    sweep: the grid read once and its interior written once (FP32)."""
+    from oracle import jacobi as ojac
+    pk, pk_kind = peaks()
+    ny = nx = JACOBI_SIDE
+    u0 = synth.laplace_grid(24, ny, nx, "random")
+    st = torch.cuda.Stream()
+    d_in = torch.from_numpy(u0).cuda()
+    d_out = torch.empty_like(d_in)
+    J = binding.Jacobi(ny, nx, dev, st.cuda_stream)
+    J.solve_device(d_in, 0.0, 32, d_out)     # warm-up: graphs captured
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    l0 = J.launches()
+    e0.record(st)
+    J.solve_device(d_in, 0.0, 0, d_out)      # the copies in and out alone
+    e1.record(st)
+    k, _ = J.solve_device(d_in, 0.0, JACOBI_SWEEPS, d_out)
+    e2.record(st)
+    torch.cuda.synchronize()
+    launches = J.launches() - l0
+    t_sweeps = (e1.elapsed_time(e2) - e0.elapsed_time(e1)) / 1e3
+    per_sweep = t_sweeps / k
+    alg = 4.0 * ny * nx + 4.0 * (ny - 2) * (nx - 2)
+    gbs = alg / per_sweep / 1e9
+    h_out = np.empty_like(u0)
+    t0 = time.perf_counter()
+    _, k2, _ = J.solve(u0, 0.0, JACOBI_SWEEPS, h_out)
+    e2e_s = time.perf_counter() - t0
+    J.close()
+    # oracle: FP64 sweeps of the same grid on the host, bounded sample
+    n, t0, u = 0, time.perf_counter(), u0.astype(np.float64)
+    while True:
+        u, _ = ojac.sweep(u)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= cpu_budget_s:
+            break
+    return {"grid": [ny, nx], "dtype": "f32", "sweeps": k, "ms_per_sweep": 1e3 * per_sweep,
+            "sweeps_per_s": 1.0 / per_sweep, "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / pk["hbm_gbs"], "traffic": None, "kernel": "jacobi_sweep_kernel",
+                         "alg_bytes_per_sweep": alg, "peak_source": "hbm copy, %s" % pk_kind},
+            "e2e": {"sweeps_per_s": k2 / e2e_s, "h2d_bytes": int(u0.nbytes), "d2h_bytes": int(u0.nbytes),
+                    "note": "%d sweeps with one H2D and one D2H of the grid" % k2},
+            "cpu_baseline": {"sweeps_per_s": n / el, "kind": "oracle (numpy FP64)", "cores": 1,
+                             "sample": "%d sweep(s) of the same grid, %.1f s" % (n, el)}}
+
+
+def run_detect(torch, binding, dev, side=416, batch=8):
+    """Detection post-processing after the 9-conv network (125 channels on a
+    13 x 13 grid per 416 x 416 frame): the three device kernels timed with
+    CUDA events on a batch's map, and frames -> detections end to end
+    (net_forward_detect: one H2D of the frames, one D2H of the detections)."""
+    spec = synth.net_9conv()
+    _, x, blob = synth.workload_net(spec, synth.SEED_9CONV, batch, side, side)
+    anchors = [(0.8, 1.2), (2.0, 3.1), (4.5, 2.2), (6.0, 7.5), (9.7, 5.0)]
+    st = torch.cuda.Stream()
+    net = binding.Net(spec.layers, 3, prec="bf16", max_batch=batch, max_side=side, stream=st.cuda_stream,
+                      device=dev)
+    net.load_weights(blob)
+    net.set_region(anchors, 20, 0.04, 0.45, 256)
+    d_x = torch.from_numpy(x).cuda()
+    c, gh, gw = net.output_shape(side, side)
+    d_map = torch.empty((batch, c, gh, gw), device="cuda")
+    d_cnt = torch.zeros(batch, dtype=torch.int32, device="cuda")
+    d_det = torch.zeros(batch * 256 * 32, dtype=torch.uint8, device="cuda")
+    net.forward_device(d_x, batch, side, side, d_map)
+    for _ in range(3):
+        net.detect_device(d_map, batch, gh, gw, d_cnt, d_det)
+    reps = 50
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(st)
+    for _ in range(reps):
+        net.detect_device(d_map, batch, gh, gw, d_cnt, d_det)
+    ev[1].record(st)
+    torch.cuda.synchronize()
+    det_ms = ev[0].elapsed_time(ev[1]) / reps
+    for _ in range(3):
+        net.forward_detect(x)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        counts, _ = net.forward_detect(x)
+    e2e = time.perf_counter() - t0
+    net.close()
+    return {"network": "9-conv", "batch": batch, "side": side, "grid": [gh, gw], "anchors": 5, "classes": 20,
+            "score_thresh": 0.04, "nms_iou": 0.45, "detect_ms_per_batch": det_ms, "kernels": 3,
+            "kept_per_frame": [int(v) for v in counts],
+            "e2e_frames_per_s": batch * reps / e2e,
+            "e2e_note": "frames -> detections through net_forward_detect (BF16 network + decode + NMS), "
+                        "one H2D and one D2H per batch"}
+
+
 class Workload:
     """Frames, weights and step functions of one bench workload."""
 
@@ -538,6 +638,8 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-serve", action="store_true", help="leave the serving streams out of the line")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="leave the detection and Jacobi measurements out of the line")
     ap.add_argument("--no-tile-search", action="store_true",
                     help="keep the analytic tile plan (skip the genetic tile-plan search)")
     args = ap.parse_args()
@@ -637,6 +739,9 @@ def main():
         line["compare"] = cmp
     if not args.no_serve and rank == 0:
         line["serving"] = run_serving(args, torch, binding, dev)
+    if not args.no_extra and rank == 0:
+        line["detect"] = run_detect(torch, binding, dev)
+        line["jacobi"] = run_jacobi(torch, binding, dev)
     if rank == 0 and not args.no_cpu_baseline:
         f0 = W.frames[0][:1]
         fps, nfr, el, cores = oracle_frames_per_s(W.spec, f0, W.blob, args.cpu_budget_s)

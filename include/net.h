@@ -228,6 +228,43 @@ net_status net_detect_device(net_t* net, const float* d_map, int batch, int gh, 
 net_status net_forward_detect(net_t* net, const float* in_nchw, int batch, int h, int w, int* counts,
                               net_detection* det);
 
+/* ---- Jacobi solver of the Laplace equation ------------------------------
+ * Paper Sec. 4: the sample application that solves the Laplace equation by
+ * the Jacobi method (13.5x there), run with the transfer rule of Sec. 3.2:
+ * the grid crosses to the device once, every sweep stays in device memory,
+ * the result crosses back once.  The grid is ny x nx float32, row-major;
+ * its first and last rows and columns are fixed boundary values.  A sweep
+ * replaces every interior point by the mean of its four neighbours in the
+ * previous iterate; the change of a sweep is the largest |new - old| over
+ * the interior; sweeps repeat while the last change exceeds tol and fewer
+ * than iter_max have run (tol = 0: exactly iter_max sweeps).  The stopping
+ * rule is applied on the device; the host polls a 16-byte state once per 16
+ * queued sweeps, and sweeps queued past the stop return at once.  FP32. */
+typedef struct net_jacobi net_jacobi_t;
+
+/* Handle for one grid size on `device` (work on cuda_stream; NULL: an own
+ * stream); allocates two device grids.  NET_E_INVAL unless 3 <= ny, nx <=
+ * 65536 (a grid needs an interior). */
+net_status net_jacobi_create(int ny, int nx, int device, void* cuda_stream, net_jacobi_t** out);
+
+/* Solves from host grid_in into host grid_out (ny * nx floats each,
+ * caller-owned; may be the same buffer); *sweeps and *change (either may be
+ * NULL) report the sweeps run and the last change.  NET_E_INVAL for tol < 0
+ * or iter_max < 0; iter_max = 0 returns the input. */
+net_status net_jacobi_solve(net_jacobi_t* j, const float* grid_in, float tol, int iter_max, float* grid_out,
+                            int* sweeps, float* change);
+
+/* As net_jacobi_solve between device grids (caller-owned, row-major ny x
+ * nx); returns when done. */
+net_status net_jacobi_solve_device(net_jacobi_t* j, const float* d_in, float tol, int iter_max, float* d_out,
+                                   int* sweeps, float* change);
+
+/* Kernels the handle has launched (every queued sweep counts two). */
+net_status net_jacobi_launches(const net_jacobi_t* j, uint64_t* total);
+
+/* Releases the handle's device and host memory.  NULL is accepted. */
+net_status net_jacobi_free(net_jacobi_t* j);
+
 /* ---- request queue (continuous batching) ------------------------------
  * Paper Sec. 1 and 5.1.1: a camera image-analysis service shared by many
  * cameras and uses.

@@ -120,6 +120,13 @@ _SIGS = {
     "net_launches": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
     "net_inject_device_fault": [ctypes.c_void_p, ctypes.c_int],
     "net_set_region": [ctypes.c_void_p, ctypes.POINTER(net_region)],
+    "net_jacobi_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
+    "net_jacobi_solve": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int, ctypes.c_void_p,
+                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)],
+    "net_jacobi_solve_device": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int, ctypes.c_void_p,
+                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)],
+    "net_jacobi_launches": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
+    "net_jacobi_free": [ctypes.c_void_p],
     "net_detect_device": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                           ctypes.c_void_p, ctypes.c_void_p],
     "net_forward_detect": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -168,6 +175,52 @@ def _ptr(a):
     if isinstance(a, np.ndarray):
         return ctypes.c_void_p(a.ctypes.data)
     return ctypes.c_void_p(int(a))
+
+
+class Jacobi:
+    """Owning wrapper of a net_jacobi_t handle (Jacobi solver of the Laplace
+    equation on an ny x nx float32 grid)."""
+
+    def __init__(self, ny: int, nx: int, device: int = 0, stream=None):
+        h = ctypes.c_void_p()
+        check(lib().net_jacobi_create(ny, nx, device, stream, ctypes.byref(h)))
+        self.h, self.ny, self.nx = h, ny, nx
+
+    def solve(self, grid: np.ndarray, tol: float, iter_max: int, out: np.ndarray = None):
+        """Host grid -> (host result, sweeps, last change)."""
+        g = np.ascontiguousarray(grid, dtype=np.float32)
+        out = np.empty_like(g) if out is None else out
+        k, ch = ctypes.c_int(), ctypes.c_float()
+        check(lib().net_jacobi_solve(self.h, _ptr(g), tol, iter_max, _ptr(out), ctypes.byref(k), ctypes.byref(ch)))
+        return out, k.value, ch.value
+
+    def solve_device(self, d_in, tol: float, iter_max: int, d_out):
+        k, ch = ctypes.c_int(), ctypes.c_float()
+        check(lib().net_jacobi_solve_device(self.h, _ptr(d_in), tol, iter_max, _ptr(d_out), ctypes.byref(k),
+                                            ctypes.byref(ch)))
+        return k.value, ch.value
+
+    def launches(self) -> int:
+        t = ctypes.c_uint64()
+        check(lib().net_jacobi_launches(self.h, ctypes.byref(t)))
+        return t.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().net_jacobi_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Net:

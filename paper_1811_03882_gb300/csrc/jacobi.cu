@@ -1,0 +1,330 @@
+// jacobi.cu — Jacobi solver of the Laplace equation, device-resident.
+//
+// Paper Sec. 4 reports a 13.5x speed-up of a sample application that solves
+// the Laplace equation by the Jacobi method; its data-transfer rule
+// (Sec. 3.2) is applied in full: the grid crosses to the device once, every
+// sweep reads and writes device memory only, and the result crosses back
+// once.  One sweep replaces each interior point of the ny x nx grid by the
+// mean of its four neighbours in the previous iterate (the first and last
+// rows and columns are fixed boundary values); sweeps repeat while the
+// largest change of an interior point exceeds tol and fewer than iter_max
+// sweeps have run.
+//
+// Device side, FP32, memory-bound (8 bytes of DRAM traffic per point and
+// sweep at best: one read, one write):
+//  * jacobi_sweep_kernel: persistent grid (a multiple of the SM count), each
+//    work tile a strip of R rows x 4*blockDim columns; a thread owns four
+//    adjacent columns and walks down the strip keeping the rows above, at
+//    and below in registers (each input row is read once per strip), the
+//    left and right neighbours coming from the adjacent lanes by shuffles.
+//    Each block writes its largest change to a partial slot.
+//  * jacobi_finish_kernel (one block): reduces the partials and applies the
+//    stopping rule on the device: sweeps += 1, done when the change is at or
+//    below tol or sweeps reached iter_max.  Both kernels return at once when
+//    done is set, so the host can queue sweeps ahead and poll the 16-byte
+//    state only every few of them.
+//  * The two buffers alternate by the parity of the sweep count, so the
+//    result is in buffer (sweeps & 1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <utility>
+
+#include "../../include/net.h"
+#include "common.cuh"
+#include "net_internal.h"
+
+using namespace dn;
+
+namespace {
+
+struct JState {
+    int sweeps;
+    int done;
+    float change;
+    int pad;
+};
+
+constexpr int kThreads = 128;   // 512 columns per tile row
+constexpr int kRows = 32;       // rows per strip
+constexpr int kChunk = 16;      // sweeps per captured graph (even: buffer parity is kept per chunk)
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+__global__ void __launch_bounds__(kThreads) jacobi_sweep_kernel(float* b0, float* b1, int ny, int nx, int P,
+                                                                const JState* __restrict__ st, float* partial,
+                                                                int col_blocks, int strips) {
+    if (st->done) return;
+    const int k = st->sweeps;
+    const float* src = (k & 1) ? b1 : b0;
+    float* dst = (k & 1) ? b0 : b1;
+    const int lane = threadIdx.x & 31;
+    float best = 0.f;
+    const int tiles = col_blocks * strips;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int cb = tile % col_blocks, sb = tile / col_blocks;
+        const int x0 = (cb * kThreads + threadIdx.x) * 4;   // first of this thread's four columns
+        const bool inb = x0 < P;                             // inside the pitched row
+        const int y0 = 1 + sb * kRows, y1 = min(y0 + kRows, ny - 1);
+        float4 up = inb ? ld4(src + (size_t)(y0 - 1) * P + x0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 cur = inb ? ld4(src + (size_t)y0 * P + x0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int y = y0; y < y1; ++y) {   // uniform over the block
+            const float4 dn = inb ? ld4(src + (size_t)(y + 1) * P + x0) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float left = __shfl_up_sync(0xffffffffu, cur.w, 1);
+            float right = __shfl_down_sync(0xffffffffu, cur.x, 1);
+            if (lane == 0) left = (inb && x0 > 0) ? src[(size_t)y * P + x0 - 1] : 0.f;
+            if (lane == 31) right = (x0 + 4 < P) ? src[(size_t)y * P + x0 + 4] : 0.f;
+            float4 nw;
+            nw.x = 0.25f * ((up.x + dn.x) + (left + cur.y));
+            nw.y = 0.25f * ((up.y + dn.y) + (cur.x + cur.z));
+            nw.z = 0.25f * ((up.z + dn.z) + (cur.y + cur.w));
+            nw.w = 0.25f * ((up.w + dn.w) + (cur.z + right));
+            // interior columns 1 .. nx - 2 take the new value; the boundary and
+            // the pitch padding keep theirs
+            const float c4[4] = {cur.x, cur.y, cur.z, cur.w};
+            float n4[4] = {nw.x, nw.y, nw.z, nw.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int x = x0 + q;
+                if (x >= 1 && x <= nx - 2) best = fmaxf(best, fabsf(n4[q] - c4[q]));
+                else n4[q] = c4[q];
+            }
+            if (inb) *reinterpret_cast<float4*>(dst + (size_t)y * P + x0) = make_float4(n4[0], n4[1], n4[2], n4[3]);
+            up = cur;
+            cur = dn;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    __shared__ float wmax[kThreads / 32];
+    if (lane == 0) wmax[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = wmax[0];
+        for (int w = 1; w < kThreads / 32; ++w) m = fmaxf(m, wmax[w]);
+        partial[blockIdx.x] = m;
+    }
+}
+
+__global__ void jacobi_finish_kernel(const float* __restrict__ partial, int n, JState* st, float tol, int iter_max) {
+    if (st->done) return;
+    float m = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, partial[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wmax[32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+        m = fmaxf(m, wmax[0]);
+        st->change = m;
+        st->sweeps += 1;
+        if (m <= tol || st->sweeps >= iter_max) st->done = 1;
+    }
+}
+
+}  // namespace
+
+struct net_jacobi {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int ny = 0, nx = 0, P = 0;        // grid and row pitch (floats, multiple of 4)
+    float* buf[2] = {nullptr, nullptr};
+    float* partial = nullptr;
+    JState* d_state = nullptr;
+    JState* h_state = nullptr;        // pinned, two slots (chunks in flight)
+    int grid = 0, col_blocks = 0, strips = 0;
+    std::map<std::pair<float, int>, cudaGraphExec_t> graphs;   // per (tol, iter_max)
+    uint64_t launches = 0;
+};
+
+#define JK(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(e_ == cudaErrorMemoryAllocation ? NET_E_OOM : NET_E_CUDA, "%s: %s", #call,   \
+                        cudaGetErrorString(e_));                                                      \
+    } while (0)
+
+static net_status jacobi_graph(net_jacobi* j, float tol, int iter_max, cudaGraphExec_t* out) {
+    auto key = std::make_pair(tol, iter_max);
+    auto it = j->graphs.find(key);
+    if (it != j->graphs.end()) {
+        *out = it->second;
+        return NET_OK;
+    }
+    cudaGraph_t g = nullptr;
+    JK(cudaStreamBeginCapture(j->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < kChunk && e == cudaSuccess; ++s) {
+        jacobi_sweep_kernel<<<j->grid, kThreads, 0, j->stream>>>(j->buf[0], j->buf[1], j->ny, j->nx, j->P, j->d_state,
+                                                                 j->partial, j->col_blocks, j->strips);
+        jacobi_finish_kernel<<<1, 1024, 0, j->stream>>>(j->partial, j->grid, j->d_state, tol, iter_max);
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaStreamEndCapture(j->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(NET_E_CUDA, "jacobi capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(NET_E_CUDA, "jacobi graph: %s", cudaGetErrorString(e));
+    if (j->graphs.size() >= 16) {
+        for (auto& kv : j->graphs) cudaGraphExecDestroy(kv.second);
+        j->graphs.clear();
+    }
+    j->graphs[key] = ex;
+    *out = ex;
+    return NET_OK;
+}
+
+extern "C" net_status net_jacobi_create(int ny, int nx, int device, void* cuda_stream, net_jacobi_t** out) {
+    if (!out) return fail(NET_E_INVAL, "NULL argument");
+    *out = nullptr;
+    if (ny < 3 || nx < 3 || ny > 65536 || nx > 65536)
+        return fail(NET_E_INVAL, "grid %d x %d: each side must be in [3, 65536] (a grid needs an interior)", ny, nx);
+    net_jacobi* j = new net_jacobi();
+    j->device = device;
+    j->ny = ny;
+    j->nx = nx;
+    j->P = rup(nx, 4);
+    auto bail = [&](net_status s) {
+        net_jacobi_free(j);
+        return s;
+    };
+    if (cudaSetDevice(device) != cudaSuccess) return bail(fail(NET_E_CUDA, "cudaSetDevice(%d)", device));
+    if (cuda_stream) {
+        j->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreate(&j->stream) != cudaSuccess) return bail(fail(NET_E_CUDA, "stream"));
+        j->own_stream = true;
+    }
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    j->col_blocks = cdiv(j->P, 4 * kThreads);
+    j->strips = cdiv(ny - 2, kRows);
+    // persistent: eight 128-thread blocks per SM, at most one per tile
+    j->grid = std::max(1, std::min(j->col_blocks * j->strips, 8 * sms));
+    const size_t bytes = (size_t)ny * j->P * sizeof(float);
+    for (int b = 0; b < 2; ++b) {
+        cudaError_t e = cudaMalloc(&j->buf[b], bytes);
+        if (e != cudaSuccess) return bail(fail(e == cudaErrorMemoryAllocation ? NET_E_OOM : NET_E_CUDA, "grid buffer"));
+        cudaMemsetAsync(j->buf[b], 0, bytes, j->stream);
+    }
+    if (cudaMalloc(&j->partial, sizeof(float) * j->grid) != cudaSuccess ||
+        cudaMalloc(&j->d_state, sizeof(JState)) != cudaSuccess ||
+        cudaHostAlloc(&j->h_state, 2 * sizeof(JState), cudaHostAllocDefault) != cudaSuccess)
+        return bail(fail(NET_E_OOM, "jacobi state"));
+    if (cudaStreamSynchronize(j->stream) != cudaSuccess) return bail(fail(NET_E_CUDA, "jacobi set-up"));
+    *out = j;
+    return NET_OK;
+}
+
+// Runs the sweeps on the handle's buffers after buf[0] and buf[1] hold the
+// initial grid; result in buf[sweeps & 1].
+static net_status jacobi_run(net_jacobi* j, float tol, int iter_max, int* sweeps, float* change) {
+    JState s0{0, iter_max <= 0 ? 1 : 0, 0.f, 0};
+    JK(cudaMemcpyAsync(j->d_state, &s0, sizeof s0, cudaMemcpyHostToDevice, j->stream));
+    if (iter_max > 0) {
+        cudaGraphExec_t ex = nullptr;
+        net_status s = jacobi_graph(j, tol, iter_max, &ex);
+        if (s != NET_OK) return s;
+        // two chunks in flight: the state of chunk c is read while chunk c + 1
+        // runs (sweeps past convergence return at once)
+        cudaEvent_t ev[2];
+        JK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+        JK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+        const int chunks = cdiv(iter_max, kChunk);
+        net_status st = NET_OK;
+        for (int c = 0; c < chunks; ++c) {
+            cudaError_t e = cudaGraphLaunch(ex, j->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&j->h_state[c & 1], j->d_state, sizeof(JState),
+                                                      cudaMemcpyDeviceToHost, j->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[c & 1], j->stream);
+            if (e != cudaSuccess) {
+                st = fail(NET_E_CUDA, "jacobi chunk: %s", cudaGetErrorString(e));
+                break;
+            }
+            j->launches += 2 * kChunk;
+            if (c > 0) {
+                e = cudaEventSynchronize(ev[(c - 1) & 1]);
+                if (e != cudaSuccess) {
+                    st = fail(NET_E_CUDA, "jacobi: %s", cudaGetErrorString(e));
+                    break;
+                }
+                if (j->h_state[(c - 1) & 1].done) break;
+            }
+        }
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        if (st != NET_OK) return st;
+    }
+    JK(cudaMemcpyAsync(&j->h_state[0], j->d_state, sizeof(JState), cudaMemcpyDeviceToHost, j->stream));
+    JK(cudaStreamSynchronize(j->stream));
+    if (sweeps) *sweeps = j->h_state[0].sweeps;
+    if (change) *change = j->h_state[0].change;
+    return NET_OK;
+}
+
+extern "C" net_status net_jacobi_solve(net_jacobi_t* j, const float* grid_in, float tol, int iter_max,
+                                       float* grid_out, int* sweeps, float* change) {
+    if (!j || !grid_in || !grid_out) return fail(NET_E_INVAL, "NULL argument");
+    if (!(tol >= 0.f) || iter_max < 0) return fail(NET_E_INVAL, "tol %g / iter_max %d", (double)tol, iter_max);
+    JK(cudaSetDevice(j->device));
+    const size_t row = (size_t)j->nx * sizeof(float), pitch = (size_t)j->P * sizeof(float);
+    // one host->device copy; the second buffer takes the boundary by a device copy
+    JK(cudaMemcpy2DAsync(j->buf[0], pitch, grid_in, row, row, j->ny, cudaMemcpyHostToDevice, j->stream));
+    JK(cudaMemcpyAsync(j->buf[1], j->buf[0], pitch * j->ny, cudaMemcpyDeviceToDevice, j->stream));
+    int k = 0;
+    net_status s = jacobi_run(j, tol, iter_max, &k, change);
+    if (s != NET_OK) return s;
+    if (sweeps) *sweeps = k;
+    JK(cudaMemcpy2DAsync(grid_out, row, j->buf[k & 1], pitch, row, j->ny, cudaMemcpyDeviceToHost, j->stream));
+    JK(cudaStreamSynchronize(j->stream));
+    return NET_OK;
+}
+
+extern "C" net_status net_jacobi_solve_device(net_jacobi_t* j, const float* d_in, float tol, int iter_max,
+                                              float* d_out, int* sweeps, float* change) {
+    if (!j || !d_in || !d_out) return fail(NET_E_INVAL, "NULL argument");
+    if (!(tol >= 0.f) || iter_max < 0) return fail(NET_E_INVAL, "tol %g / iter_max %d", (double)tol, iter_max);
+    JK(cudaSetDevice(j->device));
+    const size_t row = (size_t)j->nx * sizeof(float), pitch = (size_t)j->P * sizeof(float);
+    JK(cudaMemcpy2DAsync(j->buf[0], pitch, d_in, row, row, j->ny, cudaMemcpyDeviceToDevice, j->stream));
+    JK(cudaMemcpyAsync(j->buf[1], j->buf[0], pitch * j->ny, cudaMemcpyDeviceToDevice, j->stream));
+    int k = 0;
+    net_status s = jacobi_run(j, tol, iter_max, &k, change);
+    if (s != NET_OK) return s;
+    if (sweeps) *sweeps = k;
+    JK(cudaMemcpy2DAsync(d_out, row, j->buf[k & 1], pitch, row, j->ny, cudaMemcpyDeviceToDevice, j->stream));
+    JK(cudaStreamSynchronize(j->stream));
+    return NET_OK;
+}
+
+extern "C" net_status net_jacobi_launches(const net_jacobi_t* j, uint64_t* total) {
+    if (!j || !total) return fail(NET_E_INVAL, "NULL argument");
+    *total = j->launches;
+    return NET_OK;
+}
+
+extern "C" net_status net_jacobi_free(net_jacobi_t* j) {
+    if (!j) return NET_OK;
+    cudaSetDevice(j->device);
+    if (j->stream) cudaStreamSynchronize(j->stream);
+    for (auto& kv : j->graphs) cudaGraphExecDestroy(kv.second);
+    cudaFree(j->buf[0]);
+    cudaFree(j->buf[1]);
+    cudaFree(j->partial);
+    cudaFree(j->d_state);
+    if (j->h_state) cudaFreeHost(j->h_state);
+    if (j->own_stream && j->stream) cudaStreamDestroy(j->stream);
+    delete j;
+    return NET_OK;
+}

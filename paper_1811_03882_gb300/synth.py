@@ -271,6 +271,21 @@ def frame_for(seed: int, index: int, side: int, c: int = 3) -> np.ndarray:
     return make_frames(s, 1, c, side, side)
 
 
+def laplace_grid(seed: int, ny: int, nx: int, interior: str = "zero") -> np.ndarray:
+    """Initial grid of a Laplace problem (ny x nx float32, row-major): the
+    boundary rows and columns uniform in [0, 1); the interior zero, or
+    uniform in [0, 1) too ("random"), drawn after the boundary."""
+    s = Stream(seed)
+    g = np.zeros((ny, nx), np.float64)
+    g[0, :] = s.uniform(nx)
+    g[-1, :] = s.uniform(nx)
+    g[1:-1, 0] = s.uniform(ny - 2)
+    g[1:-1, -1] = s.uniform(ny - 2)
+    if interior == "random":
+        g[1:-1, 1:-1] = s.uniform((ny - 2) * (nx - 2)).reshape(ny - 2, nx - 2)
+    return g.astype(np.float32)
+
+
 def poisson_arrivals(rate_fps: float, duration_s: float, seed: int = SEED_SERVE,
                      sides=(320, 416, 608), cameras: int = 32):
     """Open-loop arrival schedule: ``cameras`` independent Poisson processes
