@@ -69,6 +69,7 @@ def lib():
             D = ctypes.POINTER(ctypes.c_double)
             i, l, d = ctypes.c_int, ctypes.c_long, ctypes.c_double
             L.oracle_conv2d.argtypes = [D, i, i, i, i, D, i, i, D]
+            L.oracle_conv2d_bwd_data.argtypes = [D, i, i, i, i, D, i, i, D]
             L.oracle_batchnorm.argtypes = [D, i, i, l, D, D, D, D, d]
             L.oracle_bias.argtypes = [D, i, i, l, D]
             L.oracle_leaky.argtypes = [D, l, d]
@@ -111,6 +112,18 @@ def conv2d(x, w) -> np.ndarray:
     if y.size:
         lib().oracle_conv2d(_p(x), N, C, H, W, _p(w), O, k, _p(y))
     return y
+
+
+def conv2d_bwd_data(dy, w) -> np.ndarray:
+    """Gradient of conv2d's input: dy: N,O,H,W; w: O,C,k,k -> N,C,H,W."""
+    dy, w = _f64(dy), _f64(w)
+    N, O, H, W = dy.shape
+    O2, C, k, k2 = w.shape
+    assert O == O2 and k == k2 and k % 2 == 1
+    dx = np.empty((N, C, H, W), np.float64)
+    if dx.size:
+        lib().oracle_conv2d_bwd_data(_p(dy), N, O, H, W, _p(w), C, k, _p(dx))
+    return dx
 
 
 def batchnorm(y, gamma, beta, mean, var, eps: float = BN_EPS) -> np.ndarray:

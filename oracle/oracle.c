@@ -80,6 +80,41 @@ void oracle_conv2d(const double* x, int N, int C, int H, int W,
     }
 }
 
+/* Gradient of a conv layer's input (the "nightmare" backward pass):
+ *   dx[n,c,i,j] = sum_{o,kh,kw} dy[n,o,i-kh+p,j-kw+p] * w[o,c,kh,kw],
+ * over the (i-kh+p, j-kw+p) inside the map: the derivative of
+ * y[n,o,a,b] = sum x[n,c,a+kh-p,b+kw-p] w[o,c,kh,kw] with respect to
+ * x[n,c,i,j] (a = i-kh+p, b = j-kw+p).  dy: N,O,H,W; w: O,C,k,k; dx: N,C,H,W. */
+void oracle_conv2d_bwd_data(const double* dy, int N, int O, int H, int W,
+                            const double* w, int C, int k, double* dx) {
+    const int p = (k - 1) / 2;
+    const long HW = (long)H * W;
+    long planes = (long)N * C;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long nc = 0; nc < planes; ++nc) {
+        const int n = (int)(nc / C), c = (int)(nc % C);
+        double* xp = dx + nc * HW;
+        for (long t = 0; t < HW; ++t) xp[t] = 0.0;
+        for (int o = 0; o < O; ++o) {
+            const double* yp = dy + ((long)n * O + o) * HW;
+            for (int kh = 0; kh < k; ++kh) {
+                for (int kw = 0; kw < k; ++kw) {
+                    const double wv = w[(((long)o * C + c) * k + kh) * k + kw];
+                    for (int i = 0; i < H; ++i) {
+                        const int a = i - kh + p;
+                        if (a < 0 || a >= H) continue;
+                        for (int j = 0; j < W; ++j) {
+                            const int b = j - kw + p;
+                            if (b < 0 || b >= W) continue;
+                            xp[(long)i * W + j] += yp[(long)a * W + b] * wv;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
 /* Batchnorm with running statistics, unfolded, per channel o. */
 void oracle_batchnorm(double* y, int N, int O, long HW, const double* gamma,
                       const double* beta, const double* mean, const double* var,
