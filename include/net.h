@@ -228,6 +228,34 @@ net_status net_detect_device(net_t* net, const float* d_map, int batch, int gh, 
 net_status net_forward_detect(net_t* net, const float* in_nchw, int batch, int h, int w, int* counts,
                               net_detection* det);
 
+/* ---- nightmare pass (gradient of a layer's energy) -----------------------
+ * Paper Sec. 5.1.1: the offloaded benchmark also runs Darknet's "nightmare"
+ * app, which changes an image by gradient ascent so that it excites a chosen
+ * layer more.  The objective of layer L is J = 1/2 * sum of the squares of
+ * its output (after its pool); its gradient with respect to the frames flows
+ * back through max pools (to the first maximum of each window, scan order
+ * (0,0), (0,1), (1,0), (1,1); the stride-1 pool gathers what the windows a
+ * position wins send it), leaky rectifiers (times 1 where the activation is
+ * positive, 0.1 elsewhere) and convs (backward-data: a conv with the folded
+ * weights transposed and flipped, on the same CUDA-core kernel as the
+ * forward pass; the batchnorm scale comes with the folded weights).  It runs
+ * on the FP32 path: the handle's every layer NET_FP32 (NET_E_UNSUPPORTED
+ * otherwise); the first call allocates its buffers for (max_batch,
+ * max_side) and builds the backward weights (rebuilt after
+ * net_load_weights). */
+
+/* d_in: batch x in_c x h x w float32 frames, d_grad: the same shape (device,
+ * caller-owned): dJ/d(frames) for layer `layer`; objective (host, batch
+ * doubles, may be NULL): J per frame.  Returns when done. */
+net_status net_nightmare_grad(net_t* net, const float* d_in, int batch, int h, int w, int layer, float* d_grad,
+                              double* objective);
+
+/* One ascent step on device frames in place: x += rate * g / mean(|g|) with
+ * g = dJ/dx of each frame over that frame (mean over its in_c*h*w values);
+ * objective (host, may be NULL): J per frame before the step. */
+net_status net_nightmare_step(net_t* net, float* d_frames, int batch, int h, int w, int layer, float rate,
+                              double* objective);
+
 /* ---- Jacobi solver of the Laplace equation ------------------------------
  * Paper Sec. 4: the sample application that solves the Laplace equation by
  * the Jacobi method (13.5x there), run with the transfer rule of Sec. 3.2:

@@ -120,6 +120,10 @@ _SIGS = {
     "net_launches": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
     "net_inject_device_fault": [ctypes.c_void_p, ctypes.c_int],
     "net_set_region": [ctypes.c_void_p, ctypes.POINTER(net_region)],
+    "net_nightmare_grad": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_void_p, ctypes.c_void_p],
+    "net_nightmare_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_float, ctypes.c_void_p],
     "net_jacobi_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
     "net_jacobi_solve": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int, ctypes.c_void_p,
                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)],
@@ -407,6 +411,18 @@ class Net:
         det = np.zeros((n, self.max_det), DETECTION)
         check(lib().net_forward_detect(self.h, _ptr(x), n, h, w, _ptr(counts), _ptr(det)))
         return counts, det
+
+    def nightmare_grad(self, d_in, batch, h, w, layer, d_grad):
+        """dJ/d(frames) of J = 1/2 sum(output of `layer`)^2 into d_grad; returns J per frame."""
+        obj = np.zeros(batch, np.float64)
+        check(lib().net_nightmare_grad(self.h, _ptr(d_in), batch, h, w, layer, _ptr(d_grad), _ptr(obj)))
+        return obj
+
+    def nightmare_step(self, d_frames, batch, h, w, layer, rate):
+        """One gradient-ascent step on the device frames in place; returns J before it."""
+        obj = np.zeros(batch, np.float64)
+        check(lib().net_nightmare_step(self.h, _ptr(d_frames), batch, h, w, layer, rate, _ptr(obj)))
+        return obj
 
     def inject_device_fault(self, layer: int):
         """Test hook: the next fixed-batch pass faults layer `layer` (see net.h)."""

@@ -360,6 +360,7 @@ extern "C" net_status net_load_weights(net_t* n, const float* blob, size_t n_flo
     cudaFree(tmp);
     if (e != cudaSuccess) return fail(NET_E_CUDA, "weight fold: %s", cudaGetErrorString(e));
     n->weights_loaded = true;
+    n->night_weights_stale = true;
     n->graphs_clear();
     return NET_OK;
 }
@@ -1177,6 +1178,7 @@ extern "C" net_status net_free(net_t* n) {
     cudaFree(n->d_out_stage);
     uneven_free(n);
     region_free(n);
+    night_free(n);
     if (n->own_stream) cudaStreamDestroy(n->stream);
     delete n;
     return NET_OK;

@@ -88,6 +88,7 @@ int tmb_index(int BN);
 struct UnevenState;
 struct ServeState;
 struct RegionState;
+struct NightState;
 
 }  // namespace dn
 
@@ -135,6 +136,8 @@ struct net {
     int fault_layer = -1;      // net_inject_device_fault: layer of the next pass to fault (tests)
     dn::UnevenState* uneven = nullptr;
     dn::RegionState* region = nullptr;   // detection post-processing (net_set_region)
+    dn::NightState* night = nullptr;     // nightmare pass buffers (first net_nightmare_* call)
+    bool night_weights_stale = false;    // weights reloaded since the backward weights were built
     // request queue, started by the first net_submit; serve_mu serialises
     // concurrent first submits so exactly one queue is created
     std::atomic<dn::ServeState*> serve{nullptr};
@@ -159,5 +162,6 @@ void uneven_free(net* n);
 void uneven_graphs_clear(net* n);
 void serve_stop(net* n);
 void region_free(net* n);
+void night_free(net* n);
 
 }  // namespace dn
