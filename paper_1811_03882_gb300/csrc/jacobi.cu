@@ -15,8 +15,10 @@
 //  * jacobi_sweep_kernel: persistent grid (a multiple of the SM count), each
 //    work tile a strip of R rows x 4*blockDim columns; a thread owns four
 //    adjacent columns and walks down the strip keeping the rows above, at
-//    and below in registers (each input row is read once per strip), the
-//    left and right neighbours coming from the adjacent lanes by shuffles.
+//    and below in registers (each input row is read once per strip) with the
+//    next four rows' loads in flight (bytes in flight, not instructions,
+//    bound a streaming kernel), the left and right neighbours coming from
+//    the adjacent lanes by shuffles; sixteen 128-thread blocks per SM.
 //    Each block writes its largest change to a partial slot.
 //  * jacobi_finish_kernel (one block): reduces the partials and applies the
 //    stopping rule on the device: sweeps += 1, done when the change is at or
@@ -50,6 +52,7 @@ struct JState {
 
 constexpr int kThreads = 128;   // 512 columns per tile row
 constexpr int kRows = 32;       // rows per strip
+constexpr int kAhead = 4;       // rows loaded ahead of the one being computed (loads in flight per thread)
 constexpr int kChunk = 16;      // sweeps per captured graph (even: buffer parity is kept per chunk)
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -69,32 +72,49 @@ __global__ void __launch_bounds__(kThreads) jacobi_sweep_kernel(float* b0, float
         const int x0 = (cb * kThreads + threadIdx.x) * 4;   // first of this thread's four columns
         const bool inb = x0 < P;                             // inside the pitched row
         const int y0 = 1 + sb * kRows, y1 = min(y0 + kRows, ny - 1);
-        float4 up = inb ? ld4(src + (size_t)(y0 - 1) * P + x0) : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 cur = inb ? ld4(src + (size_t)y0 * P + x0) : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int y = y0; y < y1; ++y) {   // uniform over the block
-            const float4 dn = inb ? ld4(src + (size_t)(y + 1) * P + x0) : make_float4(0.f, 0.f, 0.f, 0.f);
-            float left = __shfl_up_sync(0xffffffffu, cur.w, 1);
-            float right = __shfl_down_sync(0xffffffffu, cur.x, 1);
-            if (lane == 0) left = (inb && x0 > 0) ? src[(size_t)y * P + x0 - 1] : 0.f;
-            if (lane == 31) right = (x0 + 4 < P) ? src[(size_t)y * P + x0 + 4] : 0.f;
-            float4 nw;
-            nw.x = 0.25f * ((up.x + dn.x) + (left + cur.y));
-            nw.y = 0.25f * ((up.y + dn.y) + (cur.x + cur.z));
-            nw.z = 0.25f * ((up.z + dn.z) + (cur.y + cur.w));
-            nw.w = 0.25f * ((up.w + dn.w) + (cur.z + right));
-            // interior columns 1 .. nx - 2 take the new value; the boundary and
-            // the pitch padding keep theirs
-            const float c4[4] = {cur.x, cur.y, cur.z, cur.w};
-            float n4[4] = {nw.x, nw.y, nw.z, nw.w};
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 up = inb ? ld4(src + (size_t)(y0 - 1) * P + x0) : z4;
+        float4 cur = inb ? ld4(src + (size_t)y0 * P + x0) : z4;
+        // rows y+1 .. y+kAhead in flight: a ring of kAhead registers, slot
+        // (y - y0) % kAhead holding row y + 1 when row y is computed
+        float4 nxt[kAhead];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int x = x0 + q;
-                if (x >= 1 && x <= nx - 2) best = fmaxf(best, fabsf(n4[q] - c4[q]));
-                else n4[q] = c4[q];
+        for (int q = 0; q < kAhead; ++q) {
+            const int yy = y0 + 1 + q;
+            nxt[q] = (inb && yy <= y1) ? ld4(src + (size_t)yy * P + x0) : z4;
+        }
+        for (int yb = y0; yb < y1; yb += kAhead) {   // uniform over the block
+#pragma unroll
+            for (int q = 0; q < kAhead; ++q) {
+                const int y = yb + q;
+                if (y >= y1) break;
+                const float4 dn = nxt[q];
+                const int yy = y + 1 + kAhead;   // refill the slot with the row kAhead further down
+                nxt[q] = (inb && yy <= y1) ? ld4(src + (size_t)yy * P + x0) : z4;
+                float left = __shfl_up_sync(0xffffffffu, cur.w, 1);
+                float right = __shfl_down_sync(0xffffffffu, cur.x, 1);
+                if (lane == 0) left = (inb && x0 > 0) ? src[(size_t)y * P + x0 - 1] : 0.f;
+                if (lane == 31) right = (x0 + 4 < P) ? src[(size_t)y * P + x0 + 4] : 0.f;
+                float4 nw;
+                nw.x = 0.25f * ((up.x + dn.x) + (left + cur.y));
+                nw.y = 0.25f * ((up.y + dn.y) + (cur.x + cur.z));
+                nw.z = 0.25f * ((up.z + dn.z) + (cur.y + cur.w));
+                nw.w = 0.25f * ((up.w + dn.w) + (cur.z + right));
+                // interior columns 1 .. nx - 2 take the new value; the boundary
+                // and the pitch padding keep theirs
+                const float c4[4] = {cur.x, cur.y, cur.z, cur.w};
+                float n4[4] = {nw.x, nw.y, nw.z, nw.w};
+#pragma unroll
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    const int x = x0 + k4;
+                    if (x >= 1 && x <= nx - 2) best = fmaxf(best, fabsf(n4[k4] - c4[k4]));
+                    else n4[k4] = c4[k4];
+                }
+                if (inb)
+                    *reinterpret_cast<float4*>(dst + (size_t)y * P + x0) = make_float4(n4[0], n4[1], n4[2], n4[3]);
+                up = cur;
+                cur = dn;
             }
-            if (inb) *reinterpret_cast<float4*>(dst + (size_t)y * P + x0) = make_float4(n4[0], n4[1], n4[2], n4[3]);
-            up = cur;
-            cur = dn;
         }
     }
 #pragma unroll
@@ -210,8 +230,8 @@ extern "C" net_status net_jacobi_create(int ny, int nx, int device, void* cuda_s
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     j->col_blocks = cdiv(j->P, 4 * kThreads);
     j->strips = cdiv(ny - 2, kRows);
-    // persistent: eight 128-thread blocks per SM, at most one per tile
-    j->grid = std::max(1, std::min(j->col_blocks * j->strips, 8 * sms));
+    // persistent: sixteen 128-thread blocks per SM (2048 threads), at most one per tile
+    j->grid = std::max(1, std::min(j->col_blocks * j->strips, 16 * sms));
     const size_t bytes = (size_t)ny * j->P * sizeof(float);
     for (int b = 0; b < 2; ++b) {
         cudaError_t e = cudaMalloc(&j->buf[b], bytes);
@@ -280,13 +300,19 @@ extern "C" net_status net_jacobi_solve(net_jacobi_t* j, const float* grid_in, fl
     JK(cudaSetDevice(j->device));
     const size_t row = (size_t)j->nx * sizeof(float), pitch = (size_t)j->P * sizeof(float);
     // one host->device copy; the second buffer takes the boundary by a device copy
-    JK(cudaMemcpy2DAsync(j->buf[0], pitch, grid_in, row, row, j->ny, cudaMemcpyHostToDevice, j->stream));
+    if (pitch == row)
+        JK(cudaMemcpyAsync(j->buf[0], grid_in, row * j->ny, cudaMemcpyHostToDevice, j->stream));
+    else
+        JK(cudaMemcpy2DAsync(j->buf[0], pitch, grid_in, row, row, j->ny, cudaMemcpyHostToDevice, j->stream));
     JK(cudaMemcpyAsync(j->buf[1], j->buf[0], pitch * j->ny, cudaMemcpyDeviceToDevice, j->stream));
     int k = 0;
     net_status s = jacobi_run(j, tol, iter_max, &k, change);
     if (s != NET_OK) return s;
     if (sweeps) *sweeps = k;
-    JK(cudaMemcpy2DAsync(grid_out, row, j->buf[k & 1], pitch, row, j->ny, cudaMemcpyDeviceToHost, j->stream));
+    if (pitch == row)
+        JK(cudaMemcpyAsync(grid_out, j->buf[k & 1], row * j->ny, cudaMemcpyDeviceToHost, j->stream));
+    else
+        JK(cudaMemcpy2DAsync(grid_out, row, j->buf[k & 1], pitch, row, j->ny, cudaMemcpyDeviceToHost, j->stream));
     JK(cudaStreamSynchronize(j->stream));
     return NET_OK;
 }
