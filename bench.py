@@ -420,6 +420,56 @@ def run_detect(torch, binding, dev, side=416, batch=8):
                         "one H2D and one D2H per batch"}
 
 
+def run_nightmare(torch, binding, dev, side=416, layer=8, reps=10, cpu_budget_s=4.0):
+    """The nightmare pass (gradient ascent on the frame toward one layer's
+    energy) on the 9-conv network, FP32 path, one 416 x 416 frame, through
+    its last layer: ascent steps timed with CUDA events; algorithmic FLOPs
+    per step = the forward convs through `layer` twice (forward and
+    backward-data), against the FP32 ALU peak; the FP64 oracle's gradient
+    timed on the host over a bounded sample."""
+    from oracle import nightmare as onm
+    pk, _ = peaks()
+    spec = synth.net_9conv()
+    _, x, blob = synth.workload_net(spec, synth.SEED_9CONV, 1, side, side)
+    st = torch.cuda.Stream()
+    net = binding.Net(spec.layers, 3, prec="fp32", max_batch=1, max_side=side, stream=st.cuda_stream, device=dev)
+    net.load_weights(blob)
+    d_x = torch.from_numpy(x).cuda()
+    for _ in range(2):
+        net.nightmare_step(d_x, 1, side, side, layer, 0.01)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    l0 = net.launches()
+    ev[0].record(st)
+    for _ in range(reps):
+        J = net.nightmare_step(d_x, 1, side, side, layer, 0.01)
+    ev[1].record(st)
+    torch.cuda.synchronize()
+    launches = (net.launches() - l0) // reps
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    net.close()
+    flops, h = 0.0, side
+    for l, ci in list(zip(spec.layers, spec.cins()))[:layer + 1]:
+        flops += 2.0 * 2.0 * h * h * l.cout * ci * l.k * l.k
+        if l.pool == synth.POOL_2X2S2:
+            h //= 2
+    tf = flops / (ms / 1e3) / 1e12
+    peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    n, t0 = 0, time.perf_counter()
+    while True:
+        onm.input_grad(spec.layers, 3, x, blob, layer)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= cpu_budget_s:
+            break
+    return {"network": "9-conv", "side": side, "layer": layer, "dtype": "f32", "ms_per_step": ms,
+            "steps_per_s": 1e3 / ms, "gpu_launches_per_step": int(launches), "objective_last": float(J[0]),
+            "roofline": {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                         "traffic": None, "kernel": "conv_simt_kernel (forward + backward-data)",
+                         "flops_per_step": flops, "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"},
+            "cpu_baseline": {"steps_per_s": n / el, "kind": "oracle (FP64 gradient)", "cores": onm.oracle.threads(),
+                             "sample": "%d gradient(s), %.1f s" % (n, el)}}
+
+
 class Workload:
     """Frames, weights and step functions of one bench workload."""
 
@@ -743,6 +793,7 @@ def main():
     if not args.no_extra and rank == 0:
         line["detect"] = run_detect(torch, binding, dev)
         line["jacobi"] = run_jacobi(torch, binding, dev)
+        line["nightmare"] = run_nightmare(torch, binding, dev)
     if rank == 0 and not args.no_cpu_baseline:
         f0 = W.frames[0][:1]
         fps, nfr, el, cores = oracle_frames_per_s(W.spec, f0, W.blob, args.cpu_budget_s)

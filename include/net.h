@@ -250,6 +250,15 @@ net_status net_forward_detect(net_t* net, const float* in_nchw, int batch, int h
 net_status net_nightmare_grad(net_t* net, const float* d_in, int batch, int h, int w, int layer, float* d_grad,
                               double* objective);
 
+/* As net_nightmare_grad, and also writes, for every layer l <= layer, its
+ * activation before its pool into d_act[l] (batch x cout x H_l x W_l, the
+ * conv's output size) and the gradient with respect to its output (after
+ * its pool) into d_gout[l] (NCHW float32, device pointers, one per layer,
+ * each sized for that tensor).  Diagnostic path (per-layer checks against
+ * the oracle); the paper has no counterpart. */
+net_status net_nightmare_trace(net_t* net, const float* d_in, int batch, int h, int w, int layer, float* d_grad,
+                               float* const* d_act, float* const* d_gout);
+
 /* One ascent step on device frames in place: x += rate * g / mean(|g|) with
  * g = dJ/dx of each frame over that frame (mean over its in_c*h*w values);
  * objective (host, may be NULL): J per frame before the step. */

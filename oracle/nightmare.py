@@ -94,22 +94,29 @@ def leaky_bwd(g, z):
     return oracle._f64(g) * np.where(oracle._f64(z) > 0, 1.0, oracle.LEAKY_SLOPE)
 
 
+def layer_backward(L, p, h, gout):
+    """Gradient with respect to layer L's input from the gradient of its
+    output, given its activation before the pool h (whose sign is the
+    pre-activation's: the leaky rectifier keeps signs) and its parameters p
+    (a dict of oracle.parse_blob)."""
+    g = oracle._f64(gout)
+    if L.pool == oracle.POOL_2X2S2:
+        g = maxpool2_s2_bwd(g, h)
+    elif L.pool == oracle.POOL_2X2S1_SAME:
+        g = maxpool2_s1_same_bwd(g, h)
+    if L.act == oracle.ACT_LEAKY:
+        g = leaky_bwd(g, h)
+    if L.bn:
+        g = g * (p["gamma"] / np.sqrt(p["var"] + oracle.BN_EPS))[None, :, None, None]
+    return oracle.conv2d_bwd_data(g, p["w"])
+
+
 def input_grad(layers, in_c: int, x, blob, layer: int):
     """dJ/dx of J = 1/2 * sum(output of `layer`)^2, and J."""
     saved, out = forward_saving(layers, in_c, x, blob, layer)
     g = out.copy()
     for l in range(layer, -1, -1):
-        L, s = layers[l], saved[l]
-        if L.pool == oracle.POOL_2X2S2:
-            g = maxpool2_s2_bwd(g, s["h"])
-        elif L.pool == oracle.POOL_2X2S1_SAME:
-            g = maxpool2_s1_same_bwd(g, s["h"])
-        if L.act == oracle.ACT_LEAKY:
-            g = leaky_bwd(g, s["z"])
-        p = s["p"]
-        if L.bn:
-            g = g * (p["gamma"] / np.sqrt(p["var"] + oracle.BN_EPS))[None, :, None, None]
-        g = oracle.conv2d_bwd_data(g, p["w"])
+        g = layer_backward(layers[l], saved[l]["p"], saved[l]["h"], g)
     return g, 0.5 * float((out * out).sum())
 
 

@@ -122,6 +122,8 @@ _SIGS = {
     "net_set_region": [ctypes.c_void_p, ctypes.POINTER(net_region)],
     "net_nightmare_grad": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                            ctypes.c_void_p, ctypes.c_void_p],
+    "net_nightmare_trace": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "net_nightmare_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                            ctypes.c_float, ctypes.c_void_p],
     "net_jacobi_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
@@ -417,6 +419,12 @@ class Net:
         obj = np.zeros(batch, np.float64)
         check(lib().net_nightmare_grad(self.h, _ptr(d_in), batch, h, w, layer, _ptr(d_grad), _ptr(obj)))
         return obj
+
+    def nightmare_trace(self, d_in, batch, h, w, layer, d_grad, d_acts, d_gouts):
+        """As nightmare_grad, also each layer's pre-pool activation and output gradient."""
+        a = (ctypes.c_void_p * len(d_acts))(*[t.data_ptr() for t in d_acts])
+        g = (ctypes.c_void_p * len(d_gouts))(*[t.data_ptr() for t in d_gouts])
+        check(lib().net_nightmare_trace(self.h, _ptr(d_in), batch, h, w, layer, _ptr(d_grad), a, g))
 
     def nightmare_step(self, d_frames, batch, h, w, layer, rate):
         """One gradient-ascent step on the device frames in place; returns J before it."""

@@ -319,7 +319,8 @@ static net_status night_conv(net* n, const void* x, const void* w, int w_rows, v
 // Forward through `layer` keeping activations, then the gradient back to the
 // frames (NCHW float32 into d_grad); J = 1/2 sum(output of layer)^2 per frame
 // into S->d_red.
-static net_status night_grad(net* n, const float* d_in, int batch, int h, int w, int layer, float* d_grad) {
+static net_status night_grad(net* n, const float* d_in, int batch, int h, int w, int layer, float* d_grad,
+                             float* const* t_act = nullptr, float* const* t_gout = nullptr) {
     NightState* S = n->night;
     cudaStream_t st = n->stream;
     std::vector<int> H, W;
@@ -343,6 +344,10 @@ static net_status night_grad(net* n, const float* d_in, int batch, int h, int w,
         ep.cout = L.d.cout;
         net_status s = night_conv(n, x, L.w, L.w_rows, S->h[l], batch, H[l], W[l], L.in_cs, L.d.k, ep);
         if (s != NET_OK) return s;
+        if (t_act && t_act[l]) {
+            NK(unpack_nchw(S->h[l], t_act[l], batch, L.d.cout, H[l], W[l], cs, DT_F32, 1.f, st));
+            ++n->launches;
+        }
         if (L.d.pool == NET_POOL_2X2S2) {
             ab ^= 1;
             const long long tot = (long long)batch * H[l + 1] * W[l + 1] * cs;
@@ -365,14 +370,20 @@ static net_status night_grad(net* n, const float* d_in, int batch, int h, int w,
     frame_reduce_kernel<<<batch, 1024, 0, st>>>(x, per_frame, per_frame, 0, S->d_red);
     NK(cudaGetLastError());
     ++n->launches;
-    // ---- backward: dJ/d(output of layer) = that output
+    // ---- backward: dJ/d(output of layer) = that output.  g[1] holds the
+    // gradient before a layer's pool and leaky, g[0] the one after its conv
+    // (the next layer down's output gradient): no kernel reads the buffer it
+    // writes.
     const float* gout = x;
-    int gb = 0;
     for (int l = layer; l >= 0; --l) {
         const Layer& L = n->L[l];
         const int cs = rup(L.d.cout, 4);
         const long long tot = (long long)batch * H[l] * W[l] * cs;
-        float* gh = S->g[gb];
+        float* gh = S->g[1];
+        if (t_gout && t_gout[l]) {
+            NK(unpack_nchw(gout, t_gout[l], batch, L.d.cout, H[l + 1], W[l + 1], cs, DT_F32, 1.f, st));
+            ++n->launches;
+        }
         const int leaky = L.d.act == NET_ACT_LEAKY ? 1 : 0;
         if (L.d.pool == NET_POOL_2X2S2)
             pool_leaky_bwd_kernel<PB_S2><<<grid_for(tot, 256), 256, 0, st>>>(gout, S->h[l], gh, batch, H[l], W[l], cs,
@@ -402,12 +413,11 @@ static net_status night_grad(net* n, const float* d_in, int batch, int h, int w,
         } else {
             ep.out_layout = LAYOUT_NHWC;
             ep.out_cs = L.in_cs;
-            y = S->g[gb ^ 1];
+            y = S->g[0];
         }
         net_status s = night_conv(n, gh, S->wt[l], rup(L.cin, 256), y, batch, H[l], W[l], cs, L.d.k, ep);
         if (s != NET_OK) return s;
-        gout = S->g[gb ^ 1];
-        gb ^= 1;
+        gout = S->g[0];
     }
     return NET_OK;
 }
@@ -444,6 +454,17 @@ extern "C" net_status net_nightmare_grad(net_t* n, const float* d_in, int batch,
     NK(cudaStreamSynchronize(n->stream));
     if (objective)
         for (int f = 0; f < batch; ++f) objective[f] = 0.5 * n->night->h_red[f];
+    return check_device_error(n);
+}
+
+extern "C" net_status net_nightmare_trace(net_t* n, const float* d_in, int batch, int h, int w, int layer,
+                                          float* d_grad, float* const* d_act, float* const* d_gout) {
+    if (!d_grad || !d_act || !d_gout) return fail(NET_E_INVAL, "NULL argument");
+    net_status s = night_check(n, d_in, batch, h, w, layer);
+    if (s != NET_OK) return s;
+    s = night_grad(n, d_in, batch, h, w, layer, d_grad, d_act, d_gout);
+    if (s != NET_OK) return s;
+    NK(cudaStreamSynchronize(n->stream));
     return check_device_error(n);
 }
 

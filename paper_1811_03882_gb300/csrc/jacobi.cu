@@ -51,7 +51,6 @@ struct JState {
 };
 
 constexpr int kThreads = 128;   // 512 columns per tile row
-constexpr int kRows = 32;       // rows per strip
 constexpr int kAhead = 4;       // rows loaded ahead of the one being computed (loads in flight per thread)
 constexpr int kChunk = 16;      // sweeps per captured graph (even: buffer parity is kept per chunk)
 
@@ -59,7 +58,7 @@ __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast
 
 __global__ void __launch_bounds__(kThreads) jacobi_sweep_kernel(float* b0, float* b1, int ny, int nx, int P,
                                                                 const JState* __restrict__ st, float* partial,
-                                                                int col_blocks, int strips) {
+                                                                int col_blocks, int strips, int rows) {
     if (st->done) return;
     const int k = st->sweeps;
     const float* src = (k & 1) ? b1 : b0;
@@ -71,7 +70,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_sweep_kernel(float* b0, float
         const int cb = tile % col_blocks, sb = tile / col_blocks;
         const int x0 = (cb * kThreads + threadIdx.x) * 4;   // first of this thread's four columns
         const bool inb = x0 < P;                             // inside the pitched row
-        const int y0 = 1 + sb * kRows, y1 = min(y0 + kRows, ny - 1);
+        const int y0 = 1 + sb * rows, y1 = min(y0 + rows, ny - 1);
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 up = inb ? ld4(src + (size_t)(y0 - 1) * P + x0) : z4;
         float4 cur = inb ? ld4(src + (size_t)y0 * P + x0) : z4;
@@ -158,7 +157,7 @@ struct net_jacobi {
     float* partial = nullptr;
     JState* d_state = nullptr;
     JState* h_state = nullptr;        // pinned, two slots (chunks in flight)
-    int grid = 0, col_blocks = 0, strips = 0;
+    int grid = 0, col_blocks = 0, strips = 0, rows = 0;
     std::map<std::pair<float, int>, cudaGraphExec_t> graphs;   // per (tol, iter_max)
     uint64_t launches = 0;
 };
@@ -183,7 +182,7 @@ static net_status jacobi_graph(net_jacobi* j, float tol, int iter_max, cudaGraph
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < kChunk && e == cudaSuccess; ++s) {
         jacobi_sweep_kernel<<<j->grid, kThreads, 0, j->stream>>>(j->buf[0], j->buf[1], j->ny, j->nx, j->P, j->d_state,
-                                                                 j->partial, j->col_blocks, j->strips);
+                                                                 j->partial, j->col_blocks, j->strips, j->rows);
         jacobi_finish_kernel<<<1, 1024, 0, j->stream>>>(j->partial, j->grid, j->d_state, tol, iter_max);
         e = cudaGetLastError();
     }
@@ -228,10 +227,15 @@ extern "C" net_status net_jacobi_create(int ny, int nx, int device, void* cuda_s
     }
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    // persistent: sixteen 128-thread blocks per SM (2048 threads); the strips
+    // are cut so that the tiles come out at one per block when the grid is
+    // large (no second, partial wave), at least 8 rows each
     j->col_blocks = cdiv(j->P, 4 * kThreads);
-    j->strips = cdiv(ny - 2, kRows);
-    // persistent: sixteen 128-thread blocks per SM (2048 threads), at most one per tile
-    j->grid = std::max(1, std::min(j->col_blocks * j->strips, 16 * sms));
+    const int target = 16 * sms;
+    const int want = std::max(1, target / j->col_blocks);
+    j->rows = std::max(8, cdiv(ny - 2, want));
+    j->strips = cdiv(ny - 2, j->rows);
+    j->grid = std::max(1, std::min(j->col_blocks * j->strips, target));
     const size_t bytes = (size_t)ny * j->P * sizeof(float);
     for (int b = 0; b < 2; ++b) {
         cudaError_t e = cudaMalloc(&j->buf[b], bytes);
