@@ -205,6 +205,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+template <int CW>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
+    if constexpr (CW == 32) tmem_ld32(taddr, v);
+    else tmem_ld16(taddr, v);
+}
+
 // Problem whose M tiles contain tile mt (tile_begin is increasing).
 __device__ __forceinline__ int find_problem(const ConvProblem* probs, int nprob, int mt) {
     int lo = 0, hi = nprob - 1;
@@ -228,15 +234,24 @@ struct Smem {
 
 }  // namespace tc
 
-template <int BN, int DT>
-__global__ void __launch_bounds__(tc::THREADS, 1)
+// MB = CTAs per SM: 1, or 2 for launches of many short tiles (few K steps
+// each), whose time goes to the epilogue warps' dependent instruction chains:
+// two CTAs give each SM sub-partition four epilogue warps instead of two.
+// With MB = 2 a CTA has at most 80 registers a thread (the epilogue drains
+// 16 columns at a time), half the shared memory and at most 256 TMEM
+// columns, so that two CTAs always fit on an SM at once.
+template <int BN, int DT, int MB>
+__global__ void __launch_bounds__(tc::THREADS, MB)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     using namespace tc;
-    // accumulator buffers in TMEM (512 columns): four up to BN = 128, so the
-    // MMAs of the next tiles never wait for an epilogue's round trip
-    constexpr int NBUF = BN <= 128 ? 4 : 2;
-    constexpr int NBUF_LOG = BN <= 128 ? 2 : 1;
+    static_assert(MB == 1 || (MB == 2 && BN <= 128), "two CTAs per SM: N tiles of at most 128 columns");
+    // accumulator buffers in TMEM (512 columns an SM): four up to BN = 128,
+    // so the MMAs of the next tiles never wait for an epilogue's round trip;
+    // with two CTAs an SM, 256 columns each
+    constexpr int NBUF = MB == 2 ? 256 / BN : (BN <= 128 ? 4 : 2);
+    constexpr int NBUF_LOG = NBUF == 4 ? 2 : NBUF == 2 ? 1 : 0;
     constexpr int TMEM_COLS = NBUF * BN;
+    constexpr int CW = MB == 2 ? 16 : 32;   // epilogue columns per TMEM load
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     // ring stages of st_bytes at smem (A box, then B box), resident weights at
@@ -681,21 +696,17 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             // K-alternating mode: add the second accumulator (odd K steps),
             // 16 columns at a time to keep registers down
             auto add_pair = [&](uint32_t taddr, float* v) {
-                float u[16];
-                tc::tmem_ld16(taddr, u);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float2 r = __fadd2_rn(make_float2(v[2 * j], v[2 * j + 1]), make_float2(u[2 * j], u[2 * j + 1]));
-                    v[2 * j] = r.x;
-                    v[2 * j + 1] = r.y;
-                }
-                tc::tmem_ld16(taddr + 16u, u);
+                for (int h16 = 0; h16 < CW; h16 += 16) {
+                    float u[16];
+                    tc::tmem_ld16(taddr + (uint32_t)h16, u);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float2 r =
-                        __fadd2_rn(make_float2(v[16 + 2 * j], v[17 + 2 * j]), make_float2(u[2 * j], u[2 * j + 1]));
-                    v[16 + 2 * j] = r.x;
-                    v[17 + 2 * j] = r.y;
+                    for (int j = 0; j < 8; ++j) {
+                        const float2 r = __fadd2_rn(make_float2(v[h16 + 2 * j], v[h16 + 2 * j + 1]),
+                                                    make_float2(u[2 * j], u[2 * j + 1]));
+                        v[h16 + 2 * j] = r.x;
+                        v[h16 + 2 * j + 1] = r.y;
+                    }
                 }
             };
             bool released = false;
@@ -717,15 +728,15 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 float* wr = a.ws + (size_t)z * a.m_tiles * 128 * ncp +
                             ((size_t)mt * (ncp >> 2) + ((nt * BN + half * HC) >> 2)) * 512 + row * 4;
 #pragma unroll 1
-                for (int c0 = 0; c0 < HC; c0 += 32) {
+                for (int c0 = 0; c0 < HC; c0 += CW) {
                     if (nt * BN + half * HC + c0 >= live) break;
-                    float v[32];
+                    float v[CW];
                     __syncwarp();
-                    tc::tmem_ld32(trow + (uint32_t)c0, v);
+                    tc::tmem_ld<CW>(trow + (uint32_t)c0, v);
                     if (a.kalt) add_pair(trow + (uint32_t)(BN + c0), v);
-                    if (c0 + 32 >= HC || nt * BN + half * HC + c0 + 32 >= live) release();
+                    if (c0 + CW >= HC || nt * BN + half * HC + c0 + CW >= live) release();
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4)
+                    for (int j = 0; j < CW; j += 4)
                         *reinterpret_cast<float4*>(wr + (size_t)((c0 + j) >> 2) * 512) =
                             make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                 }
@@ -756,31 +767,31 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 const bool writer = valid && (!pool || ((lane & 1) == 0 && (lane & ymask) == 0));
                 const size_t pix = ((size_t)img * Ho + yo) * Wo + xo;
 #pragma unroll 1
-                for (int c0 = 0; c0 < HC; c0 += 32) {
+                for (int c0 = 0; c0 < HC; c0 += CW) {
                     const int o0 = nt * BN + half * HC + c0;   // first output channel of the chunk
                     if (o0 >= live) break;
                     // bias / alpha are padded with zeros to the weight rows: no bounds
                     // checks; loaded before the TMEM read so the two latencies overlap
-                    float bb[32];
+                    float bb[CW];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
+                    for (int j = 0; j < CW / 4; ++j) {
                         const float4 t = reinterpret_cast<const float4*>(e_bias + o0)[j];
                         bb[4 * j] = t.x;
                         bb[4 * j + 1] = t.y;
                         bb[4 * j + 2] = t.z;
                         bb[4 * j + 3] = t.w;
                     }
-                    float v[32];
+                    float v[CW];
                     __syncwarp();
-                    tc::tmem_ld32(trow + (uint32_t)c0, v);
+                    tc::tmem_ld<CW>(trow + (uint32_t)c0, v);
                     if (a.kalt) add_pair(trow + (uint32_t)(BN + c0), v);
-                    if (c0 + 32 >= HC || o0 + 32 >= live) release();
+                    if (c0 + CW >= HC || o0 + CW >= live) release();
                     // warp-uniform branches: each variant is one straight-line loop.
                     // Paired FP32 operations (one instruction on a register
                     // pair) round exactly as the scalar ones.
                     if (a.ep.alpha) {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
+                        for (int j = 0; j < CW / 4; ++j) {
                             const float4 t = reinterpret_cast<const float4*>(e_alpha + o0)[j];
                             const float2 lo = __ffma2_rn(make_float2(v[4 * j], v[4 * j + 1]), make_float2(t.x, t.y),
                                                          make_float2(bb[4 * j], bb[4 * j + 1]));
@@ -793,7 +804,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         }
                     } else {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
+                        for (int j = 0; j < CW / 2; ++j) {
                             const float2 r = __fadd2_rn(make_float2(v[2 * j], v[2 * j + 1]),
                                                         make_float2(bb[2 * j], bb[2 * j + 1]));
                             v[2 * j] = r.x;
@@ -804,7 +815,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         // leaky(v) = max(v, 0.1 v): v for v > 0, 0.1 v otherwise
                         const float2 slope = make_float2(kLeakySlope, kLeakySlope);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
+                        for (int j = 0; j < CW / 2; ++j) {
                             const float2 s2 = __fmul2_rn(make_float2(v[2 * j], v[2 * j + 1]), slope);
                             v[2 * j] = fmaxf(v[2 * j], s2.x);
                             v[2 * j + 1] = fmaxf(v[2 * j + 1], s2.y);
@@ -813,7 +824,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     if (a.ep.out_layout == LAYOUT_NCHW) {
                         if (pool) {
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
+                            for (int j = 0; j < CW; ++j) {
                                 v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
                                 v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], ymask));
                             }
@@ -821,7 +832,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         if (writer) {
                             float* yf = reinterpret_cast<float*>(ybase);
 #pragma unroll
-                            for (int j = 0; j < 32; ++j)
+                            for (int j = 0; j < CW; ++j)
                                 if (o0 + j < a.ep.cout)
                                     yf[(((size_t)img * a.ep.cout + o0 + j) * Ho + yo) * Wo + xo] = v[j];
                         }
@@ -830,15 +841,15 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     if (a.ep.out_dt == DT_BF16) {
                         // round first, then pool on packed pairs: RNE is monotone,
                         // so max(rn(a), rn(b)) == rn(max(a, b)) and half the shuffles go
-                        uint32_t w[16];
+                        uint32_t w[CW / 2];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
+                        for (int j = 0; j < CW / 2; ++j) {
                             __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
                             w[j] = *reinterpret_cast<uint32_t*>(&h2);
                         }
                         if (pool) {
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) {
+                            for (int j = 0; j < CW / 2; ++j) {
                                 uint32_t o = __shfl_xor_sync(0xffffffffu, w[j], 1);
                                 __nv_bfloat162 m = __hmax2(*reinterpret_cast<__nv_bfloat162*>(&w[j]),
                                                            *reinterpret_cast<__nv_bfloat162*>(&o));
@@ -852,35 +863,36 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         if (writer && o0 < a.ep.out_cs) {
                             uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ybase) +
                                                                   pix * a.ep.out_cs + o0);
-                            // out_cs is 16, 32 or a multiple of 64: a 32-channel chunk may be half outside
-                            const int nvec = (a.ep.out_cs - o0) >= 32 ? 4 : 2;
+                            // out_cs is 16, 32 or a multiple of 64: a 32-channel chunk
+                            // may be half outside, a 16-channel one is not
+                            const int nvec = (a.ep.out_cs - o0) >= CW ? CW / 8 : 2;
 #pragma unroll
-                            for (int i = 0; i < 4; ++i)
+                            for (int i = 0; i < CW / 8; ++i)
                                 if (i < nvec) dst[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
                         }
                         continue;
                     }
                     if (pool) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
+                        for (int j = 0; j < CW; ++j) {
                             v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
                             v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], ymask));
                         }
                     }
                     if (!writer || o0 >= a.ep.out_cs) continue;
                     if (a.ep.out_dt == DT_FP8) {
-                        uint4 pk[2];
+                        uint4 pk[CW / 16];
                         uint8_t* w8 = reinterpret_cast<uint8_t*>(pk);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) w8[j] = f32_to_e4m3_sat(v[j] * a.ep.out_inv_scale);
+                        for (int j = 0; j < CW; ++j) w8[j] = f32_to_e4m3_sat(v[j] * a.ep.out_inv_scale);
                         uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(ybase) + pix * a.ep.out_cs + o0);
                         // out_cs is 32, 64 or a multiple of 128 here
-                        dst[0] = pk[0];
-                        dst[1] = pk[1];
+#pragma unroll
+                        for (int i = 0; i < CW / 16; ++i) dst[i] = pk[i];
                     } else {
                         float* dst = reinterpret_cast<float*>(ybase) + pix * a.ep.out_cs + o0;
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4)
+                        for (int j = 0; j < CW; j += 4)
                             if (o0 + j < a.ep.out_cs)
                                 *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                     }
@@ -961,21 +973,22 @@ cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, 
 }
 
 constexpr size_t kSmemLimit = 232448;   // opt-in dynamic shared memory per block (227 KB)
+constexpr size_t kSmemLimit2 = 115712;  // per block with two blocks an SM (228 KB - 2 x 1 KB reserved, halved)
 
 static size_t tc_ctrl_bytes() {
     return ((sizeof(tc::Smem) + 15) & ~(size_t)15) + 2 * tc::kEpiCols * sizeof(float);
 }
-static size_t tc_avail() { return kSmemLimit - 1024 - tc_ctrl_bytes(); }
+static size_t tc_avail(int mb) { return (mb == 2 ? kSmemLimit2 : kSmemLimit) - 1024 - tc_ctrl_bytes(); }
 
 // Ring geometry: as many stages of (A box + B box, or A only with resident
 // weights) as fit beside the resident weights and the control block.
-static bool tc_geometry(int BN, int chb, int bres, int nk, TcArgs* g) {
+static bool tc_geometry(int BN, int chb, int bres, int nk, int mb, TcArgs* g) {
     const size_t a_bytes = g->tapm ? 3 * (size_t)(g->TH + 2) * g->TW * chb : 128 * (size_t)chb;
     const size_t b_bytes = (size_t)BN * chb;
     const size_t st = a_bytes + (bres ? 0 : b_bytes);
     const size_t bres_bytes = bres ? (size_t)(g->pair ? tc::kPairSlots : nk) * b_bytes : 0;
-    if (tc_avail() < bres_bytes + 2 * st) return false;
-    int nst = (int)std::min<size_t>(tc::kMaxStages, (tc_avail() - bres_bytes) / st) & ~1;
+    if (tc_avail(mb) < bres_bytes + 2 * st) return false;
+    int nst = (int)std::min<size_t>(tc::kMaxStages, (tc_avail(mb) - bres_bytes) / st) & ~1;
     // producer lanes: four per warp on deep rings (stage count cut to a
     // multiple of eight).  The lanes of a warp issue in lockstep, so on a
     // shallow ring one lane per warp keeps stages refilling one by one.
@@ -992,19 +1005,21 @@ static bool tc_geometry(int BN, int chb, int bres, int nk, TcArgs* g) {
     return true;
 }
 
-bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb) {
-    // resident weights must leave room for at least 8 A-only stages
-    return n_tiles == 1 && ksplit == 1 && (size_t)nk * BN * chb + 8 * 128 * (size_t)chb <= tc_avail();
+bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb, int mb) {
+    // resident weights must leave room for at least 8 A-only stages (4 with
+    // two CTAs an SM)
+    const size_t a_st = (mb == 2 ? 4 : 8) * 128 * (size_t)chb;
+    return n_tiles == 1 && ksplit == 1 && (size_t)nk * BN * chb + a_st <= tc_avail(mb);
 }
 
-template <int BN, int DT>
+template <int BN, int DT, int MB>
 static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int workers, cudaStream_t st) {
     TcArgs a = a0;
     // 16-byte chunks (K = 8) only in pair mode, and pair mode only in its one shape
     if ((a.chb == 16) != (a.pair != 0)) return cudaErrorInvalidValue;
     if (a.pair && (DT != DT_BF16 || !a.tapm || !a.bres || a.ksplit != 1 || a.k != 3 || a.chunks != 1 || a.kalt))
         return cudaErrorInvalidValue;
-    if (!tc_geometry(BN, a.chb, a.bres, a.k * a.k * a.chunks, &a)) return cudaErrorInvalidValue;
+    if (!tc_geometry(BN, a.chb, a.bres, a.k * a.k * a.chunks, MB, &a)) return cudaErrorInvalidValue;
     if (a.ksplit < 1 || a.n_tiles < 1 || a.chunks < 1 || a.k < 1) return cudaErrorInvalidValue;
     a.fd_ksplit = make_fast_div(a.ksplit);
     a.fd_ntiles = make_fast_div(a.n_tiles);
@@ -1013,10 +1028,12 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     a.fd_nst = make_fast_div(a.nst);
     if (a.wait_limit <= 0) a.wait_limit = tc::WAIT_LIMIT;
     const size_t smem = 1024 + (size_t)a.ctrl_off + tc_ctrl_bytes();
-    auto kern = conv_tc_kernel<BN, DT>;
+    if (smem > (MB == 2 ? kSmemLimit2 : kSmemLimit)) return cudaErrorInvalidValue;
+    auto kern = conv_tc_kernel<BN, DT, MB>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(MB == 2 ? kSmemLimit2 : kSmemLimit));
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -1037,15 +1054,24 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     return cudaLaunchKernelEx(&cfg, kern, tmB, a);
 }
 
-cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, cudaStream_t st) {
+cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, int mb,
+                           cudaStream_t st) {
+    if (mb == 2) {
+        if (dt == DT_BF16 && BN == 64) return launch_tc_bn<64, DT_BF16, 2>(tmB, a, workers, st);
+        if (dt == DT_BF16 && BN == 128) return launch_tc_bn<128, DT_BF16, 2>(tmB, a, workers, st);
+        if (dt == DT_FP8 && BN == 64) return launch_tc_bn<64, DT_FP8, 2>(tmB, a, workers, st);
+        if (dt == DT_FP8 && BN == 128) return launch_tc_bn<128, DT_FP8, 2>(tmB, a, workers, st);
+        return cudaErrorInvalidValue;
+    }
+    if (mb != 1) return cudaErrorInvalidValue;
     if (dt == DT_BF16) {
-        if (BN == 64) return launch_tc_bn<64, DT_BF16>(tmB, a, workers, st);
-        if (BN == 128) return launch_tc_bn<128, DT_BF16>(tmB, a, workers, st);
-        if (BN == 256) return launch_tc_bn<256, DT_BF16>(tmB, a, workers, st);
+        if (BN == 64) return launch_tc_bn<64, DT_BF16, 1>(tmB, a, workers, st);
+        if (BN == 128) return launch_tc_bn<128, DT_BF16, 1>(tmB, a, workers, st);
+        if (BN == 256) return launch_tc_bn<256, DT_BF16, 1>(tmB, a, workers, st);
     } else if (dt == DT_FP8) {
-        if (BN == 64) return launch_tc_bn<64, DT_FP8>(tmB, a, workers, st);
-        if (BN == 128) return launch_tc_bn<128, DT_FP8>(tmB, a, workers, st);
-        if (BN == 256) return launch_tc_bn<256, DT_FP8>(tmB, a, workers, st);
+        if (BN == 64) return launch_tc_bn<64, DT_FP8, 1>(tmB, a, workers, st);
+        if (BN == 128) return launch_tc_bn<128, DT_FP8, 1>(tmB, a, workers, st);
+        if (BN == 256) return launch_tc_bn<256, DT_FP8, 1>(tmB, a, workers, st);
     }
     return cudaErrorInvalidValue;
 }

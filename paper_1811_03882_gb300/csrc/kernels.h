@@ -191,11 +191,14 @@ cudaError_t maxpool_s1_grouped(const PoolJob* jobs, int njobs, long long total, 
 
 int tc_chunk_bytes(int Cp, int dt);
 // Whether a launch keeps all of its weights resident in shared memory: one
-// N tile, no K split, and nk boxes of BN x chunk bytes fit in the B ring.
-bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb);
+// N tile, no K split, and nk boxes of BN x chunk bytes fit in the B ring
+// (of a CTA's share of the SM: mb CTAs an SM).
+bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb, int mb);
 cudaError_t tc_encode_act(CUtensorMap* tm, const void* base, int dt, int n, int H, int W, int Cp, int TW,
                           int TH);
 cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, int KK, int Cp, int BN);
-// workers = persistent CTAs; tmB has box rows BN.
-cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, cudaStream_t st);
+// workers = persistent CTAs; tmB has box rows BN; mb = CTAs per SM (1, or 2
+// for BN <= 128: half the shared memory and TMEM, 80 registers a thread).
+cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, int mb,
+                           cudaStream_t st);
 }  // namespace dn

@@ -429,12 +429,31 @@ void dn::tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, i
     *BN = ncols > 128 ? 256 : ncols > 64 ? 128 : 64;   // refined by tc_choose_split
 }
 
-// Persistent worker count and resident-weight mode of a tensor-core launch:
-// one CTA per SM, at most one per work item.
-void dn::tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int num_sms, int* workers, int* bres) {
-    *bres = tc_b_resident(BN, n_tiles, ks, nk, chb) ? 1 : 0;
+// CTAs per SM, persistent worker count and resident-weight mode of a
+// tensor-core launch.  Two CTAs an SM (mb_req = 0: chosen here; 1 or 2:
+// forced) double the epilogue warps, which bound launches of many short
+// tiles, but halve each CTA's shared memory: only for N tiles of at most 128
+// columns, at least one tile an SM, and weights that stay resident (A-only
+// stages) or at most two K steps per work item (a halved ring of A + B
+// stages would starve a longer mainloop).
+void dn::tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int num_sms, int mb_req, int* workers,
+                    int* bres, int* mb) {
     const int items = m_tiles * n_tiles * ks;
-    *workers = std::max(1, std::min(items, num_sms));
+    const bool res2 = BN <= 128 && tc_b_resident(BN, n_tiles, ks, nk, chb, 2);
+    int m = 1;
+    if (mb_req == 2 && BN <= 128) m = 2;
+    else if (mb_req == 0 && BN <= 128 && items >= num_sms && (res2 || nk / ks <= 2)) m = 2;
+    *mb = m;
+    *bres = tc_b_resident(BN, n_tiles, ks, nk, chb, m) ? 1 : 0;
+    *workers = std::max(1, std::min(items, num_sms * m));
+}
+
+int dn::tc_mb_forced() {
+    static const int v = [] {
+        const char* e = getenv("NET_TC_MB");
+        return e ? atoi(e) : 0;
+    }();
+    return v == 1 || v == 2 ? v : 0;
 }
 
 bool dn::pdl_enabled() {
@@ -540,8 +559,8 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             if (r.ksplit > 1)
                 P->ws_bytes = std::max(P->ws_bytes, (size_t)r.ksplit * r.m_tiles * 128 * r.n_tiles * r.BN *
                                                         sizeof(float));
-            tc_workers(r.m_tiles, r.n_tiles, r.ksplit, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, &r.grid,
-                       &r.bres);
+            tc_workers(r.m_tiles, r.n_tiles, r.ksplit, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms,
+                       tc_mb_forced(), &r.grid, &r.bres, &r.mb);
             {
                 // one work item per CTA: the two MMA issuers share
                 // each tile's K steps instead of idling one of them.  Fixed-batch
@@ -592,10 +611,10 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             static const bool dump = getenv("NET_PLAN_DUMP") != nullptr;   // diagnostics: one line per layer
             if (dump)
                 fprintf(stderr,
-                        "plan b%d %dx%d layer %d: tile %dx%d BN %d m_tiles %d n_tiles %d ksplit %d grid %d "
+                        "plan b%d %dx%d layer %d: tile %dx%d BN %d m_tiles %d n_tiles %d ksplit %d grid %d mb %d "
                         "bres %d kalt %d tapm %d pair %d\n",
-                        batch, h, w, l, r.TW, r.TH, r.BN, r.m_tiles, r.n_tiles, r.ksplit, r.grid, r.bres, r.kalt,
-                        r.tapm, L.pair ? 1 : 0);
+                        batch, h, w, l, r.TW, r.TH, r.BN, r.m_tiles, r.n_tiles, r.ksplit, r.grid, r.mb, r.bres,
+                        r.kalt, r.tapm, L.pair ? 1 : 0);
         }
         P->runs.push_back(r);
         if (L.d.pool != NET_POOL_2X2S1_SAME) cur ^= 1;
@@ -716,7 +735,7 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                     a.withhold = 1;
                     n->fault_layer = -1;
                 }
-                e = conv_tc_launch(L.tmB[tmb_index(r.BN)], a, r.BN, L.in_dt, r.grid, st);
+                e = conv_tc_launch(L.tmB[tmb_index(r.BN)], a, r.BN, L.in_dt, r.grid, r.mb, st);
                 if (e == cudaSuccess && r.ksplit > 1) {
                     ++n->pending;
                     SplitReduce sr{n->ws, r.ksplit, r.m_tiles * 128, r.n_tiles * r.BN, r.TW, r.TH,

@@ -62,6 +62,7 @@ struct LayerRun {
     int ksplit = 1;                // split-K factor (partial sums in the workspace)
     int bres = 0;                  // TC: weights resident in shared memory
     int kalt = 0;                  // TC: both MMA issuers on each tile (one work item per CTA)
+    int mb = 1;                    // TC: CTAs per SM (2: short tiles, epilogue-bound)
     int tapm = 0;                  // TC: ring stages of all nine taps (3x3, resident weights)
     int sbn = 64, sth = 8, stw = 16; // CUDA-core tile
     ConvProblem* d_prob = nullptr; // TC: device problem table (one entry)
@@ -79,9 +80,13 @@ void tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, int* 
 void tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks = 16);
 // (N tile, split-K) pairs a tensor-core layer can take in its current format.
 void tc_tile_options(const net* n, int l, std::vector<std::pair<int, int>>* opts);
-// Persistent worker count and resident-weight mode of a tensor-core launch
-// (nk K steps of chb bytes per tile).
-void tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int num_sms, int* workers, int* bres);
+// CTAs per SM, persistent worker count and resident-weight mode of a
+// tensor-core launch (nk K steps of chb bytes per tile; mb_req 0: chosen).
+void tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int num_sms, int mb_req, int* workers,
+                int* bres, int* mb);
+// NET_TC_MB=1 or 2 in the environment forces the CTAs per SM of fixed-batch
+// launches (0: chosen per launch); read once per process.
+int tc_mb_forced();
 // Index into Layer::tmB of the weight map whose box has BN rows.
 int tmb_index(int BN);
 

@@ -158,7 +158,8 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
         if (L.pair)   // one N tile: the weights stay resident
             while (r.BN < ncols && r.BN < 256) r.BN *= 2;
         r.n_tiles = cdiv(ncols, r.BN);
-        tc_workers(r.m_tiles, r.n_tiles, 1, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, &r.grid, &r.bres);
+        tc_workers(r.m_tiles, r.n_tiles, 1, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, 1, &r.grid, &r.bres,
+                   &r.mb);
         if (L.pair && !r.bres) return fail(NET_E_UNSUPPORTED, "layer %d: pair mode needs resident weights", l);
         r.tapm = L.pair ? 1 : 0;
         cudaError_t e = cudaMalloc(&r.d_prob, sizeof(ConvProblem) * cnt);
@@ -235,7 +236,7 @@ static net_status enqueue_uplan(net* n, UPlan* P, int cnt, int* kernels) {
         }
         const bool prof = n->prof && (int)n->prof_ev.size() == 2 * nl;
         if (prof) e = cudaEventRecordWithFlags(n->prof_ev[2 * l], st, cudaEventRecordExternal);
-        if (e == cudaSuccess) e = conv_tc_launch(L.tmB[tmb_index(r.BN)], a, r.BN, L.in_dt, r.grid, st);
+        if (e == cudaSuccess) e = conv_tc_launch(L.tmB[tmb_index(r.BN)], a, r.BN, L.in_dt, r.grid, 1, st);
         if (e == cudaSuccess && prof) e = cudaEventRecordWithFlags(n->prof_ev[2 * l + 1], st, cudaEventRecordExternal);
         ++k;
         if (e == cudaSuccess && P->d_pool[l]) {

@@ -354,7 +354,8 @@ static net_status enqueue_step(net* n, ServeState* S, StepSlot& sl) {
             a.ep = ep;
             a.err = n->err_dev;
             P.BN = BN;
-            tc_workers(mt, a.n_tiles, 1, BN, nk, a.chb, n->num_sms, &P.workers, &a.bres);
+            int mb_unused = 1;
+            tc_workers(mt, a.n_tiles, 1, BN, nk, a.chb, n->num_sms, 1, &P.workers, &a.bres, &mb_unused);
             // pair mode needs resident weights (the launch refuses it otherwise)
             a.tapm = L.pair ? 1 : 0;
             a.pair = L.pair ? 1 : 0;
@@ -392,7 +393,7 @@ static net_status enqueue_step(net* n, ServeState* S, StepSlot& sl) {
                 ++n->launches;
             }
         } else {
-            SERVE_CK(conv_tc_launch(L.tmB[tmb_index(P.BN)], P.a, P.BN, L.in_dt, P.workers, st), "conv");
+            SERVE_CK(conv_tc_launch(L.tmB[tmb_index(P.BN)], P.a, P.BN, L.in_dt, P.workers, 1, st), "conv");
             ++n->launches;
         }
         if (P.npool) {

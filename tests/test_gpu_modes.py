@@ -1,9 +1,11 @@
 """Launch-mode switches of the tensor-core conv, each in a child process (the
 switches are read once per process): K-alternating MMA issuers off
 (NET_TC_KALT=0), programmatic dependent launch off (NET_PDL=0), tap-merged
-stages off (NET_TC_TAPM=0), and the first layer as an im2col tile of 32
+stages off (NET_TC_TAPM=0), the first layer as an im2col tile of 32
 channels written by a pack kernel (NET_L0_PAIR=0) instead of two taps per
-MMA over 8-channel pixels.  Every mode must give the oracle's answer within
+MMA over 8-channel pixels, and one CTA per SM everywhere (NET_TC_MB=1) or
+two wherever the N tile allows (NET_TC_MB=2, which also runs long A + B
+rings on half the shared memory and the 16-column epilogue).  Every mode must give the oracle's answer within
 the BF16 budget and agree with the default mode to BF16 rounding; the
 19-conv network at 2 x 160 x 160 has layers with one and with several work
 items per CTA, split-K layers and resident-weight layers."""
@@ -61,7 +63,8 @@ def test_launch_modes_match_oracle(tmp_path):
     ex = oracle.forward(spec.layers, 3, x, blob)
     ys = {}
     for name, env in (("default", {}), ("no_kalt", {"NET_TC_KALT": "0"}), ("no_pdl", {"NET_PDL": "0"}),
-                      ("im2col", {"NET_L0_PAIR": "0"}), ("no_tapm", {"NET_TC_TAPM": "0"})):
+                      ("im2col", {"NET_L0_PAIR": "0"}), ("no_tapm", {"NET_TC_TAPM": "0"}),
+                      ("mb1", {"NET_TC_MB": "1"}), ("mb2", {"NET_TC_MB": "2"})):
         y = _run(tmp_path, name, env)
         assert np.isfinite(y).all(), name
         e = oracle.normwise_rel_err(y, ex)
@@ -71,5 +74,5 @@ def test_launch_modes_match_oracle(tmp_path):
     # programmatic launch changes only when kernels start, never what they add
     np.testing.assert_array_equal(ys["no_pdl"], ys["default"])
     # the first layer's tap pairs sum the same products in another order
-    for name in ("no_kalt", "no_tapm", "im2col"):
+    for name in ("no_kalt", "no_tapm", "im2col", "mb1", "mb2"):
         assert oracle.normwise_rel_err(ys[name], ys["default"]) <= 2e-2, name
