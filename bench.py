@@ -741,6 +741,8 @@ def main():
                                          seed=5)
             info["tile_plan"] = tiles
             info["tile_search"] = tr
+        if side and p != "fp32":
+            info["cta_plan"] = W.net.plan_ctas(batch, side, side)
         return W, info
 
     W, info = setup(prec, tune=True)
@@ -771,6 +773,8 @@ def main():
         # [N tile, split-K] per layer ([0, 0]: CUDA cores), from the genetic search
         line["tile_plan"] = info["tile_plan"]
         line["tile_search"] = info["tile_search"]
+    if "cta_plan" in info:
+        line["cta_plan"] = info["cta_plan"]   # CTAs per SM of each tensor-core layer
     W.net.close()
     if not args.no_compare and side:
         # the same workload on the other paths: FP32 (CUDA cores) and FP8 (GA-tuned plan) or BF16

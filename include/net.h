@@ -387,6 +387,17 @@ net_status net_tune_precision(net_t* net, const float* d_frames, int batch, int 
  * Captured graphs and plans are rebuilt. */
 net_status net_set_layer_tiles(net_t* net, int layer, int bn, int ksplit);
 
+/* CTAs per SM of one tensor-core layer's fixed-batch launches: 1, 2 (N
+ * tiles of at most 128 columns: two CTAs share an SM, each with half the
+ * shared memory and at most 80 registers a thread, which doubles the
+ * epilogue warps an SM) or 0 (chosen per launch).  NET_E_INVAL otherwise;
+ * no paper counterpart (the search below tunes it with the paper's GA). */
+net_status net_set_layer_ctas(net_t* net, int layer, int mb);
+
+/* CTAs per SM of every layer's fixed-batch launch for a batch x h x w pass
+ * (0 for CUDA-core layers). */
+net_status net_plan_ctas(net_t* net, int batch, int h, int w, int* mb, int n);
+
 /* The tile plan the fixed-batch path uses for a batch x h x w pass, after
  * overrides: bn[n] and ksplit[n] per layer (0 for CUDA-core layers). */
 net_status net_plan_tiles(net_t* net, int batch, int h, int w, int* bn, int* ksplit, int n);
@@ -396,9 +407,10 @@ net_status net_plan_tiles(net_t* net, int batch, int h, int w, int* bn, int* ksp
  * net_tune_precision (max_err bounds the deviation from the analytic plan's
  * output; every plan computes the same sums, only their order differs), one
  * gene per tensor-core layer whose alphabet is that layer's valid (bn,
- * ksplit) pairs, mutation drawing another pair; the analytic plan is one of
- * the initial individuals.  On NET_OK the handle keeps the best plan as
- * overrides and bn_out / ksplit_out (n_layers entries) hold it. */
+ * ksplit, CTAs per SM) triples, mutation drawing another triple; the
+ * analytic plan is one of the initial individuals.  On NET_OK the handle
+ * keeps the best plan as overrides, bn_out / ksplit_out (n_layers entries)
+ * hold it and net_plan_ctas reports its CTAs per SM. */
 typedef struct {
     double ms, ms_analytic;          /* best plan / the analytic plan           */
     int evaluations, memo_hits, changed_layers;

@@ -110,6 +110,8 @@ _SIGS = {
     "net_tune_precision": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                            ctypes.POINTER(net_ga_opts), ctypes.c_void_p, ctypes.POINTER(net_ga_result)],
     "net_set_layer_tiles": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "net_set_layer_ctas": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
+    "net_plan_ctas": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int],
     "net_plan_tiles": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                        ctypes.c_int],
     "net_tune_tiles": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -356,6 +358,16 @@ class Net:
     def set_layer_tiles(self, layer, bn=0, ksplit=0):
         """Overrides one tensor-core layer's N tile / split-K (0: analytic)."""
         check(lib().net_set_layer_tiles(self.h, layer, bn, ksplit))
+
+    def set_layer_ctas(self, layer, mb=0):
+        """Overrides one tensor-core layer's CTAs per SM (1, 2; 0: chosen)."""
+        check(lib().net_set_layer_ctas(self.h, layer, mb))
+
+    def plan_ctas(self, batch, h, w):
+        """CTAs per SM of every layer's fixed-batch launch (0: CUDA cores)."""
+        mb = np.zeros(self.n_layers, np.int32)
+        check(lib().net_plan_ctas(self.h, batch, h, w, _ptr(mb), self.n_layers))
+        return [int(v) for v in mb]
 
     def plan_tiles(self, batch, h, w):
         """[(bn, ksplit)] per layer of the fixed-batch plan ((0, 0): CUDA cores)."""

@@ -485,7 +485,7 @@ void dn::tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, 
     }
 }
 
-void dn::tc_tile_options(const net* n, int l, std::vector<std::pair<int, int>>* opts) {
+void dn::tc_tile_options(const net* n, int l, std::vector<TileOpt>* opts) {
     opts->clear();
     const Layer& L = n->L[l];
     if (L.engine != ENG_TC) return;
@@ -497,7 +497,8 @@ void dn::tc_tile_options(const net* n, int l, std::vector<std::pair<int, int>>* 
         if (bn > rup(ncols, 64)) continue;
         if (L.pair && bn < ncols) continue;   // pair mode: one N tile
         for (int ks : {1, 2, 4, 8, 16})
-            if (ks == 1 || (ks * 4 <= nk && !L.pair)) opts->push_back({bn, ks});
+            if (ks == 1 || (ks * 4 <= nk && !L.pair))
+                for (int mb = 1; mb <= (bn <= 128 ? 2 : 1); ++mb) opts->push_back({bn, ks, mb});
     }
 }
 
@@ -559,8 +560,9 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             if (r.ksplit > 1)
                 P->ws_bytes = std::max(P->ws_bytes, (size_t)r.ksplit * r.m_tiles * 128 * r.n_tiles * r.BN *
                                                         sizeof(float));
-            tc_workers(r.m_tiles, r.n_tiles, r.ksplit, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms,
-                       tc_mb_forced(), &r.grid, &r.bres, &r.mb);
+            const int mb_req = (L.tile_mb == 1 || (L.tile_mb == 2 && r.BN <= 128)) ? L.tile_mb : tc_mb_forced();
+            tc_workers(r.m_tiles, r.n_tiles, r.ksplit, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, mb_req,
+                       &r.grid, &r.bres, &r.mb);
             {
                 // one work item per CTA: the two MMA issuers share
                 // each tile's K steps instead of idling one of them.  Fixed-batch
@@ -879,12 +881,12 @@ extern "C" net_status net_set_layer_tiles(net_t* n, int layer, int bn, int kspli
         return fail(NET_E_INVAL, "tile bn %d / ksplit %d not in {0,64,128,256} / {0,1,2,4,8,16}", bn, ksplit);
     Layer& L = n->L[layer];
     if (L.engine != ENG_TC && (bn || ksplit)) return fail(NET_E_INVAL, "layer %d runs on CUDA cores", layer);
-    std::vector<std::pair<int, int>> opts;
+    std::vector<TileOpt> opts;
     tc_tile_options(n, layer, &opts);
     bool bn_ok = bn == 0, ks_ok = ksplit == 0;
     for (auto& o : opts) {
-        bn_ok |= o.first == bn;
-        ks_ok |= o.second == ksplit;
+        bn_ok |= o.bn == bn;
+        ks_ok |= o.ks == ksplit;
     }
     if (!bn_ok || !ks_ok) return fail(NET_E_INVAL, "layer %d cannot take bn %d / ksplit %d", layer, bn, ksplit);
     if (L.tile_bn != bn || L.tile_ks != ksplit) {
@@ -892,6 +894,32 @@ extern "C" net_status net_set_layer_tiles(net_t* n, int layer, int bn, int kspli
         L.tile_ks = ksplit;
         invalidate_plans(n);
     }
+    return NET_OK;
+}
+
+extern "C" net_status net_set_layer_ctas(net_t* n, int layer, int mb) {
+    if (!n) return fail(NET_E_INVAL, "NULL argument");
+    if (layer < 0 || layer >= (int)n->L.size()) return fail(NET_E_INVAL, "layer %d out of range", layer);
+    if (mb < 0 || mb > 2) return fail(NET_E_INVAL, "CTAs per SM %d not in {0, 1, 2}", mb);
+    Layer& L = n->L[layer];
+    if (L.engine != ENG_TC && mb) return fail(NET_E_INVAL, "layer %d runs on CUDA cores", layer);
+    if (L.tile_mb != mb) {
+        L.tile_mb = mb;
+        invalidate_plans(n);
+    }
+    return NET_OK;
+}
+
+extern "C" net_status net_plan_ctas(net_t* n, int batch, int h, int w, int* mb, int nn) {
+    if (!n || !mb) return fail(NET_E_INVAL, "NULL argument");
+    if (nn < (int)n->L.size()) return fail(NET_E_INVAL, "need %d entries", (int)n->L.size());
+    net_status s = check_shape(n, batch, h, w);
+    if (s != NET_OK) return s;
+    CK(cudaSetDevice(n->device));
+    Plan* P = nullptr;
+    s = get_plan(n, batch, h, w, &P);
+    if (s != NET_OK) return s;
+    for (size_t l = 0; l < n->L.size(); ++l) mb[l] = n->L[l].engine == ENG_TC ? P->runs[l].mb : 0;
     return NET_OK;
 }
 

@@ -35,6 +35,7 @@ struct Layer {
     float* w32 = nullptr;     // FP32 copy of W' for calibration (FP8 nets)
     double act_scale = 1.0;   // FP8 scale of this layer's input
     int tile_bn = 0, tile_ks = 0;   // fixed-batch plan overrides: N tile, split-K (0: analytic choice)
+    int tile_mb = 0;                // ... and CTAs per SM (0: chosen per launch)
     CUtensorMap tmB[3];       // TC weights, box rows BN = 64, 128, 256
     // Layers created as FP8 tensor-core layers also keep a BF16 copy, so the
     // precision of each can be switched after loading (precision search).
@@ -78,8 +79,12 @@ struct Plan {
 // one warp: TW = 8 or 16).
 void tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, int* TW, int* TH, int* BN);
 void tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks = 16);
-// (N tile, split-K) pairs a tensor-core layer can take in its current format.
-void tc_tile_options(const net* n, int l, std::vector<std::pair<int, int>>* opts);
+// (N tile, split-K, CTAs per SM) a tensor-core layer can take in its current
+// format (two CTAs an SM for N tiles of at most 128 columns).
+struct TileOpt {
+    int bn, ks, mb;
+};
+void tc_tile_options(const net* n, int l, std::vector<TileOpt>* opts);
 // CTAs per SM, persistent worker count and resident-weight mode of a
 // tensor-core launch (nk K steps of chb bytes per tile; mb_req 0: chosen).
 void tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int num_sms, int mb_req, int* workers,

@@ -245,17 +245,18 @@ extern "C" net_status net_tune_tiles(net_t* n, const float* d_frames, int batch,
     cudaError_t e = cudaSetDevice(n->device);
     if (e != cudaSuccess) return fail(NET_E_CUDA, "%s", cudaGetErrorString(e));
     const int nl = (int)n->L.size();
-    std::vector<int> saved_bn(nl), saved_ks(nl);
+    std::vector<int> saved_bn(nl), saved_ks(nl), saved_mb(nl);
     for (int l = 0; l < nl; ++l) {
         saved_bn[l] = n->L[l].tile_bn;
         saved_ks[l] = n->L[l].tile_ks;
-        n->L[l].tile_bn = n->L[l].tile_ks = 0;   // the analytic plan first
+        saved_mb[l] = n->L[l].tile_mb;
+        n->L[l].tile_bn = n->L[l].tile_ks = n->L[l].tile_mb = 0;   // the analytic plan first
     }
     invalidate_plans(n);
-    std::vector<int> genes;                                  // layer of each gene
-    std::vector<std::vector<std::pair<int, int>>> options;   // its (bn, ksplit) alphabet
+    std::vector<int> genes;                     // layer of each gene
+    std::vector<std::vector<TileOpt>> options;  // its (bn, ksplit, CTAs per SM) alphabet
     for (int l = 0; l < nl; ++l) {
-        std::vector<std::pair<int, int>> o;
+        std::vector<TileOpt> o;
         tc_tile_options(n, l, &o);
         if (o.size() > 1) {
             genes.push_back(l);
@@ -271,6 +272,7 @@ extern "C" net_status net_tune_tiles(net_t* n, const float* d_frames, int batch,
         for (int l = 0; l < nl; ++l) {
             n->L[l].tile_bn = saved_bn[l];
             n->L[l].tile_ks = saved_ks[l];
+            n->L[l].tile_mb = saved_mb[l];
         }
         return fail(NET_E_OOM, "search buffers");
     }
@@ -285,7 +287,8 @@ extern "C" net_status net_tune_tiles(net_t* n, const float* d_frames, int batch,
     if (s == NET_OK)
         for (size_t i = 0; i < genes.size(); ++i)
             for (size_t j = 0; j < options[i].size(); ++j)
-                if (options[i][j].first == P->runs[genes[i]].BN && options[i][j].second == P->runs[genes[i]].ksplit)
+                if (options[i][j].bn == P->runs[genes[i]].BN && options[i][j].ks == P->runs[genes[i]].ksplit &&
+                    options[i][j].mb == P->runs[genes[i]].mb)
                     seed[i] = (int)j;
     if (s == NET_OK) s = run_forward(n, d_frames, batch, h, w, d_ref);
     // the handle's stream may be non-blocking: finish it before a plain copy
@@ -300,8 +303,9 @@ extern "C" net_status net_tune_tiles(net_t* n, const float* d_frames, int batch,
     int evaluations = 0, hits = 0;
     auto apply = [&](const std::vector<int>& g) {
         for (size_t i = 0; i < genes.size(); ++i) {
-            n->L[genes[i]].tile_bn = options[i][g[i]].first;
-            n->L[genes[i]].tile_ks = options[i][g[i]].second;
+            n->L[genes[i]].tile_bn = options[i][g[i]].bn;
+            n->L[genes[i]].tile_ks = options[i][g[i]].ks;
+            n->L[genes[i]].tile_mb = options[i][g[i]].mb;
         }
         invalidate_plans(n);
     };
@@ -336,7 +340,8 @@ extern "C" net_status net_tune_tiles(net_t* n, const float* d_frames, int batch,
         if (verbose) {
             fprintf(stderr, "tile plan [");
             for (size_t i = 0; i < genes.size(); ++i)
-                fprintf(stderr, " L%d:%d/%d", genes[i], options[i][g[i]].first, options[i][g[i]].second);
+                fprintf(stderr, " L%d:%d/%d/%d", genes[i], options[i][g[i]].bn, options[i][g[i]].ks,
+                        options[i][g[i]].mb);
             fprintf(stderr, " ] status %d (%s) ms %.4f err %.3e\n", (int)st, st == NET_OK ? "" : net_last_error(),
                     ev.ms, ev.err);
         }
@@ -369,6 +374,7 @@ extern "C" net_status net_tune_tiles(net_t* n, const float* d_frames, int batch,
         for (int l = 0; l < nl; ++l) {
             n->L[l].tile_bn = saved_bn[l];
             n->L[l].tile_ks = saved_ks[l];
+            n->L[l].tile_mb = saved_mb[l];
         }
         invalidate_plans(n);
     }

@@ -97,6 +97,15 @@ def test_tile_plan_overrides_and_search():
         assert e.value.status == binding.NET_E_INVAL
         net.set_layer_tiles(13, 0, 0)
         assert net.plan_tiles(batch, side, side) == base
+        # CTAs per SM: layer 3 (1x1, 64 outputs) forced to each value
+        for mb in (1, 2):
+            net.set_layer_ctas(3, mb)
+            assert net.plan_ctas(batch, side, side)[3] == mb
+            assert oracle.normwise_rel_err(net.forward(x), ex) <= 2e-2
+        net.set_layer_ctas(3, 0)
+        with pytest.raises(binding.NetError) as e:
+            net.set_layer_ctas(3, 3)
+        assert e.value.status == binding.NET_E_INVAL
         plan, res = net.tune_tiles(d_x, batch, side, side, population=6, generations=3, reps=2, seed=11)
         print("tile plan", plan, res)
         assert res["ms"] <= res["ms_analytic"] and res["evaluations"] >= 1
