@@ -560,7 +560,11 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             if (r.ksplit > 1)
                 P->ws_bytes = std::max(P->ws_bytes, (size_t)r.ksplit * r.m_tiles * 128 * r.n_tiles * r.BN *
                                                         sizeof(float));
-            const int mb_req = (L.tile_mb == 1 || (L.tile_mb == 2 && r.BN <= 128)) ? L.tile_mb : tc_mb_forced();
+            // the tap-pair first layer (32 live columns) measured slower with
+            // two CTAs an SM (its 16-column epilogue chunks double the fixed
+            // cost per chunk): one, unless forced or overridden
+            int mb_req = (L.tile_mb == 1 || (L.tile_mb == 2 && r.BN <= 128)) ? L.tile_mb : tc_mb_forced();
+            if (mb_req == 0 && L.pair) mb_req = 1;
             tc_workers(r.m_tiles, r.n_tiles, r.ksplit, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, mb_req,
                        &r.grid, &r.bres, &r.mb);
             {
