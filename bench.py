@@ -690,7 +690,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="leave the serving streams out of the line")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--no-extra", action="store_true",
-                    help="leave the detection and Jacobi measurements out of the line")
+                    help="leave the detection, nightmare and Jacobi measurements out of the line")
+    ap.add_argument("--section", choices=["detect", "jacobi", "nightmare"],
+                    help="run only this measurement and print its JSON (profiling entry point)")
     ap.add_argument("--no-tile-search", action="store_true",
                     help="keep the analytic tile plan (skip the genetic tile-plan search)")
     args = ap.parse_args()
@@ -700,6 +702,13 @@ def main():
         return run_reference(args, wl)
 
     import torch
+    if args.section:
+        from paper_1811_03882_gb300 import build, binding
+        build.build()
+        torch.cuda.set_device(0)
+        fn = {"detect": run_detect, "jacobi": run_jacobi, "nightmare": run_nightmare}[args.section]
+        print(json.dumps({"section": args.section, **fn(torch, binding, 0)}), flush=True)
+        return
     ws, rank, local = dist_env()
     if ws > 1:
         import torch.distributed as dist
