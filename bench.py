@@ -30,6 +30,8 @@ from paper_1811_03882_gb300 import synth  # noqa: E402
 
 # name -> (network, frames, side, precision, weight/frame seed)
 WORKLOADS = {
+    # the single conv layer: 1 x 16 x 32 x 32, U[-1, 1] (latency-bound: report us per call)
+    "single-conv-32-fp32": ("single-conv", 1, 32, "fp32", synth.SEED_SINGLE),
     "19conv-448-b8-bf16": ("19-conv", 8, 448, "bf16", synth.SEED_19CONV),
     "19conv-448-b8-fp8": ("19-conv", 8, 448, "fp8", synth.SEED_19CONV),
     "9conv-416-b1-fp32": ("9-conv", 1, 416, "fp32", synth.SEED_9CONV),
@@ -196,7 +198,10 @@ def run_reference(args, wl):
     netname, batch, side, prec, seed = WORKLOADS[wl]
     spec = synth.NETS[netname]()
     if side:
-        _, x, blob = synth.workload_net(spec, seed, 1, side, side)
+        if netname == "single-conv":
+            _, x, blob = synth.workload_single()
+        else:
+            _, x, blob = synth.workload_net(spec, seed, 1, side, side)
         frames = [x] * args.steps
     else:
         blob = synth.weights_for(spec, seed)
@@ -204,10 +209,10 @@ def run_reference(args, wl):
         frames = [synth.frame_for(seed, i % batch, int(sides[i % batch])) for i in range(args.steps)]
     import oracle
     oracle.build()
-    oracle.forward(spec.layers, 3, frames[0], blob)   # warm-up (one frame)
+    oracle.forward(spec.layers, spec.in_c, frames[0], blob)   # warm-up (one frame)
     t0 = time.perf_counter()
     for f in frames:
-        oracle.forward(spec.layers, 3, f, blob)
+        oracle.forward(spec.layers, spec.in_c, f, blob)
     el = time.perf_counter() - t0
     fps = args.steps / el
     line = {"impl": "reference", "metric": "frames/s", "value": fps, "unit": "frames/s",
@@ -478,7 +483,11 @@ class Workload:
         netname, batch, side, _, seed = WORKLOADS[wl]
         self.spec = spec = synth.NETS[netname]()
         self.batch, self.side, self.prec = batch, side, prec
-        if side:
+        if netname == "single-conv":
+            self.sides = [side]
+            _, x, self.blob = synth.workload_single()
+            self.frames = [x]
+        elif side:
             self.sides = [side] * batch
             _, x, self.blob = synth.workload_net(spec, seed, batch, side, side)
             self.frames = [x]
@@ -486,7 +495,7 @@ class Workload:
             self.sides = [int(v) for v in synth.uneven_sides(batch, seed)]
             self.blob = synth.weights_for(spec, seed)
             self.frames = [synth.frame_for(seed, i, s) for i, s in enumerate(self.sides)]
-        self.net = binding.Net(spec.layers, 3, prec=prec, max_batch=batch if side else 1,
+        self.net = binding.Net(spec.layers, spec.in_c, prec=prec, max_batch=batch if side else 1,
                                max_side=max(self.sides), stream=stream.cuda_stream, device=dev)
         self.net.load_weights(self.blob)
         self.stream = stream
