@@ -752,6 +752,12 @@ def main():
                 plan, ga = W.net.tune_precision(d_c, 1, cs, cs, max_err=0.05, population=12, generations=8,
                                                 reps=2, seed=3)
                 info = {"plan": plan, "ga": ga}
+        if tune and not side and p != "fp32" and not args.no_tile_search:
+            # uneven batch: the genetic search over its grouped launches (setup)
+            plan, tr = W.net.tune_uneven(W.d_in, W.sides, W.d_out, population=12, generations=8, reps=3,
+                                         seed=5)
+            info["grouped_plan"] = plan
+            info["tile_search"] = tr
         if tune and side and p != "fp32" and not args.no_tile_search:
             # the genetic tile-plan search on the workload's own batch shape
             # (setup, outside every timed region)
@@ -790,6 +796,10 @@ def main():
     if "tile_plan" in info:
         # [N tile, split-K] per layer ([0, 0]: CUDA cores), from the genetic search
         line["tile_plan"] = info["tile_plan"]
+        line["tile_search"] = info["tile_search"]
+    if "grouped_plan" in info:
+        # [N tile, CTAs per SM, stage cap] per layer of the grouped launches (0: analytic)
+        line["grouped_plan"] = info["grouped_plan"]
         line["tile_search"] = info["tile_search"]
     if "cta_plan" in info:
         line["cta_plan"] = info["cta_plan"]   # CTAs per SM of each tensor-core layer

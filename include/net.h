@@ -419,6 +419,23 @@ typedef struct {
 net_status net_tune_tiles(net_t* net, const float* d_frames, int batch, int h, int w, const net_ga_opts* opts,
                           int* bn_out, int* ksplit_out, net_tile_result* result);
 
+/* Paper Sec. 3.3 and 4 (the GA) over the grouped launches of an uneven
+ * batch (net_forward_uneven; the serving steps use the same per-layer
+ * choice): one gene per tensor-core layer whose alphabet is (N tile, CTAs
+ * per SM, ring stage cap) triples, the analytic choice first; the time is
+ * the whole batch of net_forward_uneven(d_in, side, cnt, d_out) (arguments
+ * as there).  Grouped launches never split K and the genes change neither
+ * a frame's sums nor their order, so every plan must reproduce the analytic
+ * outputs (max_err bounds the difference).  On NET_OK the handle keeps the
+ * best plan (net_plan_grouped reports it) and result holds the times.
+ * NET_E_UNSUPPORTED when a layer runs on CUDA cores. */
+net_status net_tune_uneven(net_t* net, const float* const* d_in, const int* side, int cnt, float* const* d_out,
+                           const net_ga_opts* opts, net_tile_result* result);
+
+/* The grouped-launch choice per layer: N tile (0: analytic), CTAs per SM
+ * (0 or 1: one; 2: two), ring stage cap (0: as many as fit). */
+net_status net_plan_grouped(const net_t* net, int* bn, int* mb, int* nst, int n);
+
 /* Paper Sec. 3.3 measures each candidate's run time; this is the per-layer
  * form of that measurement.
  * Per-layer timing: with enable != 0 every later forward pass records a

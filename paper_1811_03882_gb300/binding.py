@@ -111,6 +111,9 @@ _SIGS = {
                            ctypes.POINTER(net_ga_opts), ctypes.c_void_p, ctypes.POINTER(net_ga_result)],
     "net_set_layer_tiles": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "net_set_layer_ctas": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int],
+    "net_tune_uneven": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                        ctypes.POINTER(net_ga_opts), ctypes.POINTER(net_tile_result)],
+    "net_plan_grouped": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "net_plan_ctas": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int],
     "net_plan_tiles": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                        ctypes.c_int],
@@ -358,6 +361,26 @@ class Net:
     def set_layer_tiles(self, layer, bn=0, ksplit=0):
         """Overrides one tensor-core layer's N tile / split-K (0: analytic)."""
         check(lib().net_set_layer_tiles(self.h, layer, bn, ksplit))
+
+    def tune_uneven(self, d_ins, sides, d_outs, max_err=1e-6, population=12, generations=8,
+                    crossover=0.9, mutation=0.05, reps=3, seed=0):
+        """Genetic search over the grouped launches of this uneven batch;
+        returns (per-layer (bn, mb, nst) overrides, result dict)."""
+        k = len(d_ins)
+        a = (ctypes.c_void_p * k)(*[t.data_ptr() for t in d_ins])
+        s = (ctypes.c_int * k)(*[int(v) for v in sides])
+        o = (ctypes.c_void_p * k)(*[t.data_ptr() for t in d_outs])
+        opts = net_ga_opts(population, generations, crossover, mutation, max_err, reps, seed)
+        r = net_tile_result()
+        check(lib().net_tune_uneven(self.h, a, s, k, o, ctypes.byref(opts), ctypes.byref(r)))
+        return self.plan_grouped(), {f: getattr(r, f) for f, _ in net_tile_result._fields_}
+
+    def plan_grouped(self):
+        bn = np.zeros(self.n_layers, np.int32)
+        mb = np.zeros(self.n_layers, np.int32)
+        nst = np.zeros(self.n_layers, np.int32)
+        check(lib().net_plan_grouped(self.h, _ptr(bn), _ptr(mb), _ptr(nst), self.n_layers))
+        return [(int(a), int(b), int(c)) for a, b, c in zip(bn, mb, nst)]
 
     def set_layer_ctas(self, layer, mb=0):
         """Overrides one tensor-core layer's CTAs per SM (1, 2; 0: chosen)."""

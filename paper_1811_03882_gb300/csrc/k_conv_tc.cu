@@ -989,6 +989,7 @@ static bool tc_geometry(int BN, int chb, int bres, int nk, int mb, TcArgs* g) {
     const size_t bres_bytes = bres ? (size_t)(g->pair ? tc::kPairSlots : nk) * b_bytes : 0;
     if (tc_avail(mb) < bres_bytes + 2 * st) return false;
     int nst = (int)std::min<size_t>(tc::kMaxStages, (tc_avail(mb) - bres_bytes) / st) & ~1;
+    if (g->nst_cap >= 2) nst = std::min(nst, g->nst_cap & ~1);   // a tuned ring depth
     // producer lanes: four per warp on deep rings (stage count cut to a
     // multiple of eight).  The lanes of a warp issue in lockstep, so on a
     // shallow ring one lane per warp keeps stages refilling one by one.

@@ -163,6 +163,7 @@ struct TcArgs {
     Epilogue ep;
     int* err;     // bounded-wait failure code (0 = none)
     long long wait_limit;   // bound of each pipeline wait, clock64 cycles (<= 0: ~2 s)
+    int nst_cap;            // ring stages at most (even, >= 2; 0: as many as fit)
     int withhold;           // fault injection (tests): one producer skips one K step
     // division by ksplit, n_tiles, chunks, k and nst (filled by conv_tc_launch)
     FastDiv fd_ksplit, fd_ntiles, fd_chunks, fd_k, fd_nst;

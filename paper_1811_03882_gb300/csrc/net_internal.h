@@ -36,6 +36,9 @@ struct Layer {
     double act_scale = 1.0;   // FP8 scale of this layer's input
     int tile_bn = 0, tile_ks = 0;   // fixed-batch plan overrides: N tile, split-K (0: analytic choice)
     int tile_mb = 0;                // ... and CTAs per SM (0: chosen per launch)
+    // grouped launches (uneven batches, serving): N tile, CTAs per SM, ring
+    // stage cap (0: the analytic choice, one CTA an SM, as many as fit)
+    int grp_bn = 0, grp_mb = 0, grp_nst = 0;
     CUtensorMap tmB[3];       // TC weights, box rows BN = 64, 128, 256
     // Layers created as FP8 tensor-core layers also keep a BF16 copy, so the
     // precision of each can be switched after loading (precision search).
@@ -64,6 +67,7 @@ struct LayerRun {
     int bres = 0;                  // TC: weights resident in shared memory
     int kalt = 0;                  // TC: both MMA issuers on each tile (one work item per CTA)
     int mb = 1;                    // TC: CTAs per SM (2: short tiles, epilogue-bound)
+    int nst_cap = 0;               // TC: ring stages at most (0: as many as fit)
     int tapm = 0;                  // TC: ring stages of all nine taps (3x3, resident weights)
     int sbn = 64, sth = 8, stw = 16; // CUDA-core tile
     ConvProblem* d_prob = nullptr; // TC: device problem table (one entry)
@@ -170,6 +174,10 @@ net_status enqueue_uneven(net* n, const float* const* d_in, const int* side, int
                           float* const* d_out);
 void uneven_free(net* n);
 void uneven_graphs_clear(net* n);
+void uneven_plans_clear(net* n);
+// The grouped-launch tile choice of a layer, after the grp_* overrides: N
+// tile (given the analytic one), CTAs per SM and stage cap.
+void grouped_tiles(const Layer& L, int ncols, int* BN, int* mb, int* nst_cap);
 void serve_stop(net* n);
 void region_free(net* n);
 void night_free(net* n);

@@ -155,11 +155,11 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
         const int nk = L.kx * L.kx * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
         // grouped launches do not split K; pick the N tile for ks = 1
         tc_choose_split(mt, ncols, nk, n->num_sms, &r.BN, &ks_unused, 1);
-        if (L.pair)   // one N tile: the weights stay resident
-            while (r.BN < ncols && r.BN < 256) r.BN *= 2;
+        int mb_req = 1;
+        grouped_tiles(L, ncols, &r.BN, &mb_req, &r.nst_cap);
         r.n_tiles = cdiv(ncols, r.BN);
-        tc_workers(r.m_tiles, r.n_tiles, 1, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, 1, &r.grid, &r.bres,
-                   &r.mb);
+        tc_workers(r.m_tiles, r.n_tiles, 1, r.BN, nk, tc_chunk_bytes(L.in_cs, L.in_dt), n->num_sms, mb_req, &r.grid,
+                   &r.bres, &r.mb);
         if (L.pair && !r.bres) return fail(NET_E_UNSUPPORTED, "layer %d: pair mode needs resident weights", l);
         r.tapm = L.pair ? 1 : 0;
         cudaError_t e = cudaMalloc(&r.d_prob, sizeof(ConvProblem) * cnt);
@@ -216,6 +216,7 @@ static net_status enqueue_uplan(net* n, UPlan* P, int cnt, int* kernels) {
         a.ksplit = 1;
         a.ws = nullptr;
         a.bres = r.bres;
+        a.nst_cap = r.nst_cap;
         a.tapm = r.tapm;
         a.pair = L.pair ? 1 : 0;
         a.err = n->err_dev;
@@ -236,7 +237,7 @@ static net_status enqueue_uplan(net* n, UPlan* P, int cnt, int* kernels) {
         }
         const bool prof = n->prof && (int)n->prof_ev.size() == 2 * nl;
         if (prof) e = cudaEventRecordWithFlags(n->prof_ev[2 * l], st, cudaEventRecordExternal);
-        if (e == cudaSuccess) e = conv_tc_launch(L.tmB[tmb_index(r.BN)], a, r.BN, L.in_dt, r.grid, 1, st);
+        if (e == cudaSuccess) e = conv_tc_launch(L.tmB[tmb_index(r.BN)], a, r.BN, L.in_dt, r.grid, r.mb, st);
         if (e == cudaSuccess && prof) e = cudaEventRecordWithFlags(n->prof_ev[2 * l + 1], st, cudaEventRecordExternal);
         ++k;
         if (e == cudaSuccess && P->d_pool[l]) {
@@ -304,6 +305,20 @@ net_status dn::enqueue_uneven(net* n, const float* const* d_in, const int* side,
         P = it->second;
     }
     return enqueue_uplan_graph(n, P, cnt);
+}
+
+void dn::grouped_tiles(const Layer& L, int ncols, int* BN, int* mb, int* nst_cap) {
+    if (L.grp_bn > 0 && L.grp_bn <= rup(ncols, 64)) *BN = L.grp_bn;
+    if (L.pair)   // one N tile: the weights stay resident
+        while (*BN < ncols && *BN < 256) *BN *= 2;
+    *mb = (L.grp_mb == 2 && *BN <= 128) ? 2 : 1;
+    *nst_cap = L.grp_nst;
+}
+
+void dn::uneven_plans_clear(net* n) {
+    if (!n->uneven) return;
+    for (auto& kv : n->uneven->plans) delete kv.second;
+    n->uneven->plans.clear();
 }
 
 void dn::uneven_graphs_clear(net* n) {

@@ -278,7 +278,7 @@ static net_status enqueue_step(net* n, ServeState* S, StepSlot& sl) {
     struct LayerStep {
         int l = 0;
         TcArgs a{};
-        int BN = 0, workers = 1;
+        int BN = 0, workers = 1, mb = 1;
         size_t simt_begin = 0, simt_end = 0;
         int pool_begin = 0, npool = 0;
         long long pool_total = 0;
@@ -336,8 +336,8 @@ static net_status enqueue_step(net* n, ServeState* S, StepSlot& sl) {
             const int nk = L.kx * L.kx * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
             int BN = 128, ks = 1;
             tc_choose_split(mt, ncols, nk, n->num_sms, &BN, &ks, 1);
-            if (L.pair)   // one N tile: the weights stay resident
-                while (BN < ncols && BN < 256) BN *= 2;
+            int mb_req = 1, nst_cap = 0;
+            grouped_tiles(L, ncols, &BN, &mb_req, &nst_cap);
             TcArgs& a = P.a;
             a.probs = dt + ntab;
             a.nprob = na;
@@ -354,8 +354,8 @@ static net_status enqueue_step(net* n, ServeState* S, StepSlot& sl) {
             a.ep = ep;
             a.err = n->err_dev;
             P.BN = BN;
-            int mb_unused = 1;
-            tc_workers(mt, a.n_tiles, 1, BN, nk, a.chb, n->num_sms, 1, &P.workers, &a.bres, &mb_unused);
+            a.nst_cap = nst_cap;
+            tc_workers(mt, a.n_tiles, 1, BN, nk, a.chb, n->num_sms, mb_req, &P.workers, &a.bres, &P.mb);
             // pair mode needs resident weights (the launch refuses it otherwise)
             a.tapm = L.pair ? 1 : 0;
             a.pair = L.pair ? 1 : 0;
@@ -393,7 +393,7 @@ static net_status enqueue_step(net* n, ServeState* S, StepSlot& sl) {
                 ++n->launches;
             }
         } else {
-            SERVE_CK(conv_tc_launch(L.tmB[tmb_index(P.BN)], P.a, P.BN, L.in_dt, P.workers, 1, st), "conv");
+            SERVE_CK(conv_tc_launch(L.tmB[tmb_index(P.BN)], P.a, P.BN, L.in_dt, P.workers, P.mb, st), "conv");
             ++n->launches;
         }
         if (P.npool) {

@@ -401,3 +401,180 @@ extern "C" net_status net_tune_tiles(net_t* n, const float* d_frames, int batch,
     if (!found) return fail(NET_E_STATE, "no tile plan within the error budget %g", opt->max_err);
     return NET_OK;
 }
+
+// The same search over the grouped launches of an uneven batch (and of the
+// serving steps, which use the same per-layer choice): one gene per
+// tensor-core layer whose alphabet is (N tile, CTAs per SM, ring stage cap)
+// triples, the first of them the analytic choice.  Grouped launches never
+// split K, and these genes change neither a frame's sums nor their order,
+// so every candidate must reproduce the analytic plan's outputs exactly
+// (max_err still bounds them); the time is the whole batch's CUDA-graph
+// replay.
+extern "C" net_status net_tune_uneven(net_t* n, const float* const* d_in, const int* side, int cnt,
+                                      float* const* d_out, const net_ga_opts* opt, net_tile_result* res) {
+    if (!n || !d_in || !side || !d_out || !opt || !res || cnt < 1) return fail(NET_E_INVAL, "NULL argument");
+    if (!n->weights_loaded) return fail(NET_E_WEIGHTS, "weights not loaded");
+    if (opt->population < 2 || opt->generations < 1 || opt->reps < 1 || !(opt->max_err > 0) ||
+        opt->crossover < 0 || opt->crossover > 1 || opt->mutation < 0 || opt->mutation > 1)
+        return fail(NET_E_INVAL, "bad search options");
+    for (auto& L : n->L)
+        if (L.engine != ENG_TC) return fail(NET_E_UNSUPPORTED, "uneven batches have grouped launches on tensor cores only");
+    for (int f = 0; f < cnt; ++f) {
+        net_status s = check_shape(n, 1, side[f], side[f]);
+        if (s != NET_OK) return s;
+    }
+    cudaError_t e = cudaSetDevice(n->device);
+    if (e != cudaSuccess) return fail(NET_E_CUDA, "%s", cudaGetErrorString(e));
+    const int nl = (int)n->L.size();
+    struct Saved {
+        int bn, mb, nst;
+    };
+    std::vector<Saved> saved(nl);
+    for (int l = 0; l < nl; ++l) {
+        saved[l] = {n->L[l].grp_bn, n->L[l].grp_mb, n->L[l].grp_nst};
+        n->L[l].grp_bn = n->L[l].grp_mb = n->L[l].grp_nst = 0;
+    }
+    auto restore = [&] {
+        for (int l = 0; l < nl; ++l) {
+            n->L[l].grp_bn = saved[l].bn;
+            n->L[l].grp_mb = saved[l].mb;
+            n->L[l].grp_nst = saved[l].nst;
+        }
+        uneven_plans_clear(n);
+    };
+    uneven_plans_clear(n);
+    struct Opt {
+        int bn, mb, nst;
+    };
+    std::vector<int> genes;
+    std::vector<std::vector<Opt>> options;
+    for (int l = 0; l < nl; ++l) {
+        const Layer& L = n->L[l];
+        const bool last = l + 1 == nl;
+        const int ncols = std::max(L.d.cout, last ? L.d.cout : n->L[l + 1].in_cs);
+        std::vector<Opt> o{{0, 1, 0}};   // the analytic choice first
+        for (int bn : {0, 64, 128, 256}) {
+            if (bn > rup(ncols, 64)) continue;
+            if (bn && L.pair && bn < ncols) continue;
+            for (int mb = 1; mb <= 2; ++mb) {
+                if (mb == 2 && (bn == 0 || bn > 128)) continue;
+                for (int nst : {0, 8, 4})
+                    if (bn || mb != 1 || nst) o.push_back({bn, mb, nst});
+            }
+        }
+        if (o.size() > 1) {
+            genes.push_back(l);
+            options.push_back(o);
+        }
+    }
+    // outputs of every frame, concatenated
+    std::vector<size_t> nout(cnt);
+    size_t total = 0;
+    for (int f = 0; f < cnt; ++f) {
+        int c, ho, wo;
+        net_output_shape(n, side[f], side[f], &c, &ho, &wo);
+        nout[f] = (size_t)c * ho * wo;
+        total += nout[f];
+    }
+    std::vector<float> ref(total), out(total);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto gather = [&](std::vector<float>& dst) {
+        if (cudaStreamSynchronize(n->stream) != cudaSuccess) return false;
+        size_t o = 0;
+        for (int f = 0; f < cnt; ++f) {
+            if (cudaMemcpy(dst.data() + o, d_out[f], nout[f] * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return false;
+            o += nout[f];
+        }
+        return true;
+    };
+    net_status s = enqueue_uneven(n, d_in, side, cnt, d_out);
+    if (s == NET_OK && !gather(ref)) s = fail(NET_E_CUDA, "reference copy");
+    if (s == NET_OK) s = check_device_error(n);
+    double rmax = 0.0;
+    for (float v : ref) rmax = std::max(rmax, (double)std::fabs(v));
+    if (rmax == 0.0) rmax = 1.0;
+    std::map<std::vector<int>, Eval> memo;
+    int evaluations = 0, hits = 0;
+    auto apply = [&](const std::vector<int>& g) {
+        for (size_t i = 0; i < genes.size(); ++i) {
+            Layer& L = n->L[genes[i]];
+            L.grp_bn = options[i][g[i]].bn;
+            L.grp_mb = options[i][g[i]].mb;
+            L.grp_nst = options[i][g[i]].nst;
+        }
+        uneven_plans_clear(n);
+    };
+    auto evaluate = [&](const std::vector<int>& g) -> Eval {
+        auto it = memo.find(g);
+        if (it != memo.end()) {
+            ++hits;
+            return it->second;
+        }
+        Eval ev;
+        apply(g);
+        net_status st = enqueue_uneven(n, d_in, side, cnt, d_out);   // plan, capture, warm-up
+        if (st == NET_OK) {
+            cudaEventRecord(e0, n->stream);
+            for (int r = 0; r < opt->reps && st == NET_OK; ++r) st = enqueue_uneven(n, d_in, side, cnt, d_out);
+            cudaEventRecord(e1, n->stream);
+        }
+        float ms = 0.f;
+        if (st == NET_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            gather(out) && check_device_error(n) == NET_OK) {
+            double d = 0.0;
+            for (size_t i = 0; i < total; ++i) d = std::max(d, std::fabs((double)out[i] - (double)ref[i]));
+            ev.ms = ms / opt->reps;
+            ev.err = std::isfinite(d) ? d / rmax : 1e30;
+        } else {
+            ev.ms = kTimeoutMs;
+            ev.err = 1e30;
+        }
+        ev.fitness = 1.0 / std::sqrt(ev.err <= opt->max_err ? ev.ms : kTimeoutMs);
+        memo[g] = ev;
+        ++evaluations;
+        return ev;
+    };
+    std::vector<int> seed(genes.size(), 0), best_g = seed;
+    Eval best, analytic;
+    best.fitness = -1.0;
+    if (s == NET_OK) {
+        analytic = evaluate(seed);
+        if (!genes.empty()) {
+            std::vector<int> alpha;
+            for (auto& o : options) alpha.push_back((int)o.size());
+            ga_run(alpha, opt, seed, evaluate, &best_g, &best);
+        } else {
+            best = analytic;
+        }
+    }
+    const bool found = s == NET_OK && best.fitness > 0 && best.err <= opt->max_err;
+    if (found) apply(best_g);
+    else restore();
+    std::memset(res, 0, sizeof(*res));
+    res->ms = found ? best.ms : analytic.ms;
+    res->ms_analytic = analytic.ms;
+    res->evaluations = evaluations;
+    res->memo_hits = hits;
+    int changed = 0;
+    for (size_t i = 0; i < genes.size(); ++i) changed += found && best_g[i] != seed[i];
+    res->changed_layers = changed;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != NET_OK) return s;
+    if (!found) return fail(NET_E_STATE, "no grouped plan within the error budget %g", opt->max_err);
+    return NET_OK;
+}
+
+extern "C" net_status net_plan_grouped(const net_t* n, int* bn, int* mb, int* nst, int cnt) {
+    if (!n || !bn || !mb || !nst) return fail(NET_E_INVAL, "NULL argument");
+    if (cnt < (int)n->L.size()) return fail(NET_E_INVAL, "need %d entries", (int)n->L.size());
+    for (size_t l = 0; l < n->L.size(); ++l) {
+        bn[l] = n->L[l].grp_bn;
+        mb[l] = n->L[l].grp_mb;
+        nst[l] = n->L[l].grp_nst;
+    }
+    return NET_OK;
+}

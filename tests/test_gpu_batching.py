@@ -73,3 +73,30 @@ def test_uneven_64_frames_full_size():
         print("uneven frame %d side %d: err %.3e argmax %.4f" % (i, sides[i], e, agree))
         assert e <= 2e-2 and agree >= 0.99
     assert all(np.isfinite(y).all() for y in ys)
+
+
+def test_uneven_tuned_grouped_plan():
+    """The genetic search over the grouped launches (N tile, CTAs per SM,
+    ring stage cap per layer): every plan computes the same sums in the same
+    order, so the tuned batch is bit-identical to the analytic one and each
+    frame to its own pass; the frames also meet the oracle."""
+    import torch
+    spec = synth.net_9conv()
+    blob = synth.weights_for(spec, 52)
+    sides = [96, 64, 160, 32, 128, 64, 96]
+    frames = [synth.frame_for(52, i, s) for i, s in enumerate(sides)]
+    with make_net(spec, prec="bf16", max_batch=1, max_side=160) as net:
+        net.load_weights(blob)
+        before = _uneven(net, frames)
+        d_in = [torch.from_numpy(f).cuda() for f in frames]
+        d_out = [torch.empty((1,) + net.output_shape(s, s), device="cuda") for s in sides]
+        plan, res = net.tune_uneven(d_in, sides, d_out, population=8, generations=4, reps=2, seed=3)
+        print("grouped plan", plan, res)
+        assert res["ms"] <= res["ms_analytic"] and res["evaluations"] >= 1
+        assert net.plan_grouped() == plan
+        after = _uneven(net, frames)
+        alone = [_uneven(net, [f])[0] for f in frames]
+    for i, f in enumerate(frames):
+        np.testing.assert_array_equal(after[i], before[i])
+        np.testing.assert_array_equal(after[i], alone[i])
+        assert oracle.normwise_rel_err(after[i], oracle.forward(spec.layers, 3, f, blob)) <= 2e-2
