@@ -46,6 +46,7 @@ struct NightState {
     size_t ws_bytes = 0;
     float* grad = nullptr;      // net_nightmare_step: the frames' gradient, NCHW
     double* d_red = nullptr;    // per-frame reductions
+    double* d_part = nullptr;   // their per-block parts
     double* h_red = nullptr;    // pinned host copy
 };
 
@@ -62,6 +63,7 @@ void night_free(net* n) {
     cudaFree(S->ws);
     cudaFree(S->grad);
     cudaFree(S->d_red);
+    cudaFree(S->d_part);
     if (S->h_red) cudaFreeHost(S->h_red);
     delete S;
     n->night = nullptr;
@@ -168,23 +170,37 @@ __global__ void pool_leaky_bwd_kernel(const float* __restrict__ gout, const floa
 }
 
 // Per-frame sum of v^2 (kind 0) or |v| (kind 1) over `count` floats at
-// stride `fstride`, in FP64, one block per frame (fixed order: deterministic).
-__global__ void frame_reduce_kernel(const float* __restrict__ v, long long count, long long fstride, int kind,
-                                    double* out) {
-    const float* p = v + blockIdx.x * fstride;
+// stride `fstride`, in FP64, in two passes with a fixed summation order (so
+// deterministic): kRedParts blocks per frame each sum a contiguous part
+// into part[frame][block] (grid kRedParts x frames), then one thread per
+// frame adds the parts in order.
+constexpr int kRedParts = 64;
+__global__ void frame_reduce_parts_kernel(const float* __restrict__ v, long long count, long long fstride, int kind,
+                                          double* part) {
+    const float* p = v + blockIdx.y * fstride;
+    const long long per = (count + kRedParts - 1) / kRedParts;
+    const long long b = blockIdx.x * per, e = min(count, b + per);
     double s = 0.0;
-    for (long long i = threadIdx.x; i < count; i += blockDim.x) {
+    for (long long i = b + threadIdx.x; i < e; i += blockDim.x) {
         const double t = p[i];
         s += kind == 0 ? t * t : fabs(t);
     }
-    __shared__ double red[1024];
+    __shared__ double red[256];
     red[threadIdx.x] = s;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) part[blockIdx.y * kRedParts + blockIdx.x] = red[0];
+}
+
+__global__ void frame_reduce_sum_kernel(const double* __restrict__ part, int frames, double* out) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= frames) return;
+    double s = 0.0;
+    for (int b = 0; b < kRedParts; ++b) s += part[f * kRedParts + b];
+    out[f] = s;
 }
 
 // x += rate * g / mean|g| per frame (mean from frame_reduce_kernel's sums).
@@ -197,6 +213,13 @@ __global__ void ascent_kernel(float* x, const float* __restrict__ g, long long p
         const double m = sum_abs[f] / (double)per_frame;
         x[i] += (float)((double)rate * g[i] / (m > 1e-30 ? m : 1e-30));
     }
+}
+
+cudaError_t frame_reduce(const float* v, long long count, long long fstride, int kind, int frames, double* part,
+                         double* out, cudaStream_t st) {
+    frame_reduce_parts_kernel<<<dim3(kRedParts, frames), 256, 0, st>>>(v, count, fstride, kind, part);
+    frame_reduce_sum_kernel<<<(frames + 127) / 128, 128, 0, st>>>(part, frames, out);
+    return cudaGetLastError();
 }
 
 unsigned grid_for(long long total, int threads) {
@@ -251,6 +274,7 @@ static net_status night_setup(net* n) {
     NK(cudaMemsetAsync(S->zero_bias, 0, rows_max * sizeof(float), n->stream));
     NK(cudaMalloc(&S->grad, (size_t)n->max_batch * n->in_c * n->max_side * n->max_side * sizeof(float)));
     NK(cudaMalloc(&S->d_red, sizeof(double) * n->max_batch));
+    NK(cudaMalloc(&S->d_part, sizeof(double) * n->max_batch * kRedParts));
     NK(cudaHostAlloc(&S->h_red, sizeof(double) * n->max_batch, cudaHostAllocDefault));
     return NET_OK;
 }
@@ -367,9 +391,8 @@ static net_status night_grad(net* n, const float* d_in, int batch, int h, int w,
     // objective per frame: the output of `layer` (padded channels are zero)
     const int csL = rup(n->L[layer].d.cout, 4);
     const long long per_frame = (long long)H[layer + 1] * W[layer + 1] * csL;
-    frame_reduce_kernel<<<batch, 1024, 0, st>>>(x, per_frame, per_frame, 0, S->d_red);
-    NK(cudaGetLastError());
-    ++n->launches;
+    NK(frame_reduce(x, per_frame, per_frame, 0, batch, S->d_part, S->d_red, st));
+    n->launches += 2;
     // ---- backward: dJ/d(output of layer) = that output.  g[1] holds the
     // gradient before a layer's pool and leaky, g[0] the one after its conv
     // (the next layer down's output gradient): no kernel reads the buffer it
@@ -478,11 +501,10 @@ extern "C" net_status net_nightmare_step(net_t* n, float* d_frames, int batch, i
     if (s != NET_OK) return s;
     NK(cudaMemcpyAsync(S->h_red, S->d_red, sizeof(double) * batch, cudaMemcpyDeviceToHost, n->stream));
     const long long per = (long long)n->in_c * h * w;
-    frame_reduce_kernel<<<batch, 1024, 0, n->stream>>>(S->grad, per, per, 1, S->d_red);
-    NK(cudaGetLastError());
+    NK(frame_reduce(S->grad, per, per, 1, batch, S->d_part, S->d_red, n->stream));
     ascent_kernel<<<grid_for(per * batch, 256), 256, 0, n->stream>>>(d_frames, S->grad, per, batch, S->d_red, rate);
     NK(cudaGetLastError());
-    n->launches += 2;
+    n->launches += 3;
     NK(cudaStreamSynchronize(n->stream));
     if (objective)
         for (int f = 0; f < batch; ++f) objective[f] = 0.5 * S->h_red[f];

@@ -16,11 +16,14 @@
 // detections are its kept boxes class by class, each class in that order.
 //
 // Three kernels, all FP32: decode (one thread per box, threads along grid
-// columns so that each channel is read contiguously) appends candidates to
-// per-(frame, class) lists; NMS (one CTA per (frame, class)) sorts its list
-// in shared memory by a 64-bit key (inverted score bits, id), so the result
-// does not depend on the order the atomics appended in, and suppresses;
-// compaction (one warp per frame) concatenates the classes' kept boxes.
+// columns so that each channel is read contiguously; up to 32 class logits
+// in registers) appends candidates to per-(frame, class) lists; NMS (one CTA
+// per (frame, class)) sorts its list in shared memory by a 64-bit key
+// (inverted score bits, id), so the result does not depend on the order the
+// atomics appended in, and suppresses in blocks of 32 candidates (a warp
+// settles a block, the CTA applies its kept boxes to the rest: one barrier
+// per block, the decisions of one-at-a-time greedy NMS); compaction (one
+// warp per frame) concatenates the classes' kept boxes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -98,13 +101,8 @@ __global__ void region_decode_kernel(const float* __restrict__ map, int batch, i
     const float h = expf(p[3 * plane]) * anchor[2 * a + 1] / (float)GH;
     const float obj = sigm(p[4 * plane]);
     const float* lg = p + 5 * plane;
-    float m = lg[0];
-    for (int c = 1; c < C; ++c) m = fmaxf(m, lg[c * plane]);
-    float sum = 0.f;
-    for (int c = 0; c < C; ++c) sum += expf(lg[c * plane] - m);
     const int id = (i * GW + j) * A + a;
-    for (int c = 0; c < C; ++c) {
-        const float s = obj * (expf(lg[c * plane] - m) / sum);
+    auto append = [&](int c, float s) {
         if (s > thresh) {
             const int slot = atomicAdd(&cnt[f * C + c], 1);
             if (slot < maxc) {
@@ -119,6 +117,31 @@ __global__ void region_decode_kernel(const float* __restrict__ map, int batch, i
                 cand[((long long)f * C + c) * maxc + slot] = q;
             }
         }
+    };
+    if (C <= 32) {
+        // up to 32 classes: all logits in registers, their loads issued together
+        float e[32];
+        float m = -INFINITY;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            e[c] = c < C ? lg[c * plane] : -INFINITY;
+            m = fmaxf(m, e[c]);
+        }
+        float sum = 0.f;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            e[c] = c < C ? expf(e[c] - m) : 0.f;
+            sum += e[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+            if (c < C) append(c, obj * (e[c] / sum));
+    } else {
+        float m = lg[0];
+        for (int c = 1; c < C; ++c) m = fmaxf(m, lg[c * plane]);
+        float sum = 0.f;
+        for (int c = 0; c < C; ++c) sum += expf(lg[c * plane] - m);
+        for (int c = 0; c < C; ++c) append(c, obj * (expf(lg[c * plane] - m) / sum));
     }
 }
 
@@ -184,11 +207,39 @@ __global__ void __launch_bounds__(kNmsThreads) region_nms_kernel(int C, int maxc
         supp[r] = 0;
     }
     __syncthreads();
-    for (int r = 0; r < n; ++r) {
-        if (!supp[r]) {   // uniform: every thread reads the flag after the barrier
-            const float4 b = box[r];
-            for (int q = r + 1 + threadIdx.x; q < n; q += blockDim.x)
-                if (!supp[q] && iou_f(b, box[q]) > iou_thr) supp[q] = 1;
+    // greedy suppression in blocks of 32 candidates: warp 0 settles a block
+    // among itself (lane l = candidate r0 + l; in rank order each candidate
+    // still alive is kept and drops the later ones it overlaps), then the
+    // whole CTA drops every later candidate a kept one of the block overlaps.
+    // The same decisions as one candidate at a time, one barrier per block.
+    __shared__ unsigned kept_mask;
+    for (int r0 = 0; r0 < n; r0 += 32) {
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x, r = r0 + lane;
+            bool alive = r < n && !supp[r];
+            const float4 mine = r < n ? box[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = 0; i < 32; ++i) {
+                const bool ai = __shfl_sync(0xffffffffu, alive, i);
+                if (!ai) continue;   // uniform across the warp
+                const float4 bi = make_float4(__shfl_sync(0xffffffffu, mine.x, i), __shfl_sync(0xffffffffu, mine.y, i),
+                                              __shfl_sync(0xffffffffu, mine.z, i), __shfl_sync(0xffffffffu, mine.w, i));
+                if (lane > i && alive && iou_f(bi, mine) > iou_thr) alive = false;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, alive);
+            if (r < n) supp[r] = alive ? 0 : 1;
+            if (lane == 0) kept_mask = m;
+        }
+        __syncthreads();
+        const unsigned m = kept_mask;
+        for (int q = r0 + 32 + threadIdx.x; q < n; q += blockDim.x) {
+            if (supp[q]) continue;
+            const float4 bq = box[q];
+            for (unsigned mm = m; mm; mm &= mm - 1) {
+                if (iou_f(box[r0 + __ffs(mm) - 1], bq) > iou_thr) {
+                    supp[q] = 1;
+                    break;
+                }
+            }
         }
         __syncthreads();
     }

@@ -15,10 +15,11 @@
 //  * jacobi_sweep_kernel: persistent grid (a multiple of the SM count), each
 //    work tile a strip of R rows x 4*blockDim columns; a thread owns four
 //    adjacent columns and walks down the strip keeping the rows above, at
-//    and below in registers (each input row is read once per strip) with the
-//    next four rows' loads in flight (bytes in flight, not instructions,
-//    bound a streaming kernel), the left and right neighbours coming from
-//    the adjacent lanes by shuffles; sixteen 128-thread blocks per SM.
+//    and below in registers (each input row is read once per strip) and the
+//    next six rows in flight by cp.async into a per-thread shared-memory ring
+//    (bytes in flight, not instructions, bound a streaming kernel; the ring
+//    takes no registers), the left and right neighbours coming from the
+//    adjacent lanes by shuffles; sixteen 128-thread blocks per SM.
 //    Each block writes its largest change to a partial slot.
 //  * jacobi_finish_kernel (one block): reduces the partials and applies the
 //    stopping rule on the device: sweeps += 1, done when the change is at or
@@ -51,14 +52,29 @@ struct JState {
 };
 
 constexpr int kThreads = 128;   // 512 columns per tile row
-constexpr int kAhead = 4;       // rows loaded ahead of the one being computed (loads in flight per thread)
+constexpr int kAhead = 6;       // rows in flight ahead of the one being computed (per thread, cp.async ring)
 constexpr int kChunk = 16;      // sweeps per captured graph (even: buffer parity is kept per chunk)
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
-__global__ void __launch_bounds__(kThreads) jacobi_sweep_kernel(float* b0, float* b1, int ny, int nx, int P,
-                                                                const JState* __restrict__ st, float* partial,
-                                                                int col_blocks, int strips, int rows) {
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* src, bool in) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+                 "l"(src), "r"(in ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// 16 blocks of 128 threads an SM.  The rows below the one being computed
+// stream into a per-thread ring of kAhead 16-byte slots in shared memory by
+// cp.async (zero-filled past the strip), so the bytes in flight (~196 KB an
+// SM) take no registers; each thread reads only its own slots, so no block
+// barrier is needed, only the wait for its own oldest copy group.
+__global__ void __launch_bounds__(kThreads, 16) jacobi_sweep_kernel(float* b0, float* b1, int ny, int nx, int P,
+                                                                     const JState* __restrict__ st, float* partial,
+                                                                     int col_blocks, int strips, int rows) {
+    __shared__ float4 ring[kAhead][kThreads];
     if (st->done) return;
     const int k = st->sweeps;
     const float* src = (k & 1) ? b1 : b0;
@@ -74,47 +90,51 @@ __global__ void __launch_bounds__(kThreads) jacobi_sweep_kernel(float* b0, float
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 up = inb ? ld4(src + (size_t)(y0 - 1) * P + x0) : z4;
         float4 cur = inb ? ld4(src + (size_t)y0 * P + x0) : z4;
-        // rows y+1 .. y+kAhead in flight: a ring of kAhead registers, slot
-        // (y - y0) % kAhead holding row y + 1 when row y is computed
-        float4 nxt[kAhead];
+        // slot q holds row y0 + 1 + q, then every kAhead rows further down
 #pragma unroll
         for (int q = 0; q < kAhead; ++q) {
             const int yy = y0 + 1 + q;
-            nxt[q] = (inb && yy <= y1) ? ld4(src + (size_t)yy * P + x0) : z4;
+            const bool ok = inb && yy <= y1;
+            cp_async16(&ring[q][threadIdx.x], src + (size_t)(ok ? yy : 0) * P + (ok ? x0 : 0), ok);
+            cp_async_commit();
         }
-        for (int yb = y0; yb < y1; yb += kAhead) {   // uniform over the block
+        int slot = 0;
+        for (int y = y0; y < y1; ++y) {   // uniform over the block
+            cp_async_wait<kAhead - 1>();   // the oldest group: row y + 1
+            const float4 dn = ring[slot][threadIdx.x];
+            float left = __shfl_up_sync(0xffffffffu, cur.w, 1);
+            float right = __shfl_down_sync(0xffffffffu, cur.x, 1);
+            if (lane == 0) left = (inb && x0 > 0) ? src[(size_t)y * P + x0 - 1] : 0.f;
+            if (lane == 31) right = (x0 + 4 < P) ? src[(size_t)y * P + x0 + 4] : 0.f;
+            float4 nw;
+            nw.x = 0.25f * ((up.x + dn.x) + (left + cur.y));
+            nw.y = 0.25f * ((up.y + dn.y) + (cur.x + cur.z));
+            nw.z = 0.25f * ((up.z + dn.z) + (cur.y + cur.w));
+            nw.w = 0.25f * ((up.w + dn.w) + (cur.z + right));
+            // interior columns 1 .. nx - 2 take the new value; the boundary and
+            // the pitch padding keep theirs
+            const float c4[4] = {cur.x, cur.y, cur.z, cur.w};
+            float n4[4] = {nw.x, nw.y, nw.z, nw.w};
 #pragma unroll
-            for (int q = 0; q < kAhead; ++q) {
-                const int y = yb + q;
-                if (y >= y1) break;
-                const float4 dn = nxt[q];
-                const int yy = y + 1 + kAhead;   // refill the slot with the row kAhead further down
-                nxt[q] = (inb && yy <= y1) ? ld4(src + (size_t)yy * P + x0) : z4;
-                float left = __shfl_up_sync(0xffffffffu, cur.w, 1);
-                float right = __shfl_down_sync(0xffffffffu, cur.x, 1);
-                if (lane == 0) left = (inb && x0 > 0) ? src[(size_t)y * P + x0 - 1] : 0.f;
-                if (lane == 31) right = (x0 + 4 < P) ? src[(size_t)y * P + x0 + 4] : 0.f;
-                float4 nw;
-                nw.x = 0.25f * ((up.x + dn.x) + (left + cur.y));
-                nw.y = 0.25f * ((up.y + dn.y) + (cur.x + cur.z));
-                nw.z = 0.25f * ((up.z + dn.z) + (cur.y + cur.w));
-                nw.w = 0.25f * ((up.w + dn.w) + (cur.z + right));
-                // interior columns 1 .. nx - 2 take the new value; the boundary
-                // and the pitch padding keep theirs
-                const float c4[4] = {cur.x, cur.y, cur.z, cur.w};
-                float n4[4] = {nw.x, nw.y, nw.z, nw.w};
-#pragma unroll
-                for (int k4 = 0; k4 < 4; ++k4) {
-                    const int x = x0 + k4;
-                    if (x >= 1 && x <= nx - 2) best = fmaxf(best, fabsf(n4[k4] - c4[k4]));
-                    else n4[k4] = c4[k4];
-                }
-                if (inb)
-                    *reinterpret_cast<float4*>(dst + (size_t)y * P + x0) = make_float4(n4[0], n4[1], n4[2], n4[3]);
-                up = cur;
-                cur = dn;
+            for (int k4 = 0; k4 < 4; ++k4) {
+                const int x = x0 + k4;
+                if (x >= 1 && x <= nx - 2) best = fmaxf(best, fabsf(n4[k4] - c4[k4]));
+                else n4[k4] = c4[k4];
             }
+            if (inb) *reinterpret_cast<float4*>(dst + (size_t)y * P + x0) = make_float4(n4[0], n4[1], n4[2], n4[3]);
+            {
+                // refill the slot (its row is consumed: nw depends on it) with the
+                // row kAhead further down
+                const int yy = y + 1 + kAhead;
+                const bool ok = inb && yy <= y1;
+                cp_async16(&ring[slot][threadIdx.x], src + (size_t)(ok ? yy : 0) * P + (ok ? x0 : 0), ok);
+                cp_async_commit();
+            }
+            slot = slot + 1 == kAhead ? 0 : slot + 1;
+            up = cur;
+            cur = dn;
         }
+        cp_async_wait<0>();   // no copy of this strip outlives it (slots are reused by the next)
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -227,9 +247,9 @@ extern "C" net_status net_jacobi_create(int ny, int nx, int device, void* cuda_s
     }
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    // persistent: sixteen 128-thread blocks per SM (2048 threads) taking
-    // strips of 32 rows round robin (measured faster than one longer strip
-    // per block: 4.8 against 4.2 TB/s at 8192 x 8192)
+    // persistent: sixteen 128-thread blocks per SM (all resident: 32 registers
+    // a thread, 12 KB of shared memory a block) taking strips of 32 rows
+    // round robin (measured faster than one longer strip per block)
     j->col_blocks = cdiv(j->P, 4 * kThreads);
     j->rows = 32;
     j->strips = cdiv(ny - 2, j->rows);

@@ -310,24 +310,28 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     const uint32_t tmem_base = sm->tmem;
     volatile int* abort_flag = &sm->abort;
     if (a.bres && warp == 0 && lane == 0) {
-        // resident weights: every K step's [BN x chunk] box, once, side by
-        // side (the launch has one N tile and no K split).  Weights are
-        // written only by the fold at load time, which the host waits for,
-        // so these loads may overlap the previous kernel's tail.
+        // resident weights: every K step's [BN x chunk] box of this CTA's N
+        // tile, once, side by side.  The launch has no K split and a grid
+        // that is a multiple of the N tile count, so the round-robin work
+        // items (m-tile-major, N tile fastest) of a CTA all have the N tile
+        // worker % n_tiles.  Weights are written only by the fold at load
+        // time, which the host waits for, so these loads may overlap the
+        // previous kernel's tail.
         const uint32_t rb = smem_u32(&sm->bres);
+        const int nt_res = (worker - fdiv(worker, a.fd_ntiles) * a.n_tiles) * BN;   // first weight row
         if (a.pair) {
             // pair mode: slots in tap-pair order; slot 9 starts at K column
             // 9 * Cp, past the weights' last column, so TMA fills it with zeros
             tc::mbar_expect_tx(rb, (uint32_t)kPairSlots * b_bytes);
             for (int s = 0; s < kPairSlots; ++s) {
                 const int tap = s < 9 ? (s % 3) * 3 + s / 3 : 9;
-                tc::tma_load_2d(smem_u32(sBres + (size_t)s * b_bytes), &tmB, tap * a.Cp, 0, rb);
+                tc::tma_load_2d(smem_u32(sBres + (size_t)s * b_bytes), &tmB, tap * a.Cp, nt_res, rb);
             }
         } else {
             tc::mbar_expect_tx(rb, (uint32_t)nkb * b_bytes);
             int ch = 0, tap = 0;
             for (int ks = 0; ks < nkb; ++ks) {
-                tc::tma_load_2d(smem_u32(sBres + (size_t)ks * b_bytes), &tmB, tap * a.Cp + ch * a.cpc, 0, rb);
+                tc::tma_load_2d(smem_u32(sBres + (size_t)ks * b_bytes), &tmB, tap * a.Cp + ch * a.cpc, nt_res, rb);
                 if (++ch == a.chunks) {
                     ch = 0;
                     ++tap;
@@ -1010,7 +1014,8 @@ bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb, int mb) {
     // resident weights must leave room for at least 8 A-only stages (4 with
     // two CTAs an SM)
     const size_t a_st = (mb == 2 ? 4 : 8) * 128 * (size_t)chb;
-    return n_tiles == 1 && ksplit == 1 && (size_t)nk * BN * chb + a_st <= tc_avail(mb);
+    (void)n_tiles;   // several N tiles: each CTA keeps its own tile's weights (launch grid a multiple of n_tiles)
+    return ksplit == 1 && (size_t)nk * BN * chb + a_st <= tc_avail(mb);
 }
 
 template <int BN, int DT, int MB>
@@ -1018,6 +1023,9 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     TcArgs a = a0;
     // 16-byte chunks (K = 8) only in pair mode, and pair mode only in its one shape
     if ((a.chb == 16) != (a.pair != 0)) return cudaErrorInvalidValue;
+    // resident weights: one N tile per CTA, which needs a grid that is a
+    // multiple of the N tile count and no K split
+    if (a.bres && (a.ksplit != 1 || workers % a.n_tiles != 0)) return cudaErrorInvalidValue;
     if (a.pair && (DT != DT_BF16 || !a.tapm || !a.bres || a.ksplit != 1 || a.k != 3 || a.chunks != 1 || a.kalt))
         return cudaErrorInvalidValue;
     if (!tc_geometry(BN, a.chb, a.bres, a.k * a.k * a.chunks, MB, &a)) return cudaErrorInvalidValue;

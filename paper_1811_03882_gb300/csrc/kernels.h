@@ -191,9 +191,10 @@ cudaError_t maxpool_s1_grouped(const PoolJob* jobs, int njobs, long long total, 
                                cudaStream_t st);
 
 int tc_chunk_bytes(int Cp, int dt);
-// Whether a launch keeps all of its weights resident in shared memory: one
-// N tile, no K split, and nk boxes of BN x chunk bytes fit in the B ring
-// (of a CTA's share of the SM: mb CTAs an SM).
+// Whether a launch keeps its weights resident in shared memory: no K split,
+// and nk boxes of BN x chunk bytes (one N tile's weights; with several N
+// tiles each CTA serves one, the grid a multiple of n_tiles) fit beside the
+// A stages (of a CTA's share of the SM: mb CTAs an SM).
 bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb, int mb);
 cudaError_t tc_encode_act(CUtensorMap* tm, const void* base, int dt, int n, int H, int W, int Cp, int TW,
                           int TH);

@@ -446,6 +446,14 @@ void dn::tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, i
     *mb = m;
     *bres = tc_b_resident(BN, n_tiles, ks, nk, chb, m) ? 1 : 0;
     *workers = std::max(1, std::min(items, num_sms * m));
+    // resident weights with several N tiles: each CTA serves one N tile, so
+    // the grid must be a multiple of the N tile count (the round-robin items
+    // of a CTA then share it); drop residency where that rounds too far
+    if (*bres && n_tiles > 1) {
+        const int w = (*workers / n_tiles) * n_tiles;
+        if (w < n_tiles || w * 8 < *workers * 7) *bres = 0;
+        else *workers = w;
+    }
 }
 
 int dn::tc_mb_forced() {
