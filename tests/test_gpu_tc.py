@@ -273,3 +273,30 @@ def test_per_layer_error_report(prec, mix):
             assert flips <= 1e-2, (l, flips)
             assert r_loc <= 2e-3, (l, r_loc)
         a, cin = o, layer.cout
+
+
+@pytest.mark.parametrize("cin,cout,k,pool,hw,bn", [
+    (64, 256, 3, synth.POOL_NONE, (56, 40), 64),     # 4 N tiles, tap-merged stages
+    (64, 128, 3, synth.POOL_2X2S2, (48, 64), 64),    # 2 N tiles, pooled
+    (512, 256, 1, synth.POOL_NONE, (28, 28), 64),    # 1x1, 4 N tiles, 8 K chunks resident
+])
+def test_resident_weights_several_n_tiles(cin, cout, k, pool, hw, bn):
+    """Weights resident in shared memory with several N tiles: the grid is a
+    multiple of the N tile count and every CTA keeps its own tile's weights
+    (forced through the tile override).  Checked against the
+    quantisation-aware oracle like the other single layers."""
+    L = synth.Layer
+    spec = synth.NetSpec("layer", cin, [L(k, cout, True, synth.ACT_LEAKY, pool)])
+    s = synth.Stream(cin * 3 + cout + bn)
+    x = synth.make_frames(s, 2, cin, hw[0], hw[1], -1, 1)
+    blob = synth.pack_blob(spec, synth.make_params(s, spec))
+    precs = default_precs(spec, "bf16")
+    qa = oracle.forward_quant(spec.layers, cin, x, blob, precs)
+    with make_net(spec, prec="bf16", max_batch=2, max_side=max(hw)) as net:
+        net.load_weights(blob)
+        net.set_layer_tiles(0, bn, 1)
+        assert net.plan_tiles(2, hw[0], hw[1])[0] == (bn, 1)
+        y = run_device(net, x)
+    e = oracle.normwise_rel_err(y, qa)
+    print("resident %d N tiles: err %.3e" % (-(-cout // bn), e))
+    assert np.isfinite(y).all() and e <= 1e-4
