@@ -48,7 +48,7 @@ DEFAULT = "19conv-448-b8-bf16"
 # launches in one forward pass of the workload), with the first 16 hex digits
 # of the SHA-256 of the conv kernel's source when it was captured: the figure
 # is reported only while the source is unchanged, null otherwise.
-TRAFFIC = {"19conv-448-b8-bf16": {"conv_tc_kernel": (208.55e6 / 19, "cb075788d4cce2d3")}}
+TRAFFIC = {"19conv-448-b8-bf16": {"conv_tc_kernel": (208.56e6 / 19, "be000096d04b3876")}}
 KERNEL_SRC = os.path.join(ROOT, "paper_1811_03882_gb300", "csrc", "k_conv_tc.cu")
 
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
@@ -383,7 +383,7 @@ def run_jacobi(torch, binding, dev, cpu_budget_s=4.0):
 
 def run_detect(torch, binding, dev, side=416, batch=8):
     """Detection post-processing after the 9-conv network (125 channels on a
-    13 x 13 grid per 416 x 416 frame): the three device kernels timed with
+    13 x 13 grid per 416 x 416 frame): the two device kernels timed with
     CUDA events on a batch's map, and frames -> detections end to end
     (net_forward_detect: one H2D of the frames, one D2H of the detections)."""
     spec = synth.net_9conv()
@@ -418,7 +418,7 @@ def run_detect(torch, binding, dev, side=416, batch=8):
     e2e = time.perf_counter() - t0
     net.close()
     return {"network": "9-conv", "batch": batch, "side": side, "grid": [gh, gw], "anchors": 5, "classes": 20,
-            "score_thresh": 0.04, "nms_iou": 0.45, "detect_ms_per_batch": det_ms, "kernels": 3,
+            "score_thresh": 0.04, "nms_iou": 0.45, "detect_ms_per_batch": det_ms, "kernels": 2,
             "kept_per_frame": [int(v) for v in counts],
             "e2e_frames_per_s": batch * reps / e2e,
             "e2e_note": "frames -> detections through net_forward_detect (BF16 network + decode + NMS), "

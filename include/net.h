@@ -184,8 +184,8 @@ net_status net_forward_uneven(net_t* net, const float* const* d_in, const int* s
  * id) and drops a box whose IoU with a kept box of its class exceeds
  * nms_iou.  A frame's detections are its kept boxes class by class
  * (ascending), each class in that order, at most max_det of them; its count
- * is the number kept before that cut.  Decode, suppression and compaction
- * run in FP32 in three kernels; the result does not depend on the order in
+ * is the number kept before that cut.  Decode, then suppression and
+ * compaction, run in FP32 in two kernels; the result does not depend on the order in
  * which the device appended candidates. */
 #define NET_REGION_MAX_ANCHORS 16
 typedef struct {
@@ -296,7 +296,7 @@ net_status net_jacobi_solve(net_jacobi_t* j, const float* grid_in, float tol, in
 net_status net_jacobi_solve_device(net_jacobi_t* j, const float* d_in, float tol, int iter_max, float* d_out,
                                    int* sweeps, float* change);
 
-/* Kernels the handle has launched (every queued sweep counts two). */
+/* Kernels the handle has launched (one per queued sweep). */
 net_status net_jacobi_launches(const net_jacobi_t* j, uint64_t* total);
 
 /* Releases the handle's device and host memory.  NULL is accepted. */

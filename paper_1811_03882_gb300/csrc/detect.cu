@@ -15,15 +15,17 @@
 // with a kept box of its class exceeds the IoU threshold.  A frame's
 // detections are its kept boxes class by class, each class in that order.
 //
-// Three kernels, all FP32: decode (one thread per box, threads along grid
-// columns so that each channel is read contiguously; up to 32 class logits
-// in registers) appends candidates to per-(frame, class) lists; NMS (one CTA
-// per (frame, class)) sorts its list in shared memory by a 64-bit key
-// (inverted score bits, id), so the result does not depend on the order the
-// atomics appended in, and suppresses in blocks of 32 candidates (a warp
-// settles a block, the CTA applies its kept boxes to the rest: one barrier
-// per block, the decisions of one-at-a-time greedy NMS); compaction (one
-// warp per frame) concatenates the classes' kept boxes.
+// Two kernels, all FP32.  Decode: one thread per box, threads along grid
+// columns so that each channel is read contiguously, up to 32 class logits
+// in registers; candidates are appended to per-(frame, class) lists, one
+// atomic per warp and class reserving the slots of its lanes.  NMS: one CTA
+// per (frame, class) sorts its list by a 64-bit key (inverted score bits,
+// id; bitonic, keys in registers), so the result does not depend on the
+// order the atomics appended in, and suppresses in blocks of 32 candidates:
+// the overlaps inside each block are found in parallel first, then a warp
+// settles a block by bit operations and the CTA drops what its kept boxes
+// overlap (the decisions of one-at-a-time greedy NMS).  The last CTA of a
+// frame to finish concatenates the frame's classes into its detection rows.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,7 +52,7 @@ struct RegionState {
     net_region r{};
     int maxc = 0;               // candidate slots per (frame, class): grid cells x anchors
     int max_batch = 0;
-    int* d_cnt = nullptr;       // [max_batch][C] candidates, then kept, per (frame, class)
+    int* d_cnt = nullptr;       // [max_batch][C + 1]: per class candidates, then kept; classes done
     RegionCand* d_cand = nullptr;   // [max_batch][C][maxc]
     float* d_anchor = nullptr;  // [2A]
     void* d_out = nullptr;      // forward_detect: [counts (max_batch ints, 256-byte block)][dets]
@@ -74,21 +76,24 @@ void region_free(net* n) {
 
 namespace {
 
-constexpr int kMaxCand = 4096;   // candidate slots per (frame, class): the NMS sort's shared-memory bound
-constexpr int kNmsThreads = 256;
+constexpr int kMaxCand = 4096;   // candidate slots per (frame, class): the NMS sort's register/shared bound
 
 __device__ __forceinline__ float sigm(float v) { return 1.f / (1.f + expf(-v)); }
 
+// Counters, per frame f: cnt[f*(C+1) + c] the candidates (after NMS: the
+// kept boxes) of class c, cnt[f*(C+1) + C] the classes of f done with NMS.
 __global__ void region_decode_kernel(const float* __restrict__ map, int batch, int A, int C, int GH, int GW,
                                      const float* __restrict__ anchor, float thresh, int maxc, int* cnt,
                                      RegionCand* cand) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long total = (long long)batch * A * GH * GW;
-    if (t >= total) return;
+    const bool valid = t < total;
+    const int lane = threadIdx.x & 31;
     // thread order (frame, anchor, row, column): consecutive threads read
     // consecutive columns of each channel
-    const int j = (int)(t % GW);
-    long long r = t / GW;
+    const long long tt = valid ? t : total - 1;
+    const int j = (int)(tt % GW);
+    long long r = tt / GW;
     const int i = (int)(r % GH);
     r /= GH;
     const int a = (int)(r % A);
@@ -102,20 +107,33 @@ __global__ void region_decode_kernel(const float* __restrict__ map, int batch, i
     const float obj = sigm(p[4 * plane]);
     const float* lg = p + 5 * plane;
     const int id = (i * GW + j) * A + a;
-    auto append = [&](int c, float s) {
-        if (s > thresh) {
-            const int slot = atomicAdd(&cnt[f * C + c], 1);
-            if (slot < maxc) {
-                RegionCand q;
-                q.score = s;
-                q.id = id;
-                q.x = x;
-                q.y = y;
-                q.w = w;
-                q.h = h;
-                q.pad0 = q.pad1 = 0;
-                cand[((long long)f * C + c) * maxc + slot] = q;
-            }
+    // the lanes of one frame share its counters: one atomic per (warp, frame,
+    // class) reserves their slots, each lane's slot follows from the ballot
+    const unsigned peers = __match_any_sync(0xffffffffu, valid ? f : -1);
+    int* fcnt = cnt + (long long)f * (C + 1);
+    RegionCand* fcand = cand + (long long)f * C * maxc;
+    auto put = [&](int c, int slot, float s) {
+        if (slot < maxc) {
+            RegionCand q;
+            q.score = s;
+            q.id = id;
+            q.x = x;
+            q.y = y;
+            q.w = w;
+            q.h = h;
+            q.pad0 = q.pad1 = 0;
+            fcand[(long long)c * maxc + slot] = q;
+        }
+    };
+    auto append = [&](int c, float s) {   // called by all 32 lanes, c uniform
+        const bool pass = valid && s > thresh;
+        const unsigned m = __ballot_sync(0xffffffffu, pass) & peers;
+        if (pass) {
+            const int leader = __ffs(m) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&fcnt[c], __popc(m));
+            base = __shfl_sync(m, base, leader);
+            put(c, base + __popc(m & ((1u << lane) - 1u)), s);
         }
     };
     if (C <= 32) {
@@ -134,8 +152,33 @@ __global__ void region_decode_kernel(const float* __restrict__ map, int batch, i
             sum += e[c];
         }
 #pragma unroll
-        for (int c = 0; c < 32; ++c)
-            if (c < C) append(c, obj * (e[c] / sum));
+        for (int c = 0; c < 32; ++c) e[c] = obj * (e[c] / sum);
+        if (peers == 0xffffffffu) {
+            // the whole warp is one frame: lane c reserves class c's slots, all
+            // classes' atomics in flight together
+            unsigned mine = 0;
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                if (c < C) {
+                    const unsigned b = __ballot_sync(0xffffffffu, valid && e[c] > thresh);
+                    if (lane == c) mine = b;
+                }
+            }
+            int base = 0;
+            if (mine) base = atomicAdd(&fcnt[lane], __popc(mine));
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                if (c < C) {
+                    const unsigned b = __shfl_sync(0xffffffffu, mine, c);
+                    const int bc = __shfl_sync(0xffffffffu, base, c);
+                    if ((b >> lane) & 1u) put(c, bc + __popc(b & ((1u << lane) - 1u)), e[c]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                if (c < C) append(c, e[c]);
+        }
     } else {
         float m = lg[0];
         for (int c = 1; c < C; ++c) m = fmaxf(m, lg[c * plane]);
@@ -145,110 +188,226 @@ __global__ void region_decode_kernel(const float* __restrict__ map, int batch, i
     }
 }
 
-__device__ __forceinline__ float iou_f(float4 a, float4 b) {
-    const float al = a.x - a.z * 0.5f, ar = a.x + a.z * 0.5f, at = a.y - a.w * 0.5f, ab = a.y + a.w * 0.5f;
-    const float bl = b.x - b.z * 0.5f, br = b.x + b.z * 0.5f, bt = b.y - b.w * 0.5f, bb = b.y + b.w * 0.5f;
-    const float iw = fminf(ar, br) - fmaxf(al, bl);
-    const float ih = fminf(ab, bb) - fmaxf(at, bt);
-    const float inter = fmaxf(iw, 0.f) * fmaxf(ih, 0.f);
-    const float uni = a.z * a.w + b.z * b.w - inter;
-    return uni > 0.f ? inter / uni : 0.f;
+// Box edges (left, top, right, bottom) and area, from centre and size.
+__device__ __forceinline__ float4 edges_of(float x, float y, float w, float h) {
+    return make_float4(x - w * 0.5f, y - h * 0.5f, x + w * 0.5f, y + h * 0.5f);
 }
+
+// Whether IoU(a, b) exceeds thr, as inter > thr * union (no division); a
+// union of zero has IoU 0.
+__device__ __forceinline__ bool overlaps(float4 a, float area_a, float4 b, float area_b, float thr) {
+    const float iw = fminf(a.z, b.z) - fmaxf(a.x, b.x);
+    const float ih = fminf(a.w, b.w) - fmaxf(a.y, b.y);
+    const float inter = fmaxf(iw, 0.f) * fmaxf(ih, 0.f);
+    const float uni = area_a + area_b - inter;
+    return uni > 0.f ? inter > thr * uni : 0.f > thr;
+}
+
+__device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int m) {
+    const unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)v, m);
+    const unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(v >> 32), m);
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// Shared memory of the NMS kernel for P = 2^LOGP sort slots and C classes.
+struct NmsSmem {
+    size_t keys, edge, box, sc, ids, area, pre, supp, prefix, total;
+};
+__host__ __device__ inline NmsSmem nms_layout(int P, int C) {
+    NmsSmem s;
+    s.keys = 0;                              // 2 x P u64: the sort's exchange buffers ...
+    s.edge = 0;                              // ... then P float4 edges, in rank order
+    s.box = s.keys + 16 * (size_t)P;         // P float4 (x, y, w, h)
+    s.sc = s.box + 16 * (size_t)P;           // P float score
+    s.ids = s.sc + 4 * (size_t)P;            // P int box id
+    s.area = s.ids + 4 * (size_t)P;          // P float area
+    s.pre = s.area + 4 * (size_t)P;          // P u32: overlaps with earlier candidates of the same 32-block
+    s.supp = s.pre + 4 * (size_t)P;          // P u8: suppressed
+    s.prefix = (s.supp + (size_t)P + 15) & ~(size_t)15;   // C + 1 int: the frame's class offsets
+    s.total = s.prefix + 4 * ((size_t)C + 1);
+    return s;
+}
+
+__host__ __device__ constexpr int nms_threads(int logp) { return (1 << logp) < 1024 ? (1 << logp) : 1024; }
 
 // One CTA per (frame, class): sort the class's candidates by (score
 // descending, id ascending), suppress greedily, write the kept ones back to
-// the front of the list in rank order and their count to cnt.
-__global__ void __launch_bounds__(kNmsThreads) region_nms_kernel(int C, int maxc, float iou_thr, int* cnt,
-                                                                 RegionCand* cand) {
+// the front of the list in rank order and their count to the counter.  The
+// last CTA of a frame to finish (a counter per frame) concatenates the
+// frame's classes into its detection rows.
+//
+// Sort: bitonic over P = 2^LOGP slots with T = min(P, 1024) threads, keys in
+// registers (slot m*T + tid in register m); partners within a warp by
+// shuffles, in the same thread by register pairs, across warps through
+// shared memory (two buffers, so one barrier per such stage).  Suppression
+// in blocks of 32 in rank order: first, for every candidate, the bits of the
+// earlier candidates of its block that it overlaps (all threads); then per
+// block warp 0 settles who is kept by a chain of bit operations (a candidate
+// is kept when still alive and overlapping no kept one before it), and the
+// CTA drops every later candidate that a kept one overlaps.  These are the
+// decisions of greedy NMS taken one candidate at a time.
+template <int LOGP>
+__global__ void __launch_bounds__(nms_threads(LOGP)) region_nms_kernel(int C, int maxc, float iou_thr,
+                                                                       int max_det, int* cnt, RegionCand* cand,
+                                                                       int* counts, net_detection* det) {
+    constexpr int P = 1 << LOGP;
+    constexpr int T = nms_threads(LOGP);
+    constexpr int KPT = P / T;   // keys per thread
+    static_assert(KPT >= 1 && T % 32 == 0 && P <= kMaxCand, "sort slots");
     extern __shared__ __align__(16) unsigned char sm[];
-    const int fc = blockIdx.x;
-    const int n = min(cnt[fc], maxc);
-    RegionCand* L = cand + (long long)fc * maxc;
-    int np2 = 1;
-    while (np2 < n) np2 <<= 1;
-    unsigned long long* key = reinterpret_cast<unsigned long long*>(sm);
-    float4* box = reinterpret_cast<float4*>(sm + (size_t)kMaxCand * 8);
-    float* sc = reinterpret_cast<float*>(sm + (size_t)kMaxCand * 24);
-    int* ids = reinterpret_cast<int*>(sm + (size_t)kMaxCand * 28);
-    unsigned char* supp = sm + (size_t)kMaxCand * 32;
+    const NmsSmem lay = nms_layout(P, C);
+    unsigned long long* kbuf = reinterpret_cast<unsigned long long*>(sm + lay.keys);
+    float4* edge = reinterpret_cast<float4*>(sm + lay.edge);
+    float4* box = reinterpret_cast<float4*>(sm + lay.box);
+    float* sc = reinterpret_cast<float*>(sm + lay.sc);
+    int* ids = reinterpret_cast<int*>(sm + lay.ids);
+    float* area = reinterpret_cast<float*>(sm + lay.area);
+    unsigned* pre = reinterpret_cast<unsigned*>(sm + lay.pre);
+    unsigned char* supp = sm + lay.supp;
+    int* prefix = reinterpret_cast<int*>(sm + lay.prefix);
+    __shared__ unsigned s_kept;
+    __shared__ int s_r0, s_last;
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int f = blockIdx.x / C, c = blockIdx.x - f * C;
+    int* fcnt = cnt + (long long)f * (C + 1);
+    const int n = min(fcnt[c], maxc);
+    RegionCand* L = cand + ((long long)f * C + c) * maxc;
+
     // key: inverted score bits (scores are positive, so larger scores have
     // larger bits), then the id (unique within a class, 12 bits), then the
-    // slot (12 bits, carried along)
-    for (int q = threadIdx.x; q < np2; q += blockDim.x) {
+    // slot (12 bits, carried along); empty slots sort last
+    unsigned long long v[KPT];
+#pragma unroll
+    for (int m = 0; m < KPT; ++m) {
+        const int q = m * T + tid;
         if (q < n) {
             const unsigned s = __float_as_uint(L[q].score);
-            key[q] = ((unsigned long long)(0xFFFFFFFFu - s) << 32) | ((unsigned long long)L[q].id << 12) | (unsigned)q;
+            v[m] = ((unsigned long long)(0xFFFFFFFFu - s) << 32) | ((unsigned long long)L[q].id << 12) | (unsigned)q;
         } else {
-            key[q] = ~0ull;
+            v[m] = ~0ull;
         }
     }
-    __syncthreads();
-    for (int k = 2; k <= np2; k <<= 1) {   // bitonic sort, ascending
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            for (int q = threadIdx.x; q < np2; q += blockDim.x) {
-                const int o = q ^ jj;
-                if (o > q) {
+    int buf = 0;
+#pragma unroll
+    for (int lk = 1; lk <= LOGP; ++lk) {
+#pragma unroll
+        for (int lj = lk - 1; lj >= 0; --lj) {
+            const int k = 1 << lk, jj = 1 << lj;
+            if (jj >= T) {                      // partner in the same thread
+                const int s = jj / T;
+#pragma unroll
+                for (int m = 0; m < KPT; ++m) {
+                    if (m & s) continue;
+                    const int q = m * T + tid;
                     const bool up = (q & k) == 0;
-                    const unsigned long long kq = key[q], ko = key[o];
-                    if ((kq > ko) == up) {
-                        key[q] = ko;
-                        key[o] = kq;
+                    const unsigned long long lo = v[m], hi = v[m | s];
+                    if ((lo > hi) == up) {
+                        v[m] = hi;
+                        v[m | s] = lo;
                     }
                 }
-            }
-            __syncthreads();
-        }
-    }
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {   // gather in rank order
-        const RegionCand& e = L[(int)(key[r] & 0xFFFu)];
-        box[r] = make_float4(e.x, e.y, e.w, e.h);
-        sc[r] = e.score;
-        ids[r] = e.id;
-        supp[r] = 0;
-    }
-    __syncthreads();
-    // greedy suppression in blocks of 32 candidates: warp 0 settles a block
-    // among itself (lane l = candidate r0 + l; in rank order each candidate
-    // still alive is kept and drops the later ones it overlaps), then the
-    // whole CTA drops every later candidate a kept one of the block overlaps.
-    // The same decisions as one candidate at a time, one barrier per block.
-    __shared__ unsigned kept_mask;
-    for (int r0 = 0; r0 < n; r0 += 32) {
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x, r = r0 + lane;
-            bool alive = r < n && !supp[r];
-            const float4 mine = r < n ? box[r] : make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int i = 0; i < 32; ++i) {
-                const bool ai = __shfl_sync(0xffffffffu, alive, i);
-                if (!ai) continue;   // uniform across the warp
-                const float4 bi = make_float4(__shfl_sync(0xffffffffu, mine.x, i), __shfl_sync(0xffffffffu, mine.y, i),
-                                              __shfl_sync(0xffffffffu, mine.z, i), __shfl_sync(0xffffffffu, mine.w, i));
-                if (lane > i && alive && iou_f(bi, mine) > iou_thr) alive = false;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, alive);
-            if (r < n) supp[r] = alive ? 0 : 1;
-            if (lane == 0) kept_mask = m;
-        }
-        __syncthreads();
-        const unsigned m = kept_mask;
-        for (int q = r0 + 32 + threadIdx.x; q < n; q += blockDim.x) {
-            if (supp[q]) continue;
-            const float4 bq = box[q];
-            for (unsigned mm = m; mm; mm &= mm - 1) {
-                if (iou_f(box[r0 + __ffs(mm) - 1], bq) > iou_thr) {
-                    supp[q] = 1;
-                    break;
+            } else if (jj >= 32) {              // partner in another warp
+                unsigned long long* kb = kbuf + buf * P;
+#pragma unroll
+                for (int m = 0; m < KPT; ++m) kb[m * T + tid] = v[m];
+                __syncthreads();
+#pragma unroll
+                for (int m = 0; m < KPT; ++m) {
+                    const int q = m * T + tid;
+                    const unsigned long long o = kb[q ^ jj];
+                    const bool keep_min = ((q & jj) == 0) == ((q & k) == 0);
+                    v[m] = keep_min ? (o < v[m] ? o : v[m]) : (o > v[m] ? o : v[m]);
+                }
+                buf ^= 1;
+            } else {                            // partner in the same warp
+#pragma unroll
+                for (int m = 0; m < KPT; ++m) {
+                    const int q = m * T + tid;
+                    const unsigned long long o = shfl_xor_u64(v[m], jj);
+                    const bool keep_min = ((q & jj) == 0) == ((q & k) == 0);
+                    v[m] = keep_min ? (o < v[m] ? o : v[m]) : (o > v[m] ? o : v[m]);
                 }
             }
         }
+    }
+    __syncthreads();   // the exchange buffers become the edges
+    // gather in rank order
+#pragma unroll
+    for (int m = 0; m < KPT; ++m) {
+        const int r = m * T + tid;
+        if (r < n) {
+            const RegionCand& e = L[(int)(v[m] & 0xFFFu)];
+            box[r] = make_float4(e.x, e.y, e.w, e.h);
+            edge[r] = edges_of(e.x, e.y, e.w, e.h);
+            area[r] = e.w * e.h;
+            sc[r] = e.score;
+            ids[r] = e.id;
+            supp[r] = 0;
+        }
+    }
+    __syncthreads();
+    // overlaps within each block of 32 (earlier candidate first, as greedy NMS
+    // compares a kept box with a later one)
+    for (int r = tid; r < n; r += T) {
+        const int l = r & 31, r0 = r - l;
+        const float4 mine = edge[r];
+        const float am = area[r];
+        unsigned bits = 0;
+#pragma unroll 8
+        for (int q = 0; q < 31; ++q)
+            if (q < l && overlaps(edge[r0 + q], area[r0 + q], mine, am, iou_thr)) bits |= 1u << q;
+        pre[r] = bits;
+    }
+    __syncthreads();
+    int r0 = 0;
+    for (;;) {
+        if (tid < 32) {
+            // settle blocks until one keeps a box (or the list ends)
+            unsigned kept = 0;
+            while (r0 < n) {
+                const int r = r0 + lane;
+                const bool alive = r < n && !supp[r];
+                const unsigned am = __ballot_sync(0xffffffffu, alive);
+                const unsigned pb = r < n ? pre[r] : 0u;
+                kept = 0;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const unsigned pq = __shfl_sync(0xffffffffu, pb, q);
+                    if (((am >> q) & 1u) && !(pq & kept)) kept |= 1u << q;
+                }
+                if (r < n) supp[r] = ((kept >> lane) & 1u) ? 0 : 1;
+                if (kept) break;
+                r0 += 32;
+            }
+            if (lane == 0) {
+                s_kept = kept;
+                s_r0 = r0;
+            }
+        }
+        __syncthreads();
+        const unsigned kept = s_kept;
+        r0 = s_r0;
+        if (r0 >= n) break;
+        for (int q = r0 + 32 + tid; q < n; q += T) {
+            if (supp[q]) continue;
+            const float4 eq = edge[q];
+            const float aq = area[q];
+            bool drop = false;
+            for (unsigned mm = kept; mm; mm &= mm - 1) {
+                const int b = r0 + __ffs(mm) - 1;
+                drop |= overlaps(edge[b], area[b], eq, aq, iou_thr);
+            }
+            if (drop) supp[q] = 1;
+        }
+        r0 += 32;
         __syncthreads();
     }
     // kept ones to the front of the list, in rank order (warp 0, ballots)
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+    if (tid < 32) {
         int out = 0;
-        for (int r0 = 0; r0 < n; r0 += 32) {
-            const int r = r0 + lane;
+        for (int b0 = 0; b0 < n; b0 += 32) {
+            const int r = b0 + lane;
             const bool keep = r < n && !supp[r];
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             if (keep) {
@@ -265,56 +424,93 @@ __global__ void __launch_bounds__(kNmsThreads) region_nms_kernel(int C, int maxc
             }
             out += __popc(m);
         }
-        if (lane == 0) cnt[fc] = out;
+        if (lane == 0) fcnt[c] = out;
+        __threadfence();   // the list and count before this class is counted done
     }
-}
-
-// One warp per frame: the classes' kept boxes, class by class, cut at max_det.
-__global__ void region_compact_kernel(int batch, int C, int maxc, int max_det, const int* __restrict__ cnt,
-                                      const RegionCand* __restrict__ cand, int* counts, net_detection* det) {
-    const int f = blockIdx.x;
-    if (f >= batch) return;
-    const int lane = threadIdx.x;
-    int base = 0;
-    for (int c = 0; c < C; ++c) {
-        const int k = cnt[f * C + c];
-        const RegionCand* L = cand + ((long long)f * C + c) * maxc;
-        for (int q = lane; q < k && base + q < max_det; q += 32) {
-            net_detection d;
-            d.x = L[q].x;
-            d.y = L[q].y;
-            d.w = L[q].w;
-            d.h = L[q].h;
-            d.score = L[q].score;
-            d.cls = c;
-            d.id = L[q].id;
-            d.pad = 0;
-            det[(long long)f * max_det + base + q] = d;
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&fcnt[C], 1) == C - 1;
+    __syncthreads();
+    if (!s_last) return;
+    // the frame's last class: its detections are the classes' kept boxes,
+    // class by class, cut at max_det; its count is the number before the cut
+    __threadfence();
+    if (tid < 32) {
+        int base = 0;
+        for (int c0 = 0; c0 < C; c0 += 32) {
+            const int k = c0 + lane < C ? __ldcg(&fcnt[c0 + lane]) : 0;
+            int incl = k;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (c0 + lane < C) prefix[c0 + lane] = base + incl - k;
+            base += __shfl_sync(0xffffffffu, incl, 31);
         }
-        base += k;
+        if (lane == 0) {
+            prefix[C] = base;
+            counts[f] = base;
+        }
     }
-    if (lane == 0) counts[f] = base;
+    __syncthreads();
+    const int ncut = min(prefix[C], max_det);
+    const RegionCand* F = cand + (long long)f * C * maxc;
+    for (int o = tid; o < ncut; o += T) {
+        int lo = 0, hi = C - 1;   // the class c with prefix[c] <= o < prefix[c + 1]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= o) lo = mid;
+            else hi = mid - 1;
+        }
+        const RegionCand* e = F + (long long)lo * maxc + (o - prefix[lo]);
+        net_detection d;
+        d.x = __ldcg(&e->x);
+        d.y = __ldcg(&e->y);
+        d.w = __ldcg(&e->w);
+        d.h = __ldcg(&e->h);
+        d.score = __ldcg(&e->score);
+        d.cls = lo;
+        d.id = __ldcg(&e->id);
+        d.pad = 0;
+        det[(long long)f * max_det + o] = d;
+    }
 }
 
-size_t nms_smem() { return (size_t)kMaxCand * 33; }
+int nms_logp(int maxc) {
+    int lp = 8;
+    while ((1 << lp) < maxc) ++lp;
+    return lp;
+}
+
+template <int LOGP>
+cudaError_t launch_nms(int batch, int C, int maxc, float iou_thr, int max_det, int* cnt, RegionCand* cand,
+                       int* counts, net_detection* det, cudaStream_t st) {
+    const size_t smem = nms_layout(1 << LOGP, C).total;
+    cudaError_t e = cudaFuncSetAttribute(region_nms_kernel<LOGP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    region_nms_kernel<LOGP><<<batch * C, nms_threads(LOGP), smem, st>>>(C, maxc, iou_thr, max_det, cnt, cand,
+                                                                         counts, det);
+    return cudaSuccess;
+}
 
 cudaError_t enqueue_region(const RegionState& R, const float* d_map, int batch, int GH, int GW, int* d_counts,
                            net_detection* d_det, cudaStream_t st, uint64_t* launches) {
     const int A = R.r.n_anchors, C = R.r.n_classes;
-    cudaError_t e = cudaMemsetAsync(R.d_cnt, 0, sizeof(int) * (size_t)batch * C, st);
+    cudaError_t e = cudaMemsetAsync(R.d_cnt, 0, sizeof(int) * (size_t)batch * (C + 1), st);
     if (e != cudaSuccess) return e;
     const long long total = (long long)batch * A * GH * GW;
     region_decode_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
         d_map, batch, A, C, GH, GW, R.d_anchor, R.r.score_thresh, R.maxc, R.d_cnt, R.d_cand);
-    static bool attr = false;
-    if (!attr) {
-        e = cudaFuncSetAttribute(region_nms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nms_smem());
-        if (e != cudaSuccess) return e;
-        attr = true;
+    switch (nms_logp(R.maxc)) {
+        case 8: e = launch_nms<8>(batch, C, R.maxc, R.r.nms_iou, R.r.max_det, R.d_cnt, R.d_cand, d_counts, d_det, st); break;
+        case 9: e = launch_nms<9>(batch, C, R.maxc, R.r.nms_iou, R.r.max_det, R.d_cnt, R.d_cand, d_counts, d_det, st); break;
+        case 10: e = launch_nms<10>(batch, C, R.maxc, R.r.nms_iou, R.r.max_det, R.d_cnt, R.d_cand, d_counts, d_det, st); break;
+        case 11: e = launch_nms<11>(batch, C, R.maxc, R.r.nms_iou, R.r.max_det, R.d_cnt, R.d_cand, d_counts, d_det, st); break;
+        default: e = launch_nms<12>(batch, C, R.maxc, R.r.nms_iou, R.r.max_det, R.d_cnt, R.d_cand, d_counts, d_det, st); break;
     }
-    region_nms_kernel<<<batch * C, kNmsThreads, nms_smem(), st>>>(C, R.maxc, R.r.nms_iou, R.d_cnt, R.d_cand);
-    region_compact_kernel<<<batch, 32, 0, st>>>(batch, C, R.maxc, R.r.max_det, R.d_cnt, R.d_cand, d_counts, d_det);
-    *launches += 3;
+    if (e != cudaSuccess) return e;
+    *launches += 2;
     return cudaGetLastError();
 }
 
@@ -358,7 +554,7 @@ extern "C" net_status net_set_region(net_t* n, const net_region* r) {
     R->maxc = (int)maxc;
     R->max_batch = n->max_batch;
     R->out_bytes = counts_block(n->max_batch) + (size_t)n->max_batch * r->max_det * sizeof(net_detection);
-    CK(cudaMalloc(&R->d_cnt, sizeof(int) * (size_t)n->max_batch * C));
+    CK(cudaMalloc(&R->d_cnt, sizeof(int) * (size_t)n->max_batch * (C + 1)));
     CK(cudaMalloc(&R->d_cand, sizeof(RegionCand) * (size_t)n->max_batch * C * R->maxc));
     CK(cudaMalloc(&R->d_anchor, sizeof(float) * 2 * A));
     CK(cudaMalloc(&R->d_out, R->out_bytes));

@@ -20,18 +20,22 @@
 //    (bytes in flight, not instructions, bound a streaming kernel; the ring
 //    takes no registers), the left and right neighbours coming from the
 //    adjacent lanes by shuffles; sixteen 128-thread blocks per SM.
-//    Each block writes its largest change to a partial slot.
-//  * jacobi_finish_kernel (one block): reduces the partials and applies the
+//    Each block writes its largest change to a partial slot; the last block
+//    to finish (an arrival counter) reduces the partials and applies the
 //    stopping rule on the device: sweeps += 1, done when the change is at or
-//    below tol or sweeps reached iter_max.  Both kernels return at once when
+//    below tol or sweeps reached iter_max.  The kernel returns at once when
 //    done is set, so the host can queue sweeps ahead and poll the 16-byte
 //    state only every few of them.
+//  * Strips are sized so that the tiles fill the resident blocks evenly
+//    (one tile a block on a large grid: 54-row strips at 8192 x 8192), so
+//    no block runs a second round alone.
 //  * The two buffers alternate by the parity of the sweep count, so the
 //    result is in buffer (sweeps & 1).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <utility>
@@ -48,7 +52,7 @@ struct JState {
     int sweeps;
     int done;
     float change;
-    int pad;
+    unsigned arrived;   // blocks of the running sweep that are done (the last resets it)
 };
 
 constexpr int kThreads = 128;   // 512 columns per tile row
@@ -72,8 +76,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // SM) take no registers; each thread reads only its own slots, so no block
 // barrier is needed, only the wait for its own oldest copy group.
 __global__ void __launch_bounds__(kThreads, 16) jacobi_sweep_kernel(float* b0, float* b1, int ny, int nx, int P,
-                                                                     const JState* __restrict__ st, float* partial,
-                                                                     int col_blocks, int strips, int rows) {
+                                                                     JState* st, float* partial, float tol,
+                                                                     int iter_max, int col_blocks, int strips,
+                                                                     int rows) {
     __shared__ float4 ring[kAhead][kThreads];
     if (st->done) return;
     const int k = st->sweeps;
@@ -139,30 +144,34 @@ __global__ void __launch_bounds__(kThreads, 16) jacobi_sweep_kernel(float* b0, f
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
     __shared__ float wmax[kThreads / 32];
+    __shared__ int last;
     if (lane == 0) wmax[threadIdx.x >> 5] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
         float m = wmax[0];
         for (int w = 1; w < kThreads / 32; ++w) m = fmaxf(m, wmax[w]);
         partial[blockIdx.x] = m;
+        __threadfence();   // the partial before the arrival
+        // every other block read the state at its start before arriving, so
+        // the last one may update it
+        last = atomicAdd(&st->arrived, 1u) == gridDim.x - 1;
     }
-}
-
-__global__ void jacobi_finish_kernel(const float* __restrict__ partial, int n, JState* st, float tol, int iter_max) {
-    if (st->done) return;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
     float m = 0.f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, partial[i]);
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kThreads) m = fmaxf(m, __ldcg(&partial[i]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    __shared__ float wmax[32];
-    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (lane == 0) wmax[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
-        m = fmaxf(m, wmax[0]);
+        for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, wmax[w]);
         st->change = m;
-        st->sweeps += 1;
-        if (m <= tol || st->sweeps >= iter_max) st->done = 1;
+        st->sweeps = k + 1;
+        st->arrived = 0;
+        if (m <= tol || k + 1 >= iter_max) st->done = 1;
     }
 }
 
@@ -202,8 +211,8 @@ static net_status jacobi_graph(net_jacobi* j, float tol, int iter_max, cudaGraph
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < kChunk && e == cudaSuccess; ++s) {
         jacobi_sweep_kernel<<<j->grid, kThreads, 0, j->stream>>>(j->buf[0], j->buf[1], j->ny, j->nx, j->P, j->d_state,
-                                                                 j->partial, j->col_blocks, j->strips, j->rows);
-        jacobi_finish_kernel<<<1, 1024, 0, j->stream>>>(j->partial, j->grid, j->d_state, tol, iter_max);
+                                                                 j->partial, tol, iter_max, j->col_blocks, j->strips,
+                                                                 j->rows);
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaStreamEndCapture(j->stream, &g);
@@ -248,10 +257,14 @@ extern "C" net_status net_jacobi_create(int ny, int nx, int device, void* cuda_s
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     // persistent: sixteen 128-thread blocks per SM (all resident: 32 registers
-    // a thread, 12 KB of shared memory a block) taking strips of 32 rows
-    // round robin (measured faster than one longer strip per block)
+    // a thread, 12 KB of shared memory a block); the strips split the
+    // interior rows evenly over `waves` tiles per block, at least 8 rows a
+    // strip (NET_JACOBI_ROWS overrides the strip height)
     j->col_blocks = cdiv(j->P, 4 * kThreads);
-    j->rows = 32;
+    const int slots = std::max(1, 16 * sms / j->col_blocks), waves = 1;
+    j->rows = std::max(8, cdiv(ny - 2, slots * waves));
+    if (const char* v = getenv("NET_JACOBI_ROWS"))
+        if (atoi(v) > 0) j->rows = atoi(v);
     j->strips = cdiv(ny - 2, j->rows);
     j->grid = std::max(1, std::min(j->col_blocks * j->strips, 16 * sms));
     const size_t bytes = (size_t)ny * j->P * sizeof(float);
@@ -294,7 +307,7 @@ static net_status jacobi_run(net_jacobi* j, float tol, int iter_max, int* sweeps
                 st = fail(NET_E_CUDA, "jacobi chunk: %s", cudaGetErrorString(e));
                 break;
             }
-            j->launches += 2 * kChunk;
+            j->launches += kChunk;
             if (c > 0) {
                 e = cudaEventSynchronize(ev[(c - 1) & 1]);
                 if (e != cudaSuccess) {

@@ -78,14 +78,30 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// As mbar_try, acquiring at cluster scope: for barriers that threads of the
+// peer CTA of a pair arrive on.
+__device__ __forceinline__ bool mbar_try_cl(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "n"(1000000)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait; false (and the error code recorded) when `lim` clock64
-// cycles passed or another role already aborted.
+// cycles passed or another role already aborted.  CL: cluster scope.
+template <bool CL = false>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
                                           int* err, int code, long long lim) {
-    if (mbar_try(bar, parity)) return true;
+    auto tryw = [&] { return CL ? mbar_try_cl(bar, parity) : mbar_try(bar, parity); };
+    if (tryw()) return true;
     const long long t0 = clock64();
     while (true) {
-        if (mbar_try(bar, parity)) return true;
+        if (tryw()) return true;
         if (*abort_flag) return false;
         if (clock64() - t0 > lim) {
             *abort_flag = 1;
@@ -107,6 +123,47 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const void* tmap, int 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int c0, int c1, uint32_t bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+// ---- CTA pairs (cta_group::2).  A 2-CTA cluster computes an M = 256 tile:
+// the even CTA issues each MMA once for both, every CTA supplying its own
+// 128 A rows and half of the B columns from its own shared memory, at the
+// same offsets, and receiving its 128 accumulator rows in its own tensor
+// memory.  Each CTA loads only its own shared memory; a load's completion is
+// counted on the even CTA's barrier, an address in the cluster window.
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// cluster-window address of the shared variable at `local` in CTA `rank`
+__device__ __forceinline__ uint32_t cl_addr(uint32_t local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_cl(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// loads into this CTA's shared memory whose completion counts on the barrier
+// at cluster address `bar` (this CTA's or its peer's)
+__device__ __forceinline__ void tma_load_4d_pair(uint32_t dst, const void* tmap, int c0, int c1, int c2, int c3,
+                                                 uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const void* tmap, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
         "l"(tmap), "r"(c0), "r"(c1), "r"(bar)
         : "memory");
@@ -140,32 +197,52 @@ constexpr int kPairSlots = 10;
 // Instruction descriptor: D = F32, A/B = BF16 (kind::f16) or E4M3
 // (kind::f8f6f4), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 template <int DT>
-__device__ __forceinline__ uint32_t instr_desc(int n) {
+__device__ __forceinline__ uint32_t instr_desc(int n, int m = 128) {
     const uint32_t ab = DT == DT_BF16 ? 1u : 0u;
-    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-template <int DT>
+// CG = 1: one CTA; CG = 2: the CTA pair (issued by its even CTA)
+template <int DT, int CG = 1>
 __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                     uint32_t accumulate) {
-    if (DT == DT_BF16) {
+    if (DT == DT_BF16 && CG == 1) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
             : "memory");
-    } else {
+    } else if (DT == DT_BF16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else if (CG == 1) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
             : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
     }
 }
 
+// Arrives on `bar` once every MMA this thread issued has completed.  CG = 2:
+// `bar` is a cluster-window address (this CTA's barrier or its peer's).
+template <int CG = 1>
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
+    if (CG == 1)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                     : "memory");
+    else
+        asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                     : "memory");
 }
 
 __device__ __forceinline__ void fence_before() {
@@ -240,15 +317,30 @@ struct Smem {
 // With MB = 2 a CTA has at most 80 registers a thread (the epilogue drains
 // 16 columns at a time), half the shared memory and at most 256 TMEM
 // columns, so that two CTAs always fit on an SM at once.
-template <int BN, int DT, int MB>
+//
+// CG = 2: CTA pairs (2-CTA clusters, one CTA an SM).  A work item is an M =
+// 256 tile: M tiles 2u and 2u + 1 of pair item u, one a CTA (the second
+// absent when the M tile count is odd: that CTA loads a duplicate and stores
+// nothing).  Each CTA streams its A box and its half of the N tile's B box
+// (BN / 2 rows) into its own ring; the even CTA's single MMA issuer waits
+// for both halves on its own full barrier, issues cta_group::2 MMAs and
+// commits to the stage's empty barrier and the accumulator barrier of both
+// CTAs; each CTA's epilogue drains its own 128 accumulator rows and hands
+// the buffer back on the even CTA's barrier.  Per SM a K step then moves
+// 128 rows of A and BN / 2 of B instead of 128 + BN, so more stages fit and
+// each byte in flight feeds twice the MMA work.  No resident weights, tap
+// merging, tap pairs or K-alternating issuers in this mode.
+template <int BN, int DT, int MB, int CG>
 __global__ void __launch_bounds__(tc::THREADS, MB)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     using namespace tc;
     static_assert(MB == 1 || (MB == 2 && BN <= 128), "two CTAs per SM: N tiles of at most 128 columns");
+    static_assert(CG == 1 || (CG == 2 && MB == 1 && BN >= 128), "CTA pairs: one CTA an SM, N tiles of 128 or 256");
+    constexpr bool C2 = CG == 2;
     // accumulator buffers in TMEM (512 columns an SM): four up to BN = 128,
     // so the MMAs of the next tiles never wait for an epilogue's round trip;
-    // with two CTAs an SM, 256 columns each
-    constexpr int NBUF = MB == 2 ? 256 / BN : (BN <= 128 ? 4 : 2);
+    // with two CTAs an SM, 256 columns each; CTA pairs allocate 256 columns
+    constexpr int NBUF = C2 ? 256 / BN : MB == 2 ? 256 / BN : (BN <= 128 ? 4 : 2);
     constexpr int NBUF_LOG = NBUF == 4 ? 2 : NBUF == 2 ? 1 : 0;
     constexpr int TMEM_COLS = NBUF * BN;
     constexpr int CW = MB == 2 ? 16 : 32;   // epilogue columns per TMEM load
@@ -271,13 +363,19 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     const int KK = a.k * a.k;
     const int nkb = KK * a.chunks;                // weight boxes (tap, chunk) per tile
     const int nk = a.tapm ? a.chunks : nkb;       // pipeline steps per tile
-    // work items: (m-tile, n-tile, K slice), taken round robin by the CTAs
-    const int worker = blockIdx.x, nworkers = gridDim.x;
-    const int total = a.m_tiles * a.n_tiles * a.ksplit;
+    // CTA pairs: this CTA's rank (0 issues the MMAs)
+    const uint32_t rank = C2 ? cluster_rank() : 0u;
+    // work items: (m unit, n-tile, K slice), taken round robin by the CTAs
+    // (CTA pairs: by the pairs; an m unit is then two M tiles)
+    const int worker = C2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int nworkers = C2 ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    const int m_units = C2 ? (a.m_tiles + 1) >> 1 : a.m_tiles;
+    const int total = m_units * a.n_tiles * a.ksplit;
     const int pad = a.k >> 1;
-    // A bytes per stage: one 128-row box, or three (TH + 2)-row boxes (tapm)
+    // A bytes per stage: one 128-row box, or three (TH + 2)-row boxes (tapm);
+    // B: the N tile's box, or (CTA pairs) this CTA's half of it
     const uint32_t a_box = a.tapm ? (uint32_t)(a.TH + 2) * a.TW * a.chb : 128u * a.chb;
-    const uint32_t a_bytes = a.tapm ? 3u * a_box : a_box, b_bytes = (uint32_t)BN * a.chb;
+    const uint32_t a_bytes = a.tapm ? 3u * a_box : a_box, b_bytes = (uint32_t)(C2 ? BN / 2 : BN) * a.chb;
 
     if (threadIdx.x == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
@@ -289,23 +387,38 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         for (int b = 0; b < NBUF; ++b) {
             tc::mbar_init(smem_u32(&sm->accf[b]), 1);
             // the 4 warps of the warpgroup that drains buffer b; in K-alternating
-            // mode both warpgroups drain every tile (half of its columns each)
-            tc::mbar_init(smem_u32(&sm->acce[b]), a.kalt ? 8 : 4);
+            // mode both warpgroups drain every tile (half of its columns each);
+            // CTA pairs: the 8 epilogue warps of both CTAs (on the even CTA's)
+            tc::mbar_init(smem_u32(&sm->acce[b]), C2 ? 16 : a.kalt ? 8 : 4);
         }
-        tc::mbar_init(smem_u32(&sm->done), 2);   // one commit from each MMA issuer
+        // one commit from each MMA issuer (CTA pairs: the even CTA's issuer)
+        tc::mbar_init(smem_u32(&sm->done), C2 ? 1 : 2);
         tc::mbar_init(smem_u32(&sm->bres), 1);
         sm->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&sm->tmem)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        // CTA pairs: one warp of each CTA allocates, collectively, the same
+        // columns in both CTAs' tensor memory
+        if constexpr (C2) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&sm->tmem)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(&sm->tmem)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc::fence_before();
     __syncthreads();
+    // CTA pairs: both CTAs' barriers are initialised before either arrives on
+    // or loads toward the other's
+    if constexpr (C2) cluster_sync();
     tc::fence_after();
     const uint32_t tmem_base = sm->tmem;
     volatile int* abort_flag = &sm->abort;
@@ -391,7 +504,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             auto setup = [&] {   // coordinates of the lane's current tile
                 const int mn = a.ksplit > 1 ? fdiv(tile, a.fd_ksplit) : tile;
                 const int mq = fdiv(mn, a.fd_ntiles);
-                const int mt = mq;
+                // CTA pairs: M tile 2 mq + rank (an absent second tile loads a
+                // duplicate of the last one, which its epilogue does not store)
+                const int mt = C2 ? min(2 * mq + (int)rank, a.m_tiles - 1) : mq;
                 nt = mn - mq * a.n_tiles;
                 towner = t & 1;
                 if (!P1) {
@@ -456,12 +571,22 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             // kernel: its stage is free, so it is armed for the whole step and
             // the box is issued before the dependency wait
             bool pre_b = false;
+            // CTA pairs: stages are armed on the even CTA only (for both CTAs'
+            // bytes), and every load completes on the even CTA's barrier
+            const int b_row0 = C2 ? (int)rank * (BN / 2) : 0;   // this CTA's first row of the B box
+            const uint32_t st_tx = C2 ? 2u * (a_bytes + b_bytes) : a_bytes + b_bytes;
             if (!a.bres && tile < total) {
-                const int owner = a.kalt ? ((ks - ks0) & 1) : towner;
+                const int owner = C2 ? 0 : a.kalt ? ((ks - ks0) & 1) : towner;
                 const uint32_t fb = smem_u32(&sm->full[owner][ps]);
-                tc::mbar_expect_tx(fb, a_bytes + b_bytes);
-                tc::tma_load_2d(smem_u32(sRing + (size_t)ps * st_bytes + a_bytes), &tmB,
-                                (kh * a.k + kw) * a.Cp + ch * a.cpc, nt * BN, fb);
+                if constexpr (C2) {
+                    if (rank == 0) tc::mbar_expect_tx(fb, st_tx);
+                    tc::tma_load_2d_pair(smem_u32(sRing + (size_t)ps * st_bytes + a_bytes), &tmB,
+                                         (kh * a.k + kw) * a.Cp + ch * a.cpc, nt * BN + b_row0, cl_addr(fb, 0));
+                } else {
+                    tc::mbar_expect_tx(fb, st_tx);
+                    tc::tma_load_2d(smem_u32(sRing + (size_t)ps * st_bytes + a_bytes), &tmB,
+                                    (kh * a.k + kw) * a.Cp + ch * a.cpc, nt * BN, fb);
+                }
                 pre_b = true;
             }
             pdl_wait();
@@ -490,26 +615,35 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     const int s = ps;
                     // the issuer that consumes this K step: the tile's, or in
                     // K-alternating mode the K step's parity within the tile
-                    const int owner = a.kalt ? ((ks - ks0) & 1) : towner;
+                    const int owner = C2 ? 0 : a.kalt ? ((ks - ks0) & 1) : towner;
                     const uint32_t fb = smem_u32(&sm->full[owner][s]);
                     if (owner) pph1 ^= 1u << s;
                     else pph0 ^= 1u << s;
                     last_owner = (last_owner & ~(1u << s)) | ((uint32_t)owner << s);
                     issued |= 1u << s;
-                    if (!pre_b) tc::mbar_expect_tx(fb, a.bres ? a_bytes : a_bytes + b_bytes);
                     const int c0 = ch * a.cpc;
                     const int kcol = (kh * a.k + kw) * a.Cp + c0;   // K column of the weights
                     uint8_t* stg = sRing + (size_t)s * st_bytes;
-                    if (a.tapm) {   // step = chunk ks of all nine taps: one box per tap column
-                        for (int dx = 0; dx < 3; ++dx)
-                            tc::tma_load_4d(smem_u32(stg + dx * a_box), &P->tmA, ks * a.cpc, x0 + dx, y0, img, fb);
+                    if constexpr (C2) {
+                        if (!pre_b && rank == 0) tc::mbar_expect_tx(fb, st_tx);
+                        const uint32_t fbc = cl_addr(fb, 0);
+                        tc::tma_load_4d_pair(smem_u32(stg), &P->tmA, c0, x0 + kw, y0 + kh, img, fbc);
+                        if (pre_b) pre_b = false;
+                        else tc::tma_load_2d_pair(smem_u32(stg + a_bytes), &tmB, kcol, nt * BN + b_row0, fbc);
                     } else {
-                        tc::tma_load_4d(smem_u32(stg), &P->tmA, c0, x0 + kw, y0 + kh, img, fb);
-                    }
-                    if (a.bres || pre_b) {
-                        pre_b = false;
-                    } else {
-                        tc::tma_load_2d(smem_u32(stg + a_bytes), &tmB, kcol, nt * BN, fb);
+                        if (!pre_b) tc::mbar_expect_tx(fb, a.bres ? a_bytes : st_tx);
+                        if (a.tapm) {   // step = chunk ks of all nine taps: one box per tap column
+                            for (int dx = 0; dx < 3; ++dx)
+                                tc::tma_load_4d(smem_u32(stg + dx * a_box), &P->tmA, ks * a.cpc, x0 + dx, y0, img,
+                                                fb);
+                        } else {
+                            tc::tma_load_4d(smem_u32(stg), &P->tmA, c0, x0 + kw, y0 + kh, img, fb);
+                        }
+                        if (a.bres || pre_b) {
+                            pre_b = false;
+                        } else {
+                            tc::tma_load_2d(smem_u32(stg + a_bytes), &tmB, kcol, nt * BN, fb);
+                        }
                     }
                     it += S2;
                     ps += S2;
@@ -528,8 +662,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             }
             // drain: every copy issued must have landed before smem goes away.
             // Earlier uses of a stage were consumed before it was refilled, so
-            // only the last use of each stage can still be in flight.
-            for (int st = 0; st < nst; ++st) {
+            // only the last use of each stage can still be in flight.  CTA
+            // pairs: the even CTA's barriers count both CTAs' copies, so the odd
+            // CTA leaves the drain to it (the kernel's last cluster barrier
+            // orders its exit after the even CTA's drain).
+            for (int st = 0; st < nst && !(C2 && rank != 0); ++st) {
                 if (!((issued >> st) & 1u)) continue;
                 const int o = (int)((last_owner >> st) & 1u);
                 const uint32_t bar = smem_u32(&sm->full[o][st]);
@@ -551,8 +688,24 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         // take alternate K steps of it instead (K-alternating mode), each into
         // its own accumulator of the tile's pair; the epilogue adds the two.
         const int mid = warp == 1 ? 0 : 1;
-        if (lane == 0) {
-            const uint32_t idesc = tc::instr_desc<DT>(BN);
+        // CTA pairs: the even CTA's first issuer alone issues for both CTAs;
+        // it commits to a barrier of both (this CTA's, then the odd one's)
+        auto commit = [&](uint64_t* bar) {
+            if constexpr (C2) {
+                tc::mma_commit<2>(cl_addr(smem_u32(bar), 0));
+                tc::mma_commit<2>(cl_addr(smem_u32(bar), 1));
+            } else {
+                tc::mma_commit(smem_u32(bar));
+            }
+        };
+        if (C2 && lane == 0 && mid == 0 && rank != 0) {
+            // the odd CTA: its tensor memory and shared memory stay allocated
+            // until every MMA of the even CTA's issuer has completed
+            const long long t0 = clock64();
+            while (!tc::mbar_try(smem_u32(&sm->done), 0) && clock64() - t0 < WAIT_LIMIT) {
+            }
+        } else if (lane == 0 && !(C2 && mid != 0)) {
+            const uint32_t idesc = tc::instr_desc<DT>(BN, C2 ? 256 : 128);
             int it = 0, tcount = 0;
             uint32_t fph = 0u;   // bit s = phase parity of this issuer's next use of stage s
             bool ok = true;
@@ -567,7 +720,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     ks0 = fdiv(nk * z, a.fd_ksplit);
                     ks1 = fdiv(nk * (z + 1), a.fd_ksplit);
                 }
-                if (!a.kalt && (tcount & 1) != mid) {   // the other issuer's tile: its stages are skipped
+                if (!C2 && !a.kalt && (tcount & 1) != mid) {   // the other issuer's tile: its stages are skipped
                     it += ks1 - ks0;
                     continue;
                 }
@@ -576,7 +729,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 const int slot = tcount & ((1 << nsl_log) - 1);
                 const int b = a.kalt ? 2 * slot + mid : slot;
                 const uint32_t aph = (uint32_t)(tcount >> nsl_log) & 1u;
-                if (!tc::mbar_wait(smem_u32(&sm->acce[b]), aph ^ 1u, abort_flag, a.err, 2, lim)) break;
+                if (!tc::mbar_wait<C2>(smem_u32(&sm->acce[b]), aph ^ 1u, abort_flag, a.err, 2, lim)) break;
                 tc::fence_after();
                 const uint32_t dtm = tmem_base + (uint32_t)(b * BN);
                 int ms = it - fdiv(it, a.fd_nst) * nst;   // stage of this tile's first K step
@@ -608,7 +761,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                             const uint64_t ad = tc::smem_desc_plain(smem_u32(stg + o0), o1 - o0, 128u);
                             const uint64_t bd =
                                 tc::smem_desc_plain(smem_u32(sBres + (size_t)s0 * b_bytes), b_bytes, 128u);
-                            tc::mma<DT>(dtm, ad, bd, idesc, (!first || j != 0) ? 1u : 0u);
+                            tc::mma<DT, CG>(dtm, ad, bd, idesc, (!first || j != 0) ? 1u : 0u);
                         }
                         first = false;
                     } else if (a.tapm) {
@@ -620,7 +773,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                                 const uint64_t bd = tc::smem_desc(
                                     smem_u32(sBres + (size_t)((dy * 3 + dx) * a.chunks + ks) * b_bytes), a.chb);
                                 for (int j = 0; j < nmma; ++j)
-                                    tc::mma<DT>(dtm, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc,
+                                    tc::mma<DT, CG>(dtm, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc,
                                                 (!first || j != 0) ? 1u : 0u);
                                 first = false;
                             }
@@ -629,16 +782,16 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         const uint64_t bd =
                             tc::smem_desc(smem_u32(a.bres ? sBres + (size_t)ks * b_bytes : stg + a_bytes), a.chb);
                         for (int j = 0; j < nmma; ++j)
-                            tc::mma<DT>(dtm, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc,
-                                        (!first || j != 0) ? 1u : 0u);
+                            tc::mma<DT, CG>(dtm, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc,
+                                            (!first || j != 0) ? 1u : 0u);
                         first = false;
                     }
-                    tc::mma_commit(smem_u32(&sm->empty[s]));
+                    commit(&sm->empty[s]);
                 }
-                if (ok) tc::mma_commit(smem_u32(&sm->accf[b]));
+                if (ok) commit(&sm->accf[b]);
             }
             // every MMA issued has finished before TMEM and smem are released
-            tc::mma_commit(smem_u32(&sm->done));
+            commit(&sm->done);
             const long long t0 = clock64();
             while (!tc::mbar_try(smem_u32(&sm->done), 0) && clock64() - t0 < WAIT_LIMIT) {
             }
@@ -654,8 +807,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         // columns of a tile this warp drains: all, or in K-alternating mode
         // (one tile per CTA) half of them, so the last tile's epilogue, which
         // nothing overlaps, runs on both warpgroups
-        const int half = a.kalt ? grp : 0;
-        const int HC = a.kalt ? BN / 2 : BN;
+        // (CTA pairs: both warpgroups on every tile too; one issuer, one buffer
+        // sequence)
+        const int half = (a.kalt || C2) ? grp : 0;
+        const int HC = (a.kalt || C2) ? BN / 2 : BN;
         const int row = q * 32 + lane;          // pixel index in the tile
         const int py = row / a.TW, px = row % a.TW;
         const bool pool = a.ep.pool == POOL_S2;
@@ -681,19 +836,19 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         int tcount = 0;
         bool have_p = false;   // problem fields loaded (single-problem launches read them once)
         for (int tile = worker; tile < total; tile += nworkers, ++tcount) {
-            if (!a.kalt && (tcount & 1) != grp) continue;
+            if (!C2 && !a.kalt && (tcount & 1) != grp) continue;
             // the tile's accumulator (or pair of them in K-alternating mode)
             const int nsl_log = a.kalt ? NBUF_LOG - 1 : NBUF_LOG;
             const int slot = tcount & ((1 << nsl_log) - 1);
             const int b = a.kalt ? 2 * slot : slot;
             const uint32_t aph = (uint32_t)(tcount >> nsl_log) & 1u;
-            if (!tc::mbar_wait(smem_u32(&sm->accf[b]), aph, abort_flag, a.err, 4, lim)) break;
+            if (!tc::mbar_wait<C2>(smem_u32(&sm->accf[b]), aph, abort_flag, a.err, 4, lim)) break;
             if (a.kalt && !tc::mbar_wait(smem_u32(&sm->accf[b + 1]), aph, abort_flag, a.err, 4, lim)) break;
             tc::fence_after();
             const int mn = a.ksplit > 1 ? fdiv(tile, a.fd_ksplit) : tile;
             const int z = tile - mn * a.ksplit;
             const int mq = fdiv(mn, a.fd_ntiles);
-            const int mt = mq, nt = mn - mq * a.n_tiles;
+            const int mt = C2 ? 2 * mq + (int)rank : mq, nt = mn - mq * a.n_tiles;
             const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * HC);
             // the buffer goes back to the MMA issuer right after its last live
             // column is in registers; the math and stores of that chunk follow
@@ -718,11 +873,19 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) {
-                    tc::mbar_arrive(smem_u32(&sm->acce[b]));
-                    if (a.kalt) tc::mbar_arrive(smem_u32(&sm->acce[b + 1]));
+                    if constexpr (C2) {
+                        tc::mbar_arrive_cl(cl_addr(smem_u32(&sm->acce[b]), 0));   // the even CTA's
+                    } else {
+                        tc::mbar_arrive(smem_u32(&sm->acce[b]));
+                        if (a.kalt) tc::mbar_arrive(smem_u32(&sm->acce[b + 1]));
+                    }
                 }
                 released = true;
             };
+            if (C2 && mt >= a.m_tiles) {   // the absent second tile of an odd count
+                release();
+                continue;
+            }
             if (a.ksplit > 1) {
                 // raw partial sums of this K slice; the reduction applies the
                 // epilogue.  Workspace plane z is tile-major in groups of four
@@ -908,11 +1071,19 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
 
     tc::fence_before();
     __syncthreads();
+    // CTA pairs: neither CTA leaves while the other may still arrive on its
+    // barriers, load into its ring or read its shared memory
+    if constexpr (C2) cluster_sync();
     tc::fence_after();
     __syncwarp();
-    if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
-                     : "memory");
+    if (warp == 1) {
+        if constexpr (C2)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                         : "memory");
+    }
 }
 
 // ----------------------------------------------------------------- host
@@ -985,10 +1156,11 @@ static size_t tc_ctrl_bytes() {
 static size_t tc_avail(int mb) { return (mb == 2 ? kSmemLimit2 : kSmemLimit) - 1024 - tc_ctrl_bytes(); }
 
 // Ring geometry: as many stages of (A box + B box, or A only with resident
-// weights) as fit beside the resident weights and the control block.
-static bool tc_geometry(int BN, int chb, int bres, int nk, int mb, TcArgs* g) {
+// weights) as fit beside the resident weights and the control block.  CTA
+// pairs (cg = 2): a stage holds half of the B box.
+static bool tc_geometry(int BN, int chb, int bres, int nk, int mb, int cg, TcArgs* g) {
     const size_t a_bytes = g->tapm ? 3 * (size_t)(g->TH + 2) * g->TW * chb : 128 * (size_t)chb;
-    const size_t b_bytes = (size_t)BN * chb;
+    const size_t b_bytes = (size_t)(cg == 2 ? BN / 2 : BN) * chb;
     const size_t st = a_bytes + (bres ? 0 : b_bytes);
     const size_t bres_bytes = bres ? (size_t)(g->pair ? tc::kPairSlots : nk) * b_bytes : 0;
     if (tc_avail(mb) < bres_bytes + 2 * st) return false;
@@ -1018,9 +1190,13 @@ bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb, int mb) {
     return ksplit == 1 && (size_t)nk * BN * chb + a_st <= tc_avail(mb);
 }
 
-template <int BN, int DT, int MB>
+template <int BN, int DT, int MB, int CG>
 static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int workers, cudaStream_t st) {
     TcArgs a = a0;
+    // CTA pairs: streamed weights (half a box each), plain stages, one MMA
+    // issuer, an even grid of 2-CTA clusters; no fault injection
+    if (CG == 2 && (a.bres || a.tapm || a.pair || a.kalt || a.withhold || workers % 2 != 0))
+        return cudaErrorInvalidValue;
     // 16-byte chunks (K = 8) only in pair mode, and pair mode only in its one shape
     if ((a.chb == 16) != (a.pair != 0)) return cudaErrorInvalidValue;
     // resident weights: one N tile per CTA, which needs a grid that is a
@@ -1028,7 +1204,7 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     if (a.bres && (a.ksplit != 1 || workers % a.n_tiles != 0)) return cudaErrorInvalidValue;
     if (a.pair && (DT != DT_BF16 || !a.tapm || !a.bres || a.ksplit != 1 || a.k != 3 || a.chunks != 1 || a.kalt))
         return cudaErrorInvalidValue;
-    if (!tc_geometry(BN, a.chb, a.bres, a.k * a.k * a.chunks, MB, &a)) return cudaErrorInvalidValue;
+    if (!tc_geometry(BN, a.chb, a.bres, a.k * a.k * a.chunks, MB, CG, &a)) return cudaErrorInvalidValue;
     if (a.ksplit < 1 || a.n_tiles < 1 || a.chunks < 1 || a.k < 1) return cudaErrorInvalidValue;
     a.fd_ksplit = make_fast_div(a.ksplit);
     a.fd_ntiles = make_fast_div(a.n_tiles);
@@ -1038,7 +1214,7 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     if (a.wait_limit <= 0) a.wait_limit = tc::WAIT_LIMIT;
     const size_t smem = 1024 + (size_t)a.ctrl_off + tc_ctrl_bytes();
     if (smem > (MB == 2 ? kSmemLimit2 : kSmemLimit)) return cudaErrorInvalidValue;
-    auto kern = conv_tc_kernel<BN, DT, MB>;
+    auto kern = conv_tc_kernel<BN, DT, MB, CG>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1051,11 +1227,18 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     cfg.blockDim = dim3(tc::THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     int na = 0;
     if (pdl_enabled()) {
         at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         at[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    if (CG == 2) {
+        at[na].id = cudaLaunchAttributeClusterDimension;
+        at[na].val.clusterDim.x = 2;
+        at[na].val.clusterDim.y = 1;
+        at[na].val.clusterDim.z = 1;
         ++na;
     }
     cfg.attrs = at;
@@ -1063,24 +1246,33 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     return cudaLaunchKernelEx(&cfg, kern, tmB, a);
 }
 
-cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, int mb,
+cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, int mb, int cg,
                            cudaStream_t st) {
+    if (cg == 2) {
+        if (mb != 1) return cudaErrorInvalidValue;
+        if (dt == DT_BF16 && BN == 128) return launch_tc_bn<128, DT_BF16, 1, 2>(tmB, a, workers, st);
+        if (dt == DT_BF16 && BN == 256) return launch_tc_bn<256, DT_BF16, 1, 2>(tmB, a, workers, st);
+        if (dt == DT_FP8 && BN == 128) return launch_tc_bn<128, DT_FP8, 1, 2>(tmB, a, workers, st);
+        if (dt == DT_FP8 && BN == 256) return launch_tc_bn<256, DT_FP8, 1, 2>(tmB, a, workers, st);
+        return cudaErrorInvalidValue;
+    }
+    if (cg != 1) return cudaErrorInvalidValue;
     if (mb == 2) {
-        if (dt == DT_BF16 && BN == 64) return launch_tc_bn<64, DT_BF16, 2>(tmB, a, workers, st);
-        if (dt == DT_BF16 && BN == 128) return launch_tc_bn<128, DT_BF16, 2>(tmB, a, workers, st);
-        if (dt == DT_FP8 && BN == 64) return launch_tc_bn<64, DT_FP8, 2>(tmB, a, workers, st);
-        if (dt == DT_FP8 && BN == 128) return launch_tc_bn<128, DT_FP8, 2>(tmB, a, workers, st);
+        if (dt == DT_BF16 && BN == 64) return launch_tc_bn<64, DT_BF16, 2, 1>(tmB, a, workers, st);
+        if (dt == DT_BF16 && BN == 128) return launch_tc_bn<128, DT_BF16, 2, 1>(tmB, a, workers, st);
+        if (dt == DT_FP8 && BN == 64) return launch_tc_bn<64, DT_FP8, 2, 1>(tmB, a, workers, st);
+        if (dt == DT_FP8 && BN == 128) return launch_tc_bn<128, DT_FP8, 2, 1>(tmB, a, workers, st);
         return cudaErrorInvalidValue;
     }
     if (mb != 1) return cudaErrorInvalidValue;
     if (dt == DT_BF16) {
-        if (BN == 64) return launch_tc_bn<64, DT_BF16, 1>(tmB, a, workers, st);
-        if (BN == 128) return launch_tc_bn<128, DT_BF16, 1>(tmB, a, workers, st);
-        if (BN == 256) return launch_tc_bn<256, DT_BF16, 1>(tmB, a, workers, st);
+        if (BN == 64) return launch_tc_bn<64, DT_BF16, 1, 1>(tmB, a, workers, st);
+        if (BN == 128) return launch_tc_bn<128, DT_BF16, 1, 1>(tmB, a, workers, st);
+        if (BN == 256) return launch_tc_bn<256, DT_BF16, 1, 1>(tmB, a, workers, st);
     } else if (dt == DT_FP8) {
-        if (BN == 64) return launch_tc_bn<64, DT_FP8, 1>(tmB, a, workers, st);
-        if (BN == 128) return launch_tc_bn<128, DT_FP8, 1>(tmB, a, workers, st);
-        if (BN == 256) return launch_tc_bn<256, DT_FP8, 1>(tmB, a, workers, st);
+        if (BN == 64) return launch_tc_bn<64, DT_FP8, 1, 1>(tmB, a, workers, st);
+        if (BN == 128) return launch_tc_bn<128, DT_FP8, 1, 1>(tmB, a, workers, st);
+        if (BN == 256) return launch_tc_bn<256, DT_FP8, 1, 1>(tmB, a, workers, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -199,8 +199,11 @@ bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb, int mb);
 cudaError_t tc_encode_act(CUtensorMap* tm, const void* base, int dt, int n, int H, int W, int Cp, int TW,
                           int TH);
 cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, int KK, int Cp, int BN);
-// workers = persistent CTAs; tmB has box rows BN; mb = CTAs per SM (1, or 2
-// for BN <= 128: half the shared memory and TMEM, 80 registers a thread).
-cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, int mb,
+// workers = persistent CTAs; tmB has box rows BN (cg = 2: BN / 2); mb =
+// CTAs per SM (1, or 2 for BN <= 128: half the shared memory and TMEM, 80
+// registers a thread); cg = 2: CTA pairs (2-CTA clusters, workers even, one
+// M = 256 tile a pair; BN 128 or 256, mb 1, streamed weights, no tap
+// merging and one MMA issuer).
+cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, int mb, int cg,
                            cudaStream_t st);
 }  // namespace dn

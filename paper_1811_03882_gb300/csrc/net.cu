@@ -464,6 +464,15 @@ int dn::tc_mb_forced() {
     return v == 1 || v == 2 ? v : 0;
 }
 
+// CTA pairs for the layers that can take them (NET_TC_PAIR=0: never)
+bool dn::tc_pair_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("NET_TC_PAIR");
+        return e && atoi(e) == 1;
+    }();
+    return on;
+}
+
 bool dn::pdl_enabled() {
     static const bool on = [] {
         const char* e = getenv("NET_PDL");
@@ -601,6 +610,14 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
                 const int steps = r.tapm ? nk / 9 : nk;   // pipeline steps per tile
                 const int items = r.m_tiles * r.n_tiles * r.ksplit;
                 r.kalt = (kalt_on && items <= r.grid && steps / r.ksplit >= 2) ? 1 : 0;
+                // CTA pairs: layers that stream wide weight tiles (N tile of 128
+                // or 256, not resident, one CTA an SM): an M = 256 tile a pair
+                if (tc_pair_enabled() && r.mb == 1 && !r.bres && !r.tapm && !L.pair && r.BN >= 128) {
+                    const int units = cdiv(r.m_tiles, 2) * r.n_tiles * r.ksplit;
+                    r.cg = 2;
+                    r.kalt = 0;
+                    r.grid = 2 * std::max(1, std::min(units, n->num_sms / 2));
+                }
             }
             (void)tiles;
             ConvProblem hp;
@@ -626,9 +643,9 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             if (dump)
                 fprintf(stderr,
                         "plan b%d %dx%d layer %d: tile %dx%d BN %d m_tiles %d n_tiles %d ksplit %d grid %d mb %d "
-                        "bres %d kalt %d tapm %d pair %d\n",
+                        "bres %d kalt %d tapm %d pair %d cg %d\n",
                         batch, h, w, l, r.TW, r.TH, r.BN, r.m_tiles, r.n_tiles, r.ksplit, r.grid, r.mb, r.bres,
-                        r.kalt, r.tapm, L.pair ? 1 : 0);
+                        r.kalt, r.tapm, L.pair ? 1 : 0, r.cg);
         }
         P->runs.push_back(r);
         if (L.d.pool != NET_POOL_2X2S1_SAME) cur ^= 1;
@@ -742,14 +759,21 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.pair = L.pair ? 1 : 0;
                 a.ep = ep;
                 a.err = n->err_dev;
+                int grid = r.grid, cg = r.cg;
                 if (l == n->fault_layer) {
                     // net_inject_device_fault: a ~1 ms bound (clock64 cycles at
-                    // ~2 GHz) and one K step withheld by a producer, once
+                    // ~2 GHz) and one K step withheld by a producer, once (a
+                    // pair layer runs single-CTA for it: same tiles, one issuer)
                     a.wait_limit = 2000000;
                     a.withhold = 1;
                     n->fault_layer = -1;
+                    if (cg == 2) {
+                        cg = 1;
+                        grid = std::max(1, std::min(r.m_tiles * r.n_tiles * r.ksplit, n->num_sms));
+                    }
                 }
-                e = conv_tc_launch(L.tmB[tmb_index(r.BN)], a, r.BN, L.in_dt, r.grid, r.mb, st);
+                e = conv_tc_launch(L.tmB[tmb_index(cg == 2 ? r.BN / 2 : r.BN)], a, r.BN, L.in_dt, grid, r.mb, cg,
+                                   st);
                 if (e == cudaSuccess && r.ksplit > 1) {
                     ++n->pending;
                     SplitReduce sr{n->ws, r.ksplit, r.m_tiles * 128, r.n_tiles * r.BN, r.TW, r.TH,

@@ -67,6 +67,7 @@ struct LayerRun {
     int bres = 0;                  // TC: weights resident in shared memory
     int kalt = 0;                  // TC: both MMA issuers on each tile (one work item per CTA)
     int mb = 1;                    // TC: CTAs per SM (2: short tiles, epilogue-bound)
+    int cg = 1;                    // TC: 2 = CTA pairs (one M = 256 tile across two SMs)
     int nst_cap = 0;               // TC: ring stages at most (0: as many as fit)
     int tapm = 0;                  // TC: ring stages of all nine taps (3x3, resident weights)
     int sbn = 64, sth = 8, stw = 16; // CUDA-core tile
@@ -96,6 +97,8 @@ void tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int n
 // NET_TC_MB=1 or 2 in the environment forces the CTAs per SM of fixed-batch
 // launches (0: chosen per launch); read once per process.
 int tc_mb_forced();
+// NET_TC_PAIR=1: fixed-batch layers that can take CTA pairs use them; read once.
+bool tc_pair_enabled();
 // Index into Layer::tmB of the weight map whose box has BN rows.
 int tmb_index(int BN);
 

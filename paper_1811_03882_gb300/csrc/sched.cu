@@ -237,7 +237,7 @@ static net_status enqueue_uplan(net* n, UPlan* P, int cnt, int* kernels) {
         }
         const bool prof = n->prof && (int)n->prof_ev.size() == 2 * nl;
         if (prof) e = cudaEventRecordWithFlags(n->prof_ev[2 * l], st, cudaEventRecordExternal);
-        if (e == cudaSuccess) e = conv_tc_launch(L.tmB[tmb_index(r.BN)], a, r.BN, L.in_dt, r.grid, r.mb, st);
+        if (e == cudaSuccess) e = conv_tc_launch(L.tmB[tmb_index(r.BN)], a, r.BN, L.in_dt, r.grid, r.mb, 1, st);
         if (e == cudaSuccess && prof) e = cudaEventRecordWithFlags(n->prof_ev[2 * l + 1], st, cudaEventRecordExternal);
         ++k;
         if (e == cudaSuccess && P->d_pool[l]) {

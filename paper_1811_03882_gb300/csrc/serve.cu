@@ -393,7 +393,7 @@ static net_status enqueue_step(net* n, ServeState* S, StepSlot& sl) {
                 ++n->launches;
             }
         } else {
-            SERVE_CK(conv_tc_launch(L.tmB[tmb_index(P.BN)], P.a, P.BN, L.in_dt, P.workers, P.mb, st), "conv");
+            SERVE_CK(conv_tc_launch(L.tmB[tmb_index(P.BN)], P.a, P.BN, L.in_dt, P.workers, P.mb, 1, st), "conv");
             ++n->launches;
         }
         if (P.npool) {

@@ -30,10 +30,10 @@ def _lib():
     oracle.build()
 
 
-def _check_frame(fmap, cnt, dets, thr, nms_thr, max_det):
+def _check_frame(fmap, cnt, dets, thr, nms_thr, max_det, anch=ANCH, C=C):
     """One frame's GPU detections against the oracle decode of the same map."""
-    boxes = region.decode(fmap, ANCH, C)
-    ref_n, ref = region.detect(fmap[None], ANCH, C, thr, nms_thr, 10 ** 6)[0]
+    boxes = region.decode(fmap, anch, C)
+    ref_n, ref = region.detect(fmap[None], anch, C, thr, nms_thr, 10 ** 6)[0]
     got = [(int(d["cls"]), int(d["id"]), float(d["score"]), float(d["x"]), float(d["y"]), float(d["w"]),
             float(d["h"])) for d in dets[:min(cnt, max_det)]]
     # the reported rows: class order, score order within a class (ties by id)
@@ -70,12 +70,12 @@ def _check_frame(fmap, cnt, dets, thr, nms_thr, max_det):
     return cnt, ref_n, len(diff)
 
 
-def _run_maps(maps, thr, nms_thr, max_det):
+def _run_maps(maps, thr, nms_thr, max_det, anch=ANCH, C=C):
     import torch
     n, ch, gh, gw = maps.shape
     spec = synth.NetSpec("head", 8, [synth.Layer(1, ch, False, synth.ACT_LINEAR, synth.POOL_NONE)])
     with make_net(spec, prec="fp32", max_batch=n, max_side=max(gh, gw)) as net:
-        net.set_region(ANCH, C, thr, nms_thr, max_det)
+        net.set_region(anch, C, thr, nms_thr, max_det)
         d_map = torch.from_numpy(maps).cuda()
         d_cnt = torch.full((n,), -1, dtype=torch.int32, device="cuda")
         d_det = torch.zeros(n * max_det * 32, dtype=torch.uint8, device="cuda")
@@ -86,7 +86,10 @@ def _run_maps(maps, thr, nms_thr, max_det):
         return d_cnt.cpu().numpy(), det
 
 
-@pytest.mark.parametrize("thr,nms_thr,gh,gw", [(0.05, 0.45, 13, 13), (0.2, 0.3, 19, 19), (0.01, 0.6, 7, 11)])
+# grids of 245, 385, 845, 1805 and 3920 boxes: every size of the NMS sort
+# (256, 512, 1024, 2048 and 4096 slots)
+@pytest.mark.parametrize("thr,nms_thr,gh,gw", [(0.05, 0.45, 13, 13), (0.2, 0.3, 19, 19), (0.01, 0.6, 7, 11),
+                                              (0.03, 0.5, 7, 7), (0.25, 0.45, 28, 28)])
 def test_detect_random_maps_vs_oracle(thr, nms_thr, gh, gw):
     rng = np.random.default_rng(int(thr * 1000) + gh)
     maps = rng.normal(0, 2, (3, len(ANCH) * (5 + C), gh, gw)).astype(np.float32)
@@ -97,6 +100,19 @@ def test_detect_random_maps_vs_oracle(thr, nms_thr, gh, gw):
         print("frame %d: %d kept (oracle %d), %d near-threshold differences" % (f, n, ref_n, nd))
         tot += n
     assert tot > 10
+
+
+def test_detect_many_classes():
+    """40 classes (beyond the 32 the decode keeps in registers), 3 anchors."""
+    anch = ANCH[:3]
+    rng = np.random.default_rng(40)
+    maps = rng.normal(0, 2, (2, 3 * (5 + 40), 11, 11)).astype(np.float32)
+    maps[:, 4::45] += 3.0                                 # confident objectness
+    cnt, det = _run_maps(maps, 0.02, 0.45, 4096, anch, 40)
+    for f in range(2):
+        n, ref_n, nd = _check_frame(maps[f].astype(np.float64), int(cnt[f]), det[f], 0.02, 0.45, 4096, anch, 40)
+        print("frame %d: %d kept (oracle %d), %d near-threshold differences" % (f, n, ref_n, nd))
+        assert n > 10
 
 
 def test_detect_truncation_and_empty():

@@ -102,3 +102,21 @@ def test_device_api_full_size():
         k, gch = J.solve_device(d_in, 0.0, 2, d_out)
     assert k == 2
     assert _nerr(d_out.cpu().numpy(), ref) <= 8 * ULP
+
+
+@pytest.mark.parametrize("rows", ["8", "32", "200"])
+def test_strip_height_does_not_change_the_result(rows, monkeypatch):
+    """Every point's new value depends only on the previous iterate, so the
+    strip height (NET_JACOBI_ROWS; by default the rows are split evenly over
+    the resident blocks) changes neither the grid nor the stopping decision,
+    bit for bit.  With 8-row strips the grid has more tiles (513 x 5) than
+    a GB300 has resident blocks (16 x 152), so blocks take a second tile."""
+    ny, nx = 4099, 2050
+    u0 = synth.laplace_grid(25, ny, nx, "random")
+    with _solver(ny, nx) as J:
+        ref, kr, cr = J.solve(u0, 1e-4, 40)
+    monkeypatch.setenv("NET_JACOBI_ROWS", rows)
+    with _solver(ny, nx) as J:
+        out, k, c = J.solve(u0, 1e-4, 40)
+    assert (k, c) == (kr, cr)
+    np.testing.assert_array_equal(out, ref)
