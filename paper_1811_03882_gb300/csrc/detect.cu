@@ -85,19 +85,17 @@ __device__ __forceinline__ float sigm(float v) { return 1.f / (1.f + expf(-v)); 
 __global__ void region_decode_kernel(const float* __restrict__ map, int batch, int A, int C, int GH, int GW,
                                      const float* __restrict__ anchor, float thresh, int maxc, int* cnt,
                                      RegionCand* cand) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = (long long)batch * A * GH * GW;
+    // boxes of a launch: batch * A * GH * GW < 2^31 (the set-up's bounds)
+    const int t = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int total = batch * A * GH * GW;
     const bool valid = t < total;
     const int lane = threadIdx.x & 31;
     // thread order (frame, anchor, row, column): consecutive threads read
     // consecutive columns of each channel
-    const long long tt = valid ? t : total - 1;
-    const int j = (int)(tt % GW);
-    long long r = tt / GW;
-    const int i = (int)(r % GH);
-    r /= GH;
-    const int a = (int)(r % A);
-    const int f = (int)(r / A);
+    const int tt = valid ? t : total - 1;
+    const int r1 = tt / GW, j = tt - r1 * GW;
+    const int r2 = r1 / GH, i = r1 - r2 * GH;
+    const int f = r2 / A, a = r2 - f * A;
     const long long plane = (long long)GH * GW;
     const float* p = map + ((long long)f * A * (5 + C) + (long long)a * (5 + C)) * plane + (long long)i * GW + j;
     const float x = ((float)j + sigm(p[0])) / (float)GW;
@@ -151,8 +149,9 @@ __global__ void region_decode_kernel(const float* __restrict__ map, int batch, i
             e[c] = c < C ? expf(e[c] - m) : 0.f;
             sum += e[c];
         }
+        const float os = obj / sum;   // class-c score = obj * e_c / sum
 #pragma unroll
-        for (int c = 0; c < 32; ++c) e[c] = obj * (e[c] / sum);
+        for (int c = 0; c < 32; ++c) e[c] *= os;
         if (peers == 0xffffffffu) {
             // the whole warp is one frame: lane c reserves class c's slots, all
             // classes' atomics in flight together
@@ -184,7 +183,8 @@ __global__ void region_decode_kernel(const float* __restrict__ map, int batch, i
         for (int c = 1; c < C; ++c) m = fmaxf(m, lg[c * plane]);
         float sum = 0.f;
         for (int c = 0; c < C; ++c) sum += expf(lg[c * plane] - m);
-        for (int c = 0; c < C; ++c) append(c, obj * (expf(lg[c * plane] - m) / sum));
+        const float os = obj / sum;
+        for (int c = 0; c < C; ++c) append(c, expf(lg[c * plane] - m) * os);
     }
 }
 
@@ -221,7 +221,7 @@ __host__ __device__ inline NmsSmem nms_layout(int P, int C) {
     s.sc = s.box + 16 * (size_t)P;           // P float score
     s.ids = s.sc + 4 * (size_t)P;            // P int box id
     s.area = s.ids + 4 * (size_t)P;          // P float area
-    s.pre = s.area + 4 * (size_t)P;          // P u32: overlaps with earlier candidates of the same 32-block
+    s.pre = s.area + 4 * (size_t)P;          // P u32: overlaps with later candidates of the same 32-block
     s.supp = s.pre + 4 * (size_t)P;          // P u8: suppressed
     s.prefix = (s.supp + (size_t)P + 15) & ~(size_t)15;   // C + 1 int: the frame's class offsets
     s.total = s.prefix + 4 * ((size_t)C + 1);
@@ -288,9 +288,13 @@ __global__ void __launch_bounds__(nms_threads(LOGP)) region_nms_kernel(int C, in
             v[m] = ~0ull;
         }
     }
+    // the network's merges of width k sort each k-slot block on its own:
+    // stopping at the first k >= n leaves slots [0, k) sorted ascending
+    // (empty slots hold the largest key); n is uniform, so is the stop
     int buf = 0;
 #pragma unroll
     for (int lk = 1; lk <= LOGP; ++lk) {
+        if (lk > 5 && (1 << (lk - 1)) >= n) break;
 #pragma unroll
         for (int lj = lk - 1; lj >= 0; --lj) {
             const int k = 1 << lk, jj = 1 << lj;
@@ -347,34 +351,39 @@ __global__ void __launch_bounds__(nms_threads(LOGP)) region_nms_kernel(int C, in
         }
     }
     __syncthreads();
-    // overlaps within each block of 32 (earlier candidate first, as greedy NMS
-    // compares a kept box with a later one)
+    // overlaps within each block of 32: bit q of post[r] = candidate r
+    // overlaps the later candidate r0 + q of its block (earlier box first, as
+    // greedy NMS compares a kept box with a later one)
     for (int r = tid; r < n; r += T) {
         const int l = r & 31, r0 = r - l;
         const float4 mine = edge[r];
         const float am = area[r];
         unsigned bits = 0;
 #pragma unroll 8
-        for (int q = 0; q < 31; ++q)
-            if (q < l && overlaps(edge[r0 + q], area[r0 + q], mine, am, iou_thr)) bits |= 1u << q;
+        for (int q = 1; q < 32; ++q)
+            if (q > l && r0 + q < n && overlaps(mine, am, edge[r0 + q], area[r0 + q], iou_thr)) bits |= 1u << q;
         pre[r] = bits;
     }
     __syncthreads();
     int r0 = 0;
     for (;;) {
         if (tid < 32) {
-            // settle blocks until one keeps a box (or the list ends)
+            // settle blocks until one keeps a box (or the list ends): the
+            // first alive candidate is kept and drops the later ones of the
+            // block it overlaps, then the next alive one, and so on (one step
+            // per kept candidate)
             unsigned kept = 0;
             while (r0 < n) {
                 const int r = r0 + lane;
                 const bool alive = r < n && !supp[r];
-                const unsigned am = __ballot_sync(0xffffffffu, alive);
-                const unsigned pb = r < n ? pre[r] : 0u;
+                unsigned live = __ballot_sync(0xffffffffu, alive);
+                const unsigned post = r < n ? pre[r] : 0u;
                 kept = 0;
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const unsigned pq = __shfl_sync(0xffffffffu, pb, q);
-                    if (((am >> q) & 1u) && !(pq & kept)) kept |= 1u << q;
+                while (live) {
+                    const int q = __ffs(live) - 1;
+                    kept |= 1u << q;
+                    live &= ~(1u << q);
+                    live &= ~__shfl_sync(0xffffffffu, post, q);
                 }
                 if (r < n) supp[r] = ((kept >> lane) & 1u) ? 0 : 1;
                 if (kept) break;
@@ -499,8 +508,9 @@ cudaError_t enqueue_region(const RegionState& R, const float* d_map, int batch, 
     const int A = R.r.n_anchors, C = R.r.n_classes;
     cudaError_t e = cudaMemsetAsync(R.d_cnt, 0, sizeof(int) * (size_t)batch * (C + 1), st);
     if (e != cudaSuccess) return e;
+    // 64-thread blocks: a batch's few thousand boxes spread over ~100 SMs
     const long long total = (long long)batch * A * GH * GW;
-    region_decode_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+    region_decode_kernel<<<(unsigned)((total + 63) / 64), 64, 0, st>>>(
         d_map, batch, A, C, GH, GW, R.d_anchor, R.r.score_thresh, R.maxc, R.d_cnt, R.d_cand);
     switch (nms_logp(R.maxc)) {
         case 8: e = launch_nms<8>(batch, C, R.maxc, R.r.nms_iou, R.r.max_det, R.d_cnt, R.d_cand, d_counts, d_det, st); break;

@@ -26,9 +26,9 @@
 //    below tol or sweeps reached iter_max.  The kernel returns at once when
 //    done is set, so the host can queue sweeps ahead and poll the 16-byte
 //    state only every few of them.
-//  * Strips are sized so that the tiles fill the resident blocks evenly
-//    (one tile a block on a large grid: 54-row strips at 8192 x 8192), so
-//    no block runs a second round alone.
+//  * Strips of 64 rows (fewer halo rows re-read than shorter strips; measured
+//    faster at 8192 x 8192 than strips sized to give every resident block
+//    exactly one tile).
 //  * The two buffers alternate by the parity of the sweep count, so the
 //    result is in buffer (sweeps & 1).
 #include <cuda_runtime.h>
@@ -257,12 +257,10 @@ extern "C" net_status net_jacobi_create(int ny, int nx, int device, void* cuda_s
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     // persistent: sixteen 128-thread blocks per SM (all resident: 32 registers
-    // a thread, 12 KB of shared memory a block); the strips split the
-    // interior rows evenly over `waves` tiles per block, at least 8 rows a
-    // strip (NET_JACOBI_ROWS overrides the strip height)
+    // a thread, 12 KB of shared memory a block) taking strips of 64 rows
+    // round robin (NET_JACOBI_ROWS overrides the strip height)
     j->col_blocks = cdiv(j->P, 4 * kThreads);
-    const int slots = std::max(1, 16 * sms / j->col_blocks), waves = 1;
-    j->rows = std::max(8, cdiv(ny - 2, slots * waves));
+    j->rows = 64;
     if (const char* v = getenv("NET_JACOBI_ROWS"))
         if (atoi(v) > 0) j->rows = atoi(v);
     j->strips = cdiv(ny - 2, j->rows);

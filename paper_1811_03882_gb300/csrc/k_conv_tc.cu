@@ -58,6 +58,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
                  : "memory");
 }
 
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -886,14 +892,24 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 release();
                 continue;
             }
-            if (a.ksplit > 1) {
-                // raw partial sums of this K slice; the reduction applies the
-                // epilogue.  Workspace plane z is tile-major in groups of four
-                // columns ([m_tiles][ncp / 4][128 rows][4]): the 32 rows of a warp
-                // write one contiguous 512-byte run per float4 store.
-                const int ncp = a.n_tiles * BN;
-                float* wr = a.ws + (size_t)z * a.m_tiles * 128 * ncp +
-                            ((size_t)mt * (ncp >> 2) + ((nt * BN + half * HC) >> 2)) * 512 + row * 4;
+            // split-K: K slices before the last write raw partial sums.  The
+            // last one either does too (a reduction kernel applies the epilogue)
+            // or, serial split-K, waits for the earlier slices' partials of its
+            // tile, adds them in slice order and applies the epilogue itself.
+            // Workspace plane z is tile-major in groups of four columns
+            // ([m_tiles][ncp / 4][128 rows][4]): the 32 rows of a warp write
+            // one contiguous 512-byte run per float4 store.
+            const int ncp = a.n_tiles * BN;
+            // (one CTA an SM only: the two-CTA variant has no registers to spare)
+            const bool serial = MB == 1 && a.ksplit > 1 && a.ks_serial;
+            const bool partial_out = a.ksplit > 1 && (!serial || z < a.ksplit - 1);
+            // warps that drain a tile (both warpgroups when they split its columns)
+            const unsigned kWarps = (a.kalt || C2) ? 8u : 4u;
+            const size_t wsoff = ((size_t)mt * (ncp >> 2) + ((nt * BN + half * HC) >> 2)) * 512 + row * 4;
+            const size_t zplane = (size_t)a.m_tiles * 128 * ncp;
+            unsigned* tcnt = serial ? a.ks_cnt + (size_t)mt * a.n_tiles + nt : nullptr;
+            if (partial_out) {
+                float* wr = a.ws + (size_t)z * zplane + wsoff;
 #pragma unroll 1
                 for (int c0 = 0; c0 < HC; c0 += CW) {
                     if (nt * BN + half * HC + c0 >= live) break;
@@ -907,7 +923,38 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         *reinterpret_cast<float4*>(wr + (size_t)((c0 + j) >> 2) * 512) =
                             make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                 }
+                if (serial) {
+                    // this warp's partials, then its arrival on the tile's counter
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) atomicAdd(tcnt, 1u);
+                }
             } else {
+                if (serial) {
+                    // the last K slice: every earlier slice's warps have published
+                    // (bounded wait; the counter is zero again after the last
+                    // reader of this launch)
+                    const unsigned need = kWarps * (unsigned)(a.ksplit - 1);
+                    int wok = 1;
+                    if (lane == 0) {
+                        const long long t0 = clock64();
+                        while (tc::ld_acquire(tcnt) < need) {
+                            if (*abort_flag) {
+                                wok = 0;
+                                break;
+                            }
+                            if (clock64() - t0 > lim) {
+                                *abort_flag = 1;
+                                atomicExch(a.err, 7);
+                                wok = 0;
+                                break;
+                            }
+                        }
+                    }
+                    wok = __shfl_sync(0xffffffffu, wok, 0);
+                    __syncwarp();
+                    if (!wok) break;
+                }
                 // the single-problem case keeps its fields in registers (read once)
                 if (a.nprob > 1 || !have_p) {
                     have_p = true;
@@ -953,6 +1000,29 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     tc::tmem_ld<CW>(trow + (uint32_t)c0, v);
                     if (a.kalt) add_pair(trow + (uint32_t)(BN + c0), v);
                     if (c0 + CW >= HC || o0 + CW >= live) release();
+                    if (serial) {
+                        // slices 0 .. ksplit - 2 in order, then this slice's sums:
+                        // the additions of the reduction kernel, in its order
+                        // (four columns at a time, so that few registers are live)
+                        const float* rd = a.ws + wsoff + (size_t)(c0 >> 2) * 512;
+#pragma unroll
+                        for (int j = 0; j < CW; j += 4) {
+                            float4 t = __ldcg(reinterpret_cast<const float4*>(rd + (size_t)(j >> 2) * 512));
+#pragma unroll 1
+                            for (int zz = 1; zz < a.ksplit - 1; ++zz) {
+                                const float4 u = __ldcg(
+                                    reinterpret_cast<const float4*>(rd + zz * zplane + (size_t)(j >> 2) * 512));
+                                t.x += u.x;
+                                t.y += u.y;
+                                t.z += u.z;
+                                t.w += u.w;
+                            }
+                            v[j] = t.x + v[j];
+                            v[j + 1] = t.y + v[j + 1];
+                            v[j + 2] = t.z + v[j + 2];
+                            v[j + 3] = t.w + v[j + 3];
+                        }
+                    }
                     // warp-uniform branches: each variant is one straight-line loop.
                     // Paired FP32 operations (one instruction on a register
                     // pair) round exactly as the scalar ones.
@@ -1066,6 +1136,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 }
             }
             if (!released) release();   // a tile without live columns (not produced by the planner)
+            if (serial && !partial_out && lane == 0) {
+                // readers count too; the last one returns the counter to zero
+                const unsigned total_arr = kWarps * (unsigned)a.ksplit;
+                if (atomicAdd(tcnt, 1u) == total_arr - 1u) atomicExch(tcnt, 0u);
+            }
         }
     }
 

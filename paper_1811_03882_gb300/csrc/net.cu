@@ -473,6 +473,14 @@ bool dn::tc_pair_enabled() {
     return on;
 }
 
+bool dn::tc_kserial_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("NET_TC_KSERIAL");
+        return !(e && atoi(e) == 0);
+    }();
+    return on;
+}
+
 bool dn::pdl_enabled() {
     static const bool on = [] {
         const char* e = getenv("NET_PDL");
@@ -574,9 +582,11 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             }
             r.n_tiles = cdiv(ncols, r.BN);
             const int tiles = r.m_tiles * r.n_tiles;
-            if (r.ksplit > 1)
+            if (r.ksplit > 1) {
                 P->ws_bytes = std::max(P->ws_bytes, (size_t)r.ksplit * r.m_tiles * 128 * r.n_tiles * r.BN *
                                                         sizeof(float));
+                P->ks_tiles = std::max(P->ks_tiles, (size_t)r.m_tiles * r.n_tiles);
+            }
             // the tap-pair first layer (32 live columns) measured slower with
             // two CTAs an SM (its 16-column epilogue chunks double the fixed
             // cost per chunk): one, unless forced or overridden
@@ -659,6 +669,17 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
         CK(cudaMalloc(&n->ws, P->ws_bytes));
         n->ws_bytes = P->ws_bytes;
     }
+    if (P->ks_tiles > n->ks_cnt_n) {
+        // grow the serial split-K counters (zero); graphs on the old ones are dropped
+        n->graphs_clear();
+        CK(cudaStreamSynchronize(n->stream));
+        if (n->ks_cnt) cudaFree(n->ks_cnt);
+        n->ks_cnt = nullptr;
+        n->ks_cnt_n = 0;
+        CK(cudaMalloc(&n->ks_cnt, P->ks_tiles * sizeof(unsigned)));
+        CK(cudaMemset(n->ks_cnt, 0, P->ks_tiles * sizeof(unsigned)));
+        n->ks_cnt_n = P->ks_tiles;
+    }
     *out = P.get();
     n->plans[key] = P.release();
     return NET_OK;
@@ -668,6 +689,9 @@ net_status dn::check_device_error(net* n) {
     if (n->err_host && *(volatile int*)n->err_host) {
         const int code = *(volatile int*)n->err_host;
         *(volatile int*)n->err_host = 0;
+        // an aborted pass may leave serial split-K counters part-way: zero
+        // them in stream order before the next pass
+        if (n->ks_cnt) cudaMemsetAsync(n->ks_cnt, 0, n->ks_cnt_n * sizeof(unsigned), n->stream);
         return fail(NET_E_DEVICE_WAIT, "a bounded device-side wait expired (code %d)", code);
     }
     return NET_OK;
@@ -759,6 +783,8 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.pair = L.pair ? 1 : 0;
                 a.ep = ep;
                 a.err = n->err_dev;
+                a.ks_serial = (r.ksplit > 1 && r.mb == 1 && tc_kserial_enabled()) ? 1 : 0;
+                a.ks_cnt = n->ks_cnt;
                 int grid = r.grid, cg = r.cg;
                 if (l == n->fault_layer) {
                     // net_inject_device_fault: a ~1 ms bound (clock64 cycles at
@@ -774,7 +800,7 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 }
                 e = conv_tc_launch(L.tmB[tmb_index(cg == 2 ? r.BN / 2 : r.BN)], a, r.BN, L.in_dt, grid, r.mb, cg,
                                    st);
-                if (e == cudaSuccess && r.ksplit > 1) {
+                if (e == cudaSuccess && r.ksplit > 1 && !a.ks_serial) {
                     ++n->pending;
                     SplitReduce sr{n->ws, r.ksplit, r.m_tiles * 128, r.n_tiles * r.BN, r.TW, r.TH,
                                    cdiv(r.W, r.TW), cdiv(r.H, r.TH), batch, r.H, r.W, y, ep, 1};
@@ -1253,6 +1279,7 @@ extern "C" net_status net_free(net_t* n) {
     for (auto& kv : n->plans) delete kv.second;
     n->plans.clear();
     if (n->ws) cudaFree(n->ws);
+    if (n->ks_cnt) cudaFree(n->ks_cnt);
     if (n->err_host) cudaFreeHost(n->err_host);
     cudaFree(n->act[0]);
     cudaFree(n->act[1]);

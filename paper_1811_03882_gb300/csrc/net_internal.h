@@ -77,6 +77,7 @@ struct LayerRun {
 struct Plan {
     std::vector<LayerRun> runs;
     size_t ws_bytes = 0;           // split-K workspace this plan needs
+    size_t ks_tiles = 0;           // serial split-K arrival counters this plan needs
     ~Plan();
 };
 
@@ -99,6 +100,8 @@ void tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int n
 int tc_mb_forced();
 // NET_TC_PAIR=1: fixed-batch layers that can take CTA pairs use them; read once.
 bool tc_pair_enabled();
+// Serial split-K for fixed-batch tensor-core layers (NET_TC_KSERIAL=0: a reduction kernel instead).
+bool tc_kserial_enabled();
 // Index into Layer::tmB of the weight map whose box has BN rows.
 int tmb_index(int BN);
 
@@ -148,6 +151,8 @@ struct net {
     int num_sms = 148;
     float* ws = nullptr;       // split-K workspace (grown by plans, before any capture)
     size_t ws_bytes = 0;
+    unsigned* ks_cnt = nullptr;  // serial split-K arrival counters, one per (M tile, N tile); zero between launches
+    size_t ks_cnt_n = 0;
     int* err_host = nullptr;   // mapped pinned: bounded device waits that expired
     int* err_dev = nullptr;
     int fault_layer = -1;      // net_inject_device_fault: layer of the next pass to fault (tests)

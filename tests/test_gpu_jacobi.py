@@ -107,8 +107,8 @@ def test_device_api_full_size():
 @pytest.mark.parametrize("rows", ["8", "32", "200"])
 def test_strip_height_does_not_change_the_result(rows, monkeypatch):
     """Every point's new value depends only on the previous iterate, so the
-    strip height (NET_JACOBI_ROWS; by default the rows are split evenly over
-    the resident blocks) changes neither the grid nor the stopping decision,
+    strip height (NET_JACOBI_ROWS; 64 rows by default) changes neither the
+    grid nor the stopping decision,
     bit for bit.  With 8-row strips the grid has more tiles (513 x 5) than
     a GB300 has resident blocks (16 x 152), so blocks take a second tile."""
     ny, nx = 4099, 2050
