@@ -462,6 +462,23 @@ net_status net_launches(const net_t* net, uint64_t* total);
  * unaffected.  NET_E_INVAL for a layer that does not run on tensor cores. */
 net_status net_inject_device_fault(net_t* net, int layer);
 
+/* Canary guard regions, a debug aid for out-of-bounds writes; the paper
+ * has no counterpart.  With NET_GUARD=1 in the environment when the
+ * process first allocates, every device buffer the library allocates
+ * (activations, weights, workspaces, staging, detection, nightmare, Jacobi
+ * and serving buffers) has 4 KB of 0xA5 bytes directly before and after
+ * it.  net_guard_check synchronises each device that holds one, copies the
+ * regions to the host and reports the buffers checked and how many have a
+ * changed region (a write past an end); both 0 when guards are off.  Host
+ * memory is untouched; the regions are freed with their buffers. */
+net_status net_guard_check(uint64_t* buffers, uint64_t* corrupted);
+
+/* Test hook for net_guard_check: overwrites the first byte after buffer
+ * `index` (address order of the live guarded buffers) by a host-side
+ * memset, as a one-element overrun would.  NET_E_STATE when guards are
+ * off, NET_E_INVAL for an index past the live buffers. */
+net_status net_guard_poke(uint64_t index);
+
 /* ---- conv layer without allocation ------------------------------------
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory when they call (code running while a CUDA

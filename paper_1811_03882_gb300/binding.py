@@ -124,6 +124,8 @@ _SIGS = {
     "net_layer_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "net_launches": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
     "net_inject_device_fault": [ctypes.c_void_p, ctypes.c_int],
+    "net_guard_check": [ctypes.c_void_p, ctypes.c_void_p],
+    "net_guard_poke": [ctypes.c_uint64],
     "net_set_region": [ctypes.c_void_p, ctypes.POINTER(net_region)],
     "net_nightmare_grad": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                            ctypes.c_void_p, ctypes.c_void_p],
@@ -166,6 +168,19 @@ def lib():
                 f.restype = ctypes.c_char_p if name in ("net_last_error", "net_version") else ctypes.c_int
             _lib = L
     return _lib
+
+
+def guard_check():
+    """(buffers checked, buffers with a changed guard region); (0, 0) unless
+    NET_GUARD=1 (net_guard_check)."""
+    b, c = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    check(lib().net_guard_check(ctypes.byref(b), ctypes.byref(c)))
+    return int(b.value), int(c.value)
+
+
+def guard_poke(index: int):
+    """Test hook: one byte written past guarded buffer `index` (net_guard_poke)."""
+    check(lib().net_guard_poke(int(index)))
 
 
 def last_error() -> str:

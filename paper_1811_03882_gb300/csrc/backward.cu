@@ -53,17 +53,17 @@ struct NightState {
 void night_free(net* n) {
     NightState* S = n->night;
     if (!S) return;
-    for (float* p : S->h) cudaFree(p);
-    for (float* p : S->wt) cudaFree(p);
-    cudaFree(S->a[0]);
-    cudaFree(S->a[1]);
-    cudaFree(S->g[0]);
-    cudaFree(S->g[1]);
-    cudaFree(S->zero_bias);
-    cudaFree(S->ws);
-    cudaFree(S->grad);
-    cudaFree(S->d_red);
-    cudaFree(S->d_part);
+    for (float* p : S->h) dn::dfree(p);
+    for (float* p : S->wt) dn::dfree(p);
+    dn::dfree(S->a[0]);
+    dn::dfree(S->a[1]);
+    dn::dfree(S->g[0]);
+    dn::dfree(S->g[1]);
+    dn::dfree(S->zero_bias);
+    dn::dfree(S->ws);
+    dn::dfree(S->grad);
+    dn::dfree(S->d_red);
+    dn::dfree(S->d_part);
     if (S->h_red) cudaFreeHost(S->h_red);
     delete S;
     n->night = nullptr;
@@ -256,25 +256,25 @@ static net_status night_setup(net* n) {
         // the conv's output size is its input size (the pool follows)
         const size_t hb = (size_t)n->max_batch * H[l] * W[l] * cs * sizeof(float);
         float* p = nullptr;
-        NK(cudaMalloc(&p, hb));
+        NK(dn::dalloc(&p, hb));
         S->h.push_back(p);
         amax = std::max(amax, (size_t)n->max_batch * H[l] * W[l] * std::max(cs, L.in_cs) * sizeof(float));
         gmax = std::max(gmax, (size_t)n->max_batch * H[l] * W[l] * std::max(cs, L.in_cs) * sizeof(float));
         const int KK = L.d.k * L.d.k, rows_t = rup(L.cin, 256);
         rows_max = std::max(rows_max, rows_t);
         float* w = nullptr;
-        NK(cudaMalloc(&w, (size_t)rows_t * KK * cs * sizeof(float)));
+        NK(dn::dalloc(&w, (size_t)rows_t * KK * cs * sizeof(float)));
         S->wt.push_back(w);
     }
     for (int b = 0; b < 2; ++b) {
-        NK(cudaMalloc(&S->a[b], amax));
-        NK(cudaMalloc(&S->g[b], gmax));
+        NK(dn::dalloc(&S->a[b], amax));
+        NK(dn::dalloc(&S->g[b], gmax));
     }
-    NK(cudaMalloc(&S->zero_bias, rows_max * sizeof(float)));
+    NK(dn::dalloc(&S->zero_bias, rows_max * sizeof(float)));
     NK(cudaMemsetAsync(S->zero_bias, 0, rows_max * sizeof(float), n->stream));
-    NK(cudaMalloc(&S->grad, (size_t)n->max_batch * n->in_c * n->max_side * n->max_side * sizeof(float)));
-    NK(cudaMalloc(&S->d_red, sizeof(double) * n->max_batch));
-    NK(cudaMalloc(&S->d_part, sizeof(double) * n->max_batch * kRedParts));
+    NK(dn::dalloc(&S->grad, (size_t)n->max_batch * n->in_c * n->max_side * n->max_side * sizeof(float)));
+    NK(dn::dalloc(&S->d_red, sizeof(double) * n->max_batch));
+    NK(dn::dalloc(&S->d_part, sizeof(double) * n->max_batch * kRedParts));
     NK(cudaHostAlloc(&S->h_red, sizeof(double) * n->max_batch, cudaHostAllocDefault));
     return NET_OK;
 }
@@ -310,10 +310,10 @@ static net_status night_conv(net* n, const void* x, const void* w, int w_rows, v
         const size_t need = (size_t)ks * m_tiles * th * tw * n_tiles * bn * sizeof(float);
         if (need > S->ws_bytes) {
             NK(cudaStreamSynchronize(n->stream));
-            cudaFree(S->ws);
+            dn::dfree(S->ws);
             S->ws = nullptr;
             S->ws_bytes = 0;
-            NK(cudaMalloc(&S->ws, need));
+            NK(dn::dalloc(&S->ws, need));
             S->ws_bytes = need;
         }
     }

@@ -267,12 +267,12 @@ extern "C" net_status net_jacobi_create(int ny, int nx, int device, void* cuda_s
     j->grid = std::max(1, std::min(j->col_blocks * j->strips, 16 * sms));
     const size_t bytes = (size_t)ny * j->P * sizeof(float);
     for (int b = 0; b < 2; ++b) {
-        cudaError_t e = cudaMalloc(&j->buf[b], bytes);
+        cudaError_t e = dn::dalloc(&j->buf[b], bytes);
         if (e != cudaSuccess) return bail(fail(e == cudaErrorMemoryAllocation ? NET_E_OOM : NET_E_CUDA, "grid buffer"));
         cudaMemsetAsync(j->buf[b], 0, bytes, j->stream);
     }
-    if (cudaMalloc(&j->partial, sizeof(float) * j->grid) != cudaSuccess ||
-        cudaMalloc(&j->d_state, sizeof(JState)) != cudaSuccess ||
+    if (dn::dalloc(&j->partial, sizeof(float) * j->grid) != cudaSuccess ||
+        dn::dalloc(&j->d_state, sizeof(JState)) != cudaSuccess ||
         cudaHostAlloc(&j->h_state, 2 * sizeof(JState), cudaHostAllocDefault) != cudaSuccess)
         return bail(fail(NET_E_OOM, "jacobi state"));
     if (cudaStreamSynchronize(j->stream) != cudaSuccess) return bail(fail(NET_E_CUDA, "jacobi set-up"));
@@ -378,10 +378,10 @@ extern "C" net_status net_jacobi_free(net_jacobi_t* j) {
     cudaSetDevice(j->device);
     if (j->stream) cudaStreamSynchronize(j->stream);
     for (auto& kv : j->graphs) cudaGraphExecDestroy(kv.second);
-    cudaFree(j->buf[0]);
-    cudaFree(j->buf[1]);
-    cudaFree(j->partial);
-    cudaFree(j->d_state);
+    dn::dfree(j->buf[0]);
+    dn::dfree(j->buf[1]);
+    dn::dfree(j->partial);
+    dn::dfree(j->d_state);
     if (j->h_state) cudaFreeHost(j->h_state);
     if (j->own_stream && j->stream) cudaStreamDestroy(j->stream);
     delete j;

@@ -7,21 +7,19 @@
 // so its error against the FP64 oracle stays at FP32 rounding level.
 //
 // Tile: a TH x TW rectangle of output pixels of one frame times BN output
-// channels; 256 threads, each owning PPT pixels x CPT channels (CPT = 4, or
-// 8 for 128-channel tiles: 64 accumulators fed by four 16-byte shared loads
-// per K element instead of 32 by three).  Pixels are ordered by 2x2 quads
-// inside the tile and every thread owns whole quads, so the fused 2x2/s2
-// max pool of the epilogue is a register-local max.
+// channels; 256 threads.  Pixels are ordered by 2x2 quads inside the tile
+// and every thread owns whole quads, so the fused 2x2/s2 max pool of the
+// epilogue is a register-local max.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace dn {
 
-template <int BN, int TH, int TW, int CPT>
+template <int BN, int TH, int TW>
 struct SimtCfg {
     static constexpr int THREADS = 256;
     static constexpr int PX = TH * TW;          // pixels per tile
-    static constexpr int CG = BN / CPT;         // channel groups (CPT ch each)
+    static constexpr int CG = BN / 4;           // channel groups (4 ch each)
     static constexpr int PG = THREADS / CG;     // pixel groups
     static constexpr int PPT = PX / PG;         // pixels per thread
     static constexpr int QX = TW / 2;           // quads per tile row
@@ -33,14 +31,13 @@ struct SimtCfg {
     static_assert(B_VEC_TOTAL <= THREADS, "B tile split");
 };
 
-template <int BN, int TH, int TW, int CPT>
+template <int BN, int TH, int TW>
 __global__ void __launch_bounds__(256)
 conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
                  void* __restrict__ y, int H, int W, int Cp, int k, int kw_rows,
                  int tiles_x, int tiles_y, Epilogue ep, int ksplit, float* __restrict__ ws,
                  int ws_cols) {
-    using C = SimtCfg<BN, TH, TW, CPT>;
-    static_assert(CPT == 4 || CPT == 8, "channels per thread");
+    using C = SimtCfg<BN, TH, TW>;
     __shared__ __align__(16) float As[2][C::BK][C::PX];
     __shared__ __align__(16) float Bs[2][C::BK][BN];
 
@@ -109,11 +106,11 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
         }
     };
 
-    float acc[C::PPT][CPT];
+    float acc[C::PPT][4];
 #pragma unroll
     for (int i = 0; i < C::PPT; ++i)
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
 
     const int cg = tid % C::CG, pg = tid / C::CG;
     if (nsteps > 0) {
@@ -132,16 +129,14 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
                 float4 v = *reinterpret_cast<const float4*>(&As[buf][kk][pg * C::PPT + i]);
                 a[i] = v.x; a[i + 1] = v.y; a[i + 2] = v.z; a[i + 3] = v.w;
             }
-            float b[CPT];
+            float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][cg * 4]);
 #pragma unroll
-            for (int j = 0; j < CPT; j += 4) {
-                const float4 t = *reinterpret_cast<const float4*>(&Bs[buf][kk][cg * CPT + j]);
-                b[j] = t.x; b[j + 1] = t.y; b[j + 2] = t.z; b[j + 3] = t.w;
+            for (int i = 0; i < C::PPT; ++i) {
+                acc[i][0] = fmaf(a[i], b.x, acc[i][0]);
+                acc[i][1] = fmaf(a[i], b.y, acc[i][1]);
+                acc[i][2] = fmaf(a[i], b.z, acc[i][2]);
+                acc[i][3] = fmaf(a[i], b.w, acc[i][3]);
             }
-#pragma unroll
-            for (int i = 0; i < C::PPT; ++i)
-#pragma unroll
-                for (int j = 0; j < CPT; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
         if (s + 1 < nsteps) {
             store(buf ^ 1);
@@ -149,6 +144,7 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
         }
     }
 
+    const int obase = n0 + cg * 4;
     if (ksplit > 1) {
         // raw partial sums; the reduction kernel applies the epilogue
         const size_t mbase = (size_t)blockIdx.x * C::PX;
@@ -158,21 +154,13 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
             const int pos = pg * C::PPT + i;
             const int q = pos >> 2;
             const int py = 2 * (q / C::QX) + ((pos >> 1) & 1), px = 2 * (q % C::QX) + (pos & 1);
-#pragma unroll
-            for (int j = 0; j < CPT; j += 4)
-                *reinterpret_cast<float4*>(wz + (mbase + py * TW + px) * ws_cols + n0 + cg * CPT + j) =
-                    make_float4(acc[i][j], acc[i][j + 1], acc[i][j + 2], acc[i][j + 3]);
+            *reinterpret_cast<float4*>(wz + (mbase + py * TW + px) * ws_cols + obase) =
+                make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
         }
         return;
     }
 
     // ---- epilogue: alpha/bias, activation, optional 2x2/s2 max, store ----
-    // (four channels at a time: CPT / 4 groups)
-    const bool pool = ep.pool == POOL_S2;
-    const int Ho = pool ? H / 2 : H, Wo = pool ? W / 2 : W;
-#pragma unroll
-    for (int g4 = 0; g4 < CPT / 4; ++g4) {
-    const int obase = n0 + cg * CPT + 4 * g4;
     float bia[4], alp[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -180,6 +168,8 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
         bia[j] = (o < ep.cout) ? ep.bias[o] : 0.f;
         alp[j] = (o < ep.cout && ep.alpha) ? ep.alpha[o] : 1.f;
     }
+    const bool pool = ep.pool == POOL_S2;
+    const int Ho = pool ? H / 2 : H, Wo = pool ? W / 2 : W;
 #pragma unroll
     for (int qi = 0; qi < C::PPT / 4; ++qi) {
         const int q = (pg * C::PPT) / 4 + qi;
@@ -189,7 +179,7 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
         for (int p = 0; p < 4; ++p)
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                v[p][j] = act_apply(fmaf(acc[qi * 4 + p][4 * g4 + j], alp[j], bia[j]), ep.act);
+                v[p][j] = act_apply(fmaf(acc[qi * 4 + p][j], alp[j], bia[j]), ep.act);
         const int npix = pool ? 1 : 4;
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
@@ -242,26 +232,24 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
             }
         }
     }
-    }   // channel groups
 }
 
-template <int BN, int TH, int TW, int CPT>
+template <int BN, int TH, int TW>
 static cudaError_t launch_simt(const ConvLaunch& L, int ncols, cudaStream_t st) {
     const int tiles_x = cdiv(L.W, TW), tiles_y = cdiv(L.H, TH);
     const int ks = L.ksplit > 1 ? L.ksplit : 1;
     const int n_tiles = cdiv(ncols, BN);
     dim3 grid((unsigned)(L.n * tiles_x * tiles_y), (unsigned)n_tiles, (unsigned)ks);
-    conv_simt_kernel<BN, TH, TW, CPT><<<grid, 256, 0, st>>>(
+    conv_simt_kernel<BN, TH, TW><<<grid, 256, 0, st>>>(
         reinterpret_cast<const float*>(L.x), reinterpret_cast<const float*>(L.w), L.y, L.H, L.W,
         L.Cp, L.k, L.w_rows, tiles_x, tiles_y, L.ep, ks, L.ws, n_tiles * BN);
     return cudaGetLastError();
 }
 
-void simt_tile(int ncols, int* bn, int* th, int* tw, bool wide) {
+void simt_tile(int ncols, int* bn, int* th, int* tw) {
     if (ncols <= 16) { *bn = 16; *th = 16; *tw = 16; }
     else if (ncols <= 32) { *bn = 32; *th = 8; *tw = 16; }
-    else if (ncols <= 64 || !wide) { *bn = 64; *th = 8; *tw = 16; }
-    else { *bn = 128; *th = 8; *tw = 16; }
+    else { *bn = 64; *th = 8; *tw = 16; }
 }
 
 cudaError_t conv_simt(const ConvLaunch& L, cudaStream_t st) {
@@ -269,11 +257,9 @@ cudaError_t conv_simt(const ConvLaunch& L, cudaStream_t st) {
                                                       : (L.ep.out_cs > L.ep.cout ? L.ep.out_cs : L.ep.cout);
     int bn, th, tw;
     simt_tile(ncols, &bn, &th, &tw);
-    if (L.bn > 0 && L.bn < bn) bn = L.bn;   // a caller's narrower tile (its scratch is sized for it)
-    if (bn == 16) return launch_simt<16, 16, 16, 4>(L, ncols, st);
-    if (bn == 32) return launch_simt<32, 8, 16, 4>(L, ncols, st);
-    if (bn == 64) return launch_simt<64, 8, 16, 4>(L, ncols, st);
-    return launch_simt<128, 8, 16, 8>(L, ncols, st);
+    if (bn == 16) return launch_simt<16, 16, 16>(L, ncols, st);
+    if (bn == 32) return launch_simt<32, 8, 16>(L, ncols, st);
+    return launch_simt<64, 8, 16>(L, ncols, st);
 }
 
 }  // namespace dn

@@ -58,12 +58,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
                  : "memory");
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -336,10 +330,25 @@ struct Smem {
 // 128 rows of A and BN / 2 of B instead of 128 + BN, so more stages fit and
 // each byte in flight feeds twice the MMA work.  No resident weights, tap
 // merging, tap pairs or K-alternating issuers in this mode.
-template <int BN, int DT, int MB, int CG>
+template <int BN, int DT, int MB, int CG, int SP>
 __global__ void __launch_bounds__(tc::THREADS, MB)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     using namespace tc;
+    // Specialisations, their modes fixed at compile time so that the epilogue
+    // (which bounds the short-tile layers) carries no code for other cases:
+    // SP = 1, the tap-pair first layer (tap pairs on tap-merged stages,
+    // resident weights, one issuer a tile); SP = 2, any other BF16 layer; both
+    // with no K split and BF16 NHWC output without alpha
+    static_assert(SP == 0 || ((SP == 1 || SP == 2) && DT == DT_BF16 && CG == 1), "specialisations");
+    // (read where used, as the generic variant reads its launch arguments)
+#define kKalt (SP == 1 ? 0 : a.kalt)
+#define kTapm (SP == 1 ? 1 : a.tapm)
+#define kPair (SP == 1 ? 1 : SP == 2 ? 0 : a.pair)
+#define kBres (SP == 1 ? 1 : a.bres)
+#define kKsplit (SP ? 1 : a.ksplit)
+#define kAlpha (SP ? (const float*)nullptr : a.ep.alpha)
+#define kOutLayout (SP ? (int)LAYOUT_NHWC : (int)a.ep.out_layout)
+#define kOutDt (SP ? (int)DT_BF16 : (int)a.ep.out_dt)
     static_assert(MB == 1 || (MB == 2 && BN <= 128), "two CTAs per SM: N tiles of at most 128 columns");
     static_assert(CG == 1 || (CG == 2 && MB == 1 && BN >= 128), "CTA pairs: one CTA an SM, N tiles of 128 or 256");
     constexpr bool C2 = CG == 2;
@@ -368,7 +377,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int KK = a.k * a.k;
     const int nkb = KK * a.chunks;                // weight boxes (tap, chunk) per tile
-    const int nk = a.tapm ? a.chunks : nkb;       // pipeline steps per tile
+    const int nk = kTapm ? a.chunks : nkb;       // pipeline steps per tile
     // CTA pairs: this CTA's rank (0 issues the MMAs)
     const uint32_t rank = C2 ? cluster_rank() : 0u;
     // work items: (m unit, n-tile, K slice), taken round robin by the CTAs
@@ -376,12 +385,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     const int worker = C2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
     const int nworkers = C2 ? (int)(gridDim.x >> 1) : (int)gridDim.x;
     const int m_units = C2 ? (a.m_tiles + 1) >> 1 : a.m_tiles;
-    const int total = m_units * a.n_tiles * a.ksplit;
+    const int total = m_units * a.n_tiles * kKsplit;
     const int pad = a.k >> 1;
     // A bytes per stage: one 128-row box, or three (TH + 2)-row boxes (tapm);
     // B: the N tile's box, or (CTA pairs) this CTA's half of it
-    const uint32_t a_box = a.tapm ? (uint32_t)(a.TH + 2) * a.TW * a.chb : 128u * a.chb;
-    const uint32_t a_bytes = a.tapm ? 3u * a_box : a_box, b_bytes = (uint32_t)(C2 ? BN / 2 : BN) * a.chb;
+    const uint32_t a_box = kTapm ? (uint32_t)(a.TH + 2) * a.TW * a.chb : 128u * a.chb;
+    const uint32_t a_bytes = kTapm ? 3u * a_box : a_box, b_bytes = (uint32_t)(C2 ? BN / 2 : BN) * a.chb;
 
     if (threadIdx.x == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
@@ -395,7 +404,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             // the 4 warps of the warpgroup that drains buffer b; in K-alternating
             // mode both warpgroups drain every tile (half of its columns each);
             // CTA pairs: the 8 epilogue warps of both CTAs (on the even CTA's)
-            tc::mbar_init(smem_u32(&sm->acce[b]), C2 ? 16 : a.kalt ? 8 : 4);
+            tc::mbar_init(smem_u32(&sm->acce[b]), C2 ? 16 : kKalt ? 8 : 4);
         }
         // one commit from each MMA issuer (CTA pairs: the even CTA's issuer)
         tc::mbar_init(smem_u32(&sm->done), C2 ? 1 : 2);
@@ -428,7 +437,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     tc::fence_after();
     const uint32_t tmem_base = sm->tmem;
     volatile int* abort_flag = &sm->abort;
-    if (a.bres && warp == 0 && lane == 0) {
+    if (kBres && warp == 0 && lane == 0) {
         // resident weights: every K step's [BN x chunk] box of this CTA's N
         // tile, once, side by side.  The launch has no K split and a grid
         // that is a multiple of the N tile count, so the round-robin work
@@ -438,7 +447,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         // previous kernel's tail.
         const uint32_t rb = smem_u32(&sm->bres);
         const int nt_res = (worker - fdiv(worker, a.fd_ntiles) * a.n_tiles) * BN;   // first weight row
-        if (a.pair) {
+        if (kPair) {
             // pair mode: slots in tap-pair order; slot 9 starts at K column
             // 9 * Cp, past the weights' last column, so TMA fills it with zeros
             tc::mbar_expect_tx(rb, (uint32_t)kPairSlots * b_bytes);
@@ -498,8 +507,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             int towner = 0, nt = 0, img = 0, x0 = 0, y0 = 0;
             const ConvProblem* P = P1;
             auto slice = [&] {
-                if (a.ksplit > 1) {
-                    const int z = tile - fdiv(tile, a.fd_ksplit) * a.ksplit;
+                if (kKsplit > 1) {
+                    const int z = tile - fdiv(tile, a.fd_ksplit) * kKsplit;
                     ks0 = fdiv(nk * z, a.fd_ksplit);
                     ks1 = fdiv(nk * (z + 1), a.fd_ksplit);
                 } else {
@@ -508,7 +517,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 }
             };
             auto setup = [&] {   // coordinates of the lane's current tile
-                const int mn = a.ksplit > 1 ? fdiv(tile, a.fd_ksplit) : tile;
+                const int mn = kKsplit > 1 ? fdiv(tile, a.fd_ksplit) : tile;
                 const int mq = fdiv(mn, a.fd_ntiles);
                 // CTA pairs: M tile 2 mq + rank (an absent second tile loads a
                 // duplicate of the last one, which its epilogue does not store)
@@ -581,8 +590,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             // bytes), and every load completes on the even CTA's barrier
             const int b_row0 = C2 ? (int)rank * (BN / 2) : 0;   // this CTA's first row of the B box
             const uint32_t st_tx = C2 ? 2u * (a_bytes + b_bytes) : a_bytes + b_bytes;
-            if (!a.bres && tile < total) {
-                const int owner = C2 ? 0 : a.kalt ? ((ks - ks0) & 1) : towner;
+            if (!kBres && tile < total) {
+                const int owner = C2 ? 0 : kKalt ? ((ks - ks0) & 1) : towner;
                 const uint32_t fb = smem_u32(&sm->full[owner][ps]);
                 if constexpr (C2) {
                     if (rank == 0) tc::mbar_expect_tx(fb, st_tx);
@@ -621,7 +630,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     const int s = ps;
                     // the issuer that consumes this K step: the tile's, or in
                     // K-alternating mode the K step's parity within the tile
-                    const int owner = C2 ? 0 : a.kalt ? ((ks - ks0) & 1) : towner;
+                    const int owner = C2 ? 0 : kKalt ? ((ks - ks0) & 1) : towner;
                     const uint32_t fb = smem_u32(&sm->full[owner][s]);
                     if (owner) pph1 ^= 1u << s;
                     else pph0 ^= 1u << s;
@@ -637,15 +646,15 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         if (pre_b) pre_b = false;
                         else tc::tma_load_2d_pair(smem_u32(stg + a_bytes), &tmB, kcol, nt * BN + b_row0, fbc);
                     } else {
-                        if (!pre_b) tc::mbar_expect_tx(fb, a.bres ? a_bytes : st_tx);
-                        if (a.tapm) {   // step = chunk ks of all nine taps: one box per tap column
+                        if (!pre_b) tc::mbar_expect_tx(fb, kBres ? a_bytes : st_tx);
+                        if (kTapm) {   // step = chunk ks of all nine taps: one box per tap column
                             for (int dx = 0; dx < 3; ++dx)
                                 tc::tma_load_4d(smem_u32(stg + dx * a_box), &P->tmA, ks * a.cpc, x0 + dx, y0, img,
                                                 fb);
                         } else {
                             tc::tma_load_4d(smem_u32(stg), &P->tmA, c0, x0 + kw, y0 + kh, img, fb);
                         }
-                        if (a.bres || pre_b) {
+                        if (kBres || pre_b) {
                             pre_b = false;
                         } else {
                             tc::tma_load_2d(smem_u32(stg + a_bytes), &tmB, kcol, nt * BN, fb);
@@ -660,7 +669,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     advance(S2);
                 }
             }
-            if (a.bres && pid == 0 && lane == 0 &&
+            if (kBres && pid == 0 && lane == 0 &&
                 !tc::mbar_wait(smem_u32(&sm->bres), 0u, abort_flag, a.err, 5, lim)) {
                 const long long t0 = clock64();
                 while (!tc::mbar_try(smem_u32(&sm->bres), 0u) && clock64() - t0 < WAIT_LIMIT) {
@@ -715,25 +724,25 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             int it = 0, tcount = 0;
             uint32_t fph = 0u;   // bit s = phase parity of this issuer's next use of stage s
             bool ok = true;
-            if (a.bres) {
+            if (kBres) {
                 ok = tc::mbar_wait(smem_u32(&sm->bres), 0u, abort_flag, a.err, 6, lim);
                 tc::fence_after();
             }
             for (int tile = worker; tile < total && ok; tile += nworkers, ++tcount) {
                 int ks0 = 0, ks1 = nk;
-                if (a.ksplit > 1) {
-                    const int z = tile - fdiv(tile, a.fd_ksplit) * a.ksplit;
+                if (kKsplit > 1) {
+                    const int z = tile - fdiv(tile, a.fd_ksplit) * kKsplit;
                     ks0 = fdiv(nk * z, a.fd_ksplit);
                     ks1 = fdiv(nk * (z + 1), a.fd_ksplit);
                 }
-                if (!C2 && !a.kalt && (tcount & 1) != mid) {   // the other issuer's tile: its stages are skipped
+                if (!C2 && !kKalt && (tcount & 1) != mid) {   // the other issuer's tile: its stages are skipped
                     it += ks1 - ks0;
                     continue;
                 }
                 // accumulator slots: NBUF, or NBUF / 2 pairs (both powers of two)
-                const int nsl_log = a.kalt ? NBUF_LOG - 1 : NBUF_LOG;
+                const int nsl_log = kKalt ? NBUF_LOG - 1 : NBUF_LOG;
                 const int slot = tcount & ((1 << nsl_log) - 1);
-                const int b = a.kalt ? 2 * slot + mid : slot;
+                const int b = kKalt ? 2 * slot + mid : slot;
                 const uint32_t aph = (uint32_t)(tcount >> nsl_log) & 1u;
                 if (!tc::mbar_wait<C2>(smem_u32(&sm->acce[b]), aph ^ 1u, abort_flag, a.err, 2, lim)) break;
                 tc::fence_after();
@@ -743,7 +752,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
                     const int s = ms;
                     if (++ms == nst) ms = 0;
-                    if (a.kalt && ((ks - ks0) & 1) != mid) continue;   // the other issuer's K step
+                    if (kKalt && ((ks - ks0) & 1) != mid) continue;   // the other issuer's K step
                     const uint32_t ph = (fph >> s) & 1u;
                     if (!tc::mbar_wait(smem_u32(&sm->full[mid][s]), ph, abort_flag, a.err, 3, lim)) {
                         ok = false;
@@ -753,7 +762,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     tc::fence_after();
                     uint8_t* stg = sRing + (size_t)s * st_bytes;
                     const int nmma = a.chb / 32;   // 32 bytes of K per MMA
-                    if (a.pair) {
+                    if (kPair) {
                         // five MMAs of K = 16, each over two taps: the A core
                         // matrices of the second tap lie lbo bytes after the
                         // first's (for the tenth, zero-weight slot lbo is 0:
@@ -770,7 +779,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                             tc::mma<DT, CG>(dtm, ad, bd, idesc, (!first || j != 0) ? 1u : 0u);
                         }
                         first = false;
-                    } else if (a.tapm) {
+                    } else if (kTapm) {
                         // nine taps of chunk ks: tap (dy, dx) reads box dx from row dy * TW
                         for (int dx = 0; dx < 3; ++dx)
                             for (int dy = 0; dy < 3; ++dy) {
@@ -786,7 +795,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     } else {
                         const uint64_t ad = tc::smem_desc(smem_u32(stg), a.chb);
                         const uint64_t bd =
-                            tc::smem_desc(smem_u32(a.bres ? sBres + (size_t)ks * b_bytes : stg + a_bytes), a.chb);
+                            tc::smem_desc(smem_u32(kBres ? sBres + (size_t)ks * b_bytes : stg + a_bytes), a.chb);
                         for (int j = 0; j < nmma; ++j)
                             tc::mma<DT, CG>(dtm, ad + (uint64_t)(2 * j), bd + (uint64_t)(2 * j), idesc,
                                             (!first || j != 0) ? 1u : 0u);
@@ -815,8 +824,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         // nothing overlaps, runs on both warpgroups
         // (CTA pairs: both warpgroups on every tile too; one issuer, one buffer
         // sequence)
-        const int half = (a.kalt || C2) ? grp : 0;
-        const int HC = (a.kalt || C2) ? BN / 2 : BN;
+        const int half = (kKalt || C2) ? grp : 0;
+        const int HC = (kKalt || C2) ? BN / 2 : BN;
         const int row = q * 32 + lane;          // pixel index in the tile
         const int py = row / a.TW, px = row % a.TW;
         const bool pool = a.ep.pool == POOL_S2;
@@ -827,32 +836,32 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         if (epi_smem) {
             for (int i = threadIdx.x - 64; i < ncol_all; i += 256) {
                 s_bias[i] = a.ep.bias[i];
-                if (a.ep.alpha) s_alpha[i] = a.ep.alpha[i];
+                if (kAlpha) s_alpha[i] = kAlpha[i];
             }
             asm volatile("bar.sync 1, 256;" ::: "memory");   // the 8 epilogue warps
         }
         const float* e_bias = epi_smem ? s_bias : a.ep.bias;
-        const float* e_alpha = epi_smem ? s_alpha : a.ep.alpha;
+        const float* e_alpha = epi_smem ? s_alpha : kAlpha;
         const int ymask = a.TW == 16 ? 16 : 8;  // lane distance of the pixel below (pool tiles)
         // columns at or beyond `live` are padding nobody reads: skipped
-        const int live = a.ep.out_layout == LAYOUT_NCHW ? a.ep.cout : max(a.ep.out_cs, a.ep.cout);
+        const int live = kOutLayout == LAYOUT_NCHW ? a.ep.cout : max(a.ep.out_cs, a.ep.cout);
         void* pY = nullptr;
         int pH = 0, pW = 0, pTX = 1, pTY = 1, pBegin = 0;
         FastDiv fTX, fTY;
         int tcount = 0;
         bool have_p = false;   // problem fields loaded (single-problem launches read them once)
         for (int tile = worker; tile < total; tile += nworkers, ++tcount) {
-            if (!C2 && !a.kalt && (tcount & 1) != grp) continue;
+            if (!C2 && !kKalt && (tcount & 1) != grp) continue;
             // the tile's accumulator (or pair of them in K-alternating mode)
-            const int nsl_log = a.kalt ? NBUF_LOG - 1 : NBUF_LOG;
+            const int nsl_log = kKalt ? NBUF_LOG - 1 : NBUF_LOG;
             const int slot = tcount & ((1 << nsl_log) - 1);
-            const int b = a.kalt ? 2 * slot : slot;
+            const int b = kKalt ? 2 * slot : slot;
             const uint32_t aph = (uint32_t)(tcount >> nsl_log) & 1u;
             if (!tc::mbar_wait<C2>(smem_u32(&sm->accf[b]), aph, abort_flag, a.err, 4, lim)) break;
-            if (a.kalt && !tc::mbar_wait(smem_u32(&sm->accf[b + 1]), aph, abort_flag, a.err, 4, lim)) break;
+            if (kKalt && !tc::mbar_wait(smem_u32(&sm->accf[b + 1]), aph, abort_flag, a.err, 4, lim)) break;
             tc::fence_after();
-            const int mn = a.ksplit > 1 ? fdiv(tile, a.fd_ksplit) : tile;
-            const int z = tile - mn * a.ksplit;
+            const int mn = kKsplit > 1 ? fdiv(tile, a.fd_ksplit) : tile;
+            const int z = tile - mn * kKsplit;
             const int mq = fdiv(mn, a.fd_ntiles);
             const int mt = C2 ? 2 * mq + (int)rank : mq, nt = mn - mq * a.n_tiles;
             const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * HC);
@@ -883,7 +892,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         tc::mbar_arrive_cl(cl_addr(smem_u32(&sm->acce[b]), 0));   // the even CTA's
                     } else {
                         tc::mbar_arrive(smem_u32(&sm->acce[b]));
-                        if (a.kalt) tc::mbar_arrive(smem_u32(&sm->acce[b + 1]));
+                        if (kKalt) tc::mbar_arrive(smem_u32(&sm->acce[b + 1]));
                     }
                 }
                 released = true;
@@ -892,69 +901,28 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 release();
                 continue;
             }
-            // split-K: K slices before the last write raw partial sums.  The
-            // last one either does too (a reduction kernel applies the epilogue)
-            // or, serial split-K, waits for the earlier slices' partials of its
-            // tile, adds them in slice order and applies the epilogue itself.
-            // Workspace plane z is tile-major in groups of four columns
-            // ([m_tiles][ncp / 4][128 rows][4]): the 32 rows of a warp write
-            // one contiguous 512-byte run per float4 store.
-            const int ncp = a.n_tiles * BN;
-            // (one CTA an SM only: the two-CTA variant has no registers to spare)
-            const bool serial = MB == 1 && a.ksplit > 1 && a.ks_serial;
-            const bool partial_out = a.ksplit > 1 && (!serial || z < a.ksplit - 1);
-            // warps that drain a tile (both warpgroups when they split its columns)
-            const unsigned kWarps = (a.kalt || C2) ? 8u : 4u;
-            const size_t wsoff = ((size_t)mt * (ncp >> 2) + ((nt * BN + half * HC) >> 2)) * 512 + row * 4;
-            const size_t zplane = (size_t)a.m_tiles * 128 * ncp;
-            unsigned* tcnt = serial ? a.ks_cnt + (size_t)mt * a.n_tiles + nt : nullptr;
-            if (partial_out) {
-                float* wr = a.ws + (size_t)z * zplane + wsoff;
+            if (kKsplit > 1) {
+                // raw partial sums of this K slice; the reduction applies the
+                // epilogue.  Workspace plane z is tile-major in groups of four
+                // columns ([m_tiles][ncp / 4][128 rows][4]): the 32 rows of a warp
+                // write one contiguous 512-byte run per float4 store.
+                const int ncp = a.n_tiles * BN;
+                float* wr = a.ws + (size_t)z * a.m_tiles * 128 * ncp +
+                            ((size_t)mt * (ncp >> 2) + ((nt * BN + half * HC) >> 2)) * 512 + row * 4;
 #pragma unroll 1
                 for (int c0 = 0; c0 < HC; c0 += CW) {
                     if (nt * BN + half * HC + c0 >= live) break;
                     float v[CW];
                     __syncwarp();
                     tc::tmem_ld<CW>(trow + (uint32_t)c0, v);
-                    if (a.kalt) add_pair(trow + (uint32_t)(BN + c0), v);
+                    if (kKalt) add_pair(trow + (uint32_t)(BN + c0), v);
                     if (c0 + CW >= HC || nt * BN + half * HC + c0 + CW >= live) release();
 #pragma unroll
                     for (int j = 0; j < CW; j += 4)
                         *reinterpret_cast<float4*>(wr + (size_t)((c0 + j) >> 2) * 512) =
                             make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                 }
-                if (serial) {
-                    // this warp's partials, then its arrival on the tile's counter
-                    __threadfence();
-                    __syncwarp();
-                    if (lane == 0) atomicAdd(tcnt, 1u);
-                }
             } else {
-                if (serial) {
-                    // the last K slice: every earlier slice's warps have published
-                    // (bounded wait; the counter is zero again after the last
-                    // reader of this launch)
-                    const unsigned need = kWarps * (unsigned)(a.ksplit - 1);
-                    int wok = 1;
-                    if (lane == 0) {
-                        const long long t0 = clock64();
-                        while (tc::ld_acquire(tcnt) < need) {
-                            if (*abort_flag) {
-                                wok = 0;
-                                break;
-                            }
-                            if (clock64() - t0 > lim) {
-                                *abort_flag = 1;
-                                atomicExch(a.err, 7);
-                                wok = 0;
-                                break;
-                            }
-                        }
-                    }
-                    wok = __shfl_sync(0xffffffffu, wok, 0);
-                    __syncwarp();
-                    if (!wok) break;
-                }
                 // the single-problem case keeps its fields in registers (read once)
                 if (a.nprob > 1 || !have_p) {
                     have_p = true;
@@ -998,35 +966,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     float v[CW];
                     __syncwarp();
                     tc::tmem_ld<CW>(trow + (uint32_t)c0, v);
-                    if (a.kalt) add_pair(trow + (uint32_t)(BN + c0), v);
+                    if (kKalt) add_pair(trow + (uint32_t)(BN + c0), v);
                     if (c0 + CW >= HC || o0 + CW >= live) release();
-                    if (serial) {
-                        // slices 0 .. ksplit - 2 in order, then this slice's sums:
-                        // the additions of the reduction kernel, in its order
-                        // (four columns at a time, so that few registers are live)
-                        const float* rd = a.ws + wsoff + (size_t)(c0 >> 2) * 512;
-#pragma unroll
-                        for (int j = 0; j < CW; j += 4) {
-                            float4 t = __ldcg(reinterpret_cast<const float4*>(rd + (size_t)(j >> 2) * 512));
-#pragma unroll 1
-                            for (int zz = 1; zz < a.ksplit - 1; ++zz) {
-                                const float4 u = __ldcg(
-                                    reinterpret_cast<const float4*>(rd + zz * zplane + (size_t)(j >> 2) * 512));
-                                t.x += u.x;
-                                t.y += u.y;
-                                t.z += u.z;
-                                t.w += u.w;
-                            }
-                            v[j] = t.x + v[j];
-                            v[j + 1] = t.y + v[j + 1];
-                            v[j + 2] = t.z + v[j + 2];
-                            v[j + 3] = t.w + v[j + 3];
-                        }
-                    }
                     // warp-uniform branches: each variant is one straight-line loop.
                     // Paired FP32 operations (one instruction on a register
                     // pair) round exactly as the scalar ones.
-                    if (a.ep.alpha) {
+                    if (kAlpha) {
 #pragma unroll
                         for (int j = 0; j < CW / 4; ++j) {
                             const float4 t = reinterpret_cast<const float4*>(e_alpha + o0)[j];
@@ -1058,7 +1003,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                             v[2 * j + 1] = fmaxf(v[2 * j + 1], s2.y);
                         }
                     }
-                    if (a.ep.out_layout == LAYOUT_NCHW) {
+                    if (kOutLayout == LAYOUT_NCHW) {
                         if (pool) {
 #pragma unroll
                             for (int j = 0; j < CW; ++j) {
@@ -1075,7 +1020,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         }
                         continue;
                     }
-                    if (a.ep.out_dt == DT_BF16) {
+                    if (kOutDt == DT_BF16) {
                         // round first, then pool on packed pairs: RNE is monotone,
                         // so max(rn(a), rn(b)) == rn(max(a, b)) and half the shuffles go
                         uint32_t w[CW / 2];
@@ -1117,7 +1062,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         }
                     }
                     if (!writer || o0 >= a.ep.out_cs) continue;
-                    if (a.ep.out_dt == DT_FP8) {
+                    if (kOutDt == DT_FP8) {
                         uint4 pk[CW / 16];
                         uint8_t* w8 = reinterpret_cast<uint8_t*>(pk);
 #pragma unroll
@@ -1136,11 +1081,6 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 }
             }
             if (!released) release();   // a tile without live columns (not produced by the planner)
-            if (serial && !partial_out && lane == 0) {
-                // readers count too; the last one returns the counter to zero
-                const unsigned total_arr = kWarps * (unsigned)a.ksplit;
-                if (atomicAdd(tcnt, 1u) == total_arr - 1u) atomicExch(tcnt, 0u);
-            }
         }
     }
 
@@ -1160,6 +1100,15 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                          : "memory");
     }
 }
+
+#undef kKalt
+#undef kTapm
+#undef kPair
+#undef kBres
+#undef kKsplit
+#undef kAlpha
+#undef kOutLayout
+#undef kOutDt
 
 // ----------------------------------------------------------------- host
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1265,7 +1214,7 @@ bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb, int mb) {
     return ksplit == 1 && (size_t)nk * BN * chb + a_st <= tc_avail(mb);
 }
 
-template <int BN, int DT, int MB, int CG>
+template <int BN, int DT, int MB, int CG, int SP = 0>
 static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int workers, cudaStream_t st) {
     TcArgs a = a0;
     // CTA pairs: streamed weights (half a box each), plain stages, one MMA
@@ -1289,7 +1238,7 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     if (a.wait_limit <= 0) a.wait_limit = tc::WAIT_LIMIT;
     const size_t smem = 1024 + (size_t)a.ctrl_off + tc_ctrl_bytes();
     if (smem > (MB == 2 ? kSmemLimit2 : kSmemLimit)) return cudaErrorInvalidValue;
-    auto kern = conv_tc_kernel<BN, DT, MB, CG>;
+    auto kern = conv_tc_kernel<BN, DT, MB, CG, SP>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1332,6 +1281,29 @@ cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int 
         return cudaErrorInvalidValue;
     }
     if (cg != 1) return cudaErrorInvalidValue;
+    // BF16 layers without a K split and with BF16 NHWC output run the
+    // specialised variants: the tap-pair first layer SP = 1, the others SP = 2
+    // (NET_TC_SPEC=0: the generic kernel)
+    static const bool spec_on = [] {
+        const char* e = getenv("NET_TC_SPEC");
+        return !(e && atoi(e) == 0);
+    }();
+    if (spec_on && dt == DT_BF16 && a.ksplit == 1 && a.ep.out_layout == LAYOUT_NHWC && a.ep.out_dt == DT_BF16 &&
+        !a.ep.alpha) {
+        if (a.pair && a.tapm && a.bres && !a.kalt) {
+            if (BN == 64 && mb == 1) return launch_tc_bn<64, DT_BF16, 1, 1, 1>(tmB, a, workers, st);
+            if (BN == 128 && mb == 1) return launch_tc_bn<128, DT_BF16, 1, 1, 1>(tmB, a, workers, st);
+        } else if (!a.pair) {
+            if (mb == 1) {
+                if (BN == 64) return launch_tc_bn<64, DT_BF16, 1, 1, 2>(tmB, a, workers, st);
+                if (BN == 128) return launch_tc_bn<128, DT_BF16, 1, 1, 2>(tmB, a, workers, st);
+                if (BN == 256) return launch_tc_bn<256, DT_BF16, 1, 1, 2>(tmB, a, workers, st);
+            } else if (mb == 2) {
+                if (BN == 64) return launch_tc_bn<64, DT_BF16, 2, 1, 2>(tmB, a, workers, st);
+                if (BN == 128) return launch_tc_bn<128, DT_BF16, 2, 1, 2>(tmB, a, workers, st);
+            }
+        }
+    }
     if (mb == 2) {
         if (dt == DT_BF16 && BN == 64) return launch_tc_bn<64, DT_BF16, 2, 1>(tmB, a, workers, st);
         if (dt == DT_BF16 && BN == 128) return launch_tc_bn<128, DT_BF16, 2, 1>(tmB, a, workers, st);

@@ -17,14 +17,13 @@ struct ConvLaunch {
     int k;           // 1 or 3
     int w_rows;      // allocated weight rows (>= every column a tile touches)
     Epilogue ep;
-    int bn, th, tw;  // CUDA cores: bn > 0 caps the N tile (0: chosen from ep); th, tw unused
+    int bn, th, tw;  // tile: th x tw pixels x bn channels (0: choose from ep)
     int ksplit;      // > 1: K split over grid.z, raw sums to ws
     float* ws;       // split-K partial sums [ksplit][m_tiles*th*tw][n_tiles*bn]
 };
 
-// CUDA-core tile for ncols output columns (wide = false: at most 64 columns,
-// the tile the no-allocation entry point sizes its scratch for).
-void simt_tile(int ncols, int* bn, int* th, int* tw, bool wide = true);
+// CUDA-core tile choice for a layer with `ncols` output columns.
+void simt_tile(int ncols, int* bn, int* th, int* tw);
 cudaError_t conv_simt(const ConvLaunch& L, cudaStream_t st);
 
 // Split-K reduction + epilogue: y = epilogue(sum_z ws[z]) in fixed z order.
@@ -166,12 +165,6 @@ struct TcArgs {
     long long wait_limit;   // bound of each pipeline wait, clock64 cycles (<= 0: ~2 s)
     int nst_cap;            // ring stages at most (even, >= 2; 0: as many as fit)
     int withhold;           // fault injection (tests): one producer skips one K step
-    // serial split-K (ksplit > 1): the last K slice adds the earlier slices'
-    // partials of its tile itself, after ks_cnt[m_tile * n_tiles + n_tile]
-    // (zero between launches) counts their warps' arrivals; no reduction kernel
-    // (one CTA an SM only)
-    int ks_serial;
-    unsigned* ks_cnt;
     // division by ksplit, n_tiles, chunks, k and nst (filled by conv_tc_launch)
     FastDiv fd_ksplit, fd_ntiles, fd_chunks, fd_k, fd_nst;
 };

@@ -205,15 +205,15 @@ extern "C" net_status net_create(const net_desc* d, net_t** out) {
         n->L = keep;
     }
     for (int i = 0; i < 2; ++i) {
-        CK(cudaMalloc(&n->act[i], n->act_bytes));
+        CK(dn::dalloc(&n->act[i], n->act_bytes));
         CK(cudaMemsetAsync(n->act[i], 0, n->act_bytes, n->stream));
     }
     int co, ho, wo;
     net_output_shape(n.get(), n->max_side, n->max_side, &co, &ho, &wo);
     n->in_stage_bytes = (size_t)n->max_batch * n->in_c * n->max_side * n->max_side * sizeof(float);
     n->out_stage_bytes = (size_t)n->max_batch * co * ho * wo * sizeof(float);
-    CK(cudaMalloc(&n->d_in_stage, n->in_stage_bytes));
-    CK(cudaMalloc(&n->d_out_stage, n->out_stage_bytes));
+    CK(dn::dalloc(&n->d_in_stage, n->in_stage_bytes));
+    CK(dn::dalloc(&n->d_out_stage, n->out_stage_bytes));
     CK(cudaStreamSynchronize(n->stream));
     *out = n.release();
     return NET_OK;
@@ -254,12 +254,12 @@ extern "C" net_status net_load_weights(net_t* n, const float* blob, size_t n_flo
     CK(cudaSetDevice(n->device));
     CK(cudaStreamSynchronize(n->stream));
     float* d_blob = nullptr;
-    CK(cudaMalloc(&d_blob, need * sizeof(float)));
+    CK(dn::dalloc(&d_blob, need * sizeof(float)));
     cudaError_t e = cudaMemcpyAsync(d_blob, blob, need * sizeof(float), cudaMemcpyHostToDevice, n->stream);
     int maxc = 0;
     for (auto& L : n->L) maxc = std::max(maxc, L.d.cout);
     double* tmp = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&tmp, 2 * (size_t)maxc * sizeof(double));
+    if (e == cudaSuccess) e = dn::dalloc(&tmp, 2 * (size_t)maxc * sizeof(double));
     size_t off = 0;
     for (size_t l = 0; l < n->L.size() && e == cudaSuccess; ++l) {
         Layer& L = n->L[l];
@@ -280,21 +280,21 @@ extern "C" net_status net_load_weights(net_t* n, const float* blob, size_t n_flo
         const int dt = L.in_dt;
         const int KKx = L.kx * L.kx;   // taps of the stored layout (1 when im2col-packed)
         const size_t wbytes = (size_t)L.w_rows * KKx * L.in_cs * dt_size(dt);
-        if (!L.w) e = cudaMalloc(&L.w, wbytes);
+        if (!L.w) e = dn::dalloc(&L.w, wbytes);
         // bias and alpha are padded with zeros to w_rows: the tensor-core
         // epilogue reads them four at a time without bounds checks
-        if (e == cudaSuccess && !L.bias) e = cudaMalloc(&L.bias, L.w_rows * sizeof(float));
+        if (e == cudaSuccess && !L.bias) e = dn::dalloc(&L.bias, L.w_rows * sizeof(float));
         if (e == cudaSuccess) e = cudaMemsetAsync(L.bias, 0, L.w_rows * sizeof(float), n->stream);
         const bool fp8w = dt == DT_FP8 || L.fp8_capable;
-        if (e == cudaSuccess && fp8w && !L.wscale) e = cudaMalloc(&L.wscale, L.d.cout * sizeof(float));
+        if (e == cudaSuccess && fp8w && !L.wscale) e = dn::dalloc(&L.wscale, L.d.cout * sizeof(float));
         if (e == cudaSuccess && fp8w && !L.alpha) {
-            e = cudaMalloc(&L.alpha, L.w_rows * sizeof(float));
+            e = dn::dalloc(&L.alpha, L.w_rows * sizeof(float));
             if (e == cudaSuccess) e = cudaMemsetAsync(L.alpha, 0, L.w_rows * sizeof(float), n->stream);
         }
         L.cs32 = rup(L.cin, 4);
         const bool want32 = n->has_fp8 && dt != DT_F32;
         if (e == cudaSuccess && want32 && !L.w32) {
-            e = cudaMalloc(&L.w32, (size_t)L.w_rows * KK * L.cs32 * sizeof(float));
+            e = dn::dalloc(&L.w32, (size_t)L.w_rows * KK * L.cs32 * sizeof(float));
             if (e == cudaSuccess)
                 e = cudaMemsetAsync(L.w32, 0, (size_t)L.w_rows * KK * L.cs32 * sizeof(float), n->stream);
         }
@@ -340,7 +340,7 @@ extern "C" net_status net_load_weights(net_t* n, const float* blob, size_t n_flo
                     continue;
                 }
                 const size_t vb = (size_t)L.w_rows * KK * L.cs_var[v] * dt_size(vdt);
-                if (!L.w_var[v]) e = cudaMalloc(&L.w_var[v], vb);
+                if (!L.w_var[v]) e = dn::dalloc(&L.w_var[v], vb);
                 if (e != cudaSuccess) break;
                 FoldArgs b = a;
                 b.Cp = L.cs_var[v];
@@ -356,8 +356,8 @@ extern "C" net_status net_load_weights(net_t* n, const float* blob, size_t n_flo
         if (e == cudaSuccess && fp8w) e = make_alpha(L.wscale, L.act_scale, L.alpha, L.d.cout, n->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
-    cudaFree(d_blob);
-    cudaFree(tmp);
+    dn::dfree(d_blob);
+    dn::dfree(tmp);
     if (e != cudaSuccess) return fail(NET_E_CUDA, "weight fold: %s", cudaGetErrorString(e));
     n->weights_loaded = true;
     n->night_weights_stale = true;
@@ -391,7 +391,7 @@ static float in_scale(const Layer& L) { return L.in_dt == DT_FP8 ? (float)L.act_
 
 Plan::~Plan() {
     for (auto& r : runs)
-        if (r.d_prob) cudaFree(r.d_prob);
+        if (r.d_prob) dn::dfree(r.d_prob);
 }
 
 // Analytic tile/split choice for the tensor-core kernel.  The mainloop is
@@ -469,14 +469,6 @@ bool dn::tc_pair_enabled() {
     static const bool on = [] {
         const char* e = getenv("NET_TC_PAIR");
         return e && atoi(e) == 1;
-    }();
-    return on;
-}
-
-bool dn::tc_kserial_enabled() {
-    static const bool on = [] {
-        const char* e = getenv("NET_TC_KSERIAL");
-        return !(e && atoi(e) == 0);
     }();
     return on;
 }
@@ -582,11 +574,9 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             }
             r.n_tiles = cdiv(ncols, r.BN);
             const int tiles = r.m_tiles * r.n_tiles;
-            if (r.ksplit > 1) {
+            if (r.ksplit > 1)
                 P->ws_bytes = std::max(P->ws_bytes, (size_t)r.ksplit * r.m_tiles * 128 * r.n_tiles * r.BN *
                                                         sizeof(float));
-                P->ks_tiles = std::max(P->ks_tiles, (size_t)r.m_tiles * r.n_tiles);
-            }
             // the tap-pair first layer (32 live columns) measured slower with
             // two CTAs an SM (its 16-column epilogue chunks double the fixed
             // cost per chunk): one, unless forced or overridden
@@ -646,7 +636,7 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             hp.tile_begin = 0;
             // the table is complete on the device before any launch reads it
             // (kernels read it ahead of their dependency wait)
-            CK(cudaMalloc(&r.d_prob, sizeof(ConvProblem)));
+            CK(dn::dalloc(&r.d_prob, sizeof(ConvProblem)));
             CK(cudaMemcpyAsync(r.d_prob, &hp, sizeof hp, cudaMemcpyHostToDevice, n->stream));
             CK(cudaStreamSynchronize(n->stream));
             static const bool dump = getenv("NET_PLAN_DUMP") != nullptr;   // diagnostics: one line per layer
@@ -663,22 +653,11 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
     if (P->ws_bytes > n->ws_bytes) {
         // grow the split-K workspace; graphs captured on the old one are dropped
         n->graphs_clear();
-        if (n->ws) cudaFree(n->ws);
+        if (n->ws) dn::dfree(n->ws);
         n->ws = nullptr;
         n->ws_bytes = 0;
-        CK(cudaMalloc(&n->ws, P->ws_bytes));
+        CK(dn::dalloc(&n->ws, P->ws_bytes));
         n->ws_bytes = P->ws_bytes;
-    }
-    if (P->ks_tiles > n->ks_cnt_n) {
-        // grow the serial split-K counters (zero); graphs on the old ones are dropped
-        n->graphs_clear();
-        CK(cudaStreamSynchronize(n->stream));
-        if (n->ks_cnt) cudaFree(n->ks_cnt);
-        n->ks_cnt = nullptr;
-        n->ks_cnt_n = 0;
-        CK(cudaMalloc(&n->ks_cnt, P->ks_tiles * sizeof(unsigned)));
-        CK(cudaMemset(n->ks_cnt, 0, P->ks_tiles * sizeof(unsigned)));
-        n->ks_cnt_n = P->ks_tiles;
     }
     *out = P.get();
     n->plans[key] = P.release();
@@ -689,9 +668,6 @@ net_status dn::check_device_error(net* n) {
     if (n->err_host && *(volatile int*)n->err_host) {
         const int code = *(volatile int*)n->err_host;
         *(volatile int*)n->err_host = 0;
-        // an aborted pass may leave serial split-K counters part-way: zero
-        // them in stream order before the next pass
-        if (n->ks_cnt) cudaMemsetAsync(n->ks_cnt, 0, n->ks_cnt_n * sizeof(unsigned), n->stream);
         return fail(NET_E_DEVICE_WAIT, "a bounded device-side wait expired (code %d)", code);
     }
     return NET_OK;
@@ -783,8 +759,6 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.pair = L.pair ? 1 : 0;
                 a.ep = ep;
                 a.err = n->err_dev;
-                a.ks_serial = (r.ksplit > 1 && r.mb == 1 && tc_kserial_enabled()) ? 1 : 0;
-                a.ks_cnt = n->ks_cnt;
                 int grid = r.grid, cg = r.cg;
                 if (l == n->fault_layer) {
                     // net_inject_device_fault: a ~1 ms bound (clock64 cycles at
@@ -800,7 +774,7 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 }
                 e = conv_tc_launch(L.tmB[tmb_index(cg == 2 ? r.BN / 2 : r.BN)], a, r.BN, L.in_dt, grid, r.mb, cg,
                                    st);
-                if (e == cudaSuccess && r.ksplit > 1 && !a.ks_serial) {
+                if (e == cudaSuccess && r.ksplit > 1) {
                     ++n->pending;
                     SplitReduce sr{n->ws, r.ksplit, r.m_tiles * 128, r.n_tiles * r.BN, r.TW, r.TH,
                                    cdiv(r.W, r.TW), cdiv(r.H, r.TH), batch, r.H, r.W, y, ep, 1};
@@ -1009,8 +983,8 @@ static net_status async_start(net* n) {
     // asynchronous calls without touching their buffers
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        e = cudaMalloc(&A->d_in[k], n->in_stage_bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&A->d_out[k], n->out_stage_bytes);
+        e = dn::dalloc(&A->d_in[k], n->in_stage_bytes);
+        if (e == cudaSuccess) e = dn::dalloc(&A->d_out[k], n->out_stage_bytes);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&A->s_in, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&A->s_out, cudaStreamNonBlocking);
@@ -1021,8 +995,8 @@ static net_status async_start(net* n) {
     }
     if (e != cudaSuccess) {
         for (int k = 0; k < 2; ++k) {
-            cudaFree(A->d_in[k]);
-            cudaFree(A->d_out[k]);
+            dn::dfree(A->d_in[k]);
+            dn::dfree(A->d_out[k]);
         }
         if (A->s_in) cudaStreamDestroy(A->s_in);
         if (A->s_out) cudaStreamDestroy(A->s_out);
@@ -1044,8 +1018,8 @@ static void async_free(net* n) {
     cudaStreamSynchronize(n->stream);
     cudaStreamSynchronize(A->s_out);
     for (int k = 0; k < 2; ++k) {
-        cudaFree(A->d_in[k]);
-        cudaFree(A->d_out[k]);
+        dn::dfree(A->d_in[k]);
+        dn::dfree(A->d_out[k]);
     }
     cudaStreamDestroy(A->s_in);
     cudaStreamDestroy(A->s_out);
@@ -1164,8 +1138,8 @@ net_status dn::run_fp32_reference(net* n, const float* d_frames, int batch, int 
         mx = std::max(mx, (size_t)batch * H[l] * W[l] * n->L[l].cs32 * 4);
         mx = std::max(mx, (size_t)batch * H[l + 1] * W[l + 1] * rup(n->L[l].d.cout, 4) * 4);
     }
-    CK(cudaMalloc(&n->cal[0], mx));
-    cudaError_t e = cudaMalloc(&n->cal[1], mx);
+    CK(dn::dalloc(&n->cal[0], mx));
+    cudaError_t e = dn::dalloc(&n->cal[1], mx);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->cal[0], 0, mx, n->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->cal[1], 0, mx, n->stream);
     // layers whose own weights are FP32 use them directly
@@ -1181,8 +1155,8 @@ net_status dn::run_fp32_reference(net* n, const float* d_frames, int batch, int 
         if (e != cudaSuccess) s = fail(NET_E_CUDA, "reference pass: %s", cudaGetErrorString(e));
     }
     for (size_t l = 0; l < n->L.size(); ++l) n->L[l].w32 = saved[l];
-    cudaFree(n->cal[0]);
-    cudaFree(n->cal[1]);
+    dn::dfree(n->cal[0]);
+    dn::dfree(n->cal[1]);
     n->cal[0] = n->cal[1] = nullptr;
     return s;
 }
@@ -1198,16 +1172,16 @@ extern "C" net_status net_calibrate(net_t* n, const float* d_frames, int batch, 
     float *amax = nullptr, *dout = nullptr;
     int c, ho, wo;
     net_output_shape(n, h, w, &c, &ho, &wo);
-    CK(cudaMalloc(&amax, n->L.size() * sizeof(float)));
-    CK(cudaMalloc(&dout, (size_t)batch * c * ho * wo * sizeof(float)));
+    CK(dn::dalloc(&amax, n->L.size() * sizeof(float)));
+    CK(dn::dalloc(&dout, (size_t)batch * c * ho * wo * sizeof(float)));
     CK(cudaMemsetAsync(amax, 0, n->L.size() * sizeof(float), n->stream));
     s = run_fp32_reference(n, d_frames, batch, h, w, dout, amax);
     std::vector<float> hm(n->L.size());
     // the handle's stream may be non-blocking: finish it before a plain copy
     cudaError_t e = cudaStreamSynchronize(n->stream);
     if (e == cudaSuccess) e = cudaMemcpy(hm.data(), amax, hm.size() * sizeof(float), cudaMemcpyDeviceToHost);
-    cudaFree(amax);
-    cudaFree(dout);
+    dn::dfree(amax);
+    dn::dfree(dout);
     if (s != NET_OK) return s;
     if (e != cudaSuccess) return fail(NET_E_CUDA, "calibrate: %s", cudaGetErrorString(e));
     std::vector<float> sc(n->L.size());
@@ -1269,23 +1243,22 @@ extern "C" net_status net_free(net_t* n) {
     for (auto ev : n->prof_ev) cudaEventDestroy(ev);
     for (auto& L : n->L) {
         for (int v = 0; v < 2; ++v)
-            if (L.w_var[v] && L.w_var[v] != L.w) cudaFree(L.w_var[v]);
-        cudaFree(L.w);
-        cudaFree(L.bias);
-        cudaFree(L.wscale);
-        cudaFree(L.alpha);
-        cudaFree(L.w32);
+            if (L.w_var[v] && L.w_var[v] != L.w) dn::dfree(L.w_var[v]);
+        dn::dfree(L.w);
+        dn::dfree(L.bias);
+        dn::dfree(L.wscale);
+        dn::dfree(L.alpha);
+        dn::dfree(L.w32);
     }
     for (auto& kv : n->plans) delete kv.second;
     n->plans.clear();
-    if (n->ws) cudaFree(n->ws);
-    if (n->ks_cnt) cudaFree(n->ks_cnt);
+    if (n->ws) dn::dfree(n->ws);
     if (n->err_host) cudaFreeHost(n->err_host);
-    cudaFree(n->act[0]);
-    cudaFree(n->act[1]);
+    dn::dfree(n->act[0]);
+    dn::dfree(n->act[1]);
     async_free(n);
-    cudaFree(n->d_in_stage);
-    cudaFree(n->d_out_stage);
+    dn::dfree(n->d_in_stage);
+    dn::dfree(n->d_out_stage);
     uneven_free(n);
     region_free(n);
     night_free(n);

@@ -77,7 +77,6 @@ struct LayerRun {
 struct Plan {
     std::vector<LayerRun> runs;
     size_t ws_bytes = 0;           // split-K workspace this plan needs
-    size_t ks_tiles = 0;           // serial split-K arrival counters this plan needs
     ~Plan();
 };
 
@@ -100,8 +99,6 @@ void tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, int n
 int tc_mb_forced();
 // NET_TC_PAIR=1: fixed-batch layers that can take CTA pairs use them; read once.
 bool tc_pair_enabled();
-// Serial split-K for fixed-batch tensor-core layers (NET_TC_KSERIAL=0: a reduction kernel instead).
-bool tc_kserial_enabled();
 // Index into Layer::tmB of the weight map whose box has BN rows.
 int tmb_index(int BN);
 
@@ -151,8 +148,6 @@ struct net {
     int num_sms = 148;
     float* ws = nullptr;       // split-K workspace (grown by plans, before any capture)
     size_t ws_bytes = 0;
-    unsigned* ks_cnt = nullptr;  // serial split-K arrival counters, one per (M tile, N tile); zero between launches
-    size_t ks_cnt_n = 0;
     int* err_host = nullptr;   // mapped pinned: bounded device waits that expired
     int* err_dev = nullptr;
     int fault_layer = -1;      // net_inject_device_fault: layer of the next pass to fault (tests)
@@ -170,6 +165,15 @@ struct net {
 namespace dn {
 
 net_status fail(net_status s, const char* fmt, ...);
+// Device buffers of the library: cudaMalloc, with canary guard regions
+// around each buffer when NET_GUARD=1 (guard.cu, net_guard_check); freed
+// with dfree (which frees a plain cudaMalloc'd pointer too).
+cudaError_t dalloc_raw(void** p, size_t bytes);
+cudaError_t dfree(void* p);
+template <class T>
+inline cudaError_t dalloc(T** p, size_t bytes) {
+    return dalloc_raw(reinterpret_cast<void**>(p), bytes);
+}
 void layer_dims(const net* n, int h, int w, std::vector<int>& H, std::vector<int>& W);
 net_status check_shape(const net* n, int batch, int h, int w);
 size_t act_bytes_for(const net* n, int batch, int h, int w);

@@ -51,7 +51,7 @@ extern "C" net_status net_conv2d_f32_noalloc(const float* d_x, int n, int cin, i
     const int KK = k * k;
     const int w_rows = rup(cout, 256);
     int bn, th, tw;
-    simt_tile(cout, &bn, &th, &tw, false);   // the scratch bound below assumes this tile
+    simt_tile(cout, &bn, &th, &tw);
     const int tiles_x = cdiv(w, tw), tiles_y = cdiv(h, th);
     const int m_tiles = n * tiles_x * tiles_y;
     const int n_tiles = cdiv(cout, bn);
@@ -131,7 +131,6 @@ extern "C" net_status net_conv2d_f32_noalloc(const float* d_x, int n, int cin, i
     c.ep.out_cs = cout;
     c.ep.cout = cout;
     c.ksplit = ksplit;
-    c.bn = bn;
     c.ws = s_ws;
     if (e == cudaSuccess) e = conv_simt(c, st);
     if (e == cudaSuccess && ksplit > 1) {

@@ -31,10 +31,10 @@ struct UPlan {
     int kernels = 0;
     ~UPlan() {
         for (auto& r : runs)
-            if (r.d_prob) cudaFree(r.d_prob);
-        if (d_pack) cudaFree(d_pack);
+            if (r.d_prob) dn::dfree(r.d_prob);
+        if (d_pack) dn::dfree(d_pack);
         for (auto* p : d_pool)
-            if (p) cudaFree(p);
+            if (p) dn::dfree(p);
         if (graph) cudaGraphExecDestroy(graph);
     }
 };
@@ -71,12 +71,12 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
         for (auto& kv : U->plans) delete kv.second;   // plans point into the old arena
         U->plans.clear();
         for (int i = 0; i < 2; ++i) {
-            if (U->buf[i]) cudaFree(U->buf[i]);
+            if (U->buf[i]) dn::dfree(U->buf[i]);
             U->buf[i] = nullptr;
         }
         U->cap = 0;
         for (int i = 0; i < 2; ++i) {
-            cudaError_t e = cudaMalloc(&U->buf[i], need);
+            cudaError_t e = dn::dalloc(&U->buf[i], need);
             if (e != cudaSuccess) return fail(NET_E_OOM, "uneven arena %zu bytes: %s", need, cudaGetErrorString(e));
             cudaMemset(U->buf[i], 0, need);
         }
@@ -98,7 +98,7 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
             b += (long long)side[f] * side[f] * (n->L[0].im2col_k ? 1 : n->L[0].in_cs / V);
         }
         P->pack_total = b;
-        cudaError_t e = cudaMalloc(&P->d_pack, sizeof(PackJob) * cnt);
+        cudaError_t e = dn::dalloc(&P->d_pack, sizeof(PackJob) * cnt);
         if (e == cudaSuccess) e = cudaMemcpy(P->d_pack, jobs.data(), sizeof(PackJob) * cnt, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(NET_E_CUDA, "pack table: %s", cudaGetErrorString(e));
     }
@@ -162,7 +162,7 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
                    &r.bres, &r.mb);
         if (L.pair && !r.bres) return fail(NET_E_UNSUPPORTED, "layer %d: pair mode needs resident weights", l);
         r.tapm = L.pair ? 1 : 0;
-        cudaError_t e = cudaMalloc(&r.d_prob, sizeof(ConvProblem) * cnt);
+        cudaError_t e = dn::dalloc(&r.d_prob, sizeof(ConvProblem) * cnt);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(r.d_prob, probs.data(), sizeof(ConvProblem) * cnt, cudaMemcpyHostToDevice, n->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
@@ -177,7 +177,7 @@ static net_status build_uplan(net* n, const float* const* d_in, const int* side,
                 b += (long long)H[f][l + 1] * W[f][l + 1] * (n->L[l + 1].in_cs / V);
             }
             P->pool_total[l] = b;
-            e = cudaMalloc(&P->d_pool[l], sizeof(PoolJob) * cnt);
+            e = dn::dalloc(&P->d_pool[l], sizeof(PoolJob) * cnt);
             if (e == cudaSuccess) e = cudaMemcpy(P->d_pool[l], jobs.data(), sizeof(PoolJob) * cnt, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return fail(NET_E_CUDA, "pool table: %s", cudaGetErrorString(e));
         } else {
@@ -334,7 +334,7 @@ void dn::uneven_free(net* n) {
     if (!n->uneven) return;
     for (auto& kv : n->uneven->plans) delete kv.second;
     for (int i = 0; i < 2; ++i)
-        if (n->uneven->buf[i]) cudaFree(n->uneven->buf[i]);
+        if (n->uneven->buf[i]) dn::dfree(n->uneven->buf[i]);
     delete n->uneven;
     n->uneven = nullptr;
 }

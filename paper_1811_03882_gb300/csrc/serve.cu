@@ -203,10 +203,10 @@ static net_status build_request_problems(net* n, ServeState* S, Request* r) {
 
 // Releases what serve_start allocated (any part may be missing).
 static void serve_free(ServeState* S) {
-    if (S->arena) cudaFree(S->arena);
+    if (S->arena) dn::dfree(S->arena);
     for (StepSlot& sl : S->slot) {
         if (sl.h_stage) cudaFreeHost(sl.h_stage);
-        if (sl.d_stage) cudaFree(sl.d_stage);
+        if (sl.d_stage) dn::dfree(sl.d_stage);
         if (sl.h_in) cudaFreeHost(sl.h_in);
         if (sl.h_out) cudaFreeHost(sl.h_out);
         if (sl.ev_in) cudaEventDestroy(sl.ev_in);
@@ -570,7 +570,7 @@ static net_status serve_start(net* n) {
     if (e != cudaSuccess) return fail(NET_E_CUDA, "serve start: %s", cudaGetErrorString(e));
     auto cleanup = [&] { serve_free(S.get()); };
     const size_t arena = std::min(n->budget, freeb / 2);
-    if ((e = cudaMalloc(&S->arena, arena)) != cudaSuccess) {
+    if ((e = dn::dalloc(&S->arena, arena)) != cudaSuccess) {
         cleanup();
         return fail(NET_E_OOM, "serving arena %zu bytes: %s", arena, cudaGetErrorString(e));
     }
@@ -599,7 +599,7 @@ static net_status serve_start(net* n) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->s_out, cudaStreamNonBlocking);
     for (StepSlot& sl : S->slot) {
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_stage, S->stage_bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&sl.d_stage, S->stage_bytes);
+        if (e == cudaSuccess) e = dn::dalloc(&sl.d_stage, S->stage_bytes);
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_in, S->h_in_floats * sizeof(float));
         if (e == cudaSuccess) e = cudaMallocHost(&sl.h_out, S->h_out_floats * sizeof(float));
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev_in, cudaEventDisableTiming);

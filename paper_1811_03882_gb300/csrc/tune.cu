@@ -130,8 +130,8 @@ extern "C" net_status net_tune_precision(net_t* n, const float* d_frames, int ba
     net_output_shape(n, h, w, &c, &ho, &wo);
     const size_t nout = (size_t)batch * c * ho * wo;
     float *d_ref = nullptr, *d_out = nullptr;
-    if (cudaMalloc(&d_ref, nout * sizeof(float)) != cudaSuccess || cudaMalloc(&d_out, nout * sizeof(float)) != cudaSuccess) {
-        cudaFree(d_ref);
+    if (dn::dalloc(&d_ref, nout * sizeof(float)) != cudaSuccess || dn::dalloc(&d_out, nout * sizeof(float)) != cudaSuccess) {
+        dn::dfree(d_ref);
         return fail(NET_E_OOM, "search buffers");
     }
     std::vector<float> ref(nout), out(nout);
@@ -221,8 +221,8 @@ extern "C" net_status net_tune_precision(net_t* n, const float* d_frames, int ba
     res->fp8_layers = feasible ? (int)std::count(best_g.begin(), best_g.end(), 1) : -1;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(d_ref);
-    cudaFree(d_out);
+    dn::dfree(d_ref);
+    dn::dfree(d_out);
     if (s != NET_OK) return s;
     if (!feasible) return fail(NET_E_STATE, "no plan within the error budget %g", opt->max_err);
     return NET_OK;
@@ -267,8 +267,8 @@ extern "C" net_status net_tune_tiles(net_t* n, const float* d_frames, int batch,
     net_output_shape(n, h, w, &c, &ho, &wo);
     const size_t nout = (size_t)batch * c * ho * wo;
     float *d_ref = nullptr, *d_out = nullptr;
-    if (cudaMalloc(&d_ref, nout * sizeof(float)) != cudaSuccess || cudaMalloc(&d_out, nout * sizeof(float)) != cudaSuccess) {
-        cudaFree(d_ref);
+    if (dn::dalloc(&d_ref, nout * sizeof(float)) != cudaSuccess || dn::dalloc(&d_out, nout * sizeof(float)) != cudaSuccess) {
+        dn::dfree(d_ref);
         for (int l = 0; l < nl; ++l) {
             n->L[l].tile_bn = saved_bn[l];
             n->L[l].tile_ks = saved_ks[l];
@@ -395,8 +395,8 @@ extern "C" net_status net_tune_tiles(net_t* n, const float* d_frames, int batch,
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(d_ref);
-    cudaFree(d_out);
+    dn::dfree(d_ref);
+    dn::dfree(d_out);
     if (s != NET_OK) return s;
     if (!found) return fail(NET_E_STATE, "no tile plan within the error budget %g", opt->max_err);
     return NET_OK;

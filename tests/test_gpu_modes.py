@@ -7,9 +7,9 @@ MMA over 8-channel pixels, and one CTA per SM everywhere (NET_TC_MB=1) or
 two wherever the N tile allows (NET_TC_MB=2, which also runs long A + B
 rings on half the shared memory and the 16-column epilogue), and CTA pairs
 (NET_TC_PAIR=1: 2-CTA clusters, one M = 256 tile a pair, on the layers that
-stream N tiles of 128 or 256 columns), and split-K through a reduction
-kernel (NET_TC_KSERIAL=0) instead of the last K slice adding the earlier
-slices' partials itself.  Every mode must give the oracle's answer within
+stream N tiles of 128 or 256 columns), and the generic kernel for the
+tap-pair first layer instead of its specialised variant (NET_TC_SPEC=0).
+Every mode must give the oracle's answer within
 the BF16 budget and agree with the default mode to BF16 rounding; the
 19-conv network at 2 x 160 x 160 has layers with one and with several work
 items per CTA, split-K layers and resident-weight layers."""
@@ -70,7 +70,7 @@ def test_launch_modes_match_oracle(tmp_path):
                       ("im2col", {"NET_L0_PAIR": "0"}), ("no_tapm", {"NET_TC_TAPM": "0"}),
                       ("mb1", {"NET_TC_MB": "1"}), ("mb2", {"NET_TC_MB": "2"}),
                       ("pair", {"NET_TC_PAIR": "1"}), ("pair_no_kalt", {"NET_TC_PAIR": "1", "NET_TC_KALT": "0"}),
-                      ("kserial_off", {"NET_TC_KSERIAL": "0"})):
+                      ("no_spec", {"NET_TC_SPEC": "0"})):
         y = _run(tmp_path, name, env)
         assert np.isfinite(y).all(), name
         e = oracle.normwise_rel_err(y, ex)
@@ -79,9 +79,8 @@ def test_launch_modes_match_oracle(tmp_path):
         ys[name] = y
     # programmatic launch changes only when kernels start, never what they add
     np.testing.assert_array_equal(ys["no_pdl"], ys["default"])
-    # serial split-K adds the slices' partials in the reduction kernel's order
-    # (the 160 x 160 plan splits layers 4 and 8 ways)
-    np.testing.assert_array_equal(ys["kserial_off"], ys["default"])
+    # the first-layer specialisation runs the generic kernel's operations
+    np.testing.assert_array_equal(ys["no_spec"], ys["default"])
     # a CTA pair accumulates every row's products in the single-CTA order of
     # one MMA issuer: the same bits as that mode
     np.testing.assert_array_equal(ys["pair_no_kalt"], ys["no_kalt"])
