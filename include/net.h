@@ -467,9 +467,10 @@ net_status net_inject_device_fault(net_t* net, int layer);
  * process first allocates, every device buffer the library allocates
  * (activations, weights, workspaces, staging, detection, nightmare, Jacobi
  * and serving buffers) has 4 KB of 0xA5 bytes directly before and after
- * it.  net_guard_check synchronises each device that holds one, copies the
- * regions to the host and reports the buffers checked and how many have a
- * changed region (a write past an end); both 0 when guards are off.  Host
+ * it.  A buffer's regions are checked when the library frees it (after a
+ * device synchronisation); net_guard_check also checks every live buffer
+ * and reports all buffers checked so far (freed and live) and how many had
+ * a changed region (a write past an end); both 0 when guards are off.  Host
  * memory is untouched; the regions are freed with their buffers. */
 net_status net_guard_check(uint64_t* buffers, uint64_t* corrupted);
 

@@ -22,12 +22,10 @@
 // per (frame, class) sorts its list by a 64-bit key (inverted score bits,
 // id; bitonic, keys in registers), so the result does not depend on the
 // order the atomics appended in, and suppresses in blocks of 32 candidates:
-// the overlaps inside each block are found in parallel first; then, round
-// by round, one warp settles blocks by bit operations while the other warps
-// drop the later candidates that the previous round's kept boxes overlap
-// (the decisions of one-at-a-time greedy NMS, one barrier a round).  The
-// last CTA of a frame to finish concatenates the frame's classes into its
-// detection rows.
+// the overlaps inside each block are found in parallel first, then a warp
+// settles a block by bit operations and the CTA drops what its kept boxes
+// overlap (the decisions of one-at-a-time greedy NMS).  The last CTA of a
+// frame to finish concatenates the frame's classes into its detection rows.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -243,11 +241,11 @@ __host__ __device__ constexpr int nms_threads(int logp) { return (1 << logp) < 1
 // shuffles, in the same thread by register pairs, across warps through
 // shared memory (two buffers, so one barrier per such stage).  Suppression
 // in blocks of 32 in rank order: first, for every candidate, the bits of the
-// later candidates of its block that it overlaps (all threads); then, in
-// rounds, warp 0 settles blocks (the first alive candidate is kept and drops
-// the later ones it overlaps, and so on) while the other warps apply the
-// previous round's kept boxes to the candidates after them.  These are the
-// decisions of greedy NMS taken one candidate at a time.
+// later candidates of its block that it overlaps (all threads); then per
+// block warp 0 settles who is kept (the first alive candidate is kept and
+// drops the later ones it overlaps, and so on), and the CTA drops every
+// later candidate that a kept one overlaps.  These are the decisions of
+// greedy NMS taken one candidate at a time.
 template <int LOGP>
 __global__ void __launch_bounds__(nms_threads(LOGP)) region_nms_kernel(int C, int maxc, float iou_thr,
                                                                        int max_det, int* cnt, RegionCand* cand,
@@ -267,8 +265,8 @@ __global__ void __launch_bounds__(nms_threads(LOGP)) region_nms_kernel(int C, in
     unsigned* pre = reinterpret_cast<unsigned*>(sm + lay.pre);
     unsigned char* supp = sm + lay.supp;
     int* prefix = reinterpret_cast<int*>(sm + lay.prefix);
-    __shared__ unsigned s_kept[2];
-    __shared__ int s_r0[2], s_last;
+    __shared__ unsigned s_kept;
+    __shared__ int s_r0, s_last;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int f = blockIdx.x / C, c = blockIdx.x - f * C;
@@ -367,41 +365,20 @@ __global__ void __launch_bounds__(nms_threads(LOGP)) region_nms_kernel(int C, in
         pre[r] = bits;
     }
     __syncthreads();
-    // Rounds, one barrier each.  In a round, warps 1.. drop every candidate
-    // from the round's first block on that the previous round's kept boxes
-    // (K, block kb) overlap, while warp 0 settles blocks from that first
-    // block on, checking each against K itself first (both may mark the same
-    // candidate suppressed: the same decision), until a block keeps a box;
-    // that block's kept boxes are the next round's K.  Every block is
-    // settled by warp 0 after every earlier kept box was applied to it: by
-    // the warps in an earlier round, or by warp 0's own check against K.
-    int r0 = 0;                // first block warp 0 settles this round
-    unsigned K = 0;            // previous round's kept boxes (bits of block kb)
-    int kb = 0;
-    // warp 0 publishes a round's result in slot (round & 1): it may write the
-    // next slot while the other warps still read this one
-    for (int round = 0;; ++round) {
+    int r0 = 0;
+    for (;;) {
         if (tid < 32) {
+            // settle blocks until one keeps a box (or the list ends): the
+            // first alive candidate is kept and drops the later ones of the
+            // block it overlaps, then the next alive one, and so on (one step
+            // per kept candidate)
             unsigned kept = 0;
-            int rb = r0;
-            while (rb < n) {
-                const int r = rb + lane;
-                bool alive = r < n && !supp[r];
-                if (alive && K) {
-                    const float4 er = edge[r];
-                    const float ar = area[r];
-                    for (unsigned mm = K; mm; mm &= mm - 1) {
-                        const int q = kb + __ffs(mm) - 1;
-                        if (overlaps(edge[q], area[q], er, ar, iou_thr)) {
-                            alive = false;
-                            break;
-                        }
-                    }
-                }
-                // the first alive candidate is kept and drops the later ones of
-                // the block it overlaps, then the next alive one, and so on
+            while (r0 < n) {
+                const int r = r0 + lane;
+                const bool alive = r < n && !supp[r];
                 unsigned live = __ballot_sync(0xffffffffu, alive);
                 const unsigned post = r < n ? pre[r] : 0u;
+                kept = 0;
                 while (live) {
                     const int q = __ffs(live) - 1;
                     kept |= 1u << q;
@@ -410,30 +387,30 @@ __global__ void __launch_bounds__(nms_threads(LOGP)) region_nms_kernel(int C, in
                 }
                 if (r < n) supp[r] = ((kept >> lane) & 1u) ? 0 : 1;
                 if (kept) break;
-                rb += 32;
+                r0 += 32;
             }
             if (lane == 0) {
-                s_kept[round & 1] = kept;
-                s_r0[round & 1] = rb;
-            }
-        } else if (K) {
-            for (int q = r0 + (tid - 32); q < n; q += T - 32) {
-                if (supp[q]) continue;
-                const float4 eq = edge[q];
-                const float aq = area[q];
-                bool drop = false;
-                for (unsigned mm = K; mm; mm &= mm - 1) {
-                    const int b = kb + __ffs(mm) - 1;
-                    drop |= overlaps(edge[b], area[b], eq, aq, iou_thr);
-                }
-                if (drop) supp[q] = 1;
+                s_kept = kept;
+                s_r0 = r0;
             }
         }
         __syncthreads();
-        K = s_kept[round & 1];
-        kb = s_r0[round & 1];
-        r0 = kb + 32;
-        if (kb >= n) break;
+        const unsigned kept = s_kept;
+        r0 = s_r0;
+        if (r0 >= n) break;
+        for (int q = r0 + 32 + tid; q < n; q += T) {
+            if (supp[q]) continue;
+            const float4 eq = edge[q];
+            const float aq = area[q];
+            bool drop = false;
+            for (unsigned mm = kept; mm; mm &= mm - 1) {
+                const int b = r0 + __ffs(mm) - 1;
+                drop |= overlaps(edge[b], area[b], eq, aq, iou_thr);
+            }
+            if (drop) supp[q] = 1;
+        }
+        r0 += 32;
+        __syncthreads();
     }
     // kept ones to the front of the list, in rank order (warp 0, ballots)
     if (tid < 32) {

@@ -3,9 +3,10 @@
 // A debug aid for out-of-bounds writes (compute-sanitizer is not used):
 // with NET_GUARD=1 in the environment (read once, at the process's first
 // allocation), every device buffer the library allocates gets a 4 KB region
-// of 0xA5 bytes directly before and directly after it, and
-// net_guard_check compares every region with the pattern (copied back to
-// the host after a device synchronisation).  A kernel that writes past
+// of 0xA5 bytes directly before and directly after it.  A buffer's regions
+// are compared with the pattern when it is freed, and those of every live
+// buffer when net_guard_check runs (copied back to the host after a device
+// synchronisation); net_guard_check reports both.  A kernel that writes past
 // either end of a buffer, even by one byte, changes a region.  Without the
 // variable, allocation is a plain cudaMalloc.
 #include <cuda_runtime.h>
@@ -32,6 +33,7 @@ struct Region {
 };
 
 std::mutex g_mu;
+uint64_t g_freed = 0, g_freed_bad = 0;   // buffers checked at their free, and changed ones
 std::map<const void*, Region>& regions() {   // by buffer address, in address order
     static std::map<const void*, Region> m;
     return m;
@@ -43,6 +45,22 @@ bool guards_enabled() {
         return e && atoi(e) == 1;
     }();
     return on;
+}
+
+// Whether either region of r still holds the pattern everywhere (false and
+// *err set when a copy fails).  The device is synchronised first.
+bool regions_intact(const Region& r, cudaError_t* err) {
+    std::vector<unsigned char> h(kGuard);
+    *err = cudaSetDevice(r.device);
+    if (*err == cudaSuccess) *err = cudaDeviceSynchronize();
+    for (int side = 0; side < 2 && *err == cudaSuccess; ++side) {
+        const unsigned char* g = side ? r.base + kGuard + r.bytes : r.base;
+        *err = cudaMemcpy(h.data(), g, kGuard, cudaMemcpyDeviceToHost);
+        if (*err != cudaSuccess) break;
+        for (size_t i = 0; i < kGuard; ++i)
+            if (h[i] != kPattern) return false;
+    }
+    return true;
 }
 
 }  // namespace
@@ -74,9 +92,16 @@ cudaError_t dfree(void* p) {
         std::lock_guard<std::mutex> lk(g_mu);
         auto it = regions().find(p);
         if (it != regions().end()) {
-            unsigned char* base = it->second.base;
+            const Region r = it->second;
             regions().erase(it);
-            return cudaFree(base);
+            int cur = 0;
+            cudaGetDevice(&cur);
+            cudaError_t e = cudaSuccess;
+            const bool ok = regions_intact(r, &e);
+            ++g_freed;
+            if (!ok && e == cudaSuccess) ++g_freed_bad;
+            cudaSetDevice(cur);
+            return cudaFree(r.base);
         }
     }
     return cudaFree(p);
@@ -92,30 +117,20 @@ extern "C" net_status net_guard_check(uint64_t* buffers, uint64_t* corrupted) {
     std::lock_guard<std::mutex> lk(g_mu);
     int cur = 0;
     cudaGetDevice(&cur);
-    std::vector<unsigned char> h(kGuard);
+    uint64_t n = g_freed, bad = g_freed_bad;
     for (auto& kv : regions()) {
-        const Region& r = kv.second;
-        if (cudaSetDevice(r.device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        cudaError_t e = cudaSuccess;
+        const bool ok = regions_intact(kv.second, &e);
+        if (e != cudaSuccess) {
             cudaSetDevice(cur);
-            return dn::fail(NET_E_CUDA, "device %d: %s", r.device, cudaGetErrorString(cudaGetLastError()));
+            return dn::fail(NET_E_CUDA, "guard check: %s", cudaGetErrorString(e));
         }
-        bool bad = false;
-        for (int side = 0; side < 2 && !bad; ++side) {
-            const unsigned char* g = side ? r.base + kGuard + r.bytes : r.base;
-            if (cudaMemcpy(h.data(), g, kGuard, cudaMemcpyDeviceToHost) != cudaSuccess) {
-                cudaSetDevice(cur);
-                return dn::fail(NET_E_CUDA, "guard copy: %s", cudaGetErrorString(cudaGetLastError()));
-            }
-            for (size_t i = 0; i < kGuard; ++i)
-                if (h[i] != kPattern) {
-                    bad = true;
-                    break;
-                }
-        }
-        ++*buffers;
-        if (bad) ++*corrupted;
+        ++n;
+        if (!ok) ++bad;
     }
     cudaSetDevice(cur);
+    *buffers = n;
+    *corrupted = bad;
     return NET_OK;
 }
 

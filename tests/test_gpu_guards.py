@@ -2,8 +2,9 @@
 child process runs every kind of pass the library has with a guard region
 before and after each device buffer it allocates; afterwards no region may
 have changed (no kernel wrote past either end of a buffer).  Then one byte
-is written just past a buffer on the host side and the check must find
-exactly that buffer.  Every result is also compared with the same pass
+is written just past a live buffer on the host side and the check must
+find exactly that buffer.  Regions are checked when a buffer is freed and,
+for live buffers, when net_guard_check runs.  Every result is also compared with the same pass
 without guards, which must be bit-identical."""
 import os
 import subprocess
@@ -75,12 +76,19 @@ with binding.Jacobi(70, 2050) as J:
     out, k, ch = J.solve(synth.laplace_grid(74, 70, 2050, "random"), 0.0, 20)
     res["jacobi"] = out
 np.savez(sys.argv[1], **res)
-b, c = binding.guard_check()
+b, c = binding.guard_check()        # every buffer above was checked at its free
 print("GUARDS", b, c)
-if b:
-    binding.guard_poke(b // 2)
-    b2, c2 = binding.guard_check()
-    print("POKED", b2, c2)
+with make_net(spec9, prec="bf16", max_side=64) as net:   # live buffers
+    net.load_weights(blob9)
+    run_device(net, x9[:, :, :64, :64].copy())
+    b1, c1 = binding.guard_check()
+    print("LIVE", b1 - b, c1 - c)
+    if b1 > b:
+        binding.guard_poke(0)
+        b2, c2 = binding.guard_check()
+        print("POKED", b2 - b1, c2 - c1)
+b3, c3 = binding.guard_check()
+print("FREED", b3, c3)
 print("OK")
 '''
 
@@ -95,7 +103,7 @@ def _run(tmp_path, name, guard):
                        capture_output=True, text=True, timeout=900)
     assert r.returncode == 0 and "OK" in r.stdout, r.stdout[-2000:] + r.stderr[-3000:]
     lines = {l.split()[0]: [int(v) for v in l.split()[1:]] for l in r.stdout.splitlines()
-             if l.startswith(("GUARDS", "POKED"))}
+             if l.startswith(("GUARDS", "LIVE", "POKED", "FREED"))}
     return np.load(out), lines
 
 
@@ -108,10 +116,14 @@ def _lib():
 def test_no_pass_writes_past_a_buffer(tmp_path):
     ref, plain = _run(tmp_path, "plain", False)
     got, g = _run(tmp_path, "guarded", True)
-    assert plain["GUARDS"] == [0, 0]                 # guards off: nothing registered
+    assert plain["GUARDS"] == [0, 0]                 # guards off: nothing checked
     buffers, corrupted = g["GUARDS"]
-    print("guarded buffers %d, changed regions %d" % (buffers, corrupted))
+    print("guarded buffers %d (checked at their free), changed regions %d; live %s; after the poke %s; "
+          "at the end %s" % (buffers, corrupted, g["LIVE"], g["POKED"], g["FREED"]))
     assert buffers >= 40 and corrupted == 0
-    assert g["POKED"] == [buffers, 1]                # the planted overrun is found
+    live = g["LIVE"][0]
+    assert live >= 10 and g["LIVE"][1] == 0
+    assert g["POKED"] == [0, 1]                      # the planted overrun is found while live
+    assert g["FREED"][0] >= buffers + live and g["FREED"][1] == 1   # and once more at its free
     for k in ref.files:                              # guards change no result
         np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
