@@ -299,15 +299,14 @@ static net_status night_conv(net* n, const void* x, const void* w, int w_rows, v
                              int Cp, int k, const Epilogue& ep) {
     NightState* S = n->night;
     const int nc = ep.out_layout == LAYOUT_NCHW ? ep.cout : std::max(ep.out_cs, ep.cout);
-    int bn, th, tw;
-    simt_tile(nc, &bn, &th, &tw);
-    const int tx = cdiv(W, tw), ty = cdiv(H, th);
-    const int m_tiles = batch * tx * ty, n_tiles = cdiv(nc, bn);
+    const SimtGeom g = simt_geom(nc, ep.pool == POOL_S2, batch, H, W, false);
+    const int bn = g.bn;
+    const int m_tiles = g.m_tiles, n_tiles = cdiv(nc, bn);
     const int grid = m_tiles * n_tiles, nall = k * k * cdiv(Cp, 8);
     int ks = 1;
     if (grid < 2 * n->num_sms && nall >= 32) ks = std::max(1, std::min({cdiv(4 * n->num_sms, grid), nall / 16, 32}));
     if (ks > 1) {
-        const size_t need = (size_t)ks * m_tiles * th * tw * n_tiles * bn * sizeof(float);
+        const size_t need = (size_t)ks * m_tiles * g.px * n_tiles * bn * sizeof(float);
         if (need > S->ws_bytes) {
             NK(cudaStreamSynchronize(n->stream));
             dn::dfree(S->ws);
@@ -333,7 +332,8 @@ static net_status night_conv(net* n, const void* x, const void* w, int w_rows, v
     NK(conv_simt(c, n->stream));
     ++n->launches;
     if (ks > 1) {
-        SplitReduce sr{S->ws, ks, m_tiles * th * tw, n_tiles * bn, tw, th, tx, ty, batch, H, W, y, ep};
+        SplitReduce sr{S->ws, ks, m_tiles * g.px, n_tiles * bn, g.red_tw, g.red_th, g.red_tx, g.red_ty, batch, H, W,
+                       y, ep};
         NK(splitk_reduce(sr, n->stream));
         ++n->launches;
     }

@@ -9,44 +9,68 @@
 // Tile: a TH x TW rectangle of output pixels of one frame times BN output
 // channels; 256 threads.  Pixels are ordered by 2x2 quads inside the tile
 // and every thread owns whole quads, so the fused 2x2/s2 max pool of the
-// epilogue is a register-local max.
+// epilogue is a register-local max.  Layers without that pool may instead
+// take PXF consecutive output pixels in (frame, row, column) order (flat
+// tiles): no rectangle to round up to, so a 13 x 13 map computes 192
+// pixels instead of the 256 of two 8 x 16 rectangles.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace dn {
 
-template <int BN, int TH, int TW>
+template <int BN, int TH, int TW, int PXF>
 struct SimtCfg {
     static constexpr int THREADS = 256;
-    static constexpr int PX = TH * TW;          // pixels per tile
+    static constexpr int PX = PXF ? PXF : TH * TW;   // pixels per tile
     static constexpr int CG = BN / 4;           // channel groups (4 ch each)
     static constexpr int PG = THREADS / CG;     // pixel groups
     static constexpr int PPT = PX / PG;         // pixels per thread
     static constexpr int QX = TW / 2;           // quads per tile row
     static constexpr int BK = 8;                // channels per K step
-    static constexpr int A_VEC = PX * BK / 4 / THREADS;  // float4 loads per thread (A)
+    static constexpr int A_SLOTS = PX * BK / 4;              // float4 loads (A)
+    static constexpr int A_VEC = (A_SLOTS + THREADS - 1) / THREADS;   // per thread
     static constexpr int B_VEC_TOTAL = BN * BK / 4;      // float4 loads (B)
-    static_assert(PPT % 4 == 0, "threads must own whole 2x2 quads");
-    static_assert(A_VEC >= 1 && (PX * BK / 4) % THREADS == 0, "A tile split");
+    static_assert(PPT % 4 == 0 && PX == PG * PPT, "threads own four-pixel groups (2x2 quads)");
+    static_assert(PXF ? true : A_SLOTS % THREADS == 0, "A tile split");
     static_assert(B_VEC_TOTAL <= THREADS, "B tile split");
 };
 
-template <int BN, int TH, int TW>
-__global__ void __launch_bounds__(256)
+// PXF > 0: flat tiles of PXF pixels (no 2x2/s2 pool); nfr frames.  Flat
+// tiles are held to two CTAs an SM's registers.
+template <int BN, int TH, int TW, int PXF>
+__global__ void __launch_bounds__(256, PXF ? 2 : 1)
 conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
                  void* __restrict__ y, int H, int W, int Cp, int k, int kw_rows,
                  int tiles_x, int tiles_y, Epilogue ep, int ksplit, float* __restrict__ ws,
-                 int ws_cols) {
-    using C = SimtCfg<BN, TH, TW>;
+                 int ws_cols, int nfr) {
+    using C = SimtCfg<BN, TH, TW, PXF>;
+    constexpr bool FLAT = PXF > 0;
     __shared__ __align__(16) float As[2][C::BK][C::PX];
     __shared__ __align__(16) float Bs[2][C::BK][BN];
 
     const int tid = threadIdx.x;
     int t = blockIdx.x;
-    const int tx = t % tiles_x; t /= tiles_x;
-    const int ty = t % tiles_y;
-    const int n = t / tiles_y;
+    const int tx = FLAT ? 0 : t % tiles_x;
+    if (!FLAT) t /= tiles_x;
+    const int ty = FLAT ? 0 : t % tiles_y;
+    const int n = FLAT ? 0 : t / tiles_y;
     const int y0 = ty * TH, x0 = tx * TW;
+    // flat tiles: first pixel of the tile and pixels in the layer
+    const int m0 = blockIdx.x * C::PX, mtot = nfr * H * W;
+    // flat tiles: each A load slot's pixel, decoded once (frame, row, column;
+    // frame -1 past the layer's last pixel)
+    int sn[C::A_VEC], sy[C::A_VEC], sx[C::A_VEC];
+    if (FLAT) {
+#pragma unroll
+        for (int v = 0; v < C::A_VEC; ++v) {
+            const int m = m0 + ((tid + v * C::THREADS) >> 1);
+            const int row = m / W;
+            sx[v] = m - row * W;
+            sn[v] = row / H;
+            sy[v] = row - sn[v] * H;
+            if (m >= mtot || tid + v * C::THREADS >= C::A_SLOTS) sn[v] = -1;
+        }
+    }
     const int n0 = blockIdx.y * BN;
     const int pad = k / 2;
     const int KK = k * k;
@@ -69,13 +93,22 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
         for (int v = 0; v < C::A_VEC; ++v) {
             const int f = tid + v * C::THREADS;
             const int pos = f >> 1, half = f & 1;
-            const int q = pos >> 2, dy = (pos >> 1) & 1, dx = pos & 1;
-            const int py = 2 * (q / C::QX) + dy, px = 2 * (q % C::QX) + dx;
-            const int iy = y0 + py + kh - pad, ix = x0 + px + kwi - pad;
+            int iy, ix, nn;
+            if (FLAT) {
+                nn = sn[v];
+                iy = sy[v] + kh - pad;
+                ix = sx[v] + kwi - pad;
+            } else {
+                const int q = pos >> 2, dy = (pos >> 1) & 1, dx = pos & 1;
+                const int py = 2 * (q / C::QX) + dy, px = 2 * (q % C::QX) + dx;
+                nn = n;
+                iy = y0 + py + kh - pad;
+                ix = x0 + px + kwi - pad;
+            }
             const int c = c0 + half * 4;
             float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (iy >= 0 && iy < H && ix >= 0 && ix < W && c < Cp)
-                val = *reinterpret_cast<const float4*>(x + (((size_t)n * H + iy) * W + ix) * Cp + c);
+            if (nn >= 0 && iy >= 0 && iy < H && ix >= 0 && ix < W && c < Cp)
+                val = *reinterpret_cast<const float4*>(x + (((size_t)nn * H + iy) * W + ix) * Cp + c);
             ra[v] = val;
         }
         if (tid < C::B_VEC_TOTAL) {
@@ -91,6 +124,7 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
 #pragma unroll
         for (int v = 0; v < C::A_VEC; ++v) {
             const int f = tid + v * C::THREADS;
+            if (FLAT && f >= C::A_SLOTS) continue;
             const int pos = f >> 1, kb = (f & 1) * 4;
             As[buf][kb + 0][pos] = ra[v].x;
             As[buf][kb + 1][pos] = ra[v].y;
@@ -154,7 +188,8 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
             const int pos = pg * C::PPT + i;
             const int q = pos >> 2;
             const int py = 2 * (q / C::QX) + ((pos >> 1) & 1), px = 2 * (q % C::QX) + (pos & 1);
-            *reinterpret_cast<float4*>(wz + (mbase + py * TW + px) * ws_cols + obase) =
+            // flat tiles: row = pixel index; rows past the layer are never read
+            *reinterpret_cast<float4*>(wz + (mbase + (FLAT ? pos : py * TW + px)) * ws_cols + obase) =
                 make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
         }
         return;
@@ -170,6 +205,50 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
     }
     const bool pool = ep.pool == POOL_S2;
     const int Ho = pool ? H / 2 : H, Wo = pool ? W / 2 : W;
+    if constexpr (FLAT) {
+        // no pool: each of the thread's pixels on its own
+#pragma unroll
+        for (int i = 0; i < C::PPT; ++i) {
+            const int m = m0 + pg * C::PPT + i;
+            if (m >= mtot) continue;
+            float o4[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) o4[j] = act_apply(fmaf(acc[i][j], alp[j], bia[j]), ep.act);
+            if (ep.out_layout == LAYOUT_NCHW) {
+                const int row = m / W, xo = m - row * W, img = row / H, yo = row - img * H;
+                float* yf = reinterpret_cast<float*>(y);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int o = obase + j;
+                    if (o < ep.cout) yf[(((size_t)img * ep.cout + o) * H + yo) * W + xo] = o4[j];
+                }
+                continue;
+            }
+            if (obase >= ep.out_cs) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (obase + j >= ep.cout) o4[j] = 0.f;
+            const size_t off = (size_t)m * ep.out_cs + obase;   // NHWC: pixel m's row
+            if (ep.out_dt == DT_F32) {
+                *reinterpret_cast<float4*>(reinterpret_cast<float*>(y) + off) =
+                    make_float4(o4[0], o4[1], o4[2], o4[3]);
+            } else if (ep.out_dt == DT_BF16) {
+                __nv_bfloat162 lo = __floats2bfloat162_rn(o4[0], o4[1]);
+                __nv_bfloat162 hi = __floats2bfloat162_rn(o4[2], o4[3]);
+                uint2 pk;
+                pk.x = *reinterpret_cast<uint32_t*>(&lo);
+                pk.y = *reinterpret_cast<uint32_t*>(&hi);
+                *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(y) + off) = pk;
+            } else {
+                uint32_t pk = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    pk |= (uint32_t)f32_to_e4m3_sat(o4[j] * ep.out_inv_scale) << (8 * j);
+                *reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(y) + off) = pk;
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int qi = 0; qi < C::PPT / 4; ++qi) {
         const int q = (pg * C::PPT) / 4 + qi;
@@ -234,15 +313,15 @@ conv_simt_kernel(const float* __restrict__ x, const float* __restrict__ w,
     }
 }
 
-template <int BN, int TH, int TW>
-static cudaError_t launch_simt(const ConvLaunch& L, int ncols, cudaStream_t st) {
+template <int BN, int TH, int TW, int PXF>
+static cudaError_t launch_simt(const ConvLaunch& L, int ncols, int m_tiles, cudaStream_t st) {
     const int tiles_x = cdiv(L.W, TW), tiles_y = cdiv(L.H, TH);
     const int ks = L.ksplit > 1 ? L.ksplit : 1;
     const int n_tiles = cdiv(ncols, BN);
-    dim3 grid((unsigned)(L.n * tiles_x * tiles_y), (unsigned)n_tiles, (unsigned)ks);
-    conv_simt_kernel<BN, TH, TW><<<grid, 256, 0, st>>>(
+    dim3 grid((unsigned)m_tiles, (unsigned)n_tiles, (unsigned)ks);
+    conv_simt_kernel<BN, TH, TW, PXF><<<grid, 256, 0, st>>>(
         reinterpret_cast<const float*>(L.x), reinterpret_cast<const float*>(L.w), L.y, L.H, L.W,
-        L.Cp, L.k, L.w_rows, tiles_x, tiles_y, L.ep, ks, L.ws, n_tiles * BN);
+        L.Cp, L.k, L.w_rows, tiles_x, tiles_y, L.ep, ks, L.ws, n_tiles * BN, L.n);
     return cudaGetLastError();
 }
 
@@ -252,14 +331,34 @@ void simt_tile(int ncols, int* bn, int* th, int* tw) {
     else { *bn = 64; *th = 8; *tw = 16; }
 }
 
+constexpr int kFlatPx = 192;   // flat tile pixels (64-column tiles: 12 pixels a thread)
+
+SimtGeom simt_geom(int ncols, bool pool, int n, int H, int W, bool quads) {
+    SimtGeom g;
+    simt_tile(ncols, &g.bn, &g.th, &g.tw);
+    const long quad_px = (long)n * cdiv(H, g.th) * g.th * cdiv(W, g.tw) * g.tw;
+    const long flat_tiles = cdiv((long)n * H * W, (long)kFlatPx);
+    // flat tiles where they compute fewer pixels (64-column tiles, no pool)
+    g.flat = (!pool && !quads && g.bn == 64 && flat_tiles * kFlatPx < quad_px) ? 1 : 0;
+    g.px = g.flat ? kFlatPx : g.th * g.tw;
+    g.m_tiles = g.flat ? (int)flat_tiles : n * cdiv(H, g.th) * cdiv(W, g.tw);
+    // split-K reduction geometry: flat rows are pixel indices, i.e. one
+    // H x W "tile" per frame
+    g.red_tw = g.flat ? W : g.tw;
+    g.red_th = g.flat ? H : g.th;
+    g.red_tx = g.flat ? 1 : cdiv(W, g.tw);
+    g.red_ty = g.flat ? 1 : cdiv(H, g.th);
+    return g;
+}
+
 cudaError_t conv_simt(const ConvLaunch& L, cudaStream_t st) {
     const int ncols = L.ep.out_layout == LAYOUT_NCHW ? L.ep.cout
                                                       : (L.ep.out_cs > L.ep.cout ? L.ep.out_cs : L.ep.cout);
-    int bn, th, tw;
-    simt_tile(ncols, &bn, &th, &tw);
-    if (bn == 16) return launch_simt<16, 16, 16>(L, ncols, st);
-    if (bn == 32) return launch_simt<32, 8, 16>(L, ncols, st);
-    return launch_simt<64, 8, 16>(L, ncols, st);
+    const SimtGeom g = simt_geom(ncols, L.ep.pool == POOL_S2, L.n, L.H, L.W, L.quads != 0);
+    if (g.bn == 16) return launch_simt<16, 16, 16, 0>(L, ncols, g.m_tiles, st);
+    if (g.bn == 32) return launch_simt<32, 8, 16, 0>(L, ncols, g.m_tiles, st);
+    if (g.flat) return launch_simt<64, 8, 16, kFlatPx>(L, ncols, g.m_tiles, st);
+    return launch_simt<64, 8, 16, 0>(L, ncols, g.m_tiles, st);
 }
 
 }  // namespace dn

@@ -17,13 +17,24 @@ struct ConvLaunch {
     int k;           // 1 or 3
     int w_rows;      // allocated weight rows (>= every column a tile touches)
     Epilogue ep;
-    int bn, th, tw;  // tile: th x tw pixels x bn channels (0: choose from ep)
+    int bn, th, tw;  // unused by the CUDA-core conv (simt_geom chooses the tile)
+    int quads;       // 1: 2x2-quad tiles even without a pool (0: flat tiles where they save work)
     int ksplit;      // > 1: K split over grid.z, raw sums to ws
     float* ws;       // split-K partial sums [ksplit][m_tiles*th*tw][n_tiles*bn]
 };
 
 // CUDA-core tile choice for a layer with `ncols` output columns.
 void simt_tile(int ncols, int* bn, int* th, int* tw);
+// Geometry of a CUDA-core conv launch: N tile bn; th x tw quad tiles, or
+// (flat = 1: 64-column tiles without a 2x2/s2 pool, where that computes
+// fewer pixels; never when `quads`) runs of px consecutive output pixels;
+// m_tiles tiles of px pixels (the split-K workspace has m_tiles * px rows);
+// red_*: the SplitReduce tile fields for that workspace.
+struct SimtGeom {
+    int bn, th, tw, flat, px, m_tiles;
+    int red_tw, red_th, red_tx, red_ty;
+};
+SimtGeom simt_geom(int ncols, bool pool, int n, int H, int W, bool quads);
 cudaError_t conv_simt(const ConvLaunch& L, cudaStream_t st);
 
 // Split-K reduction + epilogue: y = epilogue(sum_z ws[z]) in fixed z order.

@@ -545,14 +545,15 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
         const int KK = L.kx * L.kx;
         if (L.engine == ENG_SIMT) {
             simt_tile(ncols, &r.sbn, &r.sth, &r.stw);
-            r.m_tiles = batch * cdiv(r.H, r.sth) * cdiv(r.W, r.stw);
+            const SimtGeom g = simt_geom(ncols, L.d.pool == NET_POOL_2X2S2, batch, r.H, r.W, false);
+            r.m_tiles = g.m_tiles;
             r.n_tiles = cdiv(ncols, r.sbn);
             const int grid = r.m_tiles * r.n_tiles;
             const int nall = KK * cdiv(L.in_cs, 8);
             if (grid < 2 * n->num_sms && nall >= 32)
                 r.ksplit = std::max(1, std::min({cdiv(4 * n->num_sms, grid), nall / 16, 32}));
             if (r.ksplit > 1)
-                P->ws_bytes = std::max(P->ws_bytes, (size_t)r.ksplit * r.m_tiles * r.sth * r.stw *
+                P->ws_bytes = std::max(P->ws_bytes, (size_t)r.ksplit * r.m_tiles * g.px *
                                                         r.n_tiles * r.sbn * sizeof(float));
         }
         if (L.engine == ENG_TC) {
@@ -799,11 +800,9 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 if (e == cudaSuccess && c.ksplit > 1) {
                     ++n->pending;
                     const int nc = ep.out_layout == LAYOUT_NCHW ? ep.cout : std::max(ep.out_cs, ep.cout);
-                    int bn, th, tw;
-                    simt_tile(nc, &bn, &th, &tw);
-                    const int tx = cdiv(W[l], tw), ty = cdiv(H[l], th);
-                    SplitReduce sr{n->ws, c.ksplit, batch * tx * ty * th * tw, cdiv(nc, bn) * bn, tw, th,
-                                   tx, ty, batch, H[l], W[l], y, ep};
+                    const SimtGeom g = simt_geom(nc, ep.pool == POOL_S2, batch, H[l], W[l], false);
+                    SplitReduce sr{n->ws, c.ksplit, g.m_tiles * g.px, cdiv(nc, g.bn) * g.bn, g.red_tw, g.red_th,
+                                   g.red_tx, g.red_ty, batch, H[l], W[l], y, ep};
                     e = splitk_reduce(sr, st);
                 }
             }

@@ -131,6 +131,7 @@ extern "C" net_status net_conv2d_f32_noalloc(const float* d_x, int n, int cin, i
     c.ep.out_cs = cout;
     c.ep.cout = cout;
     c.ksplit = ksplit;
+    c.quads = 1;   // the scratch bound above assumes quad tiles
     c.ws = s_ws;
     if (e == cudaSuccess) e = conv_simt(c, st);
     if (e == cudaSuccess && ksplit > 1) {
