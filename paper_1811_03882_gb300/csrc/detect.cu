@@ -152,19 +152,26 @@ __global__ void region_decode_kernel(const float* __restrict__ map, int batch, i
         const float os = obj / sum;   // class-c score = obj * e_c / sum
 #pragma unroll
         for (int c = 0; c < 32; ++c) e[c] *= os;
-        if (peers == 0xffffffffu) {
-            // the whole warp is one frame: lane c reserves class c's slots, all
-            // classes' atomics in flight together
+        // lane c reserves class c's slots for the lanes of one frame, all
+        // classes' atomics in flight together; a warp that straddles frames
+        // does this once per frame
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        unsigned rem = vmask;
+        while (rem) {   // warp-uniform
+            const int leader = __ffs(rem) - 1;
+            const unsigned grp = __shfl_sync(0xffffffffu, peers, leader) & vmask;   // the leader's frame
+            const bool in = (grp >> lane) & 1u;
             unsigned mine = 0;
 #pragma unroll
             for (int c = 0; c < 32; ++c) {
                 if (c < C) {
-                    const unsigned b = __ballot_sync(0xffffffffu, valid && e[c] > thresh);
+                    const unsigned b = __ballot_sync(0xffffffffu, in && e[c] > thresh);
                     if (lane == c) mine = b;
                 }
             }
+            int* gcnt = cnt + (long long)__shfl_sync(0xffffffffu, f, leader) * (C + 1);
             int base = 0;
-            if (mine) base = atomicAdd(&fcnt[lane], __popc(mine));
+            if (mine) base = atomicAdd(&gcnt[lane], __popc(mine));
 #pragma unroll
             for (int c = 0; c < 32; ++c) {
                 if (c < C) {
@@ -173,10 +180,7 @@ __global__ void region_decode_kernel(const float* __restrict__ map, int batch, i
                     if ((b >> lane) & 1u) put(c, bc + __popc(b & ((1u << lane) - 1u)), e[c]);
                 }
             }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 32; ++c)
-                if (c < C) append(c, e[c]);
+            rem &= ~grp;
         }
     } else {
         float m = lg[0];
