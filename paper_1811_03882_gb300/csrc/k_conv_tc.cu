@@ -282,6 +282,52 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// A TMEM load split in two: issue now, wait later, so that independent work
+// runs in between.  The wait names the destination registers as read-write
+// operands, so no use of them can be scheduled before it.
+template <int CW>
+__device__ __forceinline__ void tmem_ld_issue(uint32_t taddr, uint32_t* r) {
+    if constexpr (CW == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
+            " [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15])
+            : "r"(taddr));
+    }
+}
+template <int CW>
+__device__ __forceinline__ void tmem_ld_wait(uint32_t* r) {
+    if constexpr (CW == 32) {
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                       "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                       "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]),
+                       "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]),
+                       "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                     :
+                     : "memory");
+    } else {
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                       "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]),
+                       "+r"(r[14]), "+r"(r[15])
+                     :
+                     : "memory");
+    }
+}
+
 template <int CW>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
     if constexpr (CW == 32) tmem_ld32(taddr, v);
@@ -851,7 +897,120 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         FastDiv fTX, fTY;
         int tcount = 0;
         bool have_p = false;   // problem fields loaded (single-problem launches read them once)
-        for (int tile = worker; tile < total; tile += nworkers, ++tcount) {
+        bool pairs_done = false;
+        if constexpr (SP == 1) {
+            // The tap-pair first layer, one problem, one N tile, at most CW
+            // live columns: a warpgroup drains its next two tiles (tcount t and
+            // t + 2, accumulator buffers t & 3 and (t + 2) & 3) in one pass, so
+            // that their two dependent chains (TMEM load, tile decode,
+            // arithmetic, pool shuffles, stores) overlap.  The MMA issuer needs
+            // those buffers back only for tiles t + 4 and t + 6.  Same
+            // operations per element as the loop below.
+            static_assert(SP != 1 || NBUF == 4, "two tiles a pass take four accumulator buffers");
+            if (a.nprob == 1 && a.n_tiles == 1 && live <= CW) {
+                pairs_done = true;
+                const ConvProblem& P0 = a.probs[0];
+                void* ybase = a.y_override ? a.y_override : P0.y;
+                const int H0 = P0.H, W0 = P0.W, TX0 = P0.tiles_x, TY0 = P0.tiles_y, B0 = P0.tile_begin;
+                const FastDiv fx = P0.fd_tx, fy = P0.fd_ty;
+                const int Ho = pool ? H0 / 2 : H0, Wo = pool ? W0 / 2 : W0;
+                float bb[CW];   // the live columns' bias, once
+#pragma unroll
+                for (int j = 0; j < CW / 4; ++j) {
+                    const float4 t = reinterpret_cast<const float4*>(e_bias)[j];
+                    bb[4 * j] = t.x;
+                    bb[4 * j + 1] = t.y;
+                    bb[4 * j + 2] = t.z;
+                    bb[4 * j + 3] = t.w;
+                }
+                const uint32_t tlane = tmem_base + ((uint32_t)(q * 32) << 16);
+                auto finish = [&](int mt, const uint32_t* r) {
+                    const int local = mt - B0;
+                    const int txy = fdiv(local, fx);
+                    const int tx = local - txy * TX0;
+                    const int img = fdiv(txy, fy);
+                    const int ty = txy - img * TY0;
+                    const int gy = ty * a.TH + py, gx = tx * a.TW + px;
+                    const bool valid = gy < H0 && gx < W0;
+                    const int yo = pool ? gy / 2 : gy, xo = pool ? gx / 2 : gx;
+                    const bool writer = valid && (!pool || ((lane & 1) == 0 && (lane & ymask) == 0));
+                    const size_t pix = ((size_t)img * Ho + yo) * Wo + xo;
+                    float v[CW];
+#pragma unroll
+                    for (int j = 0; j < CW / 2; ++j) {
+                        const float2 s = __fadd2_rn(make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])),
+                                                    make_float2(bb[2 * j], bb[2 * j + 1]));
+                        v[2 * j] = s.x;
+                        v[2 * j + 1] = s.y;
+                    }
+                    if (a.ep.act == ACT_LEAKY) {
+                        const float2 slope = make_float2(kLeakySlope, kLeakySlope);
+#pragma unroll
+                        for (int j = 0; j < CW / 2; ++j) {
+                            const float2 s2 = __fmul2_rn(make_float2(v[2 * j], v[2 * j + 1]), slope);
+                            v[2 * j] = fmaxf(v[2 * j], s2.x);
+                            v[2 * j + 1] = fmaxf(v[2 * j + 1], s2.y);
+                        }
+                    }
+                    uint32_t w[CW / 2];
+#pragma unroll
+                    for (int j = 0; j < CW / 2; ++j) {
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        w[j] = *reinterpret_cast<uint32_t*>(&h2);
+                    }
+                    if (pool) {
+#pragma unroll
+                        for (int j = 0; j < CW / 2; ++j) {
+                            uint32_t o = __shfl_xor_sync(0xffffffffu, w[j], 1);
+                            __nv_bfloat162 m = __hmax2(*reinterpret_cast<__nv_bfloat162*>(&w[j]),
+                                                       *reinterpret_cast<__nv_bfloat162*>(&o));
+                            w[j] = *reinterpret_cast<uint32_t*>(&m);
+                            o = __shfl_xor_sync(0xffffffffu, w[j], ymask);
+                            m = __hmax2(*reinterpret_cast<__nv_bfloat162*>(&w[j]),
+                                        *reinterpret_cast<__nv_bfloat162*>(&o));
+                            w[j] = *reinterpret_cast<uint32_t*>(&m);
+                        }
+                    }
+                    if (writer) {
+                        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ybase) +
+                                                              pix * a.ep.out_cs);
+                        const int nvec = a.ep.out_cs >= CW ? CW / 8 : 2;
+#pragma unroll
+                        for (int i = 0; i < CW / 8; ++i)
+                            if (i < nvec) dst[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+                    }
+                };
+                for (int tc = grp;; tc += 4) {
+                    const int tile0 = worker + tc * nworkers;
+                    if (tile0 >= total) break;
+                    const int tile1 = tile0 + 2 * nworkers;
+                    const bool has1 = tile1 < total;   // warp-uniform
+                    const int b0 = tc & 3, b1 = (tc + 2) & 3;
+                    if (!tc::mbar_wait(smem_u32(&sm->accf[b0]), (uint32_t)(tc >> 2) & 1u, abort_flag, a.err, 4, lim))
+                        break;
+                    if (has1 &&
+                        !tc::mbar_wait(smem_u32(&sm->accf[b1]), (uint32_t)((tc + 2) >> 2) & 1u, abort_flag, a.err, 4, lim))
+                        break;
+                    tc::fence_after();
+                    uint32_t r0[CW], r1[CW];
+                    __syncwarp();
+                    tc::tmem_ld_issue<CW>(tlane + (uint32_t)(b0 * BN), r0);
+                    if (has1) tc::tmem_ld_issue<CW>(tlane + (uint32_t)(b1 * BN), r1);
+                    tc::tmem_ld_wait<CW>(r0);
+                    if (has1) tc::tmem_ld_wait<CW>(r1);
+                    // both buffers back to the MMA issuer
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tc::mbar_arrive(smem_u32(&sm->acce[b0]));
+                        if (has1) tc::mbar_arrive(smem_u32(&sm->acce[b1]));
+                    }
+                    finish(tile0, r0);
+                    if (has1) finish(tile1, r1);
+                }
+            }
+        }
+        for (int tile = pairs_done ? total : worker; tile < total; tile += nworkers, ++tcount) {
             if (!C2 && !kKalt && (tcount & 1) != grp) continue;
             // the tile's accumulator (or pair of them in K-alternating mode)
             const int nsl_log = kKalt ? NBUF_LOG - 1 : NBUF_LOG;
