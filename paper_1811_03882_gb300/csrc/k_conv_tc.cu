@@ -385,17 +385,18 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     // SP = 1, the tap-pair first layer (tap pairs on tap-merged stages,
     // resident weights, one issuer a tile); SP = 2, any other BF16 layer; both
     // with no K split and BF16 NHWC output without alpha.  SP = 3, a BF16
-    // layer with a K split: its epilogue writes raw partial sums only.
-    static_assert(SP == 0 || (SP >= 1 && SP <= 3 && DT == DT_BF16 && CG == 1), "specialisations");
+    // layer with a K split: its epilogue writes raw partial sums only.  SP =
+    // 4, a BF16 last layer: no K split, FP32 NCHW output without alpha.
+    static_assert(SP == 0 || (SP >= 1 && SP <= 4 && DT == DT_BF16 && CG == 1), "specialisations");
     // (read where used, as the generic variant reads its launch arguments)
 #define kKalt (SP == 1 ? 0 : a.kalt)
 #define kTapm (SP == 1 ? 1 : a.tapm)
-#define kPair (SP == 1 ? 1 : SP == 2 ? 0 : a.pair)
+#define kPair (SP == 1 ? 1 : (SP == 2 || SP == 4) ? 0 : a.pair)
 #define kBres (SP == 1 ? 1 : a.bres)
-#define kKsplit ((SP == 1 || SP == 2) ? 1 : a.ksplit)
-#define kAlpha ((SP == 1 || SP == 2) ? (const float*)nullptr : a.ep.alpha)
-#define kOutLayout ((SP == 1 || SP == 2) ? (int)LAYOUT_NHWC : (int)a.ep.out_layout)
-#define kOutDt ((SP == 1 || SP == 2) ? (int)DT_BF16 : (int)a.ep.out_dt)
+#define kKsplit ((SP == 1 || SP == 2 || SP == 4) ? 1 : a.ksplit)
+#define kAlpha ((SP == 1 || SP == 2 || SP == 4) ? (const float*)nullptr : a.ep.alpha)
+#define kOutLayout ((SP == 1 || SP == 2) ? (int)LAYOUT_NHWC : SP == 4 ? (int)LAYOUT_NCHW : (int)a.ep.out_layout)
+#define kOutDt ((SP == 1 || SP == 2) ? (int)DT_BF16 : SP == 4 ? (int)DT_F32 : (int)a.ep.out_dt)
     static_assert(MB == 1 || (MB == 2 && BN <= 128), "two CTAs per SM: N tiles of at most 128 columns");
     static_assert(CG == 1 || (CG == 2 && MB == 1 && BN >= 128), "CTA pairs: one CTA an SM, N tiles of 128 or 256");
     constexpr bool C2 = CG == 2;
@@ -1443,7 +1444,8 @@ cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int 
     if (cg != 1) return cudaErrorInvalidValue;
     // BF16 layers run specialised variants: with a K split SP = 3; without
     // one and with BF16 NHWC output, the tap-pair first layer SP = 1 and the
-    // others SP = 2 (NET_TC_SPEC=0: the generic kernel)
+    // others SP = 2; a last layer with FP32 NCHW output SP = 4 (NET_TC_SPEC=0:
+    // the generic kernel)
     static const bool spec_on = [] {
         const char* e = getenv("NET_TC_SPEC");
         return !(e && atoi(e) == 0);
@@ -1454,6 +1456,12 @@ cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int 
             if (BN == 128) return launch_tc_bn<128, DT_BF16, 1, 1, 3>(tmB, a, workers, st);
             if (BN == 256) return launch_tc_bn<256, DT_BF16, 1, 1, 3>(tmB, a, workers, st);
         }
+    }
+    if (spec_on && dt == DT_BF16 && a.ksplit == 1 && !a.pair && a.ep.out_layout == LAYOUT_NCHW &&
+        a.ep.out_dt == DT_F32 && !a.ep.alpha && mb == 1) {   // the last layer
+        if (BN == 64) return launch_tc_bn<64, DT_BF16, 1, 1, 4>(tmB, a, workers, st);
+        if (BN == 128) return launch_tc_bn<128, DT_BF16, 1, 1, 4>(tmB, a, workers, st);
+        if (BN == 256) return launch_tc_bn<256, DT_BF16, 1, 1, 4>(tmB, a, workers, st);
     }
     if (spec_on && dt == DT_BF16 && a.ksplit == 1 && a.ep.out_layout == LAYOUT_NHWC && a.ep.out_dt == DT_BF16 &&
         !a.ep.alpha) {
