@@ -169,6 +169,20 @@ __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const void* tmap,
         : "memory");
 }
 
+// 16-byte store to this CTA's shared memory; 16-byte load from any CTA's
+// shared memory of the cluster (a cluster-window address)
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, float x, float y, float z, float w) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
+}
+__device__ __forceinline__ float4 ld_cluster_v4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
 // Shared-memory matrix descriptor (tcgen05), K-major operand with 32/64/128
 // byte swizzle: start >> 4, leading offset (unused for swizzled K-major) 16,
 // stride offset = 8 rows * row bytes, fixed version bits 46..48 = 0b001.
@@ -351,6 +365,9 @@ struct Smem {
     // single waiter, which a parity wait needs: with one barrier per stage the
     // second issuer could test a stage two phases ahead and pass on old data.
     uint64_t full[2][kMaxStages], empty[kMaxStages], accf[4], acce[4], done, bres;
+    // cluster split-K: every epilogue warp of every CTA of the cluster has
+    // written its partial sums (8 x ksplit arrivals)
+    uint64_t xfull;
     uint32_t tmem;
     int abort;
 };
@@ -387,14 +404,16 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     // with no K split and BF16 NHWC output without alpha.  SP = 3, a BF16
     // layer with a K split: its epilogue writes raw partial sums only.  SP =
     // 4, a BF16 last layer: no K split, FP32 NCHW output without alpha.
-    static_assert(SP == 0 || (SP >= 1 && SP <= 4 && DT == DT_BF16 && CG == 1), "specialisations");
+    // SP = 5, a BF16 layer with a K split reduced inside its cluster (a.xred):
+    // streamed weights, one work item a CTA, BF16 NHWC or FP32 NCHW output.
+    static_assert(SP == 0 || (SP >= 1 && SP <= 5 && DT == DT_BF16 && CG == 1), "specialisations");
     // (read where used, as the generic variant reads its launch arguments)
 #define kKalt (SP == 1 ? 0 : a.kalt)
-#define kTapm (SP == 1 ? 1 : a.tapm)
-#define kPair (SP == 1 ? 1 : (SP == 2 || SP == 4) ? 0 : a.pair)
-#define kBres (SP == 1 ? 1 : a.bres)
+#define kTapm (SP == 1 ? 1 : SP == 5 ? 0 : a.tapm)
+#define kPair (SP == 1 ? 1 : (SP == 2 || SP == 4 || SP == 5) ? 0 : a.pair)
+#define kBres (SP == 1 ? 1 : SP == 5 ? 0 : a.bres)
 #define kKsplit ((SP == 1 || SP == 2 || SP == 4) ? 1 : a.ksplit)
-#define kAlpha ((SP == 1 || SP == 2 || SP == 4) ? (const float*)nullptr : a.ep.alpha)
+#define kAlpha ((SP == 1 || SP == 2 || SP == 4 || SP == 5) ? (const float*)nullptr : a.ep.alpha)
 #define kOutLayout ((SP == 1 || SP == 2) ? (int)LAYOUT_NHWC : SP == 4 ? (int)LAYOUT_NCHW : (int)a.ep.out_layout)
 #define kOutDt ((SP == 1 || SP == 2) ? (int)DT_BF16 : SP == 4 ? (int)DT_F32 : (int)a.ep.out_dt)
     static_assert(MB == 1 || (MB == 2 && BN <= 128), "two CTAs per SM: N tiles of at most 128 columns");
@@ -426,8 +445,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     const int KK = a.k * a.k;
     const int nkb = KK * a.chunks;                // weight boxes (tap, chunk) per tile
     const int nk = kTapm ? a.chunks : nkb;       // pipeline steps per tile
-    // CTA pairs: this CTA's rank (0 issues the MMAs)
-    const uint32_t rank = C2 ? cluster_rank() : 0u;
+    // CTA pairs: this CTA's rank (0 issues the MMAs); cluster split-K: the
+    // CTA's K slice (blockIdx.x modulo ksplit)
+    constexpr bool XR = SP == 5;
+    const uint32_t rank = (C2 || XR) ? cluster_rank() : 0u;
     // work items: (m unit, n-tile, K slice), taken round robin by the CTAs
     // (CTA pairs: by the pairs; an m unit is then two M tiles)
     const int worker = C2 ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
@@ -457,6 +478,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         // one commit from each MMA issuer (CTA pairs: the even CTA's issuer)
         tc::mbar_init(smem_u32(&sm->done), C2 ? 1 : 2);
         tc::mbar_init(smem_u32(&sm->bres), 1);
+        if (XR) tc::mbar_init(smem_u32(&sm->xfull), 8u * (uint32_t)a.ksplit);
         sm->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -480,8 +502,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     tc::fence_before();
     __syncthreads();
     // CTA pairs: both CTAs' barriers are initialised before either arrives on
-    // or loads toward the other's
-    if constexpr (C2) cluster_sync();
+    // or loads toward the other's (cluster split-K: before any CTA arrives on
+    // another's xfull)
+    if constexpr (C2 || XR) cluster_sync();
     tc::fence_after();
     const uint32_t tmem_base = sm->tmem;
     volatile int* abort_flag = &sm->abort;
@@ -1011,7 +1034,171 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 }
             }
         }
-        for (int tile = pairs_done ? total : worker; tile < total; tile += nworkers, ++tcount) {
+        if constexpr (XR) {
+            // Cluster split-K.  The cluster's ksplit CTAs computed K slices 0 ..
+            // ksplit - 1 (their ranks) of one tile.  Phase 1: the two
+            // warpgroups drain half of this CTA's accumulator columns each (the
+            // K-alternating pair added) into the ring, idle now that every MMA
+            // has completed, as [BN / 4][128 rows][4] floats: a warp's float4
+            // stores cover 512 contiguous bytes.  Phase 2: once every CTA's
+            // partial sums are in place, CTA r takes columns r * BN / ksplit ..
+            // (r + 1) * BN / ksplit - 1 (half of them a warpgroup), adds the
+            // slices from the CTAs' shared memory in the order 0, 1, ... (the
+            // workspace reduction's order), applies the epilogue and stores.
+            // The kernel's closing cluster barrier keeps every CTA's shared
+            // memory alive until all reads of it are done.
+            const int S = a.ksplit;
+            const int mn = fdiv(worker, a.fd_ksplit);   // one work item a CTA: the cluster's tile
+            const int mq = fdiv(mn, a.fd_ntiles);
+            const int mt = mq, nt = mn - mq * a.n_tiles;
+            const uint32_t xs = smem_u32(sRing);
+            bool ok = worker < total;
+            if (ok) ok = tc::mbar_wait(smem_u32(&sm->accf[0]), 0u, abort_flag, a.err, 4, lim);
+            if (ok && kKalt) ok = tc::mbar_wait(smem_u32(&sm->accf[1]), 0u, abort_flag, a.err, 4, lim);
+            if (ok) {
+                tc::fence_after();
+                // the ring was last written by TMA (the async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(grp * (BN / 2));
+#pragma unroll 1
+                for (int c0 = 0; c0 < BN / 2; c0 += CW) {
+                    const int c = grp * (BN / 2) + c0;   // tile column
+                    if (nt * BN + c >= live) break;
+                    float v[CW];
+                    __syncwarp();
+                    tc::tmem_ld<CW>(trow + (uint32_t)c0, v);
+                    if (kKalt) {
+#pragma unroll
+                        for (int h16 = 0; h16 < CW; h16 += 16) {
+                            float u[16];
+                            tc::tmem_ld16(trow + (uint32_t)(BN + c0 + h16), u);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const float2 r2 = __fadd2_rn(make_float2(v[h16 + 2 * j], v[h16 + 2 * j + 1]),
+                                                             make_float2(u[2 * j], u[2 * j + 1]));
+                                v[h16 + 2 * j] = r2.x;
+                                v[h16 + 2 * j + 1] = r2.y;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < CW / 4; ++j)
+                        tc::st_shared_v4(xs + (uint32_t)((((c >> 2) + j) * 128 + row) * 16), v[4 * j], v[4 * j + 1],
+                                         v[4 * j + 2], v[4 * j + 3]);
+                }
+                // the warp's stores are ordered before lane 0's release
+                __syncwarp();
+                if (lane == 0)
+                    for (int r = 0; r < S; ++r) tc::mbar_arrive_cl(cl_addr(smem_u32(&sm->xfull), (uint32_t)r));
+            }
+            if (ok) ok = tc::mbar_wait<true>(smem_u32(&sm->xfull), 0u, abort_flag, a.err, 7, lim);
+            if (ok) {
+                const int ncw = BN / S / 2;                    // this warpgroup's columns (a multiple of 8)
+                const int cb = (int)rank * (BN / S) + grp * ncw;   // its first tile column
+                uint32_t peer[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) peer[r] = r < S ? cl_addr(xs, (uint32_t)r) : 0u;
+                const ConvProblem& P = a.probs[0];
+                void* ybase = a.y_override ? a.y_override : P.y;
+                const int local = mt - P.tile_begin;
+                const int txy = fdiv(local, P.fd_tx);
+                const int tx = local - txy * P.tiles_x;
+                const int img = fdiv(txy, P.fd_ty);
+                const int ty = txy - img * P.tiles_y;
+                const int gy = ty * a.TH + py, gx = tx * a.TW + px;
+                const bool valid = gy < P.H && gx < P.W;
+                const int Ho = pool ? P.H / 2 : P.H, Wo = pool ? P.W / 2 : P.W;
+                const int yo = pool ? gy / 2 : gy, xo = pool ? gx / 2 : gx;
+                const bool writer = valid && (!pool || ((lane & 1) == 0 && (lane & ymask) == 0));
+                const size_t pix = ((size_t)img * Ho + yo) * Wo + xo;
+                const bool nchw = a.ep.out_layout == LAYOUT_NCHW;
+#pragma unroll 1
+                for (int c0 = 0; c0 < ncw; c0 += 8) {
+                    const int o0 = nt * BN + cb + c0;   // first output channel of the chunk
+                    if (o0 >= live) break;
+                    const uint32_t off = (uint32_t)((((cb + c0) >> 2) * 128 + row) * 16);
+                    float4 t[8][2];
+#pragma unroll
+                    for (int r = 0; r < 8; ++r)
+                        if (r < S) {
+                            t[r][0] = tc::ld_cluster_v4(peer[r] + off);
+                            t[r][1] = tc::ld_cluster_v4(peer[r] + off + 128u * 16u);
+                        }
+                    float v[8] = {t[0][0].x, t[0][0].y, t[0][0].z, t[0][0].w,
+                                  t[0][1].x, t[0][1].y, t[0][1].z, t[0][1].w};
+#pragma unroll
+                    for (int r = 1; r < 8; ++r)
+                        if (r < S) {
+                            v[0] += t[r][0].x;
+                            v[1] += t[r][0].y;
+                            v[2] += t[r][0].z;
+                            v[3] += t[r][0].w;
+                            v[4] += t[r][1].x;
+                            v[5] += t[r][1].y;
+                            v[6] += t[r][1].z;
+                            v[7] += t[r][1].w;
+                        }
+                    // bias (padded with zeros to the weight rows), leaky
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float2 r2 = __fadd2_rn(make_float2(v[2 * j], v[2 * j + 1]),
+                                                     make_float2(e_bias[o0 + 2 * j], e_bias[o0 + 2 * j + 1]));
+                        v[2 * j] = r2.x;
+                        v[2 * j + 1] = r2.y;
+                    }
+                    if (a.ep.act == ACT_LEAKY) {
+                        const float2 slope = make_float2(kLeakySlope, kLeakySlope);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float2 s2 = __fmul2_rn(make_float2(v[2 * j], v[2 * j + 1]), slope);
+                            v[2 * j] = fmaxf(v[2 * j], s2.x);
+                            v[2 * j + 1] = fmaxf(v[2 * j + 1], s2.y);
+                        }
+                    }
+                    if (nchw) {   // FP32 NCHW (a last layer)
+                        if (pool) {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
+                                v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], ymask));
+                            }
+                        }
+                        if (writer) {
+                            float* yf = reinterpret_cast<float*>(ybase);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                if (o0 + j < a.ep.cout)
+                                    yf[(((size_t)img * a.ep.cout + o0 + j) * Ho + yo) * Wo + xo] = v[j];
+                        }
+                        continue;
+                    }
+                    // BF16 NHWC: round, then pool on packed pairs (as the other epilogues)
+                    uint32_t w[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        w[j] = *reinterpret_cast<uint32_t*>(&h2);
+                    }
+                    if (pool) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            uint32_t o = __shfl_xor_sync(0xffffffffu, w[j], 1);
+                            __nv_bfloat162 m = __hmax2(*reinterpret_cast<__nv_bfloat162*>(&w[j]),
+                                                       *reinterpret_cast<__nv_bfloat162*>(&o));
+                            w[j] = *reinterpret_cast<uint32_t*>(&m);
+                            o = __shfl_xor_sync(0xffffffffu, w[j], ymask);
+                            m = __hmax2(*reinterpret_cast<__nv_bfloat162*>(&w[j]),
+                                        *reinterpret_cast<__nv_bfloat162*>(&o));
+                            w[j] = *reinterpret_cast<uint32_t*>(&m);
+                        }
+                    }
+                    if (writer && o0 < a.ep.out_cs)
+                        *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ybase) + pix * a.ep.out_cs + o0) =
+                            make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+        }
+        for (int tile = (XR || pairs_done) ? total : worker; tile < total; tile += nworkers, ++tcount) {
             if (!C2 && !kKalt && (tcount & 1) != grp) continue;
             // the tile's accumulator (or pair of them in K-alternating mode)
             const int nsl_log = kKalt ? NBUF_LOG - 1 : NBUF_LOG;
@@ -1248,8 +1435,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     tc::fence_before();
     __syncthreads();
     // CTA pairs: neither CTA leaves while the other may still arrive on its
-    // barriers, load into its ring or read its shared memory
-    if constexpr (C2) cluster_sync();
+    // barriers, load into its ring or read its shared memory (cluster
+    // split-K: read its partial sums)
+    if constexpr (C2 || XR) cluster_sync();
     tc::fence_after();
     __syncwarp();
     if (warp == 1) {
@@ -1391,6 +1579,23 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
         return cudaErrorInvalidValue;
     if (!tc_geometry(BN, a.chb, a.bres, a.k * a.k * a.chunks, MB, CG, &a)) return cudaErrorInvalidValue;
     if (a.ksplit < 1 || a.n_tiles < 1 || a.chunks < 1 || a.k < 1) return cudaErrorInvalidValue;
+    // cluster split-K: clusters of ksplit CTAs (2, 4 or 8; each CTA's share
+    // of a warpgroup's columns a multiple of 8), one work item a CTA, one
+    // problem, streamed weights, and a ring that holds the 128 x BN FP32
+    // partial tile (a tuned ring depth gives way to that)
+    if ((SP == 5) != (a.xred != 0)) return cudaErrorInvalidValue;
+    if (SP == 5) {
+        const int S = a.ksplit;
+        if ((S != 2 && S != 4 && S != 8) || BN % (16 * S) != 0 || a.nprob != 1 || a.bres || a.tapm || a.pair ||
+            a.withhold || workers != a.m_tiles * a.n_tiles * S)
+            return cudaErrorInvalidValue;
+        if ((size_t)a.nst * a.st_bytes < (size_t)128 * BN * sizeof(float)) {
+            a.nst_cap = 0;
+            if (!tc_geometry(BN, a.chb, 0, a.k * a.k * a.chunks, MB, CG, &a) ||
+                (size_t)a.nst * a.st_bytes < (size_t)128 * BN * sizeof(float))
+                return cudaErrorInvalidValue;
+        }
+    }
     a.fd_ksplit = make_fast_div(a.ksplit);
     a.fd_ntiles = make_fast_div(a.n_tiles);
     a.fd_chunks = make_fast_div(a.chunks);
@@ -1419,9 +1624,9 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
         at[na].val.programmaticStreamSerializationAllowed = 1;
         ++na;
     }
-    if (CG == 2) {
+    if (CG == 2 || SP == 5) {
         at[na].id = cudaLaunchAttributeClusterDimension;
-        at[na].val.clusterDim.x = 2;
+        at[na].val.clusterDim.x = CG == 2 ? 2 : (unsigned)a.ksplit;
         at[na].val.clusterDim.y = 1;
         at[na].val.clusterDim.z = 1;
         ++na;
@@ -1431,8 +1636,55 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     return cudaLaunchKernelEx(&cfg, kern, tmB, a);
 }
 
+template <int BN>
+static int xred_capacity_bn(int S) {
+    auto kern = conv_tc_kernel<BN, DT_BF16, 1, 1, 5>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(S * 64));
+    cfg.blockDim = dim3(tc::THREADS);
+    cfg.dynamicSmemBytes = kSmemLimit;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)S;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return clusters * S;
+}
+
+int tc_xred_capacity(int BN, int ksplit) {
+    if (ksplit != 2 && ksplit != 4 && ksplit != 8) return 0;
+    if (BN % (16 * ksplit) != 0) return 0;
+    static int cache[3][9] = {};   // (BN 64 / 128 / 256, ksplit); -1: queried, none
+    int& c = cache[BN == 64 ? 0 : BN == 128 ? 1 : 2][ksplit];
+    if (c == 0) {
+        const int v = BN == 64 ? xred_capacity_bn<64>(ksplit)
+                    : BN == 128 ? xred_capacity_bn<128>(ksplit)
+                    : BN == 256 ? xred_capacity_bn<256>(ksplit) : 0;
+        c = v > 0 ? v : -1;
+    }
+    return c > 0 ? c : 0;
+}
+
 cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, int mb, int cg,
                            cudaStream_t st) {
+    if (a.xred) {   // cluster split-K (BF16)
+        if (dt != DT_BF16 || mb != 1 || cg != 1) return cudaErrorInvalidValue;
+        if (BN == 64) return launch_tc_bn<64, DT_BF16, 1, 1, 5>(tmB, a, workers, st);
+        if (BN == 128) return launch_tc_bn<128, DT_BF16, 1, 1, 5>(tmB, a, workers, st);
+        if (BN == 256) return launch_tc_bn<256, DT_BF16, 1, 1, 5>(tmB, a, workers, st);
+        return cudaErrorInvalidValue;
+    }
     if (cg == 2) {
         if (mb != 1) return cudaErrorInvalidValue;
         if (dt == DT_BF16 && BN == 128) return launch_tc_bn<128, DT_BF16, 1, 2>(tmB, a, workers, st);

@@ -176,6 +176,11 @@ struct TcArgs {
     long long wait_limit;   // bound of each pipeline wait, clock64 cycles (<= 0: ~2 s)
     int nst_cap;            // ring stages at most (even, >= 2; 0: as many as fit)
     int withhold;           // fault injection (tests): one producer skips one K step
+    // xred = 1 (K split, one work item per CTA): the ksplit CTAs of a tile form
+    // one thread-block cluster and add their partial sums through distributed
+    // shared memory, each applying the epilogue to 1 / ksplit of the columns;
+    // no workspace and no reduction launch
+    int xred;
     // division by ksplit, n_tiles, chunks, k and nst (filled by conv_tc_launch)
     FastDiv fd_ksplit, fd_ntiles, fd_chunks, fd_k, fd_nst;
 };
@@ -210,11 +215,16 @@ bool tc_b_resident(int BN, int n_tiles, int ksplit, int nk, int chb, int mb);
 cudaError_t tc_encode_act(CUtensorMap* tm, const void* base, int dt, int n, int H, int W, int Cp, int TW,
                           int TH);
 cudaError_t tc_encode_weights(CUtensorMap* tm, const void* w, int dt, int rows, int KK, int Cp, int BN);
+// CTAs of one cluster-reduced launch (xred) that can be resident at once
+// with N tile BN and ksplit CTAs a cluster (0 if such clusters cannot run)
+int tc_xred_capacity(int BN, int ksplit);
 // workers = persistent CTAs; tmB has box rows BN (cg = 2: BN / 2); mb =
 // CTAs per SM (1, or 2 for BN <= 128: half the shared memory and TMEM, 80
 // registers a thread); cg = 2: CTA pairs (2-CTA clusters, workers even, one
 // M = 256 tile a pair; BN 128 or 256, mb 1, streamed weights, no tap
-// merging and one MMA issuer).
+// merging and one MMA issuer).  a.xred = 1: clusters of a.ksplit CTAs,
+// workers = m_tiles * n_tiles * ksplit (one work item a CTA), BF16 operands,
+// BF16 NHWC or FP32 NCHW output.
 cudaError_t conv_tc_launch(const CUtensorMap& tmB, const TcArgs& a, int BN, int dt, int workers, int mb, int cg,
                            cudaStream_t st);
 }  // namespace dn

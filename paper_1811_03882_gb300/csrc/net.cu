@@ -619,6 +619,18 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
                     r.kalt = 0;
                     r.grid = 2 * std::max(1, std::min(units, n->num_sms / 2));
                 }
+                // BF16 split-K with one work item a CTA that all fit at once:
+                // the ksplit CTAs of a tile form a cluster and add their partial
+                // sums through distributed shared memory (no workspace round
+                // trip, no reduction launch)
+                static const bool xred_on = [] {
+                    const char* e = getenv("NET_TC_XRED");
+                    return !(e && atoi(e) == 0);
+                }();
+                r.xred = (xred_on && L.in_dt == DT_BF16 && r.ksplit > 1 && r.mb == 1 && r.cg == 1 && !r.bres &&
+                          !r.tapm && !L.pair && items == r.grid && items <= tc_xred_capacity(r.BN, r.ksplit))
+                             ? 1
+                             : 0;
             }
             (void)tiles;
             ConvProblem hp;
@@ -644,9 +656,9 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             if (dump)
                 fprintf(stderr,
                         "plan b%d %dx%d layer %d: tile %dx%d BN %d m_tiles %d n_tiles %d ksplit %d grid %d mb %d "
-                        "bres %d kalt %d tapm %d pair %d cg %d\n",
+                        "bres %d kalt %d tapm %d pair %d cg %d xred %d\n",
                         batch, h, w, l, r.TW, r.TH, r.BN, r.m_tiles, r.n_tiles, r.ksplit, r.grid, r.mb, r.bres,
-                        r.kalt, r.tapm, L.pair ? 1 : 0, r.cg);
+                        r.kalt, r.tapm, L.pair ? 1 : 0, r.cg, r.xred);
         }
         P->runs.push_back(r);
         if (L.d.pool != NET_POOL_2X2S1_SAME) cur ^= 1;
@@ -761,12 +773,18 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.ep = ep;
                 a.err = n->err_dev;
                 int grid = r.grid, cg = r.cg;
+                // the cluster reduction's epilogue writes BF16 NHWC or FP32 NCHW
+                a.xred = (r.xred && ((ep.out_layout == LAYOUT_NHWC && ep.out_dt == DT_BF16) ||
+                                     (ep.out_layout == LAYOUT_NCHW && ep.out_dt == DT_F32)))
+                             ? 1
+                             : 0;
                 if (l == n->fault_layer) {
                     // net_inject_device_fault: a ~1 ms bound (clock64 cycles at
                     // ~2 GHz) and one K step withheld by a producer, once (a
                     // pair layer runs single-CTA for it: same tiles, one issuer)
                     a.wait_limit = 2000000;
                     a.withhold = 1;
+                    a.xred = 0;   // the withheld step's layer reduces through the workspace
                     n->fault_layer = -1;
                     if (cg == 2) {
                         cg = 1;
@@ -775,7 +793,7 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 }
                 e = conv_tc_launch(L.tmB[tmb_index(cg == 2 ? r.BN / 2 : r.BN)], a, r.BN, L.in_dt, grid, r.mb, cg,
                                    st);
-                if (e == cudaSuccess && r.ksplit > 1) {
+                if (e == cudaSuccess && r.ksplit > 1 && !a.xred) {
                     ++n->pending;
                     SplitReduce sr{n->ws, r.ksplit, r.m_tiles * 128, r.n_tiles * r.BN, r.TW, r.TH,
                                    cdiv(r.W, r.TW), cdiv(r.H, r.TH), batch, r.H, r.W, y, ep, 1};

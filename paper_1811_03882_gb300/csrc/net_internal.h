@@ -70,6 +70,7 @@ struct LayerRun {
     int cg = 1;                    // TC: 2 = CTA pairs (one M = 256 tile across two SMs)
     int nst_cap = 0;               // TC: ring stages at most (0: as many as fit)
     int tapm = 0;                  // TC: ring stages of all nine taps (3x3, resident weights)
+    int xred = 0;                  // TC: split-K reduced inside clusters of ksplit CTAs (BF16)
     int sbn = 64, sth = 8, stw = 16; // CUDA-core tile
     ConvProblem* d_prob = nullptr; // TC: device problem table (one entry)
 };

@@ -7,8 +7,10 @@ MMA over 8-channel pixels, and one CTA per SM everywhere (NET_TC_MB=1) or
 two wherever the N tile allows (NET_TC_MB=2, which also runs long A + B
 rings on half the shared memory and the 16-column epilogue), and CTA pairs
 (NET_TC_PAIR=1: 2-CTA clusters, one M = 256 tile a pair, on the layers that
-stream N tiles of 128 or 256 columns), and the generic kernel for the
-tap-pair first layer instead of its specialised variant (NET_TC_SPEC=0).
+stream N tiles of 128 or 256 columns), the generic kernel for the
+tap-pair first layer instead of its specialised variant (NET_TC_SPEC=0), and
+split-K layers reduced through the workspace by a reduction launch instead
+of inside their clusters (NET_TC_XRED=0).
 Every mode must give the oracle's answer within
 the BF16 budget and agree with the default mode to BF16 rounding; the
 19-conv network at 2 x 160 x 160 has layers with one and with several work
@@ -70,7 +72,7 @@ def test_launch_modes_match_oracle(tmp_path):
                       ("im2col", {"NET_L0_PAIR": "0"}), ("no_tapm", {"NET_TC_TAPM": "0"}),
                       ("mb1", {"NET_TC_MB": "1"}), ("mb2", {"NET_TC_MB": "2"}),
                       ("pair", {"NET_TC_PAIR": "1"}), ("pair_no_kalt", {"NET_TC_PAIR": "1", "NET_TC_KALT": "0"}),
-                      ("no_spec", {"NET_TC_SPEC": "0"})):
+                      ("no_spec", {"NET_TC_SPEC": "0"}), ("no_xred", {"NET_TC_XRED": "0"})):
         y = _run(tmp_path, name, env)
         assert np.isfinite(y).all(), name
         e = oracle.normwise_rel_err(y, ex)
@@ -81,6 +83,8 @@ def test_launch_modes_match_oracle(tmp_path):
     np.testing.assert_array_equal(ys["no_pdl"], ys["default"])
     # the first-layer specialisation runs the generic kernel's operations
     np.testing.assert_array_equal(ys["no_spec"], ys["default"])
+    # the cluster reduction adds the K slices in the workspace reduction's order
+    np.testing.assert_array_equal(ys["no_xred"], ys["default"])
     # a CTA pair accumulates every row's products in the single-CTA order of
     # one MMA issuer: the same bits as that mode
     np.testing.assert_array_equal(ys["pair_no_kalt"], ys["no_kalt"])
