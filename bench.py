@@ -572,6 +572,50 @@ class Workload:
             torch.cuda.synchronize()
 
 
+def run_trace(torch, binding, wl, args):
+    """Phase timeline of one fixed-batch pass (net_trace): per tensor-core
+    layer, from the CTAs' globaltimer stamps, in microseconds from the first
+    conv launch's start.  dep: first producer past the wait for the previous
+    kernel; fill: from there to the first K step ready; mainloop: first K
+    step to the last MMA issued; tail: last MMA issued to the epilogue's end
+    (the MMAs still in the tensor pipe, then the last tile's epilogue);
+    straggle: last CTA's end minus the median CTA's end; gap: this layer's
+    dep minus the previous layer's last CTA end."""
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    W = Workload(torch, binding, 0, wl, WORKLOADS[wl][3], stream)
+    if not W.side:
+        raise SystemExit("trace: fixed-batch workloads only")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device="cuda")
+    for _ in range(args.warmup):
+        W.step()
+    W.net.trace(True)
+    for _ in range(2):   # the first traced pass captures a new graph
+        flush.zero_()
+        W.step()
+    buf = W.net.trace_read().astype(np.int64)
+    ran = [l for l in range(buf.shape[0]) if buf[l, :, 0].any()]
+    t0 = min(int(buf[l, buf[l, :, 0] > 0, 0].min()) for l in ran)
+    layers, prev_end = [], None
+    for l in ran:
+        B = (buf[l, buf[l, :, 0] > 0] - t0) / 1000.0
+        ep_end = np.maximum(B[:, 6], B[:, 7])
+        r = {"layer": l, "ctas": int(B.shape[0]), "start": float(B[:, 0].min()),
+             "prologue": float(np.median(B[:, 1] - B[:, 0])), "dep": float(B[:, 2].min()),
+             "fill": float(np.median(B[:, 3] - B[:, 2])), "mainloop": float(np.median(B[:, 4] - B[:, 3])),
+             "tail": float(np.median(ep_end - B[:, 4])), "end": float(B[:, 8].max()),
+             "straggle": float(B[:, 8].max() - np.median(B[:, 8]))}
+        r["dep_to_end"] = r["end"] - r["dep"]
+        r["gap"] = None if prev_end is None else r["dep"] - prev_end
+        prev_end = r["end"]
+        layers.append({k: (round(v, 2) if isinstance(v, float) else v) for k, v in r.items()})
+    W.net.trace(False)
+    tot = lambda k: round(sum(x[k] for x in layers if x[k] is not None), 2)
+    return {"workload": wl, "unit": "us", "layers": layers,
+            "sums": {k: tot(k) for k in ("fill", "mainloop", "tail", "straggle", "gap", "dep_to_end")},
+            "span": round(layers[-1]["end"] - layers[0]["start"], 2)}
+
+
 def measure(torch, W, args, flush, barrier, ws, with_clocks=False, dev=0):
     """Warm-up, K device-timed steps (L2 flushed between them, outside the
     events), a second pass with per-layer conv events, and the e2e pass."""
@@ -700,7 +744,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--no-extra", action="store_true",
                     help="leave the detection, nightmare and Jacobi measurements out of the line")
-    ap.add_argument("--section", choices=["detect", "jacobi", "nightmare"],
+    ap.add_argument("--section", choices=["detect", "jacobi", "nightmare", "trace"],
                     help="run only this measurement and print its JSON (profiling entry point)")
     ap.add_argument("--no-tile-search", action="store_true",
                     help="keep the analytic tile plan (skip the genetic tile-plan search)")
@@ -715,6 +759,9 @@ def main():
         from paper_1811_03882_gb300 import build, binding
         build.build()
         torch.cuda.set_device(0)
+        if args.section == "trace":
+            print(json.dumps({"section": "trace", **run_trace(torch, binding, wl, args)}), flush=True)
+            return
         fn = {"detect": run_detect, "jacobi": run_jacobi, "nightmare": run_nightmare}[args.section]
         print(json.dumps({"section": args.section, **fn(torch, binding, 0)}), flush=True)
         return

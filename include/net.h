@@ -444,6 +444,21 @@ net_status net_plan_grouped(const net_t* net, int* bn, int* mb, int* nst, int n)
  * recent pass and writes each layer's conv-kernel time in milliseconds to
  * ms_out (host, n = n_layers entries). */
 net_status net_profile(net_t* net, int enable);
+
+/* Phase trace of the tensor-core conv launches (a diagnostic; the paper has
+ * no counterpart).  With enable != 0 (which clears the record) every later
+ * fixed-batch forward pass makes each CTA of each tensor-core layer write
+ * GPU globaltimer stamps (nanoseconds) at ten points: 0 kernel start,
+ * 1 prologue done, 2 first producer past the wait for the previous kernel,
+ * 3 first K step ready for the first MMA issuer, 4 its last MMA issued,
+ * 5 epilogue warp 2 started, 6 epilogue warp 2 done, 7 epilogue warp 6
+ * done, 8 closing barrier passed (9 unused); 0 where nothing was written
+ * (CUDA-core layers, grids beyond 512 CTAs).  net_trace_read waits for the
+ * handle's stream and copies the record, n_layers x 512 x 10 uint64 in that
+ * order, to out (host, cap entries at least); NET_E_STATE if tracing was
+ * never enabled. */
+net_status net_trace(net_t* net, int enable);
+net_status net_trace_read(net_t* net, uint64_t* out, size_t cap);
 net_status net_layer_times(net_t* net, double* ms_out, int n);
 
 /* Total number of kernels this handle has launched (a CUDA-graph replay

@@ -123,6 +123,8 @@ _SIGS = {
     "net_profile": [ctypes.c_void_p, ctypes.c_int],
     "net_layer_times": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "net_launches": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)],
+    "net_trace": [ctypes.c_void_p, ctypes.c_int],
+    "net_trace_read": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "net_inject_device_fault": [ctypes.c_void_p, ctypes.c_int],
     "net_guard_check": [ctypes.c_void_p, ctypes.c_void_p],
     "net_guard_poke": [ctypes.c_uint64],
@@ -490,6 +492,18 @@ class Net:
         t = ctypes.c_uint64()
         check(lib().net_launches(self.h, ctypes.byref(t)))
         return t.value
+
+    TRACE_CTAS, TRACE_EVENTS = 512, 10
+
+    def trace(self, enable: bool = True):
+        """Phase trace of the tensor-core launches on (clears it) or off (net_trace)."""
+        check(lib().net_trace(self.h, int(enable)))
+
+    def trace_read(self) -> np.ndarray:
+        """[n_layers, 512, 10] uint64 globaltimer stamps of the last traced pass."""
+        out = np.zeros((self.n_layers, self.TRACE_CTAS, self.TRACE_EVENTS), np.uint64)
+        check(lib().net_trace_read(self.h, out.ctypes.data, out.size))
+        return out
 
     def stats(self):
         f, p50, p99 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -31,6 +31,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -181,6 +182,13 @@ __device__ __forceinline__ float4 ld_cluster_v4(uint32_t addr) {
                  : "r"(addr)
                  : "memory");
     return v;
+}
+
+// phase trace: globaltimer (ns) of event e for this CTA
+__device__ __forceinline__ void trace_stamp(unsigned long long* tr, int e) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    tr[blockIdx.x * kTraceEvents + e] = t;
 }
 
 // Shared-memory matrix descriptor (tcgen05), K-major operand with 32/64/128
@@ -440,6 +448,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     float* s_alpha = s_bias + kEpiCols;
 
     pdl_trigger();   // the next kernel may start its prologue as SMs free up
+#define TRACE(e) \
+    do {                                   \
+        if (a.trace) tc::trace_stamp(a.trace, e); \
+    } while (0)
+    if (threadIdx.x == 0) TRACE(0);
     const long long lim = a.wait_limit;   // bound of every pipeline wait (clock64 cycles)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int KK = a.k * a.k;
@@ -506,6 +519,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     // another's xfull)
     if constexpr (C2 || XR) cluster_sync();
     tc::fence_after();
+    if (threadIdx.x == 0) TRACE(1);
     const uint32_t tmem_base = sm->tmem;
     volatile int* abort_flag = &sm->abort;
     if (kBres && warp == 0 && lane == 0) {
@@ -676,6 +690,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 pre_b = true;
             }
             pdl_wait();
+            if (warp == 0 && lane == 0) TRACE(2);
             // per issuer: bit s = phase parity of the next use of full[m][s];
             // per stage this lane fills: the issuer of its last use
             uint32_t pph0 = 0u, pph1 = 0u, last_owner = 0u, issued = 0u;
@@ -830,6 +845,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         break;
                     }
                     fph ^= 1u << s;
+                    if (mid == 0 && it == 0) TRACE(3);
                     tc::fence_after();
                     uint8_t* stg = sRing + (size_t)s * st_bytes;
                     const int nmma = a.chb / 32;   // 32 bytes of K per MMA
@@ -876,6 +892,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 }
                 if (ok) commit(&sm->accf[b]);
             }
+            if (mid == 0) TRACE(4);
             // every MMA issued has finished before TMEM and smem are released
             commit(&sm->done);
             const long long t0 = clock64();
@@ -911,6 +928,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             }
             asm volatile("bar.sync 1, 256;" ::: "memory");   // the 8 epilogue warps
         }
+        if (lane == 0 && warp == 2) TRACE(5);
         const float* e_bias = epi_smem ? s_bias : a.ep.bias;
         const float* e_alpha = epi_smem ? s_alpha : kAlpha;
         const int ymask = a.TW == 16 ? 16 : 8;  // lane distance of the pixel below (pool tiles)
@@ -1066,19 +1084,24 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     if (nt * BN + c >= live) break;
                     float v[CW];
                     __syncwarp();
-                    tc::tmem_ld<CW>(trow + (uint32_t)c0, v);
-                    if (kKalt) {
+                    {   // both accumulators' loads issued before one wait
+                        uint32_t r0[CW], r1[CW];
+                        tc::tmem_ld_issue<CW>(trow + (uint32_t)c0, r0);
+                        if (kKalt) tc::tmem_ld_issue<CW>(trow + (uint32_t)(BN + c0), r1);
+                        tc::tmem_ld_wait<CW>(r0);
+                        if (kKalt) {
+                            tc::tmem_ld_wait<CW>(r1);   // (nothing left to wait for: names r1)
 #pragma unroll
-                        for (int h16 = 0; h16 < CW; h16 += 16) {
-                            float u[16];
-                            tc::tmem_ld16(trow + (uint32_t)(BN + c0 + h16), u);
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const float2 r2 = __fadd2_rn(make_float2(v[h16 + 2 * j], v[h16 + 2 * j + 1]),
-                                                             make_float2(u[2 * j], u[2 * j + 1]));
-                                v[h16 + 2 * j] = r2.x;
-                                v[h16 + 2 * j + 1] = r2.y;
+                            for (int j = 0; j < CW / 2; ++j) {
+                                const float2 r2 =
+                                    __fadd2_rn(make_float2(__uint_as_float(r0[2 * j]), __uint_as_float(r0[2 * j + 1])),
+                                               make_float2(__uint_as_float(r1[2 * j]), __uint_as_float(r1[2 * j + 1])));
+                                v[2 * j] = r2.x;
+                                v[2 * j + 1] = r2.y;
                             }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < CW; ++j) v[j] = __uint_as_float(r0[j]);
                         }
                     }
 #pragma unroll
@@ -1092,12 +1115,20 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     for (int r = 0; r < S; ++r) tc::mbar_arrive_cl(cl_addr(smem_u32(&sm->xfull), (uint32_t)r));
             }
             if (ok) ok = tc::mbar_wait<true>(smem_u32(&sm->xfull), 0u, abort_flag, a.err, 7, lim);
-            if (ok) {
-                const int ncw = BN / S / 2;                    // this warpgroup's columns (a multiple of 8)
-                const int cb = (int)rank * (BN / S) + grp * ncw;   // its first tile column
-                uint32_t peer[8];
+            // phase 2 for a cluster of SC CTAs (a compile-time count, so that the
+            // batch of remote loads below lives in registers)
+            auto reduce = [&](auto SC) {
+                constexpr int S2 = decltype(SC)::value;
+                constexpr int NCW = BN / S2 / 2;            // this warpgroup's columns
+                static_assert(NCW % 8 == 0, "columns a warpgroup reduces: whole chunks of 8");
+                // the remote loads of G chunks of 8 columns (16 float4 a thread)
+                // are issued together: a warpgroup's columns take
+                // NCW / (8 G) = BN / 128 round trips to the peers
+                constexpr int G = 8 / S2 < NCW / 8 ? 8 / S2 : NCW / 8;
+                const int cb = (int)rank * (BN / S2) + grp * NCW;   // its first tile column
+                uint32_t peer[S2];
 #pragma unroll
-                for (int r = 0; r < 8; ++r) peer[r] = r < S ? cl_addr(xs, (uint32_t)r) : 0u;
+                for (int r = 0; r < S2; ++r) peer[r] = cl_addr(xs, (uint32_t)r);
                 const ConvProblem& P = a.probs[0];
                 void* ybase = a.y_override ? a.y_override : P.y;
                 const int local = mt - P.tile_begin;
@@ -1113,88 +1144,103 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 const size_t pix = ((size_t)img * Ho + yo) * Wo + xo;
                 const bool nchw = a.ep.out_layout == LAYOUT_NCHW;
 #pragma unroll 1
-                for (int c0 = 0; c0 < ncw; c0 += 8) {
-                    const int o0 = nt * BN + cb + c0;   // first output channel of the chunk
-                    if (o0 >= live) break;
-                    const uint32_t off = (uint32_t)((((cb + c0) >> 2) * 128 + row) * 16);
-                    float4 t[8][2];
+                for (int cg0 = 0; cg0 < NCW; cg0 += 8 * G) {
+                    if (nt * BN + cb + cg0 >= live) break;
+                    float4 t[G][S2][2];
 #pragma unroll
-                    for (int r = 0; r < 8; ++r)
-                        if (r < S) {
-                            t[r][0] = tc::ld_cluster_v4(peer[r] + off);
-                            t[r][1] = tc::ld_cluster_v4(peer[r] + off + 128u * 16u);
+                    for (int g = 0; g < G; ++g)
+#pragma unroll
+                        for (int r = 0; r < S2; ++r)
+#pragma unroll
+                            for (int h = 0; h < 2; ++h)
+                                t[g][r][h] = tc::ld_cluster_v4(
+                                    peer[r] + (uint32_t)(((((cb + cg0 + 8 * g) >> 2) + h) * 128 + row) * 16));
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const int o0 = nt * BN + cb + cg0 + 8 * g;   // first output channel of the chunk
+                        if (o0 >= live) break;
+                        float v[8] = {t[g][0][0].x, t[g][0][0].y, t[g][0][0].z, t[g][0][0].w,
+                                      t[g][0][1].x, t[g][0][1].y, t[g][0][1].z, t[g][0][1].w};
+#pragma unroll
+                        for (int r = 1; r < S2; ++r) {
+                            v[0] += t[g][r][0].x;
+                            v[1] += t[g][r][0].y;
+                            v[2] += t[g][r][0].z;
+                            v[3] += t[g][r][0].w;
+                            v[4] += t[g][r][1].x;
+                            v[5] += t[g][r][1].y;
+                            v[6] += t[g][r][1].z;
+                            v[7] += t[g][r][1].w;
                         }
-                    float v[8] = {t[0][0].x, t[0][0].y, t[0][0].z, t[0][0].w,
-                                  t[0][1].x, t[0][1].y, t[0][1].z, t[0][1].w};
-#pragma unroll
-                    for (int r = 1; r < 8; ++r)
-                        if (r < S) {
-                            v[0] += t[r][0].x;
-                            v[1] += t[r][0].y;
-                            v[2] += t[r][0].z;
-                            v[3] += t[r][0].w;
-                            v[4] += t[r][1].x;
-                            v[5] += t[r][1].y;
-                            v[6] += t[r][1].z;
-                            v[7] += t[r][1].w;
-                        }
-                    // bias (padded with zeros to the weight rows), leaky
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float2 r2 = __fadd2_rn(make_float2(v[2 * j], v[2 * j + 1]),
-                                                     make_float2(e_bias[o0 + 2 * j], e_bias[o0 + 2 * j + 1]));
-                        v[2 * j] = r2.x;
-                        v[2 * j + 1] = r2.y;
-                    }
-                    if (a.ep.act == ACT_LEAKY) {
-                        const float2 slope = make_float2(kLeakySlope, kLeakySlope);
+                        // bias (padded with zeros to the weight rows), leaky
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const float2 s2 = __fmul2_rn(make_float2(v[2 * j], v[2 * j + 1]), slope);
-                            v[2 * j] = fmaxf(v[2 * j], s2.x);
-                            v[2 * j + 1] = fmaxf(v[2 * j + 1], s2.y);
+                            const float2 r2 = __fadd2_rn(make_float2(v[2 * j], v[2 * j + 1]),
+                                                         make_float2(e_bias[o0 + 2 * j], e_bias[o0 + 2 * j + 1]));
+                            v[2 * j] = r2.x;
+                            v[2 * j + 1] = r2.y;
                         }
-                    }
-                    if (nchw) {   // FP32 NCHW (a last layer)
-                        if (pool) {
+                        if (a.ep.act == ACT_LEAKY) {
+                            const float2 slope = make_float2(kLeakySlope, kLeakySlope);
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
-                                v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], ymask));
+                            for (int j = 0; j < 4; ++j) {
+                                const float2 s2 = __fmul2_rn(make_float2(v[2 * j], v[2 * j + 1]), slope);
+                                v[2 * j] = fmaxf(v[2 * j], s2.x);
+                                v[2 * j + 1] = fmaxf(v[2 * j + 1], s2.y);
                             }
                         }
-                        if (writer) {
-                            float* yf = reinterpret_cast<float*>(ybase);
+                        if (nchw) {   // FP32 NCHW (a last layer)
+                            if (pool) {
 #pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                if (o0 + j < a.ep.cout)
-                                    yf[(((size_t)img * a.ep.cout + o0 + j) * Ho + yo) * Wo + xo] = v[j];
+                                for (int j = 0; j < 8; ++j) {
+                                    v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], 1));
+                                    v[j] = fmaxf(v[j], __shfl_xor_sync(0xffffffffu, v[j], ymask));
+                                }
+                            }
+                            if (writer) {
+                                float* yf = reinterpret_cast<float*>(ybase);
+#pragma unroll
+                                for (int j = 0; j < 8; ++j)
+                                    if (o0 + j < a.ep.cout)
+                                        yf[(((size_t)img * a.ep.cout + o0 + j) * Ho + yo) * Wo + xo] = v[j];
+                            }
+                            continue;
                         }
-                        continue;
-                    }
-                    // BF16 NHWC: round, then pool on packed pairs (as the other epilogues)
-                    uint32_t w[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                        w[j] = *reinterpret_cast<uint32_t*>(&h2);
-                    }
-                    if (pool) {
+                        // BF16 NHWC: round, then pool on packed pairs (as the other epilogues)
+                        uint32_t w[4];
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            uint32_t o = __shfl_xor_sync(0xffffffffu, w[j], 1);
-                            __nv_bfloat162 m = __hmax2(*reinterpret_cast<__nv_bfloat162*>(&w[j]),
-                                                       *reinterpret_cast<__nv_bfloat162*>(&o));
-                            w[j] = *reinterpret_cast<uint32_t*>(&m);
-                            o = __shfl_xor_sync(0xffffffffu, w[j], ymask);
-                            m = __hmax2(*reinterpret_cast<__nv_bfloat162*>(&w[j]),
-                                        *reinterpret_cast<__nv_bfloat162*>(&o));
-                            w[j] = *reinterpret_cast<uint32_t*>(&m);
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                            w[j] = *reinterpret_cast<uint32_t*>(&h2);
                         }
+                        if (pool) {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                uint32_t o = __shfl_xor_sync(0xffffffffu, w[j], 1);
+                                __nv_bfloat162 m = __hmax2(*reinterpret_cast<__nv_bfloat162*>(&w[j]),
+                                                           *reinterpret_cast<__nv_bfloat162*>(&o));
+                                w[j] = *reinterpret_cast<uint32_t*>(&m);
+                                o = __shfl_xor_sync(0xffffffffu, w[j], ymask);
+                                m = __hmax2(*reinterpret_cast<__nv_bfloat162*>(&w[j]),
+                                            *reinterpret_cast<__nv_bfloat162*>(&o));
+                                w[j] = *reinterpret_cast<uint32_t*>(&m);
+                            }
+                        }
+                        if (writer && o0 < a.ep.out_cs)
+                            *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ybase) + pix * a.ep.out_cs +
+                                                      o0) = make_uint4(w[0], w[1], w[2], w[3]);
                     }
-                    if (writer && o0 < a.ep.out_cs)
-                        *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ybase) + pix * a.ep.out_cs + o0) =
-                            make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            };
+            if (ok) {
+                if constexpr (BN >= 32) {
+                    if (S == 2) reduce(std::integral_constant<int, 2>{});
+                }
+                if constexpr (BN >= 64) {
+                    if (S == 4) reduce(std::integral_constant<int, 4>{});
+                }
+                if constexpr (BN >= 128) {
+                    if (S == 8) reduce(std::integral_constant<int, 8>{});
                 }
             }
         }
@@ -1215,20 +1261,27 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + half * HC);
             // the buffer goes back to the MMA issuer right after its last live
             // column is in registers; the math and stores of that chunk follow
-            // K-alternating mode: add the second accumulator (odd K steps),
-            // 16 columns at a time to keep registers down
-            auto add_pair = [&](uint32_t taddr, float* v) {
+            // a chunk of the tile's accumulator: in K-alternating mode both
+            // accumulators' loads are issued before one wait, and added
+            auto ld_acc = [&](uint32_t taddr, float* v) {
+                uint32_t r0[CW];
+                tc::tmem_ld_issue<CW>(taddr, r0);
+                if (kKalt) {
+                    uint32_t r1[CW];
+                    tc::tmem_ld_issue<CW>(taddr + (uint32_t)BN, r1);
+                    tc::tmem_ld_wait<CW>(r0);
+                    tc::tmem_ld_wait<CW>(r1);   // (nothing left to wait for: names r1)
 #pragma unroll
-                for (int h16 = 0; h16 < CW; h16 += 16) {
-                    float u[16];
-                    tc::tmem_ld16(taddr + (uint32_t)h16, u);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float2 r = __fadd2_rn(make_float2(v[h16 + 2 * j], v[h16 + 2 * j + 1]),
-                                                    make_float2(u[2 * j], u[2 * j + 1]));
-                        v[h16 + 2 * j] = r.x;
-                        v[h16 + 2 * j + 1] = r.y;
+                    for (int j = 0; j < CW / 2; ++j) {
+                        const float2 r = __fadd2_rn(make_float2(__uint_as_float(r0[2 * j]), __uint_as_float(r0[2 * j + 1])),
+                                                    make_float2(__uint_as_float(r1[2 * j]), __uint_as_float(r1[2 * j + 1])));
+                        v[2 * j] = r.x;
+                        v[2 * j + 1] = r.y;
                     }
+                } else {
+                    tc::tmem_ld_wait<CW>(r0);
+#pragma unroll
+                    for (int j = 0; j < CW; ++j) v[j] = __uint_as_float(r0[j]);
                 }
             };
             bool released = false;
@@ -1262,8 +1315,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     if (nt * BN + half * HC + c0 >= live) break;
                     float v[CW];
                     __syncwarp();
-                    tc::tmem_ld<CW>(trow + (uint32_t)c0, v);
-                    if (kKalt) add_pair(trow + (uint32_t)(BN + c0), v);
+                    ld_acc(trow + (uint32_t)c0, v);
                     if (c0 + CW >= HC || nt * BN + half * HC + c0 + CW >= live) release();
 #pragma unroll
                     for (int j = 0; j < CW; j += 4)
@@ -1313,8 +1365,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     }
                     float v[CW];
                     __syncwarp();
-                    tc::tmem_ld<CW>(trow + (uint32_t)c0, v);
-                    if (kKalt) add_pair(trow + (uint32_t)(BN + c0), v);
+                    ld_acc(trow + (uint32_t)c0, v);
                     if (c0 + CW >= HC || o0 + CW >= live) release();
                     // warp-uniform branches: each variant is one straight-line loop.
                     // Paired FP32 operations (one instruction on a register
@@ -1430,6 +1481,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             }
             if (!released) release();   // a tile without live columns (not produced by the planner)
         }
+        if (lane == 0 && warp == 2) TRACE(6);
+        if (lane == 0 && warp == 6) TRACE(7);
     }
 
     tc::fence_before();
@@ -1439,6 +1492,8 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     // split-K: read its partial sums)
     if constexpr (C2 || XR) cluster_sync();
     tc::fence_after();
+    if (threadIdx.x == 0) TRACE(8);
+#undef TRACE
     __syncwarp();
     if (warp == 1) {
         if constexpr (C2)

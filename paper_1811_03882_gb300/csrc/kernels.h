@@ -181,6 +181,10 @@ struct TcArgs {
     // shared memory, each applying the epilogue to 1 / ksplit of the columns;
     // no workspace and no reduction launch
     int xred;
+    // phase trace (net_trace): if not null, CTA b writes globaltimer stamps
+    // to trace[b * kTraceEvents + e] (kTraceEvents per CTA; the host passes
+    // null when the grid exceeds kTraceCtas)
+    unsigned long long* trace;
     // division by ksplit, n_tiles, chunks, k and nst (filled by conv_tc_launch)
     FastDiv fd_ksplit, fd_ntiles, fd_chunks, fd_k, fd_nst;
 };
@@ -206,6 +210,14 @@ struct PoolJob {
 cudaError_t maxpool_s1_grouped(const PoolJob* jobs, int njobs, long long total, int cs, int dt,
                                cudaStream_t st);
 
+// Phase trace of a tensor-core launch: per CTA, globaltimer stamps (ns) at
+// 0 kernel start, 1 end of the prologue (barriers, tensor memory), 2 the
+// first producer past the dependency wait, 3 the first MMA issuer's first
+// K step ready, 4 its last MMA issued, 5 epilogue warp 2 started (after the
+// bias staging), 6 epilogue warp 2 done, 7 epilogue warp 6 done, 8 the
+// kernel's closing barrier passed (before tensor memory is freed).
+constexpr int kTraceEvents = 10;
+constexpr int kTraceCtas = 512;
 int tc_chunk_bytes(int Cp, int dt);
 // Whether a launch keeps its weights resident in shared memory: no K split,
 // and nk boxes of BN x chunk bytes (one N tile's weights; with several N

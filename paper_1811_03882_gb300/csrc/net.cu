@@ -773,6 +773,9 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.ep = ep;
                 a.err = n->err_dev;
                 int grid = r.grid, cg = r.cg;
+                a.trace = (n->trace_on && n->trace_dev && grid <= kTraceCtas)
+                              ? n->trace_dev + (size_t)l * kTraceCtas * kTraceEvents
+                              : nullptr;
                 // the cluster reduction's epilogue writes BF16 NHWC or FP32 NCHW
                 a.xred = (r.xred && ((ep.out_layout == LAYOUT_NHWC && ep.out_dt == DT_BF16) ||
                                      (ep.out_layout == LAYOUT_NCHW && ep.out_dt == DT_F32)))
@@ -1139,6 +1142,29 @@ extern "C" net_status net_layer_times(net_t* n, double* ms, int cnt) {
     return NET_OK;
 }
 
+extern "C" net_status net_trace(net_t* n, int enable) {
+    if (!n) return fail(NET_E_INVAL, "NULL argument");
+    CK(cudaSetDevice(n->device));
+    CK(cudaStreamSynchronize(n->stream));
+    const size_t bytes = n->L.size() * (size_t)kTraceCtas * kTraceEvents * sizeof(unsigned long long);
+    if (enable && !n->trace_dev) CK(dn::dalloc(&n->trace_dev, bytes));
+    if (enable) CK(cudaMemset(n->trace_dev, 0, bytes));
+    n->trace_on = enable != 0;
+    n->graphs_clear();   // captured launches hold the trace pointer (or none)
+    return NET_OK;
+}
+
+extern "C" net_status net_trace_read(net_t* n, uint64_t* out, size_t cap) {
+    if (!n || !out) return fail(NET_E_INVAL, "NULL argument");
+    const size_t words = n->L.size() * (size_t)kTraceCtas * kTraceEvents;
+    if (cap < words) return fail(NET_E_INVAL, "need %zu entries", words);
+    if (!n->trace_dev) return fail(NET_E_STATE, "tracing never enabled");
+    CK(cudaSetDevice(n->device));
+    CK(cudaStreamSynchronize(n->stream));
+    CK(cudaMemcpy(out, n->trace_dev, words * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    return NET_OK;
+}
+
 extern "C" net_status net_launches(const net_t* n, uint64_t* total) {
     if (!n || !total) return fail(NET_E_INVAL, "NULL argument");
     *total = n->launches;
@@ -1258,6 +1284,7 @@ extern "C" net_status net_free(net_t* n) {
     if (n->stream) cudaStreamSynchronize(n->stream);
     n->graphs_clear();
     for (auto ev : n->prof_ev) cudaEventDestroy(ev);
+    if (n->trace_dev) dn::dfree(n->trace_dev);
     for (auto& L : n->L) {
         for (int v = 0; v < 2; ++v)
             if (L.w_var[v] && L.w_var[v] != L.w) dn::dfree(L.w_var[v]);

@@ -142,6 +142,9 @@ struct net {
     std::map<std::tuple<int, int, int, const void*, const void*>, cudaGraphExec_t> graphs;
     bool prof = false;
     std::vector<cudaEvent_t> prof_ev;   // 2 per layer
+    // phase trace (net_trace): [layer][kTraceCtas][kTraceEvents] globaltimer stamps
+    unsigned long long* trace_dev = nullptr;
+    bool trace_on = false;
     uint64_t launches = 0;              // kernels launched so far
     int pending = 0;                    // kernels enqueued by the current forward
     std::map<std::tuple<int, int, int, const void*, const void*>, int> graph_kernels;
