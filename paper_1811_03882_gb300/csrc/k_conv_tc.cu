@@ -1119,13 +1119,17 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             // batch of remote loads below lives in registers)
             auto reduce = [&](auto SC) {
                 constexpr int S2 = decltype(SC)::value;
-                constexpr int NCW = BN / S2 / 2;            // this warpgroup's columns
+                constexpr int CPO = BN / S2;                // columns this CTA reduces (a multiple of 8)
+                constexpr int WG = CPO >= 16 ? 2 : 1;       // warpgroups sharing them
+                constexpr int NCW = CPO / WG;               // this warpgroup's columns
                 static_assert(NCW % 8 == 0, "columns a warpgroup reduces: whole chunks of 8");
-                // the remote loads of G chunks of 8 columns (16 float4 a thread)
-                // are issued together: a warpgroup's columns take
-                // NCW / (8 G) = BN / 128 round trips to the peers
-                constexpr int G = 8 / S2 < NCW / 8 ? 8 / S2 : NCW / 8;
-                const int cb = (int)rank * (BN / S2) + grp * NCW;   // its first tile column
+                if (grp >= WG) return;
+                // remote loads are issued in batches of 16 float4 a thread: G
+                // chunks of 8 columns times SB slices; the additions still run
+                // in slice order 0, 1, ... for every column
+                constexpr int SB = S2 < 8 ? S2 : 8;
+                constexpr int G = 8 / SB < NCW / 8 ? 8 / SB : NCW / 8;
+                const int cb = (int)rank * CPO + grp * NCW;   // this warpgroup's first tile column
                 uint32_t peer[S2];
 #pragma unroll
                 for (int r = 0; r < S2; ++r) peer[r] = cl_addr(xs, (uint32_t)r);
@@ -1146,32 +1150,35 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
 #pragma unroll 1
                 for (int cg0 = 0; cg0 < NCW; cg0 += 8 * G) {
                     if (nt * BN + cb + cg0 >= live) break;
-                    float4 t[G][S2][2];
+                    float acc[G][8];
 #pragma unroll
-                    for (int g = 0; g < G; ++g)
+                    for (int sb0 = 0; sb0 < S2; sb0 += SB) {
+                        float4 t[G][SB][2];
 #pragma unroll
-                        for (int r = 0; r < S2; ++r)
+                        for (int g = 0; g < G; ++g)
 #pragma unroll
-                            for (int h = 0; h < 2; ++h)
-                                t[g][r][h] = tc::ld_cluster_v4(
-                                    peer[r] + (uint32_t)(((((cb + cg0 + 8 * g) >> 2) + h) * 128 + row) * 16));
+                            for (int r = 0; r < SB; ++r)
+#pragma unroll
+                                for (int h = 0; h < 2; ++h)
+                                    t[g][r][h] = tc::ld_cluster_v4(
+                                        peer[sb0 + r] + (uint32_t)(((((cb + cg0 + 8 * g) >> 2) + h) * 128 + row) * 16));
+#pragma unroll
+                        for (int g = 0; g < G; ++g)
+#pragma unroll
+                            for (int r = 0; r < SB; ++r) {
+                                const float u[8] = {t[g][r][0].x, t[g][r][0].y, t[g][r][0].z, t[g][r][0].w,
+                                                    t[g][r][1].x, t[g][r][1].y, t[g][r][1].z, t[g][r][1].w};
+#pragma unroll
+                                for (int j = 0; j < 8; ++j) acc[g][j] = (sb0 + r == 0) ? u[j] : acc[g][j] + u[j];
+                            }
+                    }
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
                         const int o0 = nt * BN + cb + cg0 + 8 * g;   // first output channel of the chunk
                         if (o0 >= live) break;
-                        float v[8] = {t[g][0][0].x, t[g][0][0].y, t[g][0][0].z, t[g][0][0].w,
-                                      t[g][0][1].x, t[g][0][1].y, t[g][0][1].z, t[g][0][1].w};
+                        float v[8];
 #pragma unroll
-                        for (int r = 1; r < S2; ++r) {
-                            v[0] += t[g][r][0].x;
-                            v[1] += t[g][r][0].y;
-                            v[2] += t[g][r][0].z;
-                            v[3] += t[g][r][0].w;
-                            v[4] += t[g][r][1].x;
-                            v[5] += t[g][r][1].y;
-                            v[6] += t[g][r][1].z;
-                            v[7] += t[g][r][1].w;
-                        }
+                        for (int j = 0; j < 8; ++j) v[j] = acc[g][j];
                         // bias (padded with zeros to the weight rows), leaky
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
@@ -1233,14 +1240,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 }
             };
             if (ok) {
-                if constexpr (BN >= 32) {
-                    if (S == 2) reduce(std::integral_constant<int, 2>{});
-                }
-                if constexpr (BN >= 64) {
-                    if (S == 4) reduce(std::integral_constant<int, 4>{});
-                }
+                if (S == 2) reduce(std::integral_constant<int, 2>{});
+                if (S == 4) reduce(std::integral_constant<int, 4>{});
+                if (S == 8) reduce(std::integral_constant<int, 8>{});
                 if constexpr (BN >= 128) {
-                    if (S == 8) reduce(std::integral_constant<int, 8>{});
+                    if (S == 16) reduce(std::integral_constant<int, 16>{});
                 }
             }
         }
@@ -1634,14 +1638,15 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
         return cudaErrorInvalidValue;
     if (!tc_geometry(BN, a.chb, a.bres, a.k * a.k * a.chunks, MB, CG, &a)) return cudaErrorInvalidValue;
     if (a.ksplit < 1 || a.n_tiles < 1 || a.chunks < 1 || a.k < 1) return cudaErrorInvalidValue;
-    // cluster split-K: clusters of ksplit CTAs (2, 4 or 8; each CTA's share
-    // of a warpgroup's columns a multiple of 8), one work item a CTA, one
+    // cluster split-K: clusters of ksplit CTAs (2, 4, 8 or 16, the last a
+    // non-portable cluster size; each CTA's share of the columns a multiple
+    // of 8), one work item a CTA, one
     // problem, streamed weights, and a ring that holds the 128 x BN FP32
     // partial tile (a tuned ring depth gives way to that)
     if ((SP == 5) != (a.xred != 0)) return cudaErrorInvalidValue;
     if (SP == 5) {
         const int S = a.ksplit;
-        if ((S != 2 && S != 4 && S != 8) || BN % (16 * S) != 0 || a.nprob != 1 || a.bres || a.tapm || a.pair ||
+        if ((S != 2 && S != 4 && S != 8 && S != 16) || BN % (8 * S) != 0 || a.nprob != 1 || a.bres || a.tapm || a.pair ||
             a.withhold || workers != a.m_tiles * a.n_tiles * S)
             return cudaErrorInvalidValue;
         if ((size_t)a.nst * a.st_bytes < (size_t)128 * BN * sizeof(float)) {
@@ -1665,6 +1670,10 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(MB == 2 ? kSmemLimit2 : kSmemLimit));
         if (e != cudaSuccess) return e;
+        if (SP == 5) {   // clusters of 16 CTAs
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+        }
         attr = true;
     }
     cudaLaunchConfig_t cfg = {};
@@ -1694,7 +1703,8 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
 template <int BN>
 static int xred_capacity_bn(int S) {
     auto kern = conv_tc_kernel<BN, DT_BF16, 1, 1, 5>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit) != cudaSuccess) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         (void)cudaGetLastError();
         return 0;
     }
@@ -1718,9 +1728,9 @@ static int xred_capacity_bn(int S) {
 }
 
 int tc_xred_capacity(int BN, int ksplit) {
-    if (ksplit != 2 && ksplit != 4 && ksplit != 8) return 0;
-    if (BN % (16 * ksplit) != 0) return 0;
-    static int cache[3][9] = {};   // (BN 64 / 128 / 256, ksplit); -1: queried, none
+    if (ksplit != 2 && ksplit != 4 && ksplit != 8 && ksplit != 16) return 0;
+    if (BN % (8 * ksplit) != 0) return 0;
+    static int cache[3][17] = {};   // (BN 64 / 128 / 256, ksplit); -1: queried, none
     int& c = cache[BN == 64 ? 0 : BN == 128 ? 1 : 2][ksplit];
     if (c == 0) {
         const int v = BN == 64 ? xred_capacity_bn<64>(ksplit)

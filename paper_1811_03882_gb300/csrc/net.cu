@@ -400,14 +400,29 @@ Plan::~Plan() {
 // N tile) plus BN x 128 B of B.  Measured K-step times with every SM busy:
 // ~900, ~1020, ~1450 cycles for BN = 64, 128, 256 (so 256 does 1.4x the
 // work per byte of 128).  Rounds of ceil(items / SMs) persistent tiles,
-// plus the split-K workspace traffic.
-static double tc_cost(long m_tiles, int ncols, int BN, int ks, int nk, int num_sms) {
+// plus the cost of a K split: reduced inside clusters (BF16, one wave), the
+// partial tile's round trip through distributed shared memory (128 x BN x 4
+// bytes at ~64 bytes a cycle) and ~1500 cycles per doubling of the cluster
+// (calibrated on the 14 x 14 layers at batch 8, where a split of 4 instead
+// of 2 measured no faster); otherwise the
+// workspace written and read back by a reduction launch whose blocks (one
+// per 128-row tile and 64 columns) fill the SMs only on large layers, plus
+// that launch's fixed cost (~3 us).
+static double tc_cost(long m_tiles, int ncols, int BN, int ks, int nk, int num_sms, bool xred) {
     static const double kstep_clk[3] = {900.0, 1020.0, 1450.0};   // BN = 64, 128, 256
     const int bi = BN == 64 ? 0 : BN == 128 ? 1 : 2;
     const long items = m_tiles * cdiv(ncols, BN) * ks;
     const long rounds = (items + num_sms - 1) / num_sms;
     double t = (double)rounds * ((double)nk / ks) * kstep_clk[bi] + rounds * 1500.0;   // + epilogue tail
-    if (ks > 1) t += (double)ks * m_tiles * 128 * cdiv(ncols, BN) * BN * 4.0 * 2.0 / 3450.0;
+    if (ks > 1) {
+        if (xred && items <= num_sms && items <= tc_xred_capacity(BN, ks)) {
+            t += 1500.0 * (1.0 + std::log2((double)ks)) + 128.0 * BN * 4.0 / 64.0;
+        } else {
+            const double blocks = (double)m_tiles * cdiv(ncols, 64);
+            const double bw = 3450.0 * std::min(1.0, blocks / num_sms);   // bytes a cycle
+            t += 6000.0 + (double)ks * m_tiles * 128 * cdiv(ncols, BN) * BN * 4.0 * 2.0 / bw;
+        }
+    }
     return t;
 }
 
@@ -456,6 +471,15 @@ void dn::tc_workers(int m_tiles, int n_tiles, int ks, int BN, int nk, int chb, i
     }
 }
 
+// split-K reduced inside clusters where it can be (NET_TC_XRED=0: never)
+bool dn::tc_xred_on() {
+    static const bool on = [] {
+        const char* e = getenv("NET_TC_XRED");
+        return !(e && atoi(e) == 0);
+    }();
+    return on;
+}
+
 int dn::tc_mb_forced() {
     static const int v = [] {
         const char* e = getenv("NET_TC_MB");
@@ -483,12 +507,12 @@ bool dn::pdl_enabled() {
 
 int dn::tmb_index(int BN) { return BN == 64 ? 0 : BN == 128 ? 1 : 2; }
 
-void dn::tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks) {
+void dn::tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks, bool xred) {
     double best = -1.0;
     for (int bn : {64, 128, 256}) {
         if (bn > rup(ncols, 64)) continue;
         for (int ks = 1; ks <= max_ks && (ks == 1 || ks * 4 <= nk); ks = ks < 2 ? ks + 1 : ks * 2) {
-            const double t = tc_cost(m_tiles, ncols, bn, ks, nk, num_sms);
+            const double t = tc_cost(m_tiles, ncols, bn, ks, nk, num_sms, xred);
             if (best < 0 || t < best) {
                 best = t;
                 *BN = bn;
@@ -564,7 +588,8 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             }
             r.m_tiles = batch * cdiv(r.H, r.TH) * cdiv(r.W, r.TW);
             const int nk = KK * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
-            tc_choose_split(r.m_tiles, ncols, nk, n->num_sms, &r.BN, &r.ksplit);
+            tc_choose_split(r.m_tiles, ncols, nk, n->num_sms, &r.BN, &r.ksplit, 16,
+                            L.in_dt == DT_BF16 && tc_xred_on());
             // overrides (net_set_layer_tiles / net_tune_tiles), if still valid
             // for the layer's current format
             if (L.tile_bn > 0 && L.tile_bn <= rup(ncols, 64)) r.BN = L.tile_bn;
@@ -623,11 +648,7 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
                 // the ksplit CTAs of a tile form a cluster and add their partial
                 // sums through distributed shared memory (no workspace round
                 // trip, no reduction launch)
-                static const bool xred_on = [] {
-                    const char* e = getenv("NET_TC_XRED");
-                    return !(e && atoi(e) == 0);
-                }();
-                r.xred = (xred_on && L.in_dt == DT_BF16 && r.ksplit > 1 && r.mb == 1 && r.cg == 1 && !r.bres &&
+                r.xred = (tc_xred_on() && L.in_dt == DT_BF16 && r.ksplit > 1 && r.mb == 1 && r.cg == 1 && !r.bres &&
                           !r.tapm && !L.pair && items == r.grid && items <= tc_xred_capacity(r.BN, r.ksplit))
                              ? 1
                              : 0;
@@ -656,9 +677,10 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             if (dump)
                 fprintf(stderr,
                         "plan b%d %dx%d layer %d: tile %dx%d BN %d m_tiles %d n_tiles %d ksplit %d grid %d mb %d "
-                        "bres %d kalt %d tapm %d pair %d cg %d xred %d\n",
+                        "bres %d kalt %d tapm %d pair %d cg %d xred %d (cluster capacity %d)\n",
                         batch, h, w, l, r.TW, r.TH, r.BN, r.m_tiles, r.n_tiles, r.ksplit, r.grid, r.mb, r.bres,
-                        r.kalt, r.tapm, L.pair ? 1 : 0, r.cg, r.xred);
+                        r.kalt, r.tapm, L.pair ? 1 : 0, r.cg, r.xred,
+                        r.ksplit > 1 && L.in_dt == DT_BF16 ? tc_xred_capacity(r.BN, r.ksplit) : 0);
         }
         P->runs.push_back(r);
         if (L.d.pool != NET_POOL_2X2S1_SAME) cur ^= 1;

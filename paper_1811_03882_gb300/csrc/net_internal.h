@@ -84,7 +84,12 @@ struct Plan {
 // TC tile choice for an H x W map (pooled layers need whole 2x2 windows in
 // one warp: TW = 8 or 16).
 void tc_choose(int batch, int H, int W, bool pool, int ncols, int num_sms, int* TW, int* TH, int* BN);
-void tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks = 16);
+// xred: the layer's K split may be reduced inside clusters (BF16 operands)
+void tc_choose_split(long m_tiles, int ncols, int nk, int num_sms, int* BN, int* ksplit, int max_ks = 16,
+                     bool xred = false);
+// NET_TC_XRED=0 in the environment keeps every K split on the workspace
+// reduction; read once per process.
+bool tc_xred_on();
 // (N tile, split-K, CTAs per SM) a tensor-core layer can take in its current
 // format (two CTAs an SM for N tiles of at most 128 columns).
 struct TileOpt {

@@ -83,11 +83,12 @@ def test_launch_modes_match_oracle(tmp_path):
     np.testing.assert_array_equal(ys["no_pdl"], ys["default"])
     # the first-layer specialisation runs the generic kernel's operations
     np.testing.assert_array_equal(ys["no_spec"], ys["default"])
-    # the cluster reduction adds the K slices in the workspace reduction's order
-    np.testing.assert_array_equal(ys["no_xred"], ys["default"])
     # a CTA pair accumulates every row's products in the single-CTA order of
     # one MMA issuer: the same bits as that mode
     np.testing.assert_array_equal(ys["pair_no_kalt"], ys["no_kalt"])
     # the first layer's tap pairs sum the same products in another order
-    for name in ("no_kalt", "no_tapm", "im2col", "mb1", "mb2", "pair"):
+    # (without the cluster reduction the planner prices K splits differently,
+    # so the splits and their summation order may change: tests/test_gpu_xred.py
+    # checks bit-identity on fixed plans)
+    for name in ("no_kalt", "no_tapm", "im2col", "mb1", "mb2", "pair", "no_xred"):
         assert oracle.normwise_rel_err(ys[name], ys["default"]) <= 2e-2, name

@@ -7,7 +7,7 @@ columns through distributed shared memory, then applies the epilogue.  The
 additions are the workspace reduction's, in its order, so the result must
 equal NET_TC_XRED=0's (workspace + reduction launch) bit for bit, with one
 launch fewer per split layer.  Cases force the N tile and split (64, 128,
-256 columns; 2, 4, 8 CTAs a cluster) on ragged maps, with and without the
+256 columns; 2, 4, 8, 16 CTAs a cluster) on ragged maps, with and without the
 fused 2x2/s2 pool, for both of the cluster epilogue's outputs: BF16 NHWC
 (a layer followed by another) and FP32 NCHW (the last layer).
 """
@@ -32,6 +32,10 @@ CASES = [
     ("mid_bn64_s2", 128, [(3, 192, synth.POOL_NONE), (1, 10, synth.POOL_NONE)], (64, 2), 2, 20, 20),
     ("mid_pool_bn256_s8", 256, [(3, 256, synth.POOL_2X2S2), (1, 20, synth.POOL_NONE)], (256, 8), 2, 16, 16),
     ("mid_bn128_s8", 512, [(3, 128, synth.POOL_NONE), (1, 24, synth.POOL_NONE)], (128, 8), 1, 9, 11),
+    # 16-CTA clusters (a non-portable size) and 8-column shares (one warpgroup reduces)
+    ("last_bn256_s16", 512, [(3, 256, synth.POOL_NONE)], (256, 16), 1, 13, 13),
+    ("mid_bn128_s16", 512, [(3, 128, synth.POOL_NONE), (1, 12, synth.POOL_NONE)], (128, 16), 1, 9, 11),
+    ("mid_pool_bn64_s8", 256, [(3, 64, synth.POOL_2X2S2), (1, 8, synth.POOL_NONE)], (64, 8), 1, 16, 16),
 ]
 
 
