@@ -120,3 +120,26 @@ def test_strip_height_does_not_change_the_result(rows, monkeypatch):
         out, k, c = J.solve(u0, 1e-4, 40)
     assert (k, c) == (kr, cr)
     np.testing.assert_array_equal(out, ref)
+
+
+@pytest.mark.parametrize("ny,nx,interior,tol,iters", [
+    (96, 96, "zero", 1e-3, 100000), (96, 96, "zero", 9e-4, 100000), (96, 96, "zero", 8e-4, 100000),
+    (37, 53, "random", 0.0, 7), (3, 130, "random", 0.0, 5), (131, 3, "random", 0.0, 4),
+    (257, 515, "random", 0.0, 33), (300, 2050, "random", 2e-4, 999), (4099, 2050, "random", 0.0, 3)])
+def test_fused_pairs_match_single_sweeps(ny, nx, interior, tol, iters, monkeypatch):
+    """Sweeps run in fused pairs (one pass over the grid computes two; a pair
+    whose first sweep meets the stopping rule is redone as a single sweep).
+    Each value is the single sweep's expression, so the grid, the sweep count
+    and the last change equal the one-sweep-a-launch path's
+    (NET_JACOBI_FUSE=0) bit for bit, whichever sweep the rule stops at
+    (odd and even counts; stops inside and at the end of a graph chunk)."""
+    u0 = synth.laplace_grid(26, ny, nx, interior)
+    with _solver(ny, nx) as J:
+        out, k, ch = J.solve(u0, tol, iters)
+    monkeypatch.setenv("NET_JACOBI_FUSE", "0")
+    with _solver(ny, nx) as J:
+        out1, k1, ch1 = J.solve(u0, tol, iters)
+    assert (k, ch) == (k1, ch1)
+    np.testing.assert_array_equal(out, out1)
+    if tol == 0.0:
+        assert k == iters
