@@ -39,6 +39,8 @@ WORKLOADS = {
     # 64 frames, sides drawn from {320, 416, 512, 608}, one grouped launch per layer
     "uneven64-9conv-bf16": ("9-conv", 64, 0, "bf16", synth.SEED_UNEVEN),
 }
+# the configurations measured beside the default one in the same line
+OTHER_CONFIGS = ("single-conv-32-fp32", "9conv-416-b1-fp32", "9conv-416-b1-bf16", "uneven64-9conv-bf16")
 # open-loop serving streams: 32 cameras, Poisson arrivals, sides {320,416,608}
 SERVE_RATES = (200.0, 1000.0, 4000.0)
 DEFAULT = "19conv-448-b8-bf16"
@@ -48,7 +50,7 @@ DEFAULT = "19conv-448-b8-bf16"
 # launches in one forward pass of the workload), with the first 16 hex digits
 # of the SHA-256 of the conv kernel's source when it was captured: the figure
 # is reported only while the source is unchanged, null otherwise.
-TRAFFIC = {"19conv-448-b8-bf16": {"conv_tc_kernel": (208.30e6 / 19, "3914c7bd10c9188f")}}
+TRAFFIC = {"19conv-448-b8-bf16": {"conv_tc_kernel": (208.4e6 / 19, "cebaf9f363764482")}}
 KERNEL_SRC = os.path.join(ROOT, "paper_1811_03882_gb300", "csrc", "k_conv_tc.cu")
 
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
@@ -745,6 +747,8 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-serve", action="store_true", help="leave the serving streams out of the line")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave the other configurations (single conv, 9-conv b1 FP32/BF16, uneven 64) out")
     ap.add_argument("--no-extra", action="store_true",
                     help="leave the detection, nightmare and Jacobi measurements out of the line")
     ap.add_argument("--section", choices=["detect", "jacobi", "nightmare", "trace"],
@@ -790,7 +794,8 @@ def main():
 
     netname, batch, side, prec, seed = WORKLOADS[wl]
 
-    def setup(p, tune=False):
+    def setup(p, tune=False, wl=wl):
+        _, batch, side, _, _ = WORKLOADS[wl]
         W = Workload(torch, binding, dev, wl, p, stream)
         info = {}
         if p == "fp8":
@@ -870,6 +875,31 @@ def main():
                 cmp[p]["tile_search"] = info2["tile_search"]
             W2.net.close()
         line["compare"] = cmp
+    if not args.no_configs and rank == 0:
+        # the other configurations of the workload set, each on its own
+        # network and batch shape (shorter runs: 20 timed steps)
+        oc = {}
+        sub = argparse.Namespace(**vars(args))
+        sub.steps = min(args.steps, 20)
+        for owl in OTHER_CONFIGS:
+            if owl == wl:
+                continue
+            p = WORKLOADS[owl][3]
+            W2, info2 = setup(p, tune=True, wl=owl)
+            m2 = measure(torch, W2, sub, flush, barrier, 1)
+            r2 = roofline(W2, m2["ms_per_step"], W2.net.layer_prec())
+            oc[owl] = {"value": m2["value"], "unit": "calls/s" if WORKLOADS[owl][0] == "single-conv" else "frames/s",
+                       "ms_per_step": m2["ms_per_step"], "frames_per_step": W2.batch,
+                       "e2e": m2["e2e_fps"], "conv_tflops": m2["conv_tflops"],
+                       "roofline": {"bound": r2["bound"], "achieved": r2["achieved"], "peak": r2["peak"],
+                                    "unit": r2["unit"], "frac": r2["frac"]},
+                       "gpu_launches_per_step": m2["launches"] / sub.steps, "steps": sub.steps,
+                       "layer_precision": W2.net.layer_prec()}
+            for k in ("tile_plan", "grouped_plan", "tile_search", "cta_plan"):
+                if k in info2:
+                    oc[owl][k] = info2[k]
+            W2.net.close()
+        line["other_configs"] = oc
     if not args.no_serve and rank == 0:
         line["serving"] = run_serving(args, torch, binding, dev)
     if not args.no_extra and rank == 0:

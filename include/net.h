@@ -402,6 +402,17 @@ net_status net_plan_ctas(net_t* net, int batch, int h, int w, int* mb, int n);
  * overrides: bn[n] and ksplit[n] per layer (0 for CUDA-core layers). */
 net_status net_plan_tiles(net_t* net, int batch, int h, int w, int* bn, int* ksplit, int n);
 
+/* Paper Sec. 3.2 (data stays on the device between the loops that use it),
+ * taken one step further: between the layers of a pass, work starts as
+ * soon as the rows it reads are written.  dep[n] per layer of a batch x h x
+ * w fixed-batch pass: 1 if the layer waits for the previous layer's row
+ * bands (each tile for the previous layer's tile rows under its input rows)
+ * instead of for the whole previous kernel, else 0.  Plain forward passes
+ * (net_forward*, net_forward_detect) use it; passes with per-layer copies
+ * out, calibration or NET_TC_FLOW=0 in the environment do not.  NULL
+ * arguments or n < n_layers: NET_E_INVAL. */
+net_status net_plan_flow(net_t* net, int batch, int h, int w, int* dep, int n);
+
 /* Paper Sec. 3.3 and 4 (the GA) over this library's tile plan.
  * Genetic search over the tile plan: the same algorithm and options as
  * net_tune_precision (max_err bounds the deviation from the analytic plan's

@@ -115,6 +115,7 @@ _SIGS = {
                         ctypes.POINTER(net_ga_opts), ctypes.POINTER(net_tile_result)],
     "net_plan_grouped": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "net_plan_ctas": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int],
+    "net_plan_flow": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int],
     "net_plan_tiles": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                        ctypes.c_int],
     "net_tune_tiles": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -408,6 +409,13 @@ class Net:
         mb = np.zeros(self.n_layers, np.int32)
         check(lib().net_plan_ctas(self.h, batch, h, w, _ptr(mb), self.n_layers))
         return [int(v) for v in mb]
+
+    def plan_flow(self, batch, h, w):
+        """Per layer of the fixed-batch plan: 1 if it waits for the previous
+        layer's row bands instead of the whole previous kernel."""
+        dep = np.zeros(self.n_layers, np.int32)
+        check(lib().net_plan_flow(self.h, batch, h, w, _ptr(dep), self.n_layers))
+        return [int(v) for v in dep]
 
     def plan_tiles(self, batch, h, w):
         """[(bn, ksplit)] per layer of the fixed-batch plan ((0, 0): CUDA cores)."""

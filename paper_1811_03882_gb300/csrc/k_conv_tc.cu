@@ -112,6 +112,73 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// Row-band dataflow between the layers of a pass: counters written by
+// another kernel, polled with relaxed gpu-scope loads (several in flight; an
+// acquire load would hold back the ones after it), then one acquire fence.
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait until the whole previous kernel is done (*done >= done_target:
+// *all_done is set, and later tiles need no wait) or the counters p[0 .. n -
+// 1] all reach `target`, then the fences that order this thread's later
+// reads, the TMA copies included, after what the counters announced.  False
+// (and the code recorded) when `lim` clock64 cycles passed or another role
+// already aborted.  done may be null.
+__device__ __forceinline__ bool flags_wait(const int* p, int n, int target, const int* done, int done_target,
+                                           bool* all_done, volatile int* abort_flag, int* err, int code,
+                                           long long lim) {
+    long long t0 = 0;
+    bool timing = false;
+    for (int i0 = 0; i0 < n;) {
+        const int d = done ? ld_relaxed_gpu(done) : 0;
+        int v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = i0 + j < n ? ld_relaxed_gpu(p + i0 + j) : target;
+        if (done && d >= done_target) {
+            *all_done = true;
+            break;
+        }
+        int ready = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ready += v[j] >= target ? 1 : 0;
+        if (ready == 4) {
+            i0 += 4;
+            continue;
+        }
+        if (*abort_flag) return false;
+        const long long now = clock64();
+        if (!timing) {
+            t0 = now;
+            timing = true;
+        } else if (now - t0 > lim) {
+            *abort_flag = 1;
+            atomicExch(err, code);
+            return false;
+        }
+        __nanosleep(128);
+    }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    return true;
+}
+
+// One increment of a counter (or of two) for the calling warp, after all of
+// its lanes' global stores: each lane's fence orders its stores before the
+// warp barrier, and lane 0 adds 1 after it.  All 32 lanes call it.  A fence
+// costs the warp about a round trip to L2, so callers issue as few as they
+// can and late.
+__device__ __forceinline__ void warp_signal(int* p, int* q = nullptr) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        if (p) asm volatile("red.relaxed.gpu.global.add.s32 [%0], 1;" ::"l"(p) : "memory");
+        if (q) asm volatile("red.relaxed.gpu.global.add.s32 [%0], 1;" ::"l"(q) : "memory");
+    }
+}
+
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const void* tmap, int c0, int c1, int c2,
                                             int c3, uint32_t bar) {
     asm volatile(
@@ -559,7 +626,11 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     // way (weights and problem tables are complete before the forward pass
     // starts).
     const bool lane_producer = warp == 0 || warp == NUM_WARPS - 2;
-    if (!lane_producer) pdl_wait();
+    // row-band dataflow (a.dep): no wait for the whole previous kernel; the
+    // producers wait for the bands each tile reads, and the epilogue for the
+    // layer whose input buffer it overwrites
+    const bool flow = a.dep != nullptr;
+    if (!lane_producer && !flow) pdl_wait();
 
     if (warp == 0 || warp == NUM_WARPS - 2) {
         // ------------------------------------------------ TMA producers
@@ -591,6 +662,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             int ch = 0, kw = 0, kh = 0;   // chunk, tap column, tap row of ks
             int towner = 0, nt = 0, img = 0, x0 = 0, y0 = 0;
             const ConvProblem* P = P1;
+            // row-band dataflow: the previous layer's bands under the current
+            // tile's input rows, waited for before the tile's first A box
+            const int Hin = P1 ? P1->H : 0;
+            const int* dep_p = nullptr;
+            int dep_n = 0;
+            bool dep_need = false, prev_done = false;
             auto slice = [&] {
                 if (kKsplit > 1) {
                     const int z = tile - fdiv(tile, a.fd_ksplit) * kKsplit;
@@ -624,6 +701,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 const int ty = txy - img * tiles_y;
                 x0 = tx * a.TW - pad;
                 y0 = ty * a.TH - pad;
+                if (flow) {   // (single-problem launches)
+                    const int r0 = max(y0, 0), r1 = min(y0 + a.TH - 1 + 2 * pad, Hin - 1);
+                    const int b0 = r0 >> a.dep_shift;
+                    dep_p = a.dep + img * a.dep_nb + b0;
+                    dep_n = (r1 >> a.dep_shift) - b0 + 1;
+                    dep_need = true;
+                }
             };
             auto decompose = [&] {   // (ch, kw, kh) of ks, by division (tile changes only)
                 const int tap = fdiv(ks, a.fd_chunks);
@@ -689,7 +773,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 }
                 pre_b = true;
             }
-            pdl_wait();
+            if (!flow) pdl_wait();
             if (warp == 0 && lane == 0) TRACE(2);
             // per issuer: bit s = phase parity of the next use of full[m][s];
             // per stage this lane fills: the issuer of its last use
@@ -698,6 +782,14 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 const bool act = ok && tile < total;
                 if (!__any_sync(gmask, act) || __any_sync(gmask, !ok)) break;
                 if (act && !tc::mbar_wait(smem_u32(&sm->empty[ps]), eph ^ 1u, abort_flag, a.err, 1, lim)) ok = false;
+                if (act && ok && dep_need && !prev_done) {
+                    // the input rows of a new tile: the previous layer's bands
+                    // complete (or the whole layer), the copies ordered after
+                    if (!tc::flags_wait(dep_p, dep_n, a.dep_target, a.dep_done, a.dep_done_target, &prev_done,
+                                        abort_flag, a.err, 8, lim))
+                        ok = false;
+                }
+                if (act && ok) dep_need = false;
                 __syncwarp(gmask);
                 if (act && ok && a.withhold && it == S2) {
                     // fault injection (tests only): the second K step of producer
@@ -777,6 +869,16 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                     const long long t0 = clock64();
                     while (!tc::mbar_try(bar, lph) && clock64() - t0 < WAIT_LIMIT) {
                     }
+                }
+            }
+            if (a.rd_sig) {
+                // every copy of this warp's lanes has landed: its reads of the
+                // input buffer are over
+                __syncwarp(gmask);
+                if (lane == 0) {
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                    asm volatile("red.relaxed.gpu.global.add.s32 [%0], 1;" ::"l"(a.rd_sig) : "memory");
                 }
             }
         }
@@ -929,6 +1031,15 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             asm volatile("bar.sync 1, 256;" ::: "memory");   // the 8 epilogue warps
         }
         if (lane == 0 && warp == 2) TRACE(5);
+        if (a.rd_dep) {
+            // row-band dataflow: the output buffer was the input of the layer
+            // two back, whose copies must all have landed before it is
+            // overwritten (on expiry the abort flag stops the pipeline)
+            bool unused = false;
+            if (lane == 0)
+                (void)tc::flags_wait(a.rd_dep, 1, a.rd_target, nullptr, 0, &unused, abort_flag, a.err, 9, lim);
+            __syncwarp();
+        }
         const float* e_bias = epi_smem ? s_bias : a.ep.bias;
         const float* e_alpha = epi_smem ? s_alpha : kAlpha;
         const int ymask = a.TW == 16 ? 16 : 8;  // lane distance of the pixel below (pool tiles)
@@ -940,6 +1051,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         int tcount = 0;
         bool have_p = false;   // problem fields loaded (single-problem launches read them once)
         bool pairs_done = false;
+        // row-band dataflow: the band counter of this warp's last tile, whose
+        // increment waits until the next tile's arithmetic is done (the
+        // increment's fence then finds the tile's stores already performed)
+        int* pend = nullptr;
         if constexpr (SP == 1) {
             // The tap-pair first layer, one problem, one N tile, at most CW
             // live columns: a warpgroup drains its next two tiles (tcount t and
@@ -1013,6 +1128,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                             w[j] = *reinterpret_cast<uint32_t*>(&m);
                         }
                     }
+                    // the previous tile's band, now that its stores have had
+                    // this tile's loads and arithmetic to drain
+                    if (pend) {
+                        tc::warp_signal(pend);
+                        pend = nullptr;
+                    }
                     if (writer) {
                         uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ybase) +
                                                               pix * a.ep.out_cs);
@@ -1021,6 +1142,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         for (int i = 0; i < CW / 8; ++i)
                             if (i < nvec) dst[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
                     }
+                    if (a.sig) pend = a.sig + img * TY0 + ty;   // signalled after the next tile's arithmetic
                 };
                 for (int tc = grp;; tc += 4) {
                     const int tile0 = worker + tc * nworkers;
@@ -1246,6 +1368,12 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 if constexpr (BN >= 128) {
                     if (S == 16) reduce(std::integral_constant<int, 16>{});
                 }
+                if (a.sig) {   // every epilogue warp of every CTA of the cluster, once (at the end)
+                    const ConvProblem& P = a.probs[0];
+                    const int txy = fdiv(mt - P.tile_begin, P.fd_tx);
+                    const int img = fdiv(txy, P.fd_ty);
+                    pend = a.sig + img * P.tiles_y + (txy - img * P.tiles_y);
+                }
             }
         }
         for (int tile = (XR || pairs_done) ? total : worker; tile < total; tile += nworkers, ++tcount) {
@@ -1406,6 +1534,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                             v[2 * j + 1] = fmaxf(v[2 * j + 1], s2.y);
                         }
                     }
+                    if (pend) {   // the previous tile's band (its stores had this chunk's loads to drain)
+                        tc::warp_signal(pend);
+                        pend = nullptr;
+                    }
                     if (kOutLayout == LAYOUT_NCHW) {
                         if (pool) {
 #pragma unroll
@@ -1482,9 +1614,16 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                                 *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                     }
                 }
+                if (a.sig) {   // this warp's share of the tile is out: signalled during the next tile
+                    if (pend) tc::warp_signal(pend);
+                    pend = a.sig + img * pTY + ty;
+                }
             }
             if (!released) release();   // a tile without live columns (not produced by the planner)
         }
+        // the last tile's band and, every tile of this warp being out, one
+        // count toward the kernel's end: one fence for both
+        if (pend || a.done_sig) tc::warp_signal(pend, a.done_sig);
         if (lane == 0 && warp == 2) TRACE(6);
         if (lane == 0 && warp == 6) TRACE(7);
     }
@@ -1644,6 +1783,12 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     // problem, streamed weights, and a ring that holds the 128 x BN FP32
     // partial tile (a tuned ring depth gives way to that)
     if ((SP == 5) != (a.xred != 0)) return cudaErrorInvalidValue;
+    // row-band dataflow: single-CTA launches over one problem; a signalling
+    // launch writes its final output itself (no workspace reduction after
+    // it), and a waiting one touches no workspace either
+    if ((a.sig || a.dep || a.rd_sig || a.rd_dep) && (CG != 1 || a.nprob != 1)) return cudaErrorInvalidValue;
+    if ((a.sig || a.dep) && a.ksplit > 1 && !a.xred) return cudaErrorInvalidValue;
+    if (a.dep && (a.dep_shift < 0 || a.dep_shift > 12 || a.dep_nb < 1 || a.dep_target < 1)) return cudaErrorInvalidValue;
     if (SP == 5) {
         const int S = a.ksplit;
         if ((S != 2 && S != 4 && S != 8 && S != 16) || BN % (8 * S) != 0 || a.nprob != 1 || a.bres || a.tapm || a.pair ||

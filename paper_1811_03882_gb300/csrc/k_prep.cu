@@ -13,11 +13,20 @@ static inline unsigned grid_for(size_t n, int threads) {
 }
 
 // ---------------------------------------------------------------- pack
+// The frame pack opens a forward pass, so it also clears the pass's
+// row-band counters (zero[0 .. nzero - 1], spread over the grid): the conv
+// layers after it count from zero.
+__device__ __forceinline__ void clear_counters(int* zero, int nzero) {
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    for (int i = b * blockDim.x + threadIdx.x; i < nzero; i += gridDim.x * gridDim.y * blockDim.x) zero[i] = 0;
+}
+
 // One grid row (blockIdx.y) per frame; a thread per (pixel, group of 16
 // bytes); 32-bit indices within a frame (the host checks the size).
 template <int DT>
 __global__ void pack_kernel(const float* __restrict__ x, void* __restrict__ y, int C, int HW, int Cp,
-                            FastDiv fd_groups, float inv_scale) {
+                            FastDiv fd_groups, float inv_scale, int* zero, int nzero) {
+    clear_counters(zero, nzero);
     constexpr int V = DT == DT_F32 ? 4 : DT == DT_BF16 ? 8 : 16;   // elements per 16 B
     const int groups = Cp / V;
     const int nn = blockIdx.y;
@@ -58,7 +67,9 @@ __global__ void pack_kernel(const float* __restrict__ x, void* __restrict__ y, i
 // BF16, at most 8 channels padded to 8 (one 16-byte group per pixel), the
 // frame's pixel count a multiple of 4: a thread packs four adjacent pixels
 // from one float4 load per channel and stores their 64 contiguous bytes.
-__global__ void pack_bf16_c8_px4_kernel(const float* __restrict__ x, void* __restrict__ y, int C, int HW4) {
+__global__ void pack_bf16_c8_px4_kernel(const float* __restrict__ x, void* __restrict__ y, int C, int HW4, int* zero,
+                                        int nzero) {
+    clear_counters(zero, nzero);
     const int nn = blockIdx.y;
     const int HW = HW4 * 4;
     const float4* xf = reinterpret_cast<const float4*>(x + (size_t)nn * C * HW);
@@ -88,14 +99,19 @@ __global__ void pack_bf16_c8_px4_kernel(const float* __restrict__ x, void* __res
 }
 
 cudaError_t pack_frames(const float* x, void* y, int n, int C, int H, int W, int Cp, int dt,
-                        float inv_scale, cudaStream_t st) {
+                        float inv_scale, cudaStream_t st, int* zero, int nzero) {
+    if (nzero > 0 && (n <= 0 || (size_t)H * W == 0)) {
+        const cudaError_t e = cudaMemsetAsync(zero, 0, (size_t)nzero * sizeof(int), st);
+        if (e != cudaSuccess) return e;
+        nzero = 0;
+    }
     if (dt == DT_BF16 && Cp == 8 && C <= 8 && n > 0 && n <= 65535 && ((size_t)H * W) % 4 == 0 &&
         (size_t)H * W < (size_t)INT32_MAX && ((uintptr_t)x & 15) == 0 && ((uintptr_t)y & 15) == 0) {
         const int HW4 = H * W / 4;
         unsigned bx = (unsigned)((HW4 + 255) / 256);
         const unsigned cap = (152u * 32u + (unsigned)n - 1) / (unsigned)n;
         if (bx > cap) bx = cap;
-        pack_bf16_c8_px4_kernel<<<dim3(bx ? bx : 1, (unsigned)n), 256, 0, st>>>(x, y, C, HW4);
+        pack_bf16_c8_px4_kernel<<<dim3(bx ? bx : 1, (unsigned)n), 256, 0, st>>>(x, y, C, HW4, zero, nzero);
         return cudaGetLastError();
     }
     const int V = dt == DT_F32 ? 4 : dt == DT_BF16 ? 8 : 16;
@@ -108,9 +124,9 @@ cudaError_t pack_frames(const float* x, void* y, int n, int C, int H, int W, int
     const dim3 g(bx ? bx : 1, (unsigned)n);
     const FastDiv fg = make_fast_div(Cp / V);
     const int HW = H * W;
-    if (dt == DT_F32) pack_kernel<DT_F32><<<g, 256, 0, st>>>(x, y, C, HW, Cp, fg, inv_scale);
-    else if (dt == DT_BF16) pack_kernel<DT_BF16><<<g, 256, 0, st>>>(x, y, C, HW, Cp, fg, inv_scale);
-    else pack_kernel<DT_FP8><<<g, 256, 0, st>>>(x, y, C, HW, Cp, fg, inv_scale);
+    if (dt == DT_F32) pack_kernel<DT_F32><<<g, 256, 0, st>>>(x, y, C, HW, Cp, fg, inv_scale, zero, nzero);
+    else if (dt == DT_BF16) pack_kernel<DT_BF16><<<g, 256, 0, st>>>(x, y, C, HW, Cp, fg, inv_scale, zero, nzero);
+    else pack_kernel<DT_FP8><<<g, 256, 0, st>>>(x, y, C, HW, Cp, fg, inv_scale, zero, nzero);
     return cudaGetLastError();
 }
 

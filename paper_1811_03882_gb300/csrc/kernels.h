@@ -53,9 +53,10 @@ struct SplitReduce {
 cudaError_t splitk_reduce(const SplitReduce& r, cudaStream_t st);
 
 // Frame NCHW float32 -> NHWC (channel stride Cp, zero padded) in dtype dt;
-// FP8 codes are value * inv_scale.
+// FP8 codes are value * inv_scale.  zero[0 .. nzero - 1] (a forward pass's
+// row-band counters) are cleared by the same launch.
 cudaError_t pack_frames(const float* x, void* y, int n, int C, int H, int W, int Cp, int dt,
-                        float inv_scale, cudaStream_t st);
+                        float inv_scale, cudaStream_t st, int* zero = nullptr, int nzero = 0);
 
 // Frame NCHW float32 -> "im2col" NHWC for a k x k first layer with few
 // channels: channel j = (kh*k + kw)*C + c of pixel (i, j) holds
@@ -187,6 +188,30 @@ struct TcArgs {
     unsigned long long* trace;
     // division by ksplit, n_tiles, chunks, k and nst (filled by conv_tc_launch)
     FastDiv fd_ksplit, fd_ntiles, fd_chunks, fd_k, fd_nst;
+    // Row-band dataflow between consecutive layers of a fixed-batch pass (all
+    // null: the dependency wait orders the launch after the whole previous
+    // kernel).  sig: this launch's output bands, one counter per (frame, tile
+    // row), to which every epilogue warp that drains a tile adds 1 once its
+    // stores are done.  dep: the previous layer's sig; instead of the
+    // dependency wait, a producer waits for the bands under a tile's input
+    // rows (a band is 2^dep_shift input rows, dep_nb bands a frame, complete
+    // at dep_target) before it loads them.  rd_sig: this launch's input-read
+    // counter (each producer warp adds 1 once its last copy has landed);
+    // rd_dep: the counter of the layer whose input buffer this launch
+    // overwrites, which the epilogue waits for (rd_target) before its first
+    // store.  done_sig: this launch's finished-warp counter (each epilogue
+    // warp adds 1 after its last tile); dep_done: the previous layer's, at
+    // dep_done_target the whole layer is out and a producer stops waiting
+    // for bands.  The counters are cleared by the pass's frame pack.
+    int* sig;
+    const int* dep;
+    int dep_shift, dep_nb, dep_target;
+    int* rd_sig;
+    const int* rd_dep;
+    int rd_target;
+    int* done_sig;
+    const int* dep_done;
+    int dep_done_target;
 };
 
 // Grouped memory-bound helpers: one launch over several frames of

@@ -204,7 +204,7 @@ extern "C" net_status net_create(const net_desc* d, net_t** out) {
         n->act_bytes = std::max(n->act_bytes, act_bytes_for(n.get(), n->max_batch, n->max_side, n->max_side));
         n->L = keep;
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {
         CK(dn::dalloc(&n->act[i], n->act_bytes));
         CK(cudaMemsetAsync(n->act[i], 0, n->act_bytes, n->stream));
     }
@@ -392,6 +392,15 @@ static float in_scale(const Layer& L) { return L.in_dt == DT_FP8 ? (float)L.act_
 Plan::~Plan() {
     for (auto& r : runs)
         if (r.d_prob) dn::dfree(r.d_prob);
+    if (flags) dn::dfree(flags);
+}
+
+bool dn::tc_flow_on() {
+    static const bool on = [] {
+        const char* e = getenv("NET_TC_FLOW");
+        return !(e && atoi(e) == 0);
+    }();
+    return on;
 }
 
 // Analytic tile/split choice for the tensor-core kernel.  The mainloop is
@@ -561,7 +570,7 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
         const bool last = l + 1 == nl;
         LayerRun r;
         r.in_buf = cur;
-        r.out_buf = cur ^ 1;
+        r.out_buf = (cur + 1) % 3;
         r.H = H[l];
         r.W = W[l];
         const int out_cs = last ? rup(L.d.cout, 4) : n->L[l + 1].in_cs;
@@ -668,6 +677,14 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             hp.tiles_y = cdiv(r.H, r.TH);
             tc_problem_divisors(hp);
             hp.tile_begin = 0;
+            // row-band counters: one per (frame, tile row) of the output, and
+            // the input-read counter
+            if (r.cg == 1) {
+                r.sig_off = P->nflags;
+                P->nflags += batch * hp.tiles_y;
+                r.rd_off = P->nflags++;
+                r.done_off = P->nflags++;
+            }
             // the table is complete on the device before any launch reads it
             // (kernels read it ahead of their dependency wait)
             CK(dn::dalloc(&r.d_prob, sizeof(ConvProblem)));
@@ -683,7 +700,12 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
                         r.ksplit > 1 && L.in_dt == DT_BF16 ? tc_xred_capacity(r.BN, r.ksplit) : 0);
         }
         P->runs.push_back(r);
-        if (L.d.pool != NET_POOL_2X2S1_SAME) cur ^= 1;
+        if (L.d.pool != NET_POOL_2X2S1_SAME) cur = (cur + 1) % 3;
+    }
+    if (P->nflags > 0) {
+        CK(dn::dalloc(&P->flags, (size_t)P->nflags * sizeof(int)));
+        CK(cudaMemsetAsync(P->flags, 0, (size_t)P->nflags * sizeof(int), n->stream));
+        CK(cudaStreamSynchronize(n->stream));
     }
     if (P->ws_bytes > n->ws_bytes) {
         // grow the split-K workspace; graphs captured on the old one are dropped
@@ -708,6 +730,47 @@ net_status dn::check_device_error(net* n) {
     return NET_OK;
 }
 
+// Row-band dataflow of a fixed-batch plan: layer l runs without the
+// dependency wait on the whole previous kernel (dep[l] = 1) when layers l - 1
+// and l are tensor-core launches whose epilogues write their final outputs
+// (no K split through the workspace, no reduction launch), no stride-1 pool
+// sits among layers l - 2 .. l - 1, and layer l - 2 (whose input buffer
+// layer l overwrites) is a tensor-core launch that counts its finished reads,
+// or the pack.  Every tile a layer l - 1 epilogue warp drains costs it a
+// release fence (about a round trip to L2), so only layers whose epilogue
+// warps drain at most four tiles each signal their bands (at 19-conv 448^2
+// b8 the first layer's 41 tiles a warp cost it 24 us of fences; a limit of
+// two or eight tiles measured slower than four).  wpt[l]: the epilogue
+// warps that add to a band per tile of layer l.  False (and nothing set)
+// when the dataflow is off.
+static bool flow_layers(const net* n, const Plan* plan, std::vector<char>& dep, std::vector<int>& wpt) {
+    const int nl = (int)n->L.size();
+    dep.assign(nl, 0);
+    wpt.assign(nl, 0);
+    if (!plan || !plan->flags || !pdl_enabled() || !tc_flow_on()) return false;
+    std::vector<char> own(nl, 0), cheap(nl, 0);
+    auto s1 = [&](int l) { return n->L[l].d.pool == NET_POOL_2X2S1_SAME; };
+    for (int l = 0; l < nl; ++l) {
+        const LayerRun& r = plan->runs[l];
+        if (n->L[l].engine != ENG_TC || r.cg != 1 || r.sig_off < 0) continue;
+        const bool last = l + 1 == nl;
+        // the cluster reduction's epilogue writes BF16 NHWC (inner layers)
+        const bool xr = r.xred && !last && !s1(l) && n->L[l + 1].in_dt == DT_BF16;
+        if (r.ksplit == 1 || xr) {
+            own[l] = 1;
+            const int items = r.m_tiles * r.n_tiles * r.ksplit;
+            const int per_cta = cdiv(items, std::max(1, r.grid));
+            const int per_warp = r.kalt || xr ? per_cta : cdiv(per_cta, 2);
+            cheap[l] = per_warp <= 4;
+            wpt[l] = xr ? 8 * r.ksplit : r.kalt ? 8 : 4;
+        }
+    }
+    for (int l = 1; l < nl; ++l)
+        dep[l] = own[l] && own[l - 1] && cheap[l - 1] && !s1(l - 1) &&
+                 (l < 2 || (n->L[l - 2].engine == ENG_TC && plan->runs[l - 2].cg == 1 && !s1(l - 2)));
+    return true;
+}
+
 net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int w, float* d_out,
                                float* const* trace, bool fp32_copy, float* amax) {
     std::vector<int> H, W;
@@ -721,8 +784,19 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
     }
     auto in_dt = [&](int l) { return fp32_copy ? DT_F32 : n->L[l].in_dt; };
     auto in_cs = [&](int l) { return fp32_copy ? n->L[l].cs32 : n->L[l].in_cs; };
-    void* buf[2] = {fp32_copy ? n->cal[0] : n->act[0], fp32_copy ? n->cal[1] : n->act[1]};
+    // the FP32 calibration copy alternates between two buffers; the pass
+    // proper runs on the ring of three
+    void* buf[3] = {fp32_copy ? n->cal[0] : n->act[0], fp32_copy ? n->cal[1] : n->act[1],
+                    fp32_copy ? nullptr : n->act[2]};
+    auto nxt = [&](int c) { return fp32_copy ? c ^ 1 : (c + 1) % 3; };
     int cur = 0;
+    // Row-band dataflow (flow_layers): not with per-layer copies out (trace),
+    // calibration or fault injection
+    std::vector<char> dep(nl, 0);
+    std::vector<int> wpt(nl, 0);
+    const bool flow_ok = !fp32_copy && !amax && !trace && plan && n->fault_layer < 0 && flow_layers(n, plan, dep, wpt);
+    int* zero = flow_ok ? plan->flags : nullptr;
+    const int nzero = flow_ok ? plan->nflags : 0;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cap);
     auto mark = [&](cudaEvent_t ev) {
@@ -736,8 +810,11 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
         e = pack_frames_im2col(d_in, buf[cur], batch, n->in_c, h, w, in_cs(0), n->L[0].im2col_k, in_dt(0),
                                1.f / in_scale(n->L[0]), st);
     } else {
-        e = pack_frames(d_in, buf[cur], batch, n->in_c, h, w, in_cs(0), in_dt(0), 1.f / in_scale(n->L[0]), st);
+        e = pack_frames(d_in, buf[cur], batch, n->in_c, h, w, in_cs(0), in_dt(0), 1.f / in_scale(n->L[0]), st, zero,
+                        nzero);
+        zero = nullptr;
     }
+    if (e == cudaSuccess && zero) e = cudaMemsetAsync(zero, 0, (size_t)nzero * sizeof(int), st);   // (im2col pack)
     if (e != cudaSuccess) return fail(NET_E_CUDA, "pack: %s", cudaGetErrorString(e));
     for (int l = 0; l < nl; ++l) {
         const Layer& L = n->L[l];
@@ -762,7 +839,7 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
             ep.out_dt = DT_F32;
             ep.out_cs = L.d.cout;
         } else {
-            y = buf[cur ^ 1];
+            y = buf[nxt(cur)];
             ep.out_layout = LAYOUT_NHWC;
             ep.out_dt = last ? DT_F32 : in_dt(l + 1);
             ep.out_cs = last ? rup(L.d.cout, 4) : in_cs(l + 1);
@@ -803,6 +880,32 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                                      (ep.out_layout == LAYOUT_NCHW && ep.out_dt == DT_F32)))
                              ? 1
                              : 0;
+                if (flow_ok && n->L[l].engine == ENG_TC && r.cg == 1 && r.rd_off >= 0) {
+                    a.rd_sig = plan->flags + r.rd_off;   // read by layer l + 2, if it waits on it
+                    if (l + 1 < nl && dep[l + 1]) {
+                        a.sig = plan->flags + r.sig_off;
+                        a.done_sig = plan->flags + r.done_off;
+                    }
+                    if (dep[l]) {
+                        const LayerRun& rp = plan->runs[l - 1];
+                        const bool pooled = n->L[l - 1].d.pool == NET_POOL_2X2S2;
+                        const int band = pooled ? rp.TH / 2 : rp.TH;   // output rows of a tile row
+                        int sh = 0;
+                        while ((1 << sh) < band) ++sh;
+                        if ((1 << sh) != band) return fail(NET_E_UNSUPPORTED, "layer %d: band of %d rows", l, band);
+                        a.dep = plan->flags + rp.sig_off;
+                        a.dep_shift = sh;
+                        a.dep_nb = cdiv(rp.H, rp.TH);
+                        a.dep_target = cdiv(rp.W, rp.TW) * rp.n_tiles * wpt[l - 1];
+                        a.dep_done = plan->flags + rp.done_off;
+                        a.dep_done_target = 8 * rp.grid;   // eight epilogue warps a CTA
+                        if (l >= 2) {
+                            const LayerRun& r2 = plan->runs[l - 2];
+                            a.rd_dep = plan->flags + r2.rd_off;
+                            a.rd_target = 2 * r2.grid;   // two producer warps a CTA
+                        }
+                    }
+                }
                 if (l == n->fault_layer) {
                     // net_inject_device_fault: a ~1 ms bound (clock64 cycles at
                     // ~2 GHz) and one K step withheld by a producer, once (a
@@ -856,10 +959,10 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
         const float osc = (last || ep.out_dt != DT_FP8) ? 1.f : in_scale(n->L[l + 1]);
         if (s1) {
             ++n->pending;
-            e = maxpool_s1_same(buf[cur ^ 1], buf[cur], batch, H[l + 1], W[l + 1], ep.out_cs, ep.out_dt, st);
+            e = maxpool_s1_same(buf[nxt(cur)], buf[cur], batch, H[l + 1], W[l + 1], ep.out_cs, ep.out_dt, st);
             // pooled result is back in buf[cur]
         } else {
-            cur ^= 1;
+            cur = nxt(cur);
         }
         if (e == cudaSuccess && (trace && trace[l]) && ++n->pending)
             e = unpack_nchw(buf[cur], trace[l], batch, L.d.cout, H[l + 1], W[l + 1], ep.out_cs, ep.out_dt, osc, st);
@@ -998,6 +1101,22 @@ extern "C" net_status net_plan_ctas(net_t* n, int batch, int h, int w, int* mb, 
     s = get_plan(n, batch, h, w, &P);
     if (s != NET_OK) return s;
     for (size_t l = 0; l < n->L.size(); ++l) mb[l] = n->L[l].engine == ENG_TC ? P->runs[l].mb : 0;
+    return NET_OK;
+}
+
+extern "C" net_status net_plan_flow(net_t* n, int batch, int h, int w, int* dep, int nn) {
+    if (!n || !dep) return fail(NET_E_INVAL, "NULL argument");
+    if (nn < (int)n->L.size()) return fail(NET_E_INVAL, "need %d entries", (int)n->L.size());
+    net_status s = check_shape(n, batch, h, w);
+    if (s != NET_OK) return s;
+    CK(cudaSetDevice(n->device));
+    Plan* P = nullptr;
+    s = get_plan(n, batch, h, w, &P);
+    if (s != NET_OK) return s;
+    std::vector<char> d;
+    std::vector<int> wpt;
+    flow_layers(n, P, d, wpt);
+    for (size_t l = 0; l < n->L.size(); ++l) dep[l] = d[l];
     return NET_OK;
 }
 
@@ -1322,6 +1441,7 @@ extern "C" net_status net_free(net_t* n) {
     if (n->err_host) cudaFreeHost(n->err_host);
     dn::dfree(n->act[0]);
     dn::dfree(n->act[1]);
+    dn::dfree(n->act[2]);
     async_free(n);
     dn::dfree(n->d_in_stage);
     dn::dfree(n->d_out_stage);

@@ -71,6 +71,8 @@ struct LayerRun {
     int nst_cap = 0;               // TC: ring stages at most (0: as many as fit)
     int tapm = 0;                  // TC: ring stages of all nine taps (3x3, resident weights)
     int xred = 0;                  // TC: split-K reduced inside clusters of ksplit CTAs (BF16)
+    int sig_off = -1, rd_off = -1, done_off = -1; // TC: row-band counters (batch x tile rows), input-read and
+                                                  // finished-warp counters in Plan::flags
     int sbn = 64, sth = 8, stw = 16; // CUDA-core tile
     ConvProblem* d_prob = nullptr; // TC: device problem table (one entry)
 };
@@ -78,8 +80,14 @@ struct LayerRun {
 struct Plan {
     std::vector<LayerRun> runs;
     size_t ws_bytes = 0;           // split-K workspace this plan needs
+    int* flags = nullptr;          // row-band dataflow counters of every TC layer (cleared by each pass's pack)
+    int nflags = 0;
     ~Plan();
 };
+// NET_TC_FLOW=0 in the environment keeps every tensor-core launch behind the
+// dependency wait on the whole previous kernel (no row-band dataflow); read
+// once per process.
+bool tc_flow_on();
 
 // TC tile choice for an H x W map (pooled layers need whole 2x2 windows in
 // one warp: TW = 8 or 16).
@@ -126,7 +134,11 @@ struct net {
     bool has_fp8 = false;
     bool weights_loaded = false;
     bool use_graphs = true;
-    void* act[2] = {nullptr, nullptr};
+    // activation buffers, a ring of three: layer l reads act[l % 3] and
+    // writes act[(l + 1) % 3] (the stride-1 pool writes back into its conv's
+    // input), so a layer that starts before the one two back has finished
+    // reading overwrites nothing it still reads
+    void* act[3] = {nullptr, nullptr, nullptr};
     size_t act_bytes = 0;
     void* cal[2] = {nullptr, nullptr};
     float* d_in_stage = nullptr;

@@ -10,7 +10,9 @@ rings on half the shared memory and the 16-column epilogue), and CTA pairs
 stream N tiles of 128 or 256 columns), the generic kernel for the
 tap-pair first layer instead of its specialised variant (NET_TC_SPEC=0), and
 split-K layers reduced through the workspace by a reduction launch instead
-of inside their clusters (NET_TC_XRED=0).
+of inside their clusters (NET_TC_XRED=0), and every layer behind the
+dependency wait on the whole previous kernel instead of the row-band
+dataflow (NET_TC_FLOW=0).
 Every mode must give the oracle's answer within
 the BF16 budget and agree with the default mode to BF16 rounding; the
 19-conv network at 2 x 160 x 160 has layers with one and with several work
@@ -72,15 +74,18 @@ def test_launch_modes_match_oracle(tmp_path):
                       ("im2col", {"NET_L0_PAIR": "0"}), ("no_tapm", {"NET_TC_TAPM": "0"}),
                       ("mb1", {"NET_TC_MB": "1"}), ("mb2", {"NET_TC_MB": "2"}),
                       ("pair", {"NET_TC_PAIR": "1"}), ("pair_no_kalt", {"NET_TC_PAIR": "1", "NET_TC_KALT": "0"}),
-                      ("no_spec", {"NET_TC_SPEC": "0"}), ("no_xred", {"NET_TC_XRED": "0"})):
+                      ("no_spec", {"NET_TC_SPEC": "0"}), ("no_xred", {"NET_TC_XRED": "0"}),
+                      ("no_flow", {"NET_TC_FLOW": "0"})):
         y = _run(tmp_path, name, env)
         assert np.isfinite(y).all(), name
         e = oracle.normwise_rel_err(y, ex)
         agree, _, _ = oracle.argmax_agreement(y, ex, 2e-2)
         assert e <= 2e-2 and agree >= 0.99, (name, e, agree)
         ys[name] = y
-    # programmatic launch changes only when kernels start, never what they add
+    # programmatic launch and the row-band dataflow change only when kernels
+    # start and what they wait for, never what they add
     np.testing.assert_array_equal(ys["no_pdl"], ys["default"])
+    np.testing.assert_array_equal(ys["no_flow"], ys["default"])
     # the first-layer specialisation runs the generic kernel's operations
     np.testing.assert_array_equal(ys["no_spec"], ys["default"])
     # a CTA pair accumulates every row's products in the single-CTA order of

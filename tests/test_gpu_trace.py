@@ -2,8 +2,11 @@
 
 The trace must not change what a pass computes, every CTA of every
 tensor-core layer must leave its stamps in program order, and the
-dependency wait must hold: no CTA of layer l + 1 gets past its wait for the
-previous kernel before the last CTA of layer l has finished.
+dependency wait must hold: no CTA of a layer that waits for the whole
+previous kernel gets past that wait before the last CTA of the previous
+layer has finished.  Layers on the row-band dataflow (net_plan_flow) start
+earlier by design; at least one layer of this pass must be one, and at
+least one must still wait for the whole previous kernel.
 """
 import numpy as np
 import pytest
@@ -36,6 +39,8 @@ def test_trace_stamps_are_ordered_and_change_nothing():
         buf = net.trace_read().astype(np.int64)
         net.trace(False)
         y3 = run_device(net, x)
+        flow = net.plan_flow(2, 160, 160)
+    assert any(flow) and not all(flow), flow
     np.testing.assert_array_equal(y1, y0)
     np.testing.assert_array_equal(y2, y0)
     np.testing.assert_array_equal(y3, y0)
@@ -54,6 +59,6 @@ def test_trace_stamps_are_ordered_and_change_nothing():
         assert (B[:, 3] <= B[:, 4]).all() and (B[:, 5] <= B[:, 6]).all(), l
         # the closing barrier comes after every role's last stamp
         assert (B[:, 8] >= B[:, [1, 2, 4, 6, 7]].max(axis=1)).all(), l
-        if prev_end is not None:
+        if prev_end is not None and not flow[l]:
             assert B[:, 2].min() >= prev_end, l  # programmatic launch waited for the whole previous grid
         prev_end = int(B[:, 8].max())
