@@ -514,7 +514,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     float* s_bias = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(sm) + ((sizeof(Smem) + 15) & ~(size_t)15));
     float* s_alpha = s_bias + kEpiCols;
 
-    pdl_trigger();   // the next kernel may start its prologue as SMs free up
+    // the next kernel may start its prologue as SMs free up (the first layer
+    // of a pass on the row-band dataflow triggers only after its dependency
+    // wait: the layers after it read counters the frame pack clears)
+    if (!a.late_trigger) pdl_trigger();
 #define TRACE(e) \
     do {                                   \
         if (a.trace) tc::trace_stamp(a.trace, e); \
@@ -630,7 +633,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     // producers wait for the bands each tile reads, and the epilogue for the
     // layer whose input buffer it overwrites
     const bool flow = a.dep != nullptr;
-    if (!lane_producer && !flow) pdl_wait();
+    if (!lane_producer && !flow) {
+        pdl_wait();
+        if (a.late_trigger) pdl_trigger();
+    }
 
     if (warp == 0 || warp == NUM_WARPS - 2) {
         // ------------------------------------------------ TMA producers
@@ -643,6 +649,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
         const int pid = warp == 0 ? 0 : 1;
         const int G = a.plane;
         const int S2 = 2 * G;
+        if (a.late_trigger && lane >= G && !flow) {   // lanes without a producer role
+            pdl_wait();
+            pdl_trigger();
+        }
         if (lane < G) {
             const unsigned gmask = (1u << G) - 1u;
             // a single-problem launch keeps the problem's fields in registers
@@ -773,7 +783,10 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                 }
                 pre_b = true;
             }
-            if (!flow) pdl_wait();
+            if (!flow) {
+                pdl_wait();
+                if (a.late_trigger) pdl_trigger();
+            }
             if (warp == 0 && lane == 0) TRACE(2);
             // per issuer: bit s = phase parity of the next use of full[m][s];
             // per stage this lane fills: the issuer of its last use

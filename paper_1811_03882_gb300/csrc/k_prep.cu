@@ -17,6 +17,10 @@ static inline unsigned grid_for(size_t n, int threads) {
 // row-band counters (zero[0 .. nzero - 1], spread over the grid): the conv
 // layers after it count from zero.
 __device__ __forceinline__ void clear_counters(int* zero, int nzero) {
+    // the first conv layer may start its prologue now (it waits for this
+    // kernel's completion before it reads the frames): 0.3658 -> 0.3626 ms
+    // per 19-conv 448^2 b8 pass
+    pdl_trigger();
     const int b = blockIdx.y * gridDim.x + blockIdx.x;
     for (int i = b * blockDim.x + threadIdx.x; i < nzero; i += gridDim.x * gridDim.y * blockDim.x) zero[i] = 0;
 }

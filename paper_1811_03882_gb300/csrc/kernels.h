@@ -212,6 +212,9 @@ struct TcArgs {
     int* done_sig;
     const int* dep_done;
     int dep_done_target;
+    // 1: let the next kernel launch only once this one is past its
+    // dependency wait (the first layer of a pass on the row-band dataflow)
+    int late_trigger;
 };
 
 // Grouped memory-bound helpers: one launch over several frames of

@@ -880,6 +880,10 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                                      (ep.out_layout == LAYOUT_NCHW && ep.out_dt == DT_F32)))
                              ? 1
                              : 0;
+                // the frame pack lets this launch start early; the layers after
+                // it must not start before the pack (which clears the counters)
+                // has completed
+                if (flow_ok && l == 0) a.late_trigger = 1;
                 if (flow_ok && n->L[l].engine == ENG_TC && r.cg == 1 && r.rd_off >= 0) {
                     a.rd_sig = plan->flags + r.rd_off;   // read by layer l + 2, if it waits on it
                     if (l + 1 < nl && dep[l + 1]) {
