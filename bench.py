@@ -50,7 +50,7 @@ DEFAULT = "19conv-448-b8-bf16"
 # launches in one forward pass of the workload), with the first 16 hex digits
 # of the SHA-256 of the conv kernel's source when it was captured: the figure
 # is reported only while the source is unchanged, null otherwise.
-TRAFFIC = {"19conv-448-b8-bf16": {"conv_tc_kernel": (208.4e6 / 19, "cebaf9f363764482")}}
+TRAFFIC = {"19conv-448-b8-bf16": {"conv_tc_kernel": (208.5e6 / 19, "afb69d3aa1b559db")}}
 KERNEL_SRC = os.path.join(ROOT, "paper_1811_03882_gb300", "csrc", "k_conv_tc.cu")
 
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
@@ -609,6 +609,10 @@ def run_trace(torch, binding, wl, args):
              "prologue": float(np.median(B[:, 1] - B[:, 0])), "dep": float(B[:, 2].min()),
              "fill": float(np.median(B[:, 3] - B[:, 2])), "mainloop": float(np.median(B[:, 4] - B[:, 3])),
              "tail": float(np.median(ep_end - B[:, 4])), "end": float(B[:, 8].max()),
+             # the tail split at warp 2's last accumulator ready: the last MMAs
+             # in the tensor pipe, then that tile's epilogue
+             "mma_drain": float(np.median(B[:, 9] - B[:, 4])) if B[:, 9].all() else None,
+             "last_epilogue": float(np.median(ep_end - B[:, 9])) if B[:, 9].all() else None,
              "straggle": float(B[:, 8].max() - np.median(B[:, 8]))}
         r["dep_to_end"] = r["end"] - r["dep"]
         r["gap"] = None if prev_end is None else r["dep"] - prev_end

@@ -460,10 +460,13 @@ net_status net_profile(net_t* net, int enable);
  * no counterpart).  With enable != 0 (which clears the record) every later
  * fixed-batch forward pass makes each CTA of each tensor-core layer write
  * GPU globaltimer stamps (nanoseconds) at ten points: 0 kernel start,
- * 1 prologue done, 2 first producer past the wait for the previous kernel,
+ * 1 prologue done, 2 first producer past the wait for the previous kernel
+ * (a layer on the row-band dataflow has none: its producer's start),
  * 3 first K step ready for the first MMA issuer, 4 its last MMA issued,
  * 5 epilogue warp 2 started, 6 epilogue warp 2 done, 7 epilogue warp 6
- * done, 8 closing barrier passed (9 unused); 0 where nothing was written
+ * done, 8 closing barrier passed, 9 epilogue warp 2's last accumulator
+ * ready (its last tile's MMAs complete; not written by the tap-pair first
+ * layer, whose epilogue is its bound); 0 where nothing was written
  * (CUDA-core layers, grids beyond 512 CTAs).  net_trace_read waits for the
  * handle's stream and copies the record, n_layers x 512 x 10 uint64 in that
  * order, to out (host, cap entries at least); NET_E_STATE if tracing was

@@ -170,6 +170,32 @@ __device__ __forceinline__ bool flags_wait(const int* p, int n, int target, cons
 // warp barrier, and lane 0 adds 1 after it.  All 32 lanes call it.  A fence
 // costs the warp about a round trip to L2, so callers issue as few as they
 // can and late.
+// Coalesced BF16 stores of an unpooled epilogue chunk.  Lane i of a warp
+// holds NV 16-byte pieces of one pixel's channels, and lanes 4k .. 4k + 3
+// (NV = 4) or 2k, 2k + 1 (NV = 2) are horizontally adjacent pixels of one
+// tile row.  A transpose by xor shuffles (one round per factor of two) leaves
+// lane 4k + j holding piece j of each of its group's pixels, so one store
+// instruction writes whole 16 NV-byte runs instead of one 16-byte piece of
+// 32 pixels.
+template <int NV>
+__device__ __forceinline__ void group_transpose(uint4 (&v)[NV], int lane) {
+#pragma unroll
+    for (int s = 1; s < NV; s <<= 1) {
+        const bool hi = (lane & s) != 0;
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+            if (a & s) continue;
+            uint4 t = hi ? v[a] : v[a + s];
+            t.x = __shfl_xor_sync(0xffffffffu, t.x, s);
+            t.y = __shfl_xor_sync(0xffffffffu, t.y, s);
+            t.z = __shfl_xor_sync(0xffffffffu, t.z, s);
+            t.w = __shfl_xor_sync(0xffffffffu, t.w, s);
+            if (hi) v[a] = t;
+            else v[a + s] = t;
+        }
+    }
+}
+
 __device__ __forceinline__ void warp_signal(int* p, int* q = nullptr) {
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
     __syncwarp();
@@ -1208,6 +1234,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             bool ok = worker < total;
             if (ok) ok = tc::mbar_wait(smem_u32(&sm->accf[0]), 0u, abort_flag, a.err, 4, lim);
             if (ok && kKalt) ok = tc::mbar_wait(smem_u32(&sm->accf[1]), 0u, abort_flag, a.err, 4, lim);
+            if (ok && lane == 0 && warp == 2) TRACE(9);
             if (ok) {
                 tc::fence_after();
                 // the ring was last written by TMA (the async proxy)
@@ -1398,6 +1425,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             const uint32_t aph = (uint32_t)(tcount >> nsl_log) & 1u;
             if (!tc::mbar_wait<C2>(smem_u32(&sm->accf[b]), aph, abort_flag, a.err, 4, lim)) break;
             if (kKalt && !tc::mbar_wait(smem_u32(&sm->accf[b + 1]), aph, abort_flag, a.err, 4, lim)) break;
+            if (lane == 0 && warp == 2) TRACE(9);
             tc::fence_after();
             const int mn = kKsplit > 1 ? fdiv(tile, a.fd_ksplit) : tile;
             const int z = tile - mn * kKsplit;
@@ -1589,6 +1617,24 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                                             *reinterpret_cast<__nv_bfloat162*>(&o));
                                 w[j] = *reinterpret_cast<uint32_t*>(&m);
                             }
+                        }
+                        if (MB == 1 && SP != 1 && !pool && a.ep.out_cs - o0 >= CW) {
+                            // whole chunk: stored through the lane-group transpose
+                            // (one CTA an SM: the 80-register variant would spill;
+                            // the tap-pair first layer always pools)
+                            constexpr int NV = CW / 8;
+                            uint4 pc[NV];
+#pragma unroll
+                            for (int i = 0; i < NV; ++i) pc[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+                            tc::group_transpose<NV>(pc, lane);
+                            const int jj = lane & (NV - 1), gx0 = gx - jj;   // piece jj of pixels gx0 ..
+                            __nv_bfloat16* row0 = reinterpret_cast<__nv_bfloat16*>(ybase) +
+                                                  (((size_t)img * pH + gy) * pW + gx0) * a.ep.out_cs + o0 + 8 * jj;
+#pragma unroll
+                            for (int i = 0; i < NV; ++i)
+                                if (gy < pH && gx0 + i < pW)
+                                    *reinterpret_cast<uint4*>(row0 + (size_t)i * a.ep.out_cs) = pc[i];
+                            continue;
                         }
                         if (writer && o0 < a.ep.out_cs) {
                             uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ybase) +

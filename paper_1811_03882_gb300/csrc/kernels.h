@@ -243,7 +243,8 @@ cudaError_t maxpool_s1_grouped(const PoolJob* jobs, int njobs, long long total, 
 // first producer past the dependency wait, 3 the first MMA issuer's first
 // K step ready, 4 its last MMA issued, 5 epilogue warp 2 started (after the
 // bias staging), 6 epilogue warp 2 done, 7 epilogue warp 6 done, 8 the
-// kernel's closing barrier passed (before tensor memory is freed).
+// kernel's closing barrier passed (before tensor memory is freed), 9 warp
+// 2's last accumulator ready.
 constexpr int kTraceEvents = 10;
 constexpr int kTraceCtas = 512;
 int tc_chunk_bytes(int Cp, int dt);

@@ -57,8 +57,11 @@ def test_trace_stamps_are_ordered_and_change_nothing():
         # issuer: first K step, last MMA; warp 2: epilogue start and end
         assert (B[:, 0] <= B[:, 1]).all() and (B[:, 1] <= B[:, 2]).all(), l
         assert (B[:, 3] <= B[:, 4]).all() and (B[:, 5] <= B[:, 6]).all(), l
-        # the closing barrier comes after every role's last stamp
+        # the closing barrier comes after every role's last stamp; warp 2's
+        # last accumulator is ready between its start and its end
         assert (B[:, 8] >= B[:, [1, 2, 4, 6, 7]].max(axis=1)).all(), l
+        if B[:, 9].any():                       # (the tap-pair first layer leaves it out)
+            assert (B[:, 9] >= B[:, 5]).all() and (B[:, 6] >= B[:, 9]).all(), l
         if prev_end is not None and not flow[l]:
             assert B[:, 2].min() >= prev_end, l  # programmatic launch waited for the whole previous grid
         prev_end = int(B[:, 8].max())
