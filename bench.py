@@ -603,6 +603,7 @@ def run_trace(torch, binding, wl, args):
     t0 = min(int(buf[l, buf[l, :, 0] > 0, 0].min()) for l in ran)
     layers, prev_end = [], None
     for l in ran:
+        has9 = bool((buf[l, buf[l, :, 0] > 0, 9] > 0).all())   # (the tap-pair first layer leaves it out)
         B = (buf[l, buf[l, :, 0] > 0] - t0) / 1000.0
         ep_end = np.maximum(B[:, 6], B[:, 7])
         r = {"layer": l, "ctas": int(B.shape[0]), "start": float(B[:, 0].min()),
@@ -611,8 +612,8 @@ def run_trace(torch, binding, wl, args):
              "tail": float(np.median(ep_end - B[:, 4])), "end": float(B[:, 8].max()),
              # the tail split at warp 2's last accumulator ready: the last MMAs
              # in the tensor pipe, then that tile's epilogue
-             "mma_drain": float(np.median(B[:, 9] - B[:, 4])) if B[:, 9].all() else None,
-             "last_epilogue": float(np.median(ep_end - B[:, 9])) if B[:, 9].all() else None,
+             "mma_drain": float(np.median(B[:, 9] - B[:, 4])) if has9 else None,
+             "last_epilogue": float(np.median(ep_end - B[:, 9])) if has9 else None,
              "straggle": float(B[:, 8].max() - np.median(B[:, 8]))}
         r["dep_to_end"] = r["end"] - r["dep"]
         r["gap"] = None if prev_end is None else r["dep"] - prev_end
