@@ -84,3 +84,44 @@ def test_dataflow_passes_bit_identical_to_whole_kernel_waits(tmp_path):
     for name in flow:
         assert np.isfinite(flow[name]).all(), name
         np.testing.assert_array_equal(flow[name], wait[name], err_msg=name)
+
+
+def test_dataflow_passes_of_two_handles_on_two_streams():
+    """Two handles, each on its own stream, issue passes without waiting for
+    each other, so their kernels share the SMs.  A layer that polls another
+    layer's counters only ever waits for kernels of its own stream that
+    started before it, so the interleaving can delay a pass but not change
+    it: every pass equals the same pass run alone."""
+    import torch
+    from paper_1811_03882_gb300 import binding
+    spec = synth.net_19conv()
+    batch, side = 4, 224
+    _, x, blob = synth.workload_net(spec, 75, batch, side, side)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    nets = [binding.Net(spec.layers, spec.in_c, prec="bf16", max_batch=batch, max_side=side,
+                        stream=st.cuda_stream) for st in streams]
+    try:
+        for n in nets:
+            n.load_weights(blob)
+        c, ho, wo = nets[0].output_shape(side, side)
+        d_in = torch.from_numpy(x).cuda()
+        # alone (each handle's plan and captured pass are built here, with
+        # nothing else running)
+        ref = torch.empty((batch, c, ho, wo), device="cuda")
+        for n in nets:
+            n.forward_device(d_in, batch, side, side, ref)
+            torch.cuda.synchronize()
+        outs = [[torch.full((batch, c, ho, wo), float("nan"), device="cuda") for _ in range(8)] for _ in nets]
+        torch.cuda.synchronize()
+        for r in range(8):
+            for k, n in enumerate(nets):
+                n.forward_device(d_in, batch, side, side, outs[k][r])
+        torch.cuda.synchronize()
+        want = ref.cpu().numpy()
+        for k in range(2):
+            for r in range(8):
+                np.testing.assert_array_equal(outs[k][r].cpu().numpy(), want, err_msg="handle %d pass %d" % (k, r))
+    finally:
+        for n in nets:
+            n.close()
+
