@@ -567,8 +567,13 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     const int pad = a.k >> 1;
     // A bytes per stage: one 128-row box, or three (TH + 2)-row boxes (tapm);
     // B: the N tile's box, or (CTA pairs) this CTA's half of it
-    const uint32_t a_box = kTapm ? (uint32_t)(a.TH + 2) * a.TW * a.chb : 128u * a.chb;
-    const uint32_t a_bytes = kTapm ? 3u * a_box : a_box, b_bytes = (uint32_t)(C2 ? BN / 2 : BN) * a.chb;
+    // (pair = 2: the tap-pair layer's stage is one box of (TH + 2) x (TW + 2)
+    // pixels, TW = 8, holding all nine taps' rows)
+    const bool box1 = kPair && a.pair == 2;
+    const uint32_t a_box = box1   ? (uint32_t)(a.TH + 2) * (a.TW + 2) * a.chb
+                           : kTapm ? (uint32_t)(a.TH + 2) * a.TW * a.chb
+                                   : 128u * a.chb;
+    const uint32_t a_bytes = (kTapm && !box1) ? 3u * a_box : a_box, b_bytes = (uint32_t)(C2 ? BN / 2 : BN) * a.chb;
 
     if (threadIdx.x == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
@@ -633,7 +638,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
             // 9 * Cp, past the weights' last column, so TMA fills it with zeros
             tc::mbar_expect_tx(rb, (uint32_t)kPairSlots * b_bytes);
             for (int s = 0; s < kPairSlots; ++s) {
-                const int tap = s < 9 ? (s % 3) * 3 + s / 3 : 9;
+                const int tap = s < 9 ? (box1 ? s : (s % 3) * 3 + s / 3) : 9;
                 tc::tma_load_2d(smem_u32(sBres + (size_t)s * b_bytes), &tmB, tap * a.Cp, nt_res, rb);
             }
         } else {
@@ -864,7 +869,9 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         else tc::tma_load_2d_pair(smem_u32(stg + a_bytes), &tmB, kcol, nt * BN + b_row0, fbc);
                     } else {
                         if (!pre_b) tc::mbar_expect_tx(fb, kBres ? a_bytes : st_tx);
-                        if (kTapm) {   // step = chunk ks of all nine taps: one box per tap column
+                        if (box1) {   // all nine taps' rows in one box
+                            tc::tma_load_4d(smem_u32(stg), &P->tmA, ks * a.cpc, x0, y0, img, fb);
+                        } else if (kTapm) {   // step = chunk ks of all nine taps: one box per tap column
                             for (int dx = 0; dx < 3; ++dx)
                                 tc::tma_load_4d(smem_u32(stg + dx * a_box), &P->tmA, ks * a.cpc, x0 + dx, y0, img,
                                                 fb);
@@ -995,13 +1002,18 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
                         // matrices of the second tap lie lbo bytes after the
                         // first's (for the tenth, zero-weight slot lbo is 0:
                         // the ninth tap's rows are read twice)
-                        const uint32_t row_b = (uint32_t)a.TW * 16u;
+                        // (one box: slot s holds tap (dy, dx) = (s / 3, s % 3) at
+                        // pixel dy * (TW + 2) + dx, a pixel row of the tile (8
+                        // pixels, one core matrix) every TW + 2 pixels)
+                        const uint32_t row_b = (uint32_t)a.TW * 16u, rowp = (uint32_t)(a.TW + 2) * 16u;
                         for (int j = 0; j < 5; ++j) {
                             const int s0 = 2 * j, s1 = 2 * j + 1;
-                            const uint32_t o0 = (uint32_t)(s0 / 3) * a_box + (uint32_t)(s0 % 3) * row_b;
-                            const uint32_t o1 =
-                                s1 < 9 ? (uint32_t)(s1 / 3) * a_box + (uint32_t)(s1 % 3) * row_b : o0;
-                            const uint64_t ad = tc::smem_desc_plain(smem_u32(stg + o0), o1 - o0, 128u);
+                            const uint32_t o0 = box1 ? (uint32_t)(s0 / 3) * rowp + (uint32_t)(s0 % 3) * 16u
+                                                     : (uint32_t)(s0 / 3) * a_box + (uint32_t)(s0 % 3) * row_b;
+                            const uint32_t o1 = s1 >= 9 ? o0
+                                                : box1  ? (uint32_t)(s1 / 3) * rowp + (uint32_t)(s1 % 3) * 16u
+                                                        : (uint32_t)(s1 / 3) * a_box + (uint32_t)(s1 % 3) * row_b;
+                            const uint64_t ad = tc::smem_desc_plain(smem_u32(stg + o0), o1 - o0, box1 ? rowp : 128u);
                             const uint64_t bd =
                                 tc::smem_desc_plain(smem_u32(sBres + (size_t)s0 * b_bytes), b_bytes, 128u);
                             tc::mma<DT, CG>(dtm, ad, bd, idesc, (!first || j != 0) ? 1u : 0u);
@@ -1789,7 +1801,11 @@ static size_t tc_avail(int mb) { return (mb == 2 ? kSmemLimit2 : kSmemLimit) - 1
 // weights) as fit beside the resident weights and the control block.  CTA
 // pairs (cg = 2): a stage holds half of the B box.
 static bool tc_geometry(int BN, int chb, int bres, int nk, int mb, int cg, TcArgs* g) {
-    const size_t a_bytes = g->tapm ? 3 * (size_t)(g->TH + 2) * g->TW * chb : 128 * (size_t)chb;
+    // (pair = 2: one box of (TH + 2) x (TW + 2) pixels, the stage rounded to
+    // 128 bytes for the copy's destination)
+    const size_t a_bytes = g->pair == 2 ? ((size_t)(g->TH + 2) * (g->TW + 2) * chb + 127) / 128 * 128
+                           : g->tapm    ? 3 * (size_t)(g->TH + 2) * g->TW * chb
+                                        : 128 * (size_t)chb;
     const size_t b_bytes = (size_t)(cg == 2 ? BN / 2 : BN) * chb;
     const size_t st = a_bytes + (bres ? 0 : b_bytes);
     const size_t bres_bytes = bres ? (size_t)(g->pair ? tc::kPairSlots : nk) * b_bytes : 0;
@@ -1834,6 +1850,7 @@ static cudaError_t launch_tc_bn(const CUtensorMap& tmB, const TcArgs& a0, int wo
     if (a.bres && (a.ksplit != 1 || workers % a.n_tiles != 0)) return cudaErrorInvalidValue;
     if (a.pair && (DT != DT_BF16 || !a.tapm || !a.bres || a.ksplit != 1 || a.k != 3 || a.chunks != 1 || a.kalt))
         return cudaErrorInvalidValue;
+    if (a.pair == 2 && (a.TW != 8 || a.TH != 16 || a.chb != 16)) return cudaErrorInvalidValue;   // one box a stage
     if (!tc_geometry(BN, a.chb, a.bres, a.k * a.k * a.chunks, MB, CG, &a)) return cudaErrorInvalidValue;
     if (a.ksplit < 1 || a.n_tiles < 1 || a.chunks < 1 || a.k < 1) return cudaErrorInvalidValue;
     // cluster split-K: clusters of ksplit CTAs (2, 4, 8 or 16, the last a

@@ -171,7 +171,7 @@ struct TcArgs {
     // tap-merged stages without swizzle, resident weights): each K = 16 MMA
     // covers two taps, its A descriptor's leading-dimension offset pointing
     // from the first tap's core matrices to the second's
-    int pair;
+    int pair;     // (2: the same with one box of (TH + 2) x (TW + 2) pixels a stage, TW = 8, TH = 16)
     Epilogue ep;
     int* err;     // bounded-wait failure code (0 = none)
     long long wait_limit;   // bound of each pipeline wait, clock64 cycles (<= 0: ~2 s)

@@ -595,6 +595,15 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
                 r.TW = 16;   // pair mode runs on tap-merged 16 x 8 stages
                 r.TH = 8;
             }
+            // pair mode on 8 x 16 tiles: one TMA box a stage (NET_L0_BOX1=0: three)
+            static const bool box1_on = [] {
+                const char* e = getenv("NET_L0_BOX1");
+                return !(e && atoi(e) == 0);
+            }();
+            if (L.pair && box1_on) {
+                r.TW = 8;
+                r.TH = 16;
+            }
             r.m_tiles = batch * cdiv(r.H, r.TH) * cdiv(r.W, r.TW);
             const int nk = KK * (L.in_cs / (tc_chunk_bytes(L.in_cs, L.in_dt) / (int)dt_size(L.in_dt)));
             tc_choose_split(r.m_tiles, ncols, nk, n->num_sms, &r.BN, &r.ksplit, 16,
@@ -665,8 +674,9 @@ net_status dn::get_plan(net* n, int batch, int h, int w, Plan** out) {
             (void)tiles;
             ConvProblem hp;
             std::memset(&hp, 0, sizeof hp);
-            cudaError_t e = tc_encode_act(&hp.tmA, n->act[r.in_buf], L.in_dt, batch, r.H, r.W, L.in_cs, r.TW,
-                                          r.tapm ? r.TH + 2 : r.TH);
+            const bool box1 = L.pair && r.TW == 8;   // one box of (TH + 2) x (TW + 2) pixels a stage
+            cudaError_t e = tc_encode_act(&hp.tmA, n->act[r.in_buf], L.in_dt, batch, r.H, r.W, L.in_cs,
+                                          box1 ? r.TW + 2 : r.TW, r.tapm ? r.TH + 2 : r.TH);
             if (e != cudaSuccess) return fail(NET_E_CUDA, "layer %d: activation tensor map: %s", l, cudaGetErrorString(e));
             hp.x = n->act[r.in_buf];
             hp.y = n->act[r.out_buf];
@@ -868,7 +878,7 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                 a.bres = r.bres;
                 a.kalt = r.kalt;
                 a.tapm = r.tapm;
-                a.pair = L.pair ? 1 : 0;
+                a.pair = L.pair ? (r.TW == 8 ? 2 : 1) : 0;
                 a.ep = ep;
                 a.err = n->err_dev;
                 int grid = r.grid, cg = r.cg;

@@ -12,7 +12,9 @@ tap-pair first layer instead of its specialised variant (NET_TC_SPEC=0), and
 split-K layers reduced through the workspace by a reduction launch instead
 of inside their clusters (NET_TC_XRED=0), and every layer behind the
 dependency wait on the whole previous kernel instead of the row-band
-dataflow (NET_TC_FLOW=0).
+dataflow (NET_TC_FLOW=0), and the tap-pair first layer on 16 x 8 tiles
+with three TMA boxes a stage instead of 8 x 16 tiles with one
+(NET_L0_BOX1=0).
 Every mode must give the oracle's answer within
 the BF16 budget and agree with the default mode to BF16 rounding; the
 19-conv network at 2 x 160 x 160 has layers with one and with several work
@@ -75,7 +77,7 @@ def test_launch_modes_match_oracle(tmp_path):
                       ("mb1", {"NET_TC_MB": "1"}), ("mb2", {"NET_TC_MB": "2"}),
                       ("pair", {"NET_TC_PAIR": "1"}), ("pair_no_kalt", {"NET_TC_PAIR": "1", "NET_TC_KALT": "0"}),
                       ("no_spec", {"NET_TC_SPEC": "0"}), ("no_xred", {"NET_TC_XRED": "0"}),
-                      ("no_flow", {"NET_TC_FLOW": "0"})):
+                      ("no_flow", {"NET_TC_FLOW": "0"}), ("l0_three_boxes", {"NET_L0_BOX1": "0"})):
         y = _run(tmp_path, name, env)
         assert np.isfinite(y).all(), name
         e = oracle.normwise_rel_err(y, ex)
@@ -95,5 +97,5 @@ def test_launch_modes_match_oracle(tmp_path):
     # (without the cluster reduction the planner prices K splits differently,
     # so the splits and their summation order may change: tests/test_gpu_xred.py
     # checks bit-identity on fixed plans)
-    for name in ("no_kalt", "no_tapm", "im2col", "mb1", "mb2", "pair", "no_xred"):
+    for name in ("no_kalt", "no_tapm", "im2col", "mb1", "mb2", "pair", "no_xred", "l0_three_boxes"):
         assert oracle.normwise_rel_err(ys[name], ys["default"]) <= 2e-2, name
