@@ -491,6 +491,16 @@ net_status net_launches(const net_t* net, uint64_t* total);
  * unaffected.  NET_E_INVAL for a layer that does not run on tensor cores. */
 net_status net_inject_device_fault(net_t* net, int layer);
 
+/* The same for the row-band dataflow (the paper has no counterpart): the
+ * handle's next fixed-batch pass of batch x h x w runs layer `layer`, which
+ * must wait on the previous layer's row bands in that pass (net_plan_flow),
+ * with a band count that is never reached and a ~1 ms bound on its waits:
+ * its producers' wait expires, the layer drains and returns, and the layers
+ * after it are released by its finished-warp count, so the pass ends at
+ * once with NET_E_DEVICE_WAIT (its output is not valid) and later passes are
+ * unaffected.  NET_E_INVAL for a layer that is not on the dataflow. */
+net_status net_inject_flow_fault(net_t* net, int layer, int batch, int h, int w);
+
 /* Canary guard regions, a debug aid for out-of-bounds writes; the paper
  * has no counterpart.  With NET_GUARD=1 in the environment when the
  * process first allocates, every device buffer the library allocates

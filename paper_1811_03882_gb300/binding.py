@@ -127,6 +127,7 @@ _SIGS = {
     "net_trace": [ctypes.c_void_p, ctypes.c_int],
     "net_trace_read": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t],
     "net_inject_device_fault": [ctypes.c_void_p, ctypes.c_int],
+    "net_inject_flow_fault": [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "net_guard_check": [ctypes.c_void_p, ctypes.c_void_p],
     "net_guard_poke": [ctypes.c_uint64],
     "net_set_region": [ctypes.c_void_p, ctypes.POINTER(net_region)],
@@ -495,6 +496,11 @@ class Net:
     def inject_device_fault(self, layer: int):
         """Test hook: the next fixed-batch pass faults layer `layer` (see net.h)."""
         check(lib().net_inject_device_fault(self.h, layer))
+
+    def inject_flow_fault(self, layer: int, batch: int, h: int, w: int):
+        """Test hook: the next batch x h x w pass makes layer `layer`'s band
+        wait expire (see net.h)."""
+        check(lib().net_inject_flow_fault(self.h, layer, batch, h, w))
 
     def launches(self) -> int:
         t = ctypes.c_uint64()

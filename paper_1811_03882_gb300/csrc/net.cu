@@ -920,6 +920,14 @@ net_status dn::enqueue_forward(net* n, const float* d_in, int batch, int h, int 
                         }
                     }
                 }
+                if (flow_ok && l == n->flow_fault_layer && dep[l]) {
+                    // net_inject_flow_fault: a band count the previous layer never
+                    // reaches, no whole-layer shortcut and a ~1 ms bound, once
+                    a.dep_target += 1 << 28;
+                    a.dep_done = nullptr;
+                    a.wait_limit = 2000000;
+                    n->flow_fault_layer = -1;
+                }
                 if (l == n->fault_layer) {
                     // net_inject_device_fault: a ~1 ms bound (clock64 cycles at
                     // ~2 GHz) and one K step withheld by a producer, once (a
@@ -995,7 +1003,7 @@ void net::graphs_clear() {
 }
 
 net_status dn::run_forward(net* n, const float* d_in, int batch, int h, int w, float* d_out) {
-    if (!n->use_graphs || n->fault_layer >= 0) {   // an injected fault is not baked into a graph
+    if (!n->use_graphs || n->fault_layer >= 0 || n->flow_fault_layer >= 0) {   // an injected fault is not baked into a graph
         net_status s = enqueue_forward(n, d_in, batch, h, w, d_out, nullptr, false, nullptr);
         if (s == NET_OK) n->launches += n->pending;
         return s;
@@ -1065,6 +1073,23 @@ extern "C" net_status net_inject_device_fault(net_t* n, int layer) {
     if (layer < 0 || layer >= (int)n->L.size()) return fail(NET_E_INVAL, "layer %d out of range", layer);
     if (n->L[layer].engine != ENG_TC) return fail(NET_E_INVAL, "layer %d runs on CUDA cores", layer);
     n->fault_layer = layer;
+    return NET_OK;
+}
+
+extern "C" net_status net_inject_flow_fault(net_t* n, int layer, int batch, int h, int w) {
+    if (!n) return fail(NET_E_INVAL, "NULL argument");
+    if (layer < 0 || layer >= (int)n->L.size()) return fail(NET_E_INVAL, "layer %d out of range", layer);
+    net_status s = check_shape(n, batch, h, w);
+    if (s != NET_OK) return s;
+    CK(cudaSetDevice(n->device));
+    Plan* P = nullptr;
+    s = get_plan(n, batch, h, w, &P);
+    if (s != NET_OK) return s;
+    std::vector<char> d;
+    std::vector<int> wpt;
+    if (!flow_layers(n, P, d, wpt) || !d[layer])
+        return fail(NET_E_INVAL, "layer %d does not wait on row bands in a %d x %d x %d pass", layer, batch, h, w);
+    n->flow_fault_layer = layer;
     return NET_OK;
 }
 

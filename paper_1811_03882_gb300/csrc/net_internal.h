@@ -172,6 +172,7 @@ struct net {
     int* err_host = nullptr;   // mapped pinned: bounded device waits that expired
     int* err_dev = nullptr;
     int fault_layer = -1;      // net_inject_device_fault: layer of the next pass to fault (tests)
+    int flow_fault_layer = -1; // net_inject_flow_fault: layer of the next pass whose band wait expires (tests)
     dn::UnevenState* uneven = nullptr;
     dn::RegionState* region = nullptr;   // detection post-processing (net_set_region)
     dn::NightState* night = nullptr;     // nightmare pass buffers (first net_nightmare_* call)

@@ -47,3 +47,35 @@ def test_expired_device_wait_is_reported_and_handle_recovers(layer):
         with pytest.raises(binding.NetError) as e:
             n32.inject_device_fault(layer)       # CUDA-core layers have no such waits
         assert e.value.status == binding.NET_E_INVAL
+
+
+def test_expired_band_wait_is_reported_and_pass_ends_at_once():
+    """A layer on the row-band dataflow whose band wait expires (a count the
+    previous layer never reaches, ~1 ms bound) aborts like any other wait;
+    the layers after it, which wait on its bands, are released by its
+    finished-warp count instead of waiting out their own bounds, so the pass
+    ends within a fraction of a second; the next passes are unaffected."""
+    import time
+    import torch
+    from paper_1811_03882_gb300 import binding
+    spec = synth.net_19conv()
+    _, x, blob = synth.workload_net(spec, 62, 2, 64, 64)
+    with make_net(spec, prec="bf16", max_batch=2, max_side=64) as net:
+        net.load_weights(blob)
+        y0 = net.forward(x)
+        flow = net.plan_flow(2, 64, 64)
+        layers = [l for l, f in enumerate(flow) if f]
+        assert layers, flow
+        with pytest.raises(binding.NetError):
+            net.inject_flow_fault(0, 2, 64, 64)   # the first layer never waits on bands
+        for layer in (layers[0], layers[-1]):
+            net.inject_flow_fault(layer, 2, 64, 64)
+            t0 = time.perf_counter()
+            with pytest.raises(binding.NetError) as e:
+                net.forward(x)
+            assert time.perf_counter() - t0 < 0.5, layer
+            assert e.value.status == binding.NET_E_DEVICE_WAIT
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(net.forward(x), y0)
+            np.testing.assert_array_equal(net.forward(x), y0)
+
